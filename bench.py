@@ -1,0 +1,370 @@
+"""Benchmark: time-to-rtol 1e-6 and Mpts*iter/s of the preconditioned GMRES Helmholtz solve at n = 256^3.
+
+One step = the modified right-hand side (helm_build_rhs) plus one full solve to rel-res 1e-6
+(helm_gmres_solve from x0 = 0) of the sixth-order scheme on a seeded 20-bump medium at ~10 points per
+wavelength (seeds: medium 3, angle 4), inputs resident in HBM.  The context set-up (coefficient fields,
+FP64 1D eigendecompositions) is done once before the timed region and reported as setup_s.
+Value = n^3 * (inner iterations) / seconds / 1e6, whole job over all ranks (replicas at N > 1).
+
+--impl reference times the CPU oracle (complex128 NumPy, oracle/) on a bounded sample of the same
+workload: it is the reference arm (the paper's own code is not available; its numbers are MATLAB on
+one M3 Max core and are quoted in the benchmark spec as context).
+"""
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "time-to-rtol 1e-6 (s) & Mpts·iter/s at n=256³; mixed/learned vs plain EigT"
+UNIT = "Mpts·iter/s"
+PREC_NAMES = {"fp32": 0, "tf32": 1, "3xtf32": 2}
+CLASSES = ["stencil", "xpass", "ypass", "zsolve", "dots", "update", "small", "combine", "residual", "other"]
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=3)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--n", type=int, default=256)
+    p.add_argument("--order", type=int, default=6)
+    p.add_argument("--precision", default=os.environ.get("HELM_BENCH_PRECISION", "auto"))
+    p.add_argument("--plain", type=int, default=1, help="also time plain complex64 EigT-GMRES (FP32 transforms)")
+    p.add_argument("--restart", type=int, default=30)
+    p.add_argument("--rtol", type=float, default=1e-6)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--e2e", type=int, default=1)
+    return p.parse_args()
+
+
+# ---- clocks sampled during the timed region ---------------------------------------------------
+class ClockSampler:
+    def __init__(self, index):
+        self.index = index
+        self.samples = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + q,
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+
+        def rd():
+            for line in self.proc.stdout:
+                self.samples.append([s.strip() for s in line.split(",")])
+        self.thread = threading.Thread(target=rd, daemon=True)
+        self.thread.start()
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for s in self.samples:
+            try:
+                sm.append(float(s[1]))
+                mx = float(s[2])
+                for nm, v in zip(names, s[5:9]):
+                    if v.strip().lower() in ("active", "0x1", "1"):
+                        reasons.add(nm)
+            except Exception:
+                pass
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---- per-class algorithmic work -----------------------------------------------------------------
+def algorithmic(n, order, cycles_iters):
+    """Bytes (and flops) the kernels of one solve must move, by class (the figures the design doc states)."""
+    pts = n ** 3
+    out = {}
+    st_b = (24 if order == 4 else 56) * pts
+    its = sum(cycles_iters)
+    out["stencil"] = {"bytes": st_b * its, "launches": its}
+    out["xpass"] = {"bytes": 16 * pts * 2 * its, "flops": 8 * n * pts * 2 * its, "launches": 2 * its}
+    out["ypass"] = {"bytes": 16 * pts * 2 * its, "flops": 8 * n * pts * 2 * its, "launches": 2 * its}
+    out["zsolve"] = {"bytes": 16 * pts * its, "launches": its}
+    db = ub = 0
+    for k in cycles_iters:
+        for j in range(k):
+            db += 8 * (j + 2) * pts        # j+1 basis vectors + w
+            ub += 8 * (j + 3) * pts        # j+1 basis vectors + w read, w written
+    out["dots"] = {"bytes": db, "launches": its}
+    out["update"] = {"bytes": ub, "launches": its}
+    return out
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            d = json.load(fh)
+        return d, "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "sm_max_mhz": 2070.0}, \
+            "fallback"
+
+
+def roofline(prof_ms, prof_launch, alg, precision, order):
+    pk, src = peaks()
+    # dominant kernel class by measured time
+    cls = max((c for c in alg if prof_launch.get(c, 0) > 0), key=lambda c: prof_ms.get(c, 0.0))
+    launches = prof_launch[cls]
+    avg_s = prof_ms[cls] / launches / 1e3
+    a = alg[cls]
+    if cls in ("xpass", "ypass") and precision == "fp32":
+        peak = 152 * 128 * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12    # FP32 FFMA lanes x clock
+        ach = a["flops"] / a["launches"] / avg_s / 1e12
+        return {"kernel": cls, "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                "frac": ach / peak, "traffic": None, "peak_source": "152 SM x 128 FP32 lanes x 2 x max clock"}
+    if cls in ("xpass", "ypass"):
+        peak = pk["bf16_tflops_sustained"] * (1.1 / 2.25)                      # TF32 = BF16 x nominal ratio
+        ach = a["flops"] / a["launches"] / avg_s / 1e12
+        return {"kernel": cls, "bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                "frac": ach / peak, "traffic": None, "peak_source": src + " bf16 sustained x 1.1/2.25 (TF32)"}
+    peak = pk["hbm_gbs"]
+    ach = a["bytes"] / a["launches"] / avg_s / 1e9
+    return {"kernel": cls, "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+            "traffic": None, "peak_source": src + " hbm_gbs"}
+
+
+def cycles_of(info, m):
+    its = info.iterations
+    out = []
+    while its > 0:
+        out.append(min(m, its))
+        its -= m
+    return out
+
+
+# ---- CPU oracle (reference arm and cpu_baseline) ------------------------------------------------
+def oracle_sample(n, order, m, iters=1):
+    """Time `iters` inner iterations of the oracle's GMRES on the full workload (the set-up of its
+    coefficient fields and eigendecompositions excluded).  Returns (Mpts*iter/s, seconds, cores)."""
+    import numpy as np
+
+    from oracle.eigt import EigT
+    from oracle.gmres import gmres
+    from oracle.grid import Grid
+    from oracle.operators import Operator
+    from oracle.rhs import rhs6_sampled
+    from paper_2602_07711_gb300 import media
+    k2, f, k0 = media.bumps(n, 3, 4)
+    g = Grid(n, n, n, staggered=True)
+    A = Operator(g, k2, k0, order)
+    e = EigT(g, k0)
+    F = rhs6_sampled(f, k2, A.dk2, True, g.h) if order == 6 else f
+    t = time.perf_counter()
+    _, info = gmres(A, e.apply_Minv, F, m=m, rtol=1e-30, max_it=iters)
+    dt = time.perf_counter() - t
+    cores = os.cpu_count()
+    return n ** 3 * info["iterations"] / dt / 1e6, dt, cores
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    for _ in range(args.warmup if args.warmup < 1 else 1):
+        pass
+    vals, secs = [], []
+    for _ in range(args.steps):
+        v, dt, cores = oracle_sample(args.n, args.order, args.restart, iters=1)
+        vals.append(v)
+        secs.append(dt)
+    value = sum(vals) / len(vals)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(secs) / len(secs),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
+            "data": "synthetic", "config": {"workload": "bumps20-n%d-order%d-seed3-angle4" % (args.n, args.order)},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": "1 inner GMRES(30)+EigT iteration of the complex128 oracle per step on the "
+                                       "full %d^3 workload (set-up excluded)" % args.n},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---- our arm ------------------------------------------------------------------------------------
+def run_ours(args, rank, world, local):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_2602_07711_gb300 import helm, media
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    n, order = args.n, args.order
+    precision = args.precision
+    if precision == "auto":
+        precision = "fp32"
+    k2, f, k0 = media.bumps(n, 3, 4, device=dev, as_numpy=False)
+    stream = torch.cuda.current_stream()
+    flexible = precision != "fp32"
+
+    def make(prec, flex):
+        return helm.Solver((n, n, n), k2, k0, order=order, precision=PREC_NAMES[prec], restart=args.restart,
+                           max_iter=300, rtol=args.rtol, flexible=flex)
+
+    t0 = time.perf_counter()
+    S = make(precision, flexible)
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t0
+    F = S.build_rhs(f)
+    x = torch.zeros_like(F)
+
+    def step(solver):
+        Fs = solver.build_rhs(f)
+        x.zero_()
+        _, info = solver.solve(Fs, x0=x)
+        return info
+
+    for _ in range(args.warmup):
+        step(S)
+    lib = helm.lib()
+    lib.helm_profile.argtypes = [helm.C.c_void_p, helm.C.c_int]
+    lib.helm_profile_read.argtypes = [helm.C.c_void_p, helm.C.c_void_p, helm.C.c_void_p, helm.C.c_int, helm.C.c_int]
+    lib.helm_profile(S.ctx, 1)
+    ms_arr = (helm.C.c_double * 10)()
+    ln_arr = (helm.C.c_longlong * 10)()
+    lib.helm_profile_read(S.ctx, ms_arr, ln_arr, 10, 1)
+    clocks = ClockSampler(local)
+    clocks.start()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    infos = [step(S) for _ in range(args.steps)]
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    elapsed = ev0.elapsed_time(ev1) / 1e3
+    lib.helm_profile_read(S.ctx, ms_arr, ln_arr, 10, 1)
+    lib.helm_profile(S.ctx, 0)
+    prof_ms = {c: ms_arr[i] for i, c in enumerate(CLASSES)}
+    prof_ln = {c: ln_arr[i] for i, c in enumerate(CLASSES)}
+    if world > 1:
+        t = torch.tensor([elapsed], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed = float(t.item())
+    its = sum(i.iterations for i in infos)
+    pts = n ** 3
+    value = pts * its / elapsed / 1e6 * world
+    # algorithmic bytes of the timed solves
+    alg_tot = {}
+    for i in infos:
+        for c, a in algorithmic(n, order, cycles_of(i, args.restart)).items():
+            t_ = alg_tot.setdefault(c, {"bytes": 0, "flops": 0, "launches": 0})
+            for k_ in a:
+                t_[k_] += a[k_]
+    rl = roofline(prof_ms, prof_ln, alg_tot, precision, order)
+    kernel_table = {c: {"ms": round(prof_ms[c], 3), "launches": prof_ln[c]} for c in CLASSES if prof_ln[c]}
+    # end to end through the C-ABI with host buffers (pinned), copies inside the timed region
+    e2e = None
+    if args.e2e:
+        Fh = torch.empty(F.shape, dtype=F.dtype).pin_memory()
+        Fh.copy_(S.build_rhs(f))
+        xh = torch.zeros(F.shape, dtype=F.dtype).pin_memory()
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        e_its = 0
+        for _ in range(max(1, args.steps)):
+            xh.zero_()
+            code, inf = helm.helm_gmres_solve(S.ctx, Fh, xh)
+            e_its += inf.iterations
+        torch.cuda.synchronize()
+        e_dt = time.perf_counter() - t1
+        e2e = {"value": pts * e_its / e_dt / 1e6 * world, "unit": UNIT,
+               "h2d_bytes_per_step": 2 * 16 * pts, "d2h_bytes_per_step": 16 * pts,
+               "time_to_rtol_s": e_dt / max(1, args.steps)}
+    # plain complex64 EigT-GMRES for comparison
+    plain = None
+    if args.plain and precision != "fp32":
+        P = make("fp32", False)
+        step(P)
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        pi = step(P)
+        torch.cuda.synchronize()
+        pdt = time.perf_counter() - t2
+        plain = {"time_to_rtol_s": pdt, "iterations": pi.iterations, "Mpts_iter_s": pts * pi.iterations / pdt / 1e6,
+                 "relres_true": pi.relres_true}
+        P.close()
+    # CPU oracle sample (rank 0, N = 1)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, dt, cores = oracle_sample(n, order, args.restart, iters=1)
+        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": "1 inner GMRES(30)+EigT iteration of the complex128 oracle on the full %d^3 workload "
+                         "(%.1f s; set-up excluded)" % (n, dt)}
+    launches = int(sum(prof_ln.values()))
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "c64",
+            "data": "synthetic",
+            "config": {"workload": "bumps20-n%d-order%d-seed3-angle4" % (n, order), "n": n, "order": order,
+                       "k0": k0, "precond": "EigT", "precision": precision,
+                       "krylov": ("FGMRES(%d)" if flexible else "GMRES(%d)") % args.restart, "rtol": args.rtol,
+                       "l2": "inputs larger than L2 (134 MB per complex64 vector)",
+                       "parallelism": "replicas" if world > 1 else "single"},
+            "time_to_rtol_s": elapsed / args.steps,
+            "iterations": [i.iterations for i in infos],
+            "relres_true": [i.relres_true for i in infos],
+            "setup_s": setup_s,
+            "roofline": rl,
+            "kernels": kernel_table,
+            "gpu_launches": launches,
+            "clocks": clk,
+            "e2e": e2e,
+            "plain_eigt": plain,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    S.close()
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    run_ours(args, rank, world, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

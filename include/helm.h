@@ -1,0 +1,163 @@
+/*
+ * helm.h - C-ABI of the GB300 (sm_103a) solver for the 3D Helmholtz equation with Sommerfeld
+ * absorbing boundaries, preconditioned by the exact inverse of a second-order operator that includes
+ * the absorbing boundary (EigT / PFFT), inside restarted (flexible) GMRES.
+ *
+ * Paper: Gryazin, Gonzales, Li, "High-Resolution Solvers for 3D Helmholtz Scattering Problems Using
+ * PFFT and Eigenvector-Based Preconditioning", arXiv 2602.07711.
+ *
+ * Conventions shared by every entry point
+ *   - Grid functions are complex arrays indexed [l][j][i] (z, y, x) with x fastest: the slice ordering
+ *     U_l of Sec. 4.1.  complex64 = interleaved float (re, im); complex128 = interleaved double.
+ *   - Buffers passed to a call belong to the caller.  A pointer may be host or device memory where a
+ *     comment says "host or device"; the library asks the CUDA runtime which one it is.  Everywhere else
+ *     it must be device memory.  The context (helm_ctx) owns its device workspace; helm_destroy frees it.
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Calls are stream-ordered and return
+ *     before the GPU work finishes, except helm_setup and helm_gmres_solve, which synchronise `stream`.
+ *   - Errors are returned as helm_status; the library never aborts or traps.  Device-side loops have
+ *     iteration caps and report through a status word, read back by the synchronising calls.
+ *   - A context must not be used from two host threads at once.  There is no global mutable state.
+ */
+#ifndef HELM_H
+#define HELM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct helm_ctx helm_ctx;
+
+typedef enum {
+    HELM_OK = 0,
+    HELM_ERR_ARG = 1,            /* invalid argument (sizes, null pointers, unsupported combination)   */
+    HELM_ERR_CUDA = 2,           /* a CUDA runtime/driver call failed                                   */
+    HELM_ERR_NOMEM = 3,          /* device allocation failed                                            */
+    HELM_ERR_EIG = 4,            /* 1D eigendecomposition failed its residual / orthogonality check     */
+    HELM_ERR_PIVOT = 5,          /* a tridiagonal pivot fell below 1e-30 in magnitude                   */
+    HELM_ERR_NAN = 6,            /* NaN or Inf met in a norm or a Hessenberg entry                      */
+    HELM_ERR_BREAKDOWN = 7,      /* Arnoldi breakdown h_{j+1,j} = 0 before convergence                  */
+    HELM_ERR_NOT_CONVERGED = 8,  /* max_iter reached; x holds the last iterate                         */
+    HELM_ERR_ITER_LIMIT = 9,     /* a device wait exceeded its iteration cap                           */
+    HELM_ERR_UNSUPPORTED = 10    /* configuration not built (see the comment of the option)             */
+} helm_status;
+
+/* Grid (Sec. 2.1 and Sec. 5.2).  N_x x N_y x N_z unknowns on [0,lx] x [0,ly] x [0,lz].
+ * staggered = 1: nodes at h/2 + j h, h = L/N, ghosts eliminated by Eq. D_bc (the grid of Sec. 5.2).
+ * staggered = 0: collocated nodes (i-1) h, h = L/(N-1); not built on the GPU (HELM_ERR_UNSUPPORTED). */
+typedef struct {
+    int nx, ny, nz;
+    double lx, ly, lz;
+    int staggered;
+} helm_grid;
+
+enum { HELM_PRECOND_NONE = 0, HELM_PRECOND_EIGT = 1, HELM_PRECOND_PFFT = 2 };
+
+/* Arithmetic of the eigenvector transforms (EigT steps 2 and 4).  The stencil, the z-solves and the
+ * Krylov vectors are complex64 in every mode; the Hessenberg/Givens update, the 1D eigensetup and the
+ * true residual are FP64 in every mode.
+ *   HELM_PREC_FP32    complex64 on the CUDA cores (FFMA), the "plain complex64" method
+ *   HELM_PREC_TF32    tcgen05 tensor cores, TF32 operands, FP32 accumulation in TMEM (one product)
+ *   HELM_PREC_3XTF32  tcgen05, split TF32 (hi*hi + hi*lo + lo*hi), about FP32 accuracy               */
+enum { HELM_PREC_FP32 = 0, HELM_PREC_TF32 = 1, HELM_PREC_3XTF32 = 2 };
+
+typedef struct {
+    int order;       /* 2, 4 (Eq. scheme4, any h_x, h_y, h_z) or 6 (Eq. scheme6, needs h_x = h_y = h_z)  */
+    int precond;     /* HELM_PRECOND_*                                                                    */
+    int precision;   /* HELM_PREC_*                                                                       */
+    int restart;     /* GMRES(m) restart length m, 1..64                                                  */
+    int max_iter;    /* cap on inner iterations N0                                                        */
+    double rtol;     /* stop when ||F - A U||_2 / ||F - A U^0||_2 <= rtol (rel-res of Sec. 5.1)            */
+    int flexible;    /* 1 = flexible GMRES (stores z_j = M^-1 v_j), 0 = right-preconditioned GMRES        */
+    int reorth;      /* 1 = classical Gram-Schmidt twice (CGS2), 0 = once                                 */
+} helm_options;
+
+typedef struct {
+    int status;            /* helm_status of the solve                                          */
+    int iterations;        /* N0: inner Arnoldi steps                                           */
+    int restarts;          /* completed cycles                                                  */
+    int reserved;
+    double relres_true;    /* FP64 ||F - A U|| / ||F - A U^0|| at exit                           */
+    double relres_est;     /* Givens estimate at the last step                                   */
+    double beta0;          /* ||F - A U^0||_2                                                    */
+    double seconds;        /* host wall time of the call                                         */
+} helm_solve_info;
+
+/* Data type selector for helm_apply_A. */
+enum { HELM_C64 = 0, HELM_C128 = 1 };
+
+/* helm_setup - build a solver context.
+ *   grid     grid of the problem (Sec. 2.1 / Sec. 5.2); every N >= 4; N_x even for the tensor-core modes.
+ *   k2       k^2(x,y,z) samples, complex128, N_x*N_y*N_z, host or device (Eq. problem).
+ *   k0       background wavenumber of the ABC and of the preconditioner, real (Eq. background).
+ *   k0z2     optional depth profile k0^2(z_l), N_z doubles (host), for K_z of Sec. 4.1; NULL = k0^2.
+ *   opt      scheme order, preconditioner, precision, GMRES parameters.
+ *   stream   cudaStream_t used for the set-up work; synchronised before return.
+ *   out      receives the context.
+ * Work: coefficient fields of Eq. scheme6 (fourth-order differences of k^2), the 1D eigendecompositions
+ * Lbar_nu = V D V^-1 for nu = x, y (EigT step 1) on the GPU in FP64, checked by residual and by V^-1 V = I.
+ * Errors: HELM_ERR_ARG, HELM_ERR_UNSUPPORTED, HELM_ERR_NOMEM, HELM_ERR_EIG, HELM_ERR_CUDA; *out = NULL then. */
+helm_status helm_setup(const helm_grid* grid, const void* k2, double k0, const double* k0z2,
+                       const helm_options* opt, void* stream, helm_ctx** out);
+
+/* helm_build_rhs - modified right-hand side F of the scheme from samples of f (Eqs. scheme4, scheme6).
+ *   f  complex128 samples, host or device;  F  complex128 device output.  Order 2: F = f.
+ * Derivatives of f and k^2 are sampled-data readings (fourth-order differences, mirror extension). */
+helm_status helm_build_rhs(helm_ctx* ctx, const void* f, void* F, void* stream);
+
+/* helm_apply_A - y = A x, the high-order operator with the ABC ghosts eliminated (Eqs. scheme4/scheme6,
+ * Eq. D_bc).  dtype HELM_C64: complex64 arithmetic; HELM_C128: complex128 arithmetic.  x, y device. */
+helm_status helm_apply_A(helm_ctx* ctx, const void* x, void* y, int dtype, void* stream);
+
+/* helm_apply_precond - z = M^-1 r = h_z^2 A_p^-1 r, complex64 device buffers (may alias).  A_p is the
+ * second-order constant-k0 operator with the same ABC (Kronecker form of Sec. 4.1); EigT (Eq. EIG_SOLVER)
+ * or PFFT (Eq. PFFT_SOLVER) per the context's options, transforms in the context's precision. */
+helm_status helm_apply_precond(helm_ctx* ctx, const void* r, void* z, void* stream);
+
+/* helm_precond_step - one step of EigT on complex64 device buffers, for step-by-step checks:
+ *   step 1: Ybar_l = V_y^-1 Y_l V_x^-T for every slice (forward transform, EigT step 2)
+ *   step 2: the N_x N_y tridiagonal z-solves of Eq. Indep_precond_system (EigT step 3); in may equal out
+ *   step 3: U_l = V_y Ubar_l V_x^T (inverse transform, EigT step 4)                                  */
+helm_status helm_precond_step(helm_ctx* ctx, int step, const void* in, void* out, void* stream);
+
+/* helm_get_eig - copy the FP64 1D eigendecomposition of axis 0 (x) or 1 (y) to host memory:
+ * D (N complex128), V and Vinv (N*N complex128, row-major [row][col]).  Any pointer may be NULL. */
+helm_status helm_get_eig(helm_ctx* ctx, int axis, void* D, void* V, void* Vinv);
+
+/* helm_gmres_solve - solve A x = b by restarted right-preconditioned (or flexible) GMRES(m).
+ *   b     complex128 right-hand side F (from helm_build_rhs), host or device.
+ *   x     complex128, host or device; on entry x^0, on exit the iterate (also on NOT_CONVERGED).
+ *   info  filled on return (may be NULL).
+ * Krylov vectors are complex64; inner products accumulate in FP64; the Hessenberg matrix and Givens
+ * rotations are FP64 on the GPU; x accumulates in complex128; the stopping test uses the FP64 true
+ * residual.  Synchronises `stream`. */
+helm_status helm_gmres_solve(helm_ctx* ctx, const void* b, void* x, helm_solve_info* info, void* stream);
+
+/* helm_profile - enable (1) or disable (0) per-kernel timing on this context: CUDA events are recorded
+ * on the launch stream around every kernel launch of the solver (adds no synchronisation).  The first
+ * call allocates the event pool (host-side cost only). */
+helm_status helm_profile(helm_ctx* ctx, int enable);
+
+/* helm_profile_read - accumulated milliseconds and launch counts per kernel class since the last reset,
+ * in the order: stencil (complex64 A), x-pass, y-pass, z-solve, Arnoldi dots, Arnoldi update,
+ * small FP64 kernels (reductions, Givens, least squares), solution update, FP64 true residual, other.
+ *   ms, launches  host arrays of n entries (either may be NULL);  reset != 0 clears the counters.
+ * Synchronises on the recorded events. */
+helm_status helm_profile_read(helm_ctx* ctx, double* ms, long long* launches, int n, int reset);
+
+/* helm_destroy - free the context and its device workspace (NULL is a no-op). */
+void helm_destroy(helm_ctx* ctx);
+
+/* helm_status_str - static English text of a status code. */
+const char* helm_status_str(int status);
+
+/* helm_version - library version string. */
+const char* helm_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HELM_H */

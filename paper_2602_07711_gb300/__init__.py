@@ -1,0 +1,12 @@
+"""GB300 (sm_103a) solver for the 3D Helmholtz equation with Sommerfeld absorbing boundaries:
+compact 4th/6th-order schemes, EigT (and PFFT) preconditioners that include the absorbing boundary,
+restarted/flexible GMRES (arXiv 2602.07711).
+
+The compute path is the C-ABI library libhelm.so (include/helm.h), built in-tree by build.py.
+This package only marshals arguments (torch tensors, streams) into that library.
+"""
+from .helm import (HELM_C64, HELM_C128, HELM_PREC_3XTF32, HELM_PREC_FP32, HELM_PREC_TF32, HELM_PRECOND_EIGT,
+                   HELM_PRECOND_NONE, HELM_PRECOND_PFFT, HelmError, Solver, lib, library_path)
+
+__all__ = ["Solver", "HelmError", "lib", "library_path", "HELM_C64", "HELM_C128", "HELM_PREC_FP32", "HELM_PREC_TF32",
+           "HELM_PREC_3XTF32", "HELM_PRECOND_NONE", "HELM_PRECOND_EIGT", "HELM_PRECOND_PFFT"]

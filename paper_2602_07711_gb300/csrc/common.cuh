@@ -1,0 +1,154 @@
+// Internal declarations shared by the translation units of libhelm (not part of the C-ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cstddef>
+#include "../../include/helm.h"
+
+#define HELM_CUDA_TRY(expr)                                          \
+    do {                                                             \
+        cudaError_t e__ = (expr);                                    \
+        if (e__ != cudaSuccess) return helm_fail_cuda(e__, #expr);   \
+    } while (0)
+
+helm_status helm_fail_cuda(cudaError_t e, const char* what);
+
+// Device status word bits (OR-ed by kernels, read by synchronising calls).
+enum : unsigned {
+    HELM_DEV_PIVOT = 1u,      // tiny tridiagonal pivot
+    HELM_DEV_NAN = 2u,        // NaN/Inf in a reduction
+    HELM_DEV_WAIT = 4u,       // a bounded device wait expired
+    HELM_DEV_EIG = 8u         // eigen-setup check failed
+};
+
+// ---- complex helpers -------------------------------------------------------------------------
+template <typename T> struct cplx;
+template <> struct cplx<float> { typedef float2 t; };
+template <> struct cplx<double> { typedef double2 t; };
+
+__host__ __device__ inline float2 mk(float a, float b) { return make_float2(a, b); }
+__host__ __device__ inline double2 mk(double a, double b) { return make_double2(a, b); }
+template <typename C> __host__ __device__ inline C cadd(C a, C b) { a.x += b.x; a.y += b.y; return a; }
+template <typename C> __host__ __device__ inline C csub(C a, C b) { a.x -= b.x; a.y -= b.y; return a; }
+template <typename C, typename R> __host__ __device__ inline C cscale(C a, R s) { a.x *= s; a.y *= s; return a; }
+template <typename C> __host__ __device__ inline C cmul(C a, C b) {
+    C r; r.x = a.x * b.x - a.y * b.y; r.y = a.x * b.y + a.y * b.x; return r;
+}
+template <typename C> __host__ __device__ inline C cconjmul(C a, C b) {  // conj(a) * b
+    C r; r.x = a.x * b.x + a.y * b.y; r.y = a.x * b.y - a.y * b.x; return r;
+}
+template <typename C> __host__ __device__ inline C cfma(C a, C b, C c) {  // a*b + c
+    c.x = fma(a.x, b.x, c.x); c.x = fma(-a.y, b.y, c.x);
+    c.y = fma(a.x, b.y, c.y); c.y = fma(a.y, b.x, c.y);
+    return c;
+}
+template <typename C> __host__ __device__ inline C cdiv(C a, C b) {
+    // Smith's algorithm
+    C r;
+    if (fabs(b.x) >= fabs(b.y)) {
+        auto t = b.y / b.x; auto d = b.x + b.y * t;
+        r.x = (a.x + a.y * t) / d; r.y = (a.y - a.x * t) / d;
+    } else {
+        auto t = b.x / b.y; auto d = b.x * t + b.y;
+        r.x = (a.x * t + a.y) / d; r.y = (a.y * t - a.x) / d;
+    }
+    return r;
+}
+template <typename C> __host__ __device__ inline double cabs2(C a) { return (double)a.x * a.x + (double)a.y * a.y; }
+
+// ---- stencil coefficient bundle (passed by value to kernels) --------------------------------
+template <typename R>
+struct StencilParams {
+    int nx, ny, nz;
+    R hx, hy, hz;
+    typename cplx<R>::t gx, gy, gz;      // ghost factors (Eq. D_bc)
+    const typename cplx<R>::t* k2;       // k^2 samples
+    const typename cplx<R>::t* dk2[3];   // (k^2)_x, (k^2)_y, (k^2)_z  (order 6)
+    const typename cplx<R>::t* G;        // lap(k^2) - k^4             (order 6)
+};
+
+// ---- the context -----------------------------------------------------------------------------
+struct KrylovWork;
+
+// Optional per-kernel timing: CUDA events recorded on the launch stream around every launch.
+enum ProfClass { PROF_STENCIL = 0, PROF_XPASS, PROF_YPASS, PROF_ZSOLVE, PROF_DOTS, PROF_UPDATE, PROF_SMALL,
+                 PROF_COMBINE, PROF_RESIDUAL, PROF_OTHER, PROF_NCLASS };
+struct Prof {
+    int enabled = 0;
+    int used = 0;
+    static constexpr int CAP = 16384;
+    cudaEvent_t ev[CAP];
+    int cls[CAP / 2];
+    double ms[PROF_NCLASS] = {0};
+    long long launches[PROF_NCLASS] = {0};
+    int created = 0;
+};
+void prof_begin(helm_ctx* c, cudaStream_t s, int cls);
+void prof_end(helm_ctx* c, cudaStream_t s);
+void prof_flush(helm_ctx* c);
+void prof_release(helm_ctx* c);
+
+struct helm_ctx {
+    int device;
+    helm_grid grid;
+    helm_options opt;
+    int nx, ny, nz;
+    size_t npts;
+    double h[3];
+    double k0;
+    double ax, ay;                 // alpha_d = h_z^2/h_d^2
+    double2 gam[3];                // two-point ABC ghost factors
+    double zeta[3];                // 1 for staggered grids
+    // coefficient fields
+    double2* k2_d = nullptr;
+    float2* k2_f = nullptr;
+    double2* dk2_d[3] = {nullptr, nullptr, nullptr};
+    float2* dk2_f[3] = {nullptr, nullptr, nullptr};
+    double2* G_d = nullptr;
+    float2* G_f = nullptr;
+    // 1D eigendecompositions, FP64 (row-major [row][col])
+    double2 *Dx = nullptr, *Dy = nullptr, *Vx = nullptr, *Vxi = nullptr, *Vy = nullptr, *Vyi = nullptr;
+    // complex64 transform operands
+    float2 *XF = nullptr, *XI = nullptr;    // B of the x-pass: V_x^-T (forward), V_x^T (inverse)
+    float2 *YF = nullptr, *YI = nullptr;    // A of the y-pass: V_y^-1 (forward), V_y (inverse)
+    float2 *dxs = nullptr, *dys = nullptr;  // alpha_x D_x, alpha_y D_y
+    float2 *cz = nullptr;                   // h_z^2 k0^2(z_l) - 2(alpha_x + alpha_y + 1)
+    // tensor-core operands (split TF32), allocated for the TC modes
+    float *XFr = nullptr, *XIr = nullptr;   // real-embedded x-pass B, [2N][2K] K-major (hi, lo follow)
+    float *YFr = nullptr, *YIr = nullptr;   // y-pass A: re and im planes [2][N][N] (hi, lo follow)
+    void* tmaps = nullptr;                  // host copies of TMA descriptors (gemm_tc.cu)
+    // scratch
+    float2* tmp = nullptr;                  // one complex64 grid vector
+    unsigned* status_d = nullptr;           // device status word
+    KrylovWork* kw = nullptr;
+    cudaStream_t last_stream = nullptr;
+    Prof* prof = nullptr;
+};
+
+// ---- launchers shared across translation units -----------------------------------------------
+// stencil.cu
+helm_status launch_derived_fields(helm_ctx* c, cudaStream_t s);
+helm_status launch_stencil_f32(helm_ctx* c, const float2* x, float2* y, const double* sigma, int sidx, cudaStream_t s);
+helm_status launch_stencil_f64(helm_ctx* c, const double2* x, double2* y, cudaStream_t s);
+helm_status launch_residual(helm_ctx* c, const double2* x, const double2* F, float2* r, double* part, int nblk, cudaStream_t s);
+helm_status launch_rhs(helm_ctx* c, const double2* f, double2* F, cudaStream_t s);
+// eig.cu
+helm_status run_eig_setup(helm_ctx* c, cudaStream_t s);
+// gemm_simt.cu
+void launch_cgemm_simt(int M, int N, int K, const float2* A, long lda, long sA, const float2* B, long ldb, long sB,
+                       float2* C, long ldc, long sC, int batch, float alpha, const double* alpha_dev, int aidx,
+                       cudaStream_t s);
+// gemm_tc.cu
+helm_status tc_prepare(helm_ctx* c, cudaStream_t s);
+helm_status tc_xpass(helm_ctx* c, int inverse, const float2* in, float2* out, float alpha, const double* alpha_dev,
+                     int aidx, cudaStream_t s);
+helm_status tc_ypass(helm_ctx* c, int inverse, const float2* in, float2* out, cudaStream_t s);
+void tc_release(helm_ctx* c);
+// thomas.cu
+helm_status launch_zsolve(helm_ctx* c, const float2* in, float2* out, cudaStream_t s);
+// precond.cu
+helm_status precond_apply(helm_ctx* c, const float2* r, float2* z, const double* sigma, int sidx, cudaStream_t s);
+helm_status precond_step(helm_ctx* c, int step, const float2* in, float2* out, cudaStream_t s);
+// krylov.cu
+helm_status gmres_run(helm_ctx* c, const double2* b, double2* x, helm_solve_info* info, cudaStream_t s);
+void krylov_free(helm_ctx* c);

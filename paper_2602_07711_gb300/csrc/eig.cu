@@ -1,0 +1,189 @@
+// EigT step 1 (Sec. 4.1, Eq. EIG_SOLVER): FP64 eigendecomposition Lbar = V D V^-1 of the 1D matrix
+// of Eq. lambda_mat_definition for the staggered two-point ABC (corner gamma, zeta = 1), on the GPU.
+//
+// Method (our own, for this structured matrix): with v_l = cos((l - (N+1)/2) theta) or
+// sin((l - (N+1)/2) theta), the interior rows give lambda = 2 cos theta and the two corner rows collapse
+// (by the mirror symmetry of Lbar) to one scalar equation per family:
+//     symmetric:      cos((N+1) theta/2) = gamma cos((N-1) theta/2)
+//     antisymmetric:  sin((N+1) theta/2) = gamma sin((N-1) theta/2)   (divided by sin(theta/2) to remove
+//                                                                      the spurious root theta = 0)
+// For gamma = 0 the roots are the Dirichlet angles pi j/(N+1) (Sec. 3.1, Eq. LMB_egv), odd j symmetric,
+// even j antisymmetric.  Each thread follows one root by Newton's method along gamma_t = t gamma,
+// t = 1/S .. 1.  Lbar is complex symmetric, so eigenvectors of distinct eigenvalues are orthogonal in
+// the bilinear form v^T w; normalising v^T v = 1 gives V^-1 = V^T without an inverse.  The result is
+// checked by the residual |Lbar v - d v| and by |V^-1 V - I|; a failure is retried with more
+// continuation steps and then reported as HELM_ERR_EIG.
+#include "common.cuh"
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+namespace {
+
+__device__ inline double2 c_sin(double2 z) {
+    return make_double2(sin(z.x) * cosh(z.y), cos(z.x) * sinh(z.y));
+}
+__device__ inline double2 c_cos(double2 z) {
+    return make_double2(cos(z.x) * cosh(z.y), -sin(z.x) * sinh(z.y));
+}
+__device__ inline double2 c_sqrt(double2 z) {
+    const double r = hypot(z.x, z.y);
+    if (r == 0.0) return make_double2(0.0, 0.0);
+    const double t = sqrt(0.5 * (r + fabs(z.x)));
+    if (z.x >= 0.0) return make_double2(t, z.y / (2.0 * t));
+    return make_double2(fabs(z.y) / (2.0 * t), z.y >= 0 ? t : -t);
+}
+
+// F(theta) and F'(theta) for one family.
+__device__ inline void family(double2 th, int N, double2 g, bool anti, double2& F, double2& dF) {
+    const double a = 0.5 * (N + 1), b = 0.5 * (N - 1);
+    const double2 ta = make_double2(a * th.x, a * th.y), tb = make_double2(b * th.x, b * th.y);
+    if (!anti) {
+        const double2 ca = c_cos(ta), cb = c_cos(tb), sa = c_sin(ta), sb = c_sin(tb);
+        F = csub(ca, cmul(g, cb));
+        dF = cadd(cscale(sa, -a), cscale(cmul(g, sb), b));
+    } else {
+        const double2 sa = c_sin(ta), sb = c_sin(tb), ca = c_cos(ta), cb = c_cos(tb);
+        const double2 h = make_double2(0.5 * th.x, 0.5 * th.y);
+        const double2 sh = c_sin(h), ch = c_cos(h);
+        const double2 num = csub(sa, cmul(g, sb));
+        const double2 dnum = csub(cscale(ca, a), cscale(cmul(g, cb), b));
+        const double2 dden = cscale(ch, 0.5);
+        F = cdiv(num, sh);
+        dF = cdiv(csub(cmul(dnum, sh), cmul(num, dden)), cmul(sh, sh));
+    }
+}
+
+__global__ void eig_newton_kernel(int N, double2 gamma, int steps, double2* __restrict__ D, double2* __restrict__ V,
+                                  double2* __restrict__ Vinv) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= N) return;
+    const int jp = j + 1;
+    const bool anti = (jp % 2) == 0;
+    double2 th = make_double2(M_PI * jp / (N + 1.0), 0.0);
+    for (int s = 1; s <= steps; ++s) {
+        const double t = (double)s / steps;
+        const double2 g = make_double2(t * gamma.x, t * gamma.y);
+        const int its = s < steps ? 3 : 30;
+        for (int it = 0; it < its; ++it) {
+            double2 F, dF;
+            family(th, N, g, anti, F, dF);
+            const double2 step = cdiv(F, dF);
+            if (!(isfinite(step.x) && isfinite(step.y))) break;
+            th = csub(th, step);
+        }
+    }
+    const double2 c = c_cos(th);
+    D[j] = make_double2(2.0 * c.x, 2.0 * c.y);
+    double2 nrm = make_double2(0.0, 0.0);
+    for (int l = 0; l < N; ++l) {
+        const double off = l - 0.5 * (N - 1);
+        const double2 arg = make_double2(off * th.x, off * th.y);
+        const double2 v = anti ? c_sin(arg) : c_cos(arg);
+        nrm = cadd(nrm, cmul(v, v));
+    }
+    const double2 inv = cdiv(make_double2(1.0, 0.0), c_sqrt(nrm));
+    for (int l = 0; l < N; ++l) {
+        const double off = l - 0.5 * (N - 1);
+        const double2 arg = make_double2(off * th.x, off * th.y);
+        const double2 v = cmul(anti ? c_sin(arg) : c_cos(arg), inv);
+        V[(size_t)l * N + j] = v;
+        Vinv[(size_t)j * N + l] = v;
+    }
+}
+
+__device__ inline void atomic_max_nonneg(unsigned long long* addr, double v) {
+    if (!(v >= 0.0)) v = 1e300;  // NaN counts as failure
+    atomicMax(addr, (unsigned long long)__double_as_longlong(v));
+}
+
+// res[0] = max_j |Lbar v_j - d_j v_j|_inf,  res[1] = max_{j,k} |(V^-1 V)_{jk} - delta_jk|
+__global__ void eig_check_kernel(int N, double2 gamma, const double2* __restrict__ D, const double2* __restrict__ V,
+                                 const double2* __restrict__ Vinv, unsigned long long* res) {
+    const size_t id = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    if (id >= (size_t)N * N) return;
+    const int j = (int)(id / N), k = (int)(id % N);
+    double2 acc = make_double2(0.0, 0.0);
+    for (int l = 0; l < N; ++l) acc = cadd(acc, cmul(Vinv[(size_t)j * N + l], V[(size_t)l * N + k]));
+    if (j == k) acc.x -= 1.0;
+    atomic_max_nonneg(&res[1], hypot(acc.x, acc.y));
+    if (j == 0) {
+        // residual of eigenpair k at row l = ... all rows
+        double worst = 0.0;
+        for (int l = 0; l < N; ++l) {
+            double2 lv = make_double2(0.0, 0.0);
+            if (l > 0) lv = cadd(lv, V[(size_t)(l - 1) * N + k]);
+            if (l < N - 1) lv = cadd(lv, V[(size_t)(l + 1) * N + k]);
+            if (l == 0 || l == N - 1) lv = cadd(lv, cmul(gamma, V[(size_t)l * N + k]));
+            lv = csub(lv, cmul(D[k], V[(size_t)l * N + k]));
+            worst = fmax(worst, hypot(lv.x, lv.y));
+        }
+        atomic_max_nonneg(&res[0], worst);
+    }
+}
+
+__global__ void prep_operands_kernel(int N, double alpha, const double2* __restrict__ D, const double2* __restrict__ V,
+                                     const double2* __restrict__ Vinv, float2* __restrict__ BF, float2* __restrict__ BI,
+                                     float2* __restrict__ AF, float2* __restrict__ AI, float2* __restrict__ ds) {
+    const size_t id = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    if (id >= (size_t)N * N) return;
+    const int r = (int)(id / N), q = (int)(id % N);
+    // x-pass B operands: B[k][n] = Vinv[n][k] (forward), V[n][k] (inverse)
+    if (BF) {
+        const double2 f = Vinv[(size_t)q * N + r], b = V[(size_t)q * N + r];
+        BF[id] = make_float2((float)f.x, (float)f.y);
+        BI[id] = make_float2((float)b.x, (float)b.y);
+    }
+    // y-pass A operands: A = Vinv (forward), V (inverse)
+    if (AF) {
+        const double2 f = Vinv[id], b = V[id];
+        AF[id] = make_float2((float)f.x, (float)f.y);
+        AI[id] = make_float2((float)b.x, (float)b.y);
+    }
+    if (q == 0) ds[r] = make_float2((float)(alpha * D[r].x), (float)(alpha * D[r].y));
+}
+
+helm_status eig_one_axis(int N, double2 gamma, double2* D, double2* V, double2* Vinv, unsigned long long* chk,
+                         cudaStream_t s) {
+    const int steps_try[2] = {32, 256};
+    for (int t = 0; t < 2; ++t) {
+        eig_newton_kernel<<<(N + 127) / 128, 128, 0, s>>>(N, gamma, steps_try[t], D, V, Vinv);
+        HELM_CUDA_TRY(cudaGetLastError());
+        HELM_CUDA_TRY(cudaMemsetAsync(chk, 0, 2 * sizeof(unsigned long long), s));
+        const size_t nn = (size_t)N * N;
+        eig_check_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, s>>>(N, gamma, D, V, Vinv, chk);
+        HELM_CUDA_TRY(cudaGetLastError());
+        unsigned long long h[2];
+        HELM_CUDA_TRY(cudaMemcpyAsync(h, chk, sizeof(h), cudaMemcpyDeviceToHost, s));
+        HELM_CUDA_TRY(cudaStreamSynchronize(s));
+        double res, orth;
+        memcpy(&res, &h[0], 8);
+        memcpy(&orth, &h[1], 8);
+        if (res < 1e-9 && orth < 1e-8) return HELM_OK;
+    }
+    return HELM_ERR_EIG;
+}
+
+}  // namespace
+
+helm_status run_eig_setup(helm_ctx* c, cudaStream_t s) {
+    unsigned long long* chk = nullptr;
+    HELM_CUDA_TRY(cudaMalloc(&chk, 2 * sizeof(unsigned long long)));
+    helm_status st = eig_one_axis(c->nx, c->gam[0], c->Dx, c->Vx, c->Vxi, chk, s);
+    if (st == HELM_OK) st = eig_one_axis(c->ny, c->gam[1], c->Dy, c->Vy, c->Vyi, chk, s);
+    cudaFree(chk);
+    if (st != HELM_OK) return st;
+    {
+        const size_t nn = (size_t)c->nx * c->nx;
+        prep_operands_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, s>>>(c->nx, c->ax, c->Dx, c->Vx, c->Vxi, c->XF,
+                                                                          c->XI, nullptr, nullptr, c->dxs);
+        HELM_CUDA_TRY(cudaGetLastError());
+    }
+    {
+        const size_t nn = (size_t)c->ny * c->ny;
+        prep_operands_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, s>>>(c->ny, c->ay, c->Dy, c->Vy, c->Vyi, nullptr,
+                                                                          nullptr, c->YF, c->YI, c->dys);
+        HELM_CUDA_TRY(cudaGetLastError());
+    }
+    return HELM_OK;
+}

@@ -1,0 +1,458 @@
+// Restarted right-preconditioned GMRES(m) and flexible GMRES on the device (Sec. 5: the paper uses
+// right-preconditioned restarted GMRES after Saad [s]; the flexible form is Saad's Alg. 9.6).
+//
+// Per inner step j:  z_j = M^-1 v_j  ->  w = A z_j  ->  h_{i,j} = v_i^H w, w -= sum h_{i,j} v_i (classical
+// Gram-Schmidt, optionally twice)  ->  h_{j+1,j} = ||w||, Givens rotation, residual estimate |g_{j+1}|.
+// Krylov vectors are complex64; inner products are accumulated in FP64; H, the rotations and g are FP64
+// on the device.  Normalisation is lazy: the stored vector is w and v_{j+1} = sigma_{j+1} w with
+// sigma_{j+1} = 1/h_{j+1,j}; sigma is folded into the consumers (preconditioner input, inner products,
+// updates), which saves one pass over the grid per step.
+// The iterate x is complex128.  Each cycle ends with the FP64 true residual r = F - A x (Sec. 5.1 rel-res),
+// which decides convergence and seeds the next cycle.
+#include "common.cuh"
+#include <chrono>
+#include <vector>
+
+int residual_ctas(const helm_ctx* c);
+
+struct Ctrl {
+    double beta0;   // ||F - A x0||
+    double beta;    // ||F - A x|| at the last true residual
+    double est;     // |g_{j+1}| / beta0
+    double hnext;   // h_{j+1,j}
+    double rmax;    // ||F - A x||_inf
+    int flags;      // HELM_DEV_* bits
+    int pad;
+};
+
+struct KrylovWork {
+    int m = 0, flexible = 0, NB = 0, nres = 0;
+    size_t npts = 0;
+    float2* V = nullptr;     // (m+1) stored vectors
+    float2* Z = nullptr;     // m preconditioned vectors (flexible) or one scratch vector
+    double* sigma = nullptr; // [m+1]
+    double2* H = nullptr;    // (m+1) x m, column-major
+    double* cs = nullptr;    // [m]
+    double2* sn = nullptr;   // [m]
+    double2* g = nullptr;    // [m+1]
+    double2* y = nullptr;    // [m]
+    double2* part = nullptr; // [NB][m+1]
+    double* rpart = nullptr; // [2*nres]
+    float2* coef = nullptr;  // [m+1]
+    Ctrl* ctrl_d = nullptr;
+    Ctrl* ctrl_h = nullptr;  // pinned
+    double2* xbuf = nullptr; // device copy of x when the caller passes host memory
+    double2* bbuf = nullptr;
+};
+
+namespace {
+
+constexpr int NT = 256;
+constexpr int GRP = 8;
+
+// partial inner products conj(v_i) . w for i in [0, nv), FP32 products summed 8 at a time in FP32
+// and then in FP64; part[blk * ld + i]
+__global__ void __launch_bounds__(NT) dots_kernel(const float2* __restrict__ V, size_t npts, int nv,
+                                                 const float2* __restrict__ w, double2* __restrict__ part, int ld) {
+    __shared__ double2 red[NT / 32][GRP];
+    const int tid = threadIdx.x;
+    for (int g0 = 0; g0 < nv; g0 += GRP) {
+        const int ng = min(GRP, nv - g0);
+        double2 acc[GRP];
+        float2 a32[GRP];
+#pragma unroll
+        for (int q = 0; q < GRP; ++q) { acc[q] = make_double2(0, 0); a32[q] = make_float2(0, 0); }
+        int cnt = 0;
+        for (size_t id = blockIdx.x * (size_t)NT + tid; id < npts; id += (size_t)gridDim.x * NT) {
+            const float2 wv = w[id];
+#pragma unroll
+            for (int q = 0; q < GRP; ++q)
+                if (q < ng) {
+                    const float2 v = V[(size_t)(g0 + q) * npts + id];
+                    a32[q].x = fmaf(v.x, wv.x, fmaf(v.y, wv.y, a32[q].x));
+                    a32[q].y = fmaf(v.x, wv.y, fmaf(-v.y, wv.x, a32[q].y));
+                }
+            if (++cnt == 8) {
+                cnt = 0;
+#pragma unroll
+                for (int q = 0; q < GRP; ++q) { acc[q].x += a32[q].x; acc[q].y += a32[q].y; a32[q] = make_float2(0, 0); }
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < GRP; ++q) {
+            acc[q].x += a32[q].x; acc[q].y += a32[q].y;
+            for (int o = 16; o > 0; o >>= 1) {
+                acc[q].x += __shfl_down_sync(0xffffffffu, acc[q].x, o);
+                acc[q].y += __shfl_down_sync(0xffffffffu, acc[q].y, o);
+            }
+        }
+        if ((tid & 31) == 0)
+#pragma unroll
+            for (int q = 0; q < GRP; ++q) red[tid >> 5][q] = acc[q];
+        __syncthreads();
+        if (tid < ng) {
+            double2 s = make_double2(0, 0);
+            for (int wi = 0; wi < NT / 32; ++wi) { s.x += red[wi][tid].x; s.y += red[wi][tid].y; }
+            part[(size_t)blockIdx.x * ld + g0 + tid] = s;
+        }
+        __syncthreads();
+    }
+}
+
+// h_i += sigma_i * sum_blk part  (i < nv) into H column j; coef_i = h_i(this pass) * sigma_i
+__global__ void reduce_h_kernel(const double2* __restrict__ part, int NB, int ld, int nv, const double* __restrict__ sigma,
+                                double2* __restrict__ Hcol, float2* __restrict__ coef, int first_pass) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int i = wid; i < nv; i += nw) {
+        double sx = 0, sy = 0;
+        for (int b = lane; b < NB; b += 32) { sx += part[(size_t)b * ld + i].x; sy += part[(size_t)b * ld + i].y; }
+        for (int o = 16; o > 0; o >>= 1) {
+            sx += __shfl_down_sync(0xffffffffu, sx, o);
+            sy += __shfl_down_sync(0xffffffffu, sy, o);
+        }
+        if (lane == 0) {
+            const double s = sigma[i];
+            const double2 h = make_double2(sx * s, sy * s);
+            if (first_pass) Hcol[i] = h; else Hcol[i] = cadd(Hcol[i], h);
+            coef[i] = make_float2((float)(h.x * s), (float)(h.y * s));
+        }
+    }
+}
+
+// w -= sum_i coef_i V_i (i < nv); per-block partial ||w||^2 in part[blk * ld].x
+__global__ void __launch_bounds__(NT) update_kernel(const float2* __restrict__ V, size_t npts, int nv,
+                                                   const float2* __restrict__ coef, float2* __restrict__ w,
+                                                   double2* __restrict__ part, int ld) {
+    __shared__ float2 cf[72];
+    __shared__ double red[NT / 32];
+    for (int i = threadIdx.x; i < nv; i += NT) cf[i] = coef[i];
+    __syncthreads();
+    double acc = 0.0;
+    float a32 = 0.f;
+    int cnt = 0;
+    for (size_t id = blockIdx.x * (size_t)NT + threadIdx.x; id < npts; id += (size_t)gridDim.x * NT) {
+        float2 x = w[id];
+        for (int i = 0; i < nv; ++i) {
+            const float2 v = V[(size_t)i * npts + id];
+            const float2 c = cf[i];
+            x.x -= c.x * v.x - c.y * v.y;
+            x.y -= c.x * v.y + c.y * v.x;
+        }
+        w[id] = x;
+        a32 = fmaf(x.x, x.x, fmaf(x.y, x.y, a32));
+        if (++cnt == 8) { cnt = 0; acc += a32; a32 = 0.f; }
+    }
+    acc += a32;
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0;
+        for (int wi = 0; wi < NT / 32; ++wi) s += red[wi];
+        part[(size_t)blockIdx.x * ld] = make_double2(s, 0.0);
+    }
+}
+
+__device__ inline void givens(double2 a, double2 b, double& c, double2& s) {
+    const double ab = hypot(b.x, b.y);
+    if (ab == 0.0) { c = 1.0; s = make_double2(0, 0); return; }
+    const double aa = hypot(a.x, a.y);
+    if (aa == 0.0) { c = 0.0; s = make_double2(b.x / ab, -b.y / ab); return; }
+    const double t = hypot(aa, ab);
+    c = aa / t;
+    const double2 ph = make_double2(a.x / aa, a.y / aa);          // a/|a|
+    s = cmul(ph, make_double2(b.x / t, -b.y / t));                // (a/|a|) conj(b)/t
+}
+
+// Finish column j: h_{j+1,j} from the partial norms, previous rotations, the new rotation, g, est.
+__global__ void givens_kernel(const double2* __restrict__ part, int NB, int ld, int j, int m, double2* H, double* cs,
+                              double2* sn, double2* g, double* sigma, Ctrl* ctrl) {
+    __shared__ double red[32];
+    double s = 0;
+    for (int b = threadIdx.x; b < NB; b += blockDim.x) s += part[(size_t)b * ld].x;
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    double tot = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += red[w];
+    const double hn = sqrt(tot);
+    double2* col = H + (size_t)j * (m + 1);
+    col[j + 1] = make_double2(hn, 0.0);
+    for (int i = 0; i < j; ++i) {
+        const double2 a = col[i], b = col[i + 1];
+        const double2 t = cadd(cscale(a, cs[i]), cmul(sn[i], b));
+        const double2 snc = make_double2(sn[i].x, -sn[i].y);
+        col[i + 1] = csub(cscale(b, cs[i]), cmul(snc, a));
+        col[i] = t;
+    }
+    double c;
+    double2 sj;
+    givens(col[j], col[j + 1], c, sj);
+    cs[j] = c;
+    sn[j] = sj;
+    col[j] = cadd(cscale(col[j], c), cmul(sj, col[j + 1]));
+    col[j + 1] = make_double2(0.0, 0.0);
+    const double2 gj = g[j];
+    g[j + 1] = cscale(cmul(make_double2(sj.x, -sj.y), gj), -1.0);
+    g[j] = cscale(gj, c);
+    sigma[j + 1] = hn > 0 ? 1.0 / hn : 0.0;
+    const double est = hypot(g[j + 1].x, g[j + 1].y) / ctrl->beta0;
+    ctrl->est = est;
+    ctrl->hnext = hn;
+    if (!isfinite(hn) || !isfinite(est) || !isfinite(col[j].x) || !isfinite(col[j].y)) ctrl->flags |= HELM_DEV_NAN;
+}
+
+// y = R^-1 g (k x k upper triangular part of the rotated H)
+__global__ void lsq_kernel(const double2* __restrict__ H, const double2* __restrict__ g, int k, int m, double2* y,
+                           Ctrl* ctrl) {
+    if (threadIdx.x != 0) return;
+    for (int i = k - 1; i >= 0; --i) {
+        double2 s = g[i];
+        for (int q = i + 1; q < k; ++q) s = csub(s, cmul(H[(size_t)q * (m + 1) + i], y[q]));
+        y[i] = cdiv(s, H[(size_t)i * (m + 1) + i]);
+        if (!isfinite(y[i].x) || !isfinite(y[i].y)) ctrl->flags |= HELM_DEV_NAN;
+    }
+}
+
+// flexible: x += sum_i y_i Z_i  (FP64 accumulation)
+__global__ void __launch_bounds__(NT) combine_flex_kernel(const float2* __restrict__ Z, size_t npts, int k,
+                                                         const double2* __restrict__ y, double2* __restrict__ x) {
+    __shared__ double2 ys[64];
+    for (int i = threadIdx.x; i < k; i += NT) ys[i] = y[i];
+    __syncthreads();
+    for (size_t id = blockIdx.x * (size_t)NT + threadIdx.x; id < npts; id += (size_t)gridDim.x * NT) {
+        double2 a = x[id];
+        for (int i = 0; i < k; ++i) {
+            const float2 z = Z[(size_t)i * npts + id];
+            a.x += ys[i].x * z.x - ys[i].y * z.y;
+            a.y += ys[i].x * z.y + ys[i].y * z.x;
+        }
+        x[id] = a;
+    }
+}
+
+// right-preconditioned: u = sum_i (y_i sigma_i) V_i  (complex64)
+__global__ void __launch_bounds__(NT) combine_v_kernel(const float2* __restrict__ V, size_t npts, int k,
+                                                      const double2* __restrict__ y, const double* __restrict__ sigma,
+                                                      float2* __restrict__ u) {
+    __shared__ double2 ys[64];
+    for (int i = threadIdx.x; i < k; i += NT) ys[i] = cscale(y[i], sigma[i]);
+    __syncthreads();
+    for (size_t id = blockIdx.x * (size_t)NT + threadIdx.x; id < npts; id += (size_t)gridDim.x * NT) {
+        double ax = 0, ay = 0;
+        for (int i = 0; i < k; ++i) {
+            const float2 v = V[(size_t)i * npts + id];
+            ax += ys[i].x * v.x - ys[i].y * v.y;
+            ay += ys[i].x * v.y + ys[i].y * v.x;
+        }
+        u[id] = make_float2((float)ax, (float)ay);
+    }
+}
+
+__global__ void add_kernel(const float2* __restrict__ z, double2* __restrict__ x, size_t npts) {
+    for (size_t id = blockIdx.x * (size_t)blockDim.x + threadIdx.x; id < npts; id += (size_t)gridDim.x * blockDim.x) {
+        x[id].x += z[id].x;
+        x[id].y += z[id].y;
+    }
+}
+
+// beta = ||r||_2, rmax = ||r||_inf from the residual partials; sigma_0 = 1/beta, g = (beta, 0, ...)
+__global__ void resnorm_kernel(const double* __restrict__ rpart, int n, double* sigma, double2* g, int m, Ctrl* ctrl,
+                               int first) {
+    __shared__ double rs[32], rm[32];
+    double s = 0, mx = 0;
+    for (int b = threadIdx.x; b < n; b += blockDim.x) { s += rpart[2 * b]; mx = fmax(mx, rpart[2 * b + 1]); }
+    for (int o = 16; o > 0; o >>= 1) {
+        s += __shfl_down_sync(0xffffffffu, s, o);
+        mx = fmax(mx, __shfl_down_sync(0xffffffffu, mx, o));
+    }
+    if ((threadIdx.x & 31) == 0) { rs[threadIdx.x >> 5] = s; rm[threadIdx.x >> 5] = mx; }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    double tot = 0, mm = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { tot += rs[w]; mm = fmax(mm, rm[w]); }
+    const double beta = sqrt(tot);
+    ctrl->beta = beta;
+    ctrl->rmax = mm;
+    if (first) { ctrl->beta0 = beta; ctrl->flags = 0; }
+    if (!isfinite(beta)) ctrl->flags |= HELM_DEV_NAN;
+    sigma[0] = beta > 0 ? 1.0 / beta : 0.0;
+    g[0] = make_double2(beta, 0.0);
+    for (int i = 1; i <= m; ++i) g[i] = make_double2(0.0, 0.0);
+}
+
+bool is_device_ptr(const void* p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) { cudaGetLastError(); return false; }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+helm_status ensure_work(helm_ctx* c) {
+    const int m = c->opt.restart, flex = c->opt.flexible;
+    KrylovWork* k = c->kw;
+    if (k && k->m == m && k->flexible == flex) return HELM_OK;
+    krylov_free(c);
+    k = new KrylovWork();
+    c->kw = k;
+    k->m = m; k->flexible = flex; k->npts = c->npts;
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
+    k->NB = 4 * (sms > 0 ? sms : 148);
+    k->nres = residual_ctas(c);
+    const size_t vb = c->npts * sizeof(float2);
+    if (cudaMalloc(&k->V, vb * (m + 1)) != cudaSuccess) return HELM_ERR_NOMEM;
+    if (cudaMalloc(&k->Z, vb * (flex ? m : 1)) != cudaSuccess) return HELM_ERR_NOMEM;
+    HELM_CUDA_TRY(cudaMalloc(&k->sigma, sizeof(double) * (m + 1)));
+    HELM_CUDA_TRY(cudaMalloc(&k->H, sizeof(double2) * (m + 1) * m));
+    HELM_CUDA_TRY(cudaMalloc(&k->cs, sizeof(double) * m));
+    HELM_CUDA_TRY(cudaMalloc(&k->sn, sizeof(double2) * m));
+    HELM_CUDA_TRY(cudaMalloc(&k->g, sizeof(double2) * (m + 1)));
+    HELM_CUDA_TRY(cudaMalloc(&k->y, sizeof(double2) * m));
+    HELM_CUDA_TRY(cudaMalloc(&k->part, sizeof(double2) * (size_t)k->NB * (m + 1)));
+    HELM_CUDA_TRY(cudaMalloc(&k->rpart, sizeof(double) * 2 * k->nres));
+    HELM_CUDA_TRY(cudaMalloc(&k->coef, sizeof(float2) * (m + 1)));
+    HELM_CUDA_TRY(cudaMalloc(&k->ctrl_d, sizeof(Ctrl)));
+    HELM_CUDA_TRY(cudaMallocHost(&k->ctrl_h, sizeof(Ctrl)));
+    HELM_CUDA_TRY(cudaMemset(k->H, 0, sizeof(double2) * (m + 1) * m));
+    HELM_CUDA_TRY(cudaMemset(k->ctrl_d, 0, sizeof(Ctrl)));
+    return HELM_OK;
+}
+
+helm_status read_ctrl(KrylovWork* k, cudaStream_t s) {
+    HELM_CUDA_TRY(cudaMemcpyAsync(k->ctrl_h, k->ctrl_d, sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
+    HELM_CUDA_TRY(cudaStreamSynchronize(s));
+    return HELM_OK;
+}
+
+helm_status true_residual(helm_ctx* c, const double2* b, const double2* x, int first, cudaStream_t s) {
+    KrylovWork* k = c->kw;
+    helm_status st = launch_residual(c, x, b, k->V, k->rpart, k->nres, s);
+    if (st != HELM_OK) return st;
+    prof_begin(c, s, PROF_SMALL);
+    resnorm_kernel<<<1, 256, 0, s>>>(k->rpart, k->nres, k->sigma, k->g, k->m, k->ctrl_d, first);
+    prof_end(c, s);
+    HELM_CUDA_TRY(cudaGetLastError());
+    return read_ctrl(k, s);
+}
+
+}  // namespace
+
+void krylov_free(helm_ctx* c) {
+    KrylovWork* k = c->kw;
+    if (!k) return;
+    cudaFree(k->V); cudaFree(k->Z); cudaFree(k->sigma); cudaFree(k->H); cudaFree(k->cs); cudaFree(k->sn);
+    cudaFree(k->g); cudaFree(k->y); cudaFree(k->part); cudaFree(k->rpart); cudaFree(k->coef); cudaFree(k->ctrl_d);
+    cudaFreeHost(k->ctrl_h); cudaFree(k->xbuf); cudaFree(k->bbuf);
+    delete k;
+    c->kw = nullptr;
+}
+
+helm_status gmres_run(helm_ctx* c, const double2* b_in, double2* x_in, helm_solve_info* info, cudaStream_t s) {
+    const auto t0 = std::chrono::steady_clock::now();
+    helm_status st = ensure_work(c);
+    if (st != HELM_OK) return st;
+    KrylovWork* k = c->kw;
+    const size_t npts = c->npts, vbytes = npts * sizeof(double2);
+    const int m = c->opt.restart, flex = c->opt.flexible;
+    const bool xdev = is_device_ptr(x_in), bdev = is_device_ptr(b_in);
+    double2* x = x_in;
+    const double2* b = b_in;
+    if (!xdev) {
+        if (!k->xbuf) HELM_CUDA_TRY(cudaMalloc(&k->xbuf, vbytes));
+        HELM_CUDA_TRY(cudaMemcpyAsync(k->xbuf, x_in, vbytes, cudaMemcpyHostToDevice, s));
+        x = k->xbuf;
+    }
+    if (!bdev) {
+        if (!k->bbuf) HELM_CUDA_TRY(cudaMalloc(&k->bbuf, vbytes));
+        HELM_CUDA_TRY(cudaMemcpyAsync(k->bbuf, b_in, vbytes, cudaMemcpyHostToDevice, s));
+        b = k->bbuf;
+    }
+    HELM_CUDA_TRY(cudaMemsetAsync(c->status_d, 0, sizeof(unsigned), s));
+    const int NB = k->NB, ld = m + 1;
+    const int ublocks = NB;
+    int its = 0, restarts = 0;
+    helm_status result = HELM_ERR_NOT_CONVERGED;
+    if ((st = true_residual(c, b, x, 1, s)) != HELM_OK) return st;
+    const double beta0 = k->ctrl_h->beta0;
+    double est = 1.0;
+    if (!(beta0 > 0)) {
+        result = (k->ctrl_h->flags & HELM_DEV_NAN) ? HELM_ERR_NAN : HELM_OK;
+    } else {
+        for (;;) {
+            if (k->ctrl_h->beta / beta0 <= c->opt.rtol) { result = HELM_OK; break; }
+            if (k->ctrl_h->flags & HELM_DEV_NAN) { result = HELM_ERR_NAN; break; }
+            if (its >= c->opt.max_iter) { result = HELM_ERR_NOT_CONVERGED; break; }
+            int kk = 0;
+            bool breakdown = false;
+            for (int j = 0; j < m; ++j) {
+                float2* vj = k->V + (size_t)j * npts;
+                float2* w = k->V + (size_t)(j + 1) * npts;
+                float2* z = flex ? k->Z + (size_t)j * npts : k->Z;
+                if ((st = precond_apply(c, vj, z, k->sigma, j, s)) != HELM_OK) return st;
+                if ((st = launch_stencil_f32(c, z, w, nullptr, 0, s)) != HELM_OK) return st;
+                const int passes = c->opt.reorth ? 2 : 1;
+                for (int pass = 0; pass < passes; ++pass) {
+                    prof_begin(c, s, PROF_DOTS);
+                    dots_kernel<<<NB, NT, 0, s>>>(k->V, npts, j + 1, w, k->part, ld);
+                    prof_end(c, s);
+                    prof_begin(c, s, PROF_SMALL);
+                    reduce_h_kernel<<<1, 256, 0, s>>>(k->part, NB, ld, j + 1, k->sigma, k->H + (size_t)j * (m + 1),
+                                                      k->coef, pass == 0);
+                    prof_end(c, s);
+                    prof_begin(c, s, PROF_UPDATE);
+                    update_kernel<<<ublocks, NT, 0, s>>>(k->V, npts, j + 1, k->coef, w, k->part, ld);
+                    prof_end(c, s);
+                }
+                prof_begin(c, s, PROF_SMALL);
+                givens_kernel<<<1, 256, 0, s>>>(k->part, NB, ld, j, m, k->H, k->cs, k->sn, k->g, k->sigma, k->ctrl_d);
+                prof_end(c, s);
+                HELM_CUDA_TRY(cudaGetLastError());
+                if ((st = read_ctrl(k, s)) != HELM_OK) return st;
+                ++its;
+                kk = j + 1;
+                est = k->ctrl_h->est;
+                if (k->ctrl_h->flags & HELM_DEV_NAN) break;
+                if (est <= c->opt.rtol || its >= c->opt.max_iter) break;
+                if (!(k->ctrl_h->hnext > 0)) { breakdown = true; break; }
+            }
+            if (k->ctrl_h->flags & HELM_DEV_NAN) { result = HELM_ERR_NAN; break; }
+            prof_begin(c, s, PROF_SMALL);
+            lsq_kernel<<<1, 32, 0, s>>>(k->H, k->g, kk, m, k->y, k->ctrl_d);
+            prof_end(c, s);
+            if (flex) {
+                prof_begin(c, s, PROF_COMBINE);
+                combine_flex_kernel<<<NB, NT, 0, s>>>(k->Z, npts, kk, k->y, x);
+                prof_end(c, s);
+            } else {
+                float2* u = k->V + (size_t)kk * npts;   // V_kk is not needed by the update
+                prof_begin(c, s, PROF_COMBINE);
+                combine_v_kernel<<<NB, NT, 0, s>>>(k->V, npts, kk, k->y, k->sigma, u);
+                prof_end(c, s);
+                if ((st = precond_apply(c, u, u, nullptr, 0, s)) != HELM_OK) return st;
+                prof_begin(c, s, PROF_COMBINE);
+                add_kernel<<<NB, NT, 0, s>>>(u, x, npts);
+                prof_end(c, s);
+            }
+            HELM_CUDA_TRY(cudaGetLastError());
+            ++restarts;
+            if ((st = true_residual(c, b, x, 0, s)) != HELM_OK) return st;
+            if (breakdown && k->ctrl_h->beta / beta0 > c->opt.rtol) { result = HELM_ERR_BREAKDOWN; break; }
+        }
+    }
+    unsigned dstat = 0;
+    HELM_CUDA_TRY(cudaMemcpyAsync(&dstat, c->status_d, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+    if (!xdev) HELM_CUDA_TRY(cudaMemcpyAsync(x_in, x, vbytes, cudaMemcpyDeviceToHost, s));
+    HELM_CUDA_TRY(cudaStreamSynchronize(s));
+    if (result == HELM_OK && (dstat & HELM_DEV_PIVOT)) result = HELM_ERR_PIVOT;
+    if (info) {
+        info->status = result;
+        info->iterations = its;
+        info->restarts = restarts;
+        info->relres_true = beta0 > 0 ? k->ctrl_h->beta / beta0 : 0.0;
+        info->relres_est = est;
+        info->beta0 = beta0;
+        info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    }
+    return result;
+}

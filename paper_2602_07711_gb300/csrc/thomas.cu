@@ -1,0 +1,197 @@
+// EigT step 3 (Sec. 4.1): the N_x N_y independent complex tridiagonal systems of
+// Eq. Indep_precond_system along z,
+//   (gamma_z + b_1) u_1 + zeta_z u_2 = y_1
+//   u_{l-1} + b_l u_l + u_{l+1} = y_l
+//   zeta_z u_{N-1} + (gamma_z + b_N) u_N = y_N,
+//   b_l = alpha_x d_{x,i} + alpha_y d_{y,j} + h_z^2 k0^2(z_l) - 2(alpha_x + alpha_y + 1).
+//
+// Design (ours): the systems are lines of stride N_x N_y through HBM, so a CTA takes L consecutive
+// lines (consecutive i: every access is a contiguous L x 8-byte row) and cuts each line into W chunks
+// of at most MCH rows, one chunk per thread.  Each thread keeps its chunk in registers and eliminates
+// it twice without pivoting (down, then up), which expresses the chunk's end values through its
+// neighbours' end values.  One thread per line solves that small block-tridiagonal interface system
+// (2 unknowns per chunk) from shared memory, and every thread then finishes its chunk by a Thomas sweep
+// with known boundary values.  HBM traffic is one read and one write per point (16 B/pt).
+#include "common.cuh"
+
+namespace {
+
+struct ZParams {
+    int nx, ny, nz, W;
+    const float2* dxs;   // alpha_x d_{x,i}
+    const float2* dys;   // alpha_y d_{y,j}
+    const float2* cz;    // h_z^2 k0^2(z_l) - 2(alpha_x + alpha_y + 1)
+    float2 gz;           // gamma_z
+    float zz;            // zeta_z
+};
+
+__device__ inline float2 f2(float a, float b) { return make_float2(a, b); }
+
+// a / b for the well-scaled pivots of these systems (|b| ~ 1e-3 .. 1e2): a conj(b) / |b|^2
+__device__ inline float2 qdiv(float2 a, float2 b) {
+    const float r = 1.f / fmaf(b.x, b.x, b.y * b.y);
+    return make_float2((a.x * b.x + a.y * b.y) * r, (a.y * b.x - a.x * b.y) * r);
+}
+
+__device__ inline void note_pivot(float2 d, unsigned* status) {
+    if (!(fabsf(d.x) + fabsf(d.y) > 1e-30f)) atomicOr(status, (unsigned)HELM_DEV_PIVOT);
+}
+
+template <int L, int MCH>
+__global__ void __launch_bounds__(L * 32)
+zsolve_kernel(ZParams p, const float2* in, float2* out, unsigned* status) {
+    // per chunk and line: [0] g_s, [1] p_s, [2] q_s, [3] g_e, [4] p_e, [5] q_e; reused by the interface
+    // solve for Y_c / X_c (slots 0 and 3) and Gamma_c (slots 1 and 2)
+    __shared__ float2 sh[6][32][L];
+    const int lane = threadIdx.x, w = threadIdx.y;
+    const int W = p.W, nz = p.nz;
+    const int i = blockIdx.x * L + lane, j = blockIdx.y;
+    const bool live = i < p.nx;
+    // balanced chunks: every chunk has at least two rows when nz >= 2W (MCH >= 4 guarantees it)
+    const int s = (int)(((long)w * nz) / W), e = (int)(((long)(w + 1) * nz) / W) - 1;
+    const int len = e - s + 1;
+    const size_t plane = (size_t)p.nx * p.ny;
+    const size_t base = (size_t)j * p.nx + (live ? i : 0);
+    float2 dxy = f2(0.f, 0.f);
+    if (live) dxy = cadd(p.dxs[i], p.dys[j]);
+
+    auto diag = [dxy, p, nz](int l) {
+        float2 b = cadd(dxy, p.cz[l]);
+        if (l == 0 || l == nz - 1) b = cadd(b, p.gz);
+        return b;
+    };
+    auto sub = [p, nz](int l) { return l == 0 ? 0.f : (l == nz - 1 ? p.zz : 1.f); };
+    auto sup = [p, nz](int l) { return l == nz - 1 ? 0.f : (l == 0 ? p.zz : 1.f); };
+
+    float2 y[MCH];
+#pragma unroll
+    for (int k = 0; k < MCH; ++k)
+        y[k] = (live && k < len) ? in[base + (size_t)(s + k) * plane] : f2(0.f, 0.f);
+
+    // down elimination with x_{s-1} as parameter: x_e = d' + l' x_{s-1} - c' x_{e+1}
+    float2 cp = f2(0.f, 0.f), dp = f2(0.f, 0.f), lp = f2(0.f, 0.f);
+#pragma unroll
+    for (int k = 0; k < MCH; ++k) {
+        if (k < len) {
+            const int l = s + k;
+            const float a = sub(l);
+            const float2 den = (k == 0) ? diag(l) : csub(diag(l), cscale(cp, a));
+            note_pivot(den, status);
+            const float2 nd = (k == 0) ? qdiv(y[k], den) : qdiv(csub(y[k], cscale(dp, a)), den);
+            const float2 nl = (k == 0) ? qdiv(f2(-a, 0.f), den) : qdiv(cscale(lp, -a), den);
+            cp = qdiv(f2(sup(l), 0.f), den);
+            dp = nd;
+            lp = nl;
+        }
+    }
+    // up elimination with x_{e+1} as parameter: x_s = dh - ch x_{s-1} + rh x_{e+1}
+    float2 ch = f2(0.f, 0.f), dh = f2(0.f, 0.f), rh = f2(0.f, 0.f);
+#pragma unroll
+    for (int kk = 0; kk < MCH; ++kk) {
+        const int k = MCH - 1 - kk;   // reverse order, written as a forward loop so it unrolls
+        if (k < len) {
+            const int l = s + k;
+            const float c = sup(l);
+            const bool first = (k == len - 1);
+            const float2 den = first ? diag(l) : csub(diag(l), cscale(ch, c));
+            note_pivot(den, status);
+            const float2 nd = first ? qdiv(y[k], den) : qdiv(csub(y[k], cscale(dh, c)), den);
+            const float2 nr = first ? qdiv(f2(-c, 0.f), den) : qdiv(cscale(rh, -c), den);
+            ch = qdiv(f2(sub(l), 0.f), den);
+            dh = nd;
+            rh = nr;
+        }
+    }
+    sh[0][w][lane] = dh;                       // g_s
+    sh[1][w][lane] = cscale(ch, -1.f);         // p_s (coefficient of x_{s-1})
+    sh[2][w][lane] = rh;                       // q_s (coefficient of x_{e+1})
+    sh[3][w][lane] = dp;                       // g_e
+    sh[4][w][lane] = lp;                       // p_e
+    sh[5][w][lane] = cscale(cp, -1.f);         // q_e
+    __syncthreads();
+
+    // interface system: X_c = (x_s, x_e) of chunk c,  X_c + A_c X_{c-1} + C_c X_{c+1} = G_c with
+    // A_c = [[0, -p_s], [0, -p_e]] and C_c = [[-q_s, 0], [-q_e, 0]].  Block LU, one thread per line:
+    // B_c = I - A_c Gamma_{c-1}, Y_c = B_c^-1 (G_c - A_c Y_{c-1}), Gamma_c = B_c^-1 C_c (first column only).
+    if (w == 0) {
+        float2 G1 = f2(0.f, 0.f), Y1 = f2(0.f, 0.f);
+        for (int c = 0; c < W; ++c) {
+            const float2 ps = sh[1][c][lane], qs = sh[2][c][lane], pe = sh[4][c][lane], qe = sh[5][c][lane];
+            const float2 b00 = cadd(f2(1.f, 0.f), cmul(ps, G1));
+            const float2 b10 = cmul(pe, G1);                 // B_c = [[b00, 0], [b10, 1]]
+            const float2 r0 = cadd(sh[0][c][lane], cmul(ps, Y1));
+            const float2 r1 = cadd(sh[3][c][lane], cmul(pe, Y1));
+            note_pivot(b00, status);
+            const float2 y0 = qdiv(r0, b00);
+            const float2 y1 = csub(r1, cmul(b10, y0));
+            const float2 g0 = qdiv(cscale(qs, -1.f), b00);
+            const float2 g1 = csub(cscale(qe, -1.f), cmul(b10, g0));
+            sh[0][c][lane] = y0; sh[3][c][lane] = y1;
+            sh[1][c][lane] = g0; sh[2][c][lane] = g1;
+            G1 = g1; Y1 = y1;
+        }
+        float2 nxt = f2(0.f, 0.f);   // X_{c+1}[0]
+        for (int c = W - 1; c >= 0; --c) {
+            const float2 x0 = csub(sh[0][c][lane], cmul(sh[1][c][lane], nxt));
+            const float2 x1 = csub(sh[3][c][lane], cmul(sh[2][c][lane], nxt));
+            sh[0][c][lane] = x0; sh[3][c][lane] = x1;
+            nxt = x0;
+        }
+    }
+    __syncthreads();
+
+    // finish the chunk by a Thomas sweep with known x_{s-1} (Lv) and x_{e+1} (Rv)
+    const float2 Lv = w > 0 ? sh[3][w - 1][lane] : f2(0.f, 0.f);
+    const float2 Rv = w < W - 1 ? sh[0][w + 1][lane] : f2(0.f, 0.f);
+    float2 cpk[MCH];
+    float2 c_prev = f2(0.f, 0.f), d_prev = Lv;
+#pragma unroll
+    for (int k = 0; k < MCH; ++k) {
+        cpk[k] = f2(0.f, 0.f);
+        if (k < len) {
+            const int l = s + k;
+            const float a = sub(l);
+            const float2 den = (k == 0) ? diag(l) : csub(diag(l), cscale(c_prev, a));
+            float2 rhs = csub(y[k], cscale(d_prev, a));
+            const bool last = (k == len - 1);
+            if (last) rhs = csub(rhs, cscale(Rv, sup(l)));
+            cpk[k] = qdiv(f2(last ? 0.f : sup(l), 0.f), den);
+            y[k] = qdiv(rhs, den);
+            c_prev = cpk[k];
+            d_prev = y[k];
+        }
+    }
+    float2 xn = f2(0.f, 0.f);
+#pragma unroll
+    for (int kk = 0; kk < MCH; ++kk) {
+        const int k = MCH - 1 - kk;
+        if (k < len) {
+            xn = csub(y[k], cmul(cpk[k], xn));
+            if (live) out[base + (size_t)(s + k) * plane] = xn;
+        }
+    }
+}
+
+}  // namespace
+
+helm_status launch_zsolve(helm_ctx* c, const float2* in, float2* out, cudaStream_t s) {
+    ZParams p;
+    p.nx = c->nx; p.ny = c->ny; p.nz = c->nz;
+    p.dxs = c->dxs; p.dys = c->dys; p.cz = c->cz;
+    p.gz = make_float2((float)c->gam[2].x, (float)c->gam[2].y);
+    p.zz = (float)c->zeta[2];
+    if (c->nz > 512) return HELM_ERR_UNSUPPORTED;
+    prof_begin(c, s, PROF_ZSOLVE);
+    if (c->nz <= 256) {
+        p.W = (c->nz + 7) / 8;
+        dim3 grid((c->nx + 31) / 32, c->ny), block(32, p.W);
+        zsolve_kernel<32, 8><<<grid, block, 0, s>>>(p, in, out, c->status_d);
+    } else {
+        p.W = (c->nz + 15) / 16;
+        dim3 grid((c->nx + 15) / 16, c->ny), block(16, p.W);
+        zsolve_kernel<16, 16><<<grid, block, 0, s>>>(p, in, out, c->status_d);
+    }
+    prof_end(c, s);
+    HELM_CUDA_TRY(cudaGetLastError());
+    return HELM_OK;
+}

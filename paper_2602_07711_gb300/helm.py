@@ -1,0 +1,220 @@
+"""ctypes binding of libhelm.so (include/helm.h).  Argument marshalling only: every step of the solver
+runs in the library's CUDA kernels.  Torch supplies device memory and the current stream.
+
+The module-level functions carry the C names (helm_setup, helm_apply_A, ...); `Solver` wraps a context.
+If the library has not been built, every entry point raises instead of falling back to anything else.
+"""
+import ctypes as C
+import os
+import time
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+library_path = os.path.join(HERE, "libhelm.so")
+
+HELM_PRECOND_NONE, HELM_PRECOND_EIGT, HELM_PRECOND_PFFT = 0, 1, 2
+HELM_PREC_FP32, HELM_PREC_TF32, HELM_PREC_3XTF32 = 0, 1, 2
+HELM_C64, HELM_C128 = 0, 1
+
+STATUS = {0: "HELM_OK", 1: "HELM_ERR_ARG", 2: "HELM_ERR_CUDA", 3: "HELM_ERR_NOMEM", 4: "HELM_ERR_EIG",
+          5: "HELM_ERR_PIVOT", 6: "HELM_ERR_NAN", 7: "HELM_ERR_BREAKDOWN", 8: "HELM_ERR_NOT_CONVERGED",
+          9: "HELM_ERR_ITER_LIMIT", 10: "HELM_ERR_UNSUPPORTED"}
+
+
+class HelmError(RuntimeError):
+    def __init__(self, code, where):
+        self.code = code
+        super().__init__("%s failed: %s (%d)" % (where, STATUS.get(code, "?"), code))
+
+
+class helm_grid(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("lx", C.c_double), ("ly", C.c_double),
+                ("lz", C.c_double), ("staggered", C.c_int)]
+
+
+class helm_options(C.Structure):
+    _fields_ = [("order", C.c_int), ("precond", C.c_int), ("precision", C.c_int), ("restart", C.c_int),
+                ("max_iter", C.c_int), ("rtol", C.c_double), ("flexible", C.c_int), ("reorth", C.c_int)]
+
+
+class helm_solve_info(C.Structure):
+    _fields_ = [("status", C.c_int), ("iterations", C.c_int), ("restarts", C.c_int), ("reserved", C.c_int),
+                ("relres_true", C.c_double), ("relres_est", C.c_double), ("beta0", C.c_double),
+                ("seconds", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+
+
+_lib = None
+
+# name -> (restype, argtypes)
+_SIGS = {
+    "helm_setup": (C.c_int, [C.POINTER(helm_grid), C.c_void_p, C.c_double, C.c_void_p, C.POINTER(helm_options),
+                             C.c_void_p, C.POINTER(C.c_void_p)]),
+    "helm_build_rhs": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "helm_apply_A": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
+    "helm_apply_precond": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "helm_precond_step": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "helm_get_eig": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "helm_gmres_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(helm_solve_info), C.c_void_p]),
+    "helm_destroy": (None, [C.c_void_p]),
+    "helm_status_str": (C.c_char_p, [C.c_int]),
+    "helm_version": (C.c_char_p, []),
+}
+
+
+def lib():
+    """Load libhelm.so (raises if it was not built: there is no other implementation)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(library_path):
+            raise RuntimeError("libhelm.so not found at %s; build it with __graft_entry__.build()" % library_path)
+        L = C.CDLL(library_path)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(code, where):
+    if code != 0:
+        raise HelmError(code, where)
+
+
+def _stream(stream):
+    import torch
+    if stream is None:
+        return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    return C.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+def _ptr(t):
+    """Data pointer of a torch tensor (contiguous) or a numpy array (host memory)."""
+    if isinstance(t, np.ndarray):
+        assert t.flags["C_CONTIGUOUS"]
+        return C.c_void_p(t.ctypes.data)
+    assert t.is_contiguous()
+    return C.c_void_p(t.data_ptr())
+
+
+def helm_setup(grid, k2, k0, k0z2, options, stream=None):
+    ctx = C.c_void_p()
+    z = None
+    if k0z2 is not None:
+        z = np.ascontiguousarray(k0z2, dtype=np.float64)
+    code = lib().helm_setup(C.byref(grid), _ptr(k2), float(k0), C.c_void_p(z.ctypes.data) if z is not None else None,
+                            C.byref(options), _stream(stream), C.byref(ctx))
+    _check(code, "helm_setup")
+    return ctx
+
+
+def helm_build_rhs(ctx, f, F, stream=None):
+    _check(lib().helm_build_rhs(ctx, _ptr(f), _ptr(F), _stream(stream)), "helm_build_rhs")
+
+
+def helm_apply_A(ctx, x, y, dtype, stream=None):
+    _check(lib().helm_apply_A(ctx, _ptr(x), _ptr(y), int(dtype), _stream(stream)), "helm_apply_A")
+
+
+def helm_apply_precond(ctx, r, z, stream=None):
+    _check(lib().helm_apply_precond(ctx, _ptr(r), _ptr(z), _stream(stream)), "helm_apply_precond")
+
+
+def helm_precond_step(ctx, step, x, y, stream=None):
+    _check(lib().helm_precond_step(ctx, int(step), _ptr(x), _ptr(y), _stream(stream)), "helm_precond_step")
+
+
+def helm_get_eig(ctx, axis, n):
+    D = np.zeros(n, np.complex128)
+    V = np.zeros((n, n), np.complex128)
+    Vi = np.zeros((n, n), np.complex128)
+    _check(lib().helm_get_eig(ctx, int(axis), _ptr(D), _ptr(V), _ptr(Vi)), "helm_get_eig")
+    return D, V, Vi
+
+
+def helm_gmres_solve(ctx, b, x, stream=None):
+    info = helm_solve_info()
+    code = lib().helm_gmres_solve(ctx, _ptr(b), _ptr(x), C.byref(info), _stream(stream))
+    return code, info
+
+
+def helm_destroy(ctx):
+    if ctx:
+        lib().helm_destroy(ctx)
+
+
+class Solver:
+    """One problem: grid, k^2 samples (complex128, host numpy or torch tensor), background k0, options."""
+
+    def __init__(self, n, k2, k0, order=4, L=(1.0, 1.0, 1.0), precond=HELM_PRECOND_EIGT, precision=HELM_PREC_FP32,
+                 restart=30, max_iter=300, rtol=1e-6, flexible=False, reorth=False, k0z2=None, stream=None):
+        nx, ny, nz = n
+        self.shape = (nz, ny, nx)
+        self.n = (nx, ny, nz)
+        self.grid = helm_grid(nx, ny, nz, L[0], L[1], L[2], 1)
+        self.options = helm_options(order, precond, precision, restart, max_iter, rtol, int(flexible), int(reorth))
+        if isinstance(k2, np.ndarray):
+            k2 = np.ascontiguousarray(k2, dtype=np.complex128)
+        self.ctx = helm_setup(self.grid, k2, k0, k0z2, self.options, stream)
+
+    def close(self):
+        if self.ctx:
+            helm_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # torch conveniences
+    def _empty(self, dtype):
+        import torch
+        return torch.empty(self.shape, dtype=dtype, device="cuda")
+
+    def build_rhs(self, f, stream=None):
+        import torch
+        F = self._empty(torch.complex128)
+        helm_build_rhs(self.ctx, f, F, stream)
+        return F
+
+    def apply_A(self, x, stream=None):
+        import torch
+        y = self._empty(x.dtype)
+        helm_apply_A(self.ctx, x, y, HELM_C64 if x.dtype == torch.complex64 else HELM_C128, stream)
+        return y
+
+    def apply_precond(self, r, stream=None):
+        import torch
+        z = self._empty(torch.complex64)
+        helm_apply_precond(self.ctx, r, z, stream)
+        return z
+
+    def precond_step(self, step, x, stream=None):
+        import torch
+        y = self._empty(torch.complex64)
+        helm_precond_step(self.ctx, step, x, y, stream)
+        return y
+
+    def get_eig(self, axis):
+        return helm_get_eig(self.ctx, axis, self.n[axis])
+
+    def solve(self, b, x0=None, stream=None, check=True):
+        """x such that A x = b (b complex128 on the device or in host memory)."""
+        import torch
+        if x0 is None:
+            if isinstance(b, np.ndarray):
+                x = np.zeros(self.shape, np.complex128)
+            else:
+                x = torch.zeros(self.shape, dtype=torch.complex128, device=b.device)
+        else:
+            x = x0
+        code, info = helm_gmres_solve(self.ctx, b, x, stream)
+        if check and code not in (0,):
+            raise HelmError(code, "helm_gmres_solve")
+        return x, info

@@ -1,0 +1,59 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every function include/helm.h declares
+(no GPU needed: nothing here launches work)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "helm.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(helm_[A-Za-z_0-9]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def libpath():
+    from paper_2602_07711_gb300 import build as b
+    if not os.path.exists(b.LIB) or any(os.path.getmtime(s) > os.path.getmtime(b.LIB) for s in b.sources()):
+        b.build()
+    return b.LIB
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for n in ("helm_setup", "helm_apply_A", "helm_apply_precond", "helm_gmres_solve", "helm_build_rhs", "helm_destroy"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(libpath):
+    L = ctypes.CDLL(libpath)
+    for n in _declared():
+        assert hasattr(L, n), n
+
+
+def test_status_strings_and_version(libpath):
+    from paper_2602_07711_gb300 import helm
+    L = helm.lib()
+    assert L.helm_version().startswith(b"helm-gb300")
+    for code in range(11):
+        assert L.helm_status_str(code) and L.helm_status_str(code) != b"unknown status"
+
+
+def test_setup_rejects_bad_arguments_without_gpu_work(libpath):
+    from paper_2602_07711_gb300 import helm
+    import numpy as np
+    L = helm.lib()
+    ctx = ctypes.c_void_p()
+    g = helm.helm_grid(2, 8, 8, 1.0, 1.0, 1.0, 1)        # N < 4 is rejected before any CUDA call
+    o = helm.helm_options(4, 1, 0, 30, 100, 1e-6, 0, 0)
+    k2 = np.zeros(2 * 8 * 8, np.complex128)
+    assert L.helm_setup(ctypes.byref(g), k2.ctypes.data, 1.0, None, ctypes.byref(o), None, ctypes.byref(ctx)) == 1
+    g = helm.helm_grid(8, 8, 8, 1.0, 1.0, 1.0, 1)
+    o = helm.helm_options(5, 1, 0, 30, 100, 1e-6, 0, 0)    # order 5 does not exist
+    k2 = np.zeros(512, np.complex128)
+    assert L.helm_setup(ctypes.byref(g), k2.ctypes.data, 1.0, None, ctypes.byref(o), None, ctypes.byref(ctx)) == 1
+    assert L.helm_setup(None, None, 1.0, None, None, None, ctypes.byref(ctx)) == 1

