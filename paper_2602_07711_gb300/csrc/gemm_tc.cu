@@ -1,14 +1,434 @@
-// Tensor-core (tcgen05) eigenvector transforms: not built yet.
+// EigT steps 2 and 4 (Sec. 4.1, Eq. EIG_SOLVER) on the 5th-generation tensor cores (tcgen05, sm_103a):
+// the dense complex contractions Ybar_l = V_y^-1 Y_l V_x^-T and U_l = V_y Ubar_l V_x^T with TF32 operands
+// and FP32 accumulation in tensor memory.
+//
+// x-pass (right multiply, contraction over x):  every row r = (l, j) of the grid is a complex vector of
+//   length N_x.  In the interleaved (re, im) layout the row is a real vector of length 2 N_x, and the
+//   complex product with W becomes one real GEMM  Out[r] = Row[r] B^T  with the real embedding
+//     B[2n][2k] = Re W_kn,  B[2n][2k+1] = -Im W_kn,  B[2n+1][2k] = Im W_kn,  B[2n+1][2k+1] = Re W_kn.
+//   A = the grid viewed as (N_y N_z) x 2N_x (K-major, straight from HBM by TMA), B = 2N_x x 2N_x (K-major).
+// y-pass (left multiply per slice, contraction over y):  Out_l = W Y_l with Y_l viewed as N_y x 2N_x real
+//   (N contiguous, "MN-major").  Two accumulators P = Re(W) Y_l and Q = Im(W) Y_l share every B tile; the
+//   epilogue forms Out_re = P_re - Q_im, Out_im = P_im + Q_re.
+//
+// Kernel structure (one 128 x 128 output tile per CTA, 192 threads, two CTAs per SM):
+//   warp 0      TMA producer: cp.async.bulk.tensor tiles (128-byte swizzle) into a STAGES-deep ring,
+//               completion tracked by mbarrier transaction counts
+//   warp 1      allocates tensor memory; one lane issues tcgen05.mma (M=128, N=128, K=8) and commits
+//               each stage back to the producer
+//   warps 2-5   epilogue: tcgen05.ld of the accumulator lanes they own, scale, vectorised stores
+// Every mbarrier wait is bounded; on expiry the CTA raises HELM_DEV_WAIT, skips its remaining work,
+// and still frees its tensor memory.  No cluster multicast is used.
 #include "common.cuh"
+#include <cuda.h>
+#include <cudaTypedefs.h>
 
-helm_status tc_prepare(helm_ctx* c, cudaStream_t s) { (void)c; (void)s; return HELM_ERR_UNSUPPORTED; }
+namespace {
+
+constexpr int BM = 128, BN = 128, BK = 32;      // BK fp32 elements = 128 bytes = one swizzle row
+constexpr int TILE = BM * BK * 4;               // 16 KiB: a 128-row tile of one K block
+constexpr int XSTAGES = 3, YSTAGES = 2;
+constexpr long WAIT_LIMIT = 1L << 20;
+
+struct TcState {
+    PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+    float* Bx[2] = {nullptr, nullptr};   // x-pass real-embedded operands, forward / inverse, [2N][2N]
+    float* Wy[2] = {nullptr, nullptr};   // y-pass operands, [2][N_y][ldw] (re plane, im plane)
+    int ldw = 0;
+    CUtensorMap mapBx[2];
+    CUtensorMap mapWy[2];
+};
+
+__device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+    for (long it = 0; it < WAIT_LIMIT; ++it) {
+        uint32_t ok;
+        asm volatile(
+            "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(ok)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+__device__ __forceinline__ void tma_2d(uint32_t dst, const CUtensorMap* map, uint32_t bar, int c0, int c1) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(dst),
+        "l"((uint64_t)map), "r"(bar), "r"(c0), "r"(c1)
+        : "memory");
+}
+__device__ __forceinline__ void tma_3d(uint32_t dst, const CUtensorMap* map, uint32_t bar, int c0, int c1, int c2) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], [%2];" ::"r"(
+            dst),
+        "l"((uint64_t)map), "r"(bar), "r"(c0), "r"(c1), "r"(c2)
+        : "memory");
+}
+// UMMA shared-memory descriptor: 128-byte swizzle, descriptor version 1.
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+    uint64_t d = (uint64_t)((addr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)2 << 61;
+    return d;
+}
+// instruction descriptor, kind::tf32: D = F32, A = B = TF32, majors, N >> 3, M >> 4
+__host__ __device__ constexpr uint32_t idesc_tf32(int M, int N, int a_mn, int b_mn) {
+    return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)a_mn << 15) | ((uint32_t)b_mn << 16) |
+           ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+__device__ __forceinline__ void mma_tf32(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\ntcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+#define TMEM_LD32(taddr, r)                                                                                          \
+    asm volatile(                                                                                                    \
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19," \
+        "%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"                                                     \
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),            \
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),      \
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),    \
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])     \
+        : "r"(taddr))
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// ---- x-pass: Out[M][N2] = alpha * A[M][K2] B[N2][K2]^T -------------------------------------------
+__global__ void __launch_bounds__(192, 1)
+xpass_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, float* __restrict__ out,
+                int M, int N2, int K2, float alpha, const double* __restrict__ alpha_dev, int aidx, unsigned* status) {
+    extern __shared__ uint8_t dsm[];
+    __shared__ __align__(8) uint64_t full[XSTAGES], empty[XSTAGES], accf;
+    __shared__ uint32_t tslot;
+    const uint32_t raw = su32(dsm);
+    const uint32_t base = (raw + 1023u) & ~1023u;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int n0 = blockIdx.x * BN, m0 = blockIdx.y * BM;
+    const int nk = (K2 + BK - 1) / BK;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < XSTAGES; ++s) { mbar_init(su32(&full[s]), 1); mbar_init(su32(&empty[s]), 1); }
+        mbar_init(su32(&accf), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&tslot)), "r"(BN)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem = tslot;
+    bool ok = true;
+    if (warp == 0) {
+        if (lane == 0) {
+            for (int kb = 0; kb < nk && ok; ++kb) {
+                const int s = kb % XSTAGES;
+                const uint32_t ph = (kb / XSTAGES) & 1;
+                if (kb >= XSTAGES) ok = mbar_wait(su32(&empty[s]), ph ^ 1);
+                if (!ok) break;
+                const uint32_t sa = base + s * 2 * TILE, sb = sa + TILE;
+                mbar_expect_tx(su32(&full[s]), 2 * TILE);
+                tma_2d(sa, &tmA, su32(&full[s]), kb * BK, m0);
+                tma_2d(sb, &tmB, su32(&full[s]), kb * BK, n0);
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            const uint32_t idesc = idesc_tf32(BM, BN, 0, 0);
+            for (int kb = 0; kb < nk && ok; ++kb) {
+                const int s = kb % XSTAGES;
+                const uint32_t ph = (kb / XSTAGES) & 1;
+                ok = mbar_wait(su32(&full[s]), ph);
+                if (!ok) break;
+                fence_after();
+                const uint32_t sa = base + s * 2 * TILE, sb = sa + TILE;
+#pragma unroll
+                for (int kk = 0; kk < BK / 8; ++kk)
+                    mma_tf32(tmem, sdesc(sa + kk * 32, 16, 1024), sdesc(sb + kk * 32, 16, 1024), idesc,
+                             (kb | kk) ? 1u : 0u);
+                mma_commit(su32(&empty[s]));
+            }
+            mma_commit(su32(&accf));
+        }
+    } else {
+        ok = mbar_wait(su32(&accf), 0);
+        ok = __all_sync(0xffffffffu, ok);
+        fence_after();
+        const int q = warp & 3;
+        const int row = m0 + 32 * q + lane;
+        const float al = alpha * (alpha_dev ? (float)alpha_dev[aidx] : 1.f);
+        if (ok) {
+#pragma unroll 1
+            for (int c = 0; c < BN; c += 32) {
+                uint32_t r[32];
+                TMEM_LD32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)c, r);
+                tmem_wait_ld();
+                const int col = n0 + c;
+                if (row < M && col < N2) {
+                    float* dst = out + (size_t)row * N2 + col;
+                    if (col + 32 <= N2) {
+#pragma unroll
+                        for (int v = 0; v < 32; v += 4)
+                            *reinterpret_cast<float4*>(dst + v) =
+                                make_float4(al * __uint_as_float(r[v]), al * __uint_as_float(r[v + 1]),
+                                            al * __uint_as_float(r[v + 2]), al * __uint_as_float(r[v + 3]));
+                    } else {
+#pragma unroll
+                        for (int v = 0; v < 32; ++v)
+                            if (col + v < N2) dst[v] = al * __uint_as_float(r[v]);
+                    }
+                }
+            }
+        }
+    }
+    if (!ok) atomicOr(status, (unsigned)HELM_DEV_WAIT);
+    fence_before();
+    __syncthreads();
+    if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(BN) : "memory");
+}
+
+// ---- y-pass: Out_l[ny][N2] = W Y_l, W = Wr + i Wi -------------------------------------------------
+__global__ void __launch_bounds__(192, 1)
+ypass_tc_kernel(const __grid_constant__ CUtensorMap tmW, const __grid_constant__ CUtensorMap tmY, float* __restrict__ out,
+                int ny, int N2, unsigned* status) {
+    extern __shared__ uint8_t dsm[];
+    __shared__ __align__(8) uint64_t full[YSTAGES], empty[YSTAGES], accf;
+    __shared__ uint32_t tslot;
+    const uint32_t raw = su32(dsm);
+    const uint32_t base = (raw + 1023u) & ~1023u;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int n0 = blockIdx.x * BN, m0 = blockIdx.y * BM, l = blockIdx.z;
+    const int nk = (ny + BK - 1) / BK;
+    constexpr int STAGE = 3 * TILE;   // Wr tile, Wi tile, B tile (4 boxes of 32 K-rows x 128 bytes)
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < YSTAGES; ++s) { mbar_init(su32(&full[s]), 1); mbar_init(su32(&empty[s]), 1); }
+        mbar_init(su32(&accf), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&tslot)), "r"(2 * BN)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem = tslot;
+    bool ok = true;
+    if (warp == 0) {
+        if (lane == 0) {
+            for (int kb = 0; kb < nk && ok; ++kb) {
+                const int s = kb % YSTAGES;
+                const uint32_t ph = (kb / YSTAGES) & 1;
+                if (kb >= YSTAGES) ok = mbar_wait(su32(&empty[s]), ph ^ 1);
+                if (!ok) break;
+                const uint32_t sw = base + s * STAGE, sb = sw + 2 * TILE;
+                mbar_expect_tx(su32(&full[s]), STAGE);
+                tma_3d(sw, &tmW, su32(&full[s]), kb * BK, m0, 0);
+                tma_3d(sw + TILE, &tmW, su32(&full[s]), kb * BK, m0, 1);
+#pragma unroll
+                for (int b = 0; b < BN / 32; ++b) tma_3d(sb + b * 4096, &tmY, su32(&full[s]), n0 + 32 * b, kb * BK, l);
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            const uint32_t idesc = idesc_tf32(BM, BN, 0, 1);
+            for (int kb = 0; kb < nk && ok; ++kb) {
+                const int s = kb % YSTAGES;
+                const uint32_t ph = (kb / YSTAGES) & 1;
+                ok = mbar_wait(su32(&full[s]), ph);
+                if (!ok) break;
+                fence_after();
+                const uint32_t sw = base + s * STAGE, sb = sw + 2 * TILE;
+#pragma unroll
+                for (int kk = 0; kk < BK / 8; ++kk) {
+                    const uint64_t bd = sdesc(sb + kk * 1024, 4096, 1024);   // MN-major: LBO = 32-column chunk
+                    const uint32_t acc = (kb | kk) ? 1u : 0u;
+                    mma_tf32(tmem, sdesc(sw + kk * 32, 16, 1024), bd, idesc, acc);
+                    mma_tf32(tmem + BN, sdesc(sw + TILE + kk * 32, 16, 1024), bd, idesc, acc);
+                }
+                mma_commit(su32(&empty[s]));
+            }
+            mma_commit(su32(&accf));
+        }
+    } else {
+        ok = mbar_wait(su32(&accf), 0);
+        ok = __all_sync(0xffffffffu, ok);
+        fence_after();
+        const int q = warp & 3;
+        const int row = m0 + 32 * q + lane;
+        if (ok) {
+#pragma unroll 1
+            for (int c = 0; c < BN; c += 32) {
+                uint32_t p[32], qq[32];
+                TMEM_LD32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)c, p);
+                TMEM_LD32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(BN + c), qq);
+                tmem_wait_ld();
+                const int col = n0 + c;
+                if (row < ny && col < N2) {
+                    float* dst = out + ((size_t)l * ny + row) * N2 + col;
+                    float o[32];
+#pragma unroll
+                    for (int v = 0; v < 32; v += 2) {
+                        o[v] = __uint_as_float(p[v]) - __uint_as_float(qq[v + 1]);
+                        o[v + 1] = __uint_as_float(p[v + 1]) + __uint_as_float(qq[v]);
+                    }
+                    if (col + 32 <= N2) {
+#pragma unroll
+                        for (int v = 0; v < 32; v += 4)
+                            *reinterpret_cast<float4*>(dst + v) = make_float4(o[v], o[v + 1], o[v + 2], o[v + 3]);
+                    } else {
+#pragma unroll
+                        for (int v = 0; v < 32; ++v)
+                            if (col + v < N2) dst[v] = o[v];
+                    }
+                }
+            }
+        }
+    }
+    if (!ok) atomicOr(status, (unsigned)HELM_DEV_WAIT);
+    fence_before();
+    __syncthreads();
+    if (warp == 1)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * BN) : "memory");
+}
+
+// ---- operand preparation (set-up) ----------------------------------------------------------------
+__device__ __forceinline__ float to_tf32(double v) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"((float)v));
+    return __uint_as_float(r);
+}
+
+// B[2n][2k] from W_kn = src[n][k] (src row-major N x N complex128)
+__global__ void embed_x_kernel(int N, const double2* __restrict__ src, float* __restrict__ B) {
+    const size_t id = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    if (id >= (size_t)N * N) return;
+    const int n = (int)(id / N), k = (int)(id % N);
+    const double2 w = src[(size_t)n * N + k];
+    const size_t L2 = 2 * (size_t)N;
+    B[(2 * n) * L2 + 2 * k] = to_tf32(w.x);
+    B[(2 * n) * L2 + 2 * k + 1] = to_tf32(-w.y);
+    B[(2 * n + 1) * L2 + 2 * k] = to_tf32(w.y);
+    B[(2 * n + 1) * L2 + 2 * k + 1] = to_tf32(w.x);
+}
+
+// W planes: re at [0][j'][j], im at [1][j'][j], row stride ldw (zero padded)
+__global__ void split_y_kernel(int N, int ldw, const double2* __restrict__ src, float* __restrict__ W) {
+    const size_t id = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    if (id >= (size_t)N * ldw) return;
+    const int r = (int)(id / ldw), k = (int)(id % ldw);
+    const double2 w = k < N ? src[(size_t)r * N + k] : make_double2(0.0, 0.0);
+    W[(size_t)r * ldw + k] = to_tf32(w.x);
+    W[(size_t)N * ldw + (size_t)r * ldw + k] = to_tf32(w.y);
+}
+
+helm_status encode(TcState* t, CUtensorMap* map, int rank, void* ptr, const cuuint64_t* dims, const cuuint64_t* strides,
+                   const cuuint32_t* box) {
+    cuuint32_t es[3] = {1, 1, 1};
+    CUresult r = t->encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, rank, ptr, dims, strides, box, es,
+                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? HELM_OK : HELM_ERR_CUDA;
+}
+
+size_t xsmem() { return (size_t)XSTAGES * 2 * TILE + 1024; }
+size_t ysmem() { return (size_t)YSTAGES * 3 * TILE + 1024; }
+
+}  // namespace
+
+helm_status tc_prepare(helm_ctx* c, cudaStream_t s) {
+    if (c->nx % 2 != 0) return HELM_ERR_UNSUPPORTED;
+    if (c->opt.precision != HELM_PREC_TF32) return HELM_ERR_UNSUPPORTED;   // split TF32 not built yet
+    TcState* t = new TcState();
+    c->tmaps = t;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", (void**)&t->encode, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess || q != cudaDriverEntryPointSuccess || !t->encode) {
+        cudaGetLastError();
+        return HELM_ERR_CUDA;
+    }
+    const int nx = c->nx, ny = c->ny;
+    const size_t nb = (size_t)4 * nx * nx;
+    t->ldw = (ny + 3) / 4 * 4;
+    const size_t nw = (size_t)2 * ny * t->ldw;
+    for (int i = 0; i < 2; ++i) {
+        if (cudaMalloc(&t->Bx[i], nb * sizeof(float)) != cudaSuccess) { cudaGetLastError(); return HELM_ERR_NOMEM; }
+        if (cudaMalloc(&t->Wy[i], nw * sizeof(float)) != cudaSuccess) { cudaGetLastError(); return HELM_ERR_NOMEM; }
+    }
+    // forward: W_kn = Vxi[n][k]; inverse: W_kn = Vx[n][k]
+    embed_x_kernel<<<(unsigned)((nx * (size_t)nx + 255) / 256), 256, 0, s>>>(nx, c->Vxi, t->Bx[0]);
+    embed_x_kernel<<<(unsigned)((nx * (size_t)nx + 255) / 256), 256, 0, s>>>(nx, c->Vx, t->Bx[1]);
+    split_y_kernel<<<(unsigned)((ny * (size_t)t->ldw + 255) / 256), 256, 0, s>>>(ny, t->ldw, c->Vyi, t->Wy[0]);
+    split_y_kernel<<<(unsigned)((ny * (size_t)t->ldw + 255) / 256), 256, 0, s>>>(ny, t->ldw, c->Vy, t->Wy[1]);
+    HELM_CUDA_TRY(cudaGetLastError());
+    for (int i = 0; i < 2; ++i) {
+        const cuuint64_t d[2] = {(cuuint64_t)2 * nx, (cuuint64_t)2 * nx};
+        const cuuint64_t st[1] = {(cuuint64_t)2 * nx * sizeof(float)};
+        const cuuint32_t box[2] = {BK, BN};
+        if (encode(t, &t->mapBx[i], 2, t->Bx[i], d, st, box) != HELM_OK) return HELM_ERR_CUDA;
+        const cuuint64_t dw[3] = {(cuuint64_t)ny, (cuuint64_t)ny, 2};
+        const cuuint64_t sw[2] = {(cuuint64_t)t->ldw * sizeof(float), (cuuint64_t)t->ldw * ny * sizeof(float)};
+        const cuuint32_t bw[3] = {BK, BM, 1};
+        if (encode(t, &t->mapWy[i], 3, t->Wy[i], dw, sw, bw) != HELM_OK) return HELM_ERR_CUDA;
+    }
+    HELM_CUDA_TRY(cudaFuncSetAttribute(xpass_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)xsmem()));
+    HELM_CUDA_TRY(cudaFuncSetAttribute(ypass_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ysmem()));
+    return HELM_OK;
+}
+
 helm_status tc_xpass(helm_ctx* c, int inverse, const float2* in, float2* out, float alpha, const double* alpha_dev,
                      int aidx, cudaStream_t s) {
-    (void)c; (void)inverse; (void)in; (void)out; (void)alpha; (void)alpha_dev; (void)aidx; (void)s;
-    return HELM_ERR_UNSUPPORTED;
+    TcState* t = (TcState*)c->tmaps;
+    if (!t) return HELM_ERR_UNSUPPORTED;
+    const int M = c->ny * c->nz, N2 = 2 * c->nx;
+    CUtensorMap mapA;
+    const cuuint64_t d[2] = {(cuuint64_t)N2, (cuuint64_t)M};
+    const cuuint64_t st[1] = {(cuuint64_t)N2 * sizeof(float)};
+    const cuuint32_t box[2] = {BK, BM};
+    if (encode(t, &mapA, 2, (void*)in, d, st, box) != HELM_OK) return HELM_ERR_CUDA;
+    dim3 grid((N2 + BN - 1) / BN, (M + BM - 1) / BM);
+    xpass_tc_kernel<<<grid, 192, xsmem(), s>>>(mapA, t->mapBx[inverse ? 1 : 0], (float*)out, M, N2, N2, alpha, alpha_dev,
+                                                aidx, c->status_d);
+    HELM_CUDA_TRY(cudaGetLastError());
+    return HELM_OK;
 }
+
 helm_status tc_ypass(helm_ctx* c, int inverse, const float2* in, float2* out, cudaStream_t s) {
-    (void)c; (void)inverse; (void)in; (void)out; (void)s;
-    return HELM_ERR_UNSUPPORTED;
+    TcState* t = (TcState*)c->tmaps;
+    if (!t) return HELM_ERR_UNSUPPORTED;
+    const int ny = c->ny, N2 = 2 * c->nx;
+    CUtensorMap mapY;
+    const cuuint64_t d[3] = {(cuuint64_t)N2, (cuuint64_t)ny, (cuuint64_t)c->nz};
+    const cuuint64_t st[2] = {(cuuint64_t)N2 * sizeof(float), (cuuint64_t)N2 * ny * sizeof(float)};
+    const cuuint32_t box[3] = {32, BK, 1};
+    if (encode(t, &mapY, 3, (void*)in, d, st, box) != HELM_OK) return HELM_ERR_CUDA;
+    dim3 grid((N2 + BN - 1) / BN, (ny + BM - 1) / BM, c->nz);
+    ypass_tc_kernel<<<grid, 192, ysmem(), s>>>(t->mapWy[inverse ? 1 : 0], mapY, (float*)out, ny, N2, c->status_d);
+    HELM_CUDA_TRY(cudaGetLastError());
+    return HELM_OK;
 }
-void tc_release(helm_ctx* c) { (void)c; }
+
+void tc_release(helm_ctx* c) {
+    TcState* t = (TcState*)c->tmaps;
+    if (!t) return;
+    for (int i = 0; i < 2; ++i) { cudaFree(t->Bx[i]); cudaFree(t->Wy[i]); }
+    delete t;
+    c->tmaps = nullptr;
+}

@@ -445,6 +445,7 @@ helm_status gmres_run(helm_ctx* c, const double2* b_in, double2* x_in, helm_solv
     if (!xdev) HELM_CUDA_TRY(cudaMemcpyAsync(x_in, x, vbytes, cudaMemcpyDeviceToHost, s));
     HELM_CUDA_TRY(cudaStreamSynchronize(s));
     if (result == HELM_OK && (dstat & HELM_DEV_PIVOT)) result = HELM_ERR_PIVOT;
+    if (dstat & HELM_DEV_WAIT) result = HELM_ERR_ITER_LIMIT;
     if (info) {
         info->status = result;
         info->iterations = its;
