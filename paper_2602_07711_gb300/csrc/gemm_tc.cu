@@ -8,7 +8,7 @@
 //     B[2n][2k] = Re W_kn,  B[2n][2k+1] = -Im W_kn,  B[2n+1][2k] = Im W_kn,  B[2n+1][2k+1] = Re W_kn.
 //   A = the grid viewed as (N_y N_z) x 2N_x (K-major, straight from HBM by TMA), B = 2N_x x 2N_x (K-major).
 // y-pass (left multiply per slice, contraction over y):  Out_l = W Y_l with Y_l viewed as N_y x 2N_x real
-//   (N contiguous, "MN-major").  Two accumulators P = Re(W) Y_l and Q = Im(W) Y_l share every B tile; the
+//   (N contiguous, "MN-major", staged with the 32-byte-chunk 128-byte swizzle).  Two accumulators P = Re(W) Y_l and Q = Im(W) Y_l share every B tile; the
 //   epilogue forms Out_re = P_re - Q_im, Out_im = P_im + Q_re.
 //
 // Kernel structure (one 128 x 128 output tile per CTA, 192 threads, two CTAs per SM):
@@ -72,13 +72,15 @@ __device__ __forceinline__ void tma_3d(uint32_t dst, const CUtensorMap* map, uin
         "l"((uint64_t)map), "r"(bar), "r"(c0), "r"(c1), "r"(c2)
         : "memory");
 }
-// UMMA shared-memory descriptor: 128-byte swizzle, descriptor version 1.
-__device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+// UMMA shared-memory descriptor, version 1.  Layout 2 = 128-byte swizzle of 16-byte chunks (K-major
+// operands here); layout 1 = 128-byte swizzle of 32-byte chunks, the form 32-bit (TF32) MN-major operands
+// take, whose swizzle atom is 4 rows x 128 bytes (TMA: CU_TENSOR_MAP_SWIZZLE_128B_ATOM_32B).
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t sbo, uint32_t layout = 2) {
     uint64_t d = (uint64_t)((addr & 0x3FFFFu) >> 4);
     d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
     d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
     d |= (uint64_t)1 << 46;
-    d |= (uint64_t)2 << 61;
+    d |= (uint64_t)layout << 61;
     return d;
 }
 // instruction descriptor, kind::tf32: D = F32, A = B = TF32, majors, N >> 3, M >> 4
@@ -258,7 +260,8 @@ ypass_tc_kernel(const __grid_constant__ CUtensorMap tmW, const __grid_constant__
                 const uint32_t sw = base + s * STAGE, sb = sw + 2 * TILE;
 #pragma unroll
                 for (int kk = 0; kk < BK / 8; ++kk) {
-                    const uint64_t bd = sdesc(sb + kk * 1024, 4096, 1024);   // MN-major: LBO = 32-column chunk
+                    // MN-major: LBO = next 32-column chunk (4 KiB), SBO = next 4-row K group (512 B)
+                    const uint64_t bd = sdesc(sb + kk * 1024, 4096, 512, 1);
                     const uint32_t acc = (kb | kk) ? 1u : 0u;
                     mma_tf32(tmem, sdesc(sw + kk * 32, 16, 1024), bd, idesc, acc);
                     mma_tf32(tmem + BN, sdesc(sw + TILE + kk * 32, 16, 1024), bd, idesc, acc);
@@ -340,10 +343,10 @@ __global__ void split_y_kernel(int N, int ldw, const double2* __restrict__ src, 
 }
 
 helm_status encode(TcState* t, CUtensorMap* map, int rank, void* ptr, const cuuint64_t* dims, const cuuint64_t* strides,
-                   const cuuint32_t* box) {
+                   const cuuint32_t* box, CUtensorMapSwizzle swz = CU_TENSOR_MAP_SWIZZLE_128B) {
     cuuint32_t es[3] = {1, 1, 1};
     CUresult r = t->encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, rank, ptr, dims, strides, box, es,
-                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                           CU_TENSOR_MAP_INTERLEAVE_NONE, swz, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS ? HELM_OK : HELM_ERR_CUDA;
 }
@@ -418,7 +421,7 @@ helm_status tc_ypass(helm_ctx* c, int inverse, const float2* in, float2* out, cu
     const cuuint64_t d[3] = {(cuuint64_t)N2, (cuuint64_t)ny, (cuuint64_t)c->nz};
     const cuuint64_t st[2] = {(cuuint64_t)N2 * sizeof(float), (cuuint64_t)N2 * ny * sizeof(float)};
     const cuuint32_t box[3] = {32, BK, 1};
-    if (encode(t, &mapY, 3, (void*)in, d, st, box) != HELM_OK) return HELM_ERR_CUDA;
+    if (encode(t, &mapY, 3, (void*)in, d, st, box, CU_TENSOR_MAP_SWIZZLE_128B_ATOM_32B) != HELM_OK) return HELM_ERR_CUDA;
     dim3 grid((N2 + BN - 1) / BN, (ny + BM - 1) / BM, c->nz);
     ypass_tc_kernel<<<grid, 192, ysmem(), s>>>(t->mapWy[inverse ? 1 : 0], mapY, (float*)out, ny, N2, c->status_d);
     HELM_CUDA_TRY(cudaGetLastError());
