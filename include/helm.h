@@ -135,6 +135,14 @@ helm_status helm_get_eig(helm_ctx* ctx, int axis, void* D, void* V, void* Vinv);
  * residual.  Synchronises `stream`. */
 helm_status helm_gmres_solve(helm_ctx* ctx, const void* b, void* x, helm_solve_info* info, void* stream);
 
+/* helm_residual - r = b - A x and its norms, the rel-res numerator of Sec. 5.1, computed with about 44
+ * significant bits (double-float arithmetic on the FP32 pipes) from complex128 b and x.
+ *   b, x   complex128 device buffers;  r  complex64 device output (may be NULL);
+ *   nrm2   receives ||b - A x||_2, nrmi receives ||b - A x||_inf (either may be NULL).
+ * Synchronises `stream`. */
+helm_status helm_residual(helm_ctx* ctx, const void* b, const void* x, void* r, double* nrm2, double* nrmi,
+                          void* stream);
+
 /* helm_profile - enable (1) or disable (0) per-kernel timing on this context: CUDA events are recorded
  * on the launch stream around every kernel launch of the solver (adds no synchronisation).  The first
  * call allocates the event pool (host-side cost only). */

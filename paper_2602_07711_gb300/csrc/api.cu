@@ -33,7 +33,7 @@ void free_ctx(helm_ctx* c) {
     prof_release(c);
     void* ps[] = {c->k2_d, c->k2_f, c->dk2_d[0], c->dk2_d[1], c->dk2_d[2], c->dk2_f[0], c->dk2_f[1], c->dk2_f[2],
                   c->G_d, c->G_f, c->Dx, c->Dy, c->Vx, c->Vxi, c->Vy, c->Vyi, c->XF, c->XI, c->YF, c->YI,
-                  c->dxs, c->dys, c->cz, c->tmp, c->status_d};
+                  c->dxs, c->dys, c->cz, c->tmp, c->status_d, c->k2_df, c->G_df};
     for (void* p : ps) if (p) cudaFree(p);
     delete c;
 }
@@ -100,10 +100,12 @@ helm_status helm_setup(const helm_grid* grid, const void* k2, double k0, const d
     const size_t n = c->npts;
     TRY(dalloc(&c->k2_d, n));
     TRY(dalloc(&c->k2_f, n));
+    TRY(dalloc(&c->k2_df, n));
     if (opt->order == 6) {
         for (int d = 0; d < 3; ++d) { TRY(dalloc(&c->dk2_d[d], n)); TRY(dalloc(&c->dk2_f[d], n)); }
         TRY(dalloc(&c->G_d, n));
         TRY(dalloc(&c->G_f, n));
+        TRY(dalloc(&c->G_df, n));
     }
     TRY(dalloc(&c->tmp, n));
     TRY(dalloc(&c->status_d, 1));
@@ -190,6 +192,13 @@ helm_status helm_get_eig(helm_ctx* c, int axis, void* D, void* V, void* Vinv) {
 helm_status helm_gmres_solve(helm_ctx* c, const void* b, void* x, helm_solve_info* info, void* stream) {
     if (!c || !b || !x) return HELM_ERR_ARG;
     return gmres_run(c, (const double2*)b, (double2*)x, info, (cudaStream_t)stream);
+}
+
+helm_status helm_residual(helm_ctx* c, const void* b, const void* x, void* r, double* nrm2, double* nrmi,
+                          void* stream) {
+    if (!c || !b || !x) return HELM_ERR_ARG;
+    if (!dev_ptr(b) || !dev_ptr(x) || (r && !dev_ptr(r))) return HELM_ERR_ARG;
+    return residual_run(c, (const double2*)b, (const double2*)x, (float2*)r, nrm2, nrmi, (cudaStream_t)stream);
 }
 
 void helm_destroy(helm_ctx* c) { free_ctx(c); }

@@ -106,6 +106,8 @@ struct helm_ctx {
     float2* dk2_f[3] = {nullptr, nullptr, nullptr};
     double2* G_d = nullptr;
     float2* G_f = nullptr;
+    float4* k2_df = nullptr;                // double-float k^2 and G for the true residual
+    float4* G_df = nullptr;
     // 1D eigendecompositions, FP64 (row-major [row][col])
     double2 *Dx = nullptr, *Dy = nullptr, *Vx = nullptr, *Vxi = nullptr, *Vy = nullptr, *Vyi = nullptr;
     // complex64 transform operands
@@ -130,7 +132,7 @@ struct helm_ctx {
 helm_status launch_derived_fields(helm_ctx* c, cudaStream_t s);
 helm_status launch_stencil_f32(helm_ctx* c, const float2* x, float2* y, const double* sigma, int sidx, cudaStream_t s);
 helm_status launch_stencil_f64(helm_ctx* c, const double2* x, double2* y, cudaStream_t s);
-helm_status launch_residual(helm_ctx* c, const double2* x, const double2* F, float2* r, double* part, int nblk, cudaStream_t s);
+helm_status launch_residual(helm_ctx* c, const float4* x, const float4* F, float2* r, double* part, cudaStream_t s);
 helm_status launch_rhs(helm_ctx* c, const double2* f, double2* F, cudaStream_t s);
 // eig.cu
 helm_status run_eig_setup(helm_ctx* c, cudaStream_t s);
@@ -152,3 +154,5 @@ helm_status precond_step(helm_ctx* c, int step, const float2* in, float2* out, c
 // krylov.cu
 helm_status gmres_run(helm_ctx* c, const double2* b, double2* x, helm_solve_info* info, cudaStream_t s);
 void krylov_free(helm_ctx* c);
+helm_status residual_run(helm_ctx* c, const double2* b, const double2* x, float2* r, double* nrm2, double* nrmi,
+                         cudaStream_t s);

@@ -10,7 +10,9 @@
 // The iterate x is complex128.  Each cycle ends with the FP64 true residual r = F - A x (Sec. 5.1 rel-res),
 // which decides convergence and seeds the next cycle.
 #include "common.cuh"
+#include "dfloat.cuh"
 #include <chrono>
+#include <cmath>
 #include <vector>
 
 int residual_ctas(const helm_ctx* c);
@@ -43,6 +45,9 @@ struct KrylovWork {
     Ctrl* ctrl_h = nullptr;  // pinned
     double2* xbuf = nullptr; // device copy of x when the caller passes host memory
     double2* bbuf = nullptr;
+    float4* xdf = nullptr;   // the iterate in double-float (re.hi, im.hi, re.lo, im.lo)
+    float4* Fdf = nullptr;   // the right-hand side in double-float
+    unsigned* nzflag = nullptr;
 };
 
 namespace {
@@ -215,45 +220,86 @@ __global__ void lsq_kernel(const double2* __restrict__ H, const double2* __restr
     }
 }
 
-// flexible: x += sum_i y_i Z_i  (FP64 accumulation)
+// flexible: x += sum_i y_i Z_i, in double-float (y_i split from FP64, products exact via FMA)
 __global__ void __launch_bounds__(NT) combine_flex_kernel(const float2* __restrict__ Z, size_t npts, int k,
-                                                         const double2* __restrict__ y, double2* __restrict__ x) {
-    __shared__ double2 ys[64];
-    for (int i = threadIdx.x; i < k; i += NT) ys[i] = y[i];
+                                                         const double2* __restrict__ y, float4* __restrict__ x) {
+    __shared__ cdf ys[64];
+    for (int i = threadIdx.x; i < k; i += NT) ys[i] = cdf{df_from_double(y[i].x), df_from_double(y[i].y)};
     __syncthreads();
     for (size_t id = blockIdx.x * (size_t)NT + threadIdx.x; id < npts; id += (size_t)gridDim.x * NT) {
-        double2 a = x[id];
-        for (int i = 0; i < k; ++i) {
-            const float2 z = Z[(size_t)i * npts + id];
-            a.x += ys[i].x * z.x - ys[i].y * z.y;
-            a.y += ys[i].x * z.y + ys[i].y * z.x;
-        }
-        x[id] = a;
+        cdf a = cdf_from4(x[id]);
+        for (int i = 0; i < k; ++i) a = cdf_add(a, cdf_mul_f2(ys[i], Z[(size_t)i * npts + id]));
+        x[id] = cdf_to4(a);
     }
 }
 
-// right-preconditioned: u = sum_i (y_i sigma_i) V_i  (complex64)
+// right-preconditioned: u = sum_i (y_i sigma_i) V_i  (complex64; u is a complex64 preconditioner input)
 __global__ void __launch_bounds__(NT) combine_v_kernel(const float2* __restrict__ V, size_t npts, int k,
                                                       const double2* __restrict__ y, const double* __restrict__ sigma,
                                                       float2* __restrict__ u) {
-    __shared__ double2 ys[64];
-    for (int i = threadIdx.x; i < k; i += NT) ys[i] = cscale(y[i], sigma[i]);
+    __shared__ float2 ys[64];
+    for (int i = threadIdx.x; i < k; i += NT) {
+        const double2 v = cscale(y[i], sigma[i]);
+        ys[i] = make_float2((float)v.x, (float)v.y);
+    }
     __syncthreads();
     for (size_t id = blockIdx.x * (size_t)NT + threadIdx.x; id < npts; id += (size_t)gridDim.x * NT) {
-        double ax = 0, ay = 0;
-        for (int i = 0; i < k; ++i) {
-            const float2 v = V[(size_t)i * npts + id];
-            ax += ys[i].x * v.x - ys[i].y * v.y;
-            ay += ys[i].x * v.y + ys[i].y * v.x;
-        }
-        u[id] = make_float2((float)ax, (float)ay);
+        float2 a = make_float2(0.f, 0.f);
+        for (int i = 0; i < k; ++i) a = cfma(ys[i], V[(size_t)i * npts + id], a);
+        u[id] = a;
     }
 }
 
-__global__ void add_kernel(const float2* __restrict__ z, double2* __restrict__ x, size_t npts) {
+// x += z in double-float
+__global__ void add_kernel(const float2* __restrict__ z, float4* __restrict__ x, size_t npts) {
     for (size_t id = blockIdx.x * (size_t)blockDim.x + threadIdx.x; id < npts; id += (size_t)gridDim.x * blockDim.x) {
-        x[id].x += z[id].x;
-        x[id].y += z[id].y;
+        const float2 v = z[id];
+        x[id] = cdf_to4(cdf_add(cdf_from4(x[id]), cdf_from_f2(v)));
+    }
+}
+
+// FP64 -> double-float; flags a nonzero entry of a (used to recognise x0 = 0)
+__global__ void to_df_kernel(const double2* __restrict__ a, float4* __restrict__ b, size_t npts, unsigned* nz) {
+    unsigned any = 0;
+    for (size_t id = blockIdx.x * (size_t)blockDim.x + threadIdx.x; id < npts; id += (size_t)gridDim.x * blockDim.x) {
+        const double2 v = a[id];
+        const float rh = (float)v.x, ih = (float)v.y;
+        b[id] = make_float4(rh, ih, (float)(v.x - (double)rh), (float)(v.y - (double)ih));
+        any |= (v.x != 0.0 || v.y != 0.0);
+    }
+    if (nz && __any_sync(0xffffffffu, any) && (threadIdx.x & 31) == 0) atomicOr(nz, 1u);
+}
+
+__global__ void from_df_kernel(const float4* __restrict__ a, double2* __restrict__ b, size_t npts) {
+    for (size_t id = blockIdx.x * (size_t)blockDim.x + threadIdx.x; id < npts; id += (size_t)gridDim.x * blockDim.x) {
+        const float4 v = a[id];
+        b[id] = make_double2((double)v.x + (double)v.z, (double)v.y + (double)v.w);
+    }
+}
+
+// r = F (x = 0): complex64 copy of F with the residual partials of the stencil form
+__global__ void __launch_bounds__(NT) residual_zero_kernel(const float4* __restrict__ F, float2* __restrict__ r,
+                                                          size_t npts, double* __restrict__ part) {
+    __shared__ double rs[NT / 32], rm[NT / 32];
+    double s = 0, mx = 0;
+    for (size_t id = blockIdx.x * (size_t)NT + threadIdx.x; id < npts; id += (size_t)gridDim.x * NT) {
+        const float2 v = cdf_round(cdf_from4(F[id]));
+        r[id] = v;
+        const double a2 = (double)v.x * v.x + (double)v.y * v.y;
+        s += a2;
+        mx = fmax(mx, a2);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        s += __shfl_down_sync(0xffffffffu, s, o);
+        mx = fmax(mx, __shfl_down_sync(0xffffffffu, mx, o));
+    }
+    if ((threadIdx.x & 31) == 0) { rs[threadIdx.x >> 5] = s; rm[threadIdx.x >> 5] = mx; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double ss = 0, m = 0;
+        for (int w = 0; w < NT / 32; ++w) { ss += rs[w]; m = fmax(m, rm[w]); }
+        part[2 * blockIdx.x] = ss;
+        part[2 * blockIdx.x + 1] = sqrt(m);
     }
 }
 
@@ -314,6 +360,9 @@ helm_status ensure_work(helm_ctx* c) {
     HELM_CUDA_TRY(cudaMalloc(&k->coef, sizeof(float2) * (m + 1)));
     HELM_CUDA_TRY(cudaMalloc(&k->ctrl_d, sizeof(Ctrl)));
     HELM_CUDA_TRY(cudaMallocHost(&k->ctrl_h, sizeof(Ctrl)));
+    if (cudaMalloc(&k->xdf, c->npts * sizeof(float4)) != cudaSuccess) return HELM_ERR_NOMEM;
+    if (cudaMalloc(&k->Fdf, c->npts * sizeof(float4)) != cudaSuccess) return HELM_ERR_NOMEM;
+    HELM_CUDA_TRY(cudaMalloc(&k->nzflag, sizeof(unsigned)));
     HELM_CUDA_TRY(cudaMemset(k->H, 0, sizeof(double2) * (m + 1) * m));
     HELM_CUDA_TRY(cudaMemset(k->ctrl_d, 0, sizeof(Ctrl)));
     return HELM_OK;
@@ -325,10 +374,17 @@ helm_status read_ctrl(KrylovWork* k, cudaStream_t s) {
     return HELM_OK;
 }
 
-helm_status true_residual(helm_ctx* c, const double2* b, const double2* x, int first, cudaStream_t s) {
+helm_status true_residual(helm_ctx* c, bool xzero, int first, cudaStream_t s) {
     KrylovWork* k = c->kw;
-    helm_status st = launch_residual(c, x, b, k->V, k->rpart, k->nres, s);
-    if (st != HELM_OK) return st;
+    if (xzero) {
+        prof_begin(c, s, PROF_OTHER);
+        residual_zero_kernel<<<k->nres, NT, 0, s>>>(k->Fdf, k->V, c->npts, k->rpart);
+        prof_end(c, s);
+        HELM_CUDA_TRY(cudaGetLastError());
+    } else {
+        helm_status st = launch_residual(c, k->xdf, k->Fdf, k->V, k->rpart, s);
+        if (st != HELM_OK) return st;
+    }
     prof_begin(c, s, PROF_SMALL);
     resnorm_kernel<<<1, 256, 0, s>>>(k->rpart, k->nres, k->sigma, k->g, k->m, k->ctrl_d, first);
     prof_end(c, s);
@@ -343,7 +399,8 @@ void krylov_free(helm_ctx* c) {
     if (!k) return;
     cudaFree(k->V); cudaFree(k->Z); cudaFree(k->sigma); cudaFree(k->H); cudaFree(k->cs); cudaFree(k->sn);
     cudaFree(k->g); cudaFree(k->y); cudaFree(k->part); cudaFree(k->rpart); cudaFree(k->coef); cudaFree(k->ctrl_d);
-    cudaFreeHost(k->ctrl_h); cudaFree(k->xbuf); cudaFree(k->bbuf);
+    cudaFreeHost(k->ctrl_h); cudaFree(k->xbuf); cudaFree(k->bbuf); cudaFree(k->xdf); cudaFree(k->Fdf);
+    cudaFree(k->nzflag);
     delete k;
     c->kw = nullptr;
 }
@@ -373,7 +430,14 @@ helm_status gmres_run(helm_ctx* c, const double2* b_in, double2* x_in, helm_solv
     const int ublocks = NB;
     int its = 0, restarts = 0;
     helm_status result = HELM_ERR_NOT_CONVERGED;
-    if ((st = true_residual(c, b, x, 1, s)) != HELM_OK) return st;
+    // internal double-float copies of b and x; x0 = 0 is recognised and then r0 = b without a matvec
+    unsigned xnz = 0;
+    HELM_CUDA_TRY(cudaMemsetAsync(k->nzflag, 0, sizeof(unsigned), s));
+    to_df_kernel<<<NB, NT, 0, s>>>(b, k->Fdf, npts, nullptr);
+    to_df_kernel<<<NB, NT, 0, s>>>(x, k->xdf, npts, k->nzflag);
+    HELM_CUDA_TRY(cudaMemcpyAsync(&xnz, k->nzflag, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+    HELM_CUDA_TRY(cudaStreamSynchronize(s));
+    if ((st = true_residual(c, xnz == 0, 1, s)) != HELM_OK) return st;
     const double beta0 = k->ctrl_h->beta0;
     double est = 1.0;
     if (!(beta0 > 0)) {
@@ -422,7 +486,7 @@ helm_status gmres_run(helm_ctx* c, const double2* b_in, double2* x_in, helm_solv
             prof_end(c, s);
             if (flex) {
                 prof_begin(c, s, PROF_COMBINE);
-                combine_flex_kernel<<<NB, NT, 0, s>>>(k->Z, npts, kk, k->y, x);
+                combine_flex_kernel<<<NB, NT, 0, s>>>(k->Z, npts, kk, k->y, k->xdf);
                 prof_end(c, s);
             } else {
                 float2* u = k->V + (size_t)kk * npts;   // V_kk is not needed by the update
@@ -431,16 +495,17 @@ helm_status gmres_run(helm_ctx* c, const double2* b_in, double2* x_in, helm_solv
                 prof_end(c, s);
                 if ((st = precond_apply(c, u, u, nullptr, 0, s)) != HELM_OK) return st;
                 prof_begin(c, s, PROF_COMBINE);
-                add_kernel<<<NB, NT, 0, s>>>(u, x, npts);
+                add_kernel<<<NB, NT, 0, s>>>(u, k->xdf, npts);
                 prof_end(c, s);
             }
             HELM_CUDA_TRY(cudaGetLastError());
             ++restarts;
-            if ((st = true_residual(c, b, x, 0, s)) != HELM_OK) return st;
+            if ((st = true_residual(c, false, 0, s)) != HELM_OK) return st;
             if (breakdown && k->ctrl_h->beta / beta0 > c->opt.rtol) { result = HELM_ERR_BREAKDOWN; break; }
         }
     }
     unsigned dstat = 0;
+    from_df_kernel<<<NB, NT, 0, s>>>(k->xdf, x, npts);
     HELM_CUDA_TRY(cudaMemcpyAsync(&dstat, c->status_d, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
     if (!xdev) HELM_CUDA_TRY(cudaMemcpyAsync(x_in, x, vbytes, cudaMemcpyDeviceToHost, s));
     HELM_CUDA_TRY(cudaStreamSynchronize(s));
@@ -456,4 +521,25 @@ helm_status gmres_run(helm_ctx* c, const double2* b_in, double2* x_in, helm_solv
         info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     }
     return result;
+}
+
+// r = b - A x with the double-float residual kernel; |r|_2 and |r|_inf in FP64 (helm_residual).
+helm_status residual_run(helm_ctx* c, const double2* b, const double2* x, float2* r, double* nrm2, double* nrmi,
+                         cudaStream_t s) {
+    helm_status st = ensure_work(c);
+    if (st != HELM_OK) return st;
+    KrylovWork* k = c->kw;
+    const size_t npts = c->npts;
+    to_df_kernel<<<k->NB, NT, 0, s>>>(b, k->Fdf, npts, nullptr);
+    to_df_kernel<<<k->NB, NT, 0, s>>>(x, k->xdf, npts, nullptr);
+    HELM_CUDA_TRY(cudaGetLastError());
+    if ((st = launch_residual(c, k->xdf, k->Fdf, r ? r : k->V, k->rpart, s)) != HELM_OK) return st;
+    std::vector<double> h(2 * (size_t)k->nres);
+    HELM_CUDA_TRY(cudaMemcpyAsync(h.data(), k->rpart, h.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+    HELM_CUDA_TRY(cudaStreamSynchronize(s));
+    double t = 0, m = 0;
+    for (int i = 0; i < k->nres; ++i) { t += h[2 * i]; m = m > h[2 * i + 1] ? m : h[2 * i + 1]; }
+    if (nrm2) *nrm2 = sqrt(t);
+    if (nrmi) *nrmi = m;
+    return HELM_OK;
 }

@@ -1,21 +1,34 @@
 // Stencil kernels: the compact 4th/6th-order operator A with the two-point ABC ghosts eliminated,
-// its FP64 residual form, the coefficient fields of the sixth-order scheme and the modified
+// its high-precision residual form, the coefficient fields of the sixth-order scheme and the modified
 // right-hand sides.
 //
-//   Eq. scheme4 (P. Sec. 2.2): (dxx+dyy+dzz)U + sum_pairs (ha^2+hb^2)/12 da2 db2 U
-//                               + (1 + sum_d hd^2/12 dd2)(k^2 U)
+//   Eq. scheme4 (Sec. 2.2): (dxx+dyy+dzz)U + sum_pairs (ha^2+hb^2)/12 da2 db2 U + (1 + sum_d hd^2/12 dd2)(k^2 U)
 //   Eq. scheme6 (Sec. 2.3, uniform h), with the difference operators acting on the product grid
 //   functions k^2 U and the U-free parts moved to the right-hand side:
 //     L[(1 + h^2 k^2/30)U] + h^4/30 dxx dyy dzz U + k^2 U + h^2/6 M[(1 + h^2 k^2/15)U]
 //     + h^2/20 { (lap k^2 - k^4) U + 2 sum_d (k^2)_d ( d_d[(1 + h^2 k^2/6)U] + h^2/6 d_d T_d U ) }
+//   Collecting the weights of U over the 3x3x3 cube and of KU = k^2 U over its 19 face/edge points:
+//     A6 U = (1/h^2) [ (7/15) S_f + (1/10) S_e + (1/30) S_c - (64/15) U_0 ]
+//          + (14/15) KU_0 + (1/90)(KU_e - KU_f) + (h^2/20) G U_0 + (h/20) sum_d g_d D_d
+//   with S_f, S_e, S_c the sums of U over the 6 faces, 12 edges and 8 corners, KU_f and KU_e the sums of
+//   KU over faces and edges, G = lap k^2 - k^4, g_d = (k^2)_d and
+//     D_d = (U_+ - U_-) + (h^2/6)(KU_+ - KU_-) + (1/6)(T_+ - T_-),
+//   T_+- = (sum of the four transverse neighbours of the side point) - 4 (side point).
 //   Ghosts (Eq. D_bc): U_0 = gamma U_1, U_{N+1} = gamma U_N per direction (edge and corner ghosts take
 //   the product of the gammas); k^2 at a ghost is the mirror value of its neighbour.
 //
+// Arithmetic policies: complex64 (the Krylov matvec), complex128 (helm_apply_A in FP64) and
+// double-float complex (hi + lo pairs of floats, about 44 significant bits) for the true residual F - A x.
+// GB300 executes FP32 at roughly sixty times its FP64 rate, so the residual runs on the FP32 pipes with
+// error-free transformations.  The gradient terms (h/20) g_d D_d are below 1e-3 of the total at the
+// resolutions of interest and are evaluated in the policy's low precision (FP32 for complex64 and
+// double-float, FP64 for complex128).
+//
 // Design: 2.5D blocking.  A CTA owns a 32 x 8 column tile and marches along z through ZCH planes.
 // Each plane (with a one-point halo) is staged once in shared memory; every thread lifts its 3 x 3
-// neighbourhood into registers and keeps the previous two planes there, so a point costs 9 + 9
-// shared-memory reads and one HBM read/write of each field (24 B/pt at order 4, 56 B/pt at order 6).
+// neighbourhood into registers and keeps the previous two planes there.
 #include "common.cuh"
+#include "dfloat.cuh"
 
 namespace {
 
@@ -25,154 +38,210 @@ constexpr int PX = TX + 2;
 constexpr int PY = TY + 2;
 constexpr int ZCH = 32;
 
-template <typename C>
-__device__ inline C czero() { C r; r.x = 0; r.y = 0; return r; }
+// ---- arithmetic policies ----------------------------------------------------------------------
+struct P32 {
+    typedef float2 C;    // register value
+    typedef float2 M;    // storage
+    typedef float S;     // scalar
+    typedef float2 LC;   // low-precision complex for the small terms
+    static __device__ __forceinline__ C ld(const M* p, size_t i) { return p[i]; }
+    static __device__ __forceinline__ C add(C a, C b) { return make_float2(a.x + b.x, a.y + b.y); }
+    static __device__ __forceinline__ C sub(C a, C b) { return make_float2(a.x - b.x, a.y - b.y); }
+    static __device__ __forceinline__ C mul(C a, C b) { return cmul(a, b); }
+    static __device__ __forceinline__ C scl(C a, S s) { return make_float2(a.x * s, a.y * s); }
+    static __host__ __device__ __forceinline__ S cst(double v) { return (float)v; }
+    static __device__ __forceinline__ C zero() { return make_float2(0.f, 0.f); }
+    static __device__ __forceinline__ LC lo(C a) { return a; }
+    static __device__ __forceinline__ C from_lo(LC a) { return a; }
+    static __device__ __forceinline__ void st(M* d, C v) { *d = v; }
+    static __device__ __forceinline__ float2 r32(C v) { return v; }
+    static __host__ C hc(double2 v) { return make_float2((float)v.x, (float)v.y); }
+};
+struct P64 {
+    typedef double2 C;
+    typedef double2 M;
+    typedef double S;
+    typedef double2 LC;
+    static __device__ __forceinline__ C ld(const M* p, size_t i) { return p[i]; }
+    static __device__ __forceinline__ C add(C a, C b) { return make_double2(a.x + b.x, a.y + b.y); }
+    static __device__ __forceinline__ C sub(C a, C b) { return make_double2(a.x - b.x, a.y - b.y); }
+    static __device__ __forceinline__ C mul(C a, C b) { return cmul(a, b); }
+    static __device__ __forceinline__ C scl(C a, S s) { return make_double2(a.x * s, a.y * s); }
+    static __host__ __device__ __forceinline__ S cst(double v) { return v; }
+    static __device__ __forceinline__ C zero() { return make_double2(0.0, 0.0); }
+    static __device__ __forceinline__ LC lo(C a) { return a; }
+    static __device__ __forceinline__ C from_lo(LC a) { return a; }
+    static __device__ __forceinline__ void st(M* d, C v) { *d = v; }
+    static __device__ __forceinline__ float2 r32(C v) { return make_float2((float)v.x, (float)v.y); }
+    static __host__ C hc(double2 v) { return v; }
+};
+struct PDF {
+    typedef cdf C;
+    typedef float4 M;    // (re.hi, im.hi, re.lo, im.lo)
+    typedef df S;
+    typedef float2 LC;
+    static __device__ __forceinline__ C ld(const M* p, size_t i) { return cdf_from4(p[i]); }
+    static __device__ __forceinline__ C add(C a, C b) { return cdf_add(a, b); }
+    static __device__ __forceinline__ C sub(C a, C b) { return cdf_sub(a, b); }
+    static __device__ __forceinline__ C mul(C a, C b) { return cdf_mul(a, b); }
+    static __device__ __forceinline__ C scl(C a, S s) { return cdf_scale(a, s); }
+    static __host__ __device__ __forceinline__ S cst(double v) {
+        const float h = (float)v;
+        return df{h, (float)(v - (double)h)};
+    }
+    static __device__ __forceinline__ C zero() { return cdf_zero(); }
+    static __device__ __forceinline__ LC lo(C a) { return make_float2(a.re.hi, a.im.hi); }
+    static __device__ __forceinline__ C from_lo(LC a) { return cdf_from_f2(a); }
+    static __device__ __forceinline__ void st(M* d, C v) { *d = cdf_to4(v); }
+    static __device__ __forceinline__ float2 r32(C v) { return cdf_round(v); }
+    static __host__ C hc(double2 v) { return C{cst(v.x), cst(v.y)}; }
+};
 
-// Fetch U at (X, Y, Z) with the ghost rule (at most one point outside in each direction).
-template <typename R>
-__device__ inline typename cplx<R>::t fetch_u(const StencilParams<R>& p, const typename cplx<R>::t* __restrict__ U,
-                                              int X, int Y, int Z) {
-    typedef typename cplx<R>::t C;
-    int Xc = X < 0 ? 0 : (X >= p.nx ? p.nx - 1 : X);
-    int Yc = Y < 0 ? 0 : (Y >= p.ny ? p.ny - 1 : Y);
-    int Zc = Z < 0 ? 0 : (Z >= p.nz ? p.nz - 1 : Z);
-    C v = U[((size_t)Zc * p.ny + Yc) * p.nx + Xc];
-    if (Xc != X) v = cmul(v, p.gx);
-    if (Yc != Y) v = cmul(v, p.gy);
-    if (Zc != Z) v = cmul(v, p.gz);
+template <class P>
+struct SParams {
+    int nx, ny, nz;
+    typename P::C gx, gy, gz;              // ghost factors (Eq. D_bc)
+    typename P::S ihx, ihy, ihz;           // 1/h_d^2
+    typename P::S wxy, wxz, wyz;           // (ha^2 + hb^2)/(12 ha^2 hb^2), order 4
+    typename P::S h2_20;                   // h^2/20, order 6
+    float h_20, hh6;                       // h/20 and h^2/6 for the low-precision gradient terms
+    double h_20d, hh6d;
+    const typename P::M* k2;               // k^2 samples
+    const typename P::LC* dk2[3];          // (k^2)_x, (k^2)_y, (k^2)_z (order 6)
+    const typename P::M* G;                // lap(k^2) - k^4 (order 6)
+};
+
+template <class P>
+__device__ __forceinline__ typename P::C fetch_u(const SParams<P>& p, const typename P::M* __restrict__ U, int X, int Y,
+                                                 int Z) {
+    const int Xc = X < 0 ? 0 : (X >= p.nx ? p.nx - 1 : X);
+    const int Yc = Y < 0 ? 0 : (Y >= p.ny ? p.ny - 1 : Y);
+    const int Zc = Z < 0 ? 0 : (Z >= p.nz ? p.nz - 1 : Z);
+    typename P::C v = P::ld(U, ((size_t)Zc * p.ny + Yc) * p.nx + Xc);
+    if (Xc != X) v = P::mul(v, p.gx);
+    if (Yc != Y) v = P::mul(v, p.gy);
+    if (Zc != Z) v = P::mul(v, p.gz);
     return v;
 }
 
-template <typename R>
-__device__ inline typename cplx<R>::t fetch_k(const StencilParams<R>& p, int X, int Y, int Z) {
-    int Xc = X < 0 ? 0 : (X >= p.nx ? p.nx - 1 : X);
-    int Yc = Y < 0 ? 0 : (Y >= p.ny ? p.ny - 1 : Y);
-    int Zc = Z < 0 ? 0 : (Z >= p.nz ? p.nz - 1 : Z);
-    return p.k2[((size_t)Zc * p.ny + Yc) * p.nx + Xc];
+template <class P>
+__device__ __forceinline__ typename P::C fetch_k(const SParams<P>& p, int X, int Y, int Z) {
+    const int Xc = X < 0 ? 0 : (X >= p.nx ? p.nx - 1 : X);
+    const int Yc = Y < 0 ? 0 : (Y >= p.ny ? p.ny - 1 : Y);
+    const int Zc = Z < 0 ? 0 : (Z >= p.nz ? p.nz - 1 : Z);
+    return P::ld(p.k2, ((size_t)Zc * p.ny + Yc) * p.nx + Xc);
 }
 
-// A at one point from its 3x3x3 neighbourhood u[c][b][a] (a = x offset + 1, b = y, c = z).
-template <typename R, int ORDER>
-__device__ inline typename cplx<R>::t apply_point(const StencilParams<R>& p, const typename cplx<R>::t (&u)[3][3][3],
-                                                  const typename cplx<R>::t (&k)[3][3][3], size_t gidx) {
-    typedef typename cplx<R>::t C;
-    const C uc = u[1][1][1];
-    const C kc = k[1][1][1];
+template <class LC>
+__device__ __forceinline__ LC lsub(LC a, LC b) { a.x -= b.x; a.y -= b.y; return a; }
+template <class LC>
+__device__ __forceinline__ LC ladd(LC a, LC b) { a.x += b.x; a.y += b.y; return a; }
+
+// D_d from the side values (low precision): (U+ - U-) + hh6 (KU+ - KU-) + (T+ - T-)/6
+template <class P>
+__device__ __forceinline__ typename P::LC dterm(const SParams<P>& p, typename P::LC up, typename P::LC um,
+                                                typename P::LC kp, typename P::LC km, typename P::LC tp,
+                                                typename P::LC tm) {
+    typedef typename P::LC LC;
+    LC d = lsub(up, um);
+    LC k = lsub(kp, km);
+    LC t = lsub(tp, tm);
+    if (sizeof(d.x) == 8) {
+        d.x += p.hh6d * k.x + t.x / 6.0; d.y += p.hh6d * k.y + t.y / 6.0;
+    } else {
+        d.x += p.hh6 * k.x + t.x / 6.f; d.y += p.hh6 * k.y + t.y / 6.f;
+    }
+    return d;
+}
+
+// A at one point from the 3x3x3 neighbourhood u[c][b][a] (a = x offset + 1, b = y, c = z) and k^2 in kk.
+template <class P, int ORDER>
+__device__ __forceinline__ typename P::C apply_point(const SParams<P>& p, const typename P::C (&u)[3][3][3],
+                                                     const typename P::C (&kk)[3][3][3], size_t gidx) {
+    typedef typename P::C C;
+    typedef typename P::LC LC;
+    const C u0 = u[1][1][1];
+    const C K0 = P::mul(kk[1][1][1], u0);
+    const C fx = P::add(u[1][1][0], u[1][1][2]);
+    const C fy = P::add(u[1][0][1], u[1][2][1]);
+    const C fz = P::add(u[0][1][1], u[2][1][1]);
     if (ORDER == 2 || ORDER == 4) {
-        const R ihx = R(1) / (p.hx * p.hx), ihy = R(1) / (p.hy * p.hy), ihz = R(1) / (p.hz * p.hz);
-        C fx = cadd(u[1][1][0], u[1][1][2]);
-        C fy = cadd(u[1][0][1], u[1][2][1]);
-        C fz = cadd(u[0][1][1], u[2][1][1]);
-        C out;
-        out.x = (fx.x - 2 * uc.x) * ihx + (fy.x - 2 * uc.x) * ihy + (fz.x - 2 * uc.x) * ihz;
-        out.y = (fx.y - 2 * uc.y) * ihx + (fy.y - 2 * uc.y) * ihy + (fz.y - 2 * uc.y) * ihz;
-        out = cadd(out, cmul(kc, uc));
-        if (ORDER == 4) {
-            // mixed fourth differences da2 db2 U
-            C exy = cadd(cadd(u[1][0][0], u[1][0][2]), cadd(u[1][2][0], u[1][2][2]));
-            C exz = cadd(cadd(u[0][1][0], u[0][1][2]), cadd(u[2][1][0], u[2][1][2]));
-            C eyz = cadd(cadd(u[0][0][1], u[0][2][1]), cadd(u[2][0][1], u[2][2][1]));
-            const R wxy = (p.hx * p.hx + p.hy * p.hy) / R(12) * ihx * ihy;
-            const R wxz = (p.hx * p.hx + p.hz * p.hz) / R(12) * ihx * ihz;
-            const R wyz = (p.hy * p.hy + p.hz * p.hz) / R(12) * ihy * ihz;
-            C t;
-            t.x = exy.x - 2 * (fx.x + fy.x) + 4 * uc.x; t.y = exy.y - 2 * (fx.y + fy.y) + 4 * uc.y;
-            out = cadd(out, cscale(t, wxy));
-            t.x = exz.x - 2 * (fx.x + fz.x) + 4 * uc.x; t.y = exz.y - 2 * (fx.y + fz.y) + 4 * uc.y;
-            out = cadd(out, cscale(t, wxz));
-            t.x = eyz.x - 2 * (fy.x + fz.x) + 4 * uc.x; t.y = eyz.y - 2 * (fy.y + fz.y) + 4 * uc.y;
-            out = cadd(out, cscale(t, wyz));
-            // (hd^2/12) dd2 (k^2 U) = (1/12)(kU+ - 2 kU0 + kU-)
-            C kuc = cmul(kc, uc);
-            C s = cadd(cadd(cmul(k[1][1][0], u[1][1][0]), cmul(k[1][1][2], u[1][1][2])),
-                       cadd(cmul(k[1][0][1], u[1][0][1]), cmul(k[1][2][1], u[1][2][1])));
-            s = cadd(s, cadd(cmul(k[0][1][1], u[0][1][1]), cmul(k[2][1][1], u[2][1][1])));
-            t.x = (s.x - 6 * kuc.x) / R(12); t.y = (s.y - 6 * kuc.y) / R(12);
-            out = cadd(out, t);
-        }
+        const C u2 = P::add(u0, u0);
+        C out = P::add(P::add(P::scl(P::sub(fx, u2), p.ihx), P::scl(P::sub(fy, u2), p.ihy)),
+                       P::scl(P::sub(fz, u2), p.ihz));
+        if (ORDER == 2) return P::add(out, K0);
+        const C exy = P::add(P::add(u[1][0][0], u[1][0][2]), P::add(u[1][2][0], u[1][2][2]));
+        const C exz = P::add(P::add(u[0][1][0], u[0][1][2]), P::add(u[2][1][0], u[2][1][2]));
+        const C eyz = P::add(P::add(u[0][0][1], u[0][2][1]), P::add(u[2][0][1], u[2][2][1]));
+        const C u4 = P::add(u2, u2);
+        // da2 db2 U = e_ab - 2 (f_a + f_b) + 4 U_0
+        const C fxy = P::add(fx, fy), fxz = P::add(fx, fz), fyz = P::add(fy, fz);
+        out = P::add(out, P::scl(P::add(P::sub(exy, P::add(fxy, fxy)), u4), p.wxy));
+        out = P::add(out, P::scl(P::add(P::sub(exz, P::add(fxz, fxz)), u4), p.wxz));
+        out = P::add(out, P::scl(P::add(P::sub(eyz, P::add(fyz, fyz)), u4), p.wyz));
+        // (1 + sum hd^2/12 dd2)(k^2 U) = K0/2 + (sum of the six face values of k^2 U)/12
+        C kf = P::add(P::add(P::mul(kk[1][1][0], u[1][1][0]), P::mul(kk[1][1][2], u[1][1][2])),
+                      P::add(P::mul(kk[1][0][1], u[1][0][1]), P::mul(kk[1][2][1], u[1][2][1])));
+        kf = P::add(kf, P::add(P::mul(kk[0][1][1], u[0][1][1]), P::mul(kk[2][1][1], u[2][1][1])));
+        out = P::add(out, P::add(P::scl(K0, P::cst(0.5)), P::scl(kf, P::cst(1.0 / 12.0))));
         return out;
     } else {
-        const R h = p.hx, h2 = h * h, ih2 = R(1) / h2;
-        const R c30 = h2 / R(30), c15 = h2 / R(15), c6 = h2 / R(6);
-        // P_c = (1 + c k^2) U at the needed points
-        auto P = [&](int c, int b, int a, R cc) -> C { return cadd(u[c][b][a], cscale(cmul(k[c][b][a], u[c][b][a]), cc)); };
-        // faces
-        C f30 = czero<C>(), f15 = czero<C>(), fu = czero<C>();
-        const int FA[6][3] = {{1, 1, 0}, {1, 1, 2}, {1, 0, 1}, {1, 2, 1}, {0, 1, 1}, {2, 1, 1}};
-#pragma unroll
-        for (int q = 0; q < 6; ++q) {
-            const int c = FA[q][0], b = FA[q][1], a = FA[q][2];
-            f30 = cadd(f30, P(c, b, a, c30));
-            f15 = cadd(f15, P(c, b, a, c15));
-            fu = cadd(fu, u[c][b][a]);
-        }
-        C e15 = czero<C>(), eu = czero<C>();
+        const C KUxp = P::mul(kk[1][1][2], u[1][1][2]), KUxm = P::mul(kk[1][1][0], u[1][1][0]);
+        const C KUyp = P::mul(kk[1][2][1], u[1][2][1]), KUym = P::mul(kk[1][0][1], u[1][0][1]);
+        const C KUzp = P::mul(kk[2][1][1], u[2][1][1]), KUzm = P::mul(kk[0][1][1], u[0][1][1]);
+        const C Kf = P::add(P::add(P::add(KUxp, KUxm), P::add(KUyp, KUym)), P::add(KUzp, KUzm));
+        C Ke = P::zero(), Se = P::zero(), Sc = P::zero();
         const int ED[12][3] = {{1, 0, 0}, {1, 0, 2}, {1, 2, 0}, {1, 2, 2}, {0, 1, 0}, {0, 1, 2},
                                {2, 1, 0}, {2, 1, 2}, {0, 0, 1}, {0, 2, 1}, {2, 0, 1}, {2, 2, 1}};
 #pragma unroll
         for (int q = 0; q < 12; ++q) {
             const int c = ED[q][0], b = ED[q][1], a = ED[q][2];
-            e15 = cadd(e15, P(c, b, a, c15));
-            eu = cadd(eu, u[c][b][a]);
+            Ke = P::add(Ke, P::mul(kk[c][b][a], u[c][b][a]));
+            Se = P::add(Se, u[c][b][a]);
         }
-        C cu = czero<C>();
 #pragma unroll
         for (int c = 0; c < 3; c += 2)
 #pragma unroll
             for (int b = 0; b < 3; b += 2)
 #pragma unroll
-                for (int a = 0; a < 3; a += 2) cu = cadd(cu, u[c][b][a]);
-        const C p30c = P(1, 1, 1, c30), p15c = P(1, 1, 1, c15);
-        C out;
-        // L[(1 + h^2 k^2/30)U]
-        out.x = (f30.x - 6 * p30c.x) * ih2; out.y = (f30.y - 6 * p30c.y) * ih2;
-        // h^4/30 dxx dyy dzz U
-        out.x += (cu.x - 2 * eu.x + 4 * fu.x - 8 * uc.x) * (ih2 / R(30));
-        out.y += (cu.y - 2 * eu.y + 4 * fu.y - 8 * uc.y) * (ih2 / R(30));
-        // k^2 U
-        out = cadd(out, cmul(kc, uc));
-        // h^2/6 M[(1 + h^2 k^2/15)U]
-        out.x += (e15.x - 4 * f15.x + 12 * p15c.x) * (ih2 / R(6));
-        out.y += (e15.y - 4 * f15.y + 12 * p15c.y) * (ih2 / R(6));
-        // h^2/20 { G U + 2 sum_d g_d inner_d }
-        const C G = p.G[gidx];
-        C acc = cmul(G, uc);
-        const R i2h = R(1) / (R(2) * h), i12h = R(1) / (R(12) * h);
-        // S_a = sum of the four transverse neighbours of the side point a minus 4 * that point
-        // x direction: side points (1,1,0) and (1,1,2)
-        {
-            C sp = csub(cadd(cadd(u[1][0][2], u[1][2][2]), cadd(u[0][1][2], u[2][1][2])), cscale(u[1][1][2], R(4)));
-            C sm = csub(cadd(cadd(u[1][0][0], u[1][2][0]), cadd(u[0][1][0], u[2][1][0])), cscale(u[1][1][0], R(4)));
-            C in = cadd(cscale(csub(P(1, 1, 2, c6), P(1, 1, 0, c6)), i2h), cscale(csub(sp, sm), i12h));
-            acc = cadd(acc, cscale(cmul(p.dk2[0][gidx], in), R(2)));
-        }
-        {   // y direction: side points (1,2,1) and (1,0,1)
-            C sp = csub(cadd(cadd(u[1][2][0], u[1][2][2]), cadd(u[0][2][1], u[2][2][1])), cscale(u[1][2][1], R(4)));
-            C sm = csub(cadd(cadd(u[1][0][0], u[1][0][2]), cadd(u[0][0][1], u[2][0][1])), cscale(u[1][0][1], R(4)));
-            C in = cadd(cscale(csub(P(1, 2, 1, c6), P(1, 0, 1, c6)), i2h), cscale(csub(sp, sm), i12h));
-            acc = cadd(acc, cscale(cmul(p.dk2[1][gidx], in), R(2)));
-        }
-        {   // z direction: side points (2,1,1) and (0,1,1)
-            C sp = csub(cadd(cadd(u[2][1][0], u[2][1][2]), cadd(u[2][0][1], u[2][2][1])), cscale(u[2][1][1], R(4)));
-            C sm = csub(cadd(cadd(u[0][1][0], u[0][1][2]), cadd(u[0][0][1], u[0][2][1])), cscale(u[0][1][1], R(4)));
-            C in = cadd(cscale(csub(P(2, 1, 1, c6), P(0, 1, 1, c6)), i2h), cscale(csub(sp, sm), i12h));
-            acc = cadd(acc, cscale(cmul(p.dk2[2][gidx], in), R(2)));
-        }
-        out = cadd(out, cscale(acc, h2 / R(20)));
-        return out;
+                for (int a = 0; a < 3; a += 2) Sc = P::add(Sc, u[c][b][a]);
+        const C Sf = P::add(P::add(fx, fy), fz);
+        const C up = P::add(P::add(P::scl(Sf, P::cst(7.0 / 15.0)), P::scl(Se, P::cst(0.1))),
+                            P::sub(P::scl(Sc, P::cst(1.0 / 30.0)), P::scl(u0, P::cst(64.0 / 15.0))));
+        C out = P::scl(up, p.ihx);
+        out = P::add(out, P::add(P::scl(K0, P::cst(14.0 / 15.0)), P::scl(P::sub(Ke, Kf), P::cst(1.0 / 90.0))));
+        out = P::add(out, P::scl(P::mul(P::ld(p.G, gidx), u0), p.h2_20));
+        // (h/20) sum_d g_d D_d in low precision
+        auto T = [&](int c, int b, int a, int c1, int b1, int a1, int c2, int b2, int a2, int c3, int b3, int a3,
+                     int c4, int b4, int a4) {
+            return P::lo(P::sub(P::add(P::add(u[c1][b1][a1], u[c2][b2][a2]), P::add(u[c3][b3][a3], u[c4][b4][a4])),
+                                P::scl(u[c][b][a], P::cst(4.0))));
+        };
+        const LC Dx = dterm<P>(p, P::lo(u[1][1][2]), P::lo(u[1][1][0]), P::lo(KUxp), P::lo(KUxm),
+                               T(1, 1, 2, 1, 0, 2, 1, 2, 2, 0, 1, 2, 2, 1, 2), T(1, 1, 0, 1, 0, 0, 1, 2, 0, 0, 1, 0, 2, 1, 0));
+        const LC Dy = dterm<P>(p, P::lo(u[1][2][1]), P::lo(u[1][0][1]), P::lo(KUyp), P::lo(KUym),
+                               T(1, 2, 1, 1, 2, 0, 1, 2, 2, 0, 2, 1, 2, 2, 1), T(1, 0, 1, 1, 0, 0, 1, 0, 2, 0, 0, 1, 2, 0, 1));
+        const LC Dz = dterm<P>(p, P::lo(u[2][1][1]), P::lo(u[0][1][1]), P::lo(KUzp), P::lo(KUzm),
+                               T(2, 1, 1, 2, 1, 0, 2, 1, 2, 2, 0, 1, 2, 2, 1), T(0, 1, 1, 0, 1, 0, 0, 1, 2, 0, 0, 1, 0, 2, 1));
+        LC g = cmul(p.dk2[0][gidx], Dx);
+        g = ladd(g, cmul(p.dk2[1][gidx], Dy));
+        g = ladd(g, cmul(p.dk2[2][gidx], Dz));
+        if (sizeof(g.x) == 8) { g.x *= p.h_20d; g.y *= p.h_20d; } else { g.x *= p.h_20; g.y *= p.h_20; }
+        return P::add(out, P::from_lo(g));
     }
 }
 
-// MODE 0: y = scale * A x.  MODE 1: r = F - A x written as complex64, with per-CTA partial sums of
-// |r|^2 and max |r| (FP64) in part[2*cta], part[2*cta+1].
-template <typename R, int ORDER, int MODE>
+// MODE 0: Y = scale * A X (Y in the policy's storage type).
+// MODE 1: r = F - A X written as complex64, with per-CTA partial sums of |r|^2 and max |r| (FP64)
+//         in part[2*cta], part[2*cta+1].
+template <class P, int ORDER, int MODE>
 __global__ void __launch_bounds__(TX * TY)
-stencil_kernel(StencilParams<R> p, const typename cplx<R>::t* __restrict__ U, typename cplx<R>::t* __restrict__ Y,
-               const double* __restrict__ sigma, int sidx, const double2* __restrict__ F, float2* __restrict__ rout,
+stencil_kernel(SParams<P> p, const typename P::M* __restrict__ U, typename P::M* __restrict__ Y,
+               const double* __restrict__ sigma, int sidx, const typename P::M* __restrict__ F, float2* __restrict__ rout,
                double* __restrict__ part) {
-    typedef typename cplx<R>::t C;
-    __shared__ C sU[2][PY][PX];
-    __shared__ C sK[2][PY][PX];
+    typedef typename P::C C;
+    __shared__ typename P::M sU[2][PY][PX];
+    __shared__ typename P::M sK[2][PY][PX];
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
     const int z0 = blockIdx.z * ZCH;
@@ -185,8 +254,10 @@ stencil_kernel(StencilParams<R> p, const typename cplx<R>::t* __restrict__ U, ty
     auto stage = [&](int buf, int Z) {
         for (int q = tid; q < PX * PY; q += TX * TY) {
             const int ly = q / PX, lx = q - ly * PX;
-            sU[buf][ly][lx] = fetch_u<R>(p, U, x0 + lx - 1, y0 + ly - 1, Z);
-            sK[buf][ly][lx] = fetch_k<R>(p, x0 + lx - 1, y0 + ly - 1, Z);
+            const C v = fetch_u<P>(p, U, x0 + lx - 1, y0 + ly - 1, Z);
+            const C kv = fetch_k<P>(p, x0 + lx - 1, y0 + ly - 1, Z);
+            P::st(&sU[buf][ly][lx], v);
+            P::st(&sK[buf][ly][lx], kv);
         }
     };
     auto lift = [&](int buf, int slot) {
@@ -194,8 +265,8 @@ stencil_kernel(StencilParams<R> p, const typename cplx<R>::t* __restrict__ U, ty
         for (int b = 0; b < 3; ++b)
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
-                u[slot][b][a] = sU[buf][ty + b][tx + a];
-                k[slot][b][a] = sK[buf][ty + b][tx + a];
+                u[slot][b][a] = P::ld(&sU[buf][ty + b][tx + a], 0);
+                k[slot][b][a] = P::ld(&sK[buf][ty + b][tx + a], 0);
             }
     };
     int buf = 0;
@@ -208,15 +279,15 @@ stencil_kernel(StencilParams<R> p, const typename cplx<R>::t* __restrict__ U, ty
         buf ^= 1;
         if (active) {
             const size_t gidx = ((size_t)z * p.ny + gy) * p.nx + gx;
-            C v = apply_point<R, ORDER>(p, u, k, gidx);
+            C v = apply_point<P, ORDER>(p, u, k, gidx);
             if (MODE == 0) {
-                if (sigma) v = cscale(v, (R)sigma[sidx]);
-                Y[gidx] = v;
+                if (sigma) v = P::scl(v, P::cst(sigma[sidx]));
+                P::st(&Y[gidx], v);
             } else {
-                const double2 f = F[gidx];
-                const double rx = f.x - (double)v.x, ry = f.y - (double)v.y;
-                rout[gidx] = make_float2((float)rx, (float)ry);
-                const double a2 = rx * rx + ry * ry;
+                const C r = P::sub(P::ld(F, gidx), v);
+                const float2 rf = P::r32(r);
+                rout[gidx] = rf;
+                const double a2 = (double)rf.x * rf.x + (double)rf.y * rf.y;
                 ssum += a2;
                 smax = fmax(smax, a2);
             }
@@ -247,31 +318,47 @@ stencil_kernel(StencilParams<R> p, const typename cplx<R>::t* __restrict__ U, ty
     }
 }
 
-template <typename R>
-StencilParams<R> make_params(const helm_ctx* c, int f64) {
-    StencilParams<R> p;
+dim3 stencil_grid(const helm_ctx* c) {
+    return dim3((c->nx + TX - 1) / TX, (c->ny + TY - 1) / TY, (c->nz + ZCH - 1) / ZCH);
+}
+
+template <class P>
+SParams<P> make_params(const helm_ctx* c) {
+    SParams<P> p;
     p.nx = c->nx; p.ny = c->ny; p.nz = c->nz;
-    p.hx = (R)c->h[0]; p.hy = (R)c->h[1]; p.hz = (R)c->h[2];
-    p.gx = mk((R)c->gam[0].x, (R)c->gam[0].y);
-    p.gy = mk((R)c->gam[1].x, (R)c->gam[1].y);
-    p.gz = mk((R)c->gam[2].x, (R)c->gam[2].y);
+    const double hx = c->h[0], hy = c->h[1], hz = c->h[2];
+    p.gx = P::hc(c->gam[0]); p.gy = P::hc(c->gam[1]); p.gz = P::hc(c->gam[2]);
+    const double ihx = 1.0 / (hx * hx), ihy = 1.0 / (hy * hy), ihz = 1.0 / (hz * hz);
+    p.ihx = P::cst(ihx); p.ihy = P::cst(ihy); p.ihz = P::cst(ihz);
+    p.wxy = P::cst((hx * hx + hy * hy) / 12.0 * ihx * ihy);
+    p.wxz = P::cst((hx * hx + hz * hz) / 12.0 * ihx * ihz);
+    p.wyz = P::cst((hy * hy + hz * hz) / 12.0 * ihy * ihz);
+    p.h2_20 = P::cst(hx * hx / 20.0);
+    p.h_20 = (float)(hx / 20.0); p.h_20d = hx / 20.0;
+    p.hh6 = (float)(hx * hx / 6.0); p.hh6d = hx * hx / 6.0;
     for (int d = 0; d < 3; ++d) p.dk2[d] = nullptr;
     p.G = nullptr;
     return p;
 }
 
-dim3 stencil_grid(const helm_ctx* c) {
-    return dim3((c->nx + TX - 1) / TX, (c->ny + TY - 1) / TY, (c->nz + ZCH - 1) / ZCH);
-}
-
 // ---- coefficient fields of Eq. scheme6 (set-up, FP64) ----------------------------------------
 __device__ inline int mirror_stag(int i, int n) { return i < 0 ? -i - 1 : (i >= n ? 2 * n - 1 - i : i); }
 
-__global__ void derived_kernel(int nx, int ny, int nz, double hx, double hy, double hz, const double2* __restrict__ k2,
-                               double2* dkx, double2* dky, double2* dkz, double2* G, float2* fdkx, float2* fdky,
-                               float2* fdkz, float2* fG, float2* fk2) {
+__device__ __forceinline__ float4 split4(double2 v) {
+    const float rh = (float)v.x, ih = (float)v.y;
+    return make_float4(rh, ih, (float)(v.x - (double)rh), (float)(v.y - (double)ih));
+}
+
+__global__ void derived_kernel(int order, int nx, int ny, int nz, double hx, double hy, double hz,
+                               const double2* __restrict__ k2, double2* dkx, double2* dky, double2* dkz, double2* G,
+                               float2* fdkx, float2* fdky, float2* fdkz, float2* fG, float2* fk2, float4* k2df,
+                               float4* Gdf) {
     const size_t n = (size_t)nx * ny * nz;
     for (size_t id = blockIdx.x * (size_t)blockDim.x + threadIdx.x; id < n; id += (size_t)gridDim.x * blockDim.x) {
+        const double2 kc = k2[id];
+        fk2[id] = make_float2((float)kc.x, (float)kc.y);
+        k2df[id] = split4(kc);
+        if (order != 6) continue;
         const int i = (int)(id % nx), j = (int)((id / nx) % ny), l = (int)(id / ((size_t)nx * ny));
         auto at = [&](int a, int b, int c) {
             return k2[((size_t)mirror_stag(l + c, nz) * ny + mirror_stag(j + b, ny)) * nx + mirror_stag(i + a, nx)];
@@ -288,20 +375,14 @@ __global__ void derived_kernel(int nx, int ny, int nz, double hx, double hy, dou
             lap.x += (-v[4].x + 16 * v[3].x - 30 * v[2].x + 16 * v[1].x - v[0].x) / (12 * hh[d] * hh[d]);
             lap.y += (-v[4].y + 16 * v[3].y - 30 * v[2].y + 16 * v[1].y - v[0].y) / (12 * hh[d] * hh[d]);
         }
-        const double2 kc = k2[id];
         const double2 gg = csub(lap, cmul(kc, kc));
         dkx[id] = g[0]; dky[id] = g[1]; dkz[id] = g[2]; G[id] = gg;
         fdkx[id] = make_float2((float)g[0].x, (float)g[0].y);
         fdky[id] = make_float2((float)g[1].x, (float)g[1].y);
         fdkz[id] = make_float2((float)g[2].x, (float)g[2].y);
         fG[id] = make_float2((float)gg.x, (float)gg.y);
-        fk2[id] = make_float2((float)kc.x, (float)kc.y);
+        Gdf[id] = split4(gg);
     }
-}
-
-__global__ void to_f32_kernel(const double2* __restrict__ a, float2* __restrict__ b, size_t n) {
-    for (size_t id = blockIdx.x * (size_t)blockDim.x + threadIdx.x; id < n; id += (size_t)gridDim.x * blockDim.x)
-        b[id] = make_float2((float)a[id].x, (float)a[id].y);
 }
 
 // ---- modified right-hand side (set-up, FP64) -------------------------------------------------
@@ -322,15 +403,14 @@ __global__ void rhs_kernel(int order, int nx, int ny, int nz, double hx, double 
             double2 out = fc;
             for (int d = 0; d < 3; ++d) {
                 int o[3] = {0, 0, 0};
-                o[d] = 1; double2 p = at(o[0], o[1], o[2]);
+                o[d] = 1; double2 pp = at(o[0], o[1], o[2]);
                 o[d] = -1; double2 m = at(o[0], o[1], o[2]);
-                out.x += (p.x - 2 * fc.x + m.x) / 12.0;
-                out.y += (p.y - 2 * fc.y + m.y) / 12.0;
+                out.x += (pp.x - 2 * fc.x + m.x) / 12.0;
+                out.y += (pp.y - 2 * fc.y + m.y) / 12.0;
             }
             F[id] = out;
             continue;
         }
-        // order 6 (uniform h)
         const double h = hx, h2 = h * h;
         double2 lap = make_double2(0, 0), s4 = make_double2(0, 0), fd[3];
         for (int d = 0; d < 3; ++d) {
@@ -365,59 +445,54 @@ __global__ void rhs_kernel(int order, int nx, int ny, int nz, double hx, double 
         out.x = fc.x + h2 / 12.0 * lap.x + h2 * h2 / 360.0 * s4.x + h2 * h2 / 90.0 * mix.x;
         out.y = fc.y + h2 / 12.0 * lap.y + h2 * h2 / 360.0 * s4.y + h2 * h2 / 90.0 * mix.y;
         const double2 kc = k2[id];
-        double2 kf = cmul(kc, fc);
-        double2 gf = cadd(cadd(cmul(dkx[id], fd[0]), cmul(dky[id], fd[1])), cmul(dkz[id], fd[2]));
+        const double2 kf = cmul(kc, fc);
+        const double2 gf = cadd(cadd(cmul(dkx[id], fd[0]), cmul(dky[id], fd[1])), cmul(dkz[id], fd[2]));
         out.x -= h2 / 20.0 * (kf.x - h2 / 3.0 * gf.x);
         out.y -= h2 / 20.0 * (kf.y - h2 / 3.0 * gf.y);
         F[id] = out;
     }
 }
 
+template <class P, int MODE>
+void launch_stencil(helm_ctx* c, const SParams<P>& p, const typename P::M* x, typename P::M* y, const double* sigma,
+                    int sidx, const typename P::M* F, float2* r, double* part, cudaStream_t s) {
+    dim3 grid = stencil_grid(c), block(TX, TY);
+    switch (c->opt.order) {
+        case 2: stencil_kernel<P, 2, MODE><<<grid, block, 0, s>>>(p, x, y, sigma, sidx, F, r, part); break;
+        case 4: stencil_kernel<P, 4, MODE><<<grid, block, 0, s>>>(p, x, y, sigma, sidx, F, r, part); break;
+        default: stencil_kernel<P, 6, MODE><<<grid, block, 0, s>>>(p, x, y, sigma, sidx, F, r, part); break;
+    }
+}
+
 }  // namespace
 
 helm_status launch_derived_fields(helm_ctx* c, cudaStream_t s) {
-    const int blocks = 1024;
-    if (c->opt.order == 6) {
-        derived_kernel<<<blocks, 256, 0, s>>>(c->nx, c->ny, c->nz, c->h[0], c->h[1], c->h[2], c->k2_d, c->dk2_d[0],
-                                              c->dk2_d[1], c->dk2_d[2], c->G_d, c->dk2_f[0], c->dk2_f[1], c->dk2_f[2],
-                                              c->G_f, c->k2_f);
-    } else {
-        to_f32_kernel<<<blocks, 256, 0, s>>>(c->k2_d, c->k2_f, c->npts);
-    }
+    derived_kernel<<<1024, 256, 0, s>>>(c->opt.order, c->nx, c->ny, c->nz, c->h[0], c->h[1], c->h[2], c->k2_d,
+                                        c->dk2_d[0], c->dk2_d[1], c->dk2_d[2], c->G_d, c->dk2_f[0], c->dk2_f[1],
+                                        c->dk2_f[2], c->G_f, c->k2_f, c->k2_df, c->G_df);
     HELM_CUDA_TRY(cudaGetLastError());
     return HELM_OK;
 }
 
-template <typename R, int MODE>
-static void launch_stencil(helm_ctx* c, StencilParams<R> p, const typename cplx<R>::t* x, typename cplx<R>::t* y,
-                           const double* sigma, int sidx, const double2* F, float2* r, double* part, cudaStream_t s) {
-    dim3 grid = stencil_grid(c), block(TX, TY);
-    switch (c->opt.order) {
-        case 2: stencil_kernel<R, 2, MODE><<<grid, block, 0, s>>>(p, x, y, sigma, sidx, F, r, part); break;
-        case 4: stencil_kernel<R, 4, MODE><<<grid, block, 0, s>>>(p, x, y, sigma, sidx, F, r, part); break;
-        default: stencil_kernel<R, 6, MODE><<<grid, block, 0, s>>>(p, x, y, sigma, sidx, F, r, part); break;
-    }
-}
-
 helm_status launch_stencil_f32(helm_ctx* c, const float2* x, float2* y, const double* sigma, int sidx, cudaStream_t s) {
-    StencilParams<float> p = make_params<float>(c, 0);
+    SParams<P32> p = make_params<P32>(c);
     p.k2 = c->k2_f;
     for (int d = 0; d < 3; ++d) p.dk2[d] = c->dk2_f[d];
     p.G = c->G_f;
     prof_begin(c, s, PROF_STENCIL);
-    launch_stencil<float, 0>(c, p, x, y, sigma, sidx, nullptr, nullptr, nullptr, s);
+    launch_stencil<P32, 0>(c, p, x, y, sigma, sidx, nullptr, nullptr, nullptr, s);
     prof_end(c, s);
     HELM_CUDA_TRY(cudaGetLastError());
     return HELM_OK;
 }
 
 helm_status launch_stencil_f64(helm_ctx* c, const double2* x, double2* y, cudaStream_t s) {
-    StencilParams<double> p = make_params<double>(c, 1);
+    SParams<P64> p = make_params<P64>(c);
     p.k2 = c->k2_d;
     for (int d = 0; d < 3; ++d) p.dk2[d] = c->dk2_d[d];
     p.G = c->G_d;
     prof_begin(c, s, PROF_OTHER);
-    launch_stencil<double, 0>(c, p, x, y, nullptr, 0, nullptr, nullptr, nullptr, s);
+    launch_stencil<P64, 0>(c, p, x, y, nullptr, 0, nullptr, nullptr, nullptr, s);
     prof_end(c, s);
     HELM_CUDA_TRY(cudaGetLastError());
     return HELM_OK;
@@ -429,15 +504,14 @@ int residual_ctas(const helm_ctx* c) {
     return (int)(g.x * g.y * g.z);
 }
 
-helm_status launch_residual(helm_ctx* c, const double2* x, const double2* F, float2* r, double* part, int nblk,
-                            cudaStream_t s) {
-    (void)nblk;
-    StencilParams<double> p = make_params<double>(c, 1);
-    p.k2 = c->k2_d;
-    for (int d = 0; d < 3; ++d) p.dk2[d] = c->dk2_d[d];
-    p.G = c->G_d;
+// r = F - A x with x and F in double-float storage (float4 per point)
+helm_status launch_residual(helm_ctx* c, const float4* x, const float4* F, float2* r, double* part, cudaStream_t s) {
+    SParams<PDF> p = make_params<PDF>(c);
+    p.k2 = c->k2_df;
+    for (int d = 0; d < 3; ++d) p.dk2[d] = c->dk2_f[d];
+    p.G = c->G_df;
     prof_begin(c, s, PROF_RESIDUAL);
-    launch_stencil<double, 1>(c, p, x, (double2*)nullptr, nullptr, 0, F, r, part, s);
+    launch_stencil<PDF, 1>(c, p, x, (float4*)nullptr, nullptr, 0, F, r, part, s);
     prof_end(c, s);
     HELM_CUDA_TRY(cudaGetLastError());
     return HELM_OK;

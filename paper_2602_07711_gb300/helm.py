@@ -59,6 +59,10 @@ _SIGS = {
     "helm_precond_step": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
     "helm_get_eig": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
     "helm_gmres_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(helm_solve_info), C.c_void_p]),
+    "helm_residual": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_double),
+                                C.POINTER(C.c_double), C.c_void_p]),
+    "helm_profile": (C.c_int, [C.c_void_p, C.c_int]),
+    "helm_profile_read": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int]),
     "helm_destroy": (None, [C.c_void_p]),
     "helm_status_str": (C.c_char_p, [C.c_int]),
     "helm_version": (C.c_char_p, []),
@@ -142,6 +146,14 @@ def helm_gmres_solve(ctx, b, x, stream=None):
     return code, info
 
 
+def helm_residual(ctx, b, x, r=None, stream=None):
+    n2 = C.c_double()
+    ni = C.c_double()
+    _check(lib().helm_residual(ctx, _ptr(b), _ptr(x), _ptr(r) if r is not None else None, C.byref(n2), C.byref(ni),
+                               _stream(stream)), "helm_residual")
+    return n2.value, ni.value
+
+
 def helm_destroy(ctx):
     if ctx:
         lib().helm_destroy(ctx)
@@ -200,6 +212,10 @@ class Solver:
         y = self._empty(torch.complex64)
         helm_precond_step(self.ctx, step, x, y, stream)
         return y
+
+    def residual(self, b, x, stream=None):
+        """(||b - A x||_2, ||b - A x||_inf) with complex128 device b, x."""
+        return helm_residual(self.ctx, b, x, None, stream)
 
     def get_eig(self, axis):
         return helm_get_eig(self.ctx, axis, self.n[axis])

@@ -185,3 +185,22 @@ def test_second_order_operator_converges_in_one_iteration():
     b = _dev(_rand(g.shape, 9))
     x, info = S.solve(b)
     assert info.iterations == 1 and info.relres_true < 1e-5
+
+
+@pytest.mark.parametrize("order", [2, 4, 6])
+def test_residual_resolves_small_residuals(order):
+    """helm_residual (double-float) against the oracle's FP64 F - A x when ||F - A x|| ~ 1e-9 ||F||:
+    complex64 arithmetic could not resolve this residual at all."""
+    n, L = (32, 32, 32), (1.0, 1.0, 1.0)
+    g, k2, k0 = _medium(n, L)
+    A = Operator(g, k2, k0, order)
+    F = _rand(g.shape, 12)
+    x, info = gmres(A, EigT(g, k0).apply_Minv, F, m=30, rtol=1e-13, max_it=600)
+    xp = x.reshape(g.shape) + 1e-9 * np.abs(x).max() * _rand(g.shape, 13)
+    r_ref = F - A(xp)
+    S = Solver(n, k2, k0, order=order, L=L)
+    n2, ni = S.residual(_dev(F), _dev(xp))
+    ref2 = np.linalg.norm(r_ref)
+    assert ref2 < 1e-6 * np.linalg.norm(F)
+    assert abs(n2 - ref2) <= 0.02 * ref2, (n2, ref2)
+    assert abs(ni - np.abs(r_ref).max()) <= 0.05 * np.abs(r_ref).max()
