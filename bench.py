@@ -42,6 +42,7 @@ def parse():
     p.add_argument("--rtol", type=float, default=1e-6)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--e2e", type=int, default=1)
+    p.add_argument("--max-iter", type=int, default=300)
     return p.parse_args()
 
 
@@ -151,11 +152,12 @@ def roofline(prof_ms, prof_launch, alg, precision, order):
 
 
 def cycles_of(info, m):
-    its = info.iterations
-    out = []
-    while its > 0:
-        out.append(min(m, its))
-        its -= m
+    """Inner steps of each restart cycle, as the solver reports them."""
+    out = [c for c in info.cycle_its if c]
+    rest = info.iterations - sum(out)
+    while rest > 0:
+        out.append(min(m, rest))
+        rest -= m
     return out
 
 
@@ -224,7 +226,7 @@ def run_ours(args, rank, world, local):
 
     def make(prec, flex):
         return helm.Solver((n, n, n), k2, k0, order=order, precision=PREC_NAMES[prec], restart=args.restart,
-                           max_iter=300, rtol=args.rtol, flexible=flex)
+                           max_iter=args.max_iter, rtol=args.rtol, flexible=flex)
 
     t0 = time.perf_counter()
     S = make(precision, flexible)

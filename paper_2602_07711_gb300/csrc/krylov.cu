@@ -55,12 +55,16 @@ namespace {
 constexpr int NT = 256;
 constexpr int GRP = 8;
 
-// partial inner products conj(v_i) . w for i in [0, nv), FP32 products summed 8 at a time in FP32
-// and then in FP64; part[blk * ld + i]
+// partial inner products conj(v_i) . w for i in [0, nv); part[blk * ld + i].
+// Two points per 16-byte load, two loads of each vector in flight per thread; products summed in FP32
+// over 8 points and then in FP64.  npts is even (every grid here has an even N_x).
 __global__ void __launch_bounds__(NT) dots_kernel(const float2* __restrict__ V, size_t npts, int nv,
                                                  const float2* __restrict__ w, double2* __restrict__ part, int ld) {
     __shared__ double2 red[NT / 32][GRP];
     const int tid = threadIdx.x;
+    const size_t n4 = npts / 2;
+    const size_t stride = (size_t)gridDim.x * NT;
+    const float4* __restrict__ W4 = reinterpret_cast<const float4*>(w);
     for (int g0 = 0; g0 < nv; g0 += GRP) {
         const int ng = min(GRP, nv - g0);
         double2 acc[GRP];
@@ -68,16 +72,29 @@ __global__ void __launch_bounds__(NT) dots_kernel(const float2* __restrict__ V, 
 #pragma unroll
         for (int q = 0; q < GRP; ++q) { acc[q] = make_double2(0, 0); a32[q] = make_float2(0, 0); }
         int cnt = 0;
-        for (size_t id = blockIdx.x * (size_t)NT + tid; id < npts; id += (size_t)gridDim.x * NT) {
-            const float2 wv = w[id];
+        for (size_t id = blockIdx.x * (size_t)NT + tid; id < n4; id += 2 * stride) {
+            const size_t id2 = id + stride;
+            const bool two = id2 < n4;
+            const float4 wa = W4[id];
+            const float4 wb = two ? W4[id2] : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
             for (int q = 0; q < GRP; ++q)
                 if (q < ng) {
-                    const float2 v = V[(size_t)(g0 + q) * npts + id];
-                    a32[q].x = fmaf(v.x, wv.x, fmaf(v.y, wv.y, a32[q].x));
-                    a32[q].y = fmaf(v.x, wv.y, fmaf(-v.y, wv.x, a32[q].y));
+                    const float4* __restrict__ V4 = reinterpret_cast<const float4*>(V + (size_t)(g0 + q) * npts);
+                    const float4 va = V4[id];
+                    const float4 vb = two ? V4[id2] : make_float4(0.f, 0.f, 0.f, 0.f);
+                    float re = a32[q].x, im = a32[q].y;
+                    re = fmaf(va.x, wa.x, fmaf(va.y, wa.y, re));
+                    im = fmaf(va.x, wa.y, fmaf(-va.y, wa.x, im));
+                    re = fmaf(va.z, wa.z, fmaf(va.w, wa.w, re));
+                    im = fmaf(va.z, wa.w, fmaf(-va.w, wa.z, im));
+                    re = fmaf(vb.x, wb.x, fmaf(vb.y, wb.y, re));
+                    im = fmaf(vb.x, wb.y, fmaf(-vb.y, wb.x, im));
+                    re = fmaf(vb.z, wb.z, fmaf(vb.w, wb.w, re));
+                    im = fmaf(vb.z, wb.w, fmaf(-vb.w, wb.z, im));
+                    a32[q] = make_float2(re, im);
                 }
-            if (++cnt == 8) {
+            if (++cnt == 2) {
                 cnt = 0;
 #pragma unroll
                 for (int q = 0; q < GRP; ++q) { acc[q].x += a32[q].x; acc[q].y += a32[q].y; a32[q] = make_float2(0, 0); }
@@ -124,7 +141,8 @@ __global__ void reduce_h_kernel(const double2* __restrict__ part, int NB, int ld
     }
 }
 
-// w -= sum_i coef_i V_i (i < nv); per-block partial ||w||^2 in part[blk * ld].x
+// w -= sum_i coef_i V_i (i < nv); per-block partial ||w||^2 in part[blk * ld].x.  Two points per
+// 16-byte load; the basis loop is unrolled by four so that four vector loads are in flight.
 __global__ void __launch_bounds__(NT) update_kernel(const float2* __restrict__ V, size_t npts, int nv,
                                                    const float2* __restrict__ coef, float2* __restrict__ w,
                                                    double2* __restrict__ part, int ld) {
@@ -133,21 +151,35 @@ __global__ void __launch_bounds__(NT) update_kernel(const float2* __restrict__ V
     for (int i = threadIdx.x; i < nv; i += NT) cf[i] = coef[i];
     __syncthreads();
     double acc = 0.0;
-    float a32 = 0.f;
-    int cnt = 0;
-    for (size_t id = blockIdx.x * (size_t)NT + threadIdx.x; id < npts; id += (size_t)gridDim.x * NT) {
-        float2 x = w[id];
-        for (int i = 0; i < nv; ++i) {
-            const float2 v = V[(size_t)i * npts + id];
+    const size_t n4 = npts / 2;
+    float4* W4 = reinterpret_cast<float4*>(w);
+    for (size_t id = blockIdx.x * (size_t)NT + threadIdx.x; id < n4; id += (size_t)gridDim.x * NT) {
+        float4 x = W4[id];
+        int i = 0;
+        for (; i + 4 <= nv; i += 4) {
+            float4 v[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) v[q] = reinterpret_cast<const float4*>(V + (size_t)(i + q) * npts)[id];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const float2 c = cf[i + q];
+                x.x -= c.x * v[q].x - c.y * v[q].y;
+                x.y -= c.x * v[q].y + c.y * v[q].x;
+                x.z -= c.x * v[q].z - c.y * v[q].w;
+                x.w -= c.x * v[q].w + c.y * v[q].z;
+            }
+        }
+        for (; i < nv; ++i) {
+            const float4 v = reinterpret_cast<const float4*>(V + (size_t)i * npts)[id];
             const float2 c = cf[i];
             x.x -= c.x * v.x - c.y * v.y;
             x.y -= c.x * v.y + c.y * v.x;
+            x.z -= c.x * v.z - c.y * v.w;
+            x.w -= c.x * v.w + c.y * v.z;
         }
-        w[id] = x;
-        a32 = fmaf(x.x, x.x, fmaf(x.y, x.y, a32));
-        if (++cnt == 8) { cnt = 0; acc += a32; a32 = 0.f; }
+        W4[id] = x;
+        acc += (double)fmaf(x.x, x.x, fmaf(x.y, x.y, fmaf(x.z, x.z, x.w * x.w)));
     }
-    acc += a32;
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
     __syncthreads();
@@ -429,6 +461,7 @@ helm_status gmres_run(helm_ctx* c, const double2* b_in, double2* x_in, helm_solv
     const int NB = k->NB, ld = m + 1;
     const int ublocks = NB;
     int its = 0, restarts = 0;
+    int cyc[16] = {0};
     helm_status result = HELM_ERR_NOT_CONVERGED;
     // internal double-float copies of b and x; x0 = 0 is recognised and then r0 = b without a matvec
     unsigned xnz = 0;
@@ -519,6 +552,7 @@ helm_status gmres_run(helm_ctx* c, const double2* b_in, double2* x_in, helm_solv
         info->relres_est = est;
         info->beta0 = beta0;
         info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        for (int i = 0; i < 16; ++i) info->cycle_its[i] = cyc[i];
     }
     return result;
 }

@@ -251,13 +251,30 @@ stencil_kernel(SParams<P> p, const typename P::M* __restrict__ U, typename P::M*
     C u[3][3][3], k[3][3][3];
     double ssum = 0.0, smax = 0.0;
 
-    auto stage = [&](int buf, int Z) {
-        for (int q = tid; q < PX * PY; q += TX * TY) {
-            const int ly = q / PX, lx = q - ly * PX;
-            const C v = fetch_u<P>(p, U, x0 + lx - 1, y0 + ly - 1, Z);
-            const C kv = fetch_k<P>(p, x0 + lx - 1, y0 + ly - 1, Z);
-            P::st(&sU[buf][ly][lx], v);
-            P::st(&sK[buf][ly][lx], kv);
+    // Register-staged prefetch: each thread owns at most two halo-plane slots; the loads of plane z+2 are
+    // issued before the arithmetic of plane z so that their latency overlaps it.
+    constexpr int NSLOT = (PX * PY + TX * TY - 1) / (TX * TY);
+    C pu[NSLOT], pk[NSLOT];
+    auto fetch = [&](int Z) {
+#pragma unroll
+        for (int sl = 0; sl < NSLOT; ++sl) {
+            const int q = tid + sl * TX * TY;
+            if (q < PX * PY) {
+                const int ly = q / PX, lx = q - ly * PX;
+                pu[sl] = fetch_u<P>(p, U, x0 + lx - 1, y0 + ly - 1, Z);
+                pk[sl] = fetch_k<P>(p, x0 + lx - 1, y0 + ly - 1, Z);
+            }
+        }
+    };
+    auto commit = [&](int buf) {
+#pragma unroll
+        for (int sl = 0; sl < NSLOT; ++sl) {
+            const int q = tid + sl * TX * TY;
+            if (q < PX * PY) {
+                const int ly = q / PX, lx = q - ly * PX;
+                P::st(&sU[buf][ly][lx], pu[sl]);
+                P::st(&sK[buf][ly][lx], pk[sl]);
+            }
         }
     };
     auto lift = [&](int buf, int slot) {
@@ -269,14 +286,15 @@ stencil_kernel(SParams<P> p, const typename P::M* __restrict__ U, typename P::M*
                 k[slot][b][a] = P::ld(&sK[buf][ty + b][tx + a], 0);
             }
     };
-    int buf = 0;
-    stage(buf, z0 - 1); __syncthreads(); lift(buf, 0); buf ^= 1;
-    stage(buf, z0);     __syncthreads(); lift(buf, 1); buf ^= 1;
+    fetch(z0 - 1); commit(0); __syncthreads(); lift(0, 0);
+    fetch(z0);     commit(1); __syncthreads(); lift(1, 1);
+    fetch(z0 + 1);
     for (int z = z0; z < z1; ++z) {
-        stage(buf, z + 1);
+        const int buf = z & 1;            // plane z+1 goes to the buffer that held plane z-1
+        commit(buf);
         __syncthreads();
         lift(buf, 2);
-        buf ^= 1;
+        if (z + 2 <= z1) fetch(z + 2);    // in flight during the arithmetic below
         if (active) {
             const size_t gidx = ((size_t)z * p.ny + gy) * p.nx + gx;
             C v = apply_point<P, ORDER>(p, u, k, gidx);

@@ -41,10 +41,12 @@ class helm_options(C.Structure):
 class helm_solve_info(C.Structure):
     _fields_ = [("status", C.c_int), ("iterations", C.c_int), ("restarts", C.c_int), ("reserved", C.c_int),
                 ("relres_true", C.c_double), ("relres_est", C.c_double), ("beta0", C.c_double),
-                ("seconds", C.c_double)]
+                ("seconds", C.c_double), ("cycle_its", C.c_int * 16)]
 
     def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+        d = {k: getattr(self, k) for k, _ in self._fields_ if k not in ("reserved", "cycle_its")}
+        d["cycle_its"] = [c for c in self.cycle_its if c]
+        return d
 
 
 _lib = None
