@@ -33,7 +33,7 @@ void free_ctx(helm_ctx* c) {
     prof_release(c);
     void* ps[] = {c->k2_d, c->k2_f, c->dk2_d[0], c->dk2_d[1], c->dk2_d[2], c->dk2_f[0], c->dk2_f[1], c->dk2_f[2],
                   c->G_d, c->G_f, c->Dx, c->Dy, c->Vx, c->Vxi, c->Vy, c->Vyi, c->XF, c->XI, c->YF, c->YI,
-                  c->dxs, c->dys, c->cz, c->tmp, c->status_d, c->k2_df, c->G_df};
+                  c->dxs, c->dys, c->cz, c->tmp, c->status_d, c->k2_df, c->G_df, c->rhs_scratch};
     for (void* p : ps) if (p) cudaFree(p);
     delete c;
 }
@@ -154,7 +154,10 @@ helm_status helm_build_rhs(helm_ctx* c, const void* f, void* F, void* stream) {
         HELM_CUDA_TRY(cudaMemcpyAsync(buf, f, c->npts * sizeof(double2), cudaMemcpyHostToDevice, s));
         fd = buf;
     }
-    helm_status st = launch_rhs(c, fd, (double2*)F, s);
+    if (!c->rhs_scratch) {
+        if (cudaMalloc(&c->rhs_scratch, c->npts * sizeof(float4)) != cudaSuccess) { cudaGetLastError(); return HELM_ERR_NOMEM; }
+    }
+    helm_status st = launch_rhs(c, fd, (double2*)F, c->rhs_scratch, s);
     if (buf) { cudaStreamSynchronize(s); cudaFree(buf); }
     return st;
 }

@@ -108,6 +108,7 @@ struct helm_ctx {
     float2* G_f = nullptr;
     float4* k2_df = nullptr;                // double-float k^2 and G for the true residual
     float4* G_df = nullptr;
+    float4* rhs_scratch = nullptr;          // double-float copy of f for helm_build_rhs
     // 1D eigendecompositions, FP64 (row-major [row][col])
     double2 *Dx = nullptr, *Dy = nullptr, *Vx = nullptr, *Vxi = nullptr, *Vy = nullptr, *Vyi = nullptr;
     // complex64 transform operands
@@ -133,7 +134,7 @@ helm_status launch_derived_fields(helm_ctx* c, cudaStream_t s);
 helm_status launch_stencil_f32(helm_ctx* c, const float2* x, float2* y, const double* sigma, int sidx, cudaStream_t s);
 helm_status launch_stencil_f64(helm_ctx* c, const double2* x, double2* y, cudaStream_t s);
 helm_status launch_residual(helm_ctx* c, const float4* x, const float4* F, float2* r, double* part, cudaStream_t s);
-helm_status launch_rhs(helm_ctx* c, const double2* f, double2* F, cudaStream_t s);
+helm_status launch_rhs(helm_ctx* c, const double2* f, double2* F, float4* fdf, cudaStream_t s);
 // eig.cu
 helm_status run_eig_setup(helm_ctx* c, cudaStream_t s);
 // gemm_simt.cu

@@ -155,9 +155,15 @@ __device__ __forceinline__ typename P::LC dterm(const SParams<P>& p, typename P:
 }
 
 // A at one point from the 3x3x3 neighbourhood u[c][b][a] (a = x offset + 1, b = y, c = z) and k^2 in kk.
+template <class P>
+struct PointFields {            // per-point coefficient fields of the sixth-order scheme
+    typename P::C G;
+    typename P::LC g[3];
+};
+
 template <class P, int ORDER>
 __device__ __forceinline__ typename P::C apply_point(const SParams<P>& p, const typename P::C (&u)[3][3][3],
-                                                     const typename P::C (&kk)[3][3][3], size_t gidx) {
+                                                     const typename P::C (&kk)[3][3][3], const PointFields<P>& pf) {
     typedef typename P::C C;
     typedef typename P::LC LC;
     const C u0 = u[1][1][1];
@@ -210,7 +216,7 @@ __device__ __forceinline__ typename P::C apply_point(const SParams<P>& p, const 
                             P::sub(P::scl(Sc, P::cst(1.0 / 30.0)), P::scl(u0, P::cst(64.0 / 15.0))));
         C out = P::scl(up, p.ihx);
         out = P::add(out, P::add(P::scl(K0, P::cst(14.0 / 15.0)), P::scl(P::sub(Ke, Kf), P::cst(1.0 / 90.0))));
-        out = P::add(out, P::scl(P::mul(P::ld(p.G, gidx), u0), p.h2_20));
+        out = P::add(out, P::scl(P::mul(pf.G, u0), p.h2_20));
         // (h/20) sum_d g_d D_d in low precision
         auto T = [&](int c, int b, int a, int c1, int b1, int a1, int c2, int b2, int a2, int c3, int b3, int a3,
                      int c4, int b4, int a4) {
@@ -223,9 +229,9 @@ __device__ __forceinline__ typename P::C apply_point(const SParams<P>& p, const 
                                T(1, 2, 1, 1, 2, 0, 1, 2, 2, 0, 2, 1, 2, 2, 1), T(1, 0, 1, 1, 0, 0, 1, 0, 2, 0, 0, 1, 2, 0, 1));
         const LC Dz = dterm<P>(p, P::lo(u[2][1][1]), P::lo(u[0][1][1]), P::lo(KUzp), P::lo(KUzm),
                                T(2, 1, 1, 2, 1, 0, 2, 1, 2, 2, 0, 1, 2, 2, 1), T(0, 1, 1, 0, 1, 0, 0, 1, 2, 0, 0, 1, 0, 2, 1));
-        LC g = cmul(p.dk2[0][gidx], Dx);
-        g = ladd(g, cmul(p.dk2[1][gidx], Dy));
-        g = ladd(g, cmul(p.dk2[2][gidx], Dz));
+        LC g = cmul(pf.g[0], Dx);
+        g = ladd(g, cmul(pf.g[1], Dy));
+        g = ladd(g, cmul(pf.g[2], Dz));
         if (sizeof(g.x) == 8) { g.x *= p.h_20d; g.y *= p.h_20d; } else { g.x *= p.h_20; g.y *= p.h_20; }
         return P::add(out, P::from_lo(g));
     }
@@ -235,7 +241,7 @@ __device__ __forceinline__ typename P::C apply_point(const SParams<P>& p, const 
 // MODE 1: r = F - A X written as complex64, with per-CTA partial sums of |r|^2 and max |r| (FP64)
 //         in part[2*cta], part[2*cta+1].
 template <class P, int ORDER, int MODE>
-__global__ void __launch_bounds__(TX * TY)
+__global__ void __launch_bounds__(TX * TY, sizeof(typename P::C) == 8 ? 2 : 1)
 stencil_kernel(SParams<P> p, const typename P::M* __restrict__ U, typename P::M* __restrict__ Y,
                const double* __restrict__ sigma, int sidx, const typename P::M* __restrict__ F, float2* __restrict__ rout,
                double* __restrict__ part) {
@@ -286,18 +292,31 @@ stencil_kernel(SParams<P> p, const typename P::M* __restrict__ U, typename P::M*
                 k[slot][b][a] = P::ld(&sK[buf][ty + b][tx + a], 0);
             }
     };
+    // order-6 point fields are also fetched one plane ahead
+    PointFields<P> pf_cur, pf_nxt;
+    auto fetch_pf = [&](int Z, PointFields<P>& f) {
+        if (ORDER == 6 && active && Z < z1) {
+            const size_t g = ((size_t)Z * p.ny + gy) * p.nx + gx;
+            f.G = P::ld(p.G, g);
+#pragma unroll
+            for (int d = 0; d < 3; ++d) f.g[d] = p.dk2[d][g];
+        }
+    };
     fetch(z0 - 1); commit(0); __syncthreads(); lift(0, 0);
     fetch(z0);     commit(1); __syncthreads(); lift(1, 1);
     fetch(z0 + 1);
+    constexpr bool AHEAD = sizeof(typename P::C) == 8;   // complex64: fields one plane ahead
+    if (AHEAD) fetch_pf(z0, pf_cur);
     for (int z = z0; z < z1; ++z) {
         const int buf = z & 1;            // plane z+1 goes to the buffer that held plane z-1
         commit(buf);
         __syncthreads();
         lift(buf, 2);
         if (z + 2 <= z1) fetch(z + 2);    // in flight during the arithmetic below
+        if (AHEAD) fetch_pf(z + 1, pf_nxt); else fetch_pf(z, pf_cur);
         if (active) {
             const size_t gidx = ((size_t)z * p.ny + gy) * p.nx + gx;
-            C v = apply_point<P, ORDER>(p, u, k, gidx);
+            C v = apply_point<P, ORDER>(p, u, k, pf_cur);
             if (MODE == 0) {
                 if (sigma) v = P::scl(v, P::cst(sigma[sidx]));
                 P::st(&Y[gidx], v);
@@ -310,6 +329,7 @@ stencil_kernel(SParams<P> p, const typename P::M* __restrict__ U, typename P::M*
                 smax = fmax(smax, a2);
             }
         }
+        if (AHEAD) pf_cur = pf_nxt;
 #pragma unroll
         for (int b = 0; b < 3; ++b)
 #pragma unroll
@@ -403,72 +423,90 @@ __global__ void derived_kernel(int order, int nx, int ny, int nz, double hx, dou
     }
 }
 
-// ---- modified right-hand side (set-up, FP64) -------------------------------------------------
-__global__ void rhs_kernel(int order, int nx, int ny, int nz, double hx, double hy, double hz,
-                           const double2* __restrict__ f, const double2* __restrict__ k2,
-                           const double2* __restrict__ dkx, const double2* __restrict__ dky,
-                           const double2* __restrict__ dkz, double2* __restrict__ F) {
+// ---- modified right-hand side -----------------------------------------------------------------
+// F from samples of f (double-float copy fdf), k^2 (double-float) and the FP32 gradients of k^2.
+// The terms of relative size ~(k h)^2 (lap f, k^2 f) are formed in double-float; the h^4 terms, three
+// orders smaller, in FP32 from the leading parts.  Mirror extension at the faces (reading).
+__global__ void rhs_df_kernel(int order, int nx, int ny, int nz, double hx, double hy, double hz,
+                              const float4* __restrict__ fdf, const float4* __restrict__ k2df,
+                              const float2* __restrict__ dkx, const float2* __restrict__ dky,
+                              const float2* __restrict__ dkz, double2* __restrict__ F) {
     const size_t n = (size_t)nx * ny * nz;
+    const df c12 = PDF::cst(1.0 / 12.0);
     for (size_t id = blockIdx.x * (size_t)blockDim.x + threadIdx.x; id < n; id += (size_t)gridDim.x * blockDim.x) {
         const int i = (int)(id % nx), j = (int)((id / nx) % ny), l = (int)(id / ((size_t)nx * ny));
         auto at = [&](int a, int b, int c) {
-            return f[((size_t)mirror_stag(l + c, nz) * ny + mirror_stag(j + b, ny)) * nx + mirror_stag(i + a, nx)];
+            return cdf_from4(fdf[((size_t)mirror_stag(l + c, nz) * ny + mirror_stag(j + b, ny)) * nx + mirror_stag(i + a, nx)]);
         };
-        const double2 fc = f[id];
-        if (order == 2) { F[id] = fc; continue; }
-        const double hh[3] = {hx, hy, hz};
+        const cdf fc = cdf_from4(fdf[id]);
+        if (order == 2) { F[id] = cdf_to_double2(fc); continue; }
         if (order == 4) {
-            double2 out = fc;
+            // f + (1/12) sum_d (f+ - 2f + f-)
+            cdf s = cdf_zero();
             for (int d = 0; d < 3; ++d) {
                 int o[3] = {0, 0, 0};
-                o[d] = 1; double2 pp = at(o[0], o[1], o[2]);
-                o[d] = -1; double2 m = at(o[0], o[1], o[2]);
-                out.x += (pp.x - 2 * fc.x + m.x) / 12.0;
-                out.y += (pp.y - 2 * fc.y + m.y) / 12.0;
+                o[d] = 1; s = cdf_add(s, at(o[0], o[1], o[2]));
+                o[d] = -1; s = cdf_add(s, at(o[0], o[1], o[2]));
             }
-            F[id] = out;
+            const cdf c6 = cdf_add(cdf_add(fc, fc), cdf_add(cdf_add(fc, fc), cdf_add(fc, fc)));
+            F[id] = cdf_to_double2(cdf_add(fc, cdf_scale(cdf_sub(s, c6), c12)));
             continue;
         }
+        // order 6, uniform h
         const double h = hx, h2 = h * h;
-        double2 lap = make_double2(0, 0), s4 = make_double2(0, 0), fd[3];
+        const double hh[3] = {hx, hy, hz};
+        cdf lap = cdf_zero();        // sum_d h^2/12 * (4th-order lap_d f) in double-float, i.e. (h^2/12) lap f
+        float2 s4 = make_float2(0.f, 0.f), fd[3];
         for (int d = 0; d < 3; ++d) {
             int o[3] = {0, 0, 0};
-            double2 v[5];
+            cdf v[5];
             for (int s = -2; s <= 2; ++s) { o[d] = s; v[s + 2] = at(o[0], o[1], o[2]); }
-            lap.x += (-v[4].x + 16 * v[3].x - 30 * v[2].x + 16 * v[1].x - v[0].x) / (12 * hh[d] * hh[d]);
-            lap.y += (-v[4].y + 16 * v[3].y - 30 * v[2].y + 16 * v[1].y - v[0].y) / (12 * hh[d] * hh[d]);
-            const double h4 = hh[d] * hh[d] * hh[d] * hh[d];
-            s4.x += (v[4].x - 4 * v[3].x + 6 * v[2].x - 4 * v[1].x + v[0].x) / h4;
-            s4.y += (v[4].y - 4 * v[3].y + 6 * v[2].y - 4 * v[1].y + v[0].y) / h4;
-            fd[d].x = (v[3].x - v[1].x) / (2 * hh[d]);
-            fd[d].y = (v[3].y - v[1].y) / (2 * hh[d]);
+            // (-f2 + 16 f1 - 30 f0 + 16 f-1 - f-2) / 12, times (h/h_d)^2 / 12 (uniform h: 1/12)
+            cdf t = cdf_sub(cdf_scale(cdf_add(v[3], v[1]), df{16.f, 0.f}), cdf_add(v[4], v[0]));
+            t = cdf_sub(t, cdf_scale(v[2], df{30.f, 0.f}));
+            lap = cdf_add(lap, cdf_scale(t, PDF::cst(h2 / (144.0 * hh[d] * hh[d]))));
+            const float2 a0 = make_float2(v[0].re.hi, v[0].im.hi), a1 = make_float2(v[1].re.hi, v[1].im.hi);
+            const float2 a2 = make_float2(v[2].re.hi, v[2].im.hi), a3 = make_float2(v[3].re.hi, v[3].im.hi);
+            const float2 a4 = make_float2(v[4].re.hi, v[4].im.hi);
+            const float ih4 = (float)(1.0 / (hh[d] * hh[d] * hh[d] * hh[d]));
+            s4.x += (a4.x - 4 * a3.x + 6 * a2.x - 4 * a1.x + a0.x) * ih4;
+            s4.y += (a4.y - 4 * a3.y + 6 * a2.y - 4 * a1.y + a0.y) * ih4;
+            fd[d] = make_float2((a3.x - a1.x) / (float)(2 * hh[d]), (a3.y - a1.y) / (float)(2 * hh[d]));
         }
-        double2 mix = make_double2(0, 0);
+        float2 mix = make_float2(0.f, 0.f);
         const int pairs[3][2] = {{0, 1}, {0, 2}, {1, 2}};
-        const double w[3] = {1.0, -2.0, 1.0};
+        const float w[3] = {1.f, -2.f, 1.f};
         for (int q = 0; q < 3; ++q) {
-            double2 acc = make_double2(0, 0);
+            float2 acc = make_float2(0.f, 0.f);
             for (int s1 = -1; s1 <= 1; ++s1)
                 for (int s2 = -1; s2 <= 1; ++s2) {
                     int o[3] = {0, 0, 0};
                     o[pairs[q][0]] = s1; o[pairs[q][1]] = s2;
-                    const double2 v = at(o[0], o[1], o[2]);
-                    acc.x += w[s1 + 1] * w[s2 + 1] * v.x;
-                    acc.y += w[s1 + 1] * w[s2 + 1] * v.y;
+                    const cdf v = at(o[0], o[1], o[2]);
+                    acc.x += w[s1 + 1] * w[s2 + 1] * v.re.hi;
+                    acc.y += w[s1 + 1] * w[s2 + 1] * v.im.hi;
                 }
-            const double den = hh[pairs[q][0]] * hh[pairs[q][0]] * hh[pairs[q][1]] * hh[pairs[q][1]];
-            mix.x += acc.x / den; mix.y += acc.y / den;
+            const float den = (float)(1.0 / (hh[pairs[q][0]] * hh[pairs[q][0]] * hh[pairs[q][1]] * hh[pairs[q][1]]));
+            mix.x += acc.x * den; mix.y += acc.y * den;
         }
-        double2 out;
-        out.x = fc.x + h2 / 12.0 * lap.x + h2 * h2 / 360.0 * s4.x + h2 * h2 / 90.0 * mix.x;
-        out.y = fc.y + h2 / 12.0 * lap.y + h2 * h2 / 360.0 * s4.y + h2 * h2 / 90.0 * mix.y;
-        const double2 kc = k2[id];
-        const double2 kf = cmul(kc, fc);
-        const double2 gf = cadd(cadd(cmul(dkx[id], fd[0]), cmul(dky[id], fd[1])), cmul(dkz[id], fd[2]));
-        out.x -= h2 / 20.0 * (kf.x - h2 / 3.0 * gf.x);
-        out.y -= h2 / 20.0 * (kf.y - h2 / 3.0 * gf.y);
-        F[id] = out;
+        // big terms (double-float): f + (h^2/12) lap f - (h^2/20) k^2 f
+        const cdf kc = cdf_from4(k2df[id]);
+        cdf out = cdf_add(fc, lap);
+        out = cdf_sub(out, cdf_scale(cdf_mul(kc, fc), PDF::cst(h2 / 20.0)));
+        // small terms (FP32): h^4/360 s4 + h^4/90 mix + (h^4/60) sum_d g_d f_d
+        const float h4 = (float)(h2 * h2);
+        float2 g = cadd(cadd(cmul(dkx[id], fd[0]), cmul(dky[id], fd[1])), cmul(dkz[id], fd[2]));
+        float2 sm;
+        sm.x = h4 / 360.f * s4.x + h4 / 90.f * mix.x + h4 / 60.f * g.x;
+        sm.y = h4 / 360.f * s4.y + h4 / 90.f * mix.y + h4 / 60.f * g.y;
+        out = cdf_add(out, cdf_from_f2(sm));
+        F[id] = cdf_to_double2(out);
     }
+}
+
+__global__ void f64_to_df_kernel(const double2* __restrict__ a, float4* __restrict__ b, size_t n) {
+    for (size_t id = blockIdx.x * (size_t)blockDim.x + threadIdx.x; id < n; id += (size_t)gridDim.x * blockDim.x)
+        b[id] = split4(a[id]);
 }
 
 template <class P, int MODE>
@@ -535,9 +573,13 @@ helm_status launch_residual(helm_ctx* c, const float4* x, const float4* F, float
     return HELM_OK;
 }
 
-helm_status launch_rhs(helm_ctx* c, const double2* f, double2* F, cudaStream_t s) {
-    rhs_kernel<<<1024, 256, 0, s>>>(c->opt.order, c->nx, c->ny, c->nz, c->h[0], c->h[1], c->h[2], f, c->k2_d,
-                                    c->dk2_d[0], c->dk2_d[1], c->dk2_d[2], F);
+// F from samples f (FP64); fdf is a double-float scratch grid of the caller
+helm_status launch_rhs(helm_ctx* c, const double2* f, double2* F, float4* fdf, cudaStream_t s) {
+    prof_begin(c, s, PROF_OTHER);
+    f64_to_df_kernel<<<1024, 256, 0, s>>>(f, fdf, c->npts);
+    rhs_df_kernel<<<2048, 256, 0, s>>>(c->opt.order, c->nx, c->ny, c->nz, c->h[0], c->h[1], c->h[2], fdf, c->k2_df,
+                                       c->dk2_f[0], c->dk2_f[1], c->dk2_f[2], F);
+    prof_end(c, s);
     HELM_CUDA_TRY(cudaGetLastError());
     return HELM_OK;
 }
