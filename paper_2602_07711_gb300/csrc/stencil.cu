@@ -452,54 +452,46 @@ __global__ void rhs_df_kernel(int order, int nx, int ny, int nz, double hx, doub
             F[id] = cdf_to_double2(cdf_add(fc, cdf_scale(cdf_sub(s, c6), c12)));
             continue;
         }
-        // order 6, uniform h
+        // order 6, uniform h: every term in double-float (for rough f the h^4 terms are not small)
         const double h = hx, h2 = h * h;
         const double hh[3] = {hx, hy, hz};
-        cdf lap = cdf_zero();        // sum_d h^2/12 * (4th-order lap_d f) in double-float, i.e. (h^2/12) lap f
-        float2 s4 = make_float2(0.f, 0.f), fd[3];
+        cdf lap = cdf_zero(), s4 = cdf_zero();
+        float2 fd[3];
         for (int d = 0; d < 3; ++d) {
             int o[3] = {0, 0, 0};
             cdf v[5];
             for (int s = -2; s <= 2; ++s) { o[d] = s; v[s + 2] = at(o[0], o[1], o[2]); }
-            // (-f2 + 16 f1 - 30 f0 + 16 f-1 - f-2) / 12, times (h/h_d)^2 / 12 (uniform h: 1/12)
+            // (h^2/12) * (-f2 + 16 f1 - 30 f0 + 16 f-1 - f-2) / (12 h_d^2)
             cdf t = cdf_sub(cdf_scale(cdf_add(v[3], v[1]), df{16.f, 0.f}), cdf_add(v[4], v[0]));
             t = cdf_sub(t, cdf_scale(v[2], df{30.f, 0.f}));
             lap = cdf_add(lap, cdf_scale(t, PDF::cst(h2 / (144.0 * hh[d] * hh[d]))));
-            const float2 a0 = make_float2(v[0].re.hi, v[0].im.hi), a1 = make_float2(v[1].re.hi, v[1].im.hi);
-            const float2 a2 = make_float2(v[2].re.hi, v[2].im.hi), a3 = make_float2(v[3].re.hi, v[3].im.hi);
-            const float2 a4 = make_float2(v[4].re.hi, v[4].im.hi);
-            const float ih4 = (float)(1.0 / (hh[d] * hh[d] * hh[d] * hh[d]));
-            s4.x += (a4.x - 4 * a3.x + 6 * a2.x - 4 * a1.x + a0.x) * ih4;
-            s4.y += (a4.y - 4 * a3.y + 6 * a2.y - 4 * a1.y + a0.y) * ih4;
-            fd[d] = make_float2((a3.x - a1.x) / (float)(2 * hh[d]), (a3.y - a1.y) / (float)(2 * hh[d]));
+            // (h^4/360) * (f2 - 4 f1 + 6 f0 - 4 f-1 + f-2) / h_d^4
+            cdf q = cdf_sub(cdf_add(cdf_add(v[4], v[0]), cdf_scale(v[2], df{6.f, 0.f})),
+                            cdf_scale(cdf_add(v[3], v[1]), df{4.f, 0.f}));
+            s4 = cdf_add(s4, cdf_scale(q, PDF::cst(h2 * h2 / (360.0 * hh[d] * hh[d] * hh[d] * hh[d]))));
+            fd[d] = make_float2((v[3].re.hi - v[1].re.hi) / (float)(2 * hh[d]), (v[3].im.hi - v[1].im.hi) / (float)(2 * hh[d]));
         }
-        float2 mix = make_float2(0.f, 0.f);
+        cdf mix = cdf_zero();
         const int pairs[3][2] = {{0, 1}, {0, 2}, {1, 2}};
         const float w[3] = {1.f, -2.f, 1.f};
         for (int q = 0; q < 3; ++q) {
-            float2 acc = make_float2(0.f, 0.f);
+            cdf acc = cdf_zero();
             for (int s1 = -1; s1 <= 1; ++s1)
                 for (int s2 = -1; s2 <= 1; ++s2) {
                     int o[3] = {0, 0, 0};
                     o[pairs[q][0]] = s1; o[pairs[q][1]] = s2;
-                    const cdf v = at(o[0], o[1], o[2]);
-                    acc.x += w[s1 + 1] * w[s2 + 1] * v.re.hi;
-                    acc.y += w[s1 + 1] * w[s2 + 1] * v.im.hi;
+                    acc = cdf_add(acc, cdf_scale(at(o[0], o[1], o[2]), df{w[s1 + 1] * w[s2 + 1], 0.f}));
                 }
-            const float den = (float)(1.0 / (hh[pairs[q][0]] * hh[pairs[q][0]] * hh[pairs[q][1]] * hh[pairs[q][1]]));
-            mix.x += acc.x * den; mix.y += acc.y * den;
+            const double den = hh[pairs[q][0]] * hh[pairs[q][0]] * hh[pairs[q][1]] * hh[pairs[q][1]];
+            mix = cdf_add(mix, cdf_scale(acc, PDF::cst(h2 * h2 / (90.0 * den))));
         }
-        // big terms (double-float): f + (h^2/12) lap f - (h^2/20) k^2 f
         const cdf kc = cdf_from4(k2df[id]);
-        cdf out = cdf_add(fc, lap);
+        cdf out = cdf_add(cdf_add(fc, lap), cdf_add(s4, mix));
         out = cdf_sub(out, cdf_scale(cdf_mul(kc, fc), PDF::cst(h2 / 20.0)));
-        // small terms (FP32): h^4/360 s4 + h^4/90 mix + (h^4/60) sum_d g_d f_d
+        // (h^4/60) sum_d g_d f_d: gradients of k^2 are FP32 and this term is O((k h)^4) of f: FP32
         const float h4 = (float)(h2 * h2);
-        float2 g = cadd(cadd(cmul(dkx[id], fd[0]), cmul(dky[id], fd[1])), cmul(dkz[id], fd[2]));
-        float2 sm;
-        sm.x = h4 / 360.f * s4.x + h4 / 90.f * mix.x + h4 / 60.f * g.x;
-        sm.y = h4 / 360.f * s4.y + h4 / 90.f * mix.y + h4 / 60.f * g.y;
-        out = cdf_add(out, cdf_from_f2(sm));
+        const float2 g = cadd(cadd(cmul(dkx[id], fd[0]), cmul(dky[id], fd[1])), cmul(dkz[id], fd[2]));
+        out = cdf_add(out, cdf_from_f2(make_float2(h4 / 60.f * g.x, h4 / 60.f * g.y)));
         F[id] = cdf_to_double2(out);
     }
 }
