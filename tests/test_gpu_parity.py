@@ -1,7 +1,8 @@
 """Parity of the CUDA path (through the C-ABI) with the complex128 CPU oracle, element by element.
 
 Tolerances (relative, max-norm over the output unless stated):
-  complex128 kernels (apply_A FP64, build_rhs, eigensetup)      1e-11
+  complex128 kernels (apply_A FP64, eigensetup)                 1e-11
+  double-float kernels (build_rhs; ~44-bit arithmetic)          1e-10
   complex64 stencil                                            2e-6   (FP32 rounding of ~27 terms)
   complex64 EigT transforms / z-solve / preconditioner (FP32)  2e-5 * kappa(V)-scaled, see _tol_precond
   GMRES solution at rtol 1e-6 vs oracle solved to 1e-12         1e-5 in the relative 2-norm (the benchmark spec)
@@ -82,9 +83,9 @@ def test_build_rhs_matches_oracle(order):
     else:
         dk2, _ = derived_k2_fields(k2, True, g.h)
         ref = rhs6_sampled(f, k2, dk2, True, g.h)
-    assert _rel(F, ref) < 1e-11
+    assert _rel(F, ref) < 1e-10
     F2 = S.build_rhs(f).cpu().numpy()          # host input
-    assert _rel(F2, ref) < 1e-11
+    assert _rel(F2, ref) < 1e-10
 
 
 @pytest.mark.parametrize("n", [4, 5, 17, 32, 33, 64, 127, 256, 512])
