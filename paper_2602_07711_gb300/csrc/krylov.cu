@@ -56,8 +56,9 @@ constexpr int NT = 256;
 constexpr int GRP = 8;
 
 // partial inner products conj(v_i) . w for i in [0, nv); part[blk * ld + i].
-// Two points per 16-byte load, two loads of each vector in flight per thread; products summed in FP32
-// over 8 points and then in FP64.  npts is even (every grid here has an even N_x).
+// Two points per 16-byte load, two loads of each vector in flight per thread; per-thread sums are
+// compensated FP32 (Kahan), FP64 only across threads (GB300's FP64 rate made FP64 partial sums the
+// limiter).  npts is even.
 __global__ void __launch_bounds__(NT) dots_kernel(const float2* __restrict__ V, size_t npts, int nv,
                                                  const float2* __restrict__ w, double2* __restrict__ part, int ld) {
     __shared__ double2 red[NT / 32][GRP];
@@ -67,11 +68,10 @@ __global__ void __launch_bounds__(NT) dots_kernel(const float2* __restrict__ V, 
     const float4* __restrict__ W4 = reinterpret_cast<const float4*>(w);
     for (int g0 = 0; g0 < nv; g0 += GRP) {
         const int ng = min(GRP, nv - g0);
-        double2 acc[GRP];
-        float2 a32[GRP];
+        // compensated (Kahan) FP32 sums per thread; FP64 only for the cross-thread reduction
+        float2 ks[GRP], kc[GRP];
 #pragma unroll
-        for (int q = 0; q < GRP; ++q) { acc[q] = make_double2(0, 0); a32[q] = make_float2(0, 0); }
-        int cnt = 0;
+        for (int q = 0; q < GRP; ++q) { ks[q] = make_float2(0, 0); kc[q] = make_float2(0, 0); }
         for (size_t id = blockIdx.x * (size_t)NT + tid; id < n4; id += 2 * stride) {
             const size_t id2 = id + stride;
             const bool two = id2 < n4;
@@ -83,26 +83,25 @@ __global__ void __launch_bounds__(NT) dots_kernel(const float2* __restrict__ V, 
                     const float4* __restrict__ V4 = reinterpret_cast<const float4*>(V + (size_t)(g0 + q) * npts);
                     const float4 va = V4[id];
                     const float4 vb = two ? V4[id2] : make_float4(0.f, 0.f, 0.f, 0.f);
-                    float re = a32[q].x, im = a32[q].y;
-                    re = fmaf(va.x, wa.x, fmaf(va.y, wa.y, re));
-                    im = fmaf(va.x, wa.y, fmaf(-va.y, wa.x, im));
+                    float re = va.x * wa.x, im = va.x * wa.y;
+                    re = fmaf(va.y, wa.y, re);
+                    im = fmaf(-va.y, wa.x, im);
                     re = fmaf(va.z, wa.z, fmaf(va.w, wa.w, re));
                     im = fmaf(va.z, wa.w, fmaf(-va.w, wa.z, im));
                     re = fmaf(vb.x, wb.x, fmaf(vb.y, wb.y, re));
                     im = fmaf(vb.x, wb.y, fmaf(-vb.y, wb.x, im));
                     re = fmaf(vb.z, wb.z, fmaf(vb.w, wb.w, re));
                     im = fmaf(vb.z, wb.w, fmaf(-vb.w, wb.z, im));
-                    a32[q] = make_float2(re, im);
+                    float y = re - kc[q].x, t = ks[q].x + y;
+                    kc[q].x = (t - ks[q].x) - y; ks[q].x = t;
+                    y = im - kc[q].y; t = ks[q].y + y;
+                    kc[q].y = (t - ks[q].y) - y; ks[q].y = t;
                 }
-            if (++cnt == 2) {
-                cnt = 0;
-#pragma unroll
-                for (int q = 0; q < GRP; ++q) { acc[q].x += a32[q].x; acc[q].y += a32[q].y; a32[q] = make_float2(0, 0); }
-            }
         }
+        double2 acc[GRP];
 #pragma unroll
         for (int q = 0; q < GRP; ++q) {
-            acc[q].x += a32[q].x; acc[q].y += a32[q].y;
+            acc[q] = make_double2((double)ks[q].x - (double)kc[q].x, (double)ks[q].y - (double)kc[q].y);
             for (int o = 16; o > 0; o >>= 1) {
                 acc[q].x += __shfl_down_sync(0xffffffffu, acc[q].x, o);
                 acc[q].y += __shfl_down_sync(0xffffffffu, acc[q].y, o);

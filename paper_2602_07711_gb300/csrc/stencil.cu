@@ -161,24 +161,33 @@ struct PointFields {            // per-point coefficient fields of the sixth-ord
     typename P::LC g[3];
 };
 
+// U and KU = k^2 U on the 3x3 patch of one z-plane around a column; [b][a] = (y offset + 1, x offset + 1)
+template <class P>
+struct Plane {
+    typename P::C u[3][3];
+    typename P::C kc, kxm, kxp, kym, kyp;   // KU at the centre and the four in-plane neighbours
+    typename P::C kcs;                      // sum of KU over the four in-plane corners
+};
+
+// A at one point from its planes lo (z-1), mid (z) and hi (z+1).
 template <class P, int ORDER>
-__device__ __forceinline__ typename P::C apply_point(const SParams<P>& p, const typename P::C (&u)[3][3][3],
-                                                     const typename P::C (&kk)[3][3][3], const PointFields<P>& pf) {
+__device__ __forceinline__ typename P::C apply_point(const SParams<P>& p, const Plane<P>& lo, const Plane<P>& mid,
+                                                     const Plane<P>& hi, const PointFields<P>& pf) {
     typedef typename P::C C;
     typedef typename P::LC LC;
-    const C u0 = u[1][1][1];
-    const C K0 = P::mul(kk[1][1][1], u0);
-    const C fx = P::add(u[1][1][0], u[1][1][2]);
-    const C fy = P::add(u[1][0][1], u[1][2][1]);
-    const C fz = P::add(u[0][1][1], u[2][1][1]);
+    const C u0 = mid.u[1][1];
+    const C K0 = mid.kc;
+    const C fx = P::add(mid.u[1][0], mid.u[1][2]);
+    const C fy = P::add(mid.u[0][1], mid.u[2][1]);
+    const C fz = P::add(lo.u[1][1], hi.u[1][1]);
     if (ORDER == 2 || ORDER == 4) {
         const C u2 = P::add(u0, u0);
         C out = P::add(P::add(P::scl(P::sub(fx, u2), p.ihx), P::scl(P::sub(fy, u2), p.ihy)),
                        P::scl(P::sub(fz, u2), p.ihz));
         if (ORDER == 2) return P::add(out, K0);
-        const C exy = P::add(P::add(u[1][0][0], u[1][0][2]), P::add(u[1][2][0], u[1][2][2]));
-        const C exz = P::add(P::add(u[0][1][0], u[0][1][2]), P::add(u[2][1][0], u[2][1][2]));
-        const C eyz = P::add(P::add(u[0][0][1], u[0][2][1]), P::add(u[2][0][1], u[2][2][1]));
+        const C exy = P::add(P::add(mid.u[0][0], mid.u[0][2]), P::add(mid.u[2][0], mid.u[2][2]));
+        const C exz = P::add(P::add(lo.u[1][0], lo.u[1][2]), P::add(hi.u[1][0], hi.u[1][2]));
+        const C eyz = P::add(P::add(lo.u[0][1], lo.u[2][1]), P::add(hi.u[0][1], hi.u[2][1]));
         const C u4 = P::add(u2, u2);
         // da2 db2 U = e_ab - 2 (f_a + f_b) + 4 U_0
         const C fxy = P::add(fx, fy), fxz = P::add(fx, fz), fyz = P::add(fy, fz);
@@ -186,49 +195,39 @@ __device__ __forceinline__ typename P::C apply_point(const SParams<P>& p, const 
         out = P::add(out, P::scl(P::add(P::sub(exz, P::add(fxz, fxz)), u4), p.wxz));
         out = P::add(out, P::scl(P::add(P::sub(eyz, P::add(fyz, fyz)), u4), p.wyz));
         // (1 + sum hd^2/12 dd2)(k^2 U) = K0/2 + (sum of the six face values of k^2 U)/12
-        C kf = P::add(P::add(P::mul(kk[1][1][0], u[1][1][0]), P::mul(kk[1][1][2], u[1][1][2])),
-                      P::add(P::mul(kk[1][0][1], u[1][0][1]), P::mul(kk[1][2][1], u[1][2][1])));
-        kf = P::add(kf, P::add(P::mul(kk[0][1][1], u[0][1][1]), P::mul(kk[2][1][1], u[2][1][1])));
-        out = P::add(out, P::add(P::scl(K0, P::cst(0.5)), P::scl(kf, P::cst(1.0 / 12.0))));
-        return out;
+        const C kf = P::add(P::add(P::add(mid.kxm, mid.kxp), P::add(mid.kym, mid.kyp)),
+                            P::add(lo.kc, hi.kc));
+        return P::add(out, P::add(P::scl(K0, P::cst(0.5)), P::scl(kf, P::cst(1.0 / 12.0))));
     } else {
-        const C KUxp = P::mul(kk[1][1][2], u[1][1][2]), KUxm = P::mul(kk[1][1][0], u[1][1][0]);
-        const C KUyp = P::mul(kk[1][2][1], u[1][2][1]), KUym = P::mul(kk[1][0][1], u[1][0][1]);
-        const C KUzp = P::mul(kk[2][1][1], u[2][1][1]), KUzm = P::mul(kk[0][1][1], u[0][1][1]);
+        const C KUxp = mid.kxp, KUxm = mid.kxm, KUyp = mid.kyp, KUym = mid.kym;
+        const C KUzp = hi.kc, KUzm = lo.kc;
         const C Kf = P::add(P::add(P::add(KUxp, KUxm), P::add(KUyp, KUym)), P::add(KUzp, KUzm));
-        C Ke = P::zero(), Se = P::zero(), Sc = P::zero();
-        const int ED[12][3] = {{1, 0, 0}, {1, 0, 2}, {1, 2, 0}, {1, 2, 2}, {0, 1, 0}, {0, 1, 2},
-                               {2, 1, 0}, {2, 1, 2}, {0, 0, 1}, {0, 2, 1}, {2, 0, 1}, {2, 2, 1}};
-#pragma unroll
-        for (int q = 0; q < 12; ++q) {
-            const int c = ED[q][0], b = ED[q][1], a = ED[q][2];
-            Ke = P::add(Ke, P::mul(kk[c][b][a], u[c][b][a]));
-            Se = P::add(Se, u[c][b][a]);
-        }
-#pragma unroll
-        for (int c = 0; c < 3; c += 2)
-#pragma unroll
-            for (int b = 0; b < 3; b += 2)
-#pragma unroll
-                for (int a = 0; a < 3; a += 2) Sc = P::add(Sc, u[c][b][a]);
+        const C Ke = P::add(mid.kcs, P::add(P::add(P::add(lo.kxm, lo.kxp), P::add(lo.kym, lo.kyp)),
+                                            P::add(P::add(hi.kxm, hi.kxp), P::add(hi.kym, hi.kyp))));
+        const C Se = P::add(P::add(P::add(P::add(mid.u[0][0], mid.u[0][2]), P::add(mid.u[2][0], mid.u[2][2])),
+                                   P::add(P::add(lo.u[1][0], lo.u[1][2]), P::add(hi.u[1][0], hi.u[1][2]))),
+                            P::add(P::add(lo.u[0][1], lo.u[2][1]), P::add(hi.u[0][1], hi.u[2][1])));
+        const C Sc = P::add(P::add(P::add(lo.u[0][0], lo.u[0][2]), P::add(lo.u[2][0], lo.u[2][2])),
+                            P::add(P::add(hi.u[0][0], hi.u[0][2]), P::add(hi.u[2][0], hi.u[2][2])));
         const C Sf = P::add(P::add(fx, fy), fz);
         const C up = P::add(P::add(P::scl(Sf, P::cst(7.0 / 15.0)), P::scl(Se, P::cst(0.1))),
                             P::sub(P::scl(Sc, P::cst(1.0 / 30.0)), P::scl(u0, P::cst(64.0 / 15.0))));
         C out = P::scl(up, p.ihx);
         out = P::add(out, P::add(P::scl(K0, P::cst(14.0 / 15.0)), P::scl(P::sub(Ke, Kf), P::cst(1.0 / 90.0))));
         out = P::add(out, P::scl(P::mul(pf.G, u0), p.h2_20));
-        // (h/20) sum_d g_d D_d in low precision
-        auto T = [&](int c, int b, int a, int c1, int b1, int a1, int c2, int b2, int a2, int c3, int b3, int a3,
-                     int c4, int b4, int a4) {
-            return P::lo(P::sub(P::add(P::add(u[c1][b1][a1], u[c2][b2][a2]), P::add(u[c3][b3][a3], u[c4][b4][a4])),
-                                P::scl(u[c][b][a], P::cst(4.0))));
+        // (h/20) sum_d g_d D_d in low precision; T = (four transverse neighbours) - 4 (side point)
+        auto T = [&](const C& side, const C& a, const C& b, const C& c, const C& d) {
+            return P::lo(P::sub(P::add(P::add(a, b), P::add(c, d)), P::scl(side, P::cst(4.0))));
         };
-        const LC Dx = dterm<P>(p, P::lo(u[1][1][2]), P::lo(u[1][1][0]), P::lo(KUxp), P::lo(KUxm),
-                               T(1, 1, 2, 1, 0, 2, 1, 2, 2, 0, 1, 2, 2, 1, 2), T(1, 1, 0, 1, 0, 0, 1, 2, 0, 0, 1, 0, 2, 1, 0));
-        const LC Dy = dterm<P>(p, P::lo(u[1][2][1]), P::lo(u[1][0][1]), P::lo(KUyp), P::lo(KUym),
-                               T(1, 2, 1, 1, 2, 0, 1, 2, 2, 0, 2, 1, 2, 2, 1), T(1, 0, 1, 1, 0, 0, 1, 0, 2, 0, 0, 1, 2, 0, 1));
-        const LC Dz = dterm<P>(p, P::lo(u[2][1][1]), P::lo(u[0][1][1]), P::lo(KUzp), P::lo(KUzm),
-                               T(2, 1, 1, 2, 1, 0, 2, 1, 2, 2, 0, 1, 2, 2, 1), T(0, 1, 1, 0, 1, 0, 0, 1, 2, 0, 0, 1, 0, 2, 1));
+        const LC Dx = dterm<P>(p, P::lo(mid.u[1][2]), P::lo(mid.u[1][0]), P::lo(KUxp), P::lo(KUxm),
+                               T(mid.u[1][2], mid.u[0][2], mid.u[2][2], lo.u[1][2], hi.u[1][2]),
+                               T(mid.u[1][0], mid.u[0][0], mid.u[2][0], lo.u[1][0], hi.u[1][0]));
+        const LC Dy = dterm<P>(p, P::lo(mid.u[2][1]), P::lo(mid.u[0][1]), P::lo(KUyp), P::lo(KUym),
+                               T(mid.u[2][1], mid.u[2][0], mid.u[2][2], lo.u[2][1], hi.u[2][1]),
+                               T(mid.u[0][1], mid.u[0][0], mid.u[0][2], lo.u[0][1], hi.u[0][1]));
+        const LC Dz = dterm<P>(p, P::lo(hi.u[1][1]), P::lo(lo.u[1][1]), P::lo(KUzp), P::lo(KUzm),
+                               T(hi.u[1][1], hi.u[1][0], hi.u[1][2], hi.u[0][1], hi.u[2][1]),
+                               T(lo.u[1][1], lo.u[1][0], lo.u[1][2], lo.u[0][1], lo.u[2][1]));
         LC g = cmul(pf.g[0], Dx);
         g = ladd(g, cmul(pf.g[1], Dy));
         g = ladd(g, cmul(pf.g[2], Dz));
@@ -240,6 +239,9 @@ __device__ __forceinline__ typename P::C apply_point(const SParams<P>& p, const 
 // MODE 0: Y = scale * A X (Y in the policy's storage type).
 // MODE 1: r = F - A X written as complex64, with per-CTA partial sums of |r|^2 and max |r| (FP64)
 //         in part[2*cta], part[2*cta+1].
+// Each halo plane is staged as U and KU = k^2 U (one product per staged point instead of nineteen per
+// output point); the thread keeps three planes of its 3x3 patch of U (and the KU values the scheme
+// uses) in registers.
 template <class P, int ORDER, int MODE>
 __global__ void __launch_bounds__(TX * TY, sizeof(typename P::C) == 8 ? 2 : 1)
 stencil_kernel(SParams<P> p, const typename P::M* __restrict__ U, typename P::M* __restrict__ Y,
@@ -254,11 +256,9 @@ stencil_kernel(SParams<P> p, const typename P::M* __restrict__ U, typename P::M*
     const int z1 = min(z0 + ZCH, p.nz);
     const int gx = x0 + tx, gy = y0 + ty;
     const bool active = gx < p.nx && gy < p.ny;
-    C u[3][3][3], k[3][3][3];
     double ssum = 0.0, smax = 0.0;
 
-    // Register-staged prefetch: each thread owns at most two halo-plane slots; the loads of plane z+2 are
-    // issued before the arithmetic of plane z so that their latency overlaps it.
+    // register-staged prefetch of halo planes: at most two slots per thread
     constexpr int NSLOT = (PX * PY + TX * TY - 1) / (TX * TY);
     C pu[NSLOT], pk[NSLOT];
     auto fetch = [&](int Z) {
@@ -279,44 +279,39 @@ stencil_kernel(SParams<P> p, const typename P::M* __restrict__ U, typename P::M*
             if (q < PX * PY) {
                 const int ly = q / PX, lx = q - ly * PX;
                 P::st(&sU[buf][ly][lx], pu[sl]);
-                P::st(&sK[buf][ly][lx], pk[sl]);
+                P::st(&sK[buf][ly][lx], P::mul(pk[sl], pu[sl]));
             }
         }
     };
-    auto lift = [&](int buf, int slot) {
+    auto lift = [&](int buf, Plane<P>& pl) {
 #pragma unroll
         for (int b = 0; b < 3; ++b)
 #pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                u[slot][b][a] = P::ld(&sU[buf][ty + b][tx + a], 0);
-                k[slot][b][a] = P::ld(&sK[buf][ty + b][tx + a], 0);
-            }
+            for (int a = 0; a < 3; ++a) pl.u[b][a] = P::ld(&sU[buf][ty + b][tx + a], 0);
+        pl.kc = P::ld(&sK[buf][ty + 1][tx + 1], 0);
+        pl.kxm = P::ld(&sK[buf][ty + 1][tx], 0);
+        pl.kxp = P::ld(&sK[buf][ty + 1][tx + 2], 0);
+        pl.kym = P::ld(&sK[buf][ty][tx + 1], 0);
+        pl.kyp = P::ld(&sK[buf][ty + 2][tx + 1], 0);
+        if (ORDER == 6)
+            pl.kcs = P::add(P::add(P::ld(&sK[buf][ty][tx], 0), P::ld(&sK[buf][ty][tx + 2], 0)),
+                            P::add(P::ld(&sK[buf][ty + 2][tx], 0), P::ld(&sK[buf][ty + 2][tx + 2], 0)));
     };
-    // order-6 point fields are also fetched one plane ahead
-    PointFields<P> pf_cur, pf_nxt;
-    auto fetch_pf = [&](int Z, PointFields<P>& f) {
-        if (ORDER == 6 && active && Z < z1) {
-            const size_t g = ((size_t)Z * p.ny + gy) * p.nx + gx;
-            f.G = P::ld(p.G, g);
+    auto body = [&](int z, const Plane<P>& lo, const Plane<P>& mid, Plane<P>& hi) {
+        PointFields<P> pf;
+        const size_t gidx = ((size_t)z * p.ny + gy) * p.nx + gx;
+        if (ORDER == 6 && active) {
+            pf.G = P::ld(p.G, gidx);
 #pragma unroll
-            for (int d = 0; d < 3; ++d) f.g[d] = p.dk2[d][g];
+            for (int d = 0; d < 3; ++d) pf.g[d] = p.dk2[d][gidx];
         }
-    };
-    fetch(z0 - 1); commit(0); __syncthreads(); lift(0, 0);
-    fetch(z0);     commit(1); __syncthreads(); lift(1, 1);
-    fetch(z0 + 1);
-    constexpr bool AHEAD = sizeof(typename P::C) == 8;   // complex64: fields one plane ahead
-    if (AHEAD) fetch_pf(z0, pf_cur);
-    for (int z = z0; z < z1; ++z) {
-        const int buf = z & 1;            // plane z+1 goes to the buffer that held plane z-1
+        const int buf = z & 1;            // plane z+1 replaces plane z-1
         commit(buf);
         __syncthreads();
-        lift(buf, 2);
+        lift(buf, hi);
         if (z + 2 <= z1) fetch(z + 2);    // in flight during the arithmetic below
-        if (AHEAD) fetch_pf(z + 1, pf_nxt); else fetch_pf(z, pf_cur);
         if (active) {
-            const size_t gidx = ((size_t)z * p.ny + gy) * p.nx + gx;
-            C v = apply_point<P, ORDER>(p, u, k, pf_cur);
+            C v = apply_point<P, ORDER>(p, lo, mid, hi, pf);
             if (MODE == 0) {
                 if (sigma) v = P::scl(v, P::cst(sigma[sidx]));
                 P::st(&Y[gidx], v);
@@ -329,14 +324,15 @@ stencil_kernel(SParams<P> p, const typename P::M* __restrict__ U, typename P::M*
                 smax = fmax(smax, a2);
             }
         }
-        if (AHEAD) pf_cur = pf_nxt;
-#pragma unroll
-        for (int b = 0; b < 3; ++b)
-#pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                u[0][b][a] = u[1][b][a]; u[1][b][a] = u[2][b][a];
-                k[0][b][a] = k[1][b][a]; k[1][b][a] = k[2][b][a];
-            }
+    };
+    Plane<P> A, B, Cq;
+    fetch(z0 - 1); commit(0); __syncthreads(); lift(0, A);
+    fetch(z0);     commit(1); __syncthreads(); lift(1, B);
+    fetch(z0 + 1);
+    for (int z = z0; z < z1; ++z) {
+        body(z, A, B, Cq);
+        A = B;
+        B = Cq;
     }
     if (MODE == 1) {
         __shared__ double rs[TX * TY / 32], rm[TX * TY / 32];
@@ -443,7 +439,8 @@ __global__ void rhs_df_kernel(int order, int nx, int ny, int nz, double hx, doub
         if (order == 4) {
             // f + (1/12) sum_d (f+ - 2f + f-)
             cdf s = cdf_zero();
-            for (int d = 0; d < 3; ++d) {
+    #pragma unroll
+        for (int d = 0; d < 3; ++d) {
                 int o[3] = {0, 0, 0};
                 o[d] = 1; s = cdf_add(s, at(o[0], o[1], o[2]));
                 o[d] = -1; s = cdf_add(s, at(o[0], o[1], o[2]));
@@ -457,9 +454,11 @@ __global__ void rhs_df_kernel(int order, int nx, int ny, int nz, double hx, doub
         const double hh[3] = {hx, hy, hz};
         cdf lap = cdf_zero(), s4 = cdf_zero();
         float2 fd[3];
+#pragma unroll
         for (int d = 0; d < 3; ++d) {
             int o[3] = {0, 0, 0};
             cdf v[5];
+#pragma unroll
             for (int s = -2; s <= 2; ++s) { o[d] = s; v[s + 2] = at(o[0], o[1], o[2]); }
             // (h^2/12) * (-f2 + 16 f1 - 30 f0 + 16 f-1 - f-2) / (12 h_d^2)
             cdf t = cdf_sub(cdf_scale(cdf_add(v[3], v[1]), df{16.f, 0.f}), cdf_add(v[4], v[0]));
@@ -474,9 +473,12 @@ __global__ void rhs_df_kernel(int order, int nx, int ny, int nz, double hx, doub
         cdf mix = cdf_zero();
         const int pairs[3][2] = {{0, 1}, {0, 2}, {1, 2}};
         const float w[3] = {1.f, -2.f, 1.f};
+#pragma unroll
         for (int q = 0; q < 3; ++q) {
             cdf acc = cdf_zero();
+#pragma unroll
             for (int s1 = -1; s1 <= 1; ++s1)
+#pragma unroll
                 for (int s2 = -1; s2 <= 1; ++s2) {
                     int o[3] = {0, 0, 0};
                     o[pairs[q][0]] = s1; o[pairs[q][1]] = s2;

@@ -63,10 +63,14 @@ zsolve_kernel(ZParams p, const float2* in, float2* out, unsigned* status) {
     auto sub = [p, nz](int l) { return l == 0 ? 0.f : (l == nz - 1 ? p.zz : 1.f); };
     auto sup = [p, nz](int l) { return l == nz - 1 ? 0.f : (l == 0 ? p.zz : 1.f); };
 
-    float2 y[MCH];
+    float2 y[MCH], bd[MCH];
 #pragma unroll
     for (int k = 0; k < MCH; ++k)
         y[k] = (live && k < len) ? in[base + (size_t)(s + k) * plane] : f2(0.f, 0.f);
+#pragma unroll
+    for (int k = 0; k < MCH; ++k) bd[k] = (k < len) ? diag(s + k) : f2(1.f, 0.f);
+    float minpiv = 1e30f;
+    auto piv = [&](float2 d) { minpiv = fminf(minpiv, fabsf(d.x) + fabsf(d.y)); };
 
     // down elimination with x_{s-1} as parameter: x_e = d' + l' x_{s-1} - c' x_{e+1}
     float2 cp = f2(0.f, 0.f), dp = f2(0.f, 0.f), lp = f2(0.f, 0.f);
@@ -75,8 +79,8 @@ zsolve_kernel(ZParams p, const float2* in, float2* out, unsigned* status) {
         if (k < len) {
             const int l = s + k;
             const float a = sub(l);
-            const float2 den = (k == 0) ? diag(l) : csub(diag(l), cscale(cp, a));
-            note_pivot(den, status);
+            const float2 den = (k == 0) ? bd[k] : csub(bd[k], cscale(cp, a));
+            piv(den);
             const float2 nd = (k == 0) ? qdiv(y[k], den) : qdiv(csub(y[k], cscale(dp, a)), den);
             const float2 nl = (k == 0) ? qdiv(f2(-a, 0.f), den) : qdiv(cscale(lp, -a), den);
             cp = qdiv(f2(sup(l), 0.f), den);
@@ -93,8 +97,8 @@ zsolve_kernel(ZParams p, const float2* in, float2* out, unsigned* status) {
             const int l = s + k;
             const float c = sup(l);
             const bool first = (k == len - 1);
-            const float2 den = first ? diag(l) : csub(diag(l), cscale(ch, c));
-            note_pivot(den, status);
+            const float2 den = first ? bd[k] : csub(bd[k], cscale(ch, c));
+            piv(den);
             const float2 nd = first ? qdiv(y[k], den) : qdiv(csub(y[k], cscale(dh, c)), den);
             const float2 nr = first ? qdiv(f2(-c, 0.f), den) : qdiv(cscale(rh, -c), den);
             ch = qdiv(f2(sub(l), 0.f), den);
@@ -121,7 +125,7 @@ zsolve_kernel(ZParams p, const float2* in, float2* out, unsigned* status) {
             const float2 b10 = cmul(pe, G1);                 // B_c = [[b00, 0], [b10, 1]]
             const float2 r0 = cadd(sh[0][c][lane], cmul(ps, Y1));
             const float2 r1 = cadd(sh[3][c][lane], cmul(pe, Y1));
-            note_pivot(b00, status);
+            piv(b00);
             const float2 y0 = qdiv(r0, b00);
             const float2 y1 = csub(r1, cmul(b10, y0));
             const float2 g0 = qdiv(cscale(qs, -1.f), b00);
@@ -151,7 +155,7 @@ zsolve_kernel(ZParams p, const float2* in, float2* out, unsigned* status) {
         if (k < len) {
             const int l = s + k;
             const float a = sub(l);
-            const float2 den = (k == 0) ? diag(l) : csub(diag(l), cscale(c_prev, a));
+            const float2 den = (k == 0) ? bd[k] : csub(bd[k], cscale(c_prev, a));
             float2 rhs = csub(y[k], cscale(d_prev, a));
             const bool last = (k == len - 1);
             if (last) rhs = csub(rhs, cscale(Rv, sup(l)));
@@ -170,6 +174,7 @@ zsolve_kernel(ZParams p, const float2* in, float2* out, unsigned* status) {
             if (live) out[base + (size_t)(s + k) * plane] = xn;
         }
     }
+    if (live && !(minpiv > 1e-30f)) atomicOr(status, (unsigned)HELM_DEV_PIVOT);
 }
 
 }  // namespace
@@ -184,8 +189,8 @@ helm_status launch_zsolve(helm_ctx* c, const float2* in, float2* out, cudaStream
     prof_begin(c, s, PROF_ZSOLVE);
     if (c->nz <= 256) {
         p.W = (c->nz + 7) / 8;
-        dim3 grid((c->nx + 31) / 32, c->ny), block(32, p.W);
-        zsolve_kernel<32, 8><<<grid, block, 0, s>>>(p, in, out, c->status_d);
+        dim3 grid((c->nx + 15) / 16, c->ny), block(16, p.W);
+        zsolve_kernel<16, 8><<<grid, block, 0, s>>>(p, in, out, c->status_d);
     } else {
         p.W = (c->nz + 15) / 16;
         dim3 grid((c->nx + 15) / 16, c->ny), block(16, p.W);
