@@ -145,6 +145,19 @@ helm_status helm_gmres_solve(helm_ctx* ctx, const void* b, void* x, helm_solve_i
 helm_status helm_residual(helm_ctx* ctx, const void* b, const void* x, void* r, double* nrm2, double* nrmi,
                           void* stream);
 
+/* helm_residual_noalloc - the same residual and norms as helm_residual, for callers that cannot allocate
+ * device memory (for instance while a CUDA graph is being captured, or inside a framework whose memory
+ * pool is frozen after warm-up).  The paper has no counterpart: this is a library convenience.
+ *   b, x   complex128 device buffers;  r  complex64 device output (required);  nrm2, nrmi as above.
+ * Allocates nothing: its scratch (double-float copies of b and x, per-CTA partial sums) is one static
+ * device array of 65 MiB + 256 B that every GPU loading the library holds until exit.  Limit: at most
+ * 2^21 = 2,097,152 grid points (128^3) and 65536 residual CTAs; larger problems return HELM_ERR_ARG.
+ * The first call on a device looks up the array's device address; make that first call before any
+ * stream capture.  All calls share the array (each call rewrites every part it reads), so calls that
+ * overlap on the GPU race.  Synchronises `stream`. */
+helm_status helm_residual_noalloc(helm_ctx* ctx, const void* b, const void* x, void* r, double* nrm2,
+                                  double* nrmi, void* stream);
+
 /* helm_profile - enable (1) or disable (0) per-kernel timing on this context: CUDA events are recorded
  * on the launch stream around every kernel launch of the solver (adds no synchronisation).  The first
  * call allocates the event pool (host-side cost only). */

@@ -63,6 +63,8 @@ _SIGS = {
     "helm_gmres_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(helm_solve_info), C.c_void_p]),
     "helm_residual": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_double),
                                 C.POINTER(C.c_double), C.c_void_p]),
+    "helm_residual_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_double),
+                                        C.POINTER(C.c_double), C.c_void_p]),
     "helm_profile": (C.c_int, [C.c_void_p, C.c_int]),
     "helm_profile_read": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int]),
     "helm_destroy": (None, [C.c_void_p]),
@@ -154,6 +156,14 @@ def helm_residual(ctx, b, x, r=None, stream=None):
     _check(lib().helm_residual(ctx, _ptr(b), _ptr(x), _ptr(r) if r is not None else None, C.byref(n2), C.byref(ni),
                                _stream(stream)), "helm_residual")
     return n2.value, ni.value
+
+
+def helm_residual_noalloc(ctx, b, x, r, stream=None):
+    """Allocation-free residual (see include/helm.h); returns (status, ||r||_2, ||r||_inf)."""
+    n2 = C.c_double()
+    ni = C.c_double()
+    code = lib().helm_residual_noalloc(ctx, _ptr(b), _ptr(x), _ptr(r), C.byref(n2), C.byref(ni), _stream(stream))
+    return code, n2.value, ni.value
 
 
 def helm_destroy(ctx):
