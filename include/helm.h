@@ -53,6 +53,8 @@ typedef struct {
     int staggered;
 } helm_grid;
 
+/* Preconditioner M^-1 = h_z^2 A_p^-1 (Sec. 4): none, EigT (Sec. 4.1) or PFFT (Sec. 4.2; needs N_x and N_y
+ * powers of two <= 512; its sine solver uses the Dirichlet condition at the staggered face). */
 enum { HELM_PRECOND_NONE = 0, HELM_PRECOND_EIGT = 1, HELM_PRECOND_PFFT = 2 };
 
 /* Arithmetic of the eigenvector transforms (EigT steps 2 and 4).  The stencil, the z-solves and the

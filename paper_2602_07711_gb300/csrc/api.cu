@@ -30,6 +30,7 @@ void free_ctx(helm_ctx* c) {
     if (!c) return;
     krylov_free(c);
     tc_release(c);
+    pfft_release(c);
     prof_release(c);
     void* ps[] = {c->k2_d, c->k2_f, c->dk2_d[0], c->dk2_d[1], c->dk2_d[2], c->dk2_f[0], c->dk2_f[1], c->dk2_f[2],
                   c->G_d, c->G_f, c->Dx, c->Dy, c->Vx, c->Vxi, c->Vy, c->Vyi, c->XF, c->XI, c->YF, c->YI,
@@ -77,7 +78,6 @@ helm_status helm_setup(const helm_grid* grid, const void* k2, double k0, const d
     // the Krylov kernels move two points per 16-byte access: the point count must be even
     if (((size_t)grid->nx * grid->ny * grid->nz) % 2 != 0) return HELM_ERR_UNSUPPORTED;
     if (grid->nz > 512) return HELM_ERR_UNSUPPORTED;
-    if (opt->precond == HELM_PRECOND_PFFT) return HELM_ERR_UNSUPPORTED;
     cudaStream_t s = (cudaStream_t)stream;
     helm_ctx* c = new helm_ctx();
     cudaGetDevice(&c->device);
@@ -139,6 +139,7 @@ helm_status helm_setup(const helm_grid* grid, const void* k2, double k0, const d
         if (c->nx % 2 != 0) { free_ctx(c); return HELM_ERR_UNSUPPORTED; }
         TRY(tc_prepare(c, s));
     }
+    if (opt->precond == HELM_PRECOND_PFFT) TRY(pfft_prepare(c, s));
     if (cudaStreamSynchronize(s) != cudaSuccess) { free_ctx(c); return HELM_ERR_CUDA; }
     *out = c;
     return HELM_OK;

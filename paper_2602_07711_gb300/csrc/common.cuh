@@ -120,6 +120,7 @@ struct helm_ctx {
     float *XFr = nullptr, *XIr = nullptr;   // real-embedded x-pass B, [2N][2K] K-major (hi, lo follow)
     float *YFr = nullptr, *YIr = nullptr;   // y-pass A: re and im planes [2][N][N] (hi, lo follow)
     void* tmaps = nullptr;                  // host copies of TMA descriptors (gemm_tc.cu)
+    void* pfft = nullptr;                   // PFFT tables and scratch (pfft.cu)
     // scratch
     float2* tmp = nullptr;                  // one complex64 grid vector
     unsigned* status_d = nullptr;           // device status word
@@ -149,6 +150,12 @@ helm_status tc_ypass(helm_ctx* c, int inverse, const float2* in, float2* out, cu
 void tc_release(helm_ctx* c);
 // thomas.cu
 helm_status launch_zsolve(helm_ctx* c, const float2* in, float2* out, cudaStream_t s);
+helm_status launch_zsolve_gen(helm_ctx* c, const float2* in, float2* out, const float2* dxs, const float2* dys,
+                              const float2* P, const float2* Q, cudaStream_t s);
+// pfft.cu
+helm_status pfft_prepare(helm_ctx* c, cudaStream_t s);
+helm_status pfft_apply(helm_ctx* c, const float2* r, float2* z, const double* sigma, int sidx, cudaStream_t s);
+void pfft_release(helm_ctx* c);
 // precond.cu
 helm_status precond_apply(helm_ctx* c, const float2* r, float2* z, const double* sigma, int sidx, cudaStream_t s);
 helm_status precond_step(helm_ctx* c, int step, const float2* in, float2* out, cudaStream_t s);

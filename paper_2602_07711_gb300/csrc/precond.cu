@@ -74,6 +74,12 @@ helm_status precond_apply(helm_ctx* c, const float2* r, float2* z, const double*
         HELM_CUDA_TRY(cudaGetLastError());
         return HELM_OK;
     }
+    if (c->opt.precond == HELM_PRECOND_PFFT) {
+        prof_begin(c, s, PROF_OTHER);
+        st = pfft_apply(c, r, z, sigma, sidx, s);
+        prof_end(c, s);
+        return st;
+    }
     const float hz2 = (float)(c->h[2] * c->h[2]);
     if ((st = xpass(c, 0, r, c->tmp, 1.f, sigma, sidx, s)) != HELM_OK) return st;
     if ((st = ypass(c, 0, c->tmp, z, s)) != HELM_OK) return st;

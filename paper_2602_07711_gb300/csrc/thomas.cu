@@ -23,6 +23,9 @@ struct ZParams {
     const float2* cz;    // h_z^2 k0^2(z_l) - 2(alpha_x + alpha_y + 1)
     float2 gz;           // gamma_z
     float zz;            // zeta_z
+    // optional generated right-hand side: y[l][j][i] += sum_{t<4} P[t][l][j] Q[t][l][i]  (PFFT)
+    const float2* P;
+    const float2* Q;
 };
 
 __device__ inline float2 f2(float a, float b) { return make_float2(a, b); }
@@ -66,7 +69,17 @@ zsolve_kernel(ZParams p, const float2* in, float2* out, unsigned* status) {
     float2 y[MCH], bd[MCH];
 #pragma unroll
     for (int k = 0; k < MCH; ++k)
-        y[k] = (live && k < len) ? in[base + (size_t)(s + k) * plane] : f2(0.f, 0.f);
+        y[k] = (in && live && k < len) ? in[base + (size_t)(s + k) * plane] : f2(0.f, 0.f);
+    if (p.P && live) {
+#pragma unroll
+        for (int k = 0; k < MCH; ++k)
+            if (k < len) {
+                const int l = s + k;
+#pragma unroll
+                for (int t = 0; t < 4; ++t)
+                    y[k] = cadd(y[k], cmul(p.P[((size_t)t * nz + l) * p.ny + j], p.Q[((size_t)t * nz + l) * p.nx + i]));
+            }
+    }
 #pragma unroll
     for (int k = 0; k < MCH; ++k) bd[k] = (k < len) ? diag(s + k) : f2(1.f, 0.f);
     float minpiv = 1e30f;
@@ -179,10 +192,12 @@ zsolve_kernel(ZParams p, const float2* in, float2* out, unsigned* status) {
 
 }  // namespace
 
-helm_status launch_zsolve(helm_ctx* c, const float2* in, float2* out, cudaStream_t s) {
+helm_status launch_zsolve_gen(helm_ctx* c, const float2* in, float2* out, const float2* dxs, const float2* dys,
+                              const float2* P, const float2* Q, cudaStream_t s) {
     ZParams p;
     p.nx = c->nx; p.ny = c->ny; p.nz = c->nz;
-    p.dxs = c->dxs; p.dys = c->dys; p.cz = c->cz;
+    p.dxs = dxs; p.dys = dys; p.cz = c->cz;
+    p.P = P; p.Q = Q;
     p.gz = make_float2((float)c->gam[2].x, (float)c->gam[2].y);
     p.zz = (float)c->zeta[2];
     if (c->nz > 512) return HELM_ERR_UNSUPPORTED;
@@ -199,4 +214,8 @@ helm_status launch_zsolve(helm_ctx* c, const float2* in, float2* out, cudaStream
     prof_end(c, s);
     HELM_CUDA_TRY(cudaGetLastError());
     return HELM_OK;
+}
+
+helm_status launch_zsolve(helm_ctx* c, const float2* in, float2* out, cudaStream_t s) {
+    return launch_zsolve_gen(c, in, out, c->dxs, c->dys, nullptr, nullptr, s);
 }

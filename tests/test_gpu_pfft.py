@@ -1,0 +1,51 @@
+"""PFFT preconditioner (Sec. 4.2) on the GPU against the oracle, through the C-ABI.
+
+The PFFT solve and the EigT solve both invert the same A_p exactly, so the GPU's PFFT output is checked
+against both the oracle's PFFT (face-Dirichlet sine basis) and its EigT.  complex64 arithmetic: relative
+2-norm error <= 2e-5 * kappa(V_x) kappa(V_y) (the boundary correction passes through the EigT bases).
+"""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle.eigt import EigT
+from oracle.grid import Grid
+from oracle.pfft import PFFT
+from paper_2602_07711_gb300 import HELM_PRECOND_EIGT, HELM_PRECOND_PFFT, Solver, media
+
+
+def _rand(shape, seed):
+    r = np.random.default_rng(seed)
+    return r.standard_normal(shape) + 1j * r.standard_normal(shape)
+
+
+@pytest.mark.parametrize("n,L", [((32, 32, 20), (1.0, 1.0, 0.625)), ((64, 32, 33), (1.0, 0.6, 0.5)),
+                                 ((16, 64, 8), (0.25, 1.0, 0.2)), ((128, 128, 12), (1.0, 1.0, 0.1))])
+def test_pfft_preconditioner_matches_oracle(n, L):
+    g = Grid(*n, lx=L[0], ly=L[1], lz=L[2], staggered=True)
+    k0 = 2 * math.pi / (10 * g.h[0])
+    S = Solver(n, np.full(g.shape, k0 * k0, complex), k0, order=4, L=L, precond=HELM_PRECOND_PFFT)
+    y = _rand(g.shape, 7)
+    z = S.apply_precond(torch.from_numpy(y).to("cuda", torch.complex64)).cpu().numpy()
+    e = EigT(g, k0)
+    kap = np.linalg.cond(e.Vx) * np.linalg.cond(e.Vy)
+    for ref in (PFFT(g, k0, variant="face").apply_Minv(y), e.apply_Minv(y)):
+        err = np.linalg.norm(z - ref) / np.linalg.norm(ref)
+        assert err < 2e-5 * kap, (err, kap)
+
+
+def test_pfft_gmres_matches_eigt_gmres():
+    n = 64
+    k2, f, k0 = media.bumps(n, 31, 32)
+    out = {}
+    for pc in (HELM_PRECOND_EIGT, HELM_PRECOND_PFFT):
+        S = Solver((n, n, n), k2, k0, order=6, precond=pc, flexible=True, rtol=1e-6)
+        x, info = S.solve(S.build_rhs(torch.from_numpy(f).cuda()))
+        assert info.status == 0 and info.relres_true <= 1e-6
+        out[pc] = (x.cpu().numpy(), info.iterations)
+    d = np.linalg.norm(out[1][0] - out[2][0]) / np.linalg.norm(out[1][0])
+    assert d < 2e-5 and abs(out[1][1] - out[2][1]) <= 1
