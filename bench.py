@@ -25,7 +25,8 @@ sys.path.insert(0, ROOT)
 METRIC = "time-to-rtol 1e-6 (s) & Mpts·iter/s at n=256³; mixed/learned vs plain EigT"
 UNIT = "Mpts·iter/s"
 PREC_NAMES = {"fp32": 0, "tf32": 1, "3xtf32": 2}
-CLASSES = ["stencil", "xpass", "ypass", "zsolve", "dots", "update", "small", "combine", "residual", "other"]
+CLASSES = ["stencil", "xpass", "ypass", "zsolve", "dots", "update", "small", "combine", "residual", "other",
+           "learned"]
 
 
 def parse():
@@ -247,9 +248,9 @@ def run_ours(args, rank, world, local):
     lib.helm_profile.argtypes = [helm.C.c_void_p, helm.C.c_int]
     lib.helm_profile_read.argtypes = [helm.C.c_void_p, helm.C.c_void_p, helm.C.c_void_p, helm.C.c_int, helm.C.c_int]
     lib.helm_profile(S.ctx, 1)
-    ms_arr = (helm.C.c_double * 10)()
-    ln_arr = (helm.C.c_longlong * 10)()
-    lib.helm_profile_read(S.ctx, ms_arr, ln_arr, 10, 1)
+    ms_arr = (helm.C.c_double * len(CLASSES))()
+    ln_arr = (helm.C.c_longlong * len(CLASSES))()
+    lib.helm_profile_read(S.ctx, ms_arr, ln_arr, len(CLASSES), 1)
     clocks = ClockSampler(local)
     clocks.start()
     if world > 1:
@@ -265,7 +266,7 @@ def run_ours(args, rank, world, local):
         dist.barrier()
     clk = clocks.stop()
     elapsed = ev0.elapsed_time(ev1) / 1e3
-    lib.helm_profile_read(S.ctx, ms_arr, ln_arr, 10, 1)
+    lib.helm_profile_read(S.ctx, ms_arr, ln_arr, len(CLASSES), 1)
     lib.helm_profile(S.ctx, 0)
     prof_ms = {c: ms_arr[i] for i, c in enumerate(CLASSES)}
     prof_ln = {c: ln_arr[i] for i, c in enumerate(CLASSES)}

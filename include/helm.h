@@ -167,10 +167,68 @@ helm_status helm_profile(helm_ctx* ctx, int enable);
 
 /* helm_profile_read - accumulated milliseconds and launch counts per kernel class since the last reset,
  * in the order: stencil (complex64 A), x-pass, y-pass, z-solve, Arnoldi dots, Arnoldi update,
- * small FP64 kernels (reductions, Givens, least squares), solution update, FP64 true residual, other.
+ * small FP64 kernels (reductions, Givens, least squares), solution update, FP64 true residual, other,
+ * learned correction.
  *   ms, launches  host arrays of n entries (either may be NULL);  reset != 0 clears the counters.
  * Synchronises on the recorded events. */
 helm_status helm_profile_read(helm_ctx* ctx, double* ms, long long* launches, int n, int reset);
+
+/* ---- Learned correction (an extension: the paper has no counterpart) ----------------------------------
+ * A small 3D U-Net N, applied after M^-1 inside flexible GMRES:
+ *     c = s N(x),   s = RMS(M^-1 v),
+ *     x = [Re v, Im v]/RMS(v), [Re, Im](M^-1 v)/s, Re(k^2)/k0^2 - 1      (5 channels)
+ *     z = M^-1 v + alpha c,   alpha = <A c, v - A M^-1 v>/<A c, A c>   (complex64 stencil A of the context)
+ * alpha minimises |v - A z|_2, so the corrected z never has a larger preconditioned residual than M^-1 v
+ * (plain EigT is the fallback).  The correction is dropped (z = M^-1 v) when A c = 0 or a sum is not finite.
+ * Network of width c: a1 = relu(conv(x,5->c)), a2 = relu(conv(a1,c->c)), p = avgpool2(a2),
+ * b1 = relu(conv(p,c->2c)), b2 = relu(conv(b1,2c->2c)), u = [upsample2(b2), a2],
+ * d1 = relu(conv(u,3c->c)), N = conv(d1,c->2); 3x3x3 convolutions, zero padding.
+ * Parameters (float32, in this order, per layer l = 1..6): weights [Cout][Cin][3][3][3], then bias [Cout].
+ * Activations are stored in bfloat16 with float32 accumulation; training keeps float32 master weights.
+ * Tensors are [B][C][Z][Y][X] (X fastest), Z, Y, X even.  A net is used by one stream at a time. */
+typedef struct helm_net helm_net;
+
+/* helm_net_create - new network of width c (1..64), He-normal weights from `seed` (last layer x0.1),
+ * zero biases.  Errors: HELM_ERR_ARG, HELM_ERR_NOMEM, HELM_ERR_CUDA; *out = NULL then. */
+helm_status helm_net_create(int width, unsigned long long seed, helm_net** out);
+/* helm_net_destroy - free (NULL is a no-op).  Detach it from every context first. */
+void helm_net_destroy(helm_net* net);
+/* helm_net_num_params - number of float32 parameters (0 for NULL). */
+size_t helm_net_num_params(const helm_net* net);
+/* helm_net_set_params / get_params / get_grads - host float32 arrays of exactly num_params entries;
+ * synchronous.  set_params also refreshes the bfloat16 copy.  Errors: HELM_ERR_ARG on a size mismatch. */
+helm_status helm_net_set_params(helm_net* net, const float* host, size_t count);
+helm_status helm_net_get_params(helm_net* net, float* host, size_t count);
+helm_status helm_net_get_grads(helm_net* net, float* host, size_t count);
+/* helm_net_zero_grad - clear the accumulated parameter gradients (stream-ordered). */
+helm_status helm_net_zero_grad(helm_net* net, void* stream);
+/* helm_net_forward - y = N(x) for a batch: x bfloat16 device [B][5][Z][Y][X], y float32 device
+ * [B][2][Z][Y][X].  Keeps the activations for helm_net_backward.  Grows the workspace on demand. */
+helm_status helm_net_forward(helm_net* net, const void* x, float* y, int B, int Z, int Y, int X, void* stream);
+/* helm_net_backward - accumulates dL/dparams for dL/dy = gy (float32 device, shape of the last forward's y)
+ * into the gradients.  Needs a preceding helm_net_forward on the same net. */
+helm_status helm_net_backward(helm_net* net, const float* gy, void* stream);
+/* helm_net_adam - one Adam step (Kingma and Ba) with bias correction for step number `step` (>= 1). */
+helm_status helm_net_adam(helm_net* net, float lr, float beta1, float beta2, float eps, int step, void* stream);
+/* helm_net_mse - loss += 0.5 mean((y - t)^2) into the device double *loss (caller zeroes it), and
+ * gy = (y - t)/count; float32 device arrays of `count` entries. */
+helm_status helm_net_mse(const float* y, const float* t, float* gy, size_t count, double* loss, void* stream);
+/* helm_net_features - the 5 input channels x (bfloat16 device [5][nz][ny][nx]) for v and mv = M^-1 v
+ * (complex64 device) on the context's grid and k^2. */
+helm_status helm_net_features(helm_ctx* ctx, helm_net* net, const void* v, const void* mv, void* x, void* stream);
+/* helm_net_target - the training target t = (xs - xk - mv)/RMS(mv) (float32 device [2][nz][ny][nx]) for
+ * the pair v = b - A xk, A^-1 v = xs - xk, where xs solves A xs = b and mv = M^-1 v (complex64);
+ * xs, xk complex128 device fields of the context's grid. */
+helm_status helm_net_target(helm_ctx* ctx, helm_net* net, const void* xs, const void* xk, const void* mv, float* t,
+                            void* stream);
+/* helm_net_stats - six doubles: sum |v|^2 and sum |M^-1 v|^2 of the last correction, its |alpha|, the
+ * numbers of corrections dropped and applied since the net was created, and the sum over the applied ones
+ * of |v - A z|^2/|v - A M^-1 v|^2 (the residual reduction the correction bought).  Synchronous. */
+helm_status helm_net_stats(helm_net* net, double* host6);
+/* helm_attach_net - apply `net` after M^-1 in helm_apply_precond and helm_gmres_solve of this context
+ * (NULL detaches).  The context does not own the net.  Requires a flexible context and even nx, ny, nz
+ * (else HELM_ERR_ARG); sizes the net's workspace for one field of the grid. */
+helm_status helm_attach_net(helm_ctx* ctx, helm_net* net);
 
 /* helm_destroy - free the context and its device workspace (NULL is a no-op). */
 void helm_destroy(helm_ctx* ctx);

@@ -69,10 +69,11 @@ struct StencilParams {
 
 // ---- the context -----------------------------------------------------------------------------
 struct KrylovWork;
+struct helm_net;
 
 // Optional per-kernel timing: CUDA events recorded on the launch stream around every launch.
 enum ProfClass { PROF_STENCIL = 0, PROF_XPASS, PROF_YPASS, PROF_ZSOLVE, PROF_DOTS, PROF_UPDATE, PROF_SMALL,
-                 PROF_COMBINE, PROF_RESIDUAL, PROF_OTHER, PROF_NCLASS };
+                 PROF_COMBINE, PROF_RESIDUAL, PROF_OTHER, PROF_LEARNED, PROF_NCLASS };
 struct Prof {
     int enabled = 0;
     int used = 0;
@@ -125,6 +126,7 @@ struct helm_ctx {
     float2* tmp = nullptr;                  // one complex64 grid vector
     unsigned* status_d = nullptr;           // device status word
     KrylovWork* kw = nullptr;
+    helm_net* net = nullptr;                // attached learned correction (not owned)
     cudaStream_t last_stream = nullptr;
     Prof* prof = nullptr;
 };
@@ -133,6 +135,8 @@ struct helm_ctx {
 // stencil.cu
 helm_status launch_derived_fields(helm_ctx* c, cudaStream_t s);
 helm_status launch_stencil_f32(helm_ctx* c, const float2* x, float2* y, const double* sigma, int sidx, cudaStream_t s);
+helm_status launch_stencil_f32_cls(helm_ctx* c, const float2* x, float2* y, const double* sigma, int sidx, int cls,
+                                   cudaStream_t s);   // timed under profiling class cls
 helm_status launch_stencil_f64(helm_ctx* c, const double2* x, double2* y, cudaStream_t s);
 helm_status launch_residual(helm_ctx* c, const float4* x, const float4* F, float2* r, double* part, cudaStream_t s);
 helm_status launch_rhs(helm_ctx* c, const double2* f, double2* F, float4* fdf, cudaStream_t s);
@@ -156,6 +160,10 @@ helm_status launch_zsolve_gen(helm_ctx* c, const float2* in, float2* out, const 
 helm_status pfft_prepare(helm_ctx* c, cudaStream_t s);
 helm_status pfft_apply(helm_ctx* c, const float2* r, float2* z, const double* sigma, int sidx, cudaStream_t s);
 void pfft_release(helm_ctx* c);
+// learned.cu: the two halves of the learned correction around M^-1 (features and a copy of
+// v = sigma[sidx] r before, the correction of z after; r and z may alias)
+helm_status learned_pre(helm_ctx* c, const float2* r, const double* sigma, int sidx, cudaStream_t s);
+helm_status learned_post(helm_ctx* c, float2* z, cudaStream_t s);
 // precond.cu
 helm_status precond_apply(helm_ctx* c, const float2* r, float2* z, const double* sigma, int sidx, cudaStream_t s);
 helm_status precond_step(helm_ctx* c, int step, const float2* in, float2* out, cudaStream_t s);

@@ -65,7 +65,7 @@ helm_status precond_step(helm_ctx* c, int step, const float2* in, float2* out, c
     return HELM_ERR_ARG;
 }
 
-helm_status precond_apply(helm_ctx* c, const float2* r, float2* z, const double* sigma, int sidx, cudaStream_t s) {
+static helm_status precond_base(helm_ctx* c, const float2* r, float2* z, const double* sigma, int sidx, cudaStream_t s) {
     helm_status st;
     if (c->opt.precond == HELM_PRECOND_NONE) {
         prof_begin(c, s, PROF_OTHER);
@@ -86,4 +86,13 @@ helm_status precond_apply(helm_ctx* c, const float2* r, float2* z, const double*
     if ((st = launch_zsolve(c, z, z, s)) != HELM_OK) return st;
     if ((st = ypass(c, 1, z, c->tmp, s)) != HELM_OK) return st;
     return xpass(c, 1, c->tmp, z, hz2, nullptr, 0, s);
+}
+
+// M^-1 r, followed by the learned correction when a network is attached (flexible GMRES only)
+helm_status precond_apply(helm_ctx* c, const float2* r, float2* z, const double* sigma, int sidx, cudaStream_t s) {
+    helm_status st;
+    if (c->net && (st = learned_pre(c, r, sigma, sidx, s)) != HELM_OK) return st;
+    if ((st = precond_base(c, r, z, sigma, sidx, s)) != HELM_OK) return st;
+    if (c->net) return learned_post(c, z, s);
+    return HELM_OK;
 }

@@ -525,11 +525,16 @@ helm_status launch_derived_fields(helm_ctx* c, cudaStream_t s) {
 }
 
 helm_status launch_stencil_f32(helm_ctx* c, const float2* x, float2* y, const double* sigma, int sidx, cudaStream_t s) {
+    return launch_stencil_f32_cls(c, x, y, sigma, sidx, PROF_STENCIL, s);
+}
+
+helm_status launch_stencil_f32_cls(helm_ctx* c, const float2* x, float2* y, const double* sigma, int sidx, int cls,
+                                   cudaStream_t s) {
     SParams<P32> p = make_params<P32>(c);
     p.k2 = c->k2_f;
     for (int d = 0; d < 3; ++d) p.dk2[d] = c->dk2_f[d];
     p.G = c->G_f;
-    prof_begin(c, s, PROF_STENCIL);
+    prof_begin(c, s, cls);
     launch_stencil<P32, 0>(c, p, x, y, sigma, sidx, nullptr, nullptr, nullptr, s);
     prof_end(c, s);
     HELM_CUDA_TRY(cudaGetLastError());

@@ -68,6 +68,23 @@ _SIGS = {
     "helm_profile": (C.c_int, [C.c_void_p, C.c_int]),
     "helm_profile_read": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int]),
     "helm_destroy": (None, [C.c_void_p]),
+    "helm_net_create": (C.c_int, [C.c_int, C.c_ulonglong, C.POINTER(C.c_void_p)]),
+    "helm_net_destroy": (None, [C.c_void_p]),
+    "helm_net_num_params": (C.c_size_t, [C.c_void_p]),
+    "helm_net_set_params": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t]),
+    "helm_net_get_params": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t]),
+    "helm_net_get_grads": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t]),
+    "helm_net_zero_grad": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "helm_net_forward": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int,
+                                   C.c_void_p]),
+    "helm_net_backward": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "helm_net_adam": (C.c_int, [C.c_void_p, C.c_float, C.c_float, C.c_float, C.c_float, C.c_int, C.c_void_p]),
+    "helm_net_mse": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p]),
+    "helm_net_features": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "helm_net_stats": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "helm_net_target": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                  C.c_void_p]),
+    "helm_attach_net": (C.c_int, [C.c_void_p, C.c_void_p]),
     "helm_status_str": (C.c_char_p, [C.c_int]),
     "helm_version": (C.c_char_p, []),
 }
@@ -171,6 +188,95 @@ def helm_destroy(ctx):
         lib().helm_destroy(ctx)
 
 
+class Net:
+    """The learned-correction network (include/helm.h, helm_net_*); parameters live on the device."""
+
+    # per layer (name, Cout, Cin) for width c, in the library's parameter order
+    @staticmethod
+    def layers(width):
+        c = width
+        return [("c1", c, 5), ("c2", c, c), ("c3", 2 * c, c), ("c4", 2 * c, 2 * c), ("c5", c, 3 * c), ("c6", 2, c)]
+
+    def __init__(self, width=8, seed=0):
+        self.width = width
+        h = C.c_void_p()
+        _check(lib().helm_net_create(int(width), C.c_ulonglong(seed), C.byref(h)), "helm_net_create")
+        self.h = h
+        self.nparam = lib().helm_net_num_params(h)
+        self.step = 0
+
+    def close(self):
+        if self.h:
+            lib().helm_net_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def get_params(self):
+        a = np.zeros(self.nparam, np.float32)
+        _check(lib().helm_net_get_params(self.h, _ptr(a), a.size), "helm_net_get_params")
+        return a
+
+    def set_params(self, a):
+        a = np.ascontiguousarray(a, dtype=np.float32)
+        _check(lib().helm_net_set_params(self.h, _ptr(a), a.size), "helm_net_set_params")
+
+    def get_grads(self):
+        a = np.zeros(self.nparam, np.float32)
+        _check(lib().helm_net_get_grads(self.h, _ptr(a), a.size), "helm_net_get_grads")
+        return a
+
+    def unflatten(self, a):
+        """{name.w: [Cout][Cin][3][3][3], name.b: [Cout]} views of a flat parameter array."""
+        out, off = {}, 0
+        for name, co, ci in self.layers(self.width):
+            nw = co * ci * 27
+            out[name + ".w"] = a[off:off + nw].reshape(co, ci, 3, 3, 3)
+            off += nw
+            out[name + ".b"] = a[off:off + co]
+            off += co
+        return out
+
+    def flatten(self, d):
+        parts = []
+        for name, co, ci in self.layers(self.width):
+            parts += [np.asarray(d[name + ".w"], np.float32).ravel(), np.asarray(d[name + ".b"], np.float32).ravel()]
+        return np.concatenate(parts)
+
+    def zero_grad(self, stream=None):
+        _check(lib().helm_net_zero_grad(self.h, _stream(stream)), "helm_net_zero_grad")
+
+    def forward(self, x, stream=None):
+        """x: bfloat16 device tensor [B][5][Z][Y][X] -> float32 [B][2][Z][Y][X]."""
+        import torch
+        B, _, Z, Y, X = x.shape
+        y = torch.empty((B, 2, Z, Y, X), dtype=torch.float32, device=x.device)
+        _check(lib().helm_net_forward(self.h, _ptr(x), _ptr(y), B, Z, Y, X, _stream(stream)), "helm_net_forward")
+        return y
+
+    def backward(self, gy, stream=None):
+        _check(lib().helm_net_backward(self.h, _ptr(gy), _stream(stream)), "helm_net_backward")
+
+    def adam(self, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+        self.step += 1
+        _check(lib().helm_net_adam(self.h, lr, beta1, beta2, eps, self.step, _stream(stream)), "helm_net_adam")
+
+    def stats(self):
+        """[sum|v|^2, sum|M^-1 v|^2, |alpha|, dropped, applied, sum of residual-reduction ratios]."""
+        a = np.zeros(6, np.float64)
+        _check(lib().helm_net_stats(self.h, _ptr(a)), "helm_net_stats")
+        return a
+
+
+def helm_net_mse(y, t, gy, loss, stream=None):
+    """loss (device float64, 1 entry) += 0.5 mean((y-t)^2); gy = (y-t)/count."""
+    _check(lib().helm_net_mse(_ptr(y), _ptr(t), _ptr(gy), y.numel(), _ptr(loss), _stream(stream)), "helm_net_mse")
+
+
 class Solver:
     """One problem: grid, k^2 samples (complex128, host numpy or torch tensor), background k0, options."""
 
@@ -224,6 +330,27 @@ class Solver:
         y = self._empty(torch.complex64)
         helm_precond_step(self.ctx, step, x, y, stream)
         return y
+
+    def features(self, net, v, mv, stream=None):
+        """The net's 5 input channels (bfloat16 [5][nz][ny][nx]) for complex64 v and mv = M^-1 v."""
+        import torch
+        x = torch.empty((5,) + self.shape, dtype=torch.bfloat16, device=v.device)
+        _check(lib().helm_net_features(self.ctx, net.h, _ptr(v), _ptr(mv), _ptr(x), _stream(stream)),
+               "helm_net_features")
+        return x
+
+    def target(self, net, xs, xk, mv, stream=None):
+        """Training target (float32 [2][nz][ny][nx]) for v = b - A xk with A^-1 v = xs - xk, mv = M^-1 v."""
+        import torch
+        t = torch.empty((2,) + self.shape, dtype=torch.float32, device=mv.device)
+        _check(lib().helm_net_target(self.ctx, net.h, _ptr(xs), _ptr(xk), _ptr(mv), _ptr(t), _stream(stream)),
+               "helm_net_target")
+        return t
+
+    def attach(self, net):
+        """Apply `net` after M^-1 (flexible contexts); None detaches.  The caller keeps `net` alive."""
+        _check(lib().helm_attach_net(self.ctx, net.h if net is not None else None), "helm_attach_net")
+        self.net = net
 
     def residual(self, b, x, stream=None):
         """(||b - A x||_2, ||b - A x||_inf) with complex128 device b, x."""
