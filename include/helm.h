@@ -139,6 +139,27 @@ helm_status helm_get_eig(helm_ctx* ctx, int axis, void* D, void* V, void* Vinv);
  * residual.  Synchronises `stream`. */
 helm_status helm_gmres_solve(helm_ctx* ctx, const void* b, void* x, helm_solve_info* info, void* stream);
 
+/* helm_gmres_solve_batched - nrhs right-hand sides for each of nprob problems, solved together (an
+ * extension: the paper solves one problem at a time).
+ *   ctxs   nprob distinct contexts (any sizes, orders and options; EigT or no preconditioner; no attached net)
+ *   b[p]   complex128 device array [nrhs][nz][ny][nx] of problem p
+ *   x[p]   complex128 device array of the same shape: x^0 on entry, the iterates on exit
+ *   infos  nprob*nrhs entries (problem-major), may be NULL; seconds = wall time of the whole batch
+ * Each (problem, right-hand side) pair runs the same restarted (F)GMRES as helm_gmres_solve with its own
+ * Krylov workspace; the pairs run concurrently as branches of one CUDA graph whose loops and branches
+ * (iterations, restarts, convergence) are decided on the device, so the host launches the graph once and
+ * synchronises once per group of pairs that fits in 60% of the free device memory.
+ * Returns HELM_OK when every pair converged, else the status of the first pair that did not (each pair's
+ * status is in infos).  Errors: HELM_ERR_ARG (NULL, host pointers, a context twice), HELM_ERR_UNSUPPORTED
+ * (PFFT context or attached net), HELM_ERR_NOMEM, HELM_ERR_CUDA.  Synchronises `stream`. */
+helm_status helm_gmres_solve_batched(helm_ctx* const* ctxs, int nprob, const void* const* b, void* const* x, int nrhs,
+                                     helm_solve_info* infos, void* stream);
+
+/* helm_autotune - time the candidate CTA counts of the Arnoldi kernels (inner products, update, combine)
+ * on this context's grid and keep the fastest for its later solves; *nb_out (may be NULL) receives it.
+ * Results are cached per grid size for the process.  Uses temporary device memory; synchronous. */
+helm_status helm_autotune(helm_ctx* ctx, int* nb_out, void* stream);
+
 /* helm_residual - r = b - A x and its norms, the rel-res numerator of Sec. 5.1, computed with about 44
  * significant bits (double-float arithmetic on the FP32 pipes) from complex128 b and x.
  *   b, x   complex128 device buffers;  r  complex64 device output (may be NULL);
@@ -235,6 +256,10 @@ void helm_destroy(helm_ctx* ctx);
 
 /* helm_status_str - static English text of a status code. */
 const char* helm_status_str(int status);
+
+/* helm_last_error - text of the last CUDA failure that made a call on this host thread return
+ * HELM_ERR_CUDA or HELM_ERR_NOMEM ("" if none); static storage per thread. */
+const char* helm_last_error(void);
 
 /* helm_version - library version string. */
 const char* helm_version(void);

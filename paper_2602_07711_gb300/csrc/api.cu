@@ -5,12 +5,17 @@
 #include <cstring>
 #include <vector>
 
+// text of the last CUDA failure seen on this host thread (helm_last_error)
+static thread_local char g_last_error[512] = "";
+
 helm_status helm_fail_cuda(cudaError_t e, const char* what) {
-    (void)what;
+    snprintf(g_last_error, sizeof(g_last_error), "%s: %s (%d)", what ? what : "?", cudaGetErrorString(e), (int)e);
     if (e == cudaErrorMemoryAllocation) { cudaGetLastError(); return HELM_ERR_NOMEM; }
     cudaGetLastError();
     return HELM_ERR_CUDA;
 }
+
+extern "C" const char* helm_last_error(void) { return g_last_error; }
 
 namespace {
 

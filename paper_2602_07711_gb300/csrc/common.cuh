@@ -127,6 +127,7 @@ struct helm_ctx {
     unsigned* status_d = nullptr;           // device status word
     KrylovWork* kw = nullptr;
     helm_net* net = nullptr;                // attached learned correction (not owned)
+    int tune_nb = 0;                        // CTAs of the Arnoldi kernels chosen by helm_autotune (0 = default)
     cudaStream_t last_stream = nullptr;
     Prof* prof = nullptr;
 };

@@ -11,8 +11,12 @@
 // which decides convergence and seeds the next cycle.
 #include "common.cuh"
 #include "dfloat.cuh"
+#include <algorithm>
 #include <chrono>
+#include <cstdio>
 #include <cmath>
+#include <map>
+#include <mutex>
 #include <vector>
 
 int residual_ctas(const helm_ctx* c);
@@ -241,8 +245,9 @@ __global__ void givens_kernel(const double2* __restrict__ part, int NB, int ld, 
 
 // y = R^-1 g (k x k upper triangular part of the rotated H)
 __global__ void lsq_kernel(const double2* __restrict__ H, const double2* __restrict__ g, int k, int m, double2* y,
-                           Ctrl* ctrl) {
+                           Ctrl* ctrl, const int* __restrict__ kdev) {
     if (threadIdx.x != 0) return;
+    if (kdev) k = *kdev;
     for (int i = k - 1; i >= 0; --i) {
         double2 s = g[i];
         for (int q = i + 1; q < k; ++q) s = csub(s, cmul(H[(size_t)q * (m + 1) + i], y[q]));
@@ -253,8 +258,10 @@ __global__ void lsq_kernel(const double2* __restrict__ H, const double2* __restr
 
 // flexible: x += sum_i y_i Z_i, in double-float (y_i split from FP64, products exact via FMA)
 __global__ void __launch_bounds__(NT) combine_flex_kernel(const float2* __restrict__ Z, size_t npts, int k,
-                                                         const double2* __restrict__ y, float4* __restrict__ x) {
+                                                         const double2* __restrict__ y, float4* __restrict__ x,
+                                                         const int* __restrict__ kdev) {
     __shared__ cdf ys[64];
+    if (kdev) k = *kdev;
     for (int i = threadIdx.x; i < k; i += NT) ys[i] = cdf{df_from_double(y[i].x), df_from_double(y[i].y)};
     __syncthreads();
     for (size_t id = blockIdx.x * (size_t)NT + threadIdx.x; id < npts; id += (size_t)gridDim.x * NT) {
@@ -267,8 +274,9 @@ __global__ void __launch_bounds__(NT) combine_flex_kernel(const float2* __restri
 // right-preconditioned: u = sum_i (y_i sigma_i) V_i  (complex64; u is a complex64 preconditioner input)
 __global__ void __launch_bounds__(NT) combine_v_kernel(const float2* __restrict__ V, size_t npts, int k,
                                                       const double2* __restrict__ y, const double* __restrict__ sigma,
-                                                      float2* __restrict__ u) {
+                                                      float2* __restrict__ u, const int* __restrict__ kdev) {
     __shared__ float2 ys[64];
+    if (kdev) k = *kdev;
     for (int i = threadIdx.x; i < k; i += NT) {
         const double2 v = cscale(y[i], sigma[i]);
         ys[i] = make_float2((float)v.x, (float)v.y);
@@ -365,21 +373,21 @@ bool is_device_ptr(const void* p) {
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
-helm_status ensure_work(helm_ctx* c) {
-    const int m = c->opt.restart, flex = c->opt.flexible;
-    KrylovWork* k = c->kw;
-    if (k && k->m == m && k->flexible == flex) return HELM_OK;
-    krylov_free(c);
-    k = new KrylovWork();
-    c->kw = k;
+void free_work(KrylovWork* k) {
+    cudaFree(k->V); cudaFree(k->Z); cudaFree(k->sigma); cudaFree(k->H); cudaFree(k->cs); cudaFree(k->sn);
+    cudaFree(k->g); cudaFree(k->y); cudaFree(k->part); cudaFree(k->rpart); cudaFree(k->coef); cudaFree(k->ctrl_d);
+    cudaFreeHost(k->ctrl_h); cudaFree(k->xbuf); cudaFree(k->bbuf); cudaFree(k->xdf); cudaFree(k->Fdf);
+    cudaFree(k->nzflag);
+}
+
+// Krylov workspace of restart length m for the context's grid; NB = CTAs of the Arnoldi kernels.
+helm_status alloc_work(helm_ctx* c, KrylovWork* k, int m, int flex, int NB) {
     k->m = m; k->flexible = flex; k->npts = c->npts;
-    int sms = 0;
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
-    k->NB = 4 * (sms > 0 ? sms : 148);
+    k->NB = NB;
     k->nres = residual_ctas(c);
     const size_t vb = c->npts * sizeof(float2);
-    if (cudaMalloc(&k->V, vb * (m + 1)) != cudaSuccess) return HELM_ERR_NOMEM;
-    if (cudaMalloc(&k->Z, vb * (flex ? m : 1)) != cudaSuccess) return HELM_ERR_NOMEM;
+    if (cudaMalloc(&k->V, vb * (m + 1)) != cudaSuccess) { cudaGetLastError(); return HELM_ERR_NOMEM; }
+    if (cudaMalloc(&k->Z, vb * (flex ? m : 1)) != cudaSuccess) { cudaGetLastError(); return HELM_ERR_NOMEM; }
     HELM_CUDA_TRY(cudaMalloc(&k->sigma, sizeof(double) * (m + 1)));
     HELM_CUDA_TRY(cudaMalloc(&k->H, sizeof(double2) * (m + 1) * m));
     HELM_CUDA_TRY(cudaMalloc(&k->cs, sizeof(double) * m));
@@ -391,12 +399,29 @@ helm_status ensure_work(helm_ctx* c) {
     HELM_CUDA_TRY(cudaMalloc(&k->coef, sizeof(float2) * (m + 1)));
     HELM_CUDA_TRY(cudaMalloc(&k->ctrl_d, sizeof(Ctrl)));
     HELM_CUDA_TRY(cudaMallocHost(&k->ctrl_h, sizeof(Ctrl)));
-    if (cudaMalloc(&k->xdf, c->npts * sizeof(float4)) != cudaSuccess) return HELM_ERR_NOMEM;
-    if (cudaMalloc(&k->Fdf, c->npts * sizeof(float4)) != cudaSuccess) return HELM_ERR_NOMEM;
+    if (cudaMalloc(&k->xdf, c->npts * sizeof(float4)) != cudaSuccess) { cudaGetLastError(); return HELM_ERR_NOMEM; }
+    if (cudaMalloc(&k->Fdf, c->npts * sizeof(float4)) != cudaSuccess) { cudaGetLastError(); return HELM_ERR_NOMEM; }
     HELM_CUDA_TRY(cudaMalloc(&k->nzflag, sizeof(unsigned)));
     HELM_CUDA_TRY(cudaMemset(k->H, 0, sizeof(double2) * (m + 1) * m));
     HELM_CUDA_TRY(cudaMemset(k->ctrl_d, 0, sizeof(Ctrl)));
     return HELM_OK;
+}
+
+int default_nb(const helm_ctx* c) {
+    if (c->tune_nb > 0) return c->tune_nb;
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
+    return 4 * (sms > 0 ? sms : 148);
+}
+
+helm_status ensure_work(helm_ctx* c) {
+    const int m = c->opt.restart, flex = c->opt.flexible;
+    KrylovWork* k = c->kw;
+    if (k && k->m == m && k->flexible == flex && k->NB == default_nb(c)) return HELM_OK;
+    krylov_free(c);
+    k = new KrylovWork();
+    c->kw = k;
+    return alloc_work(c, k, m, flex, default_nb(c));
 }
 
 helm_status read_ctrl(KrylovWork* k, cudaStream_t s) {
@@ -428,10 +453,7 @@ helm_status true_residual(helm_ctx* c, bool xzero, int first, cudaStream_t s) {
 void krylov_free(helm_ctx* c) {
     KrylovWork* k = c->kw;
     if (!k) return;
-    cudaFree(k->V); cudaFree(k->Z); cudaFree(k->sigma); cudaFree(k->H); cudaFree(k->cs); cudaFree(k->sn);
-    cudaFree(k->g); cudaFree(k->y); cudaFree(k->part); cudaFree(k->rpart); cudaFree(k->coef); cudaFree(k->ctrl_d);
-    cudaFreeHost(k->ctrl_h); cudaFree(k->xbuf); cudaFree(k->bbuf); cudaFree(k->xdf); cudaFree(k->Fdf);
-    cudaFree(k->nzflag);
+    free_work(k);
     delete k;
     c->kw = nullptr;
 }
@@ -514,16 +536,16 @@ helm_status gmres_run(helm_ctx* c, const double2* b_in, double2* x_in, helm_solv
             }
             if (k->ctrl_h->flags & HELM_DEV_NAN) { result = HELM_ERR_NAN; break; }
             prof_begin(c, s, PROF_SMALL);
-            lsq_kernel<<<1, 32, 0, s>>>(k->H, k->g, kk, m, k->y, k->ctrl_d);
+            lsq_kernel<<<1, 32, 0, s>>>(k->H, k->g, kk, m, k->y, k->ctrl_d, nullptr);
             prof_end(c, s);
             if (flex) {
                 prof_begin(c, s, PROF_COMBINE);
-                combine_flex_kernel<<<NB, NT, 0, s>>>(k->Z, npts, kk, k->y, k->xdf);
+                combine_flex_kernel<<<NB, NT, 0, s>>>(k->Z, npts, kk, k->y, k->xdf, nullptr);
                 prof_end(c, s);
             } else {
                 float2* u = k->V + (size_t)kk * npts;   // V_kk is not needed by the update
                 prof_begin(c, s, PROF_COMBINE);
-                combine_v_kernel<<<NB, NT, 0, s>>>(k->V, npts, kk, k->y, k->sigma, u);
+                combine_v_kernel<<<NB, NT, 0, s>>>(k->V, npts, kk, k->y, k->sigma, u, nullptr);
                 prof_end(c, s);
                 if ((st = precond_apply(c, u, u, nullptr, 0, s)) != HELM_OK) return st;
                 prof_begin(c, s, PROF_COMBINE);
@@ -531,6 +553,7 @@ helm_status gmres_run(helm_ctx* c, const double2* b_in, double2* x_in, helm_solv
                 prof_end(c, s);
             }
             HELM_CUDA_TRY(cudaGetLastError());
+            if (restarts < 16) cyc[restarts] = kk;
             ++restarts;
             if ((st = true_residual(c, false, 0, s)) != HELM_OK) return st;
             if (breakdown && k->ctrl_h->beta / beta0 > c->opt.rtol) { result = HELM_ERR_BREAKDOWN; break; }
@@ -575,4 +598,468 @@ helm_status residual_run(helm_ctx* c, const double2* b, const double2* x, float2
     if (nrm2) *nrm2 = sqrt(t);
     if (nrmi) *nrmi = m;
     return HELM_OK;
+}
+
+// ---- launch-shape autotuning ------------------------------------------------------------------
+// The Arnoldi kernels (inner products, update, solution combine) are grid-stride loops whose CTA count
+// trades latency hiding against the cost of the per-CTA partial sums; the best count depends on the
+// grid size.  helm_autotune times the candidates on the context's own grid and keeps the fastest.
+
+namespace {
+
+struct TuneKey {
+    int nx, ny, nz;
+    bool operator<(const TuneKey& o) const {
+        return nx != o.nx ? nx < o.nx : (ny != o.ny ? ny < o.ny : nz < o.nz);
+    }
+};
+
+std::mutex g_tune_mu;
+std::map<TuneKey, int> g_tune_cache;
+
+}  // namespace
+
+extern "C" helm_status helm_autotune(helm_ctx* c, int* nb_out, void* stream) {
+    if (!c) return HELM_ERR_ARG;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune_cache.find(TuneKey{c->nx, c->ny, c->nz});
+        if (it != g_tune_cache.end()) {
+            c->tune_nb = it->second;
+            if (nb_out) *nb_out = c->tune_nb;
+            return HELM_OK;
+        }
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    int sms = 0;
+    HELM_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device));
+    if (sms <= 0) sms = 148;
+    const size_t npts = c->npts;
+    const int nv = 8, ld = nv + 1;
+    const int cand[] = {sms / 2, sms, 2 * sms, 4 * sms, 8 * sms};
+    const int maxnb = (int)std::min<size_t>((npts / 2 + NT - 1) / NT, (size_t)16 * sms);
+    float2* V = nullptr;
+    double2* part = nullptr;
+    float2* coef = nullptr;
+    if (cudaMalloc(&V, npts * sizeof(float2) * (nv + 1)) != cudaSuccess) { cudaGetLastError(); return HELM_ERR_NOMEM; }
+    if (cudaMalloc(&part, sizeof(double2) * ld * 16 * (size_t)sms) != cudaSuccess ||
+        cudaMalloc(&coef, sizeof(float2) * ld) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(V); cudaFree(part);
+        return HELM_ERR_NOMEM;
+    }
+    cudaMemsetAsync(V, 0, npts * sizeof(float2) * (nv + 1), s);
+    cudaMemsetAsync(coef, 0, sizeof(float2) * ld, s);
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    int best = 4 * sms;
+    float best_ms = 1e30f;
+    float2* w = V + (size_t)nv * npts;
+    for (int nb : cand) {
+        nb = std::max(1, std::min(nb, maxnb));
+        float tmin = 1e30f;
+        for (int rep = 0; rep < 4; ++rep) {
+            cudaEventRecord(e0, s);
+            dots_kernel<<<nb, NT, 0, s>>>(V, npts, nv, w, part, ld);
+            update_kernel<<<nb, NT, 0, s>>>(V, npts, nv, coef, w, part, ld);
+            cudaEventRecord(e1, s);
+            cudaEventSynchronize(e1);
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (rep > 0) tmin = std::min(tmin, ms);   // the first run is a warm-up
+        }
+        if (tmin < best_ms * 0.97f) { best_ms = tmin; best = nb; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(V); cudaFree(part); cudaFree(coef);
+    HELM_CUDA_TRY(cudaGetLastError());
+    c->tune_nb = best;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tune_cache[TuneKey{c->nx, c->ny, c->nz}] = best;
+    }
+    if (nb_out) *nb_out = best;
+    return HELM_OK;
+}
+
+// ---- batched solves ---------------------------------------------------------------------------
+// Many problems (contexts of any size and options) times nrhs right-hand sides each, solved together:
+// every (problem, right-hand side) pair is a lane with its own Krylov workspace and preconditioner
+// scratch.  One restart cycle of every lane is one CUDA graph,
+//   for each lane (independent branches):  begin; IF(go) iteration 0; ...; IF(go) iteration m-1; IF(cycle) end
+// whose conditions are set on the device (convergence estimate, iteration limit, breakdown; a finished lane
+// skips everything), so a launch costs the host one graph launch and one synchronisation per restart cycle
+// for the whole batch.  The host relaunches the graph while any lane wants another cycle (a device flag per
+// lane); there is no device-side loop, so a lane can never spin.  Lanes are grouped so that a group's
+// workspace fits in device memory.
+
+struct LaneCtl {
+    int active, kk, its, restarts, brk, cycles, max_iter, m;
+    double rtol;
+    int cyc[16];
+};
+
+namespace {
+
+// would the lane run another cycle?  (the same test opens each cycle)
+__device__ bool lane_wants_cycle(const Ctrl* ctrl, const LaneCtl* L) {
+    if (!L->active) return false;
+    if (!(ctrl->beta0 > 0)) return false;
+    if (ctrl->beta / ctrl->beta0 <= L->rtol) return false;
+    if (ctrl->flags & HELM_DEV_NAN) return false;
+    if (L->its >= L->max_iter || L->brk || L->cycles > L->max_iter) return false;
+    return true;
+}
+
+__global__ void lane_begin_kernel(const Ctrl* __restrict__ ctrl, LaneCtl* L, int* more, cudaGraphConditionalHandle hit,
+                                  cudaGraphConditionalHandle hcyc) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const bool go = lane_wants_cycle(ctrl, L);
+    if (!go) L->active = 0;
+    else L->cycles += 1;
+    L->kk = 0;
+    *more = go ? 1 : 0;
+    cudaGraphSetConditional(hit, go ? 1u : 0u);
+    cudaGraphSetConditional(hcyc, go ? 1u : 0u);
+}
+
+// end of iteration j: opens iteration j+1 (its own handle hnext; has_next = 0 after the last one)
+__global__ void lane_iter_end_kernel(const Ctrl* __restrict__ ctrl, LaneCtl* L, int j, cudaGraphConditionalHandle hnext,
+                                     int has_next) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    L->its += 1;
+    L->kk = j + 1;
+    bool go = !(ctrl->flags & HELM_DEV_NAN) && ctrl->est > L->rtol && L->its < L->max_iter && j + 1 < L->m;
+    if (!(ctrl->hnext > 0)) { go = false; L->brk = 1; }
+    if (has_next) cudaGraphSetConditional(hnext, go ? 1u : 0u);
+}
+
+__global__ void lane_cycle_end_kernel(const Ctrl* __restrict__ ctrl, LaneCtl* L, int* more) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    if (L->restarts < 16) L->cyc[L->restarts] = L->kk;
+    L->restarts += 1;
+    *more = lane_wants_cycle(ctrl, L) ? 1 : 0;
+}
+
+struct Lane {
+    helm_ctx* c = nullptr;
+    double2* b = nullptr;
+    double2* x = nullptr;
+    KrylovWork w;
+    float2* tmp = nullptr;
+    LaneCtl* L_d = nullptr;
+    int* more = nullptr;       // device flag: the lane wants another cycle
+    LaneCtl L_h{};
+    Ctrl ctrl_copy{};
+    int index = 0;
+};
+
+size_t lane_bytes(const helm_ctx* c) {
+    const int m = c->opt.restart;
+    return c->npts * (sizeof(float2) * ((size_t)m + 1 + (c->opt.flexible ? m : 1) + 1) + 2 * sizeof(float4));
+}
+
+// the preconditioner of a lane, on the lane's own scratch vector (the context's is shared by all its lanes)
+helm_status lane_precond(Lane& ln, const float2* r, float2* z, const double* sigma, int sidx, cudaStream_t s) {
+    float2* save = ln.c->tmp;
+    ln.c->tmp = ln.tmp;
+    helm_status st = precond_apply(ln.c, r, z, sigma, sidx, s);
+    ln.c->tmp = save;
+    return st;
+}
+
+helm_status lane_iteration(Lane& ln, int j, cudaGraphConditionalHandle hnext, int has_next, cudaStream_t s) {
+    helm_ctx* c = ln.c;
+    KrylovWork* k = &ln.w;
+    const size_t npts = c->npts;
+    const int m = k->m, ld = m + 1, NB = k->NB;
+    float2* vj = k->V + (size_t)j * npts;
+    float2* w = k->V + (size_t)(j + 1) * npts;
+    float2* z = k->flexible ? k->Z + (size_t)j * npts : k->Z;
+    helm_status st;
+    if ((st = lane_precond(ln, vj, z, k->sigma, j, s)) != HELM_OK) return st;
+    if ((st = launch_stencil_f32(c, z, w, nullptr, 0, s)) != HELM_OK) return st;
+    const int passes = c->opt.reorth ? 2 : 1;
+    for (int pass = 0; pass < passes; ++pass) {
+        dots_kernel<<<NB, NT, 0, s>>>(k->V, npts, j + 1, w, k->part, ld);
+        reduce_h_kernel<<<1, 256, 0, s>>>(k->part, NB, ld, j + 1, k->sigma, k->H + (size_t)j * (m + 1), k->coef,
+                                          pass == 0);
+        update_kernel<<<NB, NT, 0, s>>>(k->V, npts, j + 1, k->coef, w, k->part, ld);
+    }
+    givens_kernel<<<1, 256, 0, s>>>(k->part, NB, ld, j, m, k->H, k->cs, k->sn, k->g, k->sigma, k->ctrl_d);
+    lane_iter_end_kernel<<<1, 32, 0, s>>>(k->ctrl_d, ln.L_d, j, hnext, has_next);
+    HELM_CUDA_TRY(cudaGetLastError());
+    return HELM_OK;
+}
+
+helm_status lane_cycle_end(Lane& ln, cudaStream_t s) {
+    helm_ctx* c = ln.c;
+    KrylovWork* k = &ln.w;
+    const size_t npts = c->npts;
+    const int m = k->m, NB = k->NB;
+    const int* kk = &ln.L_d->kk;
+    helm_status st;
+    lsq_kernel<<<1, 32, 0, s>>>(k->H, k->g, 0, m, k->y, k->ctrl_d, kk);
+    if (k->flexible) {
+        combine_flex_kernel<<<NB, NT, 0, s>>>(k->Z, npts, 0, k->y, k->xdf, kk);
+    } else {
+        combine_v_kernel<<<NB, NT, 0, s>>>(k->V, npts, 0, k->y, k->sigma, k->Z, kk);
+        if ((st = lane_precond(ln, k->Z, k->Z, nullptr, 0, s)) != HELM_OK) return st;
+        add_kernel<<<NB, NT, 0, s>>>(k->Z, k->xdf, npts);
+    }
+    HELM_CUDA_TRY(cudaGetLastError());
+    if ((st = launch_residual(c, k->xdf, k->Fdf, k->V, k->rpart, s)) != HELM_OK) return st;
+    resnorm_kernel<<<1, 256, 0, s>>>(k->rpart, k->nres, k->sigma, k->g, m, k->ctrl_d, 0);
+    lane_cycle_end_kernel<<<1, 32, 0, s>>>(k->ctrl_d, ln.L_d, ln.more);
+    HELM_CUDA_TRY(cudaGetLastError());
+    return HELM_OK;
+}
+
+// Capture what `enqueue` launches on s into graph g after the nodes deps.
+template <typename F>
+helm_status capture_into(cudaGraph_t g, const cudaGraphNode_t* deps, size_t nd, cudaStream_t s, F enqueue) {
+    HELM_CUDA_TRY(cudaStreamBeginCaptureToGraph(s, g, deps, nullptr, nd, cudaStreamCaptureModeRelaxed));
+    helm_status st = enqueue();
+    cudaGraph_t out = nullptr;
+    cudaError_t e = cudaStreamEndCapture(s, &out);
+    if (st != HELM_OK) return st;
+    HELM_CUDA_TRY(e);
+    return HELM_OK;
+}
+
+helm_status add_cond(cudaGraph_t g, const cudaGraphNode_t* deps, size_t nd, cudaGraphConditionalHandle h,
+                     cudaGraphConditionalNodeType type, cudaGraphNode_t* node, cudaGraph_t* body) {
+    cudaGraphNodeParams p = {};
+    p.type = cudaGraphNodeTypeConditional;
+    p.conditional.handle = h;
+    p.conditional.type = type;
+    p.conditional.size = 1;
+    const cudaError_t e = cudaGraphAddNode(node, g, deps, nullptr, nd, &p);
+    if (e != cudaSuccess) {
+        char what[96];
+        snprintf(what, sizeof(what), "cudaGraphAddNode(conditional type %d, %zu deps)", (int)type, nd);
+        return helm_fail_cuda(e, what);
+    }
+    *body = p.conditional.phGraph_out[0];
+    return HELM_OK;
+}
+
+// the nodes of one lane's restart cycle: begin; IF iterations; IF cycle end.  Every conditional node has its
+// own handle (default 0 at each launch); the begin kernel opens iteration 0 and the cycle end, iteration j
+// opens iteration j+1.
+helm_status build_lane(cudaGraph_t G, Lane& ln, cudaStream_t s) {
+    const int m = ln.w.m;
+    std::vector<cudaGraphConditionalHandle> hit(m);
+    cudaGraphConditionalHandle hcyc;
+    for (int j = 0; j < m; ++j) HELM_CUDA_TRY(cudaGraphConditionalHandleCreate(&hit[j], G, 0, cudaGraphCondAssignDefault));
+    HELM_CUDA_TRY(cudaGraphConditionalHandleCreate(&hcyc, G, 0, cudaGraphCondAssignDefault));
+    helm_status st;
+    cudaGraphNode_t begin;
+    {
+        cudaKernelNodeParams kp = {};
+        const Ctrl* ctrl = ln.w.ctrl_d;
+        LaneCtl* L = ln.L_d;
+        int* more = ln.more;
+        cudaGraphConditionalHandle h0 = hit[0];
+        void* args[] = {(void*)&ctrl, (void*)&L, (void*)&more, (void*)&h0, (void*)&hcyc};
+        kp.func = (void*)lane_begin_kernel;
+        kp.gridDim = dim3(1);
+        kp.blockDim = dim3(32);
+        kp.kernelParams = args;
+        HELM_CUDA_TRY(cudaGraphAddKernelNode(&begin, G, nullptr, 0, &kp));
+    }
+    cudaGraphNode_t prev = begin;
+    for (int j = 0; j < m; ++j) {
+        cudaGraphNode_t node;
+        cudaGraph_t ib;
+        if ((st = add_cond(G, &prev, 1, hit[j], cudaGraphCondTypeIf, &node, &ib)) != HELM_OK) return st;
+        const cudaGraphConditionalHandle hn = j + 1 < m ? hit[j + 1] : hit[j];
+        const int has_next = j + 1 < m ? 1 : 0;
+        if ((st = capture_into(ib, nullptr, 0, s, [&]() { return lane_iteration(ln, j, hn, has_next, s); })) != HELM_OK)
+            return st;
+        prev = node;
+    }
+    cudaGraphNode_t cnode;
+    cudaGraph_t cb;
+    if ((st = add_cond(G, &prev, 1, hcyc, cudaGraphCondTypeIf, &cnode, &cb)) != HELM_OK) return st;
+    return capture_into(cb, nullptr, 0, s, [&]() { return lane_cycle_end(ln, s); });
+}
+
+void free_lane(Lane& ln) {
+    free_work(&ln.w);
+    ln.w = KrylovWork();
+    cudaFree(ln.tmp);
+    cudaFree(ln.L_d);
+    ln.tmp = nullptr;
+    ln.L_d = nullptr;
+    ln.more = nullptr;
+}
+
+helm_status run_group(std::vector<Lane*>& lanes, cudaStream_t s) {
+    helm_status st;
+    // workspace, then the double-float copies of b and x0 and the x0 = 0 flags
+    for (Lane* ln : lanes) {
+        helm_ctx* c = ln->c;
+        if ((st = alloc_work(c, &ln->w, c->opt.restart, c->opt.flexible, default_nb(c))) != HELM_OK) return st;
+        if (cudaMalloc(&ln->tmp, c->npts * sizeof(float2)) != cudaSuccess) { cudaGetLastError(); return HELM_ERR_NOMEM; }
+        HELM_CUDA_TRY(cudaMalloc(&ln->L_d, sizeof(LaneCtl)));
+        HELM_CUDA_TRY(cudaMemsetAsync(ln->w.nzflag, 0, sizeof(unsigned), s));
+        to_df_kernel<<<ln->w.NB, NT, 0, s>>>(ln->b, ln->w.Fdf, c->npts, nullptr);
+        to_df_kernel<<<ln->w.NB, NT, 0, s>>>(ln->x, ln->w.xdf, c->npts, ln->w.nzflag);
+        HELM_CUDA_TRY(cudaGetLastError());
+    }
+    std::vector<unsigned> nz(lanes.size(), 0);
+    for (size_t i = 0; i < lanes.size(); ++i)
+        HELM_CUDA_TRY(cudaMemcpyAsync(&nz[i], lanes[i]->w.nzflag, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+    HELM_CUDA_TRY(cudaStreamSynchronize(s));
+    // initial true residuals and the lane controls
+    for (size_t i = 0; i < lanes.size(); ++i) {
+        Lane* ln = lanes[i];
+        helm_ctx* c = ln->c;
+        KrylovWork* k = &ln->w;
+        if (nz[i]) {
+            if ((st = launch_residual(c, k->xdf, k->Fdf, k->V, k->rpart, s)) != HELM_OK) return st;
+        } else {
+            residual_zero_kernel<<<k->nres, NT, 0, s>>>(k->Fdf, k->V, c->npts, k->rpart);
+        }
+        resnorm_kernel<<<1, 256, 0, s>>>(k->rpart, k->nres, k->sigma, k->g, k->m, k->ctrl_d, 1);
+        LaneCtl L{};
+        L.active = 1;
+        L.max_iter = c->opt.max_iter;
+        L.m = c->opt.restart;
+        L.rtol = c->opt.rtol;
+        ln->L_h = L;
+        HELM_CUDA_TRY(cudaMemcpyAsync(ln->L_d, &ln->L_h, sizeof(LaneCtl), cudaMemcpyHostToDevice, s));
+        HELM_CUDA_TRY(cudaGetLastError());
+    }
+    HELM_CUDA_TRY(cudaStreamSynchronize(s));
+    // one graph for the group
+    int* flags = nullptr;
+    HELM_CUDA_TRY(cudaMalloc(&flags, sizeof(int) * lanes.size()));
+    for (size_t i = 0; i < lanes.size(); ++i) lanes[i]->more = flags + i;
+    cudaStream_t cs = nullptr;
+    HELM_CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    cudaGraph_t G = nullptr;
+    cudaGraphExec_t X = nullptr;
+    st = HELM_OK;
+    cudaError_t e = cudaGraphCreate(&G, 0);
+    if (e != cudaSuccess) st = helm_fail_cuda(e, "cudaGraphCreate");
+    for (size_t i = 0; st == HELM_OK && i < lanes.size(); ++i) st = build_lane(G, *lanes[i], cs);
+    if (st == HELM_OK && (e = cudaGraphInstantiate(&X, G, 0)) != cudaSuccess) st = helm_fail_cuda(e, "cudaGraphInstantiate");
+    // one launch per restart cycle while any lane wants another (bounded by the largest iteration limit)
+    int max_cycles = 1;
+    for (Lane* ln : lanes) max_cycles = std::max(max_cycles, ln->c->opt.max_iter + 1);
+    std::vector<int> more(lanes.size(), 1);
+    for (int cyc = 0; st == HELM_OK && cyc <= max_cycles; ++cyc) {
+        if ((e = cudaGraphLaunch(X, s)) != cudaSuccess) { st = helm_fail_cuda(e, "cudaGraphLaunch"); break; }
+        if ((e = cudaMemcpyAsync(more.data(), flags, sizeof(int) * lanes.size(), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+            (e = cudaStreamSynchronize(s)) != cudaSuccess) { st = helm_fail_cuda(e, "batched cycle"); break; }
+        bool any = false;
+        for (int v : more) any = any || v;
+        if (!any) break;
+    }
+    if (X) cudaGraphExecDestroy(X);
+    if (G) cudaGraphDestroy(G);
+    cudaStreamDestroy(cs);
+    cudaFree(flags);
+    for (Lane* ln : lanes) ln->more = nullptr;
+    if (st != HELM_OK) return st;
+    // solutions and controls back
+    for (Lane* ln : lanes) {
+        from_df_kernel<<<ln->w.NB, NT, 0, s>>>(ln->w.xdf, ln->x, ln->c->npts);
+        HELM_CUDA_TRY(cudaMemcpyAsync(ln->w.ctrl_h, ln->w.ctrl_d, sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
+        HELM_CUDA_TRY(cudaMemcpyAsync(&ln->L_h, ln->L_d, sizeof(LaneCtl), cudaMemcpyDeviceToHost, s));
+    }
+    HELM_CUDA_TRY(cudaStreamSynchronize(s));
+    for (Lane* ln : lanes) ln->ctrl_copy = *ln->w.ctrl_h;
+    return HELM_OK;
+}
+
+}  // namespace
+
+extern "C" helm_status helm_gmres_solve_batched(helm_ctx* const* ctxs, int nprob, const void* const* b, void* const* x,
+                                                int nrhs, helm_solve_info* infos, void* stream) {
+    if (!ctxs || !b || !x || nprob < 1 || nrhs < 1) return HELM_ERR_ARG;
+    const auto t0 = std::chrono::steady_clock::now();
+    cudaStream_t s = (cudaStream_t)stream;
+    for (int p = 0; p < nprob; ++p) {
+        helm_ctx* c = ctxs[p];
+        if (!c || !b[p] || !x[p]) return HELM_ERR_ARG;
+        if (c->opt.precond == HELM_PRECOND_PFFT || c->net) return HELM_ERR_UNSUPPORTED;
+        if (!is_device_ptr(b[p]) || !is_device_ptr(x[p])) return HELM_ERR_ARG;
+        for (int q = 0; q < p; ++q)
+            if (ctxs[q] == c) return HELM_ERR_ARG;   // each context once (its right-hand sides are its lanes)
+    }
+    std::vector<Lane> lanes((size_t)nprob * nrhs);
+    std::vector<int> prof_on(nprob, 0);
+    for (int p = 0; p < nprob; ++p) {
+        helm_ctx* c = ctxs[p];
+        if (c->prof) { prof_on[p] = c->prof->enabled; c->prof->enabled = 0; }   // no event nodes in the graph
+        HELM_CUDA_TRY(cudaMemsetAsync(c->status_d, 0, sizeof(unsigned), s));
+        for (int r = 0; r < nrhs; ++r) {
+            Lane& ln = lanes[(size_t)p * nrhs + r];
+            ln.c = c;
+            ln.b = (double2*)b[p] + (size_t)r * c->npts;
+            ln.x = (double2*)x[p] + (size_t)r * c->npts;
+            ln.index = p * nrhs + r;
+        }
+    }
+    // groups by workspace size, largest lanes first
+    std::vector<Lane*> order;
+    for (auto& ln : lanes) order.push_back(&ln);
+    std::stable_sort(order.begin(), order.end(), [](const Lane* a, const Lane* b2) { return a->c->npts > b2->c->npts; });
+    size_t freeb = 0, totb = 0;
+    HELM_CUDA_TRY(cudaMemGetInfo(&freeb, &totb));
+    const size_t budget = (size_t)(0.6 * (double)freeb);
+    helm_status result = HELM_OK;
+    size_t i = 0;
+    while (i < order.size() && result == HELM_OK) {
+        std::vector<Lane*> grp;
+        size_t used = 0;
+        while (i < order.size() && (grp.empty() || used + lane_bytes(order[i]->c) <= budget)) {
+            used += lane_bytes(order[i]->c);
+            grp.push_back(order[i++]);
+        }
+        result = run_group(grp, s);
+        for (Lane* ln : grp) free_lane(*ln);
+    }
+    for (int p = 0; p < nprob; ++p)
+        if (ctxs[p]->prof) ctxs[p]->prof->enabled = prof_on[p];
+    if (result != HELM_OK) return result;
+    std::vector<unsigned> dstat(nprob, 0);
+    for (int p = 0; p < nprob; ++p)
+        HELM_CUDA_TRY(cudaMemcpyAsync(&dstat[p], ctxs[p]->status_d, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+    HELM_CUDA_TRY(cudaStreamSynchronize(s));
+    const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    helm_status worst = HELM_OK;
+    for (size_t li = 0; li < lanes.size(); ++li) {
+        Lane& ln = lanes[li];
+        const int p = (int)(li / nrhs);
+        const LaneCtl& L = ln.L_h;
+        const double beta0 = ln.ctrl_copy.beta0, beta = ln.ctrl_copy.beta;
+        helm_status stt;
+        if (!(beta0 > 0)) stt = (ln.ctrl_copy.flags & HELM_DEV_NAN) ? HELM_ERR_NAN : HELM_OK;
+        else if (beta / beta0 <= ln.c->opt.rtol) stt = HELM_OK;
+        else if (ln.ctrl_copy.flags & HELM_DEV_NAN) stt = HELM_ERR_NAN;
+        else if (L.brk) stt = HELM_ERR_BREAKDOWN;
+        else stt = HELM_ERR_NOT_CONVERGED;
+        if (stt == HELM_OK && (dstat[p] & HELM_DEV_PIVOT)) stt = HELM_ERR_PIVOT;
+        if (dstat[p] & HELM_DEV_WAIT) stt = HELM_ERR_ITER_LIMIT;
+        if (infos) {
+            helm_solve_info& inf = infos[li];
+            inf = helm_solve_info{};
+            inf.status = stt;
+            inf.iterations = L.its;
+            inf.restarts = L.restarts;
+            inf.relres_true = beta0 > 0 ? beta / beta0 : 0.0;
+            inf.relres_est = ln.ctrl_copy.est;
+            inf.beta0 = beta0;
+            inf.seconds = secs;
+            for (int q = 0; q < 16; ++q) inf.cycle_its[q] = L.cyc[q];
+        }
+        if (worst == HELM_OK && stt != HELM_OK) worst = stt;
+    }
+    return worst;
 }

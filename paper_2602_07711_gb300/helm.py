@@ -25,7 +25,10 @@ STATUS = {0: "HELM_OK", 1: "HELM_ERR_ARG", 2: "HELM_ERR_CUDA", 3: "HELM_ERR_NOME
 class HelmError(RuntimeError):
     def __init__(self, code, where):
         self.code = code
-        super().__init__("%s failed: %s (%d)" % (where, STATUS.get(code, "?"), code))
+        msg = "%s failed: %s (%d)" % (where, STATUS.get(code, "?"), code)
+        if code in (2, 3) and _lib is not None:
+            msg += ": " + _lib.helm_last_error().decode(errors="replace")
+        super().__init__(msg)
 
 
 class helm_grid(C.Structure):
@@ -61,6 +64,9 @@ _SIGS = {
     "helm_precond_step": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
     "helm_get_eig": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
     "helm_gmres_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(helm_solve_info), C.c_void_p]),
+    "helm_gmres_solve_batched": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_int,
+                                           C.c_void_p, C.c_void_p]),
+    "helm_autotune": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "helm_residual": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_double),
                                 C.POINTER(C.c_double), C.c_void_p]),
     "helm_residual_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_double),
@@ -87,6 +93,7 @@ _SIGS = {
     "helm_attach_net": (C.c_int, [C.c_void_p, C.c_void_p]),
     "helm_status_str": (C.c_char_p, [C.c_int]),
     "helm_version": (C.c_char_p, []),
+    "helm_last_error": (C.c_char_p, []),
 }
 
 
@@ -165,6 +172,24 @@ def helm_gmres_solve(ctx, b, x, stream=None):
     info = helm_solve_info()
     code = lib().helm_gmres_solve(ctx, _ptr(b), _ptr(x), C.byref(info), _stream(stream))
     return code, info
+
+
+def helm_gmres_solve_batched(ctxs, bs, xs, nrhs, stream=None):
+    """Batched solve (include/helm.h): bs[p], xs[p] complex128 device tensors [nrhs][nz][ny][nx].
+    Returns (status, [helm_solve_info per (problem, rhs), problem-major])."""
+    n = len(ctxs)
+    carr = (C.c_void_p * n)(*[c.value if isinstance(c, C.c_void_p) else c for c in ctxs])
+    barr = (C.c_void_p * n)(*[b.data_ptr() for b in bs])
+    xarr = (C.c_void_p * n)(*[x.data_ptr() for x in xs])
+    infos = (helm_solve_info * (n * nrhs))()
+    code = lib().helm_gmres_solve_batched(carr, n, barr, xarr, int(nrhs), infos, _stream(stream))
+    return code, list(infos)
+
+
+def helm_autotune(ctx, stream=None):
+    nb = C.c_int()
+    _check(lib().helm_autotune(ctx, C.byref(nb), _stream(stream)), "helm_autotune")
+    return nb.value
 
 
 def helm_residual(ctx, b, x, r=None, stream=None):
@@ -277,6 +302,18 @@ def helm_net_mse(y, t, gy, loss, stream=None):
     _check(lib().helm_net_mse(_ptr(y), _ptr(t), _ptr(gy), y.numel(), _ptr(loss), _stream(stream)), "helm_net_mse")
 
 
+def solve_batched(solvers, bs, x0s=None, stream=None):
+    """Solve every solver's right-hand sides bs[p] (complex128 device [nrhs][nz][ny][nx], same nrhs for all)
+    in one batched call; returns (xs, infos) with infos[p][r]."""
+    import torch
+    nrhs = bs[0].shape[0]
+    xs = [torch.zeros_like(b) if x0s is None else x0s[p] for p, b in enumerate(bs)]
+    code, infos = helm_gmres_solve_batched([S.ctx for S in solvers], bs, xs, nrhs, stream)
+    if code not in (0, 8):
+        raise HelmError(code, "helm_gmres_solve_batched")
+    return xs, [infos[p * nrhs:(p + 1) * nrhs] for p in range(len(solvers))]
+
+
 class Solver:
     """One problem: grid, k^2 samples (complex128, host numpy or torch tensor), background k0, options."""
 
@@ -330,6 +367,10 @@ class Solver:
         y = self._empty(torch.complex64)
         helm_precond_step(self.ctx, step, x, y, stream)
         return y
+
+    def autotune(self, stream=None):
+        """Pick the Arnoldi kernels' CTA count for this grid by timing (cached per grid size)."""
+        return helm_autotune(self.ctx, stream)
 
     def features(self, net, v, mv, stream=None):
         """The net's 5 input channels (bfloat16 [5][nz][ny][nx]) for complex64 v and mv = M^-1 v."""
