@@ -44,6 +44,12 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--e2e", type=int, default=1)
     p.add_argument("--max-iter", type=int, default=300)
+    p.add_argument("--workload", default="n256", choices=["n256", "batched", "pfft", "learned"],
+                   help="n256: the headline solve; batched: 64 uneven problems x 4 right-hand sides in one "
+                        "batched call; pfft: 512^3 layered medium, PFFT vs EigT; learned: 384^3 high-contrast "
+                        "medium, learned correction vs plain EigT")
+    p.add_argument("--problems", type=int, default=64, help="batched workload: number of problems")
+    p.add_argument("--rhs", type=int, default=4, help="batched workload: right-hand sides per problem")
     return p.parse_args()
 
 
@@ -220,7 +226,7 @@ def run_ours(args, rank, world, local):
     n, order = args.n, args.order
     precision = args.precision
     if precision == "auto":
-        precision = "fp32"
+        precision = "tf32"
     k2, f, k0 = media.bumps(n, 3, 4, device=dev, as_numpy=False)
     stream = torch.cuda.current_stream()
     flexible = precision != "fp32"
@@ -353,6 +359,197 @@ def run_ours(args, rank, world, local):
     S.close()
 
 
+# ---- other workloads (one JSON line each; not the headline line) ---------------------------------
+def _base_line(args, world, value, elapsed, workload, extra):
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / max(1, args.steps), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "c64", "data": "synthetic",
+            "config": dict({"workload": workload}, **extra.pop("config", {}))}
+    line.update(extra)
+    return line
+
+
+def run_batched(args, rank, world, local):
+    """64 problems of n ~ U{48,64,96,128,160}, ~U[6,12] points per wavelength, 20-bump media, order ~ U{4,6},
+    4 incident directions each (seed 6 draws the problem table); one helm_gmres_solve_batched call per step,
+    against the same lanes solved one after another with helm_gmres_solve."""
+    import numpy as np
+    import torch
+
+    from paper_2602_07711_gb300 import helm, media
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    rng = np.random.default_rng(6 + 1000 * rank)
+    sizes = rng.choice([48, 64, 96, 128, 160], size=args.problems)
+    ppws = rng.uniform(6.0, 12.0, size=args.problems)
+    orders = rng.choice([4, 6], size=args.problems)
+    prec = PREC_NAMES["tf32" if args.precision == "auto" else args.precision]
+    solvers, Bs = [], []
+    t0 = time.perf_counter()
+    for p in range(args.problems):
+        n = int(sizes[p])
+        fs = []
+        for r in range(args.rhs):
+            k2, f, k0 = media.bumps(n, 1000 + p, 5000 + 17 * p + r, ppw=float(ppws[p]), device=dev, as_numpy=False)
+            fs.append(f)
+        S = helm.Solver((n, n, n), k2, k0, order=int(orders[p]), precision=prec, restart=args.restart,
+                        max_iter=args.max_iter, rtol=args.rtol, flexible=prec != 0)
+        solvers.append(S)
+        Bs.append(torch.stack([S.build_rhs(f) for f in fs]).contiguous())
+        del k2, fs
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t0
+    tune = [S.autotune() for S in solvers]
+    Xs = [torch.zeros_like(B) for B in Bs]
+    t0 = time.perf_counter()
+    try:
+        plan = helm.Batch(solvers, Bs, Xs)          # lanes' workspaces + the restart-cycle graph, built once
+    except helm.HelmError:
+        plan = None                                  # does not fit at once: the one-shot call splits into groups
+    plan_s = time.perf_counter() - t0
+
+    def step():
+        for X in Xs:
+            X.zero_()
+        if plan is not None:
+            code, infos = plan.run()
+            return code, [i for row in infos for i in row]
+        return helm.helm_gmres_solve_batched([S.ctx for S in solvers], Bs, Xs, args.rhs)
+
+    for _ in range(args.warmup):
+        step()
+    clocks = ClockSampler(local)
+    clocks.start()
+    stream = torch.cuda.current_stream()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    res = [step() for _ in range(args.steps)]
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    elapsed = ev0.elapsed_time(ev1) / 1e3
+    pt_its = 0
+    its_all, stat_all = [], []
+    for code, infos in res:
+        for li, inf in enumerate(infos):
+            n = int(sizes[li // args.rhs])
+            pt_its += n ** 3 * inf.iterations
+            its_all.append(inf.iterations)
+            stat_all.append(inf.status)
+    value = pt_its / elapsed / 1e6 * world
+    # the same lanes one after another through the single-solve entry point
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    seq_its = 0
+    for p, S in enumerate(solvers):
+        for r in range(args.rhs):
+            x = torch.zeros_like(Bs[p][r])
+            _, inf = S.solve(Bs[p][r], x0=x, check=False)
+            seq_its += int(sizes[p]) ** 3 * inf.iterations
+    torch.cuda.synchronize()
+    seq_s = time.perf_counter() - t1
+    launches = None
+    if rank == 0:
+        line = _base_line(args, world, value, elapsed, "batched-%dx%d" % (args.problems, args.rhs), {
+            "config": {"problems": args.problems, "rhs": args.rhs, "sizes": [int(v) for v in sizes],
+                       "orders": [int(v) for v in orders], "precision": "tf32" if prec == 1 else "fp32",
+                       "krylov": "FGMRES(%d)" % args.restart, "rtol": args.rtol, "seed": 6},
+            "time_per_batch_s": elapsed / args.steps, "lanes": args.problems * args.rhs,
+            "iterations_total": sum(its_all) // max(1, args.steps), "status_nonzero": sum(1 for v in stat_all if v),
+            "sequential": {"seconds": seq_s, "Mpts_iter_s": seq_its / seq_s / 1e6,
+                           "speedup_of_batched": seq_s / (elapsed / args.steps)},
+            "autotuned_nb": sorted(set(tune)), "setup_s": setup_s, "plan_s": plan_s,
+            "plan": "helm_batch (built once)" if plan is not None else "helm_gmres_solve_batched (groups per call)",
+            "clocks": clk, "gpu_launches": launches,
+            "roofline": None, "cpu_baseline": None, "e2e": None})
+        print(json.dumps(line), flush=True)
+    if plan is not None:
+        plan.close()
+    for S in solvers:
+        S.close()
+
+
+def _timed_solve(S, f, steps):
+    import torch
+    stream = torch.cuda.current_stream()
+    F = S.build_rhs(f)
+    x = torch.zeros_like(F)
+    S.solve(F, x0=x, check=False)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    infos = []
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for _ in range(steps):
+        F = S.build_rhs(f)
+        x.zero_()
+        _, inf = S.solve(F, x0=x, check=False)
+        infos.append(inf)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    return ev0.elapsed_time(ev1) / 1e3 / steps, infos
+
+
+def run_pfft(args, rank, world, local):
+    """512^3, order 6, 8 points per wavelength, 8 layers k^2/k0^2 ~ U[0.7,1.3] plus 3 spheres (seed 5);
+    FGMRES(30) with the PFFT preconditioner against EigT on the same problem, both with the depth profile
+    K_z = k0^2(z) of the layers (the plane averages of Re k^2) and EigT also with constant k0."""
+    import torch
+
+    from paper_2602_07711_gb300 import helm, media
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    n = 512 if args.n == 256 else args.n
+    k2, f, k0 = media.layered(n, 5, ppw=8.0, device=dev, as_numpy=False)
+    k0z2 = k2.real.mean(dim=(1, 2)).cpu().numpy()
+    out = {}
+    for name, pc, prof in (("pfft_kz", helm.HELM_PRECOND_PFFT, k0z2), ("eigt_kz", helm.HELM_PRECOND_EIGT, k0z2),
+                           ("eigt_const", helm.HELM_PRECOND_EIGT, None)):
+        S = helm.Solver((n, n, n), k2, k0, order=6, precond=pc, precision=1, restart=args.restart,
+                        max_iter=args.max_iter, rtol=args.rtol, flexible=True, k0z2=prof)
+        dt, infos = _timed_solve(S, f, max(1, args.steps))
+        out[name] = {"time_to_rtol_s": dt, "iterations": infos[-1].iterations, "status": infos[-1].status,
+                     "relres_true": infos[-1].relres_true, "Mpts_iter_s": n ** 3 * infos[-1].iterations / dt / 1e6,
+                     "ms_per_iteration": 1e3 * dt / max(1, infos[-1].iterations)}
+        S.close()
+    if rank == 0:
+        v = out["pfft_kz"]["Mpts_iter_s"] * world
+        line = _base_line(args, world, v, out["pfft_kz"]["time_to_rtol_s"] * args.steps,
+                          "layered8+3spheres-n%d-order6-seed5" % n,
+                          {"config": {"n": n, "precond": "PFFT vs EigT", "precision": "tf32",
+                                      "krylov": "FGMRES(%d)" % args.restart, "kz": "plane averages of Re k^2"},
+                           "runs": out, "roofline": None, "cpu_baseline": None, "e2e": None})
+        print(json.dumps(line), flush=True)
+
+
+def run_learned(args, rank, world, local):
+    """384^3, order 6, 8 points per wavelength, k^2/k0^2 in [0.5,1.8] (8 layers + 5 spheres): the U-Net is
+    trained on the GPU on pairs from 96^3 solves of the same family, then FGMRES(30)+EigT with and without it."""
+    import numpy as np
+    import torch
+
+    from paper_2602_07711_gb300 import Net, learned
+    torch.cuda.set_device(local)
+    n = 384 if args.n == 256 else args.n
+    t0 = time.perf_counter()
+    X, T = learned.generate_pairs(n=96, seeds=range(100, 116), iters=(0, 3, 8), arnoldi=4)
+    net = Net(8, seed=0)
+    log = learned.train(net, X, T, steps=300, batch=2)
+    train_s = time.perf_counter() - t0
+    val = learned.evaluate(net, *learned.generate_pairs(n=96, seeds=range(200, 202), iters=(0, 4), arnoldi=2))
+    r = learned.compare(net, n, 7, rtol=args.rtol, max_iter=args.max_iter, repeats=1)
+    if rank == 0:
+        v = n ** 3 * r["learned"]["iterations"] / r["learned"]["seconds"] / 1e6
+        line = _base_line(args, world, v, r["learned"]["seconds"], "highcontrast-n%d-order6-seed7" % n,
+                          {"config": {"n": n, "net_width": 8, "params": int(net.nparam), "pairs": int(X.shape[0]),
+                                      "krylov": "FGMRES(%d)" % args.restart},
+                           "train_s": train_s, "train_log": log[-3:], "val_loss_vs_zero": val, "compare": r,
+                           "roofline": None, "cpu_baseline": None, "e2e": None})
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -364,7 +561,14 @@ def main():
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
-    run_ours(args, rank, world, local)
+    if args.workload == "n256":
+        run_ours(args, rank, world, local)
+    elif args.workload == "batched":
+        run_batched(args, rank, world, local)
+    elif args.workload == "pfft":
+        run_pfft(args, rank, world, local)
+    else:
+        run_learned(args, rank, world, local)
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()

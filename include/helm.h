@@ -155,6 +155,20 @@ helm_status helm_gmres_solve(helm_ctx* ctx, const void* b, void* x, helm_solve_i
 helm_status helm_gmres_solve_batched(helm_ctx* const* ctxs, int nprob, const void* const* b, void* const* x, int nrhs,
                                      helm_solve_info* infos, void* stream);
 
+/* Batch plans: the lanes' workspaces and the instantiated restart-cycle graph of helm_gmres_solve_batched,
+ * built once and run many times (the set-up stays out of repeated solves).
+ * helm_batch_create - plan for the same arguments as helm_gmres_solve_batched; b and x are read and written
+ *   by every helm_batch_run (their contents may change between runs, not their addresses).  All lanes must
+ *   fit in 85% of the free device memory (else HELM_ERR_NOMEM; helm_gmres_solve_batched splits instead).
+ * helm_batch_run - solve every lane from the current b and x0 (as helm_gmres_solve_batched; infos
+ *   problem-major, seconds = this run).  Synchronises `stream`.
+ * helm_batch_destroy - free the plan (NULL is a no-op); the contexts must outlive it. */
+typedef struct helm_batch helm_batch;
+helm_status helm_batch_create(helm_ctx* const* ctxs, int nprob, const void* const* b, void* const* x, int nrhs,
+                              void* stream, helm_batch** out);
+helm_status helm_batch_run(helm_batch* batch, helm_solve_info* infos, void* stream);
+void helm_batch_destroy(helm_batch* batch);
+
 /* helm_autotune - time the candidate CTA counts of the Arnoldi kernels (inner products, update, combine)
  * on this context's grid and keep the fastest for its later solves; *nb_out (may be NULL) receives it.
  * Results are cached per grid size for the process.  Uses temporary device memory; synchronous. */

@@ -897,28 +897,76 @@ void free_lane(Lane& ln) {
     ln.more = nullptr;
 }
 
-helm_status run_group(std::vector<Lane*>& lanes, cudaStream_t s) {
+}  // namespace
+
+// A batch plan: the lanes' workspaces and the instantiated restart-cycle graph, reusable across runs.
+struct helm_batch {
+    std::vector<Lane> lanes;
+    std::vector<helm_ctx*> ctxs;
+    int nprob = 0, nrhs = 0;
+    int* flags = nullptr;
+    cudaGraph_t G = nullptr;
+    cudaGraphExec_t X = nullptr;
+    cudaStream_t cs = nullptr;
+};
+
+namespace {
+
+void plan_free(helm_batch* P) {
+    if (P->X) cudaGraphExecDestroy(P->X);
+    if (P->G) cudaGraphDestroy(P->G);
+    if (P->cs) cudaStreamDestroy(P->cs);
+    cudaFree(P->flags);
+    for (Lane& ln : P->lanes) free_lane(ln);
+    P->X = nullptr; P->G = nullptr; P->cs = nullptr; P->flags = nullptr;
+}
+
+// workspace of every lane and the graph of one restart cycle of all lanes
+helm_status plan_build(helm_batch* P) {
     helm_status st;
-    // workspace, then the double-float copies of b and x0 and the x0 = 0 flags
-    for (Lane* ln : lanes) {
-        helm_ctx* c = ln->c;
-        if ((st = alloc_work(c, &ln->w, c->opt.restart, c->opt.flexible, default_nb(c))) != HELM_OK) return st;
-        if (cudaMalloc(&ln->tmp, c->npts * sizeof(float2)) != cudaSuccess) { cudaGetLastError(); return HELM_ERR_NOMEM; }
-        HELM_CUDA_TRY(cudaMalloc(&ln->L_d, sizeof(LaneCtl)));
-        HELM_CUDA_TRY(cudaMemsetAsync(ln->w.nzflag, 0, sizeof(unsigned), s));
-        to_df_kernel<<<ln->w.NB, NT, 0, s>>>(ln->b, ln->w.Fdf, c->npts, nullptr);
-        to_df_kernel<<<ln->w.NB, NT, 0, s>>>(ln->x, ln->w.xdf, c->npts, ln->w.nzflag);
+    for (Lane& ln : P->lanes) {
+        helm_ctx* c = ln.c;
+        if ((st = alloc_work(c, &ln.w, c->opt.restart, c->opt.flexible, default_nb(c))) != HELM_OK) return st;
+        if (cudaMalloc(&ln.tmp, c->npts * sizeof(float2)) != cudaSuccess) { cudaGetLastError(); return HELM_ERR_NOMEM; }
+        HELM_CUDA_TRY(cudaMalloc(&ln.L_d, sizeof(LaneCtl)));
+    }
+    HELM_CUDA_TRY(cudaMalloc(&P->flags, sizeof(int) * P->lanes.size()));
+    for (size_t i = 0; i < P->lanes.size(); ++i) P->lanes[i].more = P->flags + i;
+    HELM_CUDA_TRY(cudaStreamCreateWithFlags(&P->cs, cudaStreamNonBlocking));
+    HELM_CUDA_TRY(cudaGraphCreate(&P->G, 0));
+    std::vector<int> prof_on(P->ctxs.size(), 0);
+    for (size_t p = 0; p < P->ctxs.size(); ++p)
+        if (P->ctxs[p]->prof) { prof_on[p] = P->ctxs[p]->prof->enabled; P->ctxs[p]->prof->enabled = 0; }  // no event nodes
+    st = HELM_OK;
+    for (size_t i = 0; st == HELM_OK && i < P->lanes.size(); ++i) st = build_lane(P->G, P->lanes[i], P->cs);
+    for (size_t p = 0; p < P->ctxs.size(); ++p)
+        if (P->ctxs[p]->prof) P->ctxs[p]->prof->enabled = prof_on[p];
+    if (st != HELM_OK) return st;
+    const cudaError_t e = cudaGraphInstantiate(&P->X, P->G, 0);
+    if (e != cudaSuccess) return helm_fail_cuda(e, "cudaGraphInstantiate");
+    return HELM_OK;
+}
+
+// one solve of every lane from the current contents of b and x
+helm_status plan_run(helm_batch* P, cudaStream_t s) {
+    helm_status st;
+    std::vector<Lane>& lanes = P->lanes;
+    for (helm_ctx* c : P->ctxs) HELM_CUDA_TRY(cudaMemsetAsync(c->status_d, 0, sizeof(unsigned), s));
+    for (Lane& ln : lanes) {
+        HELM_CUDA_TRY(cudaMemsetAsync(ln.w.nzflag, 0, sizeof(unsigned), s));
+        to_df_kernel<<<ln.w.NB, NT, 0, s>>>(ln.b, ln.w.Fdf, ln.c->npts, nullptr);
+        to_df_kernel<<<ln.w.NB, NT, 0, s>>>(ln.x, ln.w.xdf, ln.c->npts, ln.w.nzflag);
         HELM_CUDA_TRY(cudaGetLastError());
     }
     std::vector<unsigned> nz(lanes.size(), 0);
     for (size_t i = 0; i < lanes.size(); ++i)
-        HELM_CUDA_TRY(cudaMemcpyAsync(&nz[i], lanes[i]->w.nzflag, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+        HELM_CUDA_TRY(cudaMemcpyAsync(&nz[i], lanes[i].w.nzflag, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
     HELM_CUDA_TRY(cudaStreamSynchronize(s));
-    // initial true residuals and the lane controls
+    // initial true residuals (r0 = b without a matvec when x0 = 0) and the lane controls
     for (size_t i = 0; i < lanes.size(); ++i) {
-        Lane* ln = lanes[i];
-        helm_ctx* c = ln->c;
-        KrylovWork* k = &ln->w;
+        Lane& ln = lanes[i];
+        helm_ctx* c = ln.c;
+        KrylovWork* k = &ln.w;
         if (nz[i]) {
             if ((st = launch_residual(c, k->xdf, k->Fdf, k->V, k->rpart, s)) != HELM_OK) return st;
         } else {
@@ -930,60 +978,38 @@ helm_status run_group(std::vector<Lane*>& lanes, cudaStream_t s) {
         L.max_iter = c->opt.max_iter;
         L.m = c->opt.restart;
         L.rtol = c->opt.rtol;
-        ln->L_h = L;
-        HELM_CUDA_TRY(cudaMemcpyAsync(ln->L_d, &ln->L_h, sizeof(LaneCtl), cudaMemcpyHostToDevice, s));
+        ln.L_h = L;
+        HELM_CUDA_TRY(cudaMemcpyAsync(ln.L_d, &ln.L_h, sizeof(LaneCtl), cudaMemcpyHostToDevice, s));
         HELM_CUDA_TRY(cudaGetLastError());
     }
-    HELM_CUDA_TRY(cudaStreamSynchronize(s));
-    // one graph for the group
-    int* flags = nullptr;
-    HELM_CUDA_TRY(cudaMalloc(&flags, sizeof(int) * lanes.size()));
-    for (size_t i = 0; i < lanes.size(); ++i) lanes[i]->more = flags + i;
-    cudaStream_t cs = nullptr;
-    HELM_CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
-    cudaGraph_t G = nullptr;
-    cudaGraphExec_t X = nullptr;
-    st = HELM_OK;
-    cudaError_t e = cudaGraphCreate(&G, 0);
-    if (e != cudaSuccess) st = helm_fail_cuda(e, "cudaGraphCreate");
-    for (size_t i = 0; st == HELM_OK && i < lanes.size(); ++i) st = build_lane(G, *lanes[i], cs);
-    if (st == HELM_OK && (e = cudaGraphInstantiate(&X, G, 0)) != cudaSuccess) st = helm_fail_cuda(e, "cudaGraphInstantiate");
-    // one launch per restart cycle while any lane wants another (bounded by the largest iteration limit)
+    // one graph launch per restart cycle while any lane wants another (bounded by the largest iteration limit)
     int max_cycles = 1;
-    for (Lane* ln : lanes) max_cycles = std::max(max_cycles, ln->c->opt.max_iter + 1);
+    for (Lane& ln : lanes) max_cycles = std::max(max_cycles, ln.c->opt.max_iter + 1);
     std::vector<int> more(lanes.size(), 1);
-    for (int cyc = 0; st == HELM_OK && cyc <= max_cycles; ++cyc) {
-        if ((e = cudaGraphLaunch(X, s)) != cudaSuccess) { st = helm_fail_cuda(e, "cudaGraphLaunch"); break; }
-        if ((e = cudaMemcpyAsync(more.data(), flags, sizeof(int) * lanes.size(), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
-            (e = cudaStreamSynchronize(s)) != cudaSuccess) { st = helm_fail_cuda(e, "batched cycle"); break; }
+    cudaError_t e;
+    for (int cyc = 0; cyc <= max_cycles; ++cyc) {
+        if ((e = cudaGraphLaunch(P->X, s)) != cudaSuccess) return helm_fail_cuda(e, "cudaGraphLaunch");
+        if ((e = cudaMemcpyAsync(more.data(), P->flags, sizeof(int) * lanes.size(), cudaMemcpyDeviceToHost, s)) !=
+                cudaSuccess ||
+            (e = cudaStreamSynchronize(s)) != cudaSuccess)
+            return helm_fail_cuda(e, "batched restart cycle");
         bool any = false;
         for (int v : more) any = any || v;
         if (!any) break;
     }
-    if (X) cudaGraphExecDestroy(X);
-    if (G) cudaGraphDestroy(G);
-    cudaStreamDestroy(cs);
-    cudaFree(flags);
-    for (Lane* ln : lanes) ln->more = nullptr;
-    if (st != HELM_OK) return st;
     // solutions and controls back
-    for (Lane* ln : lanes) {
-        from_df_kernel<<<ln->w.NB, NT, 0, s>>>(ln->w.xdf, ln->x, ln->c->npts);
-        HELM_CUDA_TRY(cudaMemcpyAsync(ln->w.ctrl_h, ln->w.ctrl_d, sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
-        HELM_CUDA_TRY(cudaMemcpyAsync(&ln->L_h, ln->L_d, sizeof(LaneCtl), cudaMemcpyDeviceToHost, s));
+    for (Lane& ln : lanes) {
+        from_df_kernel<<<ln.w.NB, NT, 0, s>>>(ln.w.xdf, ln.x, ln.c->npts);
+        HELM_CUDA_TRY(cudaMemcpyAsync(ln.w.ctrl_h, ln.w.ctrl_d, sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
+        HELM_CUDA_TRY(cudaMemcpyAsync(&ln.L_h, ln.L_d, sizeof(LaneCtl), cudaMemcpyDeviceToHost, s));
     }
     HELM_CUDA_TRY(cudaStreamSynchronize(s));
-    for (Lane* ln : lanes) ln->ctrl_copy = *ln->w.ctrl_h;
+    for (Lane& ln : lanes) ln.ctrl_copy = *ln.w.ctrl_h;
     return HELM_OK;
 }
 
-}  // namespace
-
-extern "C" helm_status helm_gmres_solve_batched(helm_ctx* const* ctxs, int nprob, const void* const* b, void* const* x,
-                                                int nrhs, helm_solve_info* infos, void* stream) {
+helm_status check_batch_args(helm_ctx* const* ctxs, int nprob, const void* const* b, void* const* x, int nrhs) {
     if (!ctxs || !b || !x || nprob < 1 || nrhs < 1) return HELM_ERR_ARG;
-    const auto t0 = std::chrono::steady_clock::now();
-    cudaStream_t s = (cudaStream_t)stream;
     for (int p = 0; p < nprob; ++p) {
         helm_ctx* c = ctxs[p];
         if (!c || !b[p] || !x[p]) return HELM_ERR_ARG;
@@ -992,74 +1018,143 @@ extern "C" helm_status helm_gmres_solve_batched(helm_ctx* const* ctxs, int nprob
         for (int q = 0; q < p; ++q)
             if (ctxs[q] == c) return HELM_ERR_ARG;   // each context once (its right-hand sides are its lanes)
     }
-    std::vector<Lane> lanes((size_t)nprob * nrhs);
-    std::vector<int> prof_on(nprob, 0);
-    for (int p = 0; p < nprob; ++p) {
-        helm_ctx* c = ctxs[p];
-        if (c->prof) { prof_on[p] = c->prof->enabled; c->prof->enabled = 0; }   // no event nodes in the graph
-        HELM_CUDA_TRY(cudaMemsetAsync(c->status_d, 0, sizeof(unsigned), s));
-        for (int r = 0; r < nrhs; ++r) {
-            Lane& ln = lanes[(size_t)p * nrhs + r];
-            ln.c = c;
-            ln.b = (double2*)b[p] + (size_t)r * c->npts;
-            ln.x = (double2*)x[p] + (size_t)r * c->npts;
-            ln.index = p * nrhs + r;
-        }
+    return HELM_OK;
+}
+
+Lane make_lane(helm_ctx* c, const void* b, void* x, int r, int index) {
+    Lane ln;
+    ln.c = c;
+    ln.b = (double2*)b + (size_t)r * c->npts;
+    ln.x = (double2*)x + (size_t)r * c->npts;
+    ln.index = index;
+    return ln;
+}
+
+// per-lane status and info from the lane controls (same rules as helm_gmres_solve)
+helm_status lane_info(const Lane& ln, unsigned dstat, double secs, helm_solve_info* inf) {
+    const LaneCtl& L = ln.L_h;
+    const double beta0 = ln.ctrl_copy.beta0, beta = ln.ctrl_copy.beta;
+    helm_status stt;
+    if (!(beta0 > 0)) stt = (ln.ctrl_copy.flags & HELM_DEV_NAN) ? HELM_ERR_NAN : HELM_OK;
+    else if (beta / beta0 <= ln.c->opt.rtol) stt = HELM_OK;
+    else if (ln.ctrl_copy.flags & HELM_DEV_NAN) stt = HELM_ERR_NAN;
+    else if (L.brk) stt = HELM_ERR_BREAKDOWN;
+    else stt = HELM_ERR_NOT_CONVERGED;
+    if (stt == HELM_OK && (dstat & HELM_DEV_PIVOT)) stt = HELM_ERR_PIVOT;
+    if (dstat & HELM_DEV_WAIT) stt = HELM_ERR_ITER_LIMIT;
+    if (inf) {
+        *inf = helm_solve_info{};
+        inf->status = stt;
+        inf->iterations = L.its;
+        inf->restarts = L.restarts;
+        inf->relres_true = beta0 > 0 ? beta / beta0 : 0.0;
+        inf->relres_est = ln.ctrl_copy.est;
+        inf->beta0 = beta0;
+        inf->seconds = secs;
+        for (int q = 0; q < 16; ++q) inf->cycle_its[q] = L.cyc[q];
     }
-    // groups by workspace size, largest lanes first
-    std::vector<Lane*> order;
-    for (auto& ln : lanes) order.push_back(&ln);
-    std::stable_sort(order.begin(), order.end(), [](const Lane* a, const Lane* b2) { return a->c->npts > b2->c->npts; });
-    size_t freeb = 0, totb = 0;
-    HELM_CUDA_TRY(cudaMemGetInfo(&freeb, &totb));
-    const size_t budget = (size_t)(0.6 * (double)freeb);
-    helm_status result = HELM_OK;
-    size_t i = 0;
-    while (i < order.size() && result == HELM_OK) {
-        std::vector<Lane*> grp;
-        size_t used = 0;
-        while (i < order.size() && (grp.empty() || used + lane_bytes(order[i]->c) <= budget)) {
-            used += lane_bytes(order[i]->c);
-            grp.push_back(order[i++]);
-        }
-        result = run_group(grp, s);
-        for (Lane* ln : grp) free_lane(*ln);
-    }
-    for (int p = 0; p < nprob; ++p)
-        if (ctxs[p]->prof) ctxs[p]->prof->enabled = prof_on[p];
-    if (result != HELM_OK) return result;
-    std::vector<unsigned> dstat(nprob, 0);
-    for (int p = 0; p < nprob; ++p)
+    return stt;
+}
+
+helm_status fill_infos(const std::vector<Lane>& lanes, const std::vector<helm_ctx*>& ctxs, int nrhs, double secs,
+                       helm_solve_info* infos, cudaStream_t s) {
+    std::vector<unsigned> dstat(ctxs.size(), 0);
+    for (size_t p = 0; p < ctxs.size(); ++p)
         HELM_CUDA_TRY(cudaMemcpyAsync(&dstat[p], ctxs[p]->status_d, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
     HELM_CUDA_TRY(cudaStreamSynchronize(s));
-    const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     helm_status worst = HELM_OK;
-    for (size_t li = 0; li < lanes.size(); ++li) {
-        Lane& ln = lanes[li];
-        const int p = (int)(li / nrhs);
-        const LaneCtl& L = ln.L_h;
-        const double beta0 = ln.ctrl_copy.beta0, beta = ln.ctrl_copy.beta;
-        helm_status stt;
-        if (!(beta0 > 0)) stt = (ln.ctrl_copy.flags & HELM_DEV_NAN) ? HELM_ERR_NAN : HELM_OK;
-        else if (beta / beta0 <= ln.c->opt.rtol) stt = HELM_OK;
-        else if (ln.ctrl_copy.flags & HELM_DEV_NAN) stt = HELM_ERR_NAN;
-        else if (L.brk) stt = HELM_ERR_BREAKDOWN;
-        else stt = HELM_ERR_NOT_CONVERGED;
-        if (stt == HELM_OK && (dstat[p] & HELM_DEV_PIVOT)) stt = HELM_ERR_PIVOT;
-        if (dstat[p] & HELM_DEV_WAIT) stt = HELM_ERR_ITER_LIMIT;
-        if (infos) {
-            helm_solve_info& inf = infos[li];
-            inf = helm_solve_info{};
-            inf.status = stt;
-            inf.iterations = L.its;
-            inf.restarts = L.restarts;
-            inf.relres_true = beta0 > 0 ? beta / beta0 : 0.0;
-            inf.relres_est = ln.ctrl_copy.est;
-            inf.beta0 = beta0;
-            inf.seconds = secs;
-            for (int q = 0; q < 16; ++q) inf.cycle_its[q] = L.cyc[q];
-        }
+    for (const Lane& ln : lanes) {
+        const helm_status stt = lane_info(ln, dstat[ln.index / nrhs], secs, infos ? infos + ln.index : nullptr);
         if (worst == HELM_OK && stt != HELM_OK) worst = stt;
     }
     return worst;
+}
+
+}  // namespace
+
+extern "C" helm_status helm_batch_create(helm_ctx* const* ctxs, int nprob, const void* const* b, void* const* x,
+                                         int nrhs, void* stream, helm_batch** out) {
+    if (!out) return HELM_ERR_ARG;
+    *out = nullptr;
+    helm_status st = check_batch_args(ctxs, nprob, b, x, nrhs);
+    if (st != HELM_OK) return st;
+    size_t need = 0;
+    for (int p = 0; p < nprob; ++p) need += (size_t)nrhs * lane_bytes(ctxs[p]);
+    size_t freeb = 0, totb = 0;
+    HELM_CUDA_TRY(cudaMemGetInfo(&freeb, &totb));
+    if (need > (size_t)(0.85 * (double)freeb)) return HELM_ERR_NOMEM;
+    helm_batch* P = new helm_batch();
+    P->nprob = nprob;
+    P->nrhs = nrhs;
+    for (int p = 0; p < nprob; ++p) {
+        P->ctxs.push_back(ctxs[p]);
+        for (int r = 0; r < nrhs; ++r) P->lanes.push_back(make_lane(ctxs[p], b[p], x[p], r, p * nrhs + r));
+    }
+    (void)stream;
+    if ((st = plan_build(P)) != HELM_OK) {
+        plan_free(P);
+        delete P;
+        return st;
+    }
+    *out = P;
+    return HELM_OK;
+}
+
+extern "C" helm_status helm_batch_run(helm_batch* P, helm_solve_info* infos, void* stream) {
+    if (!P) return HELM_ERR_ARG;
+    const auto t0 = std::chrono::steady_clock::now();
+    cudaStream_t s = (cudaStream_t)stream;
+    helm_status st = plan_run(P, s);
+    if (st != HELM_OK) return st;
+    const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    return fill_infos(P->lanes, P->ctxs, P->nrhs, secs, infos, s);
+}
+
+extern "C" void helm_batch_destroy(helm_batch* P) {
+    if (!P) return;
+    plan_free(P);
+    delete P;
+}
+
+extern "C" helm_status helm_gmres_solve_batched(helm_ctx* const* ctxs, int nprob, const void* const* b, void* const* x,
+                                                int nrhs, helm_solve_info* infos, void* stream) {
+    helm_status st = check_batch_args(ctxs, nprob, b, x, nrhs);
+    if (st != HELM_OK) return st;
+    const auto t0 = std::chrono::steady_clock::now();
+    cudaStream_t s = (cudaStream_t)stream;
+    std::vector<Lane> all;
+    for (int p = 0; p < nprob; ++p)
+        for (int r = 0; r < nrhs; ++r) all.push_back(make_lane(ctxs[p], b[p], x[p], r, p * nrhs + r));
+    // groups by workspace size, largest lanes first, each fitting in 60% of the free memory
+    std::vector<size_t> order(all.size());
+    for (size_t i = 0; i < order.size(); ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t c) { return all[a].c->npts > all[c].c->npts; });
+    size_t freeb = 0, totb = 0;
+    HELM_CUDA_TRY(cudaMemGetInfo(&freeb, &totb));
+    const size_t budget = (size_t)(0.6 * (double)freeb);
+    std::vector<Lane> done;
+    size_t i = 0;
+    while (i < order.size()) {
+        helm_batch P;
+        size_t used = 0;
+        while (i < order.size() && (P.lanes.empty() || used + lane_bytes(all[order[i]].c) <= budget)) {
+            used += lane_bytes(all[order[i]].c);
+            P.lanes.push_back(all[order[i++]]);
+        }
+        for (Lane& ln : P.lanes)
+            if (std::find(P.ctxs.begin(), P.ctxs.end(), ln.c) == P.ctxs.end()) P.ctxs.push_back(ln.c);
+        st = plan_build(&P);
+        if (st == HELM_OK) st = plan_run(&P, s);
+        for (Lane& ln : P.lanes) {
+            Lane d = ln;
+            d.w = KrylovWork();
+            d.tmp = nullptr; d.L_d = nullptr; d.more = nullptr;
+            done.push_back(d);
+        }
+        plan_free(&P);
+        if (st != HELM_OK) return st;
+    }
+    const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    std::vector<helm_ctx*> cv(ctxs, ctxs + nprob);
+    return fill_infos(done, cv, nrhs, secs, infos, s);
 }

@@ -67,6 +67,10 @@ _SIGS = {
     "helm_gmres_solve_batched": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_int,
                                            C.c_void_p, C.c_void_p]),
     "helm_autotune": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "helm_batch_create": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p,
+                                    C.POINTER(C.c_void_p)]),
+    "helm_batch_run": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "helm_batch_destroy": (None, [C.c_void_p]),
     "helm_residual": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_double),
                                 C.POINTER(C.c_double), C.c_void_p]),
     "helm_residual_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_double),
@@ -184,6 +188,44 @@ def helm_gmres_solve_batched(ctxs, bs, xs, nrhs, stream=None):
     infos = (helm_solve_info * (n * nrhs))()
     code = lib().helm_gmres_solve_batched(carr, n, barr, xarr, int(nrhs), infos, _stream(stream))
     return code, list(infos)
+
+
+class Batch:
+    """A batch plan (helm_batch_*): solvers[p] with right-hand sides bs[p] and iterates xs[p]
+    (complex128 device tensors [nrhs][nz][ny][nx] whose addresses stay fixed)."""
+
+    def __init__(self, solvers, bs, xs, stream=None):
+        self.solvers, self.bs, self.xs = list(solvers), list(bs), list(xs)
+        self.nrhs = int(bs[0].shape[0])
+        n = len(self.solvers)
+        carr = (C.c_void_p * n)(*[S.ctx.value for S in self.solvers])
+        barr = (C.c_void_p * n)(*[b.data_ptr() for b in self.bs])
+        xarr = (C.c_void_p * n)(*[x.data_ptr() for x in self.xs])
+        h = C.c_void_p()
+        _check(lib().helm_batch_create(carr, n, barr, xarr, self.nrhs, _stream(stream), C.byref(h)),
+               "helm_batch_create")
+        self.h = h
+
+    def run(self, stream=None):
+        """Returns (status, infos[p][r])."""
+        n = len(self.solvers)
+        infos = (helm_solve_info * (n * self.nrhs))()
+        code = lib().helm_batch_run(self.h, infos, _stream(stream))
+        if code not in (0, 8):
+            raise HelmError(code, "helm_batch_run")
+        flat = list(infos)
+        return code, [flat[p * self.nrhs:(p + 1) * self.nrhs] for p in range(n)]
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().helm_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def helm_autotune(ctx, stream=None):

@@ -10,8 +10,8 @@ import pytest
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-from paper_2602_07711_gb300 import (HELM_PREC_FP32, HELM_PREC_TF32, HELM_PRECOND_PFFT, HelmError, Solver, helm,
-                                    media, solve_batched)
+from paper_2602_07711_gb300 import (HELM_PREC_FP32, HELM_PREC_TF32, HELM_PRECOND_PFFT, Batch, HelmError, Solver,
+                                    helm, media, solve_batched)
 
 
 def _problem(n, seed, ppw, nrhs, order, precision, flexible, restart=30, max_iter=300, rtol=1e-6):
@@ -74,6 +74,35 @@ def test_batch_with_restarts_warm_start_and_mixed_outcomes():
         x1, i1 = S2.solve(B2[r].contiguous(), x0=x0[r].clone(), check=False)
         assert i1.iterations == infos[1][r].iterations
         assert _rel(xs[1][r], x1) < 1e-9
+
+
+def test_batch_plan_runs_repeatedly_and_matches_the_one_shot_call():
+    Ss, Bs = [], []
+    for (n, order, prec, flex, ppw) in [(24, 6, HELM_PREC_TF32, True, 8.0), (32, 4, HELM_PREC_FP32, True, 10.0)]:
+        S, B = _problem(n, n + 1, ppw, 3, order, prec, flex)
+        Ss.append(S)
+        Bs.append(B)
+    Xs = [torch.zeros_like(B) for B in Bs]
+    plan = Batch(Ss, Bs, Xs)
+    _, inf1 = plan.run()
+    x1 = [X.clone() for X in Xs]
+    for X in Xs:
+        X.zero_()
+    _, inf2 = plan.run()
+    xs, inf3 = solve_batched(Ss, Bs)
+    for p in range(2):
+        assert torch.equal(Xs[p], x1[p])
+        assert _rel(xs[p], Xs[p]) < 1e-12
+        for r in range(3):
+            assert inf1[p][r].iterations == inf2[p][r].iterations == inf3[p][r].iterations
+            assert inf1[p][r].status == 0
+    # new right-hand sides in the same buffers
+    Bs[0][0].mul_(2.0)
+    for X in Xs:
+        X.zero_()
+    _, inf4 = plan.run()
+    assert _rel(Xs[0][0], 2.0 * x1[0][0]) < 1e-5 and inf4[0][0].status == 0
+    plan.close()
 
 
 def test_batch_rejects_bad_arguments():
