@@ -120,6 +120,7 @@ helm_status helm_setup(const helm_grid* grid, const void* k2, double k0, const d
     if (cudaMemcpyAsync(c->k2_d, k2, n * sizeof(double2), dev_ptr(k2) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
                         s) != cudaSuccess) { free_ctx(c); return HELM_ERR_CUDA; }
     TRY(launch_derived_fields(c, s));
+    TRY(stencil_fast_prepare());
     // eigen set-up
     TRY(dalloc(&c->Dx, c->nx)); TRY(dalloc(&c->Dy, c->ny));
     TRY(dalloc(&c->Vx, (size_t)c->nx * c->nx)); TRY(dalloc(&c->Vxi, (size_t)c->nx * c->nx));

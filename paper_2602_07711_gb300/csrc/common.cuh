@@ -141,6 +141,10 @@ helm_status launch_stencil_f32_cls(helm_ctx* c, const float2* x, float2* y, cons
 helm_status launch_stencil_f64(helm_ctx* c, const double2* x, double2* y, cudaStream_t s);
 helm_status launch_residual(helm_ctx* c, const float4* x, const float4* F, float2* r, double* part, cudaStream_t s);
 helm_status launch_rhs(helm_ctx* c, const double2* f, double2* F, float4* fdf, cudaStream_t s);
+// stencil_fast.cu: the complex64 matvec of orders 4 and 6 (cp.async plane ring, plane-quantity form)
+helm_status stencil_fast_prepare();
+bool stencil_fast_supported(const helm_ctx* c);
+helm_status launch_stencil_fast(helm_ctx* c, const float2* x, float2* y, const double* sigma, int sidx, cudaStream_t s);
 // eig.cu
 helm_status run_eig_setup(helm_ctx* c, cudaStream_t s);
 // gemm_simt.cu

@@ -530,6 +530,12 @@ helm_status launch_stencil_f32(helm_ctx* c, const float2* x, float2* y, const do
 
 helm_status launch_stencil_f32_cls(helm_ctx* c, const float2* x, float2* y, const double* sigma, int sidx, int cls,
                                    cudaStream_t s) {
+    if (stencil_fast_supported(c)) {
+        prof_begin(c, s, cls);
+        helm_status st = launch_stencil_fast(c, x, y, sigma, sidx, s);
+        prof_end(c, s);
+        return st;
+    }
     SParams<P32> p = make_params<P32>(c);
     p.k2 = c->k2_f;
     for (int d = 0; d < 3; ++d) p.dk2[d] = c->dk2_f[d];

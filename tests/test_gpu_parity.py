@@ -53,8 +53,9 @@ def _medium(n, L, seed=0):
 
 SIZES = {
     2: [((40, 36, 33), (1.0, 0.9, 0.85))],
-    4: [((40, 36, 33), (1.0, 0.9, 0.85)), ((32, 32, 32), (1.0, 1.0, 1.0))],
-    6: [((40, 36, 33), (40 / 40, 36 / 40, 33 / 40)), ((32, 32, 32), (1.0, 1.0, 1.0))],
+    4: [((40, 36, 33), (1.0, 0.9, 0.85)), ((32, 32, 32), (1.0, 1.0, 1.0)), ((66, 10, 70), (1.0, 0.2, 0.9))],
+    6: [((40, 36, 33), (40 / 40, 36 / 40, 33 / 40)), ((32, 32, 32), (1.0, 1.0, 1.0)),
+        ((70, 18, 66), (70 / 70, 18 / 70, 66 / 70))],
 }
 
 
