@@ -36,6 +36,7 @@ void free_ctx(helm_ctx* c) {
     krylov_free(c);
     tc_release(c);
     pfft_release(c);
+    stencil_fast_release(c);
     prof_release(c);
     void* ps[] = {c->k2_d, c->k2_f, c->dk2_d[0], c->dk2_d[1], c->dk2_d[2], c->dk2_f[0], c->dk2_f[1], c->dk2_f[2],
                   c->G_d, c->G_f, c->Dx, c->Dy, c->Vx, c->Vxi, c->Vy, c->Vyi, c->XF, c->XI, c->YF, c->YI,
@@ -120,7 +121,7 @@ helm_status helm_setup(const helm_grid* grid, const void* k2, double k0, const d
     if (cudaMemcpyAsync(c->k2_d, k2, n * sizeof(double2), dev_ptr(k2) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
                         s) != cudaSuccess) { free_ctx(c); return HELM_ERR_CUDA; }
     TRY(launch_derived_fields(c, s));
-    TRY(stencil_fast_prepare());
+    TRY(stencil_fast_prepare(c));
     // eigen set-up
     TRY(dalloc(&c->Dx, c->nx)); TRY(dalloc(&c->Dy, c->ny));
     TRY(dalloc(&c->Vx, (size_t)c->nx * c->nx)); TRY(dalloc(&c->Vxi, (size_t)c->nx * c->nx));

@@ -122,12 +122,14 @@ struct helm_ctx {
     float *YFr = nullptr, *YIr = nullptr;   // y-pass A: re and im planes [2][N][N] (hi, lo follow)
     void* tmaps = nullptr;                  // host copies of TMA descriptors (gemm_tc.cu)
     void* pfft = nullptr;                   // PFFT tables and scratch (pfft.cu)
+    void* sfast = nullptr;                  // TMA descriptors of the stencil's fixed operands (stencil_fast.cu)
     // scratch
     float2* tmp = nullptr;                  // one complex64 grid vector
     unsigned* status_d = nullptr;           // device status word
     KrylovWork* kw = nullptr;
     helm_net* net = nullptr;                // attached learned correction (not owned)
     int tune_nb = 0;                        // CTAs of the Arnoldi kernels chosen by helm_autotune (0 = default)
+    int tune_stencil = 0;                   // complex64 matvec variant chosen by helm_autotune (0 = cp.async ring)
     cudaStream_t last_stream = nullptr;
     Prof* prof = nullptr;
 };
@@ -142,7 +144,12 @@ helm_status launch_stencil_f64(helm_ctx* c, const double2* x, double2* y, cudaSt
 helm_status launch_residual(helm_ctx* c, const float4* x, const float4* F, float2* r, double* part, cudaStream_t s);
 helm_status launch_rhs(helm_ctx* c, const double2* f, double2* F, float4* fdf, cudaStream_t s);
 // stencil_fast.cu: the complex64 matvec of orders 4 and 6 (cp.async plane ring, plane-quantity form)
-helm_status stencil_fast_prepare();
+helm_status stencil_fast_prepare(helm_ctx* c);
+void stencil_fast_release(helm_ctx* c);
+int stencil_variants(const helm_ctx* c);
+helm_status residual_fast_prepare();
+helm_status launch_residual_fast(helm_ctx* c, const float4* x, const float4* F, float2* r, double* part,
+                                 cudaStream_t s);   // same grid (and partial count) as the generic residual
 bool stencil_fast_supported(const helm_ctx* c);
 helm_status launch_stencil_fast(helm_ctx* c, const float2* x, float2* y, const double* sigma, int sidx, cudaStream_t s);
 // eig.cu

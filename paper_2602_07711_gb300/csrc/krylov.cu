@@ -608,14 +608,20 @@ helm_status residual_run(helm_ctx* c, const double2* b, const double2* x, float2
 namespace {
 
 struct TuneKey {
-    int nx, ny, nz;
+    int nx, ny, nz, order;
     bool operator<(const TuneKey& o) const {
-        return nx != o.nx ? nx < o.nx : (ny != o.ny ? ny < o.ny : nz < o.nz);
+        if (nx != o.nx) return nx < o.nx;
+        if (ny != o.ny) return ny < o.ny;
+        if (nz != o.nz) return nz < o.nz;
+        return order < o.order;
     }
+};
+struct TuneVal {
+    int nb, stencil;
 };
 
 std::mutex g_tune_mu;
-std::map<TuneKey, int> g_tune_cache;
+std::map<TuneKey, TuneVal> g_tune_cache;
 
 }  // namespace
 
@@ -623,9 +629,10 @@ extern "C" helm_status helm_autotune(helm_ctx* c, int* nb_out, void* stream) {
     if (!c) return HELM_ERR_ARG;
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
-        auto it = g_tune_cache.find(TuneKey{c->nx, c->ny, c->nz});
+        auto it = g_tune_cache.find(TuneKey{c->nx, c->ny, c->nz, c->opt.order});
         if (it != g_tune_cache.end()) {
-            c->tune_nb = it->second;
+            c->tune_nb = it->second.nb;
+            c->tune_stencil = std::min(it->second.stencil, stencil_variants(c) - 1);
             if (nb_out) *nb_out = c->tune_nb;
             return HELM_OK;
         }
@@ -671,6 +678,24 @@ extern "C" helm_status helm_autotune(helm_ctx* c, int* nb_out, void* stream) {
         }
         if (tmin < best_ms * 0.97f) { best_ms = tmin; best = nb; }
     }
+    // the matvec variant: time each on the context's grid (input and output in the scratch vectors)
+    int best_st = 0;
+    float best_st_ms = 1e30f;
+    for (int v = 0; v < stencil_variants(c); ++v) {
+        c->tune_stencil = v;
+        float tmin = 1e30f;
+        for (int rep = 0; rep < 4; ++rep) {
+            cudaEventRecord(e0, s);
+            launch_stencil_f32(c, V, V + npts, nullptr, 0, s);
+            cudaEventRecord(e1, s);
+            cudaEventSynchronize(e1);
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (rep > 0) tmin = std::min(tmin, ms);
+        }
+        if (tmin < best_st_ms * 0.97f) { best_st_ms = tmin; best_st = v; }
+    }
+    c->tune_stencil = best_st;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     cudaFree(V); cudaFree(part); cudaFree(coef);
@@ -678,7 +703,7 @@ extern "C" helm_status helm_autotune(helm_ctx* c, int* nb_out, void* stream) {
     c->tune_nb = best;
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
-        g_tune_cache[TuneKey{c->nx, c->ny, c->nz}] = best;
+        g_tune_cache[TuneKey{c->nx, c->ny, c->nz, c->opt.order}] = TuneVal{best, best_st};
     }
     if (nb_out) *nb_out = best;
     return HELM_OK;

@@ -567,6 +567,12 @@ int residual_ctas(const helm_ctx* c) {
 
 // r = F - A x with x and F in double-float storage (float4 per point)
 helm_status launch_residual(helm_ctx* c, const float4* x, const float4* F, float2* r, double* part, cudaStream_t s) {
+    if (stencil_fast_supported(c)) {
+        prof_begin(c, s, PROF_RESIDUAL);
+        helm_status st = launch_residual_fast(c, x, F, r, part, s);
+        prof_end(c, s);
+        return st;
+    }
     SParams<PDF> p = make_params<PDF>(c);
     p.k2 = c->k2_df;
     for (int d = 0; d < 3; ++d) p.dk2[d] = c->dk2_f[d];

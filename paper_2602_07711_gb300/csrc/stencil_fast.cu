@@ -18,10 +18,19 @@
 //
 // Data movement: a CTA owns a 32 x 8 column tile and marches through a z-chunk.  Planes of U and k^2
 // with a one-point halo, and the per-point fields G, g_x, g_y, g_z, stream into a four-slot shared
-// memory ring by cp.async, two planes ahead of the arithmetic; one barrier per plane.  Halo points
-// outside the grid are loaded from the clamped position and multiplied by the ghost factors gamma_d
-// (products at edges and corners) when lifted; k^2 there is the mirror (clamped) value.
+// memory ring two planes ahead of the arithmetic, one barrier per plane:
+//   TMA kernel (even N_x): one thread issues cp.async.bulk.tensor tile loads per plane (a 36 x 10 tile of
+//     U and of k^2 starting two points left of the tile so that the 16-byte rule holds, four 32 x 8 field
+//     tiles), completion counted by one mbarrier per slot with bounded waits.  A prepare pass turns the
+//     landed k^2 into KU = k^2 U in place; out-of-grid halo points (TMA fills them with zeros) are then
+//     written as gamma-multiples of their interior neighbours, U and KU alike (KU is linear in U and k^2
+//     at a ghost is the mirror value), and the ghost planes z = -1, N_z come from the clamped plane times
+//     gamma_z.
+//   cp.async kernel (odd N_x): 8-byte cp.async of the clamped halo points, ghost factors applied as the
+//     thread lifts its patch.
 #include "common.cuh"
+#include <cuda.h>
+#include <cudaTypedefs.h>
 
 namespace {
 
@@ -212,18 +221,275 @@ stencil_fast_kernel(FParams p, const float2* __restrict__ U, float2* __restrict_
 template <int ORDER>
 size_t fast_smem() { return FNS * sizeof(FStage<ORDER>); }
 
+// ---- TMA kernel --------------------------------------------------------------------------------
+constexpr int TPX = 36;                          // tile row of the TMA halo: x0-2 .. x0+33
+constexpr int TU_BYTES = TPX * FPY * 8;          // 2880
+constexpr int TU_PAD = 2944;                     // 128-byte multiple
+constexpr int TF_BYTES = FNT * 8;                // 2048 per field
+template <int ORDER>
+struct TLayout {
+    static constexpr int U_OFF = 0, K_OFF = TU_PAD, F_OFF = 2 * TU_PAD;
+    static constexpr int STAGE = 2 * TU_PAD + (ORDER == 6 ? 4 * TF_BYTES : 0);
+    static constexpr int BAR_OFF = FNS * STAGE;
+    static constexpr int SMEM = BAR_OFF + FNS * 8 + 128;   // + alignment slack
+};
+constexpr long TWAIT_LIMIT = 1L << 22;
+
+__device__ __forceinline__ uint32_t s32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void tbar_init(uint32_t bar) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void tbar_expect(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool tbar_wait(uint32_t bar, uint32_t parity) {
+    for (long it = 0; it < TWAIT_LIMIT; ++it) {
+        uint32_t ok;
+        asm volatile(
+            "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(ok)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+__device__ __forceinline__ void tload3(uint32_t dst, const CUtensorMap* map, uint32_t bar, int c0, int c1, int c2) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], [%2];" ::"r"(
+            dst),
+        "l"((uint64_t)map), "r"(bar), "r"(c0), "r"(c1), "r"(c2)
+        : "memory");
+}
+
+template <int ORDER>
+__global__ void __launch_bounds__(FNT, 4)
+stencil_tma_kernel(const __grid_constant__ CUtensorMap mU, const __grid_constant__ CUtensorMap mK,
+                   const __grid_constant__ CUtensorMap mG, const __grid_constant__ CUtensorMap mGx,
+                   const __grid_constant__ CUtensorMap mGy, const __grid_constant__ CUtensorMap mGz, FParams p,
+                   float2* __restrict__ Y, const double* __restrict__ sigma, int sidx, unsigned* status) {
+    typedef TLayout<ORDER> L;
+    extern __shared__ unsigned char traw[];
+    unsigned char* base = (unsigned char*)(((uintptr_t)traw + 127) & ~(uintptr_t)127);
+    const uint32_t sbase = s32(base);
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * FTX + tx;
+    const int x0 = blockIdx.x * FTX, y0 = blockIdx.y * FTY;
+    const int z0 = blockIdx.z * FZCH;
+    const int z1 = min(z0 + FZCH, p.nz);
+    const int gx = x0 + tx, gy = y0 + ty;
+    const bool active = gx < p.nx && gy < p.ny;
+    const bool edge = x0 == 0 || p.nx <= x0 + FTX || y0 == 0 || p.ny <= y0 + FTY;   // the halo leaves the grid
+    const float sg = sigma ? (float)sigma[sidx] : 1.f;
+    if (tid == 0) {
+        for (int sl = 0; sl < FNS; ++sl) tbar_init(sbase + L::BAR_OFF + 8 * sl);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    __syncthreads();
+    // thread 0: stage plane P (relative index r = P - z0 + 1) into slot r % 4
+    auto issue = [&](int P) {
+        const int r = P - z0 + 1, sl = r & (FNS - 1);
+        const uint32_t st = sbase + sl * L::STAGE, bar = sbase + L::BAR_OFF + 8 * sl;
+        const int Pc = min(max(P, 0), p.nz - 1);
+        const bool fields = ORDER == 6 && P >= z0 && P < z1;
+        tbar_expect(bar, 2 * TU_BYTES + (fields ? 4 * TF_BYTES : 0));
+        tload3(st + L::U_OFF, &mU, bar, 2 * (x0 - 2), y0 - 1, Pc);
+        tload3(st + L::K_OFF, &mK, bar, 2 * (x0 - 2), y0 - 1, Pc);
+        if (fields) {
+            tload3(st + L::F_OFF, &mG, bar, 2 * x0, y0, P);
+            tload3(st + L::F_OFF + TF_BYTES, &mGx, bar, 2 * x0, y0, P);
+            tload3(st + L::F_OFF + 2 * TF_BYTES, &mGy, bar, 2 * x0, y0, P);
+            tload3(st + L::F_OFF + 3 * TF_BYTES, &mGz, bar, 2 * x0, y0, P);
+        }
+    };
+    bool failed = false;
+    if (tid == 0) { issue(z0 - 1); issue(z0); }
+
+    float2 cA = make_float2(0, 0), cX = cA, cY = cA, cZ = cA;
+    float2 nA = cA, nX = cA, nY = cA, nZ = cA;
+    for (int P = z0 - 1; P <= z1; ++P) {
+        const int r = P - z0 + 1, sl = r & (FNS - 1);
+        if (!failed && !tbar_wait(sbase + L::BAR_OFF + 8 * sl, (r >> 2) & 1)) {
+            failed = true;
+            if (tid == 0) atomicOr(status, HELM_DEV_WAIT);
+        }
+        float2* sU = reinterpret_cast<float2*>(base + sl * L::STAGE + L::U_OFF);
+        float2* sK = reinterpret_cast<float2*>(base + sl * L::STAGE + L::K_OFF);
+        // prepare: KU = k^2 U in place; ghost planes are gamma_z times the clamped plane
+        const bool zghost = P < 0 || P >= p.nz;
+        for (int q = tid; q < FHALO; q += FNT) {
+            const int ly = q / FPX, lx = q - ly * FPX + 1;
+            const int i = ly * TPX + lx;
+            float2 u = sU[i];
+            if (zghost) { u = f2mul(u, p.gz); sU[i] = u; }
+            sK[i] = f2mul(sK[i], u);
+        }
+        if (edge) {
+            __syncthreads();
+            // out-of-grid halo points next to the grid: gamma multiples of the interior neighbour
+            for (int q = tid; q < FHALO; q += FNT) {
+                const int ly = q / FPX, lx = q - ly * FPX + 1;
+                const int X = x0 + lx - 2, Yy = y0 + ly - 1;
+                const bool xo = X == -1 || X == p.nx, yo = Yy == -1 || Yy == p.ny;
+                if ((xo || yo) && X >= -1 && X <= p.nx && Yy >= -1 && Yy <= p.ny) {
+                    const int sx = lx + (X == -1 ? 1 : (X == p.nx ? -1 : 0));
+                    const int sy = ly + (Yy == -1 ? 1 : (Yy == p.ny ? -1 : 0));
+                    float2 f = make_float2(1.f, 0.f);
+                    if (xo) f = p.gx;
+                    if (yo) f = f2mul(f, p.gy);
+                    sU[ly * TPX + lx] = f2mul(f, sU[sy * TPX + sx]);
+                    sK[ly * TPX + lx] = f2mul(f, sK[sy * TPX + sx]);
+                }
+            }
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // generic writes before later TMA writes
+        __syncthreads();   // slot P prepared; every thread is done with plane P-1 (and the slot of P-2)
+        if (tid == 0 && P + 2 <= z1 && !failed) issue(P + 2);
+        float2 u[3][3];
+        float2 kc, kf4 = make_float2(0, 0), kcs = kf4, dkx = kf4, dky = kf4;
+#pragma unroll
+        for (int b = 0; b < 3; ++b)
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                const int i = (ty + b) * TPX + tx + 1 + a;
+                u[b][a] = sU[i];
+                if (ORDER == 6 || a == 1 || b == 1) {
+                    const float2 kv = sK[i];
+                    if (a == 1 && b == 1) kc = kv;
+                    else if (a == 1 || b == 1) kf4 = f2add(kf4, kv);
+                    else kcs = f2add(kcs, kv);
+                    if (b == 1 && a == 0) dkx = f2sub(dkx, kv);
+                    if (b == 1 && a == 2) dkx = f2add(dkx, kv);
+                    if (a == 1 && b == 0) dky = f2sub(dky, kv);
+                    if (a == 1 && b == 2) dky = f2add(dky, kv);
+                }
+            }
+        const float2 c = u[1][1];
+        const float2 fx = f2add(u[1][0], u[1][2]), fy = f2add(u[0][1], u[2][1]);
+        const float2 e = f2add(f2add(u[0][0], u[0][2]), f2add(u[2][0], u[2][2]));
+        const bool out_prev = P - 1 >= z0 && P - 1 < z1;
+        const bool do_mid = P >= z0 && P < z1;
+        if (ORDER == 6) {
+            const float2* F = reinterpret_cast<const float2*>(base + sl * L::STAGE + L::F_OFF);
+            const float2* Fp = reinterpret_cast<const float2*>(base + ((r - 1) & (FNS - 1)) * L::STAGE + L::F_OFF);
+            const float ih = p.ihx;
+            float2 As = f2scl(f2fma(1.f / 30.f, e, f2fma(0.1f, f2add(fx, fy), f2scl(c, 7.f / 15.f))), ih);
+            As = f2fma(1.f / 90.f, f2sub(kf4, kc), As);
+            const float2 dx1 = f2sub(u[1][2], u[1][0]), dy1 = f2sub(u[2][1], u[0][1]);
+            const float2 Xs = f2scl(dx1, 1.f / 6.f), Ys = f2scl(dy1, 1.f / 6.f);
+            const float2 Zs = f2add(f2fma(p.hh6, kc, c), f2scl(f2fma(-4.f, c, f2add(fx, fy)), 1.f / 6.f));
+            if (out_prev) {
+                const float2 A = f2add(cA, As);
+                float2 g = f2mul(Fp[FNT + tid], f2add(cX, Xs));
+                g = f2add(g, f2mul(Fp[2 * FNT + tid], f2add(cY, Ys)));
+                g = f2add(g, f2mul(Fp[3 * FNT + tid], f2add(cZ, Zs)));
+                const float2 v = f2fma(p.h_20, g, A);
+                if (active) Y[((size_t)(P - 1) * p.ny + gy) * p.nx + gx] = f2scl(v, sg);
+            }
+            cA = nA; cX = nX; cY = nY; cZ = nZ;
+            if (do_mid) {
+                float2 Am = f2scl(f2fma(-64.f / 15.f, c, f2fma(0.1f, e, f2scl(f2add(fx, fy), 7.f / 15.f))), ih);
+                Am = f2fma(14.f / 15.f, kc, Am);
+                Am = f2fma(1.f / 90.f, f2sub(kcs, kf4), Am);
+                Am = f2fma(p.h2_20, f2mul(F[tid], c), Am);
+                const float2 tdx = f2sub(f2add(u[0][2], u[2][2]), f2add(u[0][0], u[2][0]));
+                const float2 tdy = f2sub(f2add(u[2][0], u[2][2]), f2add(u[0][0], u[0][2]));
+                const float2 Xm = f2add(f2fma(p.hh6, dkx, dx1), f2scl(f2fma(-4.f, dx1, tdx), 1.f / 6.f));
+                const float2 Ym = f2add(f2fma(p.hh6, dky, dy1), f2scl(f2fma(-4.f, dy1, tdy), 1.f / 6.f));
+                cA = f2add(cA, Am); cX = f2add(cX, Xm); cY = f2add(cY, Ym);
+            }
+            nA = As; nX = Xs; nY = Ys; nZ = make_float2(-Zs.x, -Zs.y);
+        } else {
+            const float2 As = f2fma(1.f / 12.f, kc,
+                                    f2add(f2scl(c, p.ihz),
+                                          f2add(f2scl(f2fma(-2.f, c, fx), p.wxz), f2scl(f2fma(-2.f, c, fy), p.wyz))));
+            if (out_prev && active)
+                Y[((size_t)(P - 1) * p.ny + gy) * p.nx + gx] = f2scl(f2add(cA, As), sg);
+            cA = nA;
+            if (do_mid) {
+                const float2 c2 = f2add(c, c), c4 = f2add(c2, c2);
+                float2 Am = f2add(f2scl(f2sub(fx, c2), p.ihx), f2scl(f2sub(fy, c2), p.ihy));
+                Am = f2fma(-2.f * p.ihz, c, Am);
+                Am = f2fma(p.wxy, f2add(f2fma(-2.f, f2add(fx, fy), e), c4), Am);
+                Am = f2fma(p.wxz, f2fma(-2.f, fx, c4), Am);
+                Am = f2fma(p.wyz, f2fma(-2.f, fy, c4), Am);
+                Am = f2fma(0.5f, kc, Am);
+                Am = f2fma(1.f / 12.f, kf4, Am);
+                cA = f2add(cA, Am);
+            }
+            nA = As;
+        }
+    }
+    if (failed && tid == 0) {
+        // let the copies still in flight land before the CTA's shared memory goes away (bounded)
+        for (int sl = 0; sl < FNS; ++sl) {
+            uint32_t dummy = 0;
+            (void)dummy;
+            tbar_wait(sbase + L::BAR_OFF + 8 * sl, 0);
+            tbar_wait(sbase + L::BAR_OFF + 8 * sl, 1);
+        }
+    }
+}
+
+struct FastMaps {
+    PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+    CUtensorMap mK, mF[4];
+};
+
+helm_status encode3(FastMaps* m, CUtensorMap* map, const void* ptr, int nx, int ny, int nz, int boxw, int boxh) {
+    const cuuint64_t dims[3] = {(cuuint64_t)2 * nx, (cuuint64_t)ny, (cuuint64_t)nz};
+    const cuuint64_t strides[2] = {(cuuint64_t)2 * nx * sizeof(float), (cuuint64_t)2 * nx * ny * sizeof(float)};
+    const cuuint32_t box[3] = {(cuuint32_t)boxw, (cuuint32_t)boxh, 1};
+    const cuuint32_t es[3] = {1, 1, 1};
+    CUresult r = m->encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void*>(ptr), dims, strides, box, es,
+                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? HELM_OK : HELM_ERR_CUDA;
+}
+
 }  // namespace
 
-// Set the shared-memory limit of the kernels once per device (set-up time, not inside a capture).
-helm_status stencil_fast_prepare() {
+// Set-up (not inside a capture): the kernels' shared-memory limits and, for even N_x, the TMA descriptors
+// of the fixed operands (k^2 and the sixth-order fields).
+helm_status stencil_fast_prepare(helm_ctx* c) {
     HELM_CUDA_TRY(cudaFuncSetAttribute(stencil_fast_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)fast_smem<4>()));
     HELM_CUDA_TRY(cudaFuncSetAttribute(stencil_fast_kernel<6>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)fast_smem<6>()));
+    HELM_CUDA_TRY(cudaFuncSetAttribute(stencil_tma_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       TLayout<4>::SMEM));
+    HELM_CUDA_TRY(cudaFuncSetAttribute(stencil_tma_kernel<6>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       TLayout<6>::SMEM));
+    if (residual_fast_prepare() != HELM_OK) return HELM_ERR_CUDA;
+    if (c->nx % 2 != 0 || !stencil_fast_supported(c)) return HELM_OK;
+    FastMaps* m = new FastMaps();
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", (void**)&m->encode, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess || q != cudaDriverEntryPointSuccess || !m->encode) {
+        cudaGetLastError();
+        delete m;
+        return HELM_OK;   // no TMA descriptors: the cp.async kernel serves
+    }
+    helm_status st = encode3(m, &m->mK, c->k2_f, c->nx, c->ny, c->nz, 2 * TPX, FPY);
+    if (st == HELM_OK && c->opt.order == 6) {
+        const float2* f[4] = {c->G_f, c->dk2_f[0], c->dk2_f[1], c->dk2_f[2]};
+        for (int i = 0; i < 4 && st == HELM_OK; ++i) st = encode3(m, &m->mF[i], f[i], c->nx, c->ny, c->nz, 2 * FTX, FTY);
+    } else if (st == HELM_OK) {
+        for (int i = 0; i < 4; ++i) m->mF[i] = m->mK;   // unused by the fourth-order kernel
+    }
+    if (st != HELM_OK) { delete m; return HELM_OK; }
+    c->sfast = m;
     return HELM_OK;
 }
 
+void stencil_fast_release(helm_ctx* c) {
+    delete (FastMaps*)c->sfast;
+    c->sfast = nullptr;
+}
+
 bool stencil_fast_supported(const helm_ctx* c) { return c->opt.order == 4 || c->opt.order == 6; }
+
+// Variants of the complex64 matvec a context can run: 0 = cp.async ring (always), 1 = TMA ring (even N_x).
+int stencil_variants(const helm_ctx* c) { return c->sfast ? 2 : 1; }
 
 helm_status launch_stencil_fast(helm_ctx* c, const float2* x, float2* y, const double* sigma, int sidx, cudaStream_t s) {
     FParams p;
@@ -244,10 +510,293 @@ helm_status launch_stencil_fast(helm_ctx* c, const float2* x, float2* y, const d
     p.fld[0] = c->G_f;
     for (int d = 0; d < 3; ++d) p.fld[d + 1] = c->dk2_f[d];
     dim3 grid((c->nx + FTX - 1) / FTX, (c->ny + FTY - 1) / FTY, (c->nz + FZCH - 1) / FZCH), block(FTX, FTY);
+    if (c->sfast && c->tune_stencil == 1) {
+        FastMaps* m = (FastMaps*)c->sfast;
+        CUtensorMap mU;
+        if (encode3(m, &mU, x, c->nx, c->ny, c->nz, 2 * TPX, FPY) == HELM_OK) {
+            if (c->opt.order == 6)
+                stencil_tma_kernel<6><<<grid, block, TLayout<6>::SMEM, s>>>(mU, m->mK, m->mF[0], m->mF[1], m->mF[2],
+                                                                           m->mF[3], p, y, sigma, sidx, c->status_d);
+            else
+                stencil_tma_kernel<4><<<grid, block, TLayout<4>::SMEM, s>>>(mU, m->mK, m->mF[0], m->mF[1], m->mF[2],
+                                                                           m->mF[3], p, y, sigma, sidx, c->status_d);
+            HELM_CUDA_TRY(cudaGetLastError());
+            return HELM_OK;
+        }
+    }
     if (c->opt.order == 6)
         stencil_fast_kernel<6><<<grid, block, fast_smem<6>(), s>>>(p, x, y, sigma, sidx);
     else
         stencil_fast_kernel<4><<<grid, block, fast_smem<4>(), s>>>(p, x, y, sigma, sidx);
+    HELM_CUDA_TRY(cudaGetLastError());
+    return HELM_OK;
+}
+
+// ---- the true residual r = F - A x in double-float -------------------------------------------
+// Same plane-quantity form and z-march as the complex64 matvec, with x, k^2, G and F in double-float
+// (float4: re.hi, im.hi, re.lo, im.lo) and every term of A in double-float except the gradient terms
+// (h/20) g_d D_d, below 1e-3 of the total, which take the leading parts in FP32.  Planes stream into a
+// four-slot ring by 16-byte cp.async of the clamped halo points; a prepare pass per plane applies the
+// ghost factors (double-float) and forms KU = k^2 U once per staged point.  Writes r rounded to complex64
+// and per-CTA partial sums of |r|^2 and max |r| in FP64.
+#include "dfloat.cuh"
+
+namespace {
+
+template <int ORDER>
+struct RStage {
+    float4 u[FHALO];
+    float4 k[FHALO];
+    float4 F[FNT];
+    float4 G[ORDER == 6 ? FNT : 1];
+    float2 g[ORDER == 6 ? 3 : 1][ORDER == 6 ? FNT : 1];
+};
+
+struct RParams {
+    int nx, ny, nz;
+    cdf gx, gy, gz;
+    df ihx, ihy, ihz, wxy, wxz, wyz, h2_20;
+    float h_20, hh6;
+    const float4* k2;
+    const float4* G;
+    const float2* g[3];
+    const float4* F;
+};
+
+__device__ __forceinline__ void cp16(void* smem, const void* gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+// double-float constants, evaluated by the compiler
+constexpr df dfc(double v) { return df{(float)v, (float)(v - (double)(float)v)}; }
+template <int NUM, int DEN>
+__device__ __forceinline__ cdf cdf_sc(cdf a) {
+    constexpr df s = dfc((double)NUM / (double)DEN);
+    return cdf_scale(a, s);
+}
+__device__ __forceinline__ float2 hi2(cdf a) { return make_float2(a.re.hi, a.im.hi); }
+
+template <int ORDER>
+__global__ void __launch_bounds__(FNT, 2)
+residual_fast_kernel(RParams p, const float4* __restrict__ X, float2* __restrict__ rout, double* __restrict__ part) {
+    extern __shared__ __align__(16) unsigned char rsm[];
+    RStage<ORDER>* ring = reinterpret_cast<RStage<ORDER>*>(rsm);
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * FTX + tx;
+    const int x0 = blockIdx.x * FTX, y0 = blockIdx.y * FTY;
+    const int z0 = blockIdx.z * FZCH;
+    const int z1 = min(z0 + FZCH, p.nz);
+    const int gx = x0 + tx, gy = y0 + ty;
+    const bool active = gx < p.nx && gy < p.ny;
+    // this thread's staging slots (fixed across planes): clamped in-plane offset and the x/y ghost factor
+    size_t soff[2] = {0, 0};
+    int sfix[2] = {0, 0};
+    cdf sgam[2];
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const int q = tid + k * FNT;
+        sgam[k] = cdf{df{1.f, 0.f}, df{0.f, 0.f}};
+        if (q < FHALO) {
+            const int ly = q / FPX, lx = q - ly * FPX;
+            const int Xg = x0 + lx - 1, Yg = y0 + ly - 1;
+            const int Xc = min(max(Xg, 0), p.nx - 1), Yc = min(max(Yg, 0), p.ny - 1);
+            soff[k] = (size_t)Yc * p.nx + Xc;
+            if (Xc != Xg) { sgam[k] = p.gx; sfix[k] = 1; }
+            if (Yc != Yg) { sgam[k] = sfix[k] ? cdf_mul(sgam[k], p.gy) : p.gy; sfix[k] = 1; }
+        }
+    }
+    const size_t poff = (size_t)gy * p.nx + gx;
+    const size_t plane = (size_t)p.nx * p.ny;
+    auto issue = [&](int P) {
+        if (P <= z1) {
+            RStage<ORDER>& S = ring[(P + FNS) % FNS];
+            const int Pc = min(max(P, 0), p.nz - 1);
+            const size_t pb = (size_t)Pc * plane;
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+                const int q = tid + k * FNT;
+                if (q < FHALO) {
+                    cp16(&S.u[q], X + pb + soff[k]);
+                    cp16(&S.k[q], p.k2 + pb + soff[k]);
+                }
+            }
+            if (P >= z0 && P < z1 && active) {
+                const size_t g = (size_t)P * plane + poff;
+                cp16(&S.F[tid], p.F + g);
+                if (ORDER == 6) {
+                    cp16(&S.G[tid], p.G + g);
+#pragma unroll
+                    for (int d = 0; d < 3; ++d) cp8(&S.g[d][tid], p.g[d] + g);
+                }
+            }
+        }
+        cp_commit();
+    };
+
+    cdf cA = cdf_zero(), nA = cdf_zero();
+    float2 cX = make_float2(0, 0), cY = cX, cZ = cX, nX = cX, nY = cX, nZ = cX;
+    double ssum = 0.0, smax = 0.0;
+    issue(z0 - 1);
+    issue(z0);
+    for (int P = z0 - 1; P <= z1; ++P) {
+        RStage<ORDER>& S = ring[(P + FNS) % FNS];
+        cp_wait1();
+        __syncthreads();          // plane P landed for every thread; everyone is done with plane P-1
+        const bool zghost = P < 0 || P >= p.nz;
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            const int q = tid + k * FNT;
+            if (q < FHALO) {
+                cdf u = cdf_from4(S.u[q]);
+                if (sfix[k]) u = cdf_mul(u, sgam[k]);
+                if (zghost) u = cdf_mul(u, p.gz);
+                if (sfix[k] || zghost) S.u[q] = cdf_to4(u);
+                S.k[q] = cdf_to4(cdf_mul(cdf_from4(S.k[q]), u));
+            }
+        }
+        __syncthreads();          // U with ghosts and KU of plane P ready
+        issue(P + 2);             // into the slot of plane P-2, which nobody reads any more
+        cdf c, fx, fy, e, kc, kf4, kcs;
+        float2 dx1, dy1, tdx, tdy, dkx, dky;
+        {
+            auto U = [&](int b, int a) { return cdf_from4(S.u[(ty + b) * FPX + tx + a]); };
+            auto K = [&](int b, int a) { return cdf_from4(S.k[(ty + b) * FPX + tx + a]); };
+            const cdf u10 = U(1, 0), u12 = U(1, 2), u01 = U(0, 1), u21 = U(2, 1);
+            const cdf u00 = U(0, 0), u02 = U(0, 2), u20 = U(2, 0), u22 = U(2, 2);
+            c = U(1, 1);
+            fx = cdf_add(u10, u12);
+            fy = cdf_add(u01, u21);
+            e = cdf_add(cdf_add(u00, u02), cdf_add(u20, u22));
+            dx1 = f2sub(hi2(u12), hi2(u10));
+            dy1 = f2sub(hi2(u21), hi2(u01));
+            tdx = f2sub(f2add(hi2(u02), hi2(u22)), f2add(hi2(u00), hi2(u20)));
+            tdy = f2sub(f2add(hi2(u20), hi2(u22)), f2add(hi2(u00), hi2(u02)));
+            const cdf k10 = K(1, 0), k12 = K(1, 2), k01 = K(0, 1), k21 = K(2, 1);
+            kc = K(1, 1);
+            kf4 = cdf_add(cdf_add(k10, k12), cdf_add(k01, k21));
+            dkx = f2sub(hi2(k12), hi2(k10));
+            dky = f2sub(hi2(k21), hi2(k01));
+            if (ORDER == 6) kcs = cdf_add(cdf_add(K(0, 0), K(0, 2)), cdf_add(K(2, 0), K(2, 2)));
+        }
+        const bool out_prev = P - 1 >= z0 && P - 1 < z1;
+        const bool do_mid = P >= z0 && P < z1;
+        const RStage<ORDER>& Sp = ring[(P - 1 + FNS) % FNS];
+        const cdf fxy = cdf_add(fx, fy);
+        cdf As;
+        float2 Xs = make_float2(0, 0), Ys = Xs, Zs = Xs;
+        if (ORDER == 6) {
+            As = cdf_scale(cdf_add(cdf_add(cdf_sc<7, 15>(c), cdf_sc<1, 10>(fxy)), cdf_sc<1, 30>(e)), p.ihx);
+            As = cdf_add(As, cdf_sc<1, 90>(cdf_sub(kf4, kc)));
+            Xs = f2scl(dx1, 1.f / 6.f);
+            Ys = f2scl(dy1, 1.f / 6.f);
+            const float2 ch = hi2(c);
+            Zs = f2add(f2fma(p.hh6, hi2(kc), ch), f2scl(f2fma(-4.f, ch, hi2(fxy)), 1.f / 6.f));
+        } else {
+            const cdf c2 = cdf_add(c, c);
+            As = cdf_add(cdf_add(cdf_scale(c, p.ihz), cdf_scale(cdf_sub(fx, c2), p.wxz)),
+                         cdf_add(cdf_scale(cdf_sub(fy, c2), p.wyz), cdf_sc<1, 12>(kc)));
+        }
+        if (out_prev) {
+            cdf A = cdf_add(cA, As);
+            if (ORDER == 6) {
+                float2 g = f2mul(Sp.g[0][tid], f2add(cX, Xs));
+                g = f2add(g, f2mul(Sp.g[1][tid], f2add(cY, Ys)));
+                g = f2add(g, f2mul(Sp.g[2][tid], f2add(cZ, Zs)));
+                A = cdf_add(A, cdf_from_f2(f2scl(g, p.h_20)));
+            }
+            if (active) {
+                const cdf r = cdf_sub(cdf_from4(Sp.F[tid]), A);
+                const float2 rf = cdf_round(r);
+                rout[(size_t)(P - 1) * plane + poff] = rf;
+                const double a2 = (double)rf.x * rf.x + (double)rf.y * rf.y;
+                ssum += a2;
+                smax = fmax(smax, a2);
+            }
+        }
+        cA = nA; cX = nX; cY = nY; cZ = nZ;
+        if (do_mid) {
+            if (ORDER == 6) {
+                cdf Am = cdf_scale(cdf_sub(cdf_add(cdf_sc<7, 15>(fxy), cdf_sc<1, 10>(e)), cdf_sc<64, 15>(c)),
+                                   p.ihx);
+                Am = cdf_add(Am, cdf_add(cdf_sc<14, 15>(kc), cdf_sc<1, 90>(cdf_sub(kcs, kf4))));
+                Am = cdf_add(Am, cdf_scale(cdf_mul(cdf_from4(S.G[tid]), c), p.h2_20));
+                const float2 Xm = f2add(f2fma(p.hh6, dkx, dx1), f2scl(f2fma(-4.f, dx1, tdx), 1.f / 6.f));
+                const float2 Ym = f2add(f2fma(p.hh6, dky, dy1), f2scl(f2fma(-4.f, dy1, tdy), 1.f / 6.f));
+                cA = cdf_add(cA, Am);
+                cX = f2add(cX, Xm);
+                cY = f2add(cY, Ym);
+            } else {
+                const cdf c2 = cdf_add(c, c), c4 = cdf_add(c2, c2);
+                cdf Am = cdf_add(cdf_scale(cdf_sub(fx, c2), p.ihx), cdf_scale(cdf_sub(fy, c2), p.ihy));
+                Am = cdf_sub(Am, cdf_scale(c2, p.ihz));
+                Am = cdf_add(Am, cdf_scale(cdf_add(cdf_sub(e, cdf_add(fxy, fxy)), c4), p.wxy));
+                Am = cdf_add(Am, cdf_scale(cdf_sub(c4, cdf_add(fx, fx)), p.wxz));
+                Am = cdf_add(Am, cdf_scale(cdf_sub(c4, cdf_add(fy, fy)), p.wyz));
+                Am = cdf_add(Am, cdf_add(cdf_sc<1, 2>(kc), cdf_sc<1, 12>(kf4)));
+                cA = cdf_add(cA, Am);
+            }
+        }
+        nA = As; nX = Xs; nY = Ys; nZ = make_float2(-Zs.x, -Zs.y);
+    }
+    __shared__ double rs[FNT / 32], rm[FNT / 32];
+    for (int o = 16; o > 0; o >>= 1) {
+        ssum += __shfl_down_sync(0xffffffffu, ssum, o);
+        smax = fmax(smax, __shfl_down_sync(0xffffffffu, smax, o));
+    }
+    if ((tid & 31) == 0) { rs[tid >> 5] = ssum; rm[tid >> 5] = smax; }
+    __syncthreads();
+    if (tid == 0) {
+        double s = 0, m = 0;
+        for (int w = 0; w < FNT / 32; ++w) { s += rs[w]; m = fmax(m, rm[w]); }
+        const int cta = (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+        part[2 * cta] = s;
+        part[2 * cta + 1] = sqrt(m);
+    }
+}
+
+template <int ORDER>
+int rsmem() { return (int)(FNS * sizeof(RStage<ORDER>)); }
+
+cdf cdf_host(double2 v) {
+    const float rh = (float)v.x, ih = (float)v.y;
+    return cdf{df{rh, (float)(v.x - (double)rh)}, df{ih, (float)(v.y - (double)ih)}};
+}
+df df_host(double v) {
+    const float h = (float)v;
+    return df{h, (float)(v - (double)h)};
+}
+
+}  // namespace
+
+helm_status residual_fast_prepare() {
+    HELM_CUDA_TRY(cudaFuncSetAttribute(residual_fast_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, rsmem<4>()));
+    HELM_CUDA_TRY(cudaFuncSetAttribute(residual_fast_kernel<6>, cudaFuncAttributeMaxDynamicSharedMemorySize, rsmem<6>()));
+    return HELM_OK;
+}
+
+// grid of the residual kernels: 32 x 8 columns, 32-plane chunks (one partial pair per CTA)
+helm_status launch_residual_fast(helm_ctx* c, const float4* x, const float4* F, float2* r, double* part,
+                                 cudaStream_t s) {
+    RParams p;
+    p.nx = c->nx; p.ny = c->ny; p.nz = c->nz;
+    p.gx = cdf_host(c->gam[0]); p.gy = cdf_host(c->gam[1]); p.gz = cdf_host(c->gam[2]);
+    const double hx = c->h[0], hy = c->h[1], hz = c->h[2];
+    const double ihx = 1.0 / (hx * hx), ihy = 1.0 / (hy * hy), ihz = 1.0 / (hz * hz);
+    p.ihx = df_host(ihx); p.ihy = df_host(ihy); p.ihz = df_host(ihz);
+    p.wxy = df_host((hx * hx + hy * hy) / 12.0 * ihx * ihy);
+    p.wxz = df_host((hx * hx + hz * hz) / 12.0 * ihx * ihz);
+    p.wyz = df_host((hy * hy + hz * hz) / 12.0 * ihy * ihz);
+    p.h2_20 = df_host(hx * hx / 20.0);
+    p.h_20 = (float)(hx / 20.0);
+    p.hh6 = (float)(hx * hx / 6.0);
+    p.k2 = c->k2_df;
+    p.G = c->G_df;
+    for (int d = 0; d < 3; ++d) p.g[d] = c->dk2_f[d];
+    p.F = F;
+    dim3 grid((c->nx + FTX - 1) / FTX, (c->ny + FTY - 1) / FTY, (c->nz + FZCH - 1) / FZCH), block(FTX, FTY);
+    if (c->opt.order == 6)
+        residual_fast_kernel<6><<<grid, block, rsmem<6>(), s>>>(p, x, r, part);
+    else
+        residual_fast_kernel<4><<<grid, block, rsmem<4>(), s>>>(p, x, r, part);
     HELM_CUDA_TRY(cudaGetLastError());
     return HELM_OK;
 }
