@@ -460,7 +460,7 @@ def run_batched(args, rank, world, local):
             "iterations_total": sum(its_all) // max(1, args.steps), "status_nonzero": sum(1 for v in stat_all if v),
             "sequential": {"seconds": seq_s, "Mpts_iter_s": seq_its / seq_s / 1e6,
                            "speedup_of_batched": seq_s / (elapsed / args.steps)},
-            "autotuned_nb": sorted(set(tune)), "setup_s": setup_s, "plan_s": plan_s,
+            "autotuned_nb": sorted(set(t[0] for t in tune)), "autotuned_matvec": sorted(set(t[1] for t in tune)), "setup_s": setup_s, "plan_s": plan_s,
             "plan": "helm_batch (built once)" if plan is not None else "helm_gmres_solve_batched (groups per call)",
             "clocks": clk, "gpu_launches": launches,
             "roofline": None, "cpu_baseline": None, "e2e": None})

@@ -625,7 +625,7 @@ std::map<TuneKey, TuneVal> g_tune_cache;
 
 }  // namespace
 
-extern "C" helm_status helm_autotune(helm_ctx* c, int* nb_out, void* stream) {
+extern "C" helm_status helm_autotune(helm_ctx* c, int* nb_out, int* variant_out, void* stream) {
     if (!c) return HELM_ERR_ARG;
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
@@ -634,6 +634,7 @@ extern "C" helm_status helm_autotune(helm_ctx* c, int* nb_out, void* stream) {
             c->tune_nb = it->second.nb;
             c->tune_stencil = std::min(it->second.stencil, stencil_variants(c) - 1);
             if (nb_out) *nb_out = c->tune_nb;
+            if (variant_out) *variant_out = c->tune_stencil;
             return HELM_OK;
         }
     }
@@ -706,6 +707,7 @@ extern "C" helm_status helm_autotune(helm_ctx* c, int* nb_out, void* stream) {
         g_tune_cache[TuneKey{c->nx, c->ny, c->nz, c->opt.order}] = TuneVal{best, best_st};
     }
     if (nb_out) *nb_out = best;
+    if (variant_out) *variant_out = best_st;
     return HELM_OK;
 }
 

@@ -26,8 +26,9 @@
 //     written as gamma-multiples of their interior neighbours, U and KU alike (KU is linear in U and k^2
 //     at a ghost is the mirror value), and the ghost planes z = -1, N_z come from the clamped plane times
 //     gamma_z.
-//   cp.async kernel (odd N_x): 8-byte cp.async of the clamped halo points, ghost factors applied as the
-//     thread lifts its patch.
+//   cp.async kernel: 8-byte cp.async of the clamped halo points (each thread stages the same points of
+//     every plane, so their offsets and ghost factors are computed once); a prepare pass per plane
+//     applies the ghost factors and forms KU = k^2 U once per staged point.
 #include "common.cuh"
 #include <cuda.h>
 #include <cudaTypedefs.h>
@@ -75,8 +76,8 @@ __device__ __forceinline__ float2 f2mul(float2 a, float2 b) {
     return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
 }
 
-template <int ORDER>
-__global__ void __launch_bounds__(FNT, 4)
+template <int ORDER, int MINB>
+__global__ void __launch_bounds__(FNT, MINB)
 stencil_fast_kernel(FParams p, const float2* __restrict__ U, float2* __restrict__ Y, const double* __restrict__ sigma,
                     int sidx) {
     extern __shared__ __align__(16) unsigned char fsm[];
@@ -87,25 +88,37 @@ stencil_fast_kernel(FParams p, const float2* __restrict__ U, float2* __restrict_
     const int z1 = min(z0 + FZCH, p.nz);
     const int gx = x0 + tx, gy = y0 + ty;
     const bool active = gx < p.nx && gy < p.ny;
-    const bool xyedge = gx == 0 || gx == p.nx - 1 || gy == 0 || gy == p.ny - 1;
     const float sg = sigma ? (float)sigma[sidx] : 1.f;
+    // this thread's staging slots (fixed across planes): clamped in-plane offset in the low 30 bits,
+    // bit 30 = x ghost, bit 31 = y ghost
+    unsigned sl[2] = {0u, 0u};
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const int q = tid + k * FNT;
+        if (q < FHALO) {
+            const int ly = q / FPX, lx = q - ly * FPX;
+            const int Xg = x0 + lx - 1, Yg = y0 + ly - 1;
+            const int Xc = min(max(Xg, 0), p.nx - 1), Yc = min(max(Yg, 0), p.ny - 1);
+            sl[k] = (unsigned)(Yc * p.nx + Xc) | (Xc != Xg ? 1u << 30 : 0u) | (Yc != Yg ? 1u << 31 : 0u);
+        }
+    }
+    const size_t plane = (size_t)p.nx * p.ny;
+    const int poff = gy * p.nx + gx;
 
-    // stage plane P (ghost planes P = -1, nz come from the clamped plane) into its ring slot
     auto issue = [&](int P) {
         if (P <= z1) {
             FStage<ORDER>& S = ring[(P + FNS) % FNS];
             const int Pc = min(max(P, 0), p.nz - 1);
-            const size_t pbase = (size_t)Pc * p.ny;
-            for (int q = tid; q < FHALO; q += FNT) {
-                const int ly = q / FPX, lx = q - ly * FPX;
-                const int X = min(max(x0 + lx - 1, 0), p.nx - 1);
-                const int Yc = min(max(y0 + ly - 1, 0), p.ny - 1);
-                const size_t g = (pbase + Yc) * p.nx + X;
-                cp8(&S.u[q], U + g);
-                cp8(&S.k[q], p.k2 + g);
-            }
+            const float2* Ub = U + (size_t)Pc * plane;
+            const float2* Kb = p.k2 + (size_t)Pc * plane;
+#pragma unroll
+            for (int k = 0; k < 2; ++k)
+                if (tid + k * FNT < FHALO) {
+                    cp8(&S.u[tid + k * FNT], Ub + (sl[k] & 0x3FFFFFFFu));
+                    cp8(&S.k[tid + k * FNT], Kb + (sl[k] & 0x3FFFFFFFu));
+                }
             if (ORDER == 6 && P >= z0 && P < z1 && active) {
-                const size_t g = (pbase + gy) * p.nx + gx;
+                const size_t g = (size_t)P * plane + poff;
 #pragma unroll
                 for (int f = 0; f < 4; ++f) cp8(&S.f[f][tid], p.fld[f] + g);
             }
@@ -120,35 +133,37 @@ stencil_fast_kernel(FParams p, const float2* __restrict__ U, float2* __restrict_
     issue(z0 - 1);
     issue(z0);
     for (int P = z0 - 1; P <= z1; ++P) {
+        FStage<ORDER>& S = ring[(P + FNS) % FNS];
         cp_wait1();          // plane P has landed (only plane P+1 may still be in flight)
-        __syncthreads();     // ... for every thread; and every thread is done with plane P-2's slot
-        issue(P + 2);
-        const FStage<ORDER>& S = ring[(P + FNS) % FNS];
-        // the 3x3 patch of U (ghost factors applied) and the sums of KU = k^2 U the scheme needs
+        __syncthreads();     // ... for every thread; and every thread is done with plane P-1
+        // prepare this thread's staged points: ghost factors, then KU = k^2 U once per point
         const bool zghost = P < 0 || P >= p.nz;
-        const bool fix = xyedge || zghost;
-        const float2 one = make_float2(1.f, 0.f);
-        const float2 fz = zghost ? p.gz : one;
-        const float2 fxm = gx == 0 ? p.gx : one, fxp = gx == p.nx - 1 ? p.gx : one;
-        const float2 fym = gy == 0 ? p.gy : one, fyp = gy == p.ny - 1 ? p.gy : one;
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            const int q = tid + k * FNT;
+            if (q < FHALO) {
+                float2 u = S.u[q];
+                if ((sl[k] >> 30) || zghost) {
+                    if (sl[k] & (1u << 30)) u = f2mul(u, p.gx);
+                    if (sl[k] & (1u << 31)) u = f2mul(u, p.gy);
+                    if (zghost) u = f2mul(u, p.gz);
+                    S.u[q] = u;
+                }
+                S.k[q] = f2mul(S.k[q], u);
+            }
+        }
+        __syncthreads();     // U and KU of plane P ready for every thread
+        issue(P + 2);        // into the slot of plane P-2, which nobody reads any more
         float2 u[3][3];
         float2 kc = make_float2(0, 0), kf4 = kc, kcs = kc, dkx = kc, dky = kc;
 #pragma unroll
         for (int b = 0; b < 3; ++b)
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
-                float2 v = S.u[(ty + b) * FPX + tx + a];
-                if (fix) {
-                    float2 f = fz;
-                    if (a == 0) f = f2mul(f, fxm);
-                    if (a == 2) f = f2mul(f, fxp);
-                    if (b == 0) f = f2mul(f, fym);
-                    if (b == 2) f = f2mul(f, fyp);
-                    v = f2mul(v, f);
-                }
-                u[b][a] = v;
+                const int i = (ty + b) * FPX + tx + a;
+                u[b][a] = S.u[i];
                 if (ORDER == 6 || a == 1 || b == 1) {
-                    const float2 kv = f2mul(S.k[(ty + b) * FPX + tx + a], v);
+                    const float2 kv = S.k[i];
                     if (a == 1 && b == 1) kc = kv;
                     else if (a == 1 || b == 1) kf4 = f2add(kf4, kv);
                     else kcs = f2add(kcs, kv);
@@ -178,7 +193,7 @@ stencil_fast_kernel(FParams p, const float2* __restrict__ U, float2* __restrict_
                 g = f2add(g, f2mul(Sp.f[2][tid], f2add(cY, Ys)));
                 g = f2add(g, f2mul(Sp.f[3][tid], f2add(cZ, Zs)));
                 const float2 v = f2fma(p.h_20, g, A);
-                if (active) Y[((size_t)(P - 1) * p.ny + gy) * p.nx + gx] = f2scl(v, sg);
+                if (active) Y[(size_t)(P - 1) * plane + poff] = f2scl(v, sg);
             }
             // the output at plane P: lo part (already in nxt) + this plane as mid
             cA = nA; cX = nX; cY = nY; cZ = nZ;
@@ -199,8 +214,7 @@ stencil_fast_kernel(FParams p, const float2* __restrict__ U, float2* __restrict_
             const float2 As = f2fma(1.f / 12.f, kc,
                                     f2add(f2scl(c, p.ihz),
                                           f2add(f2scl(f2fma(-2.f, c, fx), p.wxz), f2scl(f2fma(-2.f, c, fy), p.wyz))));
-            if (out_prev && active)
-                Y[((size_t)(P - 1) * p.ny + gy) * p.nx + gx] = f2scl(f2add(cA, As), sg);
+            if (out_prev && active) Y[(size_t)(P - 1) * plane + poff] = f2scl(f2add(cA, As), sg);
             cA = nA;
             if (do_mid) {
                 const float2 c2 = f2add(c, c), c4 = f2add(c2, c2);
@@ -451,15 +465,21 @@ helm_status encode3(FastMaps* m, CUtensorMap* map, const void* ptr, int nx, int 
 // Set-up (not inside a capture): the kernels' shared-memory limits and, for even N_x, the TMA descriptors
 // of the fixed operands (k^2 and the sixth-order fields).
 helm_status stencil_fast_prepare(helm_ctx* c) {
-    HELM_CUDA_TRY(cudaFuncSetAttribute(stencil_fast_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    HELM_CUDA_TRY(cudaFuncSetAttribute(stencil_fast_kernel<4, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)fast_smem<4>()));
-    HELM_CUDA_TRY(cudaFuncSetAttribute(stencil_fast_kernel<6>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    HELM_CUDA_TRY(cudaFuncSetAttribute(stencil_fast_kernel<6, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)fast_smem<6>()));
+    HELM_CUDA_TRY(cudaFuncSetAttribute(stencil_fast_kernel<4, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)fast_smem<4>()));
+    HELM_CUDA_TRY(cudaFuncSetAttribute(stencil_fast_kernel<6, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)fast_smem<6>()));
     HELM_CUDA_TRY(cudaFuncSetAttribute(stencil_tma_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        TLayout<4>::SMEM));
     HELM_CUDA_TRY(cudaFuncSetAttribute(stencil_tma_kernel<6>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        TLayout<6>::SMEM));
     if (residual_fast_prepare() != HELM_OK) return HELM_ERR_CUDA;
+    // measured default: the sixth-order kernel needs about 80 registers (three CTAs per SM, no spills)
+    c->tune_stencil = c->opt.order == 6 ? 2 : 0;
     if (c->nx % 2 != 0 || !stencil_fast_supported(c)) return HELM_OK;
     FastMaps* m = new FastMaps();
     cudaDriverEntryPointQueryResult q;
@@ -488,8 +508,9 @@ void stencil_fast_release(helm_ctx* c) {
 
 bool stencil_fast_supported(const helm_ctx* c) { return c->opt.order == 4 || c->opt.order == 6; }
 
-// Variants of the complex64 matvec a context can run: 0 = cp.async ring (always), 1 = TMA ring (even N_x).
-int stencil_variants(const helm_ctx* c) { return c->sfast ? 2 : 1; }
+// Variants of the complex64 matvec a context can run: 0 = cp.async ring at four CTAs per SM, 1 = TMA ring
+// (even N_x, else the same as 0), 2 = cp.async ring at three CTAs per SM with more registers.
+int stencil_variants(const helm_ctx* c) { (void)c; return 3; }
 
 helm_status launch_stencil_fast(helm_ctx* c, const float2* x, float2* y, const double* sigma, int sidx, cudaStream_t s) {
     FParams p;
@@ -524,10 +545,14 @@ helm_status launch_stencil_fast(helm_ctx* c, const float2* x, float2* y, const d
             return HELM_OK;
         }
     }
-    if (c->opt.order == 6)
-        stencil_fast_kernel<6><<<grid, block, fast_smem<6>(), s>>>(p, x, y, sigma, sidx);
-    else
-        stencil_fast_kernel<4><<<grid, block, fast_smem<4>(), s>>>(p, x, y, sigma, sidx);
+    const bool three = c->tune_stencil == 2;   // the variant with up to 85 registers, three CTAs per SM
+    if (c->opt.order == 6) {
+        if (three) stencil_fast_kernel<6, 3><<<grid, block, fast_smem<6>(), s>>>(p, x, y, sigma, sidx);
+        else stencil_fast_kernel<6, 4><<<grid, block, fast_smem<6>(), s>>>(p, x, y, sigma, sidx);
+    } else {
+        if (three) stencil_fast_kernel<4, 3><<<grid, block, fast_smem<4>(), s>>>(p, x, y, sigma, sidx);
+        else stencil_fast_kernel<4, 4><<<grid, block, fast_smem<4>(), s>>>(p, x, y, sigma, sidx);
+    }
     HELM_CUDA_TRY(cudaGetLastError());
     return HELM_OK;
 }
