@@ -33,6 +33,7 @@ struct Ctrl {
 
 struct KrylovWork {
     int m = 0, flexible = 0, NB = 0, nres = 0;
+    int NBd = 0;             // CTAs of the inner-product kernel: one full wave of resident CTAs
     size_t npts = 0;
     float2* V = nullptr;     // (m+1) stored vectors
     float2* Z = nullptr;     // m preconditioned vectors (flexible) or one scratch vector
@@ -380,10 +381,13 @@ void free_work(KrylovWork* k) {
     cudaFree(k->nzflag);
 }
 
+int dots_ctas(const helm_ctx* c);
+
 // Krylov workspace of restart length m for the context's grid; NB = CTAs of the Arnoldi kernels.
 helm_status alloc_work(helm_ctx* c, KrylovWork* k, int m, int flex, int NB) {
     k->m = m; k->flexible = flex; k->npts = c->npts;
     k->NB = NB;
+    k->NBd = dots_ctas(c);
     k->nres = residual_ctas(c);
     const size_t vb = c->npts * sizeof(float2);
     if (cudaMalloc(&k->V, vb * (m + 1)) != cudaSuccess) { cudaGetLastError(); return HELM_ERR_NOMEM; }
@@ -394,7 +398,7 @@ helm_status alloc_work(helm_ctx* c, KrylovWork* k, int m, int flex, int NB) {
     HELM_CUDA_TRY(cudaMalloc(&k->sn, sizeof(double2) * m));
     HELM_CUDA_TRY(cudaMalloc(&k->g, sizeof(double2) * (m + 1)));
     HELM_CUDA_TRY(cudaMalloc(&k->y, sizeof(double2) * m));
-    HELM_CUDA_TRY(cudaMalloc(&k->part, sizeof(double2) * (size_t)k->NB * (m + 1)));
+    HELM_CUDA_TRY(cudaMalloc(&k->part, sizeof(double2) * (size_t)std::max(k->NB, k->NBd) * (m + 1)));
     HELM_CUDA_TRY(cudaMalloc(&k->rpart, sizeof(double) * 2 * k->nres));
     HELM_CUDA_TRY(cudaMalloc(&k->coef, sizeof(float2) * (m + 1)));
     HELM_CUDA_TRY(cudaMalloc(&k->ctrl_d, sizeof(Ctrl)));
@@ -405,6 +409,18 @@ helm_status alloc_work(helm_ctx* c, KrylovWork* k, int m, int flex, int NB) {
     HELM_CUDA_TRY(cudaMemset(k->H, 0, sizeof(double2) * (m + 1) * m));
     HELM_CUDA_TRY(cudaMemset(k->ctrl_d, 0, sizeof(Ctrl)));
     return HELM_OK;
+}
+
+// The inner-product kernel holds eight compensated sums per thread (about 80 registers, three CTAs per
+// SM): a grid of exactly the resident CTAs avoids a partial second wave.
+int dots_ctas(const helm_ctx* c) {
+    int sms = 0, per = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, dots_kernel, NT, 0) != cudaSuccess || per < 1) {
+        cudaGetLastError();
+        per = 2;
+    }
+    return (sms > 0 ? sms : 148) * per;
 }
 
 int default_nb(const helm_ctx* c) {
@@ -512,10 +528,10 @@ helm_status gmres_run(helm_ctx* c, const double2* b_in, double2* x_in, helm_solv
                 const int passes = c->opt.reorth ? 2 : 1;
                 for (int pass = 0; pass < passes; ++pass) {
                     prof_begin(c, s, PROF_DOTS);
-                    dots_kernel<<<NB, NT, 0, s>>>(k->V, npts, j + 1, w, k->part, ld);
+                    dots_kernel<<<k->NBd, NT, 0, s>>>(k->V, npts, j + 1, w, k->part, ld);
                     prof_end(c, s);
                     prof_begin(c, s, PROF_SMALL);
-                    reduce_h_kernel<<<1, 256, 0, s>>>(k->part, NB, ld, j + 1, k->sigma, k->H + (size_t)j * (m + 1),
+                    reduce_h_kernel<<<1, 256, 0, s>>>(k->part, k->NBd, ld, j + 1, k->sigma, k->H + (size_t)j * (m + 1),
                                                       k->coef, pass == 0);
                     prof_end(c, s);
                     prof_begin(c, s, PROF_UPDATE);
@@ -810,8 +826,8 @@ helm_status lane_iteration(Lane& ln, int j, cudaGraphConditionalHandle hnext, in
     if ((st = launch_stencil_f32(c, z, w, nullptr, 0, s)) != HELM_OK) return st;
     const int passes = c->opt.reorth ? 2 : 1;
     for (int pass = 0; pass < passes; ++pass) {
-        dots_kernel<<<NB, NT, 0, s>>>(k->V, npts, j + 1, w, k->part, ld);
-        reduce_h_kernel<<<1, 256, 0, s>>>(k->part, NB, ld, j + 1, k->sigma, k->H + (size_t)j * (m + 1), k->coef,
+        dots_kernel<<<k->NBd, NT, 0, s>>>(k->V, npts, j + 1, w, k->part, ld);
+        reduce_h_kernel<<<1, 256, 0, s>>>(k->part, k->NBd, ld, j + 1, k->sigma, k->H + (size_t)j * (m + 1), k->coef,
                                           pass == 0);
         update_kernel<<<NB, NT, 0, s>>>(k->V, npts, j + 1, k->coef, w, k->part, ld);
     }
