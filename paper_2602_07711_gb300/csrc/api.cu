@@ -40,7 +40,7 @@ void free_ctx(helm_ctx* c) {
     prof_release(c);
     void* ps[] = {c->k2_d, c->k2_f, c->dk2_d[0], c->dk2_d[1], c->dk2_d[2], c->dk2_f[0], c->dk2_f[1], c->dk2_f[2],
                   c->G_d, c->G_f, c->Dx, c->Dy, c->Vx, c->Vxi, c->Vy, c->Vyi, c->XF, c->XI, c->YF, c->YI,
-                  c->dxs, c->dys, c->cz, c->tmp, c->status_d, c->k2_df, c->G_df, c->rhs_scratch};
+                  c->dxs, c->dys, c->cz, c->tmp, c->status_d, c->k2_df, c->G_df, c->rhs_scratch, c->zfac};
     for (void* p : ps) if (p) cudaFree(p);
     delete c;
 }
@@ -146,6 +146,7 @@ helm_status helm_setup(const helm_grid* grid, const void* k2, double k0, const d
         if (c->nx % 2 != 0) { free_ctx(c); return HELM_ERR_UNSUPPORTED; }
         TRY(tc_prepare(c, s));
     }
+    if (opt->precond == HELM_PRECOND_EIGT) TRY(zsolve_factor(c, s));
     if (opt->precond == HELM_PRECOND_PFFT) TRY(pfft_prepare(c, s));
     if (cudaStreamSynchronize(s) != cudaSuccess) { free_ctx(c); return HELM_ERR_CUDA; }
     *out = c;

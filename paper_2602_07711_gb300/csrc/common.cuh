@@ -117,6 +117,7 @@ struct helm_ctx {
     float2 *YF = nullptr, *YI = nullptr;    // A of the y-pass: V_y^-1 (forward), V_y (inverse)
     float2 *dxs = nullptr, *dys = nullptr;  // alpha_x D_x, alpha_y D_y
     float2 *cz = nullptr;                   // h_z^2 k0^2(z_l) - 2(alpha_x + alpha_y + 1)
+    float2 *zfac = nullptr;                 // Thomas factors m of the EigT z-systems, one per point
     // tensor-core operands (split TF32), allocated for the TC modes
     float *XFr = nullptr, *XIr = nullptr;   // real-embedded x-pass B, [2N][2K] K-major (hi, lo follow)
     float *YFr = nullptr, *YIr = nullptr;   // y-pass A: re and im planes [2][N][N] (hi, lo follow)
@@ -166,6 +167,7 @@ helm_status tc_ypass(helm_ctx* c, int inverse, const float2* in, float2* out, cu
 void tc_release(helm_ctx* c);
 // thomas.cu
 helm_status launch_zsolve(helm_ctx* c, const float2* in, float2* out, cudaStream_t s);
+helm_status zsolve_factor(helm_ctx* c, cudaStream_t s);
 helm_status launch_zsolve_gen(helm_ctx* c, const float2* in, float2* out, const float2* dxs, const float2* dys,
                               const float2* P, const float2* Q, cudaStream_t s);
 // pfft.cu

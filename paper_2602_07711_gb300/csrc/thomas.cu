@@ -12,6 +12,8 @@
 // neighbours' end values.  One thread per line solves that small block-tridiagonal interface system
 // (2 unknowns per chunk) from shared memory, and every thread then finishes its chunk by a Thomas sweep
 // with known boundary values.  HBM traffic is one read and one write per point (16 B/pt).
+// This partitioned kernel serves the PFFT z-solves (generated right-hand sides, other diagonals); the
+// EigT systems use the factorised form below.
 #include "common.cuh"
 
 namespace {
@@ -32,8 +34,13 @@ __device__ inline float2 f2(float a, float b) { return make_float2(a, b); }
 
 // a / b for the well-scaled pivots of these systems (|b| ~ 1e-3 .. 1e2): a conj(b) / |b|^2
 __device__ inline float2 qdiv(float2 a, float2 b) {
-    const float r = 1.f / fmaf(b.x, b.x, b.y * b.y);
+    const float r = __frcp_rn(fmaf(b.x, b.x, b.y * b.y));
     return make_float2((a.x * b.x + a.y * b.y) * r, (a.y * b.x - a.x * b.y) * r);
+}
+// 1 / b (one correctly rounded reciprocal; every division of an elimination step shares it)
+__device__ inline float2 crcp(float2 b) {
+    const float r = __frcp_rn(fmaf(b.x, b.x, b.y * b.y));
+    return make_float2(b.x * r, -b.y * r);
 }
 
 __device__ inline void note_pivot(float2 d, unsigned* status) {
@@ -94,11 +101,10 @@ zsolve_kernel(ZParams p, const float2* in, float2* out, unsigned* status) {
             const float a = sub(l);
             const float2 den = (k == 0) ? bd[k] : csub(bd[k], cscale(cp, a));
             piv(den);
-            const float2 nd = (k == 0) ? qdiv(y[k], den) : qdiv(csub(y[k], cscale(dp, a)), den);
-            const float2 nl = (k == 0) ? qdiv(f2(-a, 0.f), den) : qdiv(cscale(lp, -a), den);
-            cp = qdiv(f2(sup(l), 0.f), den);
-            dp = nd;
-            lp = nl;
+            const float2 ri = crcp(den);
+            dp = cmul((k == 0) ? y[k] : csub(y[k], cscale(dp, a)), ri);
+            lp = (k == 0) ? cscale(ri, -a) : cmul(cscale(lp, -a), ri);
+            cp = cscale(ri, sup(l));
         }
     }
     // up elimination with x_{e+1} as parameter: x_s = dh - ch x_{s-1} + rh x_{e+1}
@@ -112,11 +118,10 @@ zsolve_kernel(ZParams p, const float2* in, float2* out, unsigned* status) {
             const bool first = (k == len - 1);
             const float2 den = first ? bd[k] : csub(bd[k], cscale(ch, c));
             piv(den);
-            const float2 nd = first ? qdiv(y[k], den) : qdiv(csub(y[k], cscale(dh, c)), den);
-            const float2 nr = first ? qdiv(f2(-c, 0.f), den) : qdiv(cscale(rh, -c), den);
-            ch = qdiv(f2(sub(l), 0.f), den);
-            dh = nd;
-            rh = nr;
+            const float2 ri = crcp(den);
+            dh = cmul(first ? y[k] : csub(y[k], cscale(dh, c)), ri);
+            rh = first ? cscale(ri, -c) : cmul(cscale(rh, -c), ri);
+            ch = cscale(ri, sub(l));
         }
     }
     sh[0][w][lane] = dh;                       // g_s
@@ -172,8 +177,9 @@ zsolve_kernel(ZParams p, const float2* in, float2* out, unsigned* status) {
             float2 rhs = csub(y[k], cscale(d_prev, a));
             const bool last = (k == len - 1);
             if (last) rhs = csub(rhs, cscale(Rv, sup(l)));
-            cpk[k] = qdiv(f2(last ? 0.f : sup(l), 0.f), den);
-            y[k] = qdiv(rhs, den);
+            const float2 ri = crcp(den);
+            cpk[k] = cscale(ri, last ? 0.f : sup(l));
+            y[k] = cmul(rhs, ri);
             c_prev = cpk[k];
             d_prev = y[k];
         }
@@ -190,7 +196,102 @@ zsolve_kernel(ZParams p, const float2* in, float2* out, unsigned* status) {
     if (live && !(minpiv > 1e-30f)) atomicOr(status, (unsigned)HELM_DEV_PIVOT);
 }
 
+// ---- factorised z-solve (EigT) -------------------------------------------------------------------
+// The systems of a context never change, so their Thomas factorisation is computed once at set-up:
+//   m_l = 1 / (b_l - a_l c'_{l-1}),   c'_l = sup_l m_l,   (a_l, sup_l the sub- and super-diagonal)
+// and stored per point (complex64).  An application is then one thread per line: forward
+// d_l = (y_l - a_l d_{l-1}) m_l written over the output, backward x_l = d_l - sup_l m_l x_{l+1}, i.e.
+// one complex product per step and sweep, no divisions, no interface system.  The backward sweep
+// re-reads d and m soon after the forward sweep wrote/read them, mostly from L2.  Lines of consecutive
+// x are consecutive threads, so every step is a contiguous row access.
+constexpr int ZU = 8;   // steps whose loads are issued together
+
+__global__ void __launch_bounds__(128) zfactor_kernel(ZParams p, float2* __restrict__ m, unsigned* status) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
+    if (i >= p.nx) return;
+    const size_t plane = (size_t)p.nx * p.ny, base = (size_t)j * p.nx + i;
+    const float2 dxy = cadd(p.dxs[i], p.dys[j]);
+    float2 cprev = f2(0.f, 0.f);
+    float minpiv = 1e30f;
+    for (int l = 0; l < p.nz; ++l) {
+        float2 b = cadd(dxy, p.cz[l]);
+        if (l == 0 || l == p.nz - 1) b = cadd(b, p.gz);
+        const float a = l == 0 ? 0.f : (l == p.nz - 1 ? p.zz : 1.f);
+        const float sup = l == p.nz - 1 ? 0.f : (l == 0 ? p.zz : 1.f);
+        const float2 den = csub(b, cscale(cprev, a));
+        minpiv = fminf(minpiv, fabsf(den.x) + fabsf(den.y));
+        const float2 mi = crcp(den);
+        m[base + (size_t)l * plane] = mi;
+        cprev = cscale(mi, sup);
+    }
+    if (!(minpiv > 1e-30f)) atomicOr(status, (unsigned)HELM_DEV_PIVOT);
+}
+
+__global__ void __launch_bounds__(128) zsolve_fact_kernel(int nx, int ny, int nz, float zz, const float2* __restrict__ m,
+                                                         const float2* in, float2* out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
+    if (i >= nx) return;
+    const size_t plane = (size_t)nx * ny, base = (size_t)j * nx + i;
+    float2 d = f2(0.f, 0.f);
+    for (int l0 = 0; l0 < nz; l0 += ZU) {
+        float2 yv[ZU], mv[ZU];
+#pragma unroll
+        for (int u = 0; u < ZU; ++u)
+            if (l0 + u < nz) {
+                yv[u] = in[base + (size_t)(l0 + u) * plane];
+                mv[u] = m[base + (size_t)(l0 + u) * plane];
+            }
+#pragma unroll
+        for (int u = 0; u < ZU; ++u) {
+            const int l = l0 + u;
+            if (l < nz) {
+                const float a = l == 0 ? 0.f : (l == nz - 1 ? zz : 1.f);
+                d = cmul(csub(yv[u], cscale(d, a)), mv[u]);
+                out[base + (size_t)l * plane] = d;
+            }
+        }
+    }
+    float2 x = f2(0.f, 0.f);
+    for (int l1 = nz; l1 > 0; l1 -= ZU) {
+        float2 dv[ZU], mv[ZU];
+#pragma unroll
+        for (int u = 0; u < ZU; ++u) {
+            const int l = l1 - 1 - u;
+            if (l >= 0) {
+                dv[u] = out[base + (size_t)l * plane];
+                mv[u] = m[base + (size_t)l * plane];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < ZU; ++u) {
+            const int l = l1 - 1 - u;
+            if (l >= 0) {
+                const float sup = l == nz - 1 ? 0.f : (l == 0 ? zz : 1.f);
+                x = csub(dv[u], cscale(cmul(mv[u], x), sup));
+                out[base + (size_t)l * plane] = x;
+            }
+        }
+    }
+}
+
 }  // namespace
+
+// Set-up: the Thomas factors of the EigT z-systems (one complex64 per point).
+helm_status zsolve_factor(helm_ctx* c, cudaStream_t s) {
+    if (!c->zfac) {
+        if (cudaMalloc(&c->zfac, c->npts * sizeof(float2)) != cudaSuccess) { cudaGetLastError(); return HELM_ERR_NOMEM; }
+    }
+    ZParams p;
+    p.nx = c->nx; p.ny = c->ny; p.nz = c->nz;
+    p.dxs = c->dxs; p.dys = c->dys; p.cz = c->cz;
+    p.P = nullptr; p.Q = nullptr;
+    p.gz = make_float2((float)c->gam[2].x, (float)c->gam[2].y);
+    p.zz = (float)c->zeta[2];
+    dim3 grid((c->nx + 127) / 128, c->ny);
+    zfactor_kernel<<<grid, 128, 0, s>>>(p, c->zfac, c->status_d);
+    HELM_CUDA_TRY(cudaGetLastError());
+    return HELM_OK;
+}
 
 helm_status launch_zsolve_gen(helm_ctx* c, const float2* in, float2* out, const float2* dxs, const float2* dys,
                               const float2* P, const float2* Q, cudaStream_t s) {
@@ -217,5 +318,11 @@ helm_status launch_zsolve_gen(helm_ctx* c, const float2* in, float2* out, const 
 }
 
 helm_status launch_zsolve(helm_ctx* c, const float2* in, float2* out, cudaStream_t s) {
-    return launch_zsolve_gen(c, in, out, c->dxs, c->dys, nullptr, nullptr, s);
+    if (!c->zfac) return launch_zsolve_gen(c, in, out, c->dxs, c->dys, nullptr, nullptr, s);
+    prof_begin(c, s, PROF_ZSOLVE);
+    dim3 grid((c->nx + 127) / 128, c->ny);
+    zsolve_fact_kernel<<<grid, 128, 0, s>>>(c->nx, c->ny, c->nz, (float)c->zeta[2], c->zfac, in, out);
+    prof_end(c, s);
+    HELM_CUDA_TRY(cudaGetLastError());
+    return HELM_OK;
 }
