@@ -423,79 +423,85 @@ __global__ void derived_kernel(int order, int nx, int ny, int nz, double hx, dou
 // F from samples of f (double-float copy fdf), k^2 (double-float) and the FP32 gradients of k^2.
 // The terms of relative size ~(k h)^2 (lap f, k^2 f) are formed in double-float; the h^4 terms, three
 // orders smaller, in FP32 from the leading parts.  Mirror extension at the faces (reading).
-__global__ void rhs_df_kernel(int order, int nx, int ny, int nz, double hx, double hy, double hz,
-                              const float4* __restrict__ fdf, const float4* __restrict__ k2df,
-                              const float2* __restrict__ dkx, const float2* __restrict__ dky,
-                              const float2* __restrict__ dkz, double2* __restrict__ F) {
-    const size_t n = (size_t)nx * ny * nz;
-    const df c12 = PDF::cst(1.0 / 12.0);
-    for (size_t id = blockIdx.x * (size_t)blockDim.x + threadIdx.x; id < n; id += (size_t)gridDim.x * blockDim.x) {
-        const int i = (int)(id % nx), j = (int)((id / nx) % ny), l = (int)(id / ((size_t)nx * ny));
-        auto at = [&](int a, int b, int c) {
-            return cdf_from4(fdf[((size_t)mirror_stag(l + c, nz) * ny + mirror_stag(j + b, ny)) * nx + mirror_stag(i + a, nx)]);
-        };
-        const cdf fc = cdf_from4(fdf[id]);
-        if (order == 2) { F[id] = cdf_to_double2(fc); continue; }
-        if (order == 4) {
-            // f + (1/12) sum_d (f+ - 2f + f-)
-            cdf s = cdf_zero();
-    #pragma unroll
-        for (int d = 0; d < 3; ++d) {
-                int o[3] = {0, 0, 0};
-                o[d] = 1; s = cdf_add(s, at(o[0], o[1], o[2]));
-                o[d] = -1; s = cdf_add(s, at(o[0], o[1], o[2]));
-            }
-            const cdf c6 = cdf_add(cdf_add(fc, fc), cdf_add(cdf_add(fc, fc), cdf_add(fc, fc)));
-            F[id] = cdf_to_double2(cdf_add(fc, cdf_scale(cdf_sub(s, c6), c12)));
-            continue;
-        }
-        // order 6, uniform h: every term in double-float (for rough f the h^4 terms are not small)
-        const double h = hx, h2 = h * h;
-        const double hh[3] = {hx, hy, hz};
-        cdf lap = cdf_zero(), s4 = cdf_zero();
-        float2 fd[3];
+// weights of the right-hand side, formed once on the host (FP64 divisions are slow on this GPU)
+struct RhsW {
+    df c12;           // 1/12 (order 4)
+    df lap[3];        // h^2 / (144 h_d^2)
+    df s4[3];         // h^4 / (360 h_d^4)
+    df mix[3];        // h^4 / (90 h_a^2 h_b^2), pairs xy, xz, yz
+    df h2_20;         // h^2 / 20
+    float h4_60;      // h^4 / 60
+    float i2h[3];     // 1 / (2 h_d)
+};
+
+__global__ void rhs_df_kernel(int order, int nx, int ny, int nz, RhsW W, const float4* __restrict__ fdf,
+                              const float4* __restrict__ k2df, const float2* __restrict__ dkx,
+                              const float2* __restrict__ dky, const float2* __restrict__ dkz,
+                              double2* __restrict__ F) {
+    // one point per thread on a 3D grid (no index divisions)
+    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y, l = blockIdx.z;
+    if (i >= nx) return;
+    const size_t id = ((size_t)l * ny + j) * nx + i;
+    auto at = [&](int a, int b, int c) {
+        return cdf_from4(fdf[((size_t)mirror_stag(l + c, nz) * ny + mirror_stag(j + b, ny)) * nx + mirror_stag(i + a, nx)]);
+    };
+    const cdf fc = cdf_from4(fdf[id]);
+    if (order == 2) { F[id] = cdf_to_double2(fc); return; }
+    if (order == 4) {
+        // f + (1/12) sum_d (f+ - 2f + f-)
+        cdf s = cdf_zero();
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
             int o[3] = {0, 0, 0};
-            cdf v[5];
-#pragma unroll
-            for (int s = -2; s <= 2; ++s) { o[d] = s; v[s + 2] = at(o[0], o[1], o[2]); }
-            // (h^2/12) * (-f2 + 16 f1 - 30 f0 + 16 f-1 - f-2) / (12 h_d^2)
-            cdf t = cdf_sub(cdf_scale(cdf_add(v[3], v[1]), df{16.f, 0.f}), cdf_add(v[4], v[0]));
-            t = cdf_sub(t, cdf_scale(v[2], df{30.f, 0.f}));
-            lap = cdf_add(lap, cdf_scale(t, PDF::cst(h2 / (144.0 * hh[d] * hh[d]))));
-            // (h^4/360) * (f2 - 4 f1 + 6 f0 - 4 f-1 + f-2) / h_d^4
-            cdf q = cdf_sub(cdf_add(cdf_add(v[4], v[0]), cdf_scale(v[2], df{6.f, 0.f})),
-                            cdf_scale(cdf_add(v[3], v[1]), df{4.f, 0.f}));
-            s4 = cdf_add(s4, cdf_scale(q, PDF::cst(h2 * h2 / (360.0 * hh[d] * hh[d] * hh[d] * hh[d]))));
-            fd[d] = make_float2((v[3].re.hi - v[1].re.hi) / (float)(2 * hh[d]), (v[3].im.hi - v[1].im.hi) / (float)(2 * hh[d]));
+            o[d] = 1; s = cdf_add(s, at(o[0], o[1], o[2]));
+            o[d] = -1; s = cdf_add(s, at(o[0], o[1], o[2]));
         }
-        cdf mix = cdf_zero();
-        const int pairs[3][2] = {{0, 1}, {0, 2}, {1, 2}};
-        const float w[3] = {1.f, -2.f, 1.f};
-#pragma unroll
-        for (int q = 0; q < 3; ++q) {
-            cdf acc = cdf_zero();
-#pragma unroll
-            for (int s1 = -1; s1 <= 1; ++s1)
-#pragma unroll
-                for (int s2 = -1; s2 <= 1; ++s2) {
-                    int o[3] = {0, 0, 0};
-                    o[pairs[q][0]] = s1; o[pairs[q][1]] = s2;
-                    acc = cdf_add(acc, cdf_scale(at(o[0], o[1], o[2]), df{w[s1 + 1] * w[s2 + 1], 0.f}));
-                }
-            const double den = hh[pairs[q][0]] * hh[pairs[q][0]] * hh[pairs[q][1]] * hh[pairs[q][1]];
-            mix = cdf_add(mix, cdf_scale(acc, PDF::cst(h2 * h2 / (90.0 * den))));
-        }
-        const cdf kc = cdf_from4(k2df[id]);
-        cdf out = cdf_add(cdf_add(fc, lap), cdf_add(s4, mix));
-        out = cdf_sub(out, cdf_scale(cdf_mul(kc, fc), PDF::cst(h2 / 20.0)));
-        // (h^4/60) sum_d g_d f_d: gradients of k^2 are FP32 and this term is O((k h)^4) of f: FP32
-        const float h4 = (float)(h2 * h2);
-        const float2 g = cadd(cadd(cmul(dkx[id], fd[0]), cmul(dky[id], fd[1])), cmul(dkz[id], fd[2]));
-        out = cdf_add(out, cdf_from_f2(make_float2(h4 / 60.f * g.x, h4 / 60.f * g.y)));
-        F[id] = cdf_to_double2(out);
+        const cdf c6 = cdf_add(cdf_add(fc, fc), cdf_add(cdf_add(fc, fc), cdf_add(fc, fc)));
+        F[id] = cdf_to_double2(cdf_add(fc, cdf_scale(cdf_sub(s, c6), W.c12)));
+        return;
     }
+    // order 6, uniform h: every term in double-float (for rough f the h^4 terms are not small)
+    cdf lap = cdf_zero(), s4 = cdf_zero();
+    float2 fd[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        int o[3] = {0, 0, 0};
+        cdf v[5];
+#pragma unroll
+        for (int q = -2; q <= 2; ++q) { o[d] = q; v[q + 2] = at(o[0], o[1], o[2]); }
+        // (h^2/12) * (-f2 + 16 f1 - 30 f0 + 16 f-1 - f-2) / (12 h_d^2)
+        cdf t = cdf_sub(cdf_scale(cdf_add(v[3], v[1]), df{16.f, 0.f}), cdf_add(v[4], v[0]));
+        t = cdf_sub(t, cdf_scale(v[2], df{30.f, 0.f}));
+        lap = cdf_add(lap, cdf_scale(t, W.lap[d]));
+        // (h^4/360) * (f2 - 4 f1 + 6 f0 - 4 f-1 + f-2) / h_d^4
+        cdf q4 = cdf_sub(cdf_add(cdf_add(v[4], v[0]), cdf_scale(v[2], df{6.f, 0.f})),
+                         cdf_scale(cdf_add(v[3], v[1]), df{4.f, 0.f}));
+        s4 = cdf_add(s4, cdf_scale(q4, W.s4[d]));
+        fd[d] = make_float2((v[3].re.hi - v[1].re.hi) * W.i2h[d], (v[3].im.hi - v[1].im.hi) * W.i2h[d]);
+    }
+    cdf mix = cdf_zero();
+    const int pairs[3][2] = {{0, 1}, {0, 2}, {1, 2}};
+    const float w[3] = {1.f, -2.f, 1.f};
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        cdf acc = cdf_zero();
+#pragma unroll
+        for (int s1 = -1; s1 <= 1; ++s1)
+#pragma unroll
+            for (int s2 = -1; s2 <= 1; ++s2) {
+                int o[3] = {0, 0, 0};
+                o[pairs[q][0]] = s1; o[pairs[q][1]] = s2;
+                acc = cdf_add(acc, cdf_scale(at(o[0], o[1], o[2]), df{w[s1 + 1] * w[s2 + 1], 0.f}));
+            }
+        mix = cdf_add(mix, cdf_scale(acc, W.mix[q]));
+    }
+    const cdf kc = cdf_from4(k2df[id]);
+    cdf out = cdf_add(cdf_add(fc, lap), cdf_add(s4, mix));
+    out = cdf_sub(out, cdf_scale(cdf_mul(kc, fc), W.h2_20));
+    // (h^4/60) sum_d g_d f_d: gradients of k^2 are FP32 and this term is O((k h)^4) of f: FP32
+    const float2 g = cadd(cadd(cmul(dkx[id], fd[0]), cmul(dky[id], fd[1])), cmul(dkz[id], fd[2]));
+    out = cdf_add(out, cdf_from_f2(make_float2(W.h4_60 * g.x, W.h4_60 * g.y)));
+    F[id] = cdf_to_double2(out);
 }
 
 __global__ void f64_to_df_kernel(const double2* __restrict__ a, float4* __restrict__ b, size_t n) {
@@ -588,7 +594,22 @@ helm_status launch_residual(helm_ctx* c, const float4* x, const float4* F, float
 helm_status launch_rhs(helm_ctx* c, const double2* f, double2* F, float4* fdf, cudaStream_t s) {
     prof_begin(c, s, PROF_OTHER);
     f64_to_df_kernel<<<1024, 256, 0, s>>>(f, fdf, c->npts);
-    rhs_df_kernel<<<2048, 256, 0, s>>>(c->opt.order, c->nx, c->ny, c->nz, c->h[0], c->h[1], c->h[2], fdf, c->k2_df,
+    RhsW W;
+    const double hh[3] = {c->h[0], c->h[1], c->h[2]};
+    const double h2 = hh[0] * hh[0];
+    W.c12 = PDF::cst(1.0 / 12.0);
+    for (int d = 0; d < 3; ++d) {
+        W.lap[d] = PDF::cst(h2 / (144.0 * hh[d] * hh[d]));
+        W.s4[d] = PDF::cst(h2 * h2 / (360.0 * hh[d] * hh[d] * hh[d] * hh[d]));
+        W.i2h[d] = (float)(1.0 / (2.0 * hh[d]));
+    }
+    const int pr[3][2] = {{0, 1}, {0, 2}, {1, 2}};
+    for (int q = 0; q < 3; ++q)
+        W.mix[q] = PDF::cst(h2 * h2 / (90.0 * hh[pr[q][0]] * hh[pr[q][0]] * hh[pr[q][1]] * hh[pr[q][1]]));
+    W.h2_20 = PDF::cst(h2 / 20.0);
+    W.h4_60 = (float)(h2 * h2 / 60.0);
+    rhs_df_kernel<<<dim3((c->nx + 127) / 128, c->ny, c->nz), 128, 0, s>>>(c->opt.order, c->nx, c->ny, c->nz, W, fdf,
+                                                                         c->k2_df,
                                        c->dk2_f[0], c->dk2_f[1], c->dk2_f[2], F);
     prof_end(c, s);
     HELM_CUDA_TRY(cudaGetLastError());
