@@ -267,7 +267,15 @@ __global__ void __launch_bounds__(NT) combine_flex_kernel(const float2* __restri
     __syncthreads();
     for (size_t id = blockIdx.x * (size_t)NT + threadIdx.x; id < npts; id += (size_t)gridDim.x * NT) {
         cdf a = cdf_from4(x[id]);
-        for (int i = 0; i < k; ++i) a = cdf_add(a, cdf_mul_f2(ys[i], Z[(size_t)i * npts + id]));
+        int i = 0;
+        for (; i + 4 <= k; i += 4) {   // four loads in flight before the dependent double-float sums
+            float2 zv[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) zv[q] = Z[(size_t)(i + q) * npts + id];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) a = cdf_add(a, cdf_mul_f2(ys[i + q], zv[q]));
+        }
+        for (; i < k; ++i) a = cdf_add(a, cdf_mul_f2(ys[i], Z[(size_t)i * npts + id]));
         x[id] = cdf_to4(a);
     }
 }

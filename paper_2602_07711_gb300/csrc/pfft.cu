@@ -37,10 +37,13 @@ bool pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
 
 // ---- batched sine transforms ----------------------------------------------------------------------
 // In-place radix-2 Stockham FFT of `lines` sequences of length n = 2N in shared memory (line stride ls).
+__device__ __forceinline__ int ilog2(int v) { return 31 - __clz(v); }   // v a power of two
+
 __device__ void fft_smem(float2* buf, int lines, int n, int ls, const float2* tw) {
-    const int half = n / 2;
-    for (int Ns = 1; Ns < n; Ns *= 2) {
-        const int nb = lines * half;
+    const int half = n / 2, lh = ilog2(half);
+    const int nb = lines * half;
+    for (int lNs = 0; (1 << lNs) < n; ++lNs) {
+        const int Ns = 1 << lNs;
         // read phase (at most MAXB butterflies per thread: the launch keeps lines * n/2 <= MAXB * blockDim)
         constexpr int MAXB = 8;
         float2 a[MAXB], b[MAXB];
@@ -48,10 +51,10 @@ __device__ void fft_smem(float2* buf, int lines, int n, int ls, const float2* tw
         for (int c = 0; c < MAXB; ++c) {
             const int q = threadIdx.x + c * blockDim.x;
             if (q < nb) {
-                const int line = q / half, j = q - line * half;
+                const int line = q >> lh, j = q & (half - 1);
                 const int k = j & (Ns - 1);
                 const float2 x0 = buf[line * ls + j];
-                const float2 x1 = cmul(buf[line * ls + j + half], tw[k * (half / Ns)]);
+                const float2 x1 = cmul(buf[line * ls + j + half], tw[k << (lh - lNs)]);
                 a[c] = cadd(x0, x1);
                 b[c] = csub(x0, x1);
             }
@@ -61,8 +64,8 @@ __device__ void fft_smem(float2* buf, int lines, int n, int ls, const float2* tw
         for (int c = 0; c < MAXB; ++c) {
             const int q = threadIdx.x + c * blockDim.x;
             if (q < nb) {
-                const int line = q / half, j = q - line * half;
-                const int d = (j / Ns) * Ns * 2 + (j & (Ns - 1));
+                const int line = q >> lh, j = q & (half - 1);
+                const int d = ((j >> lNs) << (lNs + 1)) + (j & (Ns - 1));
                 buf[line * ls + d] = a[c];
                 buf[line * ls + d + Ns] = b[c];
             }
@@ -85,8 +88,9 @@ __global__ void __launch_bounds__(256) dst_x_kernel(const float2* __restrict__ i
     const long l0 = (long)blockIdx.x * lpb;
     const int nl = (int)min((long)lpb, lines - l0);
     const float sc = scale * (sigma ? (float)sigma[sidx] : 1.f);
+    const int lN = ilog2(N);
     for (int q = threadIdx.x; q < nl * N; q += blockDim.x) {
-        const int line = q / N, e = q - line * N;
+        const int line = q >> lN, e = q & (N - 1);
         const float2 v = in[(l0 + line) * N + e];
         float2* b = buf + line * ls;
         if (!INV) {
@@ -109,7 +113,7 @@ __global__ void __launch_bounds__(256) dst_x_kernel(const float2* __restrict__ i
     __syncthreads();
     fft_smem(buf, nl, n, ls, stw);
     for (int q = threadIdx.x; q < nl * N; q += blockDim.x) {
-        const int line = q / N, e = q - line * N;
+        const int line = q >> lN, e = q & (N - 1);
         const float2* b = buf + line * ls;
         float2 r;
         if (!INV) {
@@ -135,8 +139,9 @@ __global__ void __launch_bounds__(256) dst_y_kernel(const float2* __restrict__ i
     const int i0 = blockIdx.x * ti, l = blockIdx.y;
     const int nt = min(ti, nx - i0);
     const size_t sbase = (size_t)l * N * nx;
+    const int lt = ilog2(ti);
     for (int q = threadIdx.x; q < N * ti; q += blockDim.x) {
-        const int e = q / ti, t = q - e * ti;     // consecutive threads: consecutive columns (coalesced)
+        const int e = q >> lt, t = q & (ti - 1);  // consecutive threads: consecutive columns (coalesced)
         if (t >= nt) continue;
         const float2 v = in[sbase + (size_t)e * nx + i0 + t];
         float2* b = buf + t * ls;
@@ -159,7 +164,7 @@ __global__ void __launch_bounds__(256) dst_y_kernel(const float2* __restrict__ i
     __syncthreads();
     fft_smem(buf, nt, n, ls, stw);
     for (int q = threadIdx.x; q < N * ti; q += blockDim.x) {
-        const int e = q / ti, t = q - e * ti;
+        const int e = q >> lt, t = q & (ti - 1);
         if (t >= nt) continue;
         const float2* b = buf + t * ls;
         float2 r;
