@@ -164,6 +164,9 @@ helm_status tc_prepare(helm_ctx* c, cudaStream_t s);
 helm_status tc_xpass(helm_ctx* c, int inverse, const float2* in, float2* out, float alpha, const double* alpha_dev,
                      int aidx, cudaStream_t s);
 helm_status tc_ypass(helm_ctx* c, int inverse, const float2* in, float2* out, cudaStream_t s);
+// operand sets of tc_xpass/tc_ypass (`inverse`): 0/1 EigT forward/inverse, 2/3 PFFT sine forward/inverse
+helm_status tc_prepare_sine(helm_ctx* c, const double2* Sx, const double2* Sy, const double2* SxT, const double2* SyT,
+                            cudaStream_t s);
 void tc_release(helm_ctx* c);
 // thomas.cu
 helm_status launch_zsolve(helm_ctx* c, const float2* in, float2* out, cudaStream_t s);

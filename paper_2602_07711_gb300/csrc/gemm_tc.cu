@@ -32,11 +32,12 @@ constexpr long WAIT_LIMIT = 1L << 20;
 
 struct TcState {
     PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
-    float* Bx[2] = {nullptr, nullptr};   // x-pass real-embedded operands, forward / inverse, [2N][2N]
-    float* Wy[2] = {nullptr, nullptr};   // y-pass operands, [2][N_y][ldw] (re plane, im plane)
+    // operand sets: 0/1 EigT forward/inverse (V^-1, V), 2/3 PFFT sine transforms forward/inverse (S^T, S)
+    float* Bx[4] = {nullptr, nullptr, nullptr, nullptr};   // x-pass real-embedded operands, [2N][2N]
+    float* Wy[4] = {nullptr, nullptr, nullptr, nullptr};   // y-pass operands, [2][N_y][ldw] (re, im planes)
     int ldw = 0;
-    CUtensorMap mapBx[2];
-    CUtensorMap mapWy[2];
+    CUtensorMap mapBx[4];
+    CUtensorMap mapWy[4];
 };
 
 __device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -356,6 +357,8 @@ size_t ysmem() { return (size_t)YSTAGES * 3 * TILE + 1024; }
 
 }  // namespace
 
+helm_status tc_encode_set(TcState* t, int nx, int ny, int i);
+
 helm_status tc_prepare(helm_ctx* c, cudaStream_t s) {
     if (c->nx % 2 != 0) return HELM_ERR_UNSUPPORTED;
     if (c->opt.precision != HELM_PREC_TF32) return HELM_ERR_UNSUPPORTED;   // split TF32 not built yet
@@ -381,18 +384,47 @@ helm_status tc_prepare(helm_ctx* c, cudaStream_t s) {
     split_y_kernel<<<(unsigned)((ny * (size_t)t->ldw + 255) / 256), 256, 0, s>>>(ny, t->ldw, c->Vyi, t->Wy[0]);
     split_y_kernel<<<(unsigned)((ny * (size_t)t->ldw + 255) / 256), 256, 0, s>>>(ny, t->ldw, c->Vy, t->Wy[1]);
     HELM_CUDA_TRY(cudaGetLastError());
-    for (int i = 0; i < 2; ++i) {
-        const cuuint64_t d[2] = {(cuuint64_t)2 * nx, (cuuint64_t)2 * nx};
-        const cuuint64_t st[1] = {(cuuint64_t)2 * nx * sizeof(float)};
-        const cuuint32_t box[2] = {BK, BN};
-        if (encode(t, &t->mapBx[i], 2, t->Bx[i], d, st, box) != HELM_OK) return HELM_ERR_CUDA;
-        const cuuint64_t dw[3] = {(cuuint64_t)ny, (cuuint64_t)ny, 2};
-        const cuuint64_t sw[2] = {(cuuint64_t)t->ldw * sizeof(float), (cuuint64_t)t->ldw * ny * sizeof(float)};
-        const cuuint32_t bw[3] = {BK, BM, 1};
-        if (encode(t, &t->mapWy[i], 3, t->Wy[i], dw, sw, bw) != HELM_OK) return HELM_ERR_CUDA;
-    }
+    for (int i = 0; i < 2; ++i)
+        if (tc_encode_set(t, nx, ny, i) != HELM_OK) return HELM_ERR_CUDA;
     HELM_CUDA_TRY(cudaFuncSetAttribute(xpass_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)xsmem()));
     HELM_CUDA_TRY(cudaFuncSetAttribute(ypass_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ysmem()));
+    return HELM_OK;
+}
+
+// TMA descriptors of operand set i (its matrices already written)
+helm_status tc_encode_set(TcState* t, int nx, int ny, int i) {
+    const cuuint64_t d[2] = {(cuuint64_t)2 * nx, (cuuint64_t)2 * nx};
+    const cuuint64_t st[1] = {(cuuint64_t)2 * nx * sizeof(float)};
+    const cuuint32_t box[2] = {BK, BN};
+    if (encode(t, &t->mapBx[i], 2, t->Bx[i], d, st, box) != HELM_OK) return HELM_ERR_CUDA;
+    const cuuint64_t dw[3] = {(cuuint64_t)ny, (cuuint64_t)ny, 2};
+    const cuuint64_t sw[2] = {(cuuint64_t)t->ldw * sizeof(float), (cuuint64_t)t->ldw * ny * sizeof(float)};
+    const cuuint32_t bw[3] = {BK, BM, 1};
+    if (encode(t, &t->mapWy[i], 3, t->Wy[i], dw, sw, bw) != HELM_OK) return HELM_ERR_CUDA;
+    return HELM_OK;
+}
+
+// PFFT on the tensor cores: operand sets 2 (forward: rows times S_x, S_y^T times slices) and 3 (inverse:
+// rows times S_x^T, S_y times slices) from the FP64 sine bases S[l][j] (row-major, real).
+helm_status tc_prepare_sine(helm_ctx* c, const double2* Sx, const double2* Sy, const double2* SxT, const double2* SyT,
+                            cudaStream_t s) {
+    TcState* t = (TcState*)c->tmaps;
+    if (!t) return HELM_ERR_UNSUPPORTED;
+    const int nx = c->nx, ny = c->ny;
+    const size_t nb = (size_t)4 * nx * nx, nw = (size_t)2 * ny * t->ldw;
+    for (int i = 2; i < 4; ++i) {
+        if (cudaMalloc(&t->Bx[i], nb * sizeof(float)) != cudaSuccess) { cudaGetLastError(); return HELM_ERR_NOMEM; }
+        if (cudaMalloc(&t->Wy[i], nw * sizeof(float)) != cudaSuccess) { cudaGetLastError(); return HELM_ERR_NOMEM; }
+    }
+    // x-pass computes row . src^T: forward wants row . S_x (src = S_x^T), inverse row . S_x^T (src = S_x)
+    embed_x_kernel<<<(unsigned)((nx * (size_t)nx + 255) / 256), 256, 0, s>>>(nx, SxT, t->Bx[2]);
+    embed_x_kernel<<<(unsigned)((nx * (size_t)nx + 255) / 256), 256, 0, s>>>(nx, Sx, t->Bx[3]);
+    // y-pass computes src . slice: forward S_y^T, inverse S_y
+    split_y_kernel<<<(unsigned)((ny * (size_t)t->ldw + 255) / 256), 256, 0, s>>>(ny, t->ldw, SyT, t->Wy[2]);
+    split_y_kernel<<<(unsigned)((ny * (size_t)t->ldw + 255) / 256), 256, 0, s>>>(ny, t->ldw, Sy, t->Wy[3]);
+    HELM_CUDA_TRY(cudaGetLastError());
+    for (int i = 2; i < 4; ++i)
+        if (tc_encode_set(t, nx, ny, i) != HELM_OK) return HELM_ERR_CUDA;
     return HELM_OK;
 }
 
@@ -407,7 +439,7 @@ helm_status tc_xpass(helm_ctx* c, int inverse, const float2* in, float2* out, fl
     const cuuint32_t box[2] = {BK, BM};
     if (encode(t, &mapA, 2, (void*)in, d, st, box) != HELM_OK) return HELM_ERR_CUDA;
     dim3 grid((N2 + BN - 1) / BN, (M + BM - 1) / BM);
-    xpass_tc_kernel<<<grid, 192, xsmem(), s>>>(mapA, t->mapBx[inverse ? 1 : 0], (float*)out, M, N2, N2, alpha, alpha_dev,
+    xpass_tc_kernel<<<grid, 192, xsmem(), s>>>(mapA, t->mapBx[inverse], (float*)out, M, N2, N2, alpha, alpha_dev,
                                                 aidx, c->status_d);
     HELM_CUDA_TRY(cudaGetLastError());
     return HELM_OK;
@@ -423,7 +455,7 @@ helm_status tc_ypass(helm_ctx* c, int inverse, const float2* in, float2* out, cu
     const cuuint32_t box[3] = {32, BK, 1};
     if (encode(t, &mapY, 3, (void*)in, d, st, box, CU_TENSOR_MAP_SWIZZLE_128B_ATOM_32B) != HELM_OK) return HELM_ERR_CUDA;
     dim3 grid((N2 + BN - 1) / BN, (ny + BM - 1) / BM, c->nz);
-    ypass_tc_kernel<<<grid, 192, ysmem(), s>>>(t->mapWy[inverse ? 1 : 0], mapY, (float*)out, ny, N2, c->status_d);
+    ypass_tc_kernel<<<grid, 192, ysmem(), s>>>(t->mapWy[inverse], mapY, (float*)out, ny, N2, c->status_d);
     HELM_CUDA_TRY(cudaGetLastError());
     return HELM_OK;
 }
@@ -431,7 +463,7 @@ helm_status tc_ypass(helm_ctx* c, int inverse, const float2* in, float2* out, cu
 void tc_release(helm_ctx* c) {
     TcState* t = (TcState*)c->tmaps;
     if (!t) return;
-    for (int i = 0; i < 2; ++i) { cudaFree(t->Bx[i]); cudaFree(t->Wy[i]); }
+    for (int i = 0; i < 4; ++i) { cudaFree(t->Bx[i]); cudaFree(t->Wy[i]); }
     delete t;
     c->tmaps = nullptr;
 }

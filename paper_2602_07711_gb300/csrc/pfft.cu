@@ -333,6 +333,37 @@ helm_status pfft_prepare(helm_ctx* c, cudaStream_t s) {
     const size_t fv = (size_t)4 * nz * nm;
     if ((st = dmal(&P->fa, fv)) || (st = dmal(&P->fb, fv)) || (st = dmal(&P->fc, fv))) return st;
     if ((st = dmal(&P->P, (size_t)4 * nz * ny)) || (st = dmal(&P->Q, (size_t)4 * nz * nx))) return st;
+    if (c->tmaps) {
+        // TF32 contexts: the sine transforms run as dense products on the tensor cores (operand sets 2, 3)
+        std::vector<double2> hS[4];
+        const int nn[2] = {nx, ny};
+        for (int a = 0; a < 2; ++a) {
+            const int N = nn[a];
+            hS[2 * a].resize((size_t)N * N);
+            hS[2 * a + 1].resize((size_t)N * N);
+            for (int l = 0; l < N; ++l)
+                for (int e = 0; e < N; ++e) {
+                    const int j = e + 1;
+                    const double cc = j < N ? sqrt(2.0 / N) : sqrt(1.0 / N);
+                    const double v = cc * sin(M_PI * j * (2.0 * l + 1) / (2.0 * N));
+                    hS[2 * a][(size_t)l * N + e] = make_double2(v, 0.0);       // S[l][j]
+                    hS[2 * a + 1][(size_t)e * N + l] = make_double2(v, 0.0);   // S^T
+                }
+        }
+        double2* dS[4] = {nullptr, nullptr, nullptr, nullptr};
+        for (int k = 0; k < 4; ++k) {
+            if (cudaMalloc(&dS[k], hS[k].size() * sizeof(double2)) != cudaSuccess) {
+                cudaGetLastError();
+                for (int q = 0; q < k; ++q) cudaFree(dS[q]);
+                return HELM_ERR_NOMEM;
+            }
+            HELM_CUDA_TRY(cudaMemcpyAsync(dS[k], hS[k].data(), hS[k].size() * sizeof(double2), cudaMemcpyHostToDevice, s));
+        }
+        st = tc_prepare_sine(c, dS[0], dS[2], dS[1], dS[3], s);
+        cudaStreamSynchronize(s);
+        for (int k = 0; k < 4; ++k) cudaFree(dS[k]);
+        if (st != HELM_OK) return st;
+    }
     const int lpbx = lines_per_block(nx), lpby = cols_per_block(ny);
     HELM_CUDA_TRY(cudaFuncSetAttribute(dst_x_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)xsmem(nx, lpbx)));
     HELM_CUDA_TRY(cudaFuncSetAttribute(dst_x_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)xsmem(nx, lpbx)));
@@ -359,6 +390,16 @@ helm_status dst2d(helm_ctx* c, PfftState* P, int inv, const float2* in, float2* 
     const long lines = (long)ny * nz;
     const int lpbx = lines_per_block(nx), tiy = cols_per_block(ny);
     const dim3 gy((nx + tiy - 1) / tiy, nz);
+    if (c->tmaps) {
+        // tensor-core products with the sine bases (same data flow as the EigT transforms)
+        helm_status st;
+        if (!inv) {
+            if ((st = tc_xpass(c, 2, in, c->tmp, 1.f, sigma, sidx, s)) != HELM_OK) return st;
+            return tc_ypass(c, 2, c->tmp, out, s);
+        }
+        if ((st = tc_ypass(c, 3, in, c->tmp, s)) != HELM_OK) return st;
+        return tc_xpass(c, 3, c->tmp, out, scale, nullptr, 0, s);
+    }
     if (!inv) {
         // x then y: in -> ctx tmp -> out
         dst_x_kernel<0><<<(unsigned)((lines + lpbx - 1) / lpbx), 256, xsmem(nx, lpbx), s>>>(

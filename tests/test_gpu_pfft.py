@@ -15,7 +15,7 @@ pytestmark = pytest.mark.gpu
 from oracle.eigt import EigT
 from oracle.grid import Grid
 from oracle.pfft import PFFT
-from paper_2602_07711_gb300 import HELM_PRECOND_EIGT, HELM_PRECOND_PFFT, Solver, media
+from paper_2602_07711_gb300 import HELM_PREC_TF32, HELM_PRECOND_EIGT, HELM_PRECOND_PFFT, Solver, media
 
 
 def _rand(shape, seed):
@@ -49,3 +49,33 @@ def test_pfft_gmres_matches_eigt_gmres():
         out[pc] = (x.cpu().numpy(), info.iterations)
     d = np.linalg.norm(out[1][0] - out[2][0]) / np.linalg.norm(out[1][0])
     assert d < 2e-5 and abs(out[1][1] - out[2][1]) <= 1
+
+
+@pytest.mark.parametrize("n,L", [((32, 32, 20), (1.0, 1.0, 0.625)), ((128, 64, 12), (1.0, 0.5, 0.1))])
+def test_pfft_tensor_core_transforms_match_oracle(n, L):
+    """TF32 contexts run the sine transforms as tcgen05 products with the sine bases: the TF32 bound of
+    the EigT transforms applies (2e-3 x kappa in the 2-norm)."""
+    g = Grid(*n, lx=L[0], ly=L[1], lz=L[2], staggered=True)
+    k0 = 2 * math.pi / (10 * g.h[0])
+    S = Solver(n, np.full(g.shape, k0 * k0, complex), k0, order=4, L=L, precond=HELM_PRECOND_PFFT,
+               precision=HELM_PREC_TF32, flexible=True)
+    y = _rand(g.shape, 8)
+    z = S.apply_precond(torch.from_numpy(y).to("cuda", torch.complex64)).cpu().numpy()
+    e = EigT(g, k0)
+    kap = np.linalg.cond(e.Vx) * np.linalg.cond(e.Vy)
+    ref = PFFT(g, k0, variant="face").apply_Minv(y)
+    err = np.linalg.norm(z - ref) / np.linalg.norm(ref)
+    assert err < 2e-3 * kap, (err, kap)
+
+
+def test_pfft_tensor_core_fgmres_converges_like_eigt():
+    n = 64
+    k2, f, k0 = media.bumps(n, 33, 34)
+    out = {}
+    for pc in (HELM_PRECOND_EIGT, HELM_PRECOND_PFFT):
+        S = Solver((n, n, n), k2, k0, order=6, precond=pc, precision=HELM_PREC_TF32, flexible=True, rtol=1e-6)
+        x, info = S.solve(S.build_rhs(torch.from_numpy(f).cuda()))
+        assert info.status == 0 and info.relres_true <= 1e-6
+        out[pc] = (x.cpu().numpy(), info.iterations)
+    d = np.linalg.norm(out[1][0] - out[2][0]) / np.linalg.norm(out[1][0])
+    assert d < 1e-5 and abs(out[1][1] - out[2][1]) <= 2
