@@ -146,7 +146,7 @@ helm_status helm_setup(const helm_grid* grid, const void* k2, double k0, const d
         if (c->nx % 2 != 0) { free_ctx(c); return HELM_ERR_UNSUPPORTED; }
         TRY(tc_prepare(c, s));
     }
-    if (opt->precond == HELM_PRECOND_EIGT) TRY(zsolve_factor(c, s));
+    if (opt->precond == HELM_PRECOND_EIGT || opt->precond == HELM_PRECOND_PFFT) TRY(zsolve_factor(c, s));
     if (opt->precond == HELM_PRECOND_PFFT) TRY(pfft_prepare(c, s));
     if (cudaStreamSynchronize(s) != cudaSuccess) { free_ctx(c); return HELM_ERR_CUDA; }
     *out = c;

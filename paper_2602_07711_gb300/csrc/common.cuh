@@ -171,6 +171,9 @@ void tc_release(helm_ctx* c);
 // thomas.cu
 helm_status launch_zsolve(helm_ctx* c, const float2* in, float2* out, cudaStream_t s);
 helm_status zsolve_factor(helm_ctx* c, cudaStream_t s);
+helm_status zsolve_factor_with(helm_ctx* c, const float2* dxs, const float2* dys, float2** m, cudaStream_t s);
+helm_status launch_zsolve_fact(helm_ctx* c, const float2* m, const float2* in, float2* out, const float2* P,
+                               const float2* Q, cudaStream_t s);
 helm_status launch_zsolve_gen(helm_ctx* c, const float2* in, float2* out, const float2* dxs, const float2* dys,
                               const float2* P, const float2* Q, cudaStream_t s);
 // pfft.cu

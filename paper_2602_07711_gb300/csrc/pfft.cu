@@ -31,6 +31,7 @@ struct PfftState {
     float2* Yh = nullptr;                           // transformed right-hand side (kept for step 3)
     float2 *fa = nullptr, *fb = nullptr, *fc = nullptr;   // frame work vectors [4][nz][nmax]
     float2 *P = nullptr, *Q = nullptr;              // outer-product factors [4][nz][ny], [4][nz][nx]
+    float2* zfacF = nullptr;                        // Thomas factors of the z-systems of A_p^F
 };
 
 bool pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
@@ -333,6 +334,7 @@ helm_status pfft_prepare(helm_ctx* c, cudaStream_t s) {
     const size_t fv = (size_t)4 * nz * nm;
     if ((st = dmal(&P->fa, fv)) || (st = dmal(&P->fb, fv)) || (st = dmal(&P->fc, fv))) return st;
     if ((st = dmal(&P->P, (size_t)4 * nz * ny)) || (st = dmal(&P->Q, (size_t)4 * nz * nx))) return st;
+    if ((st = zsolve_factor_with(c, P->dxF, P->dyF, &P->zfacF, s))) return st;
     if (c->tmaps) {
         // TF32 contexts: the sine transforms run as dense products on the tensor cores (operand sets 2, 3)
         std::vector<double2> hS[4];
@@ -376,7 +378,7 @@ void pfft_release(helm_ctx* c) {
     PfftState* P = (PfftState*)c->pfft;
     if (!P) return;
     void* ps[] = {P->twx, P->twy, P->fwx, P->fwy, P->gpx, P->gpy, P->gmx, P->gmy, P->Sx, P->Sy, P->Vx, P->Vxi,
-                  P->Vy, P->Vyi, P->dxF, P->dyF, P->Yh, P->fa, P->fb, P->fc, P->P, P->Q};
+                  P->Vy, P->Vyi, P->dxF, P->dyF, P->Yh, P->fa, P->fb, P->fc, P->P, P->Q, P->zfacF};
     for (void* p : ps) if (p) cudaFree(p);
     delete P;
     c->pfft = nullptr;
@@ -451,7 +453,7 @@ helm_status pfft_apply(helm_ctx* c, const float2* r, float2* z, const double* si
     const float2 ey = make_float2((float)(c->ay * (-1.0 - c->gam[1].x)), (float)(c->ay * (-c->gam[1].y)));
     // 1. Yh = S_y^T Y S_x ; Th = z-solve_F(Yh) -> tmp2 (z is free until the end)
     if ((st = dst2d(c, P, 0, r, P->Yh, 1.f, sigma, sidx, s)) != HELM_OK) return st;
-    if ((st = launch_zsolve_gen(c, P->Yh, z, P->dxF, P->dyF, nullptr, nullptr, s)) != HELM_OK) return st;
+    if ((st = launch_zsolve_fact(c, P->zfacF, P->Yh, z, nullptr, nullptr, s)) != HELM_OK) return st;
     // 2. Theta on the frame (fb), R vectors (fc): rows scaled by e_y, columns by e_x
     if ((st = frame_of(c, P, z, P->Sx, P->Sy, P->fb, s)) != HELM_OK) return st;
     frame_scale_kernel<<<(unsigned)((2 * blk + 255) / 256), 256, 0, s>>>(P->fb, nullptr, P->fc, 2 * blk, ey);
@@ -480,7 +482,7 @@ helm_status pfft_apply(helm_ctx* c, const float2* r, float2* z, const double* si
     HELM_CUDA_TRY(cudaMemcpy2DAsync(P->Q + (size_t)nz * nx, nx * sizeof(float2), P->fa + 3 * blk, nm * sizeof(float2),
                                     nx * sizeof(float2), nz, cudaMemcpyDeviceToDevice, s));
     //    Wbar = z-solve_EigT(Rbar) into z; W on the frame (fc) from Wbar with the EigT bases
-    if ((st = launch_zsolve_gen(c, nullptr, z, c->dxs, c->dys, P->P, P->Q, s)) != HELM_OK) return st;
+    if ((st = launch_zsolve_fact(c, c->zfac, nullptr, z, P->P, P->Q, s)) != HELM_OK) return st;
     if ((st = frame_of(c, P, z, P->Vx, P->Vy, P->fc, s)) != HELM_OK) return st;
     // 3. R2 = (A_p^F - A_p)(Theta + W) on the frame -> fc (rows e_y, columns e_x)
     frame_scale_kernel<<<(unsigned)((2 * blk + 255) / 256), 256, 0, s>>>(P->fb, P->fc, P->fc, 2 * blk, ey);
@@ -509,7 +511,7 @@ helm_status pfft_apply(helm_ctx* c, const float2* r, float2* z, const double* si
     HELM_CUDA_TRY(cudaMemcpy2DAsync(P->Q + (size_t)nz * nx, nx * sizeof(float2), P->fa + 3 * blk, nm * sizeof(float2),
                                     nx * sizeof(float2), nz, cudaMemcpyDeviceToDevice, s));
     //    Uh = z-solve_F(Yh + sine transform of R2) in place in Yh; U = h_z^2 S_y Uh S_x^T
-    if ((st = launch_zsolve_gen(c, P->Yh, P->Yh, P->dxF, P->dyF, P->P, P->Q, s)) != HELM_OK) return st;
+    if ((st = launch_zsolve_fact(c, P->zfacF, P->Yh, P->Yh, P->P, P->Q, s)) != HELM_OK) return st;
     const float hz2 = (float)(c->h[2] * c->h[2]);
     return dst2d(c, P, 1, P->Yh, z, hz2, nullptr, 0, s);
 }

@@ -228,7 +228,8 @@ __global__ void __launch_bounds__(128) zfactor_kernel(ZParams p, float2* __restr
 }
 
 __global__ void __launch_bounds__(128) zsolve_fact_kernel(int nx, int ny, int nz, float zz, const float2* __restrict__ m,
-                                                         const float2* in, float2* out) {
+                                                         const float2* in, float2* out, const float2* __restrict__ P,
+                                                         const float2* __restrict__ Q) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
     if (i >= nx) return;
     const size_t plane = (size_t)nx * ny, base = (size_t)j * nx + i;
@@ -238,9 +239,21 @@ __global__ void __launch_bounds__(128) zsolve_fact_kernel(int nx, int ny, int nz
 #pragma unroll
         for (int u = 0; u < ZU; ++u)
             if (l0 + u < nz) {
-                yv[u] = in[base + (size_t)(l0 + u) * plane];
+                yv[u] = in ? in[base + (size_t)(l0 + u) * plane] : f2(0.f, 0.f);
                 mv[u] = m[base + (size_t)(l0 + u) * plane];
             }
+        if (P) {
+            // generated right-hand side: y[l][j][i] += sum_{t<4} P[t][l][j] Q[t][l][i]
+#pragma unroll
+            for (int u = 0; u < ZU; ++u) {
+                const int l = l0 + u;
+                if (l < nz) {
+#pragma unroll
+                    for (int t = 0; t < 4; ++t)
+                        yv[u] = cadd(yv[u], cmul(P[((size_t)t * nz + l) * ny + j], Q[((size_t)t * nz + l) * nx + i]));
+                }
+            }
+        }
 #pragma unroll
         for (int u = 0; u < ZU; ++u) {
             const int l = l0 + u;
@@ -276,19 +289,33 @@ __global__ void __launch_bounds__(128) zsolve_fact_kernel(int nx, int ny, int nz
 
 }  // namespace
 
-// Set-up: the Thomas factors of the EigT z-systems (one complex64 per point).
-helm_status zsolve_factor(helm_ctx* c, cudaStream_t s) {
-    if (!c->zfac) {
-        if (cudaMalloc(&c->zfac, c->npts * sizeof(float2)) != cudaSuccess) { cudaGetLastError(); return HELM_ERR_NOMEM; }
+// Set-up: the Thomas factors of the z-systems with lateral eigenvalue shifts dxs_i + dys_j (one complex64
+// per point) into *m (allocated here if NULL).
+helm_status zsolve_factor_with(helm_ctx* c, const float2* dxs, const float2* dys, float2** m, cudaStream_t s) {
+    if (!*m) {
+        if (cudaMalloc(m, c->npts * sizeof(float2)) != cudaSuccess) { cudaGetLastError(); return HELM_ERR_NOMEM; }
     }
     ZParams p;
     p.nx = c->nx; p.ny = c->ny; p.nz = c->nz;
-    p.dxs = c->dxs; p.dys = c->dys; p.cz = c->cz;
+    p.dxs = dxs; p.dys = dys; p.cz = c->cz;
     p.P = nullptr; p.Q = nullptr;
     p.gz = make_float2((float)c->gam[2].x, (float)c->gam[2].y);
     p.zz = (float)c->zeta[2];
     dim3 grid((c->nx + 127) / 128, c->ny);
-    zfactor_kernel<<<grid, 128, 0, s>>>(p, c->zfac, c->status_d);
+    zfactor_kernel<<<grid, 128, 0, s>>>(p, *m, c->status_d);
+    HELM_CUDA_TRY(cudaGetLastError());
+    return HELM_OK;
+}
+
+helm_status zsolve_factor(helm_ctx* c, cudaStream_t s) { return zsolve_factor_with(c, c->dxs, c->dys, &c->zfac, s); }
+
+// factorised solve with factors m, optional input (NULL = 0) and optional generated right-hand side
+helm_status launch_zsolve_fact(helm_ctx* c, const float2* m, const float2* in, float2* out, const float2* P,
+                               const float2* Q, cudaStream_t s) {
+    prof_begin(c, s, PROF_ZSOLVE);
+    dim3 grid((c->nx + 127) / 128, c->ny);
+    zsolve_fact_kernel<<<grid, 128, 0, s>>>(c->nx, c->ny, c->nz, (float)c->zeta[2], m, in, out, P, Q);
+    prof_end(c, s);
     HELM_CUDA_TRY(cudaGetLastError());
     return HELM_OK;
 }
@@ -319,10 +346,5 @@ helm_status launch_zsolve_gen(helm_ctx* c, const float2* in, float2* out, const 
 
 helm_status launch_zsolve(helm_ctx* c, const float2* in, float2* out, cudaStream_t s) {
     if (!c->zfac) return launch_zsolve_gen(c, in, out, c->dxs, c->dys, nullptr, nullptr, s);
-    prof_begin(c, s, PROF_ZSOLVE);
-    dim3 grid((c->nx + 127) / 128, c->ny);
-    zsolve_fact_kernel<<<grid, 128, 0, s>>>(c->nx, c->ny, c->nz, (float)c->zeta[2], c->zfac, in, out);
-    prof_end(c, s);
-    HELM_CUDA_TRY(cudaGetLastError());
-    return HELM_OK;
+    return launch_zsolve_fact(c, c->zfac, in, out, nullptr, nullptr, s);
 }
