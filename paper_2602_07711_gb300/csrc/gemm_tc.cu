@@ -48,6 +48,9 @@ __device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
 __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
 }
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
     for (long it = 0; it < WAIT_LIMIT; ++it) {
         uint32_t ok;
@@ -313,6 +316,128 @@ ypass_tc_kernel(const __grid_constant__ CUtensorMap tmW, const __grid_constant__
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * BN) : "memory");
 }
 
+// ---- persistent x-pass: one CTA walks many output tiles, the accumulator is double-buffered in tensor
+// memory so that the epilogue of tile t overlaps the loads and MMAs of tile t+1 (the y-pass, whose two
+// accumulators per tile would need all 512 columns for double buffering, keeps one tile per CTA) --------
+// Barriers: full/empty per shared-memory stage (the stage counter runs across tiles), accf[b] (MMA ->
+// epilogue: accumulator buffer b holds a finished tile), acce[b] (epilogue -> MMA: buffer b drained; four
+// arrivals, one per epilogue warp).  Tiles are ordered N-fastest so that consecutive tiles of a CTA share
+// their A rows in L2.
+__global__ void __launch_bounds__(192, 1)
+xpass_tc_pers_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                     float* __restrict__ out, int M, int N2, int K2, float alpha, const double* __restrict__ alpha_dev,
+                     int aidx, unsigned* status) {
+    extern __shared__ uint8_t dsm[];
+    __shared__ __align__(8) uint64_t full[XSTAGES], empty[XSTAGES], accf[2], acce[2];
+    __shared__ uint32_t tslot;
+    const uint32_t raw = su32(dsm);
+    const uint32_t base = (raw + 1023u) & ~1023u;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nk = (K2 + BK - 1) / BK;
+    const int ntn = (N2 + BN - 1) / BN, ntm = (M + BM - 1) / BM, ntiles = ntn * ntm;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < XSTAGES; ++s) { mbar_init(su32(&full[s]), 1); mbar_init(su32(&empty[s]), 1); }
+        for (int b = 0; b < 2; ++b) { mbar_init(su32(&accf[b]), 1); mbar_init(su32(&acce[b]), 4); }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&tslot)), "r"(2 * BN)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem = tslot;
+    bool ok = true;
+    if (warp == 0) {
+        if (lane == 0) {
+            long it = 0;
+            for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+                const int n0 = (t % ntn) * BN, m0 = (t / ntn) * BM;
+                for (int kb = 0; kb < nk && ok; ++kb, ++it) {
+                    const int s = (int)(it % XSTAGES);
+                    const uint32_t ph = (uint32_t)((it / XSTAGES) & 1);
+                    if (it >= XSTAGES) ok = mbar_wait(su32(&empty[s]), ph ^ 1);
+                    if (!ok) break;
+                    const uint32_t sa = base + s * 2 * TILE, sb = sa + TILE;
+                    mbar_expect_tx(su32(&full[s]), 2 * TILE);
+                    tma_2d(sa, &tmA, su32(&full[s]), kb * BK, m0);
+                    tma_2d(sb, &tmB, su32(&full[s]), kb * BK, n0);
+                }
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            const uint32_t idesc = idesc_tf32(BM, BN, 0, 0);
+            long it = 0;
+            int lt = 0;
+            for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++lt) {
+                const int b = lt & 1;
+                if (lt >= 2) ok = mbar_wait(su32(&acce[b]), (uint32_t)(((lt >> 1) - 1) & 1));
+                if (!ok) break;
+                fence_after();
+                const uint32_t acc_t = tmem + (uint32_t)(b * BN);
+                for (int kb = 0; kb < nk && ok; ++kb, ++it) {
+                    const int s = (int)(it % XSTAGES);
+                    const uint32_t ph = (uint32_t)((it / XSTAGES) & 1);
+                    ok = mbar_wait(su32(&full[s]), ph);
+                    if (!ok) break;
+                    fence_after();
+                    const uint32_t sa = base + s * 2 * TILE, sb = sa + TILE;
+#pragma unroll
+                    for (int kk = 0; kk < BK / 8; ++kk)
+                        mma_tf32(acc_t, sdesc(sa + kk * 32, 16, 1024), sdesc(sb + kk * 32, 16, 1024), idesc,
+                                 (kb | kk) ? 1u : 0u);
+                    mma_commit(su32(&empty[s]));
+                }
+                if (ok) mma_commit(su32(&accf[b]));
+            }
+        }
+    } else {
+        const int q = warp & 3;
+        const float al = alpha * (alpha_dev ? (float)alpha_dev[aidx] : 1.f);
+        int lt = 0;
+        for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++lt) {
+            const int b = lt & 1;
+            const int n0 = (t % ntn) * BN, m0 = (t / ntn) * BM;
+            ok = __all_sync(0xffffffffu, mbar_wait(su32(&accf[b]), (uint32_t)((lt >> 1) & 1)));
+            if (!ok) break;
+            fence_after();
+            const int row = m0 + 32 * q + lane;
+#pragma unroll 1
+            for (int c = 0; c < BN; c += 32) {
+                uint32_t r[32];
+                TMEM_LD32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * BN + c), r);
+                tmem_wait_ld();
+                const int col = n0 + c;
+                if (row < M && col < N2) {
+                    float* dst = out + (size_t)row * N2 + col;
+                    if (col + 32 <= N2) {
+#pragma unroll
+                        for (int v = 0; v < 32; v += 4)
+                            *reinterpret_cast<float4*>(dst + v) =
+                                make_float4(al * __uint_as_float(r[v]), al * __uint_as_float(r[v + 1]),
+                                            al * __uint_as_float(r[v + 2]), al * __uint_as_float(r[v + 3]));
+                    } else {
+#pragma unroll
+                        for (int v = 0; v < 32; ++v)
+                            if (col + v < N2) dst[v] = al * __uint_as_float(r[v]);
+                    }
+                }
+            }
+            fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(su32(&acce[b]));
+        }
+    }
+    if (!ok) atomicOr(status, (unsigned)HELM_DEV_WAIT);
+    fence_before();
+    __syncthreads();
+    if (warp == 1)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * BN) : "memory");
+}
+
 // ---- operand preparation (set-up) ----------------------------------------------------------------
 __device__ __forceinline__ float to_tf32(double v) {
     uint32_t r;
@@ -354,6 +479,7 @@ helm_status encode(TcState* t, CUtensorMap* map, int rank, void* ptr, const cuui
 
 size_t xsmem() { return (size_t)XSTAGES * 2 * TILE + 1024; }
 size_t ysmem() { return (size_t)YSTAGES * 3 * TILE + 1024; }
+int g_sms = 0;
 
 }  // namespace
 
@@ -388,6 +514,8 @@ helm_status tc_prepare(helm_ctx* c, cudaStream_t s) {
         if (tc_encode_set(t, nx, ny, i) != HELM_OK) return HELM_ERR_CUDA;
     HELM_CUDA_TRY(cudaFuncSetAttribute(xpass_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)xsmem()));
     HELM_CUDA_TRY(cudaFuncSetAttribute(ypass_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ysmem()));
+    HELM_CUDA_TRY(cudaFuncSetAttribute(xpass_tc_pers_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)xsmem()));
+    HELM_CUDA_TRY(cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, c->device));
     return HELM_OK;
 }
 
@@ -439,8 +567,15 @@ helm_status tc_xpass(helm_ctx* c, int inverse, const float2* in, float2* out, fl
     const cuuint32_t box[2] = {BK, BM};
     if (encode(t, &mapA, 2, (void*)in, d, st, box) != HELM_OK) return HELM_ERR_CUDA;
     dim3 grid((N2 + BN - 1) / BN, (M + BM - 1) / BM);
-    xpass_tc_kernel<<<grid, 192, xsmem(), s>>>(mapA, t->mapBx[inverse], (float*)out, M, N2, N2, alpha, alpha_dev,
-                                                aidx, c->status_d);
+    if (c->tune_tc == 1 && g_sms > 0) {
+        const int ntiles = (int)(grid.x * grid.y);
+        const int pg = ntiles < 2 * g_sms ? ntiles : 2 * g_sms;
+        xpass_tc_pers_kernel<<<pg, 192, xsmem(), s>>>(mapA, t->mapBx[inverse], (float*)out, M, N2, N2, alpha, alpha_dev,
+                                                      aidx, c->status_d);
+    } else {
+        xpass_tc_kernel<<<grid, 192, xsmem(), s>>>(mapA, t->mapBx[inverse], (float*)out, M, N2, N2, alpha, alpha_dev,
+                                                    aidx, c->status_d);
+    }
     HELM_CUDA_TRY(cudaGetLastError());
     return HELM_OK;
 }
