@@ -158,6 +158,32 @@ def roofline(prof_ms, prof_launch, alg, precision, order):
             "traffic": None, "peak_source": src + " hbm_gbs"}
 
 
+# ---- replicas over ranks ----------------------------------------------------------------------
+def replica_totals(elapsed, units, device):
+    """Whole-job figures of N independent replicas: the slowest rank's timed seconds (MAX) and the units
+    (points x iterations) all ranks processed (SUM).  No data-path collective: only these two numbers."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(elapsed), float(units)
+    t = torch.tensor([float(elapsed)], dtype=torch.float64, device=device)
+    u = torch.tensor([float(units)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
+def problem_table(problems, rank, seed=6):
+    """Seeded problem table of the batched workload for one rank (rank r draws from seed + 1000 r, so the
+    ranks of a replica run solve different problems of the same distribution)."""
+    import numpy as np
+    rng = np.random.default_rng(seed + 1000 * rank)
+    sizes = rng.choice([48, 64, 96, 128, 160], size=problems)
+    ppws = rng.uniform(6.0, 12.0, size=problems)
+    orders = rng.choice([4, 6], size=problems)
+    return sizes, ppws, orders
+
+
 def cycles_of(info, m):
     """Inner steps of each restart cycle, as the solver reports them."""
     out = [c for c in info.cycle_its if c]
@@ -276,13 +302,10 @@ def run_ours(args, rank, world, local):
     lib.helm_profile(S.ctx, 0)
     prof_ms = {c: ms_arr[i] for i, c in enumerate(CLASSES)}
     prof_ln = {c: ln_arr[i] for i, c in enumerate(CLASSES)}
-    if world > 1:
-        t = torch.tensor([elapsed], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed = float(t.item())
     its = sum(i.iterations for i in infos)
     pts = n ** 3
-    value = pts * its / elapsed / 1e6 * world
+    elapsed, units = replica_totals(elapsed, pts * its, dev)
+    value = units / elapsed / 1e6
     # algorithmic bytes of the timed solves
     alg_tot = {}
     for i in infos:
@@ -379,10 +402,7 @@ def run_batched(args, rank, world, local):
     from paper_2602_07711_gb300 import helm, media
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    rng = np.random.default_rng(6 + 1000 * rank)
-    sizes = rng.choice([48, 64, 96, 128, 160], size=args.problems)
-    ppws = rng.uniform(6.0, 12.0, size=args.problems)
-    orders = rng.choice([4, 6], size=args.problems)
+    sizes, ppws, orders = problem_table(args.problems, rank)
     prec = PREC_NAMES["tf32" if args.precision == "auto" else args.precision]
     solvers, Bs = [], []
     t0 = time.perf_counter()
@@ -421,6 +441,9 @@ def run_batched(args, rank, world, local):
     clocks = ClockSampler(local)
     clocks.start()
     stream = torch.cuda.current_stream()
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
     torch.cuda.synchronize()
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
@@ -428,6 +451,8 @@ def run_batched(args, rank, world, local):
     res = [step() for _ in range(args.steps)]
     ev1.record(stream)
     torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
     clk = clocks.stop()
     elapsed = ev0.elapsed_time(ev1) / 1e3
     pt_its = 0
@@ -438,7 +463,8 @@ def run_batched(args, rank, world, local):
             pt_its += n ** 3 * inf.iterations
             its_all.append(inf.iterations)
             stat_all.append(inf.status)
-    value = pt_its / elapsed / 1e6 * world
+    elapsed, pt_its_all = replica_totals(elapsed, pt_its, dev)
+    value = pt_its_all / elapsed / 1e6
     # the same lanes one after another through the single-solve entry point
     torch.cuda.synchronize()
     t1 = time.perf_counter()
