@@ -460,39 +460,53 @@ __global__ void rhs_df_kernel(int order, int nx, int ny, int nz, RhsW W, const f
         F[id] = cdf_to_double2(cdf_add(fc, cdf_scale(cdf_sub(s, c6), W.c12)));
         return;
     }
-    // order 6, uniform h: every term in double-float (for rough f the h^4 terms are not small)
-    cdf lap = cdf_zero(), s4 = cdf_zero();
+    // order 6, uniform h: every term in double-float (for rough f the h^4 terms are not small).  The
+    // integer weights are applied as exact power-of-two scalings; the edge points of the mixed
+    // differences are the line neighbours already loaded, so only the corners are new loads.
+    auto p2 = [](cdf a, float sc) {   // a * sc, sc a power of two: exact
+        return cdf{df{a.re.hi * sc, a.re.lo * sc}, df{a.im.hi * sc, a.im.lo * sc}};
+    };
+    cdf s13[3], s04[3];
     float2 fd[3];
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
         int o[3] = {0, 0, 0};
-        cdf v[5];
-#pragma unroll
-        for (int q = -2; q <= 2; ++q) { o[d] = q; v[q + 2] = at(o[0], o[1], o[2]); }
-        // (h^2/12) * (-f2 + 16 f1 - 30 f0 + 16 f-1 - f-2) / (12 h_d^2)
-        cdf t = cdf_sub(cdf_scale(cdf_add(v[3], v[1]), df{16.f, 0.f}), cdf_add(v[4], v[0]));
-        t = cdf_sub(t, cdf_scale(v[2], df{30.f, 0.f}));
-        lap = cdf_add(lap, cdf_scale(t, W.lap[d]));
-        // (h^4/360) * (f2 - 4 f1 + 6 f0 - 4 f-1 + f-2) / h_d^4
-        cdf q4 = cdf_sub(cdf_add(cdf_add(v[4], v[0]), cdf_scale(v[2], df{6.f, 0.f})),
-                         cdf_scale(cdf_add(v[3], v[1]), df{4.f, 0.f}));
-        s4 = cdf_add(s4, cdf_scale(q4, W.s4[d]));
-        fd[d] = make_float2((v[3].re.hi - v[1].re.hi) * W.i2h[d], (v[3].im.hi - v[1].im.hi) * W.i2h[d]);
+        o[d] = 1; const cdf vp1 = at(o[0], o[1], o[2]);
+        o[d] = -1; const cdf vm1 = at(o[0], o[1], o[2]);
+        o[d] = 2; const cdf vp2 = at(o[0], o[1], o[2]);
+        o[d] = -2; const cdf vm2 = at(o[0], o[1], o[2]);
+        s13[d] = cdf_add(vp1, vm1);
+        s04[d] = cdf_add(vp2, vm2);
+        fd[d] = make_float2((vp1.re.hi - vm1.re.hi) * W.i2h[d], (vp1.im.hi - vm1.im.hi) * W.i2h[d]);
     }
-    cdf mix = cdf_zero();
+    const cdf f30 = cdf_sub(p2(fc, 32.f), p2(fc, 2.f));   // 30 f
+    const cdf f6 = cdf_add(p2(fc, 4.f), p2(fc, 2.f));     // 6 f
+    const cdf f4 = p2(fc, 4.f);
+    cdf lap = cdf_zero(), s4 = cdf_zero(), mix = cdf_zero();
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        // (h^2/12) (-f2 + 16 f1 - 30 f0 + 16 f-1 - f-2) / (12 h_d^2)
+        const cdf t = cdf_sub(cdf_sub(p2(s13[d], 16.f), s04[d]), f30);
+        lap = cdf_add(lap, cdf_scale(t, W.lap[d]));
+        // (h^4/360) (f2 - 4 f1 + 6 f0 - 4 f-1 + f-2) / h_d^4
+        const cdf q4 = cdf_sub(cdf_add(s04[d], f6), p2(s13[d], 4.f));
+        s4 = cdf_add(s4, cdf_scale(q4, W.s4[d]));
+    }
     const int pairs[3][2] = {{0, 1}, {0, 2}, {1, 2}};
-    const float w[3] = {1.f, -2.f, 1.f};
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
-        cdf acc = cdf_zero();
+        // (d_a^2 d_b^2 f) h_a^2 h_b^2 = corners - 2 edges + 4 centre
+        cdf corners = cdf_zero();
 #pragma unroll
-        for (int s1 = -1; s1 <= 1; ++s1)
+        for (int s1 = -1; s1 <= 1; s1 += 2)
 #pragma unroll
-            for (int s2 = -1; s2 <= 1; ++s2) {
+            for (int s2 = -1; s2 <= 1; s2 += 2) {
                 int o[3] = {0, 0, 0};
                 o[pairs[q][0]] = s1; o[pairs[q][1]] = s2;
-                acc = cdf_add(acc, cdf_scale(at(o[0], o[1], o[2]), df{w[s1 + 1] * w[s2 + 1], 0.f}));
+                corners = cdf_add(corners, at(o[0], o[1], o[2]));
             }
+        const cdf e = cdf_add(s13[pairs[q][0]], s13[pairs[q][1]]);
+        const cdf acc = cdf_add(cdf_sub(corners, p2(e, 2.f)), f4);
         mix = cdf_add(mix, cdf_scale(acc, W.mix[q]));
     }
     const cdf kc = cdf_from4(k2df[id]);
