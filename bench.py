@@ -49,6 +49,7 @@ def parse():
                         "batched call; pfft: 512^3 layered medium, PFFT vs EigT; learned: 384^3 high-contrast "
                         "medium, learned correction vs plain EigT")
     p.add_argument("--problems", type=int, default=64, help="batched workload: number of problems")
+    p.add_argument("--autotune", type=int, default=1, help="time the kernel variants on the grid before the run")
     p.add_argument("--rhs", type=int, default=4, help="batched workload: right-hand sides per problem")
     return p.parse_args()
 
@@ -136,11 +137,11 @@ def peaks():
 
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu capture of the
-# kernel on this workload, kept while the kernel is unchanged: (class, n, order) -> bytes per launch
-MEASURED_TRAFFIC = {("dots", 256, 6): 1.7036e9}
+# kernel on this workload, kept while the kernel is unchanged: (class, n, order, variant) -> bytes
+MEASURED_TRAFFIC = {}
 
 
-def roofline(prof_ms, prof_launch, alg, precision, order, n=None):
+def roofline(prof_ms, prof_launch, alg, precision, order, n=None, variant=None):
     pk, src = peaks()
     # dominant kernel class by measured time
     cls = max((c for c in alg if prof_launch.get(c, 0) > 0), key=lambda c: prof_ms.get(c, 0.0))
@@ -160,7 +161,7 @@ def roofline(prof_ms, prof_launch, alg, precision, order, n=None):
     peak = pk["hbm_gbs"]
     ach = a["bytes"] / a["launches"] / avg_s / 1e9
     return {"kernel": cls, "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
-            "traffic": MEASURED_TRAFFIC.get((cls, n, order)), "peak_source": src + " hbm_gbs",
+            "traffic": MEASURED_TRAFFIC.get((cls, n, order, variant)), "peak_source": src + " hbm_gbs",
             "algorithmic_bytes_per_launch": a["bytes"] / a["launches"]}
 
 
@@ -271,6 +272,7 @@ def run_ours(args, rank, world, local):
     S = make(precision, flexible)
     torch.cuda.synchronize()
     setup_s = time.perf_counter() - t0
+    tuned = S.autotune() if args.autotune else None
     F = S.build_rhs(f)
     x = torch.zeros_like(F)
 
@@ -319,7 +321,7 @@ def run_ours(args, rank, world, local):
             t_ = alg_tot.setdefault(c, {"bytes": 0, "flops": 0, "launches": 0})
             for k_ in a:
                 t_[k_] += a[k_]
-    rl = roofline(prof_ms, prof_ln, alg_tot, precision, order, n)
+    rl = roofline(prof_ms, prof_ln, alg_tot, precision, order, n, None if tuned is None else tuned[2])
     kernel_table = {c: {"ms": round(prof_ms[c], 3), "launches": prof_ln[c]} for c in CLASSES if prof_ln[c]}
     # end to end through the C-ABI with host buffers (pinned), copies inside the timed region
     e2e = None
@@ -370,6 +372,8 @@ def run_ours(args, rank, world, local):
                        "k0": k0, "precond": "EigT", "precision": precision,
                        "krylov": ("FGMRES(%d)" if flexible else "GMRES(%d)") % args.restart, "rtol": args.rtol,
                        "l2": "inputs larger than L2 (134 MB per complex64 vector)",
+                       "autotuned": None if tuned is None else {"update_ctas": tuned[0], "matvec_variant": tuned[1],
+                                                                "dots_variant": tuned[2]},
                        "parallelism": "replicas" if world > 1 else "single"},
             "time_to_rtol_s": elapsed / args.steps,
             "iterations": [i.iterations for i in infos],
@@ -492,7 +496,8 @@ def run_batched(args, rank, world, local):
             "iterations_total": sum(its_all) // max(1, args.steps), "status_nonzero": sum(1 for v in stat_all if v),
             "sequential": {"seconds": seq_s, "Mpts_iter_s": seq_its / seq_s / 1e6,
                            "speedup_of_batched": seq_s / (elapsed / args.steps)},
-            "autotuned_nb": sorted(set(t[0] for t in tune)), "autotuned_matvec": sorted(set(t[1] for t in tune)), "setup_s": setup_s, "plan_s": plan_s,
+            "autotuned_nb": sorted(set(t[0] for t in tune)), "autotuned_matvec": sorted(set(t[1] for t in tune)),
+            "autotuned_dots": sorted(set(t[2] for t in tune)), "setup_s": setup_s, "plan_s": plan_s,
             "plan": "helm_batch (built once)" if plan is not None else "helm_gmres_solve_batched (groups per call)",
             "clocks": clk, "gpu_launches": launches,
             "roofline": None, "cpu_baseline": None, "e2e": None})

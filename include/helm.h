@@ -169,12 +169,13 @@ helm_status helm_batch_create(helm_ctx* const* ctxs, int nprob, const void* cons
 helm_status helm_batch_run(helm_batch* batch, helm_solve_info* infos, void* stream);
 void helm_batch_destroy(helm_batch* batch);
 
-/* helm_autotune - time, on this context's grid, the candidate CTA counts of the Arnoldi kernels (inner
- * products, update, combine) and the variants of the complex64 matvec (0: cp.async plane ring at four CTAs
- * per SM, 1: TMA plane ring, 2: cp.async ring at three CTAs per SM), and keep the fastest of each for the
- * context's later solves; *nb_out and *variant_out (either may be NULL) receive the choices.  Results are
- * cached per grid size and order for the process.  Uses temporary device memory; synchronous. */
-helm_status helm_autotune(helm_ctx* ctx, int* nb_out, int* variant_out, void* stream);
+/* helm_autotune - time, on this context's grid, the candidate CTA counts of the Arnoldi update and combine
+ * kernels, the variants of the complex64 matvec (0: cp.async plane ring at four CTAs per SM, 1: TMA plane
+ * ring, 2: cp.async ring at three CTAs per SM) and of the inner-product kernel (0: groups of eight, 1/2:
+ * software-pipelined groups of four/eight), and keep the fastest of each for the context's later solves;
+ * *nb_out, *variant_out and *dots_out (any may be NULL) receive the choices.  Results are cached per grid
+ * size and order for the process.  Uses temporary device memory; synchronous. */
+helm_status helm_autotune(helm_ctx* ctx, int* nb_out, int* variant_out, int* dots_out, void* stream);
 
 /* helm_residual - r = b - A x and its norms, the rel-res numerator of Sec. 5.1, computed with about 44
  * significant bits (double-float arithmetic on the FP32 pipes) from complex128 b and x.

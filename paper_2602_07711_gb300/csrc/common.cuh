@@ -132,6 +132,7 @@ struct helm_ctx {
     int tune_nb = 0;                        // CTAs of the Arnoldi kernels chosen by helm_autotune (0 = default)
     int tune_stencil = 0;                   // complex64 matvec variant chosen by helm_autotune (0 = cp.async ring)
     int tune_tc = 1;                        // x-pass on the tensor cores: 1 persistent, 0 one tile per CTA
+    int tune_dots = 2;                      // inner-product kernel variant (helm_autotune; 2 measured best)
     cudaStream_t last_stream = nullptr;
     Prof* prof = nullptr;
 };

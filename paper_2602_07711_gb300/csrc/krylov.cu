@@ -125,6 +125,84 @@ __global__ void __launch_bounds__(NT) dots_kernel(const float2* __restrict__ V, 
     }
 }
 
+// Software-pipelined variant: groups of G basis vectors, one 16-byte load per vector and thread per
+// iteration, and the next iteration's loads issued before this iteration's compensated sums, so every
+// warp keeps two iterations of loads in flight instead of waiting a full memory latency per iteration.
+template <int G>
+__global__ void __launch_bounds__(NT) dots_pipe_kernel(const float2* __restrict__ V, size_t npts, int nv,
+                                                      const float2* __restrict__ w, double2* __restrict__ part, int ld) {
+    __shared__ double2 red[NT / 32][G];
+    const int tid = threadIdx.x;
+    const size_t n4 = npts / 2;
+    const size_t stride = (size_t)gridDim.x * NT;
+    const float4* __restrict__ W4 = reinterpret_cast<const float4*>(w);
+    for (int g0 = 0; g0 < nv; g0 += G) {
+        const int ng = min(G, nv - g0);
+        float2 ks[G], kc[G];
+        const float4* __restrict__ V4[G];
+#pragma unroll
+        for (int q = 0; q < G; ++q) {
+            ks[q] = make_float2(0, 0);
+            kc[q] = make_float2(0, 0);
+            V4[q] = reinterpret_cast<const float4*>(V + (size_t)(g0 + (q < ng ? q : 0)) * npts);
+        }
+        size_t id = blockIdx.x * (size_t)NT + tid;
+        float4 wa = make_float4(0.f, 0.f, 0.f, 0.f), va[G];
+        if (id < n4) {
+            wa = W4[id];
+#pragma unroll
+            for (int q = 0; q < G; ++q) va[q] = q < ng ? V4[q][id] : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        for (; id < n4; id += stride) {
+            const size_t nid = id + stride;
+            float4 wb = make_float4(0.f, 0.f, 0.f, 0.f), vb[G];
+#pragma unroll
+            for (int q = 0; q < G; ++q) vb[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (nid < n4) {
+                wb = W4[nid];
+#pragma unroll
+                for (int q = 0; q < G; ++q)
+                    if (q < ng) vb[q] = V4[q][nid];
+            }
+#pragma unroll
+            for (int q = 0; q < G; ++q) {
+                const float4 a = va[q];
+                float re = a.x * wa.x, im = a.x * wa.y;
+                re = fmaf(a.y, wa.y, re);
+                im = fmaf(-a.y, wa.x, im);
+                re = fmaf(a.z, wa.z, fmaf(a.w, wa.w, re));
+                im = fmaf(a.z, wa.w, fmaf(-a.w, wa.z, im));
+                float y = re - kc[q].x, t = ks[q].x + y;
+                kc[q].x = (t - ks[q].x) - y; ks[q].x = t;
+                y = im - kc[q].y; t = ks[q].y + y;
+                kc[q].y = (t - ks[q].y) - y; ks[q].y = t;
+            }
+            wa = wb;
+#pragma unroll
+            for (int q = 0; q < G; ++q) va[q] = vb[q];
+        }
+        double2 acc[G];
+#pragma unroll
+        for (int q = 0; q < G; ++q) {
+            acc[q] = make_double2((double)ks[q].x - (double)kc[q].x, (double)ks[q].y - (double)kc[q].y);
+            for (int o = 16; o > 0; o >>= 1) {
+                acc[q].x += __shfl_down_sync(0xffffffffu, acc[q].x, o);
+                acc[q].y += __shfl_down_sync(0xffffffffu, acc[q].y, o);
+            }
+        }
+        if ((tid & 31) == 0)
+#pragma unroll
+            for (int q = 0; q < G; ++q) red[tid >> 5][q] = acc[q];
+        __syncthreads();
+        if (tid < ng) {
+            double2 sum = make_double2(0, 0);
+            for (int wi = 0; wi < NT / 32; ++wi) { sum.x += red[wi][tid].x; sum.y += red[wi][tid].y; }
+            part[(size_t)blockIdx.x * ld + g0 + tid] = sum;
+        }
+        __syncthreads();
+    }
+}
+
 // h_i += sigma_i * sum_blk part  (i < nv) into H column j; coef_i = h_i(this pass) * sigma_i
 __global__ void reduce_h_kernel(const double2* __restrict__ part, int NB, int ld, int nv, const double* __restrict__ sigma,
                                 double2* __restrict__ Hcol, float2* __restrict__ coef, int first_pass) {
@@ -390,6 +468,8 @@ void free_work(KrylovWork* k) {
 }
 
 int dots_ctas(const helm_ctx* c);
+int launch_dots(const helm_ctx* c, const float2* V, size_t npts, int nv, const float2* w, double2* part, int ld,
+                int nbd, cudaStream_t s);
 
 // Krylov workspace of restart length m for the context's grid; NB = CTAs of the Arnoldi kernels.
 helm_status alloc_work(helm_ctx* c, KrylovWork* k, int m, int flex, int NB) {
@@ -419,16 +499,41 @@ helm_status alloc_work(helm_ctx* c, KrylovWork* k, int m, int flex, int NB) {
     return HELM_OK;
 }
 
-// The inner-product kernel holds eight compensated sums per thread (about 80 registers, three CTAs per
-// SM): a grid of exactly the resident CTAs avoids a partial second wave.
-int dots_ctas(const helm_ctx* c) {
+// The inner-product kernels hold several compensated sums per thread (many registers, few CTAs per SM):
+// a grid of exactly the resident CTAs avoids a partial second wave.  Variants (helm_autotune picks):
+// 0 = groups of eight, two loads per vector per iteration; 1 = pipelined groups of four; 2 = pipelined
+// groups of eight.
+const void* dots_fn(int v) {
+    if (v == 1) return (const void*)dots_pipe_kernel<4>;
+    if (v == 2) return (const void*)dots_pipe_kernel<8>;
+    return (const void*)dots_kernel;
+}
+
+int dots_ctas_for(const helm_ctx* c, int v) {
     int sms = 0, per = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, dots_kernel, NT, 0) != cudaSuccess || per < 1) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, dots_fn(v), NT, 0) != cudaSuccess || per < 1) {
         cudaGetLastError();
         per = 2;
     }
     return (sms > 0 ? sms : 148) * per;
+}
+
+int dots_ctas(const helm_ctx* c) {
+    int m = 0;
+    for (int v = 0; v < 3; ++v) m = std::max(m, dots_ctas_for(c, v));
+    return m;   // partial buffers sized for any variant
+}
+
+int launch_dots(const helm_ctx* c, const float2* V, size_t npts, int nv, const float2* w, double2* part, int ld,
+                int nbd, cudaStream_t s) {
+    (void)nbd;
+    const int v = c->tune_dots;
+    const int nb = dots_ctas_for(c, v);
+    if (v == 1) dots_pipe_kernel<4><<<nb, NT, 0, s>>>(V, npts, nv, w, part, ld);
+    else if (v == 2) dots_pipe_kernel<8><<<nb, NT, 0, s>>>(V, npts, nv, w, part, ld);
+    else dots_kernel<<<nb, NT, 0, s>>>(V, npts, nv, w, part, ld);
+    return nb;
 }
 
 int default_nb(const helm_ctx* c) {
@@ -536,10 +641,10 @@ helm_status gmres_run(helm_ctx* c, const double2* b_in, double2* x_in, helm_solv
                 const int passes = c->opt.reorth ? 2 : 1;
                 for (int pass = 0; pass < passes; ++pass) {
                     prof_begin(c, s, PROF_DOTS);
-                    dots_kernel<<<k->NBd, NT, 0, s>>>(k->V, npts, j + 1, w, k->part, ld);
+                    const int nbd = launch_dots(c, k->V, npts, j + 1, w, k->part, ld, k->NBd, s);
                     prof_end(c, s);
                     prof_begin(c, s, PROF_SMALL);
-                    reduce_h_kernel<<<1, 256, 0, s>>>(k->part, k->NBd, ld, j + 1, k->sigma, k->H + (size_t)j * (m + 1),
+                    reduce_h_kernel<<<1, 256, 0, s>>>(k->part, nbd, ld, j + 1, k->sigma, k->H + (size_t)j * (m + 1),
                                                       k->coef, pass == 0);
                     prof_end(c, s);
                     prof_begin(c, s, PROF_UPDATE);
@@ -641,7 +746,7 @@ struct TuneKey {
     }
 };
 struct TuneVal {
-    int nb, stencil;
+    int nb, stencil, dots;
 };
 
 std::mutex g_tune_mu;
@@ -649,7 +754,7 @@ std::map<TuneKey, TuneVal> g_tune_cache;
 
 }  // namespace
 
-extern "C" helm_status helm_autotune(helm_ctx* c, int* nb_out, int* variant_out, void* stream) {
+extern "C" helm_status helm_autotune(helm_ctx* c, int* nb_out, int* variant_out, int* dots_out, void* stream) {
     if (!c) return HELM_ERR_ARG;
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
@@ -657,8 +762,10 @@ extern "C" helm_status helm_autotune(helm_ctx* c, int* nb_out, int* variant_out,
         if (it != g_tune_cache.end()) {
             c->tune_nb = it->second.nb;
             c->tune_stencil = std::min(it->second.stencil, stencil_variants(c) - 1);
+            c->tune_dots = it->second.dots;
             if (nb_out) *nb_out = c->tune_nb;
             if (variant_out) *variant_out = c->tune_stencil;
+            if (dots_out) *dots_out = c->tune_dots;
             return HELM_OK;
         }
     }
@@ -721,6 +828,24 @@ extern "C" helm_status helm_autotune(helm_ctx* c, int* nb_out, int* variant_out,
         if (tmin < best_st_ms * 0.97f) { best_st_ms = tmin; best_st = v; }
     }
     c->tune_stencil = best_st;
+    // the inner-product variant, on eight basis vectors
+    int best_d = 0;
+    float best_d_ms = 1e30f;
+    for (int v = 0; v < 3; ++v) {
+        c->tune_dots = v;
+        float tmin = 1e30f;
+        for (int rep = 0; rep < 4; ++rep) {
+            cudaEventRecord(e0, s);
+            launch_dots(c, V, npts, nv, w, part, ld, 0, s);
+            cudaEventRecord(e1, s);
+            cudaEventSynchronize(e1);
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (rep > 0) tmin = std::min(tmin, ms);
+        }
+        if (tmin < best_d_ms * 0.97f) { best_d_ms = tmin; best_d = v; }
+    }
+    c->tune_dots = best_d;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     cudaFree(V); cudaFree(part); cudaFree(coef);
@@ -728,10 +853,11 @@ extern "C" helm_status helm_autotune(helm_ctx* c, int* nb_out, int* variant_out,
     c->tune_nb = best;
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
-        g_tune_cache[TuneKey{c->nx, c->ny, c->nz, c->opt.order}] = TuneVal{best, best_st};
+        g_tune_cache[TuneKey{c->nx, c->ny, c->nz, c->opt.order}] = TuneVal{best, best_st, best_d};
     }
     if (nb_out) *nb_out = best;
     if (variant_out) *variant_out = best_st;
+    if (dots_out) *dots_out = best_d;
     return HELM_OK;
 }
 
@@ -834,8 +960,8 @@ helm_status lane_iteration(Lane& ln, int j, cudaGraphConditionalHandle hnext, in
     if ((st = launch_stencil_f32(c, z, w, nullptr, 0, s)) != HELM_OK) return st;
     const int passes = c->opt.reorth ? 2 : 1;
     for (int pass = 0; pass < passes; ++pass) {
-        dots_kernel<<<k->NBd, NT, 0, s>>>(k->V, npts, j + 1, w, k->part, ld);
-        reduce_h_kernel<<<1, 256, 0, s>>>(k->part, k->NBd, ld, j + 1, k->sigma, k->H + (size_t)j * (m + 1), k->coef,
+        const int nbd = launch_dots(c, k->V, npts, j + 1, w, k->part, ld, k->NBd, s);
+        reduce_h_kernel<<<1, 256, 0, s>>>(k->part, nbd, ld, j + 1, k->sigma, k->H + (size_t)j * (m + 1), k->coef,
                                           pass == 0);
         update_kernel<<<NB, NT, 0, s>>>(k->V, npts, j + 1, k->coef, w, k->part, ld);
     }

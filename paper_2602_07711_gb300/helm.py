@@ -66,7 +66,7 @@ _SIGS = {
     "helm_gmres_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(helm_solve_info), C.c_void_p]),
     "helm_gmres_solve_batched": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_int,
                                            C.c_void_p, C.c_void_p]),
-    "helm_autotune": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "helm_autotune": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "helm_batch_create": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p,
                                     C.POINTER(C.c_void_p)]),
     "helm_batch_run": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
@@ -229,11 +229,12 @@ class Batch:
 
 
 def helm_autotune(ctx, stream=None):
-    """(CTA count of the Arnoldi kernels, matvec variant) chosen for the context."""
+    """(CTA count of the Arnoldi update, matvec variant, inner-product variant) chosen for the context."""
     nb = C.c_int()
     var = C.c_int()
-    _check(lib().helm_autotune(ctx, C.byref(nb), C.byref(var), _stream(stream)), "helm_autotune")
-    return nb.value, var.value
+    dv = C.c_int()
+    _check(lib().helm_autotune(ctx, C.byref(nb), C.byref(var), C.byref(dv), _stream(stream)), "helm_autotune")
+    return nb.value, var.value, dv.value
 
 
 def helm_residual(ctx, b, x, r=None, stream=None):
@@ -413,8 +414,8 @@ class Solver:
         return y
 
     def autotune(self, stream=None):
-        """Pick the Arnoldi kernels' CTA count and the matvec variant for this grid by timing (cached per
-        grid size and order); returns (CTA count, variant)."""
+        """Pick the Arnoldi kernels' CTA count and the matvec and inner-product variants for this grid by
+        timing (cached per grid size and order); returns (CTA count, matvec variant, inner-product variant)."""
         return helm_autotune(self.ctx, stream)
 
     def features(self, net, v, mv, stream=None):
