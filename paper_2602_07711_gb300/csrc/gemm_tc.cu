@@ -28,6 +28,9 @@ namespace {
 constexpr int BM = 128, BN = 128, BK = 32;      // BK fp32 elements = 128 bytes = one swizzle row
 constexpr int TILE = BM * BK * 4;               // 16 KiB: a 128-row tile of one K block
 constexpr int XSTAGES = 3, YSTAGES = 2;
+constexpr int XEPI_LD = 20;                                  // x-pass staging row: 16 floats + 4 pad
+constexpr int XEPI_BYTES = 4 * 32 * XEPI_LD * 4;             // four epilogue warps x 32 rows
+constexpr int YEPI_LD = 36;                                  // y-pass staging row: 32 floats + 4 pad
 constexpr long WAIT_LIMIT = 1L << 20;
 
 struct TcState {
@@ -279,7 +282,10 @@ ypass_tc_kernel(const __grid_constant__ CUtensorMap tmW, const __grid_constant__
         ok = __all_sync(0xffffffffu, ok);
         fence_after();
         const int q = warp & 3;
-        const int row = m0 + 32 * q + lane;
+        // every MMA has completed, so the pipeline stages are free: each warp stages its 32 rows of a
+        // 32-column chunk there (stride YEPI_LD floats) and stores full 128-byte row segments
+        float* stg = reinterpret_cast<float*>(dsm + (base - raw)) + q * 32 * YEPI_LD;
+        const int rbase = m0 + 32 * q;
         if (ok) {
 #pragma unroll 1
             for (int c = 0; c < BN; c += 32) {
@@ -287,25 +293,30 @@ ypass_tc_kernel(const __grid_constant__ CUtensorMap tmW, const __grid_constant__
                 TMEM_LD32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)c, p);
                 TMEM_LD32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(BN + c), qq);
                 tmem_wait_ld();
-                const int col = n0 + c;
-                if (row < ny && col < N2) {
-                    float* dst = out + ((size_t)l * ny + row) * N2 + col;
-                    float o[32];
 #pragma unroll
-                    for (int v = 0; v < 32; v += 2) {
-                        o[v] = __uint_as_float(p[v]) - __uint_as_float(qq[v + 1]);
-                        o[v + 1] = __uint_as_float(p[v + 1]) + __uint_as_float(qq[v]);
-                    }
-                    if (col + 32 <= N2) {
+                for (int v = 0; v < 32; v += 4)
+                    *reinterpret_cast<float4*>(stg + lane * YEPI_LD + v) =
+                        make_float4(__uint_as_float(p[v]) - __uint_as_float(qq[v + 1]),
+                                    __uint_as_float(p[v + 1]) + __uint_as_float(qq[v]),
+                                    __uint_as_float(p[v + 2]) - __uint_as_float(qq[v + 3]),
+                                    __uint_as_float(p[v + 3]) + __uint_as_float(qq[v + 2]));
+                __syncwarp();
 #pragma unroll
-                        for (int v = 0; v < 32; v += 4)
-                            *reinterpret_cast<float4*>(dst + v) = make_float4(o[v], o[v + 1], o[v + 2], o[v + 3]);
-                    } else {
-#pragma unroll
-                        for (int v = 0; v < 32; ++v)
-                            if (col + v < N2) dst[v] = o[v];
+                for (int i = 0; i < 8; ++i) {
+                    const int rr = 4 * i + (lane >> 3), cc = 4 * (lane & 7);
+                    const int grow = rbase + rr, gcol = n0 + c + cc;
+                    const float4 v = *reinterpret_cast<const float4*>(stg + rr * YEPI_LD + cc);
+                    if (grow < ny && gcol < N2) {
+                        float* dst = out + ((size_t)l * ny + grow) * N2 + gcol;
+                        if (gcol + 4 <= N2) *reinterpret_cast<float4*>(dst) = v;
+                        else {
+                            dst[0] = v.x;
+                            if (gcol + 1 < N2) dst[1] = v.y;
+                            if (gcol + 2 < N2) dst[2] = v.z;
+                        }
                     }
                 }
+                __syncwarp();
             }
         }
     }
@@ -335,6 +346,7 @@ xpass_tc_pers_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_const
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nk = (K2 + BK - 1) / BK;
     const int ntn = (N2 + BN - 1) / BN, ntm = (M + BM - 1) / BM, ntiles = ntn * ntm;
+    float* epi = reinterpret_cast<float*>(dsm + (base - raw) + XSTAGES * 2 * TILE);   // epilogue staging rows
     if (threadIdx.x == 0) {
         for (int s = 0; s < XSTAGES; ++s) { mbar_init(su32(&full[s]), 1); mbar_init(su32(&empty[s]), 1); }
         for (int b = 0; b < 2; ++b) { mbar_init(su32(&accf[b]), 1); mbar_init(su32(&acce[b]), 4); }
@@ -404,26 +416,39 @@ xpass_tc_pers_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_const
             ok = __all_sync(0xffffffffu, mbar_wait(su32(&accf[b]), (uint32_t)((lt >> 1) & 1)));
             if (!ok) break;
             fence_after();
-            const int row = m0 + 32 * q + lane;
+            // each thread holds one row of the accumulator; 16-column halves go through this warp's staging
+            // rows (stride XEPI_LD floats, conflict-free both ways) so that the stores are 64-byte row segments
+            float* stg = epi + q * 32 * XEPI_LD;
+            const int rbase = m0 + 32 * q;
 #pragma unroll 1
             for (int c = 0; c < BN; c += 32) {
                 uint32_t r[32];
                 TMEM_LD32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * BN + c), r);
                 tmem_wait_ld();
-                const int col = n0 + c;
-                if (row < M && col < N2) {
-                    float* dst = out + (size_t)row * N2 + col;
-                    if (col + 32 <= N2) {
 #pragma unroll
-                        for (int v = 0; v < 32; v += 4)
-                            *reinterpret_cast<float4*>(dst + v) =
-                                make_float4(al * __uint_as_float(r[v]), al * __uint_as_float(r[v + 1]),
-                                            al * __uint_as_float(r[v + 2]), al * __uint_as_float(r[v + 3]));
-                    } else {
+                for (int h = 0; h < 2; ++h) {
 #pragma unroll
-                        for (int v = 0; v < 32; ++v)
-                            if (col + v < N2) dst[v] = al * __uint_as_float(r[v]);
+                    for (int v = 0; v < 16; v += 4)
+                        *reinterpret_cast<float4*>(stg + lane * XEPI_LD + v) =
+                            make_float4(al * __uint_as_float(r[16 * h + v]), al * __uint_as_float(r[16 * h + v + 1]),
+                                        al * __uint_as_float(r[16 * h + v + 2]), al * __uint_as_float(r[16 * h + v + 3]));
+                    __syncwarp();
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        const int rr = 8 * i + (lane >> 2), cc = 4 * (lane & 3);
+                        const int grow = rbase + rr, gcol = n0 + c + 16 * h + cc;
+                        const float4 v = *reinterpret_cast<const float4*>(stg + rr * XEPI_LD + cc);
+                        if (grow < M && gcol < N2) {
+                            float* dst = out + (size_t)grow * N2 + gcol;
+                            if (gcol + 4 <= N2) *reinterpret_cast<float4*>(dst) = v;
+                            else {
+                                dst[0] = v.x;
+                                if (gcol + 1 < N2) dst[1] = v.y;
+                                if (gcol + 2 < N2) dst[2] = v.z;
+                            }
+                        }
                     }
+                    __syncwarp();
                 }
             }
             fence_before();
@@ -478,6 +503,7 @@ helm_status encode(TcState* t, CUtensorMap* map, int rank, void* ptr, const cuui
 }
 
 size_t xsmem() { return (size_t)XSTAGES * 2 * TILE + 1024; }
+size_t xpsmem() { return xsmem() + XEPI_BYTES; }
 size_t ysmem() { return (size_t)YSTAGES * 3 * TILE + 1024; }
 int g_sms = 0;
 
@@ -514,7 +540,7 @@ helm_status tc_prepare(helm_ctx* c, cudaStream_t s) {
         if (tc_encode_set(t, nx, ny, i) != HELM_OK) return HELM_ERR_CUDA;
     HELM_CUDA_TRY(cudaFuncSetAttribute(xpass_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)xsmem()));
     HELM_CUDA_TRY(cudaFuncSetAttribute(ypass_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ysmem()));
-    HELM_CUDA_TRY(cudaFuncSetAttribute(xpass_tc_pers_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)xsmem()));
+    HELM_CUDA_TRY(cudaFuncSetAttribute(xpass_tc_pers_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)xpsmem()));
     HELM_CUDA_TRY(cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, c->device));
     return HELM_OK;
 }
@@ -570,7 +596,7 @@ helm_status tc_xpass(helm_ctx* c, int inverse, const float2* in, float2* out, fl
     if (c->tune_tc == 1 && g_sms > 0) {
         const int ntiles = (int)(grid.x * grid.y);
         const int pg = ntiles < 2 * g_sms ? ntiles : 2 * g_sms;
-        xpass_tc_pers_kernel<<<pg, 192, xsmem(), s>>>(mapA, t->mapBx[inverse], (float*)out, M, N2, N2, alpha, alpha_dev,
+        xpass_tc_pers_kernel<<<pg, 192, xpsmem(), s>>>(mapA, t->mapBx[inverse], (float*)out, M, N2, N2, alpha, alpha_dev,
                                                       aidx, c->status_d);
     } else {
         xpass_tc_kernel<<<grid, 192, xsmem(), s>>>(mapA, t->mapBx[inverse], (float*)out, M, N2, N2, alpha, alpha_dev,

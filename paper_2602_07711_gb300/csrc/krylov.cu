@@ -53,12 +53,16 @@ struct KrylovWork {
     float4* xdf = nullptr;   // the iterate in double-float (re.hi, im.hi, re.lo, im.lo)
     float4* Fdf = nullptr;   // the right-hand side in double-float
     unsigned* nzflag = nullptr;
+    Ctrl* slots_h = nullptr;         // pinned [m]: the controls after each iteration of a cycle
+    cudaEvent_t* ev_slot = nullptr;  // [m]: recorded after each slot's copy
 };
 
 namespace {
 
 constexpr int NT = 256;
 constexpr int GRP = 8;
+// smallest one-step reduction of the GMRES residual estimate assumed by the look-ahead of the solve loop
+constexpr double kLookaheadDrop = 0.05;
 
 // partial inner products conj(v_i) . w for i in [0, nv); part[blk * ld + i].
 // Two points per 16-byte load, two loads of each vector in flight per thread; per-thread sums are
@@ -465,6 +469,12 @@ void free_work(KrylovWork* k) {
     cudaFree(k->g); cudaFree(k->y); cudaFree(k->part); cudaFree(k->rpart); cudaFree(k->coef); cudaFree(k->ctrl_d);
     cudaFreeHost(k->ctrl_h); cudaFree(k->xbuf); cudaFree(k->bbuf); cudaFree(k->xdf); cudaFree(k->Fdf);
     cudaFree(k->nzflag);
+    cudaFreeHost(k->slots_h);
+    if (k->ev_slot) {
+        for (int j = 0; j < k->m; ++j)
+            if (k->ev_slot[j]) cudaEventDestroy(k->ev_slot[j]);
+        delete[] k->ev_slot;
+    }
 }
 
 int dots_ctas(const helm_ctx* c);
@@ -553,6 +563,15 @@ helm_status ensure_work(helm_ctx* c) {
     return alloc_work(c, k, m, flex, default_nb(c));
 }
 
+// control slots and events of the single-solve loop (batch lanes do not use them)
+helm_status ensure_slots(KrylovWork* k) {
+    if (k->slots_h) return HELM_OK;
+    HELM_CUDA_TRY(cudaMallocHost(&k->slots_h, sizeof(Ctrl) * k->m));
+    k->ev_slot = new cudaEvent_t[k->m]();
+    for (int j = 0; j < k->m; ++j) HELM_CUDA_TRY(cudaEventCreateWithFlags(&k->ev_slot[j], cudaEventDisableTiming));
+    return HELM_OK;
+}
+
 helm_status read_ctrl(KrylovWork* k, cudaStream_t s) {
     HELM_CUDA_TRY(cudaMemcpyAsync(k->ctrl_h, k->ctrl_d, sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
     HELM_CUDA_TRY(cudaStreamSynchronize(s));
@@ -592,6 +611,7 @@ helm_status gmres_run(helm_ctx* c, const double2* b_in, double2* x_in, helm_solv
     helm_status st = ensure_work(c);
     if (st != HELM_OK) return st;
     KrylovWork* k = c->kw;
+    if ((st = ensure_slots(k)) != HELM_OK) return st;
     const size_t npts = c->npts, vbytes = npts * sizeof(double2);
     const int m = c->opt.restart, flex = c->opt.flexible;
     const bool xdev = is_device_ptr(x_in), bdev = is_device_ptr(b_in);
@@ -630,14 +650,16 @@ helm_status gmres_run(helm_ctx* c, const double2* b_in, double2* x_in, helm_solv
             if (k->ctrl_h->beta / beta0 <= c->opt.rtol) { result = HELM_OK; break; }
             if (k->ctrl_h->flags & HELM_DEV_NAN) { result = HELM_ERR_NAN; break; }
             if (its >= c->opt.max_iter) { result = HELM_ERR_NOT_CONVERGED; break; }
-            int kk = 0;
+            int kk = 0, launched = 0;
             bool breakdown = false;
-            for (int j = 0; j < m; ++j) {
+            // iteration j of the cycle; its control block is copied to slot j behind it
+            auto enqueue = [&](int j) -> helm_status {
                 float2* vj = k->V + (size_t)j * npts;
                 float2* w = k->V + (size_t)(j + 1) * npts;
                 float2* z = flex ? k->Z + (size_t)j * npts : k->Z;
-                if ((st = precond_apply(c, vj, z, k->sigma, j, s)) != HELM_OK) return st;
-                if ((st = launch_stencil_f32(c, z, w, nullptr, 0, s)) != HELM_OK) return st;
+                helm_status e;
+                if ((e = precond_apply(c, vj, z, k->sigma, j, s)) != HELM_OK) return e;
+                if ((e = launch_stencil_f32(c, z, w, nullptr, 0, s)) != HELM_OK) return e;
                 const int passes = c->opt.reorth ? 2 : 1;
                 for (int pass = 0; pass < passes; ++pass) {
                     prof_begin(c, s, PROF_DOTS);
@@ -655,14 +677,37 @@ helm_status gmres_run(helm_ctx* c, const double2* b_in, double2* x_in, helm_solv
                 givens_kernel<<<1, 256, 0, s>>>(k->part, NB, ld, j, m, k->H, k->cs, k->sn, k->g, k->sigma, k->ctrl_d);
                 prof_end(c, s);
                 HELM_CUDA_TRY(cudaGetLastError());
-                if ((st = read_ctrl(k, s)) != HELM_OK) return st;
+                HELM_CUDA_TRY(cudaMemcpyAsync(&k->slots_h[j], k->ctrl_d, sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
+                HELM_CUDA_TRY(cudaEventRecord(k->ev_slot[j], s));
+                return HELM_OK;
+            };
+            // Look-ahead: while the last known estimate is far above rtol, iteration j+1 is enqueued before
+            // the estimate of iteration j is read, so the device never waits for the host.  An iteration
+            // enqueued beyond the end of the cycle leaves columns j+1.. of H and g[j+2] behind, which the
+            // least-squares solve of the first kk columns does not read; the control block is restored.
+            double est_prev = k->ctrl_h->beta / beta0;
+            for (int j = 0; j < m; ++j) {
+                if (launched <= j) {
+                    if ((st = enqueue(j)) != HELM_OK) return st;
+                    launched = j + 1;
+                }
+                if (j + 1 < m && its + 2 <= c->opt.max_iter && est_prev * kLookaheadDrop > c->opt.rtol) {
+                    if ((st = enqueue(j + 1)) != HELM_OK) return st;
+                    launched = j + 2;
+                }
+                HELM_CUDA_TRY(cudaEventSynchronize(k->ev_slot[j]));
+                const Ctrl& cj = k->slots_h[j];
                 ++its;
                 kk = j + 1;
-                est = k->ctrl_h->est;
-                if (k->ctrl_h->flags & HELM_DEV_NAN) break;
+                est = cj.est;
+                est_prev = est;
+                if (cj.flags & HELM_DEV_NAN) break;
                 if (est <= c->opt.rtol || its >= c->opt.max_iter) break;
-                if (!(k->ctrl_h->hnext > 0)) { breakdown = true; break; }
+                if (!(cj.hnext > 0)) { breakdown = true; break; }
             }
+            *k->ctrl_h = k->slots_h[kk - 1];
+            if (launched > kk)
+                HELM_CUDA_TRY(cudaMemcpyAsync(k->ctrl_d, &k->slots_h[kk - 1], sizeof(Ctrl), cudaMemcpyHostToDevice, s));
             if (k->ctrl_h->flags & HELM_DEV_NAN) { result = HELM_ERR_NAN; break; }
             prof_begin(c, s, PROF_SMALL);
             lsq_kernel<<<1, 32, 0, s>>>(k->H, k->g, kk, m, k->y, k->ctrl_d, nullptr);
