@@ -208,23 +208,33 @@ __global__ void __launch_bounds__(NT) dots_pipe_kernel(const float2* __restrict_
 }
 
 // h_i += sigma_i * sum_blk part  (i < nv) into H column j; coef_i = h_i(this pass) * sigma_i
+// one block per basis vector i: h_i = sigma_i * sum over blocks of the partial products, coef_i = sigma_i h_i
 __global__ void reduce_h_kernel(const double2* __restrict__ part, int NB, int ld, int nv, const double* __restrict__ sigma,
                                 double2* __restrict__ Hcol, float2* __restrict__ coef, int first_pass) {
+    __shared__ double rx[32], ry[32];
+    const int i = blockIdx.x;
+    if (i >= nv) return;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int i = wid; i < nv; i += nw) {
-        double sx = 0, sy = 0;
-        for (int b = lane; b < NB; b += 32) { sx += part[(size_t)b * ld + i].x; sy += part[(size_t)b * ld + i].y; }
-        for (int o = 16; o > 0; o >>= 1) {
-            sx += __shfl_down_sync(0xffffffffu, sx, o);
-            sy += __shfl_down_sync(0xffffffffu, sy, o);
-        }
-        if (lane == 0) {
-            const double s = sigma[i];
-            const double2 h = make_double2(sx * s, sy * s);
-            if (first_pass) Hcol[i] = h; else Hcol[i] = cadd(Hcol[i], h);
-            coef[i] = make_float2((float)(h.x * s), (float)(h.y * s));
-        }
+    double sx = 0, sy = 0;
+    for (int b = threadIdx.x; b < NB; b += blockDim.x) {
+        const double2 v = part[(size_t)b * ld + i];
+        sx += v.x;
+        sy += v.y;
     }
+    for (int o = 16; o > 0; o >>= 1) {
+        sx += __shfl_down_sync(0xffffffffu, sx, o);
+        sy += __shfl_down_sync(0xffffffffu, sy, o);
+    }
+    if (lane == 0) { rx[wid] = sx; ry[wid] = sy; }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    sx = 0;
+    sy = 0;
+    for (int w = 0; w < nw; ++w) { sx += rx[w]; sy += ry[w]; }
+    const double sg = sigma[i];
+    const double2 h = make_double2(sx * sg, sy * sg);
+    Hcol[i] = first_pass ? h : cadd(Hcol[i], h);
+    coef[i] = make_float2((float)(h.x * sg), (float)(h.y * sg));
 }
 
 // w -= sum_i coef_i V_i (i < nv); per-block partial ||w||^2 in part[blk * ld].x.  Two points per
@@ -288,9 +298,17 @@ __device__ inline void givens(double2 a, double2 b, double& c, double2& s) {
 }
 
 // Finish column j: h_{j+1,j} from the partial norms, previous rotations, the new rotation, g, est.
+// Finish column j: h_{j+1,j} from the partial norms, previous rotations, the new rotation, g, est.  The
+// column and the previous rotations are staged in shared memory by the whole block; one thread then
+// applies the rotations.
 __global__ void givens_kernel(const double2* __restrict__ part, int NB, int ld, int j, int m, double2* H, double* cs,
                               double2* sn, double2* g, double* sigma, Ctrl* ctrl) {
     __shared__ double red[32];
+    __shared__ double2 col[72], snv[72];
+    __shared__ double csv[72];
+    double2* hcol = H + (size_t)j * (m + 1);
+    for (int i = threadIdx.x; i < j; i += blockDim.x) { csv[i] = cs[i]; snv[i] = sn[i]; }
+    for (int i = threadIdx.x; i <= j; i += blockDim.x) col[i] = hcol[i];
     double s = 0;
     for (int b = threadIdx.x; b < NB; b += blockDim.x) s += part[(size_t)b * ld].x;
     for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
@@ -300,13 +318,12 @@ __global__ void givens_kernel(const double2* __restrict__ part, int NB, int ld, 
     double tot = 0;
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += red[w];
     const double hn = sqrt(tot);
-    double2* col = H + (size_t)j * (m + 1);
     col[j + 1] = make_double2(hn, 0.0);
     for (int i = 0; i < j; ++i) {
         const double2 a = col[i], b = col[i + 1];
-        const double2 t = cadd(cscale(a, cs[i]), cmul(sn[i], b));
-        const double2 snc = make_double2(sn[i].x, -sn[i].y);
-        col[i + 1] = csub(cscale(b, cs[i]), cmul(snc, a));
+        const double2 t = cadd(cscale(a, csv[i]), cmul(snv[i], b));
+        const double2 snc = make_double2(snv[i].x, -snv[i].y);
+        col[i + 1] = csub(cscale(b, csv[i]), cmul(snc, a));
         col[i] = t;
     }
     double c;
@@ -315,7 +332,8 @@ __global__ void givens_kernel(const double2* __restrict__ part, int NB, int ld, 
     cs[j] = c;
     sn[j] = sj;
     col[j] = cadd(cscale(col[j], c), cmul(sj, col[j + 1]));
-    col[j + 1] = make_double2(0.0, 0.0);
+    for (int i = 0; i <= j; ++i) hcol[i] = col[i];
+    hcol[j + 1] = make_double2(0.0, 0.0);
     const double2 gj = g[j];
     g[j + 1] = cscale(cmul(make_double2(sj.x, -sj.y), gj), -1.0);
     g[j] = cscale(gj, c);
@@ -345,7 +363,7 @@ __global__ void __launch_bounds__(NT) combine_flex_kernel(const float2* __restri
                                                          const int* __restrict__ kdev) {
     __shared__ cdf ys[64];
     if (kdev) k = *kdev;
-    for (int i = threadIdx.x; i < k; i += NT) ys[i] = cdf{df_from_double(y[i].x), df_from_double(y[i].y)};
+    for (int i = threadIdx.x; i < k; i += NT) ys[i] = cdf_make(df_from_double(y[i].x), df_from_double(y[i].y));
     __syncthreads();
     for (size_t id = blockIdx.x * (size_t)NT + threadIdx.x; id < npts; id += (size_t)gridDim.x * NT) {
         cdf a = cdf_from4(x[id]);
@@ -666,7 +684,7 @@ helm_status gmres_run(helm_ctx* c, const double2* b_in, double2* x_in, helm_solv
                     const int nbd = launch_dots(c, k->V, npts, j + 1, w, k->part, ld, k->NBd, s);
                     prof_end(c, s);
                     prof_begin(c, s, PROF_SMALL);
-                    reduce_h_kernel<<<1, 256, 0, s>>>(k->part, nbd, ld, j + 1, k->sigma, k->H + (size_t)j * (m + 1),
+                    reduce_h_kernel<<<j + 1, 128, 0, s>>>(k->part, nbd, ld, j + 1, k->sigma, k->H + (size_t)j * (m + 1),
                                                       k->coef, pass == 0);
                     prof_end(c, s);
                     prof_begin(c, s, PROF_UPDATE);
@@ -1006,7 +1024,7 @@ helm_status lane_iteration(Lane& ln, int j, cudaGraphConditionalHandle hnext, in
     const int passes = c->opt.reorth ? 2 : 1;
     for (int pass = 0; pass < passes; ++pass) {
         const int nbd = launch_dots(c, k->V, npts, j + 1, w, k->part, ld, k->NBd, s);
-        reduce_h_kernel<<<1, 256, 0, s>>>(k->part, nbd, ld, j + 1, k->sigma, k->H + (size_t)j * (m + 1), k->coef,
+        reduce_h_kernel<<<j + 1, 128, 0, s>>>(k->part, nbd, ld, j + 1, k->sigma, k->H + (size_t)j * (m + 1), k->coef,
                                           pass == 0);
         update_kernel<<<NB, NT, 0, s>>>(k->V, npts, j + 1, k->coef, w, k->part, ld);
     }
