@@ -363,7 +363,7 @@ __global__ void __launch_bounds__(NT) combine_flex_kernel(const float2* __restri
                                                          const int* __restrict__ kdev) {
     __shared__ cdf ys[64];
     if (kdev) k = *kdev;
-    for (int i = threadIdx.x; i < k; i += NT) ys[i] = cdf_make(df_from_double(y[i].x), df_from_double(y[i].y));
+    for (int i = threadIdx.x; i < k; i += NT) ys[i] = cdf{df_from_double(y[i].x), df_from_double(y[i].y)};
     __syncthreads();
     for (size_t id = blockIdx.x * (size_t)NT + threadIdx.x; id < npts; id += (size_t)gridDim.x * NT) {
         cdf a = cdf_from4(x[id]);

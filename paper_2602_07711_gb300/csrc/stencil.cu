@@ -90,14 +90,11 @@ struct PDF {
         return df{h, (float)(v - (double)h)};
     }
     static __device__ __forceinline__ C zero() { return cdf_zero(); }
-    static __device__ __forceinline__ LC lo(C a) { return a.hi; }
+    static __device__ __forceinline__ LC lo(C a) { return make_float2(a.re.hi, a.im.hi); }
     static __device__ __forceinline__ C from_lo(LC a) { return cdf_from_f2(a); }
     static __device__ __forceinline__ void st(M* d, C v) { *d = cdf_to4(v); }
     static __device__ __forceinline__ float2 r32(C v) { return cdf_round(v); }
-    static __host__ C hc(double2 v) {
-        const df r = cst(v.x), i = cst(v.y);
-        return C{make_float2(r.hi, i.hi), make_float2(r.lo, i.lo)};
-    }
+    static __host__ C hc(double2 v) { return C{cst(v.x), cst(v.y)}; }
 };
 
 template <class P>
@@ -467,7 +464,7 @@ __global__ void rhs_df_kernel(int order, int nx, int ny, int nz, RhsW W, const f
     // integer weights are applied as exact power-of-two scalings; the edge points of the mixed
     // differences are the line neighbours already loaded, so only the corners are new loads.
     auto p2 = [](cdf a, float sc) {   // a * sc, sc a power of two: exact
-        return cdf{px_mul(a.hi, px_splat(sc)), px_mul(a.lo, px_splat(sc))};
+        return cdf{df{a.re.hi * sc, a.re.lo * sc}, df{a.im.hi * sc, a.im.lo * sc}};
     };
     cdf s13[3], s04[3];
     float2 fd[3];
@@ -480,7 +477,7 @@ __global__ void rhs_df_kernel(int order, int nx, int ny, int nz, RhsW W, const f
         o[d] = -2; const cdf vm2 = at(o[0], o[1], o[2]);
         s13[d] = cdf_add(vp1, vm1);
         s04[d] = cdf_add(vp2, vm2);
-        fd[d] = make_float2((vp1.hi.x - vm1.hi.x) * W.i2h[d], (vp1.hi.y - vm1.hi.y) * W.i2h[d]);
+        fd[d] = make_float2((vp1.re.hi - vm1.re.hi) * W.i2h[d], (vp1.im.hi - vm1.im.hi) * W.i2h[d]);
     }
     const cdf f30 = cdf_sub(p2(fc, 32.f), p2(fc, 2.f));   // 30 f
     const cdf f6 = cdf_add(p2(fc, 4.f), p2(fc, 2.f));     // 6 f

@@ -30,7 +30,6 @@
 //     every plane, so their offsets and ghost factors are computed once); a prepare pass per plane
 //     applies the ghost factors and forms KU = k^2 U once per staged point.
 #include "common.cuh"
-#include "f32x2.cuh"
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -67,11 +66,12 @@ __device__ __forceinline__ void cp8(void* smem, const void* gmem) {
 __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
 
-// componentwise complex arithmetic with real coefficients as packed two-lane FP32 instructions
-__device__ __forceinline__ float2 f2add(float2 a, float2 b) { return px_add(a, b); }
-__device__ __forceinline__ float2 f2sub(float2 a, float2 b) { return px_sub(a, b); }
-__device__ __forceinline__ float2 f2scl(float2 a, float s) { return px_mul(a, px_splat(s)); }
-__device__ __forceinline__ float2 f2fma(float s, float2 a, float2 b) { return px_fma(px_splat(s), a, b); }   // s a + b
+__device__ __forceinline__ float2 f2add(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 f2sub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 f2scl(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+__device__ __forceinline__ float2 f2fma(float s, float2 a, float2 b) {   // s a + b
+    return make_float2(fmaf(s, a.x, b.x), fmaf(s, a.y, b.y));
+}
 __device__ __forceinline__ float2 f2mul(float2 a, float2 b) {
     return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
 }
@@ -599,7 +599,7 @@ __device__ __forceinline__ cdf cdf_sc(cdf a) {
     constexpr df s = dfc((double)NUM / (double)DEN);
     return cdf_scale(a, s);
 }
-__device__ __forceinline__ float2 hi2(cdf a) { return a.hi; }
+__device__ __forceinline__ float2 hi2(cdf a) { return make_float2(a.re.hi, a.im.hi); }
 
 template <int ORDER>
 __global__ void __launch_bounds__(FNT, 2)
@@ -619,7 +619,7 @@ residual_fast_kernel(RParams p, const float4* __restrict__ X, float2* __restrict
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
         const int q = tid + k * FNT;
-        sgam[k] = cdf{make_float2(1.f, 0.f), make_float2(0.f, 0.f)};
+        sgam[k] = cdf{df{1.f, 0.f}, df{0.f, 0.f}};
         if (q < FHALO) {
             const int ly = q / FPX, lx = q - ly * FPX;
             const int Xg = x0 + lx - 1, Yg = y0 + ly - 1;
@@ -783,7 +783,7 @@ int rsmem() { return (int)(FNS * sizeof(RStage<ORDER>)); }
 
 cdf cdf_host(double2 v) {
     const float rh = (float)v.x, ih = (float)v.y;
-    return cdf{make_float2(rh, ih), make_float2((float)(v.x - (double)rh), (float)(v.y - (double)ih))};
+    return cdf{df{rh, (float)(v.x - (double)rh)}, df{ih, (float)(v.y - (double)ih)}};
 }
 df df_host(double v) {
     const float h = (float)v;
