@@ -40,6 +40,7 @@ struct TcState {
     float* Wy[4] = {nullptr, nullptr, nullptr, nullptr};   // y-pass operands, [2][N_y][ldw] (re, im planes)
     int ldw = 0;
     CUtensorMap mapBx[4];
+    CUtensorMap mapBx256[4];   // the same operands in 256-row boxes (256-wide x-pass tiles)
     CUtensorMap mapWy[4];
 };
 
@@ -327,6 +328,14 @@ ypass_tc_kernel(const __grid_constant__ CUtensorMap tmW, const __grid_constant__
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * BN) : "memory");
 }
 
+// stage counts of the persistent x-pass: 128-wide tiles two CTAs per SM, 256-wide tiles one CTA per SM
+// (2 x 256 accumulator columns fill the tensor memory); 1024 bytes of slack align the ring
+template <int BNT>
+struct PersX {
+    static constexpr int STAGES = BNT == 256 ? 4 : XSTAGES;
+    static constexpr size_t SMEM = (size_t)STAGES * (BM * BK * 4 + BNT * BK * 4) + XEPI_BYTES + 1024;
+};
+
 // ---- persistent x-pass: one CTA walks many output tiles, the accumulator is double-buffered in tensor
 // memory so that the epilogue of tile t overlaps the loads and MMAs of tile t+1 (the y-pass, whose two
 // accumulators per tile would need all 512 columns for double buffering, keeps one tile per CTA) --------
@@ -334,26 +343,28 @@ ypass_tc_kernel(const __grid_constant__ CUtensorMap tmW, const __grid_constant__
 // epilogue: accumulator buffer b holds a finished tile), acce[b] (epilogue -> MMA: buffer b drained; four
 // arrivals, one per epilogue warp).  Tiles are ordered N-fastest so that consecutive tiles of a CTA share
 // their A rows in L2.
+template <int BNT>
 __global__ void __launch_bounds__(192, 1)
 xpass_tc_pers_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                      float* __restrict__ out, int M, int N2, int K2, float alpha, const double* __restrict__ alpha_dev,
                      int aidx, unsigned* status) {
     extern __shared__ uint8_t dsm[];
-    __shared__ __align__(8) uint64_t full[XSTAGES], empty[XSTAGES], accf[2], acce[2];
+    constexpr int NS = PersX<BNT>::STAGES, BTILE = BNT * BK * 4, STAGE = TILE + BTILE;
+    __shared__ __align__(8) uint64_t full[NS], empty[NS], accf[2], acce[2];
     __shared__ uint32_t tslot;
     const uint32_t raw = su32(dsm);
     const uint32_t base = (raw + 1023u) & ~1023u;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nk = (K2 + BK - 1) / BK;
-    const int ntn = (N2 + BN - 1) / BN, ntm = (M + BM - 1) / BM, ntiles = ntn * ntm;
-    float* epi = reinterpret_cast<float*>(dsm + (base - raw) + XSTAGES * 2 * TILE);   // epilogue staging rows
+    const int ntn = (N2 + BNT - 1) / BNT, ntm = (M + BM - 1) / BM, ntiles = ntn * ntm;
+    float* epi = reinterpret_cast<float*>(dsm + (base - raw) + NS * STAGE);   // epilogue staging rows
     if (threadIdx.x == 0) {
-        for (int s = 0; s < XSTAGES; ++s) { mbar_init(su32(&full[s]), 1); mbar_init(su32(&empty[s]), 1); }
+        for (int s = 0; s < NS; ++s) { mbar_init(su32(&full[s]), 1); mbar_init(su32(&empty[s]), 1); }
         for (int b = 0; b < 2; ++b) { mbar_init(su32(&accf[b]), 1); mbar_init(su32(&acce[b]), 4); }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 1) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&tslot)), "r"(2 * BN)
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&tslot)), "r"(2 * BNT)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -366,14 +377,14 @@ xpass_tc_pers_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_const
         if (lane == 0) {
             long it = 0;
             for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
-                const int n0 = (t % ntn) * BN, m0 = (t / ntn) * BM;
+                const int n0 = (t % ntn) * BNT, m0 = (t / ntn) * BM;
                 for (int kb = 0; kb < nk && ok; ++kb, ++it) {
-                    const int s = (int)(it % XSTAGES);
-                    const uint32_t ph = (uint32_t)((it / XSTAGES) & 1);
-                    if (it >= XSTAGES) ok = mbar_wait(su32(&empty[s]), ph ^ 1);
+                    const int s = (int)(it % NS);
+                    const uint32_t ph = (uint32_t)((it / NS) & 1);
+                    if (it >= NS) ok = mbar_wait(su32(&empty[s]), ph ^ 1);
                     if (!ok) break;
-                    const uint32_t sa = base + s * 2 * TILE, sb = sa + TILE;
-                    mbar_expect_tx(su32(&full[s]), 2 * TILE);
+                    const uint32_t sa = base + s * STAGE, sb = sa + TILE;
+                    mbar_expect_tx(su32(&full[s]), STAGE);
                     tma_2d(sa, &tmA, su32(&full[s]), kb * BK, m0);
                     tma_2d(sb, &tmB, su32(&full[s]), kb * BK, n0);
                 }
@@ -381,7 +392,7 @@ xpass_tc_pers_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_const
         }
     } else if (warp == 1) {
         if (lane == 0) {
-            const uint32_t idesc = idesc_tf32(BM, BN, 0, 0);
+            const uint32_t idesc = idesc_tf32(BM, BNT, 0, 0);
             long it = 0;
             int lt = 0;
             for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++lt) {
@@ -389,14 +400,14 @@ xpass_tc_pers_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_const
                 if (lt >= 2) ok = mbar_wait(su32(&acce[b]), (uint32_t)(((lt >> 1) - 1) & 1));
                 if (!ok) break;
                 fence_after();
-                const uint32_t acc_t = tmem + (uint32_t)(b * BN);
+                const uint32_t acc_t = tmem + (uint32_t)(b * BNT);
                 for (int kb = 0; kb < nk && ok; ++kb, ++it) {
-                    const int s = (int)(it % XSTAGES);
-                    const uint32_t ph = (uint32_t)((it / XSTAGES) & 1);
+                    const int s = (int)(it % NS);
+                    const uint32_t ph = (uint32_t)((it / NS) & 1);
                     ok = mbar_wait(su32(&full[s]), ph);
                     if (!ok) break;
                     fence_after();
-                    const uint32_t sa = base + s * 2 * TILE, sb = sa + TILE;
+                    const uint32_t sa = base + s * STAGE, sb = sa + TILE;
 #pragma unroll
                     for (int kk = 0; kk < BK / 8; ++kk)
                         mma_tf32(acc_t, sdesc(sa + kk * 32, 16, 1024), sdesc(sb + kk * 32, 16, 1024), idesc,
@@ -412,7 +423,7 @@ xpass_tc_pers_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_const
         int lt = 0;
         for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++lt) {
             const int b = lt & 1;
-            const int n0 = (t % ntn) * BN, m0 = (t / ntn) * BM;
+            const int n0 = (t % ntn) * BNT, m0 = (t / ntn) * BM;
             ok = __all_sync(0xffffffffu, mbar_wait(su32(&accf[b]), (uint32_t)((lt >> 1) & 1)));
             if (!ok) break;
             fence_after();
@@ -421,9 +432,9 @@ xpass_tc_pers_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_const
             float* stg = epi + q * 32 * XEPI_LD;
             const int rbase = m0 + 32 * q;
 #pragma unroll 1
-            for (int c = 0; c < BN; c += 32) {
+            for (int c = 0; c < BNT; c += 32) {
                 uint32_t r[32];
-                TMEM_LD32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * BN + c), r);
+                TMEM_LD32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * BNT + c), r);
                 tmem_wait_ld();
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
@@ -460,7 +471,7 @@ xpass_tc_pers_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_const
     fence_before();
     __syncthreads();
     if (warp == 1)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * BN) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * BNT) : "memory");
 }
 
 // ---- operand preparation (set-up) ----------------------------------------------------------------
@@ -503,7 +514,6 @@ helm_status encode(TcState* t, CUtensorMap* map, int rank, void* ptr, const cuui
 }
 
 size_t xsmem() { return (size_t)XSTAGES * 2 * TILE + 1024; }
-size_t xpsmem() { return xsmem() + XEPI_BYTES; }
 size_t ysmem() { return (size_t)YSTAGES * 3 * TILE + 1024; }
 int g_sms = 0;
 
@@ -540,7 +550,10 @@ helm_status tc_prepare(helm_ctx* c, cudaStream_t s) {
         if (tc_encode_set(t, nx, ny, i) != HELM_OK) return HELM_ERR_CUDA;
     HELM_CUDA_TRY(cudaFuncSetAttribute(xpass_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)xsmem()));
     HELM_CUDA_TRY(cudaFuncSetAttribute(ypass_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ysmem()));
-    HELM_CUDA_TRY(cudaFuncSetAttribute(xpass_tc_pers_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)xpsmem()));
+    HELM_CUDA_TRY(cudaFuncSetAttribute(xpass_tc_pers_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)PersX<128>::SMEM));
+    HELM_CUDA_TRY(cudaFuncSetAttribute(xpass_tc_pers_kernel<256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)PersX<256>::SMEM));
     HELM_CUDA_TRY(cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, c->device));
     return HELM_OK;
 }
@@ -551,6 +564,10 @@ helm_status tc_encode_set(TcState* t, int nx, int ny, int i) {
     const cuuint64_t st[1] = {(cuuint64_t)2 * nx * sizeof(float)};
     const cuuint32_t box[2] = {BK, BN};
     if (encode(t, &t->mapBx[i], 2, t->Bx[i], d, st, box) != HELM_OK) return HELM_ERR_CUDA;
+    if ((2 * nx) % 256 == 0) {   // the only grids that take 256-wide tiles
+        const cuuint32_t box256[2] = {BK, 256};
+        if (encode(t, &t->mapBx256[i], 2, t->Bx[i], d, st, box256) != HELM_OK) return HELM_ERR_CUDA;
+    }
     const cuuint64_t dw[3] = {(cuuint64_t)ny, (cuuint64_t)ny, 2};
     const cuuint64_t sw[2] = {(cuuint64_t)t->ldw * sizeof(float), (cuuint64_t)t->ldw * ny * sizeof(float)};
     const cuuint32_t bw[3] = {BK, BM, 1};
@@ -594,10 +611,18 @@ helm_status tc_xpass(helm_ctx* c, int inverse, const float2* in, float2* out, fl
     if (encode(t, &mapA, 2, (void*)in, d, st, box) != HELM_OK) return HELM_ERR_CUDA;
     dim3 grid((N2 + BN - 1) / BN, (M + BM - 1) / BM);
     if (c->tune_tc == 1 && g_sms > 0) {
-        const int ntiles = (int)(grid.x * grid.y);
-        const int pg = ntiles < 2 * g_sms ? ntiles : 2 * g_sms;
-        xpass_tc_pers_kernel<<<pg, 192, xpsmem(), s>>>(mapA, t->mapBx[inverse], (float*)out, M, N2, N2, alpha, alpha_dev,
-                                                      aidx, c->status_d);
+        if (N2 % 256 == 0) {
+            // 256-wide tiles, one CTA per SM
+            const int ntiles = (N2 / 256) * (int)grid.y;
+            const int pg = ntiles < g_sms ? ntiles : g_sms;
+            xpass_tc_pers_kernel<256><<<pg, 192, PersX<256>::SMEM, s>>>(mapA, t->mapBx256[inverse], (float*)out, M, N2,
+                                                                         N2, alpha, alpha_dev, aidx, c->status_d);
+        } else {
+            const int ntiles = (int)(grid.x * grid.y);
+            const int pg = ntiles < 2 * g_sms ? ntiles : 2 * g_sms;
+            xpass_tc_pers_kernel<128><<<pg, 192, PersX<128>::SMEM, s>>>(mapA, t->mapBx[inverse], (float*)out, M, N2,
+                                                                         N2, alpha, alpha_dev, aidx, c->status_d);
+        }
     } else {
         xpass_tc_kernel<<<grid, 192, xsmem(), s>>>(mapA, t->mapBx[inverse], (float*)out, M, N2, N2, alpha, alpha_dev,
                                                     aidx, c->status_d);
