@@ -287,6 +287,112 @@ __global__ void __launch_bounds__(128) zsolve_fact_kernel(int nx, int ny, int nz
     }
 }
 
+// Factorised solve, L2-resident form (no generated right-hand side, even N_x).  The backward sweep reads
+// d and m again; when every line runs at once those re-reads (16 B/pt) miss the L2, so here a persistent
+// grid of a few 64-thread CTAs per SM keeps about 20k-40k lines in flight (their d and m stay in L2) and
+// walks the rest in turn.  Each thread takes two adjacent lines (16-byte accesses) and streams its inputs
+// through a private ring of ZB blocks of ZU steps in shared memory by cp.async (one group per block, no
+// block barrier); a landed block is read into registers at once and its ZU dependent steps then run back
+// to back, so the shared-memory latency is paid once per block rather than once per step.
+constexpr int ZRT = 64, ZU2 = 8, ZB = 4;
+constexpr size_t ZRING_BYTES = (size_t)ZB * ZU2 * 2 * ZRT * sizeof(float4);   // 64 KiB
+
+__device__ __forceinline__ void zcp16(void* smem, const void* gmem) {
+    const unsigned a = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(a), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void zcommit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void zwait_ring() { asm volatile("cp.async.wait_group %0;\n" ::"n"(ZB - 1) : "memory"); }
+__device__ __forceinline__ void zwait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+__global__ void __launch_bounds__(ZRT) zsolve_ring_kernel(int nx, int ny, int nz, float zz,
+                                                         const float4* __restrict__ m, const float4* in, float4* out) {
+    extern __shared__ float4 zring[];   // [ZB * ZU2][2][ZRT]
+    const int tid = threadIdx.x;
+    const int hx = nx / 2, npairs = hx * ny;
+    const int nblk = (nz + ZU2 - 1) / ZU2;
+    const size_t plane = (size_t)hx * ny;   // in float4 (two lines) units
+    auto slot = [&](int st, int a) -> float4* { return &zring[((size_t)st * 2 + a) * ZRT + tid]; };
+    for (int pr = blockIdx.x * ZRT + tid; pr < npairs; pr += gridDim.x * ZRT) {
+        const size_t off = (size_t)pr;   // pair pr = (j, i/2) is float4 pr of every plane
+        // ---- forward: d_l = (y_l - a_l d_{l-1}) m_l, steps in increasing l
+        auto fetch_f = [&](int b) {
+            if (b < nblk) {
+#pragma unroll
+                for (int u = 0; u < ZU2; ++u) {
+                    const int l = b * ZU2 + u;
+                    if (l < nz) {
+                        zcp16(slot((b % ZB) * ZU2 + u, 0), in + off + (size_t)l * plane);
+                        zcp16(slot((b % ZB) * ZU2 + u, 1), m + off + (size_t)l * plane);
+                    }
+                }
+            }
+            zcommit();
+        };
+        for (int b = 0; b < ZB - 1; ++b) fetch_f(b);
+        float2 d0 = f2(0.f, 0.f), d1 = d0;
+        for (int b = 0; b < nblk; ++b) {
+            fetch_f(b + ZB - 1);
+            zwait_ring();   // block b has landed
+            float4 y[ZU2], mm[ZU2];
+#pragma unroll
+            for (int u = 0; u < ZU2; ++u) {
+                y[u] = *slot((b % ZB) * ZU2 + u, 0);
+                mm[u] = *slot((b % ZB) * ZU2 + u, 1);
+            }
+#pragma unroll
+            for (int u = 0; u < ZU2; ++u) {
+                const int l = b * ZU2 + u;
+                if (l < nz) {
+                    const float a = l == 0 ? 0.f : (l == nz - 1 ? zz : 1.f);
+                    d0 = cmul(csub(f2(y[u].x, y[u].y), cscale(d0, a)), f2(mm[u].x, mm[u].y));
+                    d1 = cmul(csub(f2(y[u].z, y[u].w), cscale(d1, a)), f2(mm[u].z, mm[u].w));
+                    out[off + (size_t)l * plane] = make_float4(d0.x, d0.y, d1.x, d1.y);
+                }
+            }
+        }
+        zwait_all();
+        __threadfence_block();
+        // ---- backward: x_l = d_l - s_l m_l x_{l+1}, steps in decreasing l (block b holds l = nz-1-(b ZU2 + u))
+        auto fetch_b = [&](int b) {
+            if (b < nblk) {
+#pragma unroll
+                for (int u = 0; u < ZU2; ++u) {
+                    const int l = nz - 1 - (b * ZU2 + u);
+                    if (l >= 0) {
+                        zcp16(slot((b % ZB) * ZU2 + u, 0), out + off + (size_t)l * plane);
+                        zcp16(slot((b % ZB) * ZU2 + u, 1), m + off + (size_t)l * plane);
+                    }
+                }
+            }
+            zcommit();
+        };
+        for (int b = 0; b < ZB - 1; ++b) fetch_b(b);
+        float2 x0 = f2(0.f, 0.f), x1 = x0;
+        for (int b = 0; b < nblk; ++b) {
+            fetch_b(b + ZB - 1);
+            zwait_ring();
+            float4 dv[ZU2], mm[ZU2];
+#pragma unroll
+            for (int u = 0; u < ZU2; ++u) {
+                dv[u] = *slot((b % ZB) * ZU2 + u, 0);
+                mm[u] = *slot((b % ZB) * ZU2 + u, 1);
+            }
+#pragma unroll
+            for (int u = 0; u < ZU2; ++u) {
+                const int l = nz - 1 - (b * ZU2 + u);
+                if (l >= 0) {
+                    const float sup = l == nz - 1 ? 0.f : (l == 0 ? zz : 1.f);
+                    x0 = csub(f2(dv[u].x, dv[u].y), cscale(cmul(f2(mm[u].x, mm[u].y), x0), sup));
+                    x1 = csub(f2(dv[u].z, dv[u].w), cscale(cmul(f2(mm[u].z, mm[u].w), x1), sup));
+                    out[off + (size_t)l * plane] = make_float4(x0.x, x0.y, x1.x, x1.y);
+                }
+            }
+        }
+        zwait_all();
+    }
+}
+
 }  // namespace
 
 // Set-up: the Thomas factors of the z-systems with lateral eigenvalue shifts dxs_i + dys_j (one complex64
@@ -294,6 +400,11 @@ __global__ void __launch_bounds__(128) zsolve_fact_kernel(int nx, int ny, int nz
 helm_status zsolve_factor_with(helm_ctx* c, const float2* dxs, const float2* dys, float2** m, cudaStream_t s) {
     if (!*m) {
         if (cudaMalloc(m, c->npts * sizeof(float2)) != cudaSuccess) { cudaGetLastError(); return HELM_ERR_NOMEM; }
+    }
+    if (!c->zring_sms) {   // the ring kernel of the factorised solve: shared memory and grid size
+        HELM_CUDA_TRY(cudaFuncSetAttribute(zsolve_ring_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)ZRING_BYTES));
+        HELM_CUDA_TRY(cudaDeviceGetAttribute(&c->zring_sms, cudaDevAttrMultiProcessorCount, c->device));
     }
     ZParams p;
     p.nx = c->nx; p.ny = c->ny; p.nz = c->nz;
@@ -313,6 +424,18 @@ helm_status zsolve_factor(helm_ctx* c, cudaStream_t s) { return zsolve_factor_wi
 helm_status launch_zsolve_fact(helm_ctx* c, const float2* m, const float2* in, float2* out, const float2* P,
                                const float2* Q, cudaStream_t s) {
     prof_begin(c, s, PROF_ZSOLVE);
+    if (!P && in && c->nx % 2 == 0 && c->tune_zring && c->zring_sms > 0) {
+        const int sms = c->zring_sms;
+        const int npairs = c->nx / 2 * c->ny;
+        const int need = (npairs + ZRT - 1) / ZRT;
+        const int grid = need < sms * c->tune_zring ? need : sms * c->tune_zring;
+        zsolve_ring_kernel<<<grid, ZRT, ZRING_BYTES, s>>>(c->nx, c->ny, c->nz, (float)c->zeta[2],
+                                                         reinterpret_cast<const float4*>(m),
+                                                         reinterpret_cast<const float4*>(in), reinterpret_cast<float4*>(out));
+        prof_end(c, s);
+        HELM_CUDA_TRY(cudaGetLastError());
+        return HELM_OK;
+    }
     dim3 grid((c->nx + 127) / 128, c->ny);
     zsolve_fact_kernel<<<grid, 128, 0, s>>>(c->nx, c->ny, c->nz, (float)c->zeta[2], m, in, out, P, Q);
     prof_end(c, s);
