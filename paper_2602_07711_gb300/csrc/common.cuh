@@ -133,6 +133,7 @@ struct helm_ctx {
     int tune_stencil = 0;                   // complex64 matvec variant chosen by helm_autotune (0 = cp.async ring)
     int zring_sms = 0;                      // SM count, set with the ring kernel's attributes at set-up
     int tune_zring = 2;                     // factorised z-solve: CTAs per SM of the L2-resident ring kernel (0 = one thread per line)
+    int tune_ypers = 1;                     // y-pass: 1 persistent with double-buffered accumulators, 0 one tile per CTA
     int tune_tc = 1;                        // x-pass on the tensor cores: 1 persistent, 0 one tile per CTA
     int tune_dots = 2;                      // inner-product kernel variant (helm_autotune; 2 measured best)
     cudaStream_t last_stream = nullptr;

@@ -474,6 +474,148 @@ xpass_tc_pers_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_const
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * BNT) : "memory");
 }
 
+// ---- persistent y-pass: the accumulator pair (P, Q) of a tile is double-buffered in tensor memory
+// (2 x 2 x 128 columns), so the epilogue of tile t overlaps the loads and MMAs of tile t+1; one CTA per
+// SM.  Tiles are ordered (slice, column block, row block) with the row block fastest, so that the two row
+// blocks of a data tile run at the same time on neighbouring CTAs and share it in L2.  Barriers as in the
+// persistent x-pass.
+constexpr int YPS = 4;                                         // pipeline stages
+constexpr size_t YP_SMEM = (size_t)YPS * 3 * TILE + 4 * 32 * YEPI_LD * 4 + 1024;
+
+__global__ void __launch_bounds__(192, 1)
+ypass_tc_pers_kernel(const __grid_constant__ CUtensorMap tmW, const __grid_constant__ CUtensorMap tmY,
+                     float* __restrict__ out, int ny, int N2, int nz, unsigned* status) {
+    extern __shared__ uint8_t dsm[];
+    constexpr int STAGE = 3 * TILE;   // Wr tile, Wi tile, B tile (4 boxes of 32 K-rows x 128 bytes)
+    __shared__ __align__(8) uint64_t full[YPS], empty[YPS], accf[2], acce[2];
+    __shared__ uint32_t tslot;
+    const uint32_t raw = su32(dsm);
+    const uint32_t base = (raw + 1023u) & ~1023u;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nk = (ny + BK - 1) / BK;
+    const int ntm = (ny + BM - 1) / BM, ntn = (N2 + BN - 1) / BN, ntiles = ntm * ntn * nz;
+    float* epi = reinterpret_cast<float*>(dsm + (base - raw) + YPS * STAGE);   // epilogue staging rows
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < YPS; ++s) { mbar_init(su32(&full[s]), 1); mbar_init(su32(&empty[s]), 1); }
+        for (int b = 0; b < 2; ++b) { mbar_init(su32(&accf[b]), 1); mbar_init(su32(&acce[b]), 4); }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&tslot)), "r"(4 * BN)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem = tslot;
+    bool ok = true;
+    if (warp == 0) {
+        if (lane == 0) {
+            long it = 0;
+            for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+                const int mb = t % ntm, nb = (t / ntm) % ntn, l = t / (ntm * ntn);
+                const int m0 = mb * BM, n0 = nb * BN;
+                for (int kb = 0; kb < nk && ok; ++kb, ++it) {
+                    const int s = (int)(it % YPS);
+                    const uint32_t ph = (uint32_t)((it / YPS) & 1);
+                    if (it >= YPS) ok = mbar_wait(su32(&empty[s]), ph ^ 1);
+                    if (!ok) break;
+                    const uint32_t sw = base + s * STAGE, sb = sw + 2 * TILE;
+                    mbar_expect_tx(su32(&full[s]), STAGE);
+                    tma_3d(sw, &tmW, su32(&full[s]), kb * BK, m0, 0);
+                    tma_3d(sw + TILE, &tmW, su32(&full[s]), kb * BK, m0, 1);
+#pragma unroll
+                    for (int q = 0; q < BN / 32; ++q) tma_3d(sb + q * 4096, &tmY, su32(&full[s]), n0 + 32 * q, kb * BK, l);
+                }
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            const uint32_t idesc = idesc_tf32(BM, BN, 0, 1);
+            long it = 0;
+            int lt = 0;
+            for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++lt) {
+                const int b = lt & 1;
+                if (lt >= 2) ok = mbar_wait(su32(&acce[b]), (uint32_t)(((lt >> 1) - 1) & 1));
+                if (!ok) break;
+                fence_after();
+                const uint32_t accP = tmem + (uint32_t)(b * 2 * BN), accQ = accP + BN;
+                for (int kb = 0; kb < nk && ok; ++kb, ++it) {
+                    const int s = (int)(it % YPS);
+                    const uint32_t ph = (uint32_t)((it / YPS) & 1);
+                    ok = mbar_wait(su32(&full[s]), ph);
+                    if (!ok) break;
+                    fence_after();
+                    const uint32_t sw = base + s * STAGE, sb = sw + 2 * TILE;
+#pragma unroll
+                    for (int kk = 0; kk < BK / 8; ++kk) {
+                        // MN-major: LBO = next 32-column chunk (4 KiB), SBO = next 4-row K group (512 B)
+                        const uint64_t bd = sdesc(sb + kk * 1024, 4096, 512, 1);
+                        const uint32_t acc = (kb | kk) ? 1u : 0u;
+                        mma_tf32(accP, sdesc(sw + kk * 32, 16, 1024), bd, idesc, acc);
+                        mma_tf32(accQ, sdesc(sw + TILE + kk * 32, 16, 1024), bd, idesc, acc);
+                    }
+                    mma_commit(su32(&empty[s]));
+                }
+                if (ok) mma_commit(su32(&accf[b]));
+            }
+        }
+    } else {
+        const int q = warp & 3;
+        float* stg = epi + q * 32 * YEPI_LD;
+        int lt = 0;
+        for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++lt) {
+            const int b = lt & 1;
+            const int mb = t % ntm, nb = (t / ntm) % ntn, l = t / (ntm * ntn);
+            const int m0 = mb * BM, n0 = nb * BN;
+            ok = __all_sync(0xffffffffu, mbar_wait(su32(&accf[b]), (uint32_t)((lt >> 1) & 1)));
+            if (!ok) break;
+            fence_after();
+            const int rbase = m0 + 32 * q;
+#pragma unroll 1
+            for (int c = 0; c < BN; c += 32) {
+                uint32_t p[32], qq[32];
+                TMEM_LD32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * 2 * BN + c), p);
+                TMEM_LD32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * 2 * BN + BN + c), qq);
+                tmem_wait_ld();
+#pragma unroll
+                for (int v = 0; v < 32; v += 4)
+                    *reinterpret_cast<float4*>(stg + lane * YEPI_LD + v) =
+                        make_float4(__uint_as_float(p[v]) - __uint_as_float(qq[v + 1]),
+                                    __uint_as_float(p[v + 1]) + __uint_as_float(qq[v]),
+                                    __uint_as_float(p[v + 2]) - __uint_as_float(qq[v + 3]),
+                                    __uint_as_float(p[v + 3]) + __uint_as_float(qq[v + 2]));
+                __syncwarp();
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    const int rr = 4 * i + (lane >> 3), cc = 4 * (lane & 7);
+                    const int grow = rbase + rr, gcol = n0 + c + cc;
+                    const float4 v = *reinterpret_cast<const float4*>(stg + rr * YEPI_LD + cc);
+                    if (grow < ny && gcol < N2) {
+                        float* dst = out + ((size_t)l * ny + grow) * N2 + gcol;
+                        if (gcol + 4 <= N2) *reinterpret_cast<float4*>(dst) = v;
+                        else {
+                            dst[0] = v.x;
+                            if (gcol + 1 < N2) dst[1] = v.y;
+                            if (gcol + 2 < N2) dst[2] = v.z;
+                        }
+                    }
+                }
+                __syncwarp();
+            }
+            fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(su32(&acce[b]));
+        }
+    }
+    if (!ok) atomicOr(status, (unsigned)HELM_DEV_WAIT);
+    fence_before();
+    __syncthreads();
+    if (warp == 1)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(4 * BN) : "memory");
+}
+
 // ---- operand preparation (set-up) ----------------------------------------------------------------
 __device__ __forceinline__ float to_tf32(double v) {
     uint32_t r;
@@ -550,6 +692,7 @@ helm_status tc_prepare(helm_ctx* c, cudaStream_t s) {
         if (tc_encode_set(t, nx, ny, i) != HELM_OK) return HELM_ERR_CUDA;
     HELM_CUDA_TRY(cudaFuncSetAttribute(xpass_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)xsmem()));
     HELM_CUDA_TRY(cudaFuncSetAttribute(ypass_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ysmem()));
+    HELM_CUDA_TRY(cudaFuncSetAttribute(ypass_tc_pers_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)YP_SMEM));
     HELM_CUDA_TRY(cudaFuncSetAttribute(xpass_tc_pers_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)PersX<128>::SMEM));
     HELM_CUDA_TRY(cudaFuncSetAttribute(xpass_tc_pers_kernel<256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -641,7 +784,13 @@ helm_status tc_ypass(helm_ctx* c, int inverse, const float2* in, float2* out, cu
     const cuuint32_t box[3] = {32, BK, 1};
     if (encode(t, &mapY, 3, (void*)in, d, st, box, CU_TENSOR_MAP_SWIZZLE_128B_ATOM_32B) != HELM_OK) return HELM_ERR_CUDA;
     dim3 grid((N2 + BN - 1) / BN, (ny + BM - 1) / BM, c->nz);
-    ypass_tc_kernel<<<grid, 192, ysmem(), s>>>(t->mapWy[inverse], mapY, (float*)out, ny, N2, c->status_d);
+    if (c->tune_ypers && g_sms > 0) {
+        const int ntiles = (int)(grid.x * grid.y * grid.z);
+        const int pg = ntiles < g_sms ? ntiles : g_sms;
+        ypass_tc_pers_kernel<<<pg, 192, YP_SMEM, s>>>(t->mapWy[inverse], mapY, (float*)out, ny, N2, c->nz, c->status_d);
+    } else {
+        ypass_tc_kernel<<<grid, 192, ysmem(), s>>>(t->mapWy[inverse], mapY, (float*)out, ny, N2, c->status_d);
+    }
     HELM_CUDA_TRY(cudaGetLastError());
     return HELM_OK;
 }
