@@ -44,10 +44,11 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--e2e", type=int, default=1)
     p.add_argument("--max-iter", type=int, default=300)
-    p.add_argument("--workload", default="n256", choices=["n256", "batched", "pfft", "learned"],
+    p.add_argument("--workload", default="n256", choices=["n256", "batched", "pfft", "learned", "scatter"],
                    help="n256: the headline solve; batched: 64 uneven problems x 4 right-hand sides in one "
                         "batched call; pfft: 512^3 layered medium, PFFT vs EigT; learned: 384^3 high-contrast "
-                        "medium, learned correction vs plain EigT")
+                        "medium, learned correction vs plain EigT; scatter: the single-inclusion scattering "
+                        "problem of Sec. 5.2 at 100^3, 200^3, 400^3")
     p.add_argument("--problems", type=int, default=64, help="batched workload: number of problems")
     p.add_argument("--autotune", type=int, default=0,
                    help="time the kernel variants on the grid before the run (default: the measured defaults)")
@@ -562,6 +563,44 @@ def run_pfft(args, rank, world, local):
         print(json.dumps(line), flush=True)
 
 
+# inner iterations printed for EigT2-preconditioned sixth-order GMRES(20) in the scattering table of
+# Sec. 5.2 (single inclusion), per staggered grid size: context for the iteration counts here
+PAPER_SCATTER_N0 = {100: 12, 200: 11, 400: 11}
+
+
+def run_scatter(args, rank, world, local):
+    """The single-inclusion scattering problem of Sec. 5.2 (k^2 = 1050 + 2.26i inside r = 0.1 at
+    (0.5, 0.5, 0.7), 439.2 outside, f = -(k^2 - k0^2) e^{i k0 z}, staggered grid, sixth order) at 100^3,
+    200^3 and 400^3: EigT with FGMRES(20) in mixed precision to rel-res 1e-8 on the FP64 true residual."""
+    import torch
+
+    from paper_2602_07711_gb300 import helm, media
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    rtol = 1e-8 if args.rtol == 1e-6 else args.rtol
+    restart = 20 if args.restart == 30 else args.restart
+    out = {}
+    for n in (100, 200, 400):
+        k2, f, k0 = media.sphere(n, device=dev, as_numpy=False)
+        S = helm.Solver((n, n, n), k2, k0, order=6, precond=helm.HELM_PRECOND_EIGT, precision=1, restart=restart,
+                        max_iter=args.max_iter, rtol=rtol, flexible=True)
+        dt, infos = _timed_solve(S, f, max(1, args.steps))
+        i = infos[-1]
+        out[n] = {"time_to_rtol_s": dt, "iterations": i.iterations, "cycles": list(i.cycle_its[:i.restarts]),
+                  "status": i.status, "relres_true": i.relres_true, "Mpts_iter_s": n ** 3 * i.iterations / dt / 1e6,
+                  "paper_N0_fp64": PAPER_SCATTER_N0[n]}
+        S.close()
+        del k2, f
+        torch.cuda.empty_cache()
+    if rank == 0:
+        v = out[400]["Mpts_iter_s"] * world
+        line = _base_line(args, world, v, out[400]["time_to_rtol_s"] * args.steps, "sphere-scatter-order6",
+                          {"config": {"sizes": [100, 200, 400], "precond": "EigT", "precision": "tf32",
+                                      "krylov": "FGMRES(%d)" % restart, "rtol": rtol},
+                           "runs": out, "roofline": None, "cpu_baseline": None, "e2e": None})
+        print(json.dumps(line), flush=True)
+
+
 def run_learned(args, rank, world, local):
     """384^3, order 6, 8 points per wavelength, k^2/k0^2 in [0.5,1.8] (8 layers + 5 spheres): the U-Net is
     trained on the GPU on pairs from 96^3 solves of the same family, then FGMRES(30)+EigT with and without it."""
@@ -605,6 +644,8 @@ def main():
         run_batched(args, rank, world, local)
     elif args.workload == "pfft":
         run_pfft(args, rank, world, local)
+    elif args.workload == "scatter":
+        run_scatter(args, rank, world, local)
     else:
         run_learned(args, rank, world, local)
     if world > 1:

@@ -206,3 +206,32 @@ def test_residual_resolves_small_residuals(order):
     assert ref2 < 1e-6 * np.linalg.norm(F)
     assert abs(n2 - ref2) <= 0.02 * ref2, (n2, ref2)
     assert abs(ni - np.abs(r_ref).max()) <= 0.05 * np.abs(r_ref).max()
+
+
+@pytest.mark.parametrize("rtol", [1e-6, 1e-8])
+def test_scattering_sphere_matches_oracle(rtol):
+    """The single-inclusion scattering problem of Sec. 5.2 (k^2 = 1050 + 2.26i inside r = 0.1 at
+    (0.5, 0.5, 0.7), 439.2 outside, f = -(k^2 - k0^2) e^{i k0 z}, staggered grid) at 40^3, sixth order,
+    EigT + FGMRES(20) as in the paper's table, mixed precision on the GPU against the FP64 oracle."""
+    n = 40
+    k2, f, k0 = media.sphere(n)
+    S = Solver((n, n, n), k2, k0, order=6, flexible=True, rtol=rtol, restart=20, max_iter=200)
+    F = S.build_rhs(_dev(f))
+    x, info = S.solve(F)
+    g = Grid(n, n, n, staggered=True)
+    A = Operator(g, k2, k0, 6)
+    e = EigT(g, k0)
+    Fh = F.cpu().numpy()
+    xo, _ = gmres(A, e.apply_Minv, Fh, m=20, rtol=1e-12, max_it=400)
+    xo = xo.reshape(g.shape)
+    _, io = gmres(A, e.apply_Minv, Fh, m=20, rtol=rtol, max_it=400, flexible=True)
+    xg = x.cpu().numpy()
+    assert info.status == 0 and info.relres_true <= rtol
+    assert np.linalg.norm(A(xg) - Fh) / np.linalg.norm(Fh) <= 1.5 * rtol   # the oracle's FP64 residual
+    assert np.linalg.norm(xg - xo) / np.linalg.norm(xo) <= 10 * rtol
+    if rtol >= 1e-6:
+        # within complex64's reach the Krylov process is the oracle's
+        assert abs(info.iterations - io["iterations"]) <= 1
+    else:
+        # below it the FP32 basis needs restarts from the double-float true residual
+        assert io["iterations"] <= info.iterations <= 2 * io["iterations"] + 5

@@ -17,7 +17,7 @@ from oracle.eigt import EigT
 from oracle.gmres import gmres
 from oracle.grid import Grid, gamma_two_point
 from oracle.model1d import d_r, matrices
-from oracle.operators import Operator, apply_A4, apply_A6, pad_coef
+from oracle.operators import Operator, apply_A4, apply_A6, derived_k2_fields, pad_coef
 from oracle.pfft import PFFT
 from oracle.rhs import f_derivative_fields, rhs6, rhs6_sampled
 from oracle.tridiag import thomas
@@ -326,3 +326,34 @@ def test_sampled_rhs6_matches_analytic_in_interior():
         s = slice(N // 4, 3 * N // 4)
         errs.append(np.abs(Fa - Fs)[s, s, s].max() / np.abs(Fa).max())
     assert math.log2(errs[0] / errs[1]) > 5.6, errs
+
+
+# ---- golden: Table tab:scattering_results (EigT2 iteration counts) ------------------------------
+def _golden_scatter():
+    rows = []
+    with open(os.path.join(GOLDEN, "scattering_table.txt")) as fh:
+        for line in fh:
+            if line.strip() and not line.startswith("#"):
+                n, n0 = line.split()
+                rows.append((int(n), int(n0)))
+    return rows
+
+
+@pytest.mark.parametrize("row", [r for r in _golden_scatter() if r[0] <= 100])
+def test_paper_scattering_iterations(row):
+    """The oracle's sixth-order GMRES(20) + EigT2 on the Sec. 5.2 inclusion reaches rel-res 1e-8 in the
+    printed number of inner iterations (the larger grids of the table take minutes on a CPU)."""
+    N, n0_paper = row
+    g = Grid(N, N, N, staggered=True)
+    X, Y, Z = g.mesh()
+    k02 = 439.2
+    inside = (X - 0.5) ** 2 + (Y - 0.5) ** 2 + (Z - 0.7) ** 2 <= 0.1 ** 2
+    k2 = np.where(inside, 1050 + 2.26j, k02 + 0j)
+    k0 = math.sqrt(k02)
+    f = -(k2 - k02) * np.exp(1j * k0 * Z)
+    dk2, _ = derived_k2_fields(k2, True, g.h)
+    F = rhs6_sampled(f, k2, dk2, True, g.h)
+    A = Operator(g, k2, k0, 6)
+    x, info = gmres(A, EigT(g, k0).apply_Minv, F, m=20, rtol=1e-8, max_it=100)
+    assert info["converged"] and info["iterations"] == n0_paper
+    assert np.linalg.norm(A(x.reshape(g.shape)) - F) / np.linalg.norm(F) <= 1e-8
