@@ -24,7 +24,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "time-to-rtol 1e-6 (s) & Mpts·iter/s at n=256³; mixed/learned vs plain EigT"
 UNIT = "Mpts·iter/s"
-PREC_NAMES = {"fp32": 0, "tf32": 1, "3xtf32": 2}
+PREC_NAMES = {"fp32": 0, "tf32": 1}
 CLASSES = ["stencil", "xpass", "ypass", "zsolve", "dots", "update", "small", "combine", "residual", "other",
            "learned"]
 

@@ -58,12 +58,12 @@ typedef struct {
 enum { HELM_PRECOND_NONE = 0, HELM_PRECOND_EIGT = 1, HELM_PRECOND_PFFT = 2 };
 
 /* Arithmetic of the eigenvector transforms (EigT steps 2 and 4).  The stencil, the z-solves and the
- * Krylov vectors are complex64 in every mode; the Hessenberg/Givens update, the 1D eigensetup and the
- * true residual are FP64 in every mode.
+ * Krylov vectors are complex64 in every mode; the Hessenberg/Givens update and the 1D eigensetup are FP64,
+ * the true residual, the right-hand side and the iterate double-float (about 44 bits) in every mode.
  *   HELM_PREC_FP32    complex64 on the CUDA cores (FFMA), the "plain complex64" method
- *   HELM_PREC_TF32    tcgen05 tensor cores, TF32 operands, FP32 accumulation in TMEM (one product)
- *   HELM_PREC_3XTF32  tcgen05, split TF32 (hi*hi + hi*lo + lo*hi), about FP32 accuracy               */
-enum { HELM_PREC_FP32 = 0, HELM_PREC_TF32 = 1, HELM_PREC_3XTF32 = 2 };
+ *   HELM_PREC_TF32    tcgen05 tensor cores, TF32 operands, FP32 accumulation in TMEM (one product); needs
+ *                     even N_x                                                                          */
+enum { HELM_PREC_FP32 = 0, HELM_PREC_TF32 = 1 };
 
 typedef struct {
     int order;       /* 2, 4 (Eq. scheme4, any h_x, h_y, h_z) or 6 (Eq. scheme6, needs h_x = h_y = h_z)  */

@@ -118,7 +118,7 @@ struct helm_ctx {
     float2 *dxs = nullptr, *dys = nullptr;  // alpha_x D_x, alpha_y D_y
     float2 *cz = nullptr;                   // h_z^2 k0^2(z_l) - 2(alpha_x + alpha_y + 1)
     float2 *zfac = nullptr;                 // Thomas factors m of the EigT z-systems, one per point
-    // tensor-core operands (split TF32), allocated for the TC modes
+    // tensor-core operands, allocated for the TF32 mode
     float *XFr = nullptr, *XIr = nullptr;   // real-embedded x-pass B, [2N][2K] K-major (hi, lo follow)
     float *YFr = nullptr, *YIr = nullptr;   // y-pass A: re and im planes [2][N][N] (hi, lo follow)
     void* tmaps = nullptr;                  // host copies of TMA descriptors (gemm_tc.cu)

@@ -665,7 +665,7 @@ helm_status tc_encode_set(TcState* t, int nx, int ny, int i);
 
 helm_status tc_prepare(helm_ctx* c, cudaStream_t s) {
     if (c->nx % 2 != 0) return HELM_ERR_UNSUPPORTED;
-    if (c->opt.precision != HELM_PREC_TF32) return HELM_ERR_UNSUPPORTED;   // split TF32 not built yet
+    if (c->opt.precision != HELM_PREC_TF32) return HELM_ERR_UNSUPPORTED;
     TcState* t = new TcState();
     c->tmaps = t;
     cudaDriverEntryPointQueryResult q;
