@@ -407,21 +407,43 @@ __global__ void add_kernel(const float2* __restrict__ z, float4* __restrict__ x,
 }
 
 // FP64 -> double-float; flags a nonzero entry of a (used to recognise x0 = 0)
+// The conversions stream 32 bytes per point; four independent loads per thread keep enough bytes in flight.
 __global__ void to_df_kernel(const double2* __restrict__ a, float4* __restrict__ b, size_t npts, unsigned* nz) {
     unsigned any = 0;
-    for (size_t id = blockIdx.x * (size_t)blockDim.x + threadIdx.x; id < npts; id += (size_t)gridDim.x * blockDim.x) {
-        const double2 v = a[id];
-        const float rh = (float)v.x, ih = (float)v.y;
-        b[id] = make_float4(rh, ih, (float)(v.x - (double)rh), (float)(v.y - (double)ih));
-        any |= (v.x != 0.0 || v.y != 0.0);
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    for (size_t id0 = blockIdx.x * (size_t)blockDim.x + threadIdx.x; id0 < npts; id0 += 4 * stride) {
+        double2 v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const size_t id = id0 + u * stride;
+            v[u] = id < npts ? a[id] : make_double2(0.0, 0.0);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const size_t id = id0 + u * stride;
+            if (id < npts) {
+                const float rh = (float)v[u].x, ih = (float)v[u].y;
+                b[id] = make_float4(rh, ih, (float)(v[u].x - (double)rh), (float)(v[u].y - (double)ih));
+                any |= (v[u].x != 0.0 || v[u].y != 0.0);
+            }
+        }
     }
     if (nz && __any_sync(0xffffffffu, any) && (threadIdx.x & 31) == 0) atomicOr(nz, 1u);
 }
-
 __global__ void from_df_kernel(const float4* __restrict__ a, double2* __restrict__ b, size_t npts) {
-    for (size_t id = blockIdx.x * (size_t)blockDim.x + threadIdx.x; id < npts; id += (size_t)gridDim.x * blockDim.x) {
-        const float4 v = a[id];
-        b[id] = make_double2((double)v.x + (double)v.z, (double)v.y + (double)v.w);
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    for (size_t id0 = blockIdx.x * (size_t)blockDim.x + threadIdx.x; id0 < npts; id0 += 4 * stride) {
+        float4 v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const size_t id = id0 + u * stride;
+            v[u] = id < npts ? a[id] : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const size_t id = id0 + u * stride;
+            if (id < npts) b[id] = make_double2((double)v[u].x + (double)v[u].z, (double)v[u].y + (double)v[u].w);
+        }
     }
 }
 

@@ -519,8 +519,20 @@ __global__ void rhs_df_kernel(int order, int nx, int ny, int nz, RhsW W, const f
 }
 
 __global__ void f64_to_df_kernel(const double2* __restrict__ a, float4* __restrict__ b, size_t n) {
-    for (size_t id = blockIdx.x * (size_t)blockDim.x + threadIdx.x; id < n; id += (size_t)gridDim.x * blockDim.x)
-        b[id] = split4(a[id]);
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    for (size_t id0 = blockIdx.x * (size_t)blockDim.x + threadIdx.x; id0 < n; id0 += 4 * stride) {
+        double2 v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const size_t id = id0 + u * stride;
+            v[u] = id < n ? a[id] : make_double2(0.0, 0.0);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const size_t id = id0 + u * stride;
+            if (id < n) b[id] = split4(v[u]);
+        }
+    }
 }
 
 template <class P, int MODE>
@@ -607,7 +619,7 @@ helm_status launch_residual(helm_ctx* c, const float4* x, const float4* F, float
 // F from samples f (FP64); fdf is a double-float scratch grid of the caller
 helm_status launch_rhs(helm_ctx* c, const double2* f, double2* F, float4* fdf, cudaStream_t s) {
     prof_begin(c, s, PROF_OTHER);
-    f64_to_df_kernel<<<1024, 256, 0, s>>>(f, fdf, c->npts);
+    f64_to_df_kernel<<<2048, 256, 0, s>>>(f, fdf, c->npts);
     RhsW W;
     const double hh[3] = {c->h[0], c->h[1], c->h[2]};
     const double h2 = hh[0] * hh[0];
