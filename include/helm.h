@@ -203,6 +203,12 @@ helm_status helm_residual_noalloc(helm_ctx* ctx, const void* b, const void* x, v
  * call allocates the event pool (host-side cost only). */
 helm_status helm_profile(helm_ctx* ctx, int enable);
 
+/* helm_profile_classes - as helm_profile, but events are recorded only around the launches of the kernel
+ * classes whose bits are set in mask (bit i = class i in the order of helm_profile_read; mask 0 disables
+ * timing).  Timing one class keeps the events off the rest of the solve, whose launches then follow one
+ * another without them.  Measurement only: the paper has no counterpart. */
+helm_status helm_profile_classes(helm_ctx* ctx, unsigned mask);
+
 /* helm_profile_read - accumulated milliseconds and launch counts per kernel class since the last reset,
  * in the order: stencil (complex64 A), x-pass, y-pass, z-solve, Arnoldi dots, Arnoldi update,
  * small FP64 kernels (reductions, Givens, least squares), solution update, FP64 true residual, other,

@@ -76,6 +76,8 @@ enum ProfClass { PROF_STENCIL = 0, PROF_XPASS, PROF_YPASS, PROF_ZSOLVE, PROF_DOT
                  PROF_COMBINE, PROF_RESIDUAL, PROF_OTHER, PROF_LEARNED, PROF_NCLASS };
 struct Prof {
     int enabled = 0;
+    unsigned mask = ~0u;   // classes that are timed
+    int open = 0;          // the last prof_begin recorded an event
     int used = 0;
     static constexpr int CAP = 16384;
     cudaEvent_t ev[CAP];

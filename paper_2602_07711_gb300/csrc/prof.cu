@@ -4,18 +4,22 @@
 
 void prof_begin(helm_ctx* c, cudaStream_t s, int cls) {
     Prof* p = c->prof;
-    if (!p || !p->enabled) return;
+    if (!p) return;
+    p->open = 0;
+    if (!p->enabled || !((p->mask >> cls) & 1u)) return;
     if (p->used + 2 > Prof::CAP) prof_flush(c);
     p->cls[p->used / 2] = cls;
     cudaEventRecord(p->ev[p->used], s);
     p->used += 1;
+    p->open = 1;
 }
 
 void prof_end(helm_ctx* c, cudaStream_t s) {
     Prof* p = c->prof;
-    if (!p || !p->enabled) return;
+    if (!p || !p->enabled || !p->open) return;
     cudaEventRecord(p->ev[p->used], s);
     p->used += 1;
+    p->open = 0;
 }
 
 void prof_flush(helm_ctx* c) {
@@ -43,7 +47,14 @@ extern "C" helm_status helm_profile(helm_ctx* c, int enable) {
         }
     }
     c->prof->enabled = enable ? 1 : 0;
+    c->prof->mask = ~0u;
     return HELM_OK;
+}
+
+extern "C" helm_status helm_profile_classes(helm_ctx* c, unsigned mask) {
+    helm_status st = helm_profile(c, mask != 0u);
+    if (st == HELM_OK) c->prof->mask = mask;
+    return st;
 }
 
 extern "C" helm_status helm_profile_read(helm_ctx* c, double* ms, long long* launches, int n, int reset) {

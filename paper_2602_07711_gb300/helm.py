@@ -76,6 +76,7 @@ _SIGS = {
     "helm_residual_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_double),
                                         C.POINTER(C.c_double), C.c_void_p]),
     "helm_profile": (C.c_int, [C.c_void_p, C.c_int]),
+    "helm_profile_classes": (C.c_int, [C.c_void_p, C.c_uint]),
     "helm_profile_read": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int]),
     "helm_destroy": (None, [C.c_void_p]),
     "helm_net_create": (C.c_int, [C.c_int, C.c_ulonglong, C.POINTER(C.c_void_p)]),
