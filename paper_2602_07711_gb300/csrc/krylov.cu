@@ -31,6 +31,19 @@ struct Ctrl {
     int pad;
 };
 
+// Inner tolerance of a restart cycle.  The Krylov vectors and the stencil are complex64, so a cycle can
+// lower the true residual by about 1e-5 relative to the residual it started from (the stencil's rounding,
+// amplified by its cancellation at ~10 points per wavelength); the GMRES estimate keeps falling below that
+// while the true residual does not.  A cycle therefore stops once its estimate, relative to the cycle's
+// starting residual beta_k, reaches kInnerFloor, and the next cycle restarts from the double-float true
+// residual (iterative refinement with a low-precision inner solve).  In terms of est = |g_{j+1}| / beta_0:
+// stop when est <= max(rtol, kInnerFloor * beta_k / beta_0).
+constexpr double kInnerFloor = 1e-5;
+__host__ __device__ inline double inner_threshold(double rtol, double beta_k, double beta0) {
+    const double f = beta0 > 0 ? kInnerFloor * beta_k / beta0 : 0.0;
+    return rtol > f ? rtol : f;
+}
+
 struct KrylovWork {
     int m = 0, flexible = 0, NB = 0, nres = 0;
     int NBd = 0;             // CTAs of the inner-product kernel: one full wave of resident CTAs
@@ -726,12 +739,13 @@ helm_status gmres_run(helm_ctx* c, const double2* b_in, double2* x_in, helm_solv
             // enqueued beyond the end of the cycle leaves columns j+1.. of H and g[j+2] behind, which the
             // least-squares solve of the first kk columns does not read; the control block is restored.
             double est_prev = k->ctrl_h->beta / beta0;
+            const double thr = inner_threshold(c->opt.rtol, k->ctrl_h->beta, beta0);
             for (int j = 0; j < m; ++j) {
                 if (launched <= j) {
                     if ((st = enqueue(j)) != HELM_OK) return st;
                     launched = j + 1;
                 }
-                if (j + 1 < m && its + 2 <= c->opt.max_iter && est_prev * kLookaheadDrop > c->opt.rtol) {
+                if (j + 1 < m && its + 2 <= c->opt.max_iter && est_prev * kLookaheadDrop > thr) {
                     if ((st = enqueue(j + 1)) != HELM_OK) return st;
                     launched = j + 2;
                 }
@@ -742,7 +756,7 @@ helm_status gmres_run(helm_ctx* c, const double2* b_in, double2* x_in, helm_solv
                 est = cj.est;
                 est_prev = est;
                 if (cj.flags & HELM_DEV_NAN) break;
-                if (est <= c->opt.rtol || its >= c->opt.max_iter) break;
+                if (est <= thr || its >= c->opt.max_iter) break;
                 if (!(cj.hnext > 0)) { breakdown = true; break; }
             }
             *k->ctrl_h = k->slots_h[kk - 1];
@@ -993,7 +1007,8 @@ __global__ void lane_iter_end_kernel(const Ctrl* __restrict__ ctrl, LaneCtl* L, 
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     L->its += 1;
     L->kk = j + 1;
-    bool go = !(ctrl->flags & HELM_DEV_NAN) && ctrl->est > L->rtol && L->its < L->max_iter && j + 1 < L->m;
+    bool go = !(ctrl->flags & HELM_DEV_NAN) && ctrl->est > inner_threshold(L->rtol, ctrl->beta, ctrl->beta0) &&
+              L->its < L->max_iter && j + 1 < L->m;
     if (!(ctrl->hnext > 0)) { go = false; L->brk = 1; }
     if (has_next) cudaGraphSetConditional(hnext, go ? 1u : 0u);
 }
