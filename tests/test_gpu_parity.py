@@ -229,9 +229,9 @@ def test_scattering_sphere_matches_oracle(rtol):
     assert info.status == 0 and info.relres_true <= rtol
     assert np.linalg.norm(A(xg) - Fh) / np.linalg.norm(Fh) <= 1.5 * rtol   # the oracle's FP64 residual
     assert np.linalg.norm(xg - xo) / np.linalg.norm(xo) <= 10 * rtol
-    if rtol >= 1e-6:
-        # within complex64's reach the Krylov process is the oracle's
-        assert abs(info.iterations - io["iterations"]) <= 1
-    else:
-        # below it the FP32 basis needs restarts from the double-float true residual
-        assert io["iterations"] <= info.iterations <= 2 * io["iterations"] + 5
+    # the first restart cycle is the oracle's Krylov process until its estimate has fallen by the inner
+    # tolerance of a cycle (1e-4); the later cycles restart from the double-float true residual, and a
+    # restarted GMRES never needs fewer iterations than an unrestarted one
+    _, io4 = gmres(A, e.apply_Minv, Fh, m=20, rtol=1e-4, max_it=400, flexible=True)
+    assert abs(info.cycle_its[0] - io4["iterations"]) <= 1
+    assert io["iterations"] - 1 <= info.iterations <= io["iterations"] + 5
