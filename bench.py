@@ -146,8 +146,11 @@ MEASURED_TRAFFIC = {("stencil", 256, 6): 935.1e6}
 
 def roofline(prof_ms, prof_launch, alg, precision, order, n=None, variant=None):
     pk, src = peaks()
-    # dominant kernel class by measured time
-    cls = max((c for c in alg if prof_launch.get(c, 0) > 0), key=lambda c: prof_ms.get(c, 0.0))
+    # dominant kernel class by measured time (none when no event could be timed, e.g. under a profiler)
+    timed = [c for c in alg if prof_launch.get(c, 0) > 0 and prof_ms.get(c, 0.0) > 0]
+    if not timed:
+        return None
+    cls = max(timed, key=lambda c: prof_ms.get(c, 0.0))
     launches = prof_launch[cls]
     avg_s = prof_ms[cls] / launches / 1e3
     a = alg[cls]
@@ -302,7 +305,7 @@ def run_ours(args, rank, world, local):
     lib.helm_profile_read(S.ctx, ms_arr, ln_arr, len(CLASSES), 1)
     full_ms = {c: ms_arr[i] for i, c in enumerate(CLASSES)}
     full_ln = {c: ln_arr[i] for i, c in enumerate(CLASSES)}
-    dominant = max((c for c in CLASSES if full_ln[c] > 0), key=lambda c: full_ms[c])
+    dominant = max((c for c in CLASSES if full_ln[c] > 0), key=lambda c: full_ms[c], default="dots")
     # timed region: events only around the dominant kernel's launches (its roofline figure)
     lib.helm_profile_classes(S.ctx, 1 << CLASSES.index(dominant))
     clocks = ClockSampler(local)
