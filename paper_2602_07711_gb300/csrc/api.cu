@@ -122,6 +122,7 @@ helm_status helm_setup(const helm_grid* grid, const void* k2, double k0, const d
                         s) != cudaSuccess) { free_ctx(c); return HELM_ERR_CUDA; }
     TRY(launch_derived_fields(c, s));
     TRY(stencil_fast_prepare(c));
+    TRY(stencil_real_prepare(c, s));
     // eigen set-up
     TRY(dalloc(&c->Dx, c->nx)); TRY(dalloc(&c->Dy, c->ny));
     TRY(dalloc(&c->Vx, (size_t)c->nx * c->nx)); TRY(dalloc(&c->Vxi, (size_t)c->nx * c->nx));

@@ -125,6 +125,9 @@ struct helm_ctx {
     float *YFr = nullptr, *YIr = nullptr;   // y-pass A: re and im planes [2][N][N] (hi, lo follow)
     void* tmaps = nullptr;                  // host copies of TMA descriptors (gemm_tc.cu)
     void* pfft = nullptr;                   // PFFT tables and scratch (pfft.cu)
+    float* k2r = nullptr;                   // real k^2 and real (G, g_x, g_y, g_z) for media without attenuation
+    float4* fr = nullptr;
+    int realk = 0;
     void* sfast = nullptr;                  // TMA descriptors of the stencil's fixed operands (stencil_fast.cu)
     // scratch
     float2* tmp = nullptr;                  // one complex64 grid vector
@@ -153,6 +156,7 @@ helm_status launch_residual(helm_ctx* c, const float4* x, const float4* F, float
 helm_status launch_rhs(helm_ctx* c, const double2* f, double2* F, float4* fdf, cudaStream_t s);
 // stencil_fast.cu: the complex64 matvec of orders 4 and 6 (cp.async plane ring, plane-quantity form)
 helm_status stencil_fast_prepare(helm_ctx* c);
+helm_status stencil_real_prepare(helm_ctx* c, cudaStream_t s);
 void stencil_fast_release(helm_ctx* c);
 int stencil_variants(const helm_ctx* c);
 helm_status residual_fast_prepare();

@@ -42,11 +42,20 @@ constexpr int FNT = FTX * FTY;     // 256 threads
 constexpr int FNS = 4;             // ring slots
 constexpr int FZCH = 32;           // planes per CTA
 
-template <int ORDER>
+template <int ORDER, bool RK = false>
 struct FStage {
     float2 u[FHALO];
     float2 k[FHALO];
     float2 f[ORDER == 6 ? 4 : 1][ORDER == 6 ? FNT : 2];   // G, g_x, g_y, g_z at the tile's points
+};
+// real k^2 (no attenuation): k^2 staged as float, KU formed from it; the four order-6 fields are real and
+// interleaved (G, g_x, g_y, g_z) in one float4 per point
+template <int ORDER>
+struct FStage<ORDER, true> {
+    float2 u[FHALO];
+    float2 k[FHALO];   // KU
+    float kr[FHALO];
+    float4 f4[ORDER == 6 ? FNT : 1];
 };
 
 struct FParams {
@@ -57,11 +66,21 @@ struct FParams {
     float h2_20, h_20, hh6;       // order 6: h^2/20, h/20, h^2/6
     const float2* k2;
     const float2* fld[4];         // G, g_x, g_y, g_z (order 6)
+    const float* k2r;             // real k^2 (real-medium kernels)
+    const float4* fr;             // real (G, g_x, g_y, g_z) per point (real-medium kernels, order 6)
 };
 
 __device__ __forceinline__ void cp8(void* smem, const void* gmem) {
     const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp4(void* smem, const void* gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp16f(void* smem, const void* gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
 }
 __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
@@ -76,12 +95,13 @@ __device__ __forceinline__ float2 f2mul(float2 a, float2 b) {
     return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
 }
 
-template <int ORDER, int MINB>
+template <int ORDER, int MINB, bool RK = false>
 __global__ void __launch_bounds__(FNT, MINB)
 stencil_fast_kernel(FParams p, const float2* __restrict__ U, float2* __restrict__ Y, const double* __restrict__ sigma,
                     int sidx) {
     extern __shared__ __align__(16) unsigned char fsm[];
-    FStage<ORDER>* ring = reinterpret_cast<FStage<ORDER>*>(fsm);
+    using Stage = FStage<ORDER, RK>;
+    Stage* ring = reinterpret_cast<Stage*>(fsm);
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * FTX + tx;
     const int x0 = blockIdx.x * FTX, y0 = blockIdx.y * FTY;
     const int z0 = blockIdx.z * FZCH;
@@ -107,20 +127,24 @@ stencil_fast_kernel(FParams p, const float2* __restrict__ U, float2* __restrict_
 
     auto issue = [&](int P) {
         if (P <= z1) {
-            FStage<ORDER>& S = ring[(P + FNS) % FNS];
+            Stage& S = ring[(P + FNS) % FNS];
             const int Pc = min(max(P, 0), p.nz - 1);
             const float2* Ub = U + (size_t)Pc * plane;
-            const float2* Kb = p.k2 + (size_t)Pc * plane;
 #pragma unroll
             for (int k = 0; k < 2; ++k)
                 if (tid + k * FNT < FHALO) {
                     cp8(&S.u[tid + k * FNT], Ub + (sl[k] & 0x3FFFFFFFu));
-                    cp8(&S.k[tid + k * FNT], Kb + (sl[k] & 0x3FFFFFFFu));
+                    if constexpr (RK) cp4(&S.kr[tid + k * FNT], p.k2r + (size_t)Pc * plane + (sl[k] & 0x3FFFFFFFu));
+                    else cp8(&S.k[tid + k * FNT], p.k2 + (size_t)Pc * plane + (sl[k] & 0x3FFFFFFFu));
                 }
             if (ORDER == 6 && P >= z0 && P < z1 && active) {
                 const size_t g = (size_t)P * plane + poff;
+                if constexpr (RK) {
+                    cp16f(&S.f4[tid], p.fr + g);
+                } else {
 #pragma unroll
-                for (int f = 0; f < 4; ++f) cp8(&S.f[f][tid], p.fld[f] + g);
+                    for (int f = 0; f < 4; ++f) cp8(&S.f[f][tid], p.fld[f] + g);
+                }
             }
         }
         cp_commit();   // one group per plane, empty ones included, so that wait_group counts planes
@@ -133,7 +157,7 @@ stencil_fast_kernel(FParams p, const float2* __restrict__ U, float2* __restrict_
     issue(z0 - 1);
     issue(z0);
     for (int P = z0 - 1; P <= z1; ++P) {
-        FStage<ORDER>& S = ring[(P + FNS) % FNS];
+        Stage& S = ring[(P + FNS) % FNS];
         cp_wait1();          // plane P has landed (only plane P+1 may still be in flight)
         __syncthreads();     // ... for every thread; and every thread is done with plane P-1
         // prepare this thread's staged points: ghost factors, then KU = k^2 U once per point
@@ -149,7 +173,8 @@ stencil_fast_kernel(FParams p, const float2* __restrict__ U, float2* __restrict_
                     if (zghost) u = f2mul(u, p.gz);
                     S.u[q] = u;
                 }
-                S.k[q] = f2mul(S.k[q], u);
+                if constexpr (RK) S.k[q] = f2scl(u, S.kr[q]);
+                else S.k[q] = f2mul(S.k[q], u);
             }
         }
         __syncthreads();     // U and KU of plane P ready for every thread
@@ -187,11 +212,19 @@ stencil_fast_kernel(FParams p, const float2* __restrict__ U, float2* __restrict_
             const float2 Xs = f2scl(dx1, 1.f / 6.f), Ys = f2scl(dy1, 1.f / 6.f);
             const float2 Zs = f2add(f2fma(p.hh6, kc, c), f2scl(f2fma(-4.f, c, f2add(fx, fy)), 1.f / 6.f));
             if (out_prev) {
-                const FStage<ORDER>& Sp = ring[(P - 1 + FNS) % FNS];
+                const Stage& Sp = ring[(P - 1 + FNS) % FNS];
                 const float2 A = f2add(cA, As);
-                float2 g = f2mul(Sp.f[1][tid], f2add(cX, Xs));
-                g = f2add(g, f2mul(Sp.f[2][tid], f2add(cY, Ys)));
-                g = f2add(g, f2mul(Sp.f[3][tid], f2add(cZ, Zs)));
+                float2 g;
+                if constexpr (RK) {
+                    const float4 fv = Sp.f4[tid];
+                    g = f2scl(f2add(cX, Xs), fv.y);
+                    g = f2fma(fv.z, f2add(cY, Ys), g);
+                    g = f2fma(fv.w, f2add(cZ, Zs), g);
+                } else {
+                    g = f2mul(Sp.f[1][tid], f2add(cX, Xs));
+                    g = f2add(g, f2mul(Sp.f[2][tid], f2add(cY, Ys)));
+                    g = f2add(g, f2mul(Sp.f[3][tid], f2add(cZ, Zs)));
+                }
                 const float2 v = f2fma(p.h_20, g, A);
                 if (active) Y[(size_t)(P - 1) * plane + poff] = f2scl(v, sg);
             }
@@ -201,7 +234,8 @@ stencil_fast_kernel(FParams p, const float2* __restrict__ U, float2* __restrict_
                 float2 Am = f2scl(f2fma(-64.f / 15.f, c, f2fma(0.1f, e, f2scl(f2add(fx, fy), 7.f / 15.f))), ih);
                 Am = f2fma(14.f / 15.f, kc, Am);
                 Am = f2fma(1.f / 90.f, f2sub(kcs, kf4), Am);
-                Am = f2fma(p.h2_20, f2mul(S.f[0][tid], c), Am);
+                if constexpr (RK) Am = f2fma(p.h2_20 * S.f4[tid].x, c, Am);
+                else Am = f2fma(p.h2_20, f2mul(S.f[0][tid], c), Am);
                 const float2 tdx = f2sub(f2add(u[0][2], u[2][2]), f2add(u[0][0], u[2][0]));
                 const float2 tdy = f2sub(f2add(u[2][0], u[2][2]), f2add(u[0][0], u[0][2]));
                 const float2 Xm = f2add(f2fma(p.hh6, dkx, dx1), f2scl(f2fma(-4.f, dx1, tdx), 1.f / 6.f));
@@ -232,8 +266,8 @@ stencil_fast_kernel(FParams p, const float2* __restrict__ U, float2* __restrict_
     }
 }
 
-template <int ORDER>
-size_t fast_smem() { return FNS * sizeof(FStage<ORDER>); }
+template <int ORDER, bool RK = false>
+size_t fast_smem() { return FNS * sizeof(FStage<ORDER, RK>); }
 
 // ---- TMA kernel --------------------------------------------------------------------------------
 constexpr int TPX = 36;                          // tile row of the TMA halo: x0-2 .. x0+33
@@ -473,6 +507,14 @@ helm_status stencil_fast_prepare(helm_ctx* c) {
                                        (int)fast_smem<4>()));
     HELM_CUDA_TRY(cudaFuncSetAttribute(stencil_fast_kernel<6, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)fast_smem<6>()));
+    HELM_CUDA_TRY(cudaFuncSetAttribute(stencil_fast_kernel<4, 4, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)fast_smem<4, true>()));
+    HELM_CUDA_TRY(cudaFuncSetAttribute(stencil_fast_kernel<6, 4, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)fast_smem<6, true>()));
+    HELM_CUDA_TRY(cudaFuncSetAttribute(stencil_fast_kernel<4, 3, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)fast_smem<4, true>()));
+    HELM_CUDA_TRY(cudaFuncSetAttribute(stencil_fast_kernel<6, 3, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)fast_smem<6, true>()));
     HELM_CUDA_TRY(cudaFuncSetAttribute(stencil_tma_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        TLayout<4>::SMEM));
     HELM_CUDA_TRY(cudaFuncSetAttribute(stencil_tma_kernel<6>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -504,6 +546,60 @@ helm_status stencil_fast_prepare(helm_ctx* c) {
 void stencil_fast_release(helm_ctx* c) {
     delete (FastMaps*)c->sfast;
     c->sfast = nullptr;
+    cudaFree(c->k2r);
+    cudaFree(c->fr);
+    c->k2r = nullptr;
+    c->fr = nullptr;
+    c->realk = 0;
+}
+
+namespace {
+__global__ void imag_any_kernel(const double2* __restrict__ k2, size_t n, unsigned* flag) {
+    unsigned any = 0;
+    for (size_t id = blockIdx.x * (size_t)blockDim.x + threadIdx.x; id < n; id += (size_t)gridDim.x * blockDim.x)
+        any |= k2[id].y != 0.0;
+    if (__any_sync(0xffffffffu, any) && (threadIdx.x & 31) == 0) atomicOr(flag, 1u);
+}
+__global__ void real_fields_kernel(size_t n, int order, const float2* __restrict__ k2f, const float2* __restrict__ G,
+                                   const float2* __restrict__ gx, const float2* __restrict__ gy,
+                                   const float2* __restrict__ gz, float* __restrict__ kr, float4* __restrict__ fr) {
+    for (size_t id = blockIdx.x * (size_t)blockDim.x + threadIdx.x; id < n; id += (size_t)gridDim.x * blockDim.x) {
+        kr[id] = k2f[id].x;
+        if (order == 6) fr[id] = make_float4(G[id].x, gx[id].x, gy[id].x, gz[id].x);
+    }
+}
+}  // namespace
+
+// Set-up of the real-medium matvec: when Im k^2 vanishes everywhere (a medium without attenuation), the
+// complex64 matvec stages k^2 as float and reads the four order-6 fields as one real float4 per point
+// (36 instead of 56 bytes per point, real instead of complex products).  Synchronises s.
+helm_status stencil_real_prepare(helm_ctx* c, cudaStream_t s) {
+    if (!stencil_fast_supported(c)) return HELM_OK;
+    unsigned* flag = nullptr;
+    unsigned h = 1;
+    HELM_CUDA_TRY(cudaMalloc(&flag, sizeof(unsigned)));
+    cudaError_t e = cudaMemsetAsync(flag, 0, sizeof(unsigned), s);
+    if (e == cudaSuccess) {
+        imag_any_kernel<<<1024, 256, 0, s>>>(c->k2_d, c->npts, flag);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, flag, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(flag);
+    HELM_CUDA_TRY(e);
+    if (h) return HELM_OK;   // complex k^2: the general kernels
+    if (cudaMalloc(&c->k2r, c->npts * sizeof(float)) != cudaSuccess ||
+        (c->opt.order == 6 && cudaMalloc(&c->fr, c->npts * sizeof(float4)) != cudaSuccess)) {
+        cudaGetLastError();
+        cudaFree(c->k2r);
+        c->k2r = nullptr;
+        return HELM_ERR_NOMEM;
+    }
+    real_fields_kernel<<<1024, 256, 0, s>>>(c->npts, c->opt.order, c->k2_f, c->G_f, c->dk2_f[0], c->dk2_f[1],
+                                            c->dk2_f[2], c->k2r, c->fr);
+    HELM_CUDA_TRY(cudaGetLastError());
+    c->realk = 1;
+    return HELM_OK;
 }
 
 bool stencil_fast_supported(const helm_ctx* c) { return c->opt.order == 4 || c->opt.order == 6; }
@@ -546,6 +642,19 @@ helm_status launch_stencil_fast(helm_ctx* c, const float2* x, float2* y, const d
         }
     }
     const bool three = c->tune_stencil == 2;   // the variant with up to 85 registers, three CTAs per SM
+    if (c->realk) {
+        p.k2r = c->k2r;
+        p.fr = c->fr;
+        if (c->opt.order == 6) {
+            if (three) stencil_fast_kernel<6, 3, true><<<grid, block, fast_smem<6, true>(), s>>>(p, x, y, sigma, sidx);
+            else stencil_fast_kernel<6, 4, true><<<grid, block, fast_smem<6, true>(), s>>>(p, x, y, sigma, sidx);
+        } else {
+            if (three) stencil_fast_kernel<4, 3, true><<<grid, block, fast_smem<4, true>(), s>>>(p, x, y, sigma, sidx);
+            else stencil_fast_kernel<4, 4, true><<<grid, block, fast_smem<4, true>(), s>>>(p, x, y, sigma, sidx);
+        }
+        HELM_CUDA_TRY(cudaGetLastError());
+        return HELM_OK;
+    }
     if (c->opt.order == 6) {
         if (three) stencil_fast_kernel<6, 3><<<grid, block, fast_smem<6>(), s>>>(p, x, y, sigma, sidx);
         else stencil_fast_kernel<6, 4><<<grid, block, fast_smem<6>(), s>>>(p, x, y, sigma, sidx);

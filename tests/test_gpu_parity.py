@@ -235,3 +235,17 @@ def test_scattering_sphere_matches_oracle(rtol):
     _, io4 = gmres(A, e.apply_Minv, Fh, m=20, rtol=1e-4, max_it=400, flexible=True)
     assert abs(info.cycle_its[0] - io4["iterations"]) <= 1
     assert io["iterations"] - 1 <= info.iterations <= io["iterations"] + 5
+
+
+@pytest.mark.parametrize("order,case", [(4, SIZES[4][0]), (4, SIZES[4][2]), (6, SIZES[6][0]), (6, SIZES[6][2])])
+def test_apply_A_real_medium_matches_oracle(order, case):
+    """A medium without attenuation (Im k^2 = 0) takes the real-medium complex64 matvec (k^2 staged as
+    float, the order-6 fields as one real float4 per point); same oracle and tolerance as the general one."""
+    n, L = case
+    g, k2, k0 = _medium(n, L)
+    k2 = k2.real + 0j
+    S = Solver(n, k2, k0, order=order, L=L)
+    x = _rand(g.shape, 1)
+    ref = Operator(g, k2, k0, order)(x)
+    y64 = S.apply_A(_dev(x, torch.complex64)).cpu().numpy()
+    assert _rel(y64, ref) < 2e-6
