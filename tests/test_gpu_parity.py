@@ -249,3 +249,28 @@ def test_apply_A_real_medium_matches_oracle(order, case):
     ref = Operator(g, k2, k0, order)(x)
     y64 = S.apply_A(_dev(x, torch.complex64)).cpu().numpy()
     assert _rel(y64, ref) < 2e-6
+
+
+def test_profile_classes_times_only_the_selected_class():
+    """helm_profile_classes records events only around the launches of the selected kernel classes (the
+    bench times the dominant kernel this way inside its timed region); helm_profile times every class."""
+    from paper_2602_07711_gb300 import helm
+    n = 32
+    k2, f, k0 = media.single_gaussian(n)
+    S = Solver((n, n, n), k2, k0, order=4, rtol=1e-6)
+    F = S.build_rhs(_dev(f))
+    L = helm.lib()
+    ms = (helm.C.c_double * 11)()
+    ln = (helm.C.c_longlong * 11)()
+    dots, stencil = 4, 0
+    assert L.helm_profile_classes(S.ctx, 1 << dots) == 0
+    _, info = S.solve(F)
+    assert L.helm_profile_read(S.ctx, ms, ln, 11, 1) == 0
+    # (an iteration enqueued ahead past the end of a cycle runs too)
+    assert ln[dots] >= info.iterations and ms[dots] > 0
+    assert all(ln[i] == 0 for i in range(11) if i != dots)
+    assert L.helm_profile(S.ctx, 1) == 0
+    _, info = S.solve(F)
+    assert L.helm_profile_read(S.ctx, ms, ln, 11, 1) == 0
+    assert ln[dots] >= info.iterations and ln[stencil] >= info.iterations
+    assert L.helm_profile(S.ctx, 0) == 0
