@@ -172,9 +172,12 @@ void helm_batch_destroy(helm_batch* batch);
 /* helm_autotune - time, on this context's grid, the candidate CTA counts of the Arnoldi update and combine
  * kernels, the variants of the complex64 matvec (0: cp.async plane ring at four CTAs per SM, 1: TMA plane
  * ring, 2: cp.async ring at three CTAs per SM) and of the inner-product kernel (0: groups of eight, 1/2:
- * software-pipelined groups of four/eight), and keep the fastest of each for the context's later solves;
- * *nb_out, *variant_out and *dots_out (any may be NULL) receive the choices.  Results are cached per grid
- * size and order for the process.  Uses temporary device memory; synchronous. */
+ * software-pipelined groups of four/eight); in TF32 contexts the tensor-core transform passes (persistent
+ * with double-buffered accumulators, or one tile per CTA), timed on a preconditioner application; in EigT
+ * contexts with even N_x the factorised z-solve (the L2-resident kernel at 1-3 CTAs per SM, or one thread
+ * per line).  The fastest of each is kept for the context's later solves; *nb_out, *variant_out and
+ * *dots_out (any may be NULL) receive the first three choices.  Results are cached per grid size and order
+ * for the process.  Uses temporary device memory; synchronous. */
 helm_status helm_autotune(helm_ctx* ctx, int* nb_out, int* variant_out, int* dots_out, void* stream);
 
 /* helm_residual - r = b - A x and its norms, the rel-res numerator of Sec. 5.1, computed with about 44

@@ -876,7 +876,7 @@ struct TuneKey {
     }
 };
 struct TuneVal {
-    int nb, stencil, dots;
+    int nb, stencil, dots, tc, ypers, zring;
 };
 
 std::mutex g_tune_mu;
@@ -893,6 +893,9 @@ extern "C" helm_status helm_autotune(helm_ctx* c, int* nb_out, int* variant_out,
             c->tune_nb = it->second.nb;
             c->tune_stencil = std::min(it->second.stencil, stencil_variants(c) - 1);
             c->tune_dots = it->second.dots;
+            c->tune_tc = it->second.tc;
+            c->tune_ypers = it->second.ypers;
+            c->tune_zring = it->second.zring;
             if (nb_out) *nb_out = c->tune_nb;
             if (variant_out) *variant_out = c->tune_stencil;
             if (dots_out) *dots_out = c->tune_dots;
@@ -976,6 +979,45 @@ extern "C" helm_status helm_autotune(helm_ctx* c, int* nb_out, int* variant_out,
         if (tmin < best_d_ms * 0.97f) { best_d_ms = tmin; best_d = v; }
     }
     c->tune_dots = best_d;
+    auto time_it = [&](auto&& launch) {
+        float tmin = 1e30f;
+        for (int rep = 0; rep < 4; ++rep) {
+            cudaEventRecord(e0, s);
+            launch();
+            cudaEventRecord(e1, s);
+            cudaEventSynchronize(e1);
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (rep > 0) tmin = std::min(tmin, ms);
+        }
+        return tmin;
+    };
+    // the tensor-core transform variants (persistent or one tile per CTA), timed on a whole preconditioner
+    // application
+    if (c->opt.precision == HELM_PREC_TF32 && c->tmaps && c->opt.precond != HELM_PRECOND_NONE) {
+        int btc = c->tune_tc, byp = c->tune_ypers;
+        float bms = 1e30f;
+        for (int tc = 1; tc >= 0; --tc)
+            for (int yp = 1; yp >= 0; --yp) {
+                c->tune_tc = tc;
+                c->tune_ypers = yp;
+                const float ms = time_it([&] { precond_apply(c, V, V + npts, nullptr, 0, s); });
+                if (ms < bms * 0.97f) { bms = ms; btc = tc; byp = yp; }
+            }
+        c->tune_tc = btc;
+        c->tune_ypers = byp;
+    }
+    // the factorised z-solve: CTAs per SM of the L2-resident kernel (0 = one thread per line)
+    if (c->zfac && c->opt.precond == HELM_PRECOND_EIGT && c->nx % 2 == 0) {
+        int bz = c->tune_zring;
+        float bms = 1e30f;
+        for (int zr = 0; zr <= 3; ++zr) {
+            c->tune_zring = zr;
+            const float ms = time_it([&] { launch_zsolve(c, V, V + npts, s); });
+            if (ms < bms * 0.97f) { bms = ms; bz = zr; }
+        }
+        c->tune_zring = bz;
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     cudaFree(V); cudaFree(part); cudaFree(coef);
@@ -983,7 +1025,8 @@ extern "C" helm_status helm_autotune(helm_ctx* c, int* nb_out, int* variant_out,
     c->tune_nb = best;
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
-        g_tune_cache[TuneKey{c->nx, c->ny, c->nz, c->opt.order}] = TuneVal{best, best_st, best_d};
+        g_tune_cache[TuneKey{c->nx, c->ny, c->nz, c->opt.order}] =
+            TuneVal{best, best_st, best_d, c->tune_tc, c->tune_ypers, c->tune_zring};
     }
     if (nb_out) *nb_out = best;
     if (variant_out) *variant_out = best_st;
