@@ -134,8 +134,11 @@ helm_status helm_get_eig(helm_ctx* ctx, int axis, void* D, void* V, void* Vinv);
  *   b     complex128 right-hand side F (from helm_build_rhs), host or device.
  *   x     complex128, host or device; on entry x^0, on exit the iterate (also on NOT_CONVERGED).
  *   info  filled on return (may be NULL).
- * Krylov vectors are complex64; inner products accumulate in FP64; the Hessenberg matrix and Givens
- * rotations are FP64 on the GPU; x accumulates in complex128; the stopping test uses the FP64 true
+ * Krylov vectors are complex64; inner products accumulate in compensated FP32 per thread and FP64 across
+ * threads; the Hessenberg matrix and Givens rotations are FP64 on the GPU; x accumulates in double-float
+ * (~44 bits); the stopping test uses the true residual in double-float.  A restart cycle ends after m
+ * steps, at rtol, or once its residual estimate has fallen 1e-4 below the cycle's starting true residual
+ * (a complex64 cycle cannot lower the true residual much further); the next cycle restarts from the true
  * residual.  Synchronises `stream`. */
 helm_status helm_gmres_solve(helm_ctx* ctx, const void* b, void* x, helm_solve_info* info, void* stream);
 
