@@ -216,22 +216,68 @@ __global__ void frame_rows_kernel(const float2* __restrict__ C, int nx, int ny, 
 
 // out[b][r] = alpha * sum_k M(r, k) in[b][k]; M(r, k) = Mat[r][k] (trans = 0) or Mat[k][r] (trans = 1).
 // optional add: out += add (same layout).  Vectors of length n, stride ld; one CTA per vector.
+// Batched dense matrix times vector: out_b = alpha Mat v_b (+ add_b) for the nvec vectors v_b = in[b ld ..],
+// NV vectors per block (every row of Mat read from L2 serves NV of them).  trans = 0 reads Mat row by row
+// (one warp per row, lanes along the row, warp-shuffle sums); trans = 1 multiplies by Mat^T (one thread per
+// output, lanes along the row index), so both forms read Mat coalesced.
+template <int NV>
 __global__ void matvec_kernel(const float2* __restrict__ Mat, int n, int trans, const float2* __restrict__ in,
-                              float2* __restrict__ out, int ld, float2 alpha, const float2* __restrict__ add) {
-    extern __shared__ float2 v[];
-    const int b = blockIdx.x;
-    for (int k = threadIdx.x; k < n; k += blockDim.x) v[k] = in[(size_t)b * ld + k];
+                              float2* __restrict__ out, int ld, float2 alpha, const float2* __restrict__ add, int nvec) {
+    extern __shared__ float2 v[];   // [NV][n]
+    const int b0 = blockIdx.x * NV;
+    const int nb = min(NV, nvec - b0);
+    for (int q = 0; q < NV; ++q)
+        for (int k = threadIdx.x; k < n; k += blockDim.x)
+            v[q * n + k] = q < nb ? in[(size_t)(b0 + q) * ld + k] : make_float2(0.f, 0.f);
     __syncthreads();
-    for (int r = threadIdx.x; r < n; r += blockDim.x) {
-        float2 acc = make_float2(0.f, 0.f);
-        if (trans)
-            for (int k = 0; k < n; ++k) acc = cfma(Mat[(size_t)k * n + r], v[k], acc);
-        else
-            for (int k = 0; k < n; ++k) acc = cfma(Mat[(size_t)r * n + k], v[k], acc);
-        acc = cmul(alpha, acc);
-        if (add) acc = cadd(acc, add[(size_t)b * ld + r]);
-        out[(size_t)b * ld + r] = acc;
+    if (trans) {
+        for (int r = threadIdx.x; r < n; r += blockDim.x) {
+            float2 acc[NV];
+#pragma unroll
+            for (int q = 0; q < NV; ++q) acc[q] = make_float2(0.f, 0.f);
+            for (int k = 0; k < n; ++k) {
+                const float2 m = Mat[(size_t)k * n + r];
+#pragma unroll
+                for (int q = 0; q < NV; ++q) acc[q] = cfma(m, v[q * n + k], acc[q]);
+            }
+            for (int q = 0; q < nb; ++q) {
+                float2 o = cmul(alpha, acc[q]);
+                if (add) o = cadd(o, add[(size_t)(b0 + q) * ld + r]);
+                out[(size_t)(b0 + q) * ld + r] = o;
+            }
+        }
+    } else {
+        const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+        for (int r = threadIdx.x >> 5; r < n; r += nw) {
+            float2 acc[NV];
+#pragma unroll
+            for (int q = 0; q < NV; ++q) acc[q] = make_float2(0.f, 0.f);
+            for (int k = lane; k < n; k += 32) {
+                const float2 m = Mat[(size_t)r * n + k];
+#pragma unroll
+                for (int q = 0; q < NV; ++q) acc[q] = cfma(m, v[q * n + k], acc[q]);
+            }
+#pragma unroll
+            for (int q = 0; q < NV; ++q)
+                for (int o = 16; o > 0; o >>= 1) {
+                    acc[q].x += __shfl_down_sync(0xffffffffu, acc[q].x, o);
+                    acc[q].y += __shfl_down_sync(0xffffffffu, acc[q].y, o);
+                }
+            if (lane == 0)
+                for (int q = 0; q < nb; ++q) {
+                    float2 o = cmul(alpha, acc[q]);
+                    if (add) o = cadd(o, add[(size_t)(b0 + q) * ld + r]);
+                    out[(size_t)(b0 + q) * ld + r] = o;
+                }
+        }
     }
+}
+
+constexpr int MV_NV = 1;   // one vector per block: nz blocks fill the GPU
+void launch_matvec(int nvec, cudaStream_t s, const float2* Mat, int n, int trans, const float2* in, float2* out, int ld,
+                   float2 alpha, const float2* add) {
+    matvec_kernel<MV_NV><<<(nvec + MV_NV - 1) / MV_NV, 256, MV_NV * n * sizeof(float2), s>>>(Mat, n, trans, in, out, ld,
+                                                                                         alpha, add, nvec);
 }
 
 // out[t][l][m] = vec[m] for every slice l (t fixed): fills the slice-independent outer-product factors
@@ -431,10 +477,10 @@ helm_status frame_of(helm_ctx* c, PfftState* P, const float2* C, const float2* M
     frame_rows_kernel<<<dim3((ny + 7) / 8, nz), 256, 0, s>>>(C, nx, ny, Mx, Mx + (size_t)(nx - 1) * nx, UL, UR, nm);
     const float2 one = make_float2(1.f, 0.f);
     // rows: Theta[0][i] = sum_i' Mx[i][i'] TT[i'];  columns: Theta[j][0] = sum_j' My[j][j'] UL[j']
-    matvec_kernel<<<nz, 256, nx * sizeof(float2), s>>>(Mx, nx, 0, TT, fr, nm, one, nullptr);
-    matvec_kernel<<<nz, 256, nx * sizeof(float2), s>>>(Mx, nx, 0, TB, fr + blk, nm, one, nullptr);
-    matvec_kernel<<<nz, 256, ny * sizeof(float2), s>>>(My, ny, 0, UL, fr + 2 * blk, nm, one, nullptr);
-    matvec_kernel<<<nz, 256, ny * sizeof(float2), s>>>(My, ny, 0, UR, fr + 3 * blk, nm, one, nullptr);
+    launch_matvec(nz, s, Mx, nx, 0, TT, fr, nm, one, nullptr);
+    launch_matvec(nz, s, Mx, nx, 0, TB, fr + blk, nm, one, nullptr);
+    launch_matvec(nz, s, My, ny, 0, UL, fr + 2 * blk, nm, one, nullptr);
+    launch_matvec(nz, s, My, ny, 0, UR, fr + 3 * blk, nm, one, nullptr);
     HELM_CUDA_TRY(cudaGetLastError());
     return HELM_OK;
 }
@@ -467,10 +513,10 @@ helm_status pfft_apply(helm_ctx* c, const float2* r, float2* z, const double* si
     fill_kernel<<<(unsigned)((nz * (size_t)nx + 255) / 256), 256, 0, s>>>(P->Q + 2 * (size_t)nz * nx, nz, nx, P->Vxi, nx, 0);
     fill_kernel<<<(unsigned)((nz * (size_t)nx + 255) / 256), 256, 0, s>>>(P->Q + 3 * (size_t)nz * nx, nz, nx, P->Vxi, nx, nx - 1);
     // matvec outputs are written with stride n of the factor arrays
-    matvec_kernel<<<nz, 256, ny * sizeof(float2), s>>>(P->Vyi, ny, 0, P->fc + 2 * blk, P->fa, nm, one, nullptr);
-    matvec_kernel<<<nz, 256, ny * sizeof(float2), s>>>(P->Vyi, ny, 0, P->fc + 3 * blk, P->fa + blk, nm, one, nullptr);
-    matvec_kernel<<<nz, 256, nx * sizeof(float2), s>>>(P->Vxi, nx, 0, P->fc, P->fa + 2 * blk, nm, one, nullptr);
-    matvec_kernel<<<nz, 256, nx * sizeof(float2), s>>>(P->Vxi, nx, 0, P->fc + blk, P->fa + 3 * blk, nm, one, nullptr);
+    launch_matvec(nz, s, P->Vyi, ny, 0, P->fc + 2 * blk, P->fa, nm, one, nullptr);
+    launch_matvec(nz, s, P->Vyi, ny, 0, P->fc + 3 * blk, P->fa + blk, nm, one, nullptr);
+    launch_matvec(nz, s, P->Vxi, nx, 0, P->fc, P->fa + 2 * blk, nm, one, nullptr);
+    launch_matvec(nz, s, P->Vxi, nx, 0, P->fc + blk, P->fa + 3 * blk, nm, one, nullptr);
     HELM_CUDA_TRY(cudaGetLastError());
     // repack to the factor layouts P[t][l][j], Q[t][l][i]
     HELM_CUDA_TRY(cudaMemcpy2DAsync(P->P + 2 * (size_t)nz * ny, ny * sizeof(float2), P->fa, nm * sizeof(float2),
@@ -497,10 +543,10 @@ helm_status pfft_apply(helm_ctx* c, const float2* r, float2* z, const double* si
     fill_kernel<<<(unsigned)((nz * (size_t)nx + 255) / 256), 256, 0, s>>>(P->Q + 2 * (size_t)nz * nx, nz, nx, P->Sx, 1, 0);
     fill_kernel<<<(unsigned)((nz * (size_t)nx + 255) / 256), 256, 0, s>>>(P->Q + 3 * (size_t)nz * nx, nz, nx,
                                                                         P->Sx + (size_t)(nx - 1) * nx, 1, 0);
-    matvec_kernel<<<nz, 256, ny * sizeof(float2), s>>>(P->Sy, ny, 1, P->fc + 2 * blk, P->fa, nm, one, nullptr);
-    matvec_kernel<<<nz, 256, ny * sizeof(float2), s>>>(P->Sy, ny, 1, P->fc + 3 * blk, P->fa + blk, nm, one, nullptr);
-    matvec_kernel<<<nz, 256, nx * sizeof(float2), s>>>(P->Sx, nx, 1, P->fc, P->fa + 2 * blk, nm, one, nullptr);
-    matvec_kernel<<<nz, 256, nx * sizeof(float2), s>>>(P->Sx, nx, 1, P->fc + blk, P->fa + 3 * blk, nm, one, nullptr);
+    launch_matvec(nz, s, P->Sy, ny, 1, P->fc + 2 * blk, P->fa, nm, one, nullptr);
+    launch_matvec(nz, s, P->Sy, ny, 1, P->fc + 3 * blk, P->fa + blk, nm, one, nullptr);
+    launch_matvec(nz, s, P->Sx, nx, 1, P->fc, P->fa + 2 * blk, nm, one, nullptr);
+    launch_matvec(nz, s, P->Sx, nx, 1, P->fc + blk, P->fa + 3 * blk, nm, one, nullptr);
     HELM_CUDA_TRY(cudaGetLastError());
     HELM_CUDA_TRY(cudaMemcpy2DAsync(P->P + 2 * (size_t)nz * ny, ny * sizeof(float2), P->fa, nm * sizeof(float2),
                                     ny * sizeof(float2), nz, cudaMemcpyDeviceToDevice, s));
