@@ -12,8 +12,8 @@
 // neighbours' end values.  One thread per line solves that small block-tridiagonal interface system
 // (2 unknowns per chunk) from shared memory, and every thread then finishes its chunk by a Thomas sweep
 // with known boundary values.  HBM traffic is one read and one write per point (16 B/pt).
-// This partitioned kernel serves the PFFT z-solves (generated right-hand sides, other diagonals); the
-// EigT systems use the factorised form below.
+// This partitioned kernel solves the systems when no set-up factors exist; every EigT and PFFT context
+// factorises its systems at set-up, so the factorised forms below serve the solver.
 #include "common.cuh"
 
 namespace {
