@@ -54,8 +54,11 @@ typedef struct {
 } helm_grid;
 
 /* Preconditioner M^-1 = h_z^2 A_p^-1 (Sec. 4): none, EigT (Sec. 4.1) or PFFT (Sec. 4.2; needs N_x and N_y
- * powers of two <= 512; its sine solver uses the Dirichlet condition at the staggered face). */
-enum { HELM_PRECOND_NONE = 0, HELM_PRECOND_EIGT = 1, HELM_PRECOND_PFFT = 2 };
+ * powers of two <= 512; its sine solver uses the Dirichlet condition at the staggered face).  FFT2 is the
+ * Dirichlet solve alone, M^-1 = h_z^2 (A_p^F)^-1 (Eq. TFprec; step 1 of PFFT without the boundary
+ * correction): the FFT-based second-order preconditioner the paper compares against (Sec. 5), same size
+ * limits as PFFT. */
+enum { HELM_PRECOND_NONE = 0, HELM_PRECOND_EIGT = 1, HELM_PRECOND_PFFT = 2, HELM_PRECOND_FFT2 = 3 };
 
 /* Arithmetic of the eigenvector transforms (EigT steps 2 and 4).  The stencil, the z-solves and the
  * Krylov vectors are complex64 in every mode; the Hessenberg/Givens update and the 1D eigensetup are FP64,

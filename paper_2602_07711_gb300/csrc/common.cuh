@@ -190,6 +190,8 @@ helm_status launch_zsolve_gen(helm_ctx* c, const float2* in, float2* out, const 
 // pfft.cu
 helm_status pfft_prepare(helm_ctx* c, cudaStream_t s);
 helm_status pfft_apply(helm_ctx* c, const float2* r, float2* z, const double* sigma, int sidx, cudaStream_t s);
+helm_status pfft_apply_dirichlet(helm_ctx* c, const float2* r, float2* z, const double* sigma, int sidx,
+                                 cudaStream_t s);
 void pfft_release(helm_ctx* c);
 // learned.cu: the two halves of the learned correction around M^-1 (features and a copy of
 // v = sigma[sidx] r before, the correction of z after; r and z may alias)

@@ -1364,7 +1364,8 @@ helm_status check_batch_args(helm_ctx* const* ctxs, int nprob, const void* const
     for (int p = 0; p < nprob; ++p) {
         helm_ctx* c = ctxs[p];
         if (!c || !b[p] || !x[p]) return HELM_ERR_ARG;
-        if (c->opt.precond == HELM_PRECOND_PFFT || c->net) return HELM_ERR_UNSUPPORTED;
+        if (c->opt.precond == HELM_PRECOND_PFFT || c->opt.precond == HELM_PRECOND_FFT2 || c->net)
+            return HELM_ERR_UNSUPPORTED;
         if (!is_device_ptr(b[p]) || !is_device_ptr(x[p])) return HELM_ERR_ARG;
         for (int q = 0; q < p; ++q)
             if (ctxs[q] == c) return HELM_ERR_ARG;   // each context once (its right-hand sides are its lanes)

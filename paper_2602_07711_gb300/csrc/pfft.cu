@@ -487,6 +487,19 @@ helm_status frame_of(helm_ctx* c, PfftState* P, const float2* C, const float2* M
 
 }  // namespace
 
+// FFT2: the Dirichlet solve alone, z = h_z^2 (A_p^F)^-1 r (step 1 of PFFT: sine transforms of every slice,
+// the factorised z-solves with the Dirichlet lateral eigenvalues, inverse sine transforms)
+helm_status pfft_apply_dirichlet(helm_ctx* c, const float2* r, float2* z, const double* sigma, int sidx,
+                                 cudaStream_t s) {
+    PfftState* P = (PfftState*)c->pfft;
+    if (!P) return HELM_ERR_UNSUPPORTED;
+    helm_status st;
+    if ((st = dst2d(c, P, 0, r, P->Yh, 1.f, sigma, sidx, s)) != HELM_OK) return st;
+    if ((st = launch_zsolve_fact(c, P->zfacF, P->Yh, P->Yh, nullptr, nullptr, s)) != HELM_OK) return st;
+    const float hz2 = (float)(c->h[2] * c->h[2]);
+    return dst2d(c, P, 1, P->Yh, z, hz2, nullptr, 0, s);
+}
+
 helm_status pfft_apply(helm_ctx* c, const float2* r, float2* z, const double* sigma, int sidx, cudaStream_t s) {
     PfftState* P = (PfftState*)c->pfft;
     if (!P) return HELM_ERR_UNSUPPORTED;

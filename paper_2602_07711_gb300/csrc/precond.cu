@@ -74,9 +74,10 @@ static helm_status precond_base(helm_ctx* c, const float2* r, float2* z, const d
         HELM_CUDA_TRY(cudaGetLastError());
         return HELM_OK;
     }
-    if (c->opt.precond == HELM_PRECOND_PFFT) {
+    if (c->opt.precond == HELM_PRECOND_PFFT || c->opt.precond == HELM_PRECOND_FFT2) {
         prof_begin(c, s, PROF_OTHER);
-        st = pfft_apply(c, r, z, sigma, sidx, s);
+        st = c->opt.precond == HELM_PRECOND_PFFT ? pfft_apply(c, r, z, sigma, sidx, s)
+                                                 : pfft_apply_dirichlet(c, r, z, sigma, sidx, s);
         prof_end(c, s);
         return st;
     }

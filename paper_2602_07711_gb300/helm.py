@@ -13,7 +13,7 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 library_path = os.path.join(HERE, "libhelm.so")
 
-HELM_PRECOND_NONE, HELM_PRECOND_EIGT, HELM_PRECOND_PFFT = 0, 1, 2
+HELM_PRECOND_NONE, HELM_PRECOND_EIGT, HELM_PRECOND_PFFT, HELM_PRECOND_FFT2 = 0, 1, 2, 3
 HELM_PREC_FP32, HELM_PREC_TF32 = 0, 1
 HELM_C64, HELM_C128 = 0, 1
 

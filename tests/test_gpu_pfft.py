@@ -15,7 +15,7 @@ pytestmark = pytest.mark.gpu
 from oracle.eigt import EigT
 from oracle.grid import Grid
 from oracle.pfft import PFFT
-from paper_2602_07711_gb300 import HELM_PREC_TF32, HELM_PRECOND_EIGT, HELM_PRECOND_PFFT, Solver, media
+from paper_2602_07711_gb300 import HELM_PREC_TF32, HELM_PRECOND_EIGT, HELM_PRECOND_FFT2, HELM_PRECOND_PFFT, Solver, media
 
 
 def _rand(shape, seed):
@@ -79,3 +79,34 @@ def test_pfft_tensor_core_fgmres_converges_like_eigt():
         out[pc] = (x.cpu().numpy(), info.iterations)
     d = np.linalg.norm(out[1][0] - out[2][0]) / np.linalg.norm(out[1][0])
     assert d < 1e-5 and abs(out[1][1] - out[2][1]) <= 2
+
+
+@pytest.mark.parametrize("n,L", [((32, 32, 20), (1.0, 1.0, 0.625)), ((64, 32, 33), (1.0, 0.6, 0.5))])
+def test_fft2_preconditioner_matches_oracle(n, L):
+    """FFT2 = h_z^2 (A_p^F)^-1 (the Dirichlet sine solve of PFFT's first step) against the oracle's."""
+    g = Grid(*n, lx=L[0], ly=L[1], lz=L[2], staggered=True)
+    k0 = 2 * math.pi / (10 * g.h[0])
+    S = Solver(n, np.full(g.shape, k0 * k0, complex), k0, order=4, L=L, precond=HELM_PRECOND_FFT2)
+    y = _rand(g.shape, 9)
+    z = S.apply_precond(torch.from_numpy(y).to("cuda", torch.complex64)).cpu().numpy()
+    hz = g.h[2]
+    ref = hz * hz * PFFT(g, k0, variant="face").solve_F(y).reshape(g.shape)
+    # FP32 sine transforms and z-solves; without the absorbing condition the Dirichlet z-systems have no
+    # damping and come closer to singular than EigT's, which amplifies the rounding (1.6e-5 measured at 32^3)
+    assert np.linalg.norm(z - ref) / np.linalg.norm(ref) < 1e-4
+
+
+def test_fft2_needs_many_more_iterations_than_eigt():
+    """The paper's comparison (Sec. 5): a preconditioner with the absorbing condition (EigT) converges in a
+    handful of iterations where the Dirichlet one (FFT2) needs many; both reach the same solution."""
+    n = 64
+    k2, f, k0 = media.bumps(n, 31, 32)
+    out = {}
+    for pc in (HELM_PRECOND_EIGT, HELM_PRECOND_FFT2):
+        S = Solver((n, n, n), k2, k0, order=6, precond=pc, flexible=True, rtol=1e-6, max_iter=400)
+        x, info = S.solve(S.build_rhs(torch.from_numpy(f).cuda()))
+        assert info.status == 0 and info.relres_true <= 1e-6
+        out[pc] = (x.cpu().numpy(), info.iterations)
+    d = np.linalg.norm(out[HELM_PRECOND_EIGT][0] - out[HELM_PRECOND_FFT2][0]) / np.linalg.norm(out[HELM_PRECOND_EIGT][0])
+    assert d < 2e-5
+    assert out[HELM_PRECOND_FFT2][1] >= 3 * out[HELM_PRECOND_EIGT][1]
