@@ -8,7 +8,7 @@ Value = n^3 * (inner iterations) / seconds / 1e6, whole job over all ranks (repl
 
 --impl reference times the CPU oracle (complex128 NumPy, oracle/) on a bounded sample of the same
 workload: it is the reference arm (the paper's own code is not available; its numbers are MATLAB on
-one M3 Max core and are quoted in the benchmark spec as context).
+one M3 Max core, quoted only as context).
 """
 import argparse
 import json
@@ -109,7 +109,7 @@ class ClockSampler:
 
 # ---- per-class algorithmic work -----------------------------------------------------------------
 def algorithmic(n, order, cycles_iters, real_medium=False):
-    """Bytes (and flops) the kernels of one solve must move, by class (the figures the design doc states).
+    """Bytes (and flops) the kernels of one solve must move, by class (per-point byte counts of each kernel class).
     A medium without attenuation takes the real-medium matvec: k^2 as float, the order-6 fields as one
     real float4 per point."""
     pts = n ** 3

@@ -6,7 +6,7 @@ of operators are products of the one-dimensional weight sets.
 
 Ghost rules (how the layer outside the unknowns is filled):
   'staggered'   Eq. D_bc: U_0 = gamma U_1, U_{N+1} = gamma U_N, per direction; an edge or corner
-                ghost therefore carries the product of the gammas (reading).
+                ghost therefore carries the product of the gammas (our reading of the corner).
   'collocated3' second-order three-point closure of the ABC on a collocated grid: the central
                 difference of du/dn - i k0 u = 0 at the boundary node gives U_0 = U_2 + 2 i k0 h U_1
                 (this is the Lambda-bar corner gamma = 2 i k0 h, zeta = 2 of Sec. 4.1).
@@ -132,7 +132,7 @@ def apply_A6(P, K2P, dk2, lapk2, h):
     L_h[(1 + h^2 k^2/30) U] + h^4/30 dxx dyy dzz U + k^2 U + h^2/6 M_h[(1 + h^2 k^2/15) U]
     + h^2/20 { (lap k^2 - k^4) U + 2 sum_d (k^2)_d ( delta_d[(1 + h^2 k^2/6) U] + h^2/6 delta_d T_d U ) }
     with L_h = sum delta^2, M_h = dxx dyy + dxx dzz + dyy dzz, T_x = dyy + dzz (cyclic).
-    Readings: the difference operators act on the product grid functions k^2 U (the
+    Our readings: the difference operators act on the product grid functions k^2 U (the
     notation of Eq. scheme4); the (lap k^2 - k^4) term multiplies U; k^2 f and the f_d parts of
     Delta_h(k^2 U) are U-independent and live in the right-hand side (rhs.rhs6).
     dk2 = (k2_x, k2_y, k2_z) and lapk2 are given at the unknowns.
@@ -159,7 +159,7 @@ def apply_A6(P, K2P, dk2, lapk2, h):
 
 
 def derived_k2_fields(k2, staggered, h):
-    """Sampled-data reading of the continuous derivatives of k^2 in Eq. scheme6:
+    """Sampled-data reading of the continuous derivatives of k^2 in Eq. scheme6 (our reading):
     fourth-order five-point central differences with two mirror layers.  Returns (dk2, lapk2)."""
     Q = pad_coef(k2, staggered, width=2)
     nz, ny, nx = k2.shape

@@ -8,7 +8,7 @@ Lbar_z and K_z.  Eq. PFFT_SOLVER:
 The paper's sparse forward/inverse transforms and the reuse of the transformed Y are savings that do
 not change the result; this oracle forms every vector in full.
 
-Dirichlet variants (reading for the grid sizes used here):
+Dirichlet variants (our reading for the grid sizes used here):
   'node'  Lambda of Eq. lambda_mat_definition_new (zero corners): eigenvectors sin(pi i l/(N+1)),
           eigenvalues 2 cos(pi i/(N+1)) (Sec. 3.1), i.e. the DST-I (the paper's FFT grids 2^k - 1).
   'face'  Dirichlet at the staggered face, ghost U_0 = -U_1 (corner -1): eigenvectors

@@ -4,7 +4,7 @@ rhs4:  f^(IV) = (1 + sum_alpha h_alpha^2/12 delta_alpha^2) f                 (Eq
 rhs6:  f^(VI) - h^2/20 [k^2 f - h^2/3 sum_d (k^2)_d f_d]                        (Eq. scheme6)
        f^(VI) = f + h^2/12 lap f + h^4/360 (f_xxxx + f_yyyy + f_zzzz) + h^4/90 (f_xxyy + f_xxzz + f_yyzz)
 The k^2 f and f_d parts come from Delta_h(k^2 U) of Eq. scheme6, which do not involve U.
-Reading: "nabla^4 f" of Eq. scheme6 is the sum of pure fourth derivatives; with this
+Our reading: "nabla^4 f" of Eq. scheme6 is the sum of pure fourth derivatives; with this
 reading (and only with it) the scheme has sixth-order truncation error.
 """
 import numpy as np
@@ -41,7 +41,7 @@ def rhs6(f, lapf, sum4f, mixf, df, k2, dk2, h):
 
 
 def f_derivative_fields(f, staggered, h):
-    """Sampled-data reading of the derivatives of f in Eq. scheme6: lap f by fourth-order
+    """Sampled-data reading of the derivatives of f in Eq. scheme6 (our reading): lap f by fourth-order
     five-point differences; pure fourth derivatives by delta^4; mixed ones by delta^2 delta^2;
     f_d by delta_d.  Two mirror layers.  Returns (lapf, sum4f, mixf, (fx, fy, fz))."""
     Q = pad_coef(f, staggered, width=2)

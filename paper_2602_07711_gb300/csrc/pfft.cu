@@ -1,7 +1,7 @@
 // PFFT preconditioner (Sec. 4.2, Eq. PFFT_SOLVER): A_p U = Y solved with a sine-transform solver for A_p^F
 // (Eq. TFprec) and a boundary correction.  Staggered grid, two-point ABC (zeta = 1), Dirichlet at the
 // face for A_p^F (ghost -U_1, corner -1): its x/y eigenvectors are S[l][j] = c_j sin(pi j (2l+1)/(2N)),
-// eigenvalues 2 cos(pi j/N), j = 1..N (the DST-II basis; reading for the staggered grid).
+// eigenvalues 2 cos(pi j/N), j = 1..N (the DST-II basis: our reading of "Dirichlet" for the staggered grid).
 //
 //   1. Yh = S_y^T Y_l S_x (2D sine transform of every slice), Th = z-solve_F(Yh)
 //   2. Theta on the boundary frame only (rows j = 0, N-1, columns i = 0, N-1) from Th (sparse inverse
