@@ -21,6 +21,7 @@ Module map (each function cites the passage it follows):
   metrics     rel-res, relmax-res, L2-err, max-err, relmax-err (Sec. 5.1)
   model1d     the 1D model problem of Sec. 3 (Eqs. vect_eq, coef_gen, precond)
   manufactured  the separable test solution of Sec. 5.1
+  closure     high-order ABC closure on collocated grids for the manufactured tests (reading of Sec. 2.1)
 
 Parity status: every function is pinned by a ``-m "not gpu"`` test in tests/test_oracle_*.py.
 """

@@ -10,11 +10,14 @@ Ghost rules (how the layer outside the unknowns is filled):
   'collocated3' second-order three-point closure of the ABC on a collocated grid: the central
                 difference of du/dn - i k0 u = 0 at the boundary node gives U_0 = U_2 + 2 i k0 h U_1
                 (this is the Lambda-bar corner gamma = 2 i k0 h, zeta = 2 of Sec. 4.1).
-  'given'       the caller supplies the ghost layer (manufactured-solution tests).
+  'collocated_ho' the high-order closure of oracle/closure.py (manufactured-solution tests, collocated).
+  'zero'        the ghost layer stays zero; the caller moves known ghost values to the right-hand side.
 Coefficient fields (k^2, f) are extended by mirror symmetry: about the face for staggered grids,
 about the boundary node for collocated grids (zero-gradient extension; reading).
 """
 import numpy as np
+
+from .closure import pad_ghost_ho
 
 
 def pad_ghost(U, rule, gammas=None, k0=None, h=None):
@@ -201,6 +204,8 @@ class Operator:
             self.dk2, self.lapk2 = dk2, lapk2
 
     def pad(self, U):
+        if self.rule == "collocated_ho":
+            return pad_ghost_ho(U, self.k0, self.grid.h)
         return pad_ghost(U, self.rule, gammas=self.gammas, k0=self.k0, h=self.grid.h)
 
     def apply_padded(self, P):
