@@ -20,7 +20,7 @@ from oracle.grid import Grid, gamma_two_point
 from oracle.model1d import d_r, matrices
 from oracle.operators import Operator, apply_A4, apply_A6, derived_k2_fields, pad_coef
 from oracle.pfft import PFFT
-from oracle.rhs import f_derivative_fields, rhs6, rhs6_sampled
+from oracle.rhs import f_derivative_fields, rhs4_padded, rhs6, rhs6_sampled
 from oracle.tridiag import thomas
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
@@ -230,14 +230,7 @@ def _truncation(order, h, ev):
     hh = (h, h, h)
     if order == 4:
         AU = apply_A4(Up, Kp, hh)
-        fP = ev("f", P)                       # f^(IV) = (1 + sum h^2/12 delta^2) f with exact f samples
-        F = fP[1:-1, 1:-1, 1:-1].copy()
-        for axis in range(3):
-            sl_p = [slice(1, -1)] * 3
-            sl_m = [slice(1, -1)] * 3
-            sl_p[2 - axis] = slice(2, None)
-            sl_m[2 - axis] = slice(0, -2)
-            F = F + (fP[tuple(sl_p)] - 2 * fP[1:-1, 1:-1, 1:-1] + fP[tuple(sl_m)]) / 12.0
+        F = rhs4_padded(ev("f", P), hh)          # f^(IV) from exact f samples, one layer beyond
         return np.abs(AU - F).max()
     dk2 = (ev("k2x", C), ev("k2y", C), ev("k2z", C))
     AU = apply_A6(Up, Kp, dk2, ev("lapk2", C), hh)
@@ -266,15 +259,7 @@ def _manufactured_rhs(order, g, k0):
         return rhs6(f, lapf, sum4, mix, df, k2, zero, g.h)
     ax = [np.arange(-1, n + 1) * hd for n, hd in zip(g.n, g.h)]
     Zp, Yp, Xp = np.meshgrid(ax[2], ax[1], ax[0], indexing="ij")
-    fP = mf.f_exact(Xp, Yp, Zp, k0)
-    F = fP[1:-1, 1:-1, 1:-1].copy()
-    for axis in range(3):
-        sl_p = [slice(1, -1)] * 3
-        sl_m = [slice(1, -1)] * 3
-        sl_p[2 - axis] = slice(2, None)
-        sl_m[2 - axis] = slice(0, -2)
-        F = F + (fP[tuple(sl_p)] - 2 * fP[1:-1, 1:-1, 1:-1] + fP[tuple(sl_m)]) / 12.0
-    return F
+    return rhs4_padded(mf.f_exact(Xp, Yp, Zp, k0), g.h)
 
 
 def _const_operator(g, k0, order, rule):
