@@ -103,6 +103,33 @@ def test_1d_spectrum_closed_form(r):
     assert abs(d_r(tau, r) - math.cos(tau)) < tau ** (2 * r + 2) / math.factorial(2 * r + 2) * 1.01
 
 
+@pytest.mark.parametrize("r", [2, 3])
+def test_1d_gmres_meets_the_theorem_estimate(r):
+    """Theorem last_1D_theorem: right-preconditioned GMRES on the order-2r 1D scheme with the second-order
+    preconditioner has ||r_n|| <= (2 tau^2/delta0 sum_l k^(2l)/(4^l (2(l+2))!))^n ||r_0||; the iteration
+    count falls as N grows (the property stated after the proof)."""
+    k = 15.0
+    counts = []
+    for N in (40, 80, 160):
+        h = 1.0 / (N + 1)
+        tau = k * h
+        A, Ap = matrices(N, k, r)
+        i = np.arange(1, N + 1)
+        delta0 = np.min(np.abs(4.0 * np.sin(i * np.pi * h / 2) ** 2 / h ** 2 - k * k)) / (k * k)
+        q = 2.0 * tau ** 2 / delta0 * sum(k ** (2 * l) / (4 ** l * math.factorial(2 * (l + 2))) for l in range(r - 1))
+        assert q < 1.0
+        hist = []
+        b = np.random.default_rng(N).standard_normal(N) + 0j
+        _, info = gmres(lambda v: A @ v, lambda v: np.linalg.solve(Ap, v), b, m=N, rtol=1e-13, max_it=N,
+                        history=hist)
+        for n, rel in enumerate(hist, start=1):
+            if q ** n < 1e-12:
+                break
+            assert rel <= q ** n * (1 + 1e-9), (N, n, rel, q ** n)
+        counts.append(next(n for n, rel in enumerate(hist, start=1) if rel <= 1e-10))
+    assert counts[0] >= counts[1] >= counts[2] and counts[0] > counts[2], counts
+
+
 # ---- Thomas (Eq. Indep_precond_system) --------------------------------------------------------
 def test_thomas_vs_banded_solver():
     n, m = 37, 5
