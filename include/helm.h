@@ -46,7 +46,12 @@ typedef enum {
 
 /* Grid (Sec. 2.1 and Sec. 5.2).  N_x x N_y x N_z unknowns on [0,lx] x [0,ly] x [0,lz].
  * staggered = 1: nodes at h/2 + j h, h = L/N, ghosts eliminated by Eq. D_bc (the grid of Sec. 5.2).
- * staggered = 0: collocated nodes (i-1) h, h = L/(N-1); not built on the GPU (HELM_ERR_UNSUPPORTED). */
+ * staggered = 0: collocated nodes (i-1) h, h = L/(N-1), boundary nodes are unknowns; the ghosts follow
+ *   the three-point second-order closure of the ABC, U_0 = U_2 + 2 i k0 h U_1 per direction (edge and
+ *   corner ghosts: the one-dimensional rules applied in turn), and the preconditioner is EigT3 (Lbar with
+ *   gamma = 2 i k0 h, zeta = 2; Sec. 4.1).  k^2 and f are reflected about the boundary node.  The matvec
+ *   and the residual run on the general stencil kernels (the fast ones are staggered).  EigT only
+ *   (PFFT and FFT2: HELM_ERR_UNSUPPORTED); the 1D eigensetup needs k0 h <= 1 (HELM_ERR_EIG beyond). */
 typedef struct {
     int nx, ny, nz;
     double lx, ly, lz;

@@ -80,7 +80,9 @@ helm_status helm_setup(const helm_grid* grid, const void* k2, double k0, const d
     if (opt->order != 2 && opt->order != 4 && opt->order != 6) return HELM_ERR_ARG;
     if (opt->restart < 1 || opt->restart > 64 || opt->max_iter < 1 || !(opt->rtol > 0)) return HELM_ERR_ARG;
     if (opt->precond < 0 || opt->precond > 3 || opt->precision < 0 || opt->precision > 1) return HELM_ERR_ARG;
-    if (!grid->staggered) return HELM_ERR_UNSUPPORTED;
+    const int colloc = grid->staggered ? 0 : 1;
+    // the PFFT and FFT2 sine solvers are built for the staggered face
+    if (colloc && (opt->precond == HELM_PRECOND_PFFT || opt->precond == HELM_PRECOND_FFT2)) return HELM_ERR_UNSUPPORTED;
     // the Krylov kernels move two points per 16-byte access: the point count must be even
     if (((size_t)grid->nx * grid->ny * grid->nz) % 2 != 0) return HELM_ERR_UNSUPPORTED;
     if (grid->nz > 512) return HELM_ERR_UNSUPPORTED;
@@ -91,7 +93,10 @@ helm_status helm_setup(const helm_grid* grid, const void* k2, double k0, const d
     c->opt = *opt;
     c->nx = grid->nx; c->ny = grid->ny; c->nz = grid->nz;
     c->npts = (size_t)c->nx * c->ny * c->nz;
-    c->h[0] = grid->lx / grid->nx; c->h[1] = grid->ly / grid->ny; c->h[2] = grid->lz / grid->nz;
+    c->colloc = colloc;
+    // staggered: nodes h/2 + j h, h = L/N (Sec. 5.2); collocated: nodes j h, h = L/(N-1) (Sec. 2.1)
+    c->h[0] = grid->lx / (grid->nx - colloc); c->h[1] = grid->ly / (grid->ny - colloc);
+    c->h[2] = grid->lz / (grid->nz - colloc);
     if (opt->order == 6) {
         const double tol = 1e-12 * c->h[0];
         if (fabs(c->h[1] - c->h[0]) > tol || fabs(c->h[2] - c->h[0]) > tol) { delete c; return HELM_ERR_ARG; }
@@ -100,10 +105,17 @@ helm_status helm_setup(const helm_grid* grid, const void* k2, double k0, const d
     c->ax = c->h[2] * c->h[2] / (c->h[0] * c->h[0]);
     c->ay = c->h[2] * c->h[2] / (c->h[1] * c->h[1]);
     for (int d = 0; d < 3; ++d) {
-        // gamma = (2 + i k0 h)/(2 - i k0 h), Eq. D_bc
         const double a = k0 * c->h[d], den = 4.0 + a * a;
-        c->gam[d] = make_double2((4.0 - a * a) / den, 4.0 * a / den);
-        c->zeta[d] = 1.0;
+        if (colloc) {
+            // central difference of du/dn = i k0 u at the boundary node: U_0 = U_2 + 2 i k0 h U_1, which puts
+            // gamma = 2 i k0 h on the corner of Lbar and zeta = 2 next to it (Sec. 4.1)
+            c->gam[d] = make_double2(0.0, 2.0 * a);
+            c->zeta[d] = 2.0;
+        } else {
+            // gamma = (2 + i k0 h)/(2 - i k0 h), Eq. D_bc
+            c->gam[d] = make_double2((4.0 - a * a) / den, 4.0 * a / den);
+            c->zeta[d] = 1.0;
+        }
     }
     const size_t n = c->npts;
     TRY(dalloc(&c->k2_d, n));

@@ -100,8 +100,9 @@ struct helm_ctx {
     double h[3];
     double k0;
     double ax, ay;                 // alpha_d = h_z^2/h_d^2
-    double2 gam[3];                // two-point ABC ghost factors
-    double zeta[3];                // 1 for staggered grids
+    double2 gam[3];                // corner entry of Lbar: two-point ghost factor (staggered), 2 i k0 h (collocated)
+    double zeta[3];                // corner neighbour of Lbar: 1 staggered, 2 collocated
+    int colloc = 0;                // collocated grid: ghost U_0 = U_2 + 2 i k0 h U_1 per direction
     // coefficient fields
     double2* k2_d = nullptr;
     float2* k2_f = nullptr;

@@ -1,5 +1,6 @@
 // EigT step 1 (Sec. 4.1, Eq. EIG_SOLVER): FP64 eigendecomposition Lbar = V D V^-1 of the 1D matrix
-// of Eq. lambda_mat_definition for the staggered two-point ABC (corner gamma, zeta = 1), on the GPU.
+// of Eq. lambda_mat_definition, on the GPU: the staggered two-point ABC (corner gamma, zeta = 1) and the
+// collocated three-point ABC (gamma = 2 i k0 h, zeta = 2).
 //
 // Method (our own, for this structured matrix): with v_l = cos((l - (N+1)/2) theta) or
 // sin((l - (N+1)/2) theta), the interior rows give lambda = 2 cos theta and the two corner rows collapse
@@ -13,6 +14,16 @@
 // the bilinear form v^T w; normalising v^T v = 1 gives V^-1 = V^T without an inverse.  The result is
 // checked by the residual |Lbar v - d v| and by |V^-1 V - I|; a failure is retried with more
 // continuation steps and then reported as HELM_ERR_EIG.
+//
+// zeta = 2: the same vectors satisfy the interior rows; with b = (N-1)/2 the corner rows become
+//     symmetric:      -2 sin(b theta) sin(theta) = gamma cos(b theta)
+//     antisymmetric:   2 cos(b theta) sin(theta) = gamma sin(b theta)       (divided by sin(theta/2))
+// At gamma = 0 (the Neumann-like matrix) the roots are pi j/(N-1), j = 0..N-1, even j symmetric; j = 0
+// and j = N-1 are double roots (theta = 0, pi), so their first continuation step starts from the
+// small-gamma expansions theta^2 = -gamma/(2b) and (pi - theta)^2 = gamma/(2b).  Lbar = W S W^-1 with
+// W = diag(sqrt 2, 1, .., 1, sqrt 2) and S complex symmetric, so V^-1 = V^T W^-2 once v^T W^-2 v = 1
+// (the end entries weigh one half).  The straight continuation path is reliable for |gamma| <= 2
+// (k0 h <= 1, at least six points per wavelength); beyond that the check reports HELM_ERR_EIG.
 #include "common.cuh"
 #include <cmath>
 #include <cstring>
@@ -54,20 +65,44 @@ __device__ inline void family(double2 th, int N, double2 g, bool anti, double2& 
     }
 }
 
-__global__ void eig_newton_kernel(int N, double2 gamma, int steps, double2* __restrict__ D, double2* __restrict__ V,
-                                  double2* __restrict__ Vinv) {
+// F(theta) and F'(theta) for one family of the zeta = 2 matrix.
+__device__ inline void family_z2(double2 th, int N, double2 g, bool anti, double2& F, double2& dF) {
+    const double b = 0.5 * (N - 1);
+    const double2 tb = make_double2(b * th.x, b * th.y);
+    const double2 sb = c_sin(tb), cb = c_cos(tb), s1 = c_sin(th), c1 = c_cos(th);
+    if (!anti) {
+        // F = -2 sin(b t) sin t - g cos(b t)
+        F = csub(cscale(cmul(sb, s1), -2.0), cmul(g, cb));
+        dF = cadd(cadd(cscale(cmul(cb, s1), -2.0 * b), cscale(cmul(sb, c1), -2.0)), cscale(cmul(g, sb), b));
+    } else {
+        // (2 cos(b t) sin t - g sin(b t)) / sin(t/2)
+        const double2 num = csub(cscale(cmul(cb, s1), 2.0), cmul(g, sb));
+        const double2 dnum = csub(cadd(cscale(cmul(sb, s1), -2.0 * b), cscale(cmul(cb, c1), 2.0)), cscale(cmul(g, cb), b));
+        const double2 h = make_double2(0.5 * th.x, 0.5 * th.y);
+        const double2 sh = c_sin(h), ch = c_cos(h);
+        F = cdiv(num, sh);
+        dF = cdiv(csub(cmul(dnum, sh), cmul(num, cscale(ch, 0.5))), cmul(sh, sh));
+    }
+}
+
+__global__ void eig_newton_kernel(int N, double2 gamma, int z2, int steps, double2* __restrict__ D,
+                                  double2* __restrict__ V, double2* __restrict__ Vinv) {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= N) return;
     const int jp = j + 1;
-    const bool anti = (jp % 2) == 0;
-    double2 th = make_double2(M_PI * jp / (N + 1.0), 0.0);
+    const bool anti = z2 ? (j % 2) == 1 : (jp % 2) == 0;
+    double2 th = make_double2(z2 ? M_PI * j / (N - 1.0) : M_PI * jp / (N + 1.0), 0.0);
+    const double b = 0.5 * (N - 1);
     for (int s = 1; s <= steps; ++s) {
         const double t = (double)s / steps;
         const double2 g = make_double2(t * gamma.x, t * gamma.y);
+        if (z2 && s == 1 && j == 0) th = c_sqrt(make_double2(-g.x / (2.0 * b), -g.y / (2.0 * b)));
+        if (z2 && s == 1 && j == N - 1) th = csub(make_double2(M_PI, 0.0), c_sqrt(make_double2(g.x / (2.0 * b), g.y / (2.0 * b))));
         const int its = s < steps ? 3 : 30;
         for (int it = 0; it < its; ++it) {
             double2 F, dF;
-            family(th, N, g, anti, F, dF);
+            if (z2) family_z2(th, N, g, anti, F, dF);
+            else family(th, N, g, anti, F, dF);
             const double2 step = cdiv(F, dF);
             if (!(isfinite(step.x) && isfinite(step.y))) break;
             th = csub(th, step);
@@ -80,15 +115,17 @@ __global__ void eig_newton_kernel(int N, double2 gamma, int steps, double2* __re
         const double off = l - 0.5 * (N - 1);
         const double2 arg = make_double2(off * th.x, off * th.y);
         const double2 v = anti ? c_sin(arg) : c_cos(arg);
-        nrm = cadd(nrm, cmul(v, v));
+        const double wt = (z2 && (l == 0 || l == N - 1)) ? 0.5 : 1.0;
+        nrm = cadd(nrm, cscale(cmul(v, v), wt));
     }
     const double2 inv = cdiv(make_double2(1.0, 0.0), c_sqrt(nrm));
     for (int l = 0; l < N; ++l) {
         const double off = l - 0.5 * (N - 1);
         const double2 arg = make_double2(off * th.x, off * th.y);
         const double2 v = cmul(anti ? c_sin(arg) : c_cos(arg), inv);
+        const double wt = (z2 && (l == 0 || l == N - 1)) ? 0.5 : 1.0;
         V[(size_t)l * N + j] = v;
-        Vinv[(size_t)j * N + l] = v;
+        Vinv[(size_t)j * N + l] = cscale(v, wt);
     }
 }
 
@@ -98,8 +135,9 @@ __device__ inline void atomic_max_nonneg(unsigned long long* addr, double v) {
 }
 
 // res[0] = max_j |Lbar v_j - d_j v_j|_inf,  res[1] = max_{j,k} |(V^-1 V)_{jk} - delta_jk|
-__global__ void eig_check_kernel(int N, double2 gamma, const double2* __restrict__ D, const double2* __restrict__ V,
-                                 const double2* __restrict__ Vinv, unsigned long long* res) {
+__global__ void eig_check_kernel(int N, double2 gamma, double zeta, const double2* __restrict__ D,
+                                 const double2* __restrict__ V, const double2* __restrict__ Vinv,
+                                 unsigned long long* res) {
     const size_t id = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
     if (id >= (size_t)N * N) return;
     const int j = (int)(id / N), k = (int)(id % N);
@@ -112,8 +150,8 @@ __global__ void eig_check_kernel(int N, double2 gamma, const double2* __restrict
         double worst = 0.0;
         for (int l = 0; l < N; ++l) {
             double2 lv = make_double2(0.0, 0.0);
-            if (l > 0) lv = cadd(lv, V[(size_t)(l - 1) * N + k]);
-            if (l < N - 1) lv = cadd(lv, V[(size_t)(l + 1) * N + k]);
+            if (l > 0) lv = cadd(lv, cscale(V[(size_t)(l - 1) * N + k], l == N - 1 ? zeta : 1.0));
+            if (l < N - 1) lv = cadd(lv, cscale(V[(size_t)(l + 1) * N + k], l == 0 ? zeta : 1.0));
             if (l == 0 || l == N - 1) lv = cadd(lv, cmul(gamma, V[(size_t)l * N + k]));
             lv = csub(lv, cmul(D[k], V[(size_t)l * N + k]));
             worst = fmax(worst, hypot(lv.x, lv.y));
@@ -143,15 +181,16 @@ __global__ void prep_operands_kernel(int N, double alpha, const double2* __restr
     if (q == 0) ds[r] = make_float2((float)(alpha * D[r].x), (float)(alpha * D[r].y));
 }
 
-helm_status eig_one_axis(int N, double2 gamma, double2* D, double2* V, double2* Vinv, unsigned long long* chk,
-                         cudaStream_t s) {
+helm_status eig_one_axis(int N, double2 gamma, double zeta, double2* D, double2* V, double2* Vinv,
+                         unsigned long long* chk, cudaStream_t s) {
     const int steps_try[2] = {32, 256};
+    const int z2 = zeta != 1.0;
     for (int t = 0; t < 2; ++t) {
-        eig_newton_kernel<<<(N + 127) / 128, 128, 0, s>>>(N, gamma, steps_try[t], D, V, Vinv);
+        eig_newton_kernel<<<(N + 127) / 128, 128, 0, s>>>(N, gamma, z2, steps_try[t], D, V, Vinv);
         HELM_CUDA_TRY(cudaGetLastError());
         HELM_CUDA_TRY(cudaMemsetAsync(chk, 0, 2 * sizeof(unsigned long long), s));
         const size_t nn = (size_t)N * N;
-        eig_check_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, s>>>(N, gamma, D, V, Vinv, chk);
+        eig_check_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, s>>>(N, gamma, zeta, D, V, Vinv, chk);
         HELM_CUDA_TRY(cudaGetLastError());
         unsigned long long h[2];
         HELM_CUDA_TRY(cudaMemcpyAsync(h, chk, sizeof(h), cudaMemcpyDeviceToHost, s));
@@ -169,8 +208,8 @@ helm_status eig_one_axis(int N, double2 gamma, double2* D, double2* V, double2* 
 helm_status run_eig_setup(helm_ctx* c, cudaStream_t s) {
     unsigned long long* chk = nullptr;
     HELM_CUDA_TRY(cudaMalloc(&chk, 2 * sizeof(unsigned long long)));
-    helm_status st = eig_one_axis(c->nx, c->gam[0], c->Dx, c->Vx, c->Vxi, chk, s);
-    if (st == HELM_OK) st = eig_one_axis(c->ny, c->gam[1], c->Dy, c->Vy, c->Vyi, chk, s);
+    helm_status st = eig_one_axis(c->nx, c->gam[0], c->zeta[0], c->Dx, c->Vx, c->Vxi, chk, s);
+    if (st == HELM_OK) st = eig_one_axis(c->ny, c->gam[1], c->zeta[1], c->Dy, c->Vy, c->Vyi, chk, s);
     cudaFree(chk);
     if (st != HELM_OK) return st;
     {

@@ -16,6 +16,10 @@
 //   T_+- = (sum of the four transverse neighbours of the side point) - 4 (side point).
 //   Ghosts (Eq. D_bc): U_0 = gamma U_1, U_{N+1} = gamma U_N per direction (edge and corner ghosts take
 //   the product of the gammas); k^2 at a ghost is the mirror value of its neighbour.
+//   Collocated grids (these kernels only; the fast kernels are staggered): the three-point closure
+//   U_0 = U_2 + g U_1, U_{N+1} = U_{N-1} + g U_N with g = 2 i k0 h, applied direction by direction, so an
+//   edge or corner ghost is the tensor product of the one-dimensional rules; k^2 and f are reflected about
+//   the boundary node.
 //
 // Arithmetic policies: complex64 (the Krylov matvec), complex128 (helm_apply_A in FP64) and
 // double-float complex (hi + lo pairs of floats, about 44 significant bits) for the true residual F - A x.
@@ -100,7 +104,8 @@ struct PDF {
 template <class P>
 struct SParams {
     int nx, ny, nz;
-    typename P::C gx, gy, gz;              // ghost factors (Eq. D_bc)
+    int colloc;                            // 1: collocated three-point closure, 0: staggered two-point
+    typename P::C gx, gy, gz;              // ghost factors (Eq. D_bc), or 2 i k0 h_d when collocated
     typename P::S ihx, ihy, ihz;           // 1/h_d^2
     typename P::S wxy, wxz, wyz;           // (ha^2 + hb^2)/(12 ha^2 hb^2), order 4
     typename P::S h2_20;                   // h^2/20, order 6
@@ -111,9 +116,44 @@ struct SParams {
     const typename P::M* G;                // lap(k^2) - k^4 (order 6)
 };
 
+// One-dimensional collocated ghost rule: an index below the grid reads nodes 1 and 0 (weights 1 and g),
+// one above reads n-2 and n-1.  Indexes further out (tile padding that no output uses) read the same
+// in-range nodes.  Returns the number of terms.
+__device__ __forceinline__ int colloc_terms(int v, int n, int* idx) {
+    if (v < 0) { idx[0] = 1; idx[1] = 0; return 2; }
+    if (v >= n) { idx[0] = n - 2; idx[1] = n - 1; return 2; }
+    idx[0] = v;
+    return 1;
+}
+
+template <class P>
+__device__ __noinline__ typename P::C fetch_u_colloc(const SParams<P>& p, const typename P::M* __restrict__ U, int X,
+                                                     int Y, int Z) {
+    int ix[2], iy[2], iz[2];
+    const int nxx = colloc_terms(X, p.nx, ix), nyy = colloc_terms(Y, p.ny, iy), nzz = colloc_terms(Z, p.nz, iz);
+    typename P::C acc = P::zero();
+    for (int c = 0; c < nzz; ++c)
+        for (int b = 0; b < nyy; ++b)
+            for (int a = 0; a < nxx; ++a) {
+                typename P::C v = P::ld(U, ((size_t)iz[c] * p.ny + iy[b]) * p.nx + ix[a]);
+                if (a) v = P::mul(v, p.gx);
+                if (b) v = P::mul(v, p.gy);
+                if (c) v = P::mul(v, p.gz);
+                acc = P::add(acc, v);
+            }
+    return acc;
+}
+
+__device__ __forceinline__ int reflect_node(int v, int n) {
+    int r = v < 0 ? -v : (v >= n ? 2 * (n - 1) - v : v);
+    return r < 0 ? 0 : (r >= n ? n - 1 : r);
+}
+
 template <class P>
 __device__ __forceinline__ typename P::C fetch_u(const SParams<P>& p, const typename P::M* __restrict__ U, int X, int Y,
                                                  int Z) {
+    if (p.colloc && (X < 0 || X >= p.nx || Y < 0 || Y >= p.ny || Z < 0 || Z >= p.nz))
+        return fetch_u_colloc<P>(p, U, X, Y, Z);
     const int Xc = X < 0 ? 0 : (X >= p.nx ? p.nx - 1 : X);
     const int Yc = Y < 0 ? 0 : (Y >= p.ny ? p.ny - 1 : Y);
     const int Zc = Z < 0 ? 0 : (Z >= p.nz ? p.nz - 1 : Z);
@@ -126,6 +166,8 @@ __device__ __forceinline__ typename P::C fetch_u(const SParams<P>& p, const type
 
 template <class P>
 __device__ __forceinline__ typename P::C fetch_k(const SParams<P>& p, int X, int Y, int Z) {
+    if (p.colloc)
+        return P::ld(p.k2, ((size_t)reflect_node(Z, p.nz) * p.ny + reflect_node(Y, p.ny)) * p.nx + reflect_node(X, p.nx));
     const int Xc = X < 0 ? 0 : (X >= p.nx ? p.nx - 1 : X);
     const int Yc = Y < 0 ? 0 : (Y >= p.ny ? p.ny - 1 : Y);
     const int Zc = Z < 0 ? 0 : (Z >= p.nz ? p.nz - 1 : Z);
@@ -360,6 +402,7 @@ template <class P>
 SParams<P> make_params(const helm_ctx* c) {
     SParams<P> p;
     p.nx = c->nx; p.ny = c->ny; p.nz = c->nz;
+    p.colloc = c->colloc;
     const double hx = c->h[0], hy = c->h[1], hz = c->h[2];
     p.gx = P::hc(c->gam[0]); p.gy = P::hc(c->gam[1]); p.gz = P::hc(c->gam[2]);
     const double ihx = 1.0 / (hx * hx), ihy = 1.0 / (hy * hy), ihz = 1.0 / (hz * hz);
@@ -377,13 +420,15 @@ SParams<P> make_params(const helm_ctx* c) {
 
 // ---- coefficient fields of Eq. scheme6 (set-up, FP64) ----------------------------------------
 __device__ inline int mirror_stag(int i, int n) { return i < 0 ? -i - 1 : (i >= n ? 2 * n - 1 - i : i); }
+// mirror about the face (staggered) or about the boundary node (collocated), for offsets of at most 2
+__device__ inline int mirror_ext(int i, int n, int colloc) { return colloc ? reflect_node(i, n) : mirror_stag(i, n); }
 
 __device__ __forceinline__ float4 split4(double2 v) {
     const float rh = (float)v.x, ih = (float)v.y;
     return make_float4(rh, ih, (float)(v.x - (double)rh), (float)(v.y - (double)ih));
 }
 
-__global__ void derived_kernel(int order, int nx, int ny, int nz, double hx, double hy, double hz,
+__global__ void derived_kernel(int order, int colloc, int nx, int ny, int nz, double hx, double hy, double hz,
                                const double2* __restrict__ k2, double2* dkx, double2* dky, double2* dkz, double2* G,
                                float2* fdkx, float2* fdky, float2* fdkz, float2* fG, float2* fk2, float4* k2df,
                                float4* Gdf) {
@@ -395,7 +440,8 @@ __global__ void derived_kernel(int order, int nx, int ny, int nz, double hx, dou
         if (order != 6) continue;
         const int i = (int)(id % nx), j = (int)((id / nx) % ny), l = (int)(id / ((size_t)nx * ny));
         auto at = [&](int a, int b, int c) {
-            return k2[((size_t)mirror_stag(l + c, nz) * ny + mirror_stag(j + b, ny)) * nx + mirror_stag(i + a, nx)];
+            return k2[((size_t)mirror_ext(l + c, nz, colloc) * ny + mirror_ext(j + b, ny, colloc)) * nx +
+                      mirror_ext(i + a, nx, colloc)];
         };
         double2 g[3];
         double2 lap = make_double2(0, 0);
@@ -434,7 +480,7 @@ struct RhsW {
     float i2h[3];     // 1 / (2 h_d)
 };
 
-__global__ void rhs_df_kernel(int order, int nx, int ny, int nz, RhsW W, const float4* __restrict__ fdf,
+__global__ void rhs_df_kernel(int order, int colloc, int nx, int ny, int nz, RhsW W, const float4* __restrict__ fdf,
                               const float4* __restrict__ k2df, const float2* __restrict__ dkx,
                               const float2* __restrict__ dky, const float2* __restrict__ dkz,
                               double2* __restrict__ F) {
@@ -443,7 +489,8 @@ __global__ void rhs_df_kernel(int order, int nx, int ny, int nz, RhsW W, const f
     if (i >= nx) return;
     const size_t id = ((size_t)l * ny + j) * nx + i;
     auto at = [&](int a, int b, int c) {
-        return cdf_from4(fdf[((size_t)mirror_stag(l + c, nz) * ny + mirror_stag(j + b, ny)) * nx + mirror_stag(i + a, nx)]);
+        return cdf_from4(fdf[((size_t)mirror_ext(l + c, nz, colloc) * ny + mirror_ext(j + b, ny, colloc)) * nx +
+                             mirror_ext(i + a, nx, colloc)]);
     };
     const cdf fc = cdf_from4(fdf[id]);
     if (order == 2) { F[id] = cdf_to_double2(fc); return; }
@@ -549,7 +596,7 @@ void launch_stencil(helm_ctx* c, const SParams<P>& p, const typename P::M* x, ty
 }  // namespace
 
 helm_status launch_derived_fields(helm_ctx* c, cudaStream_t s) {
-    derived_kernel<<<1024, 256, 0, s>>>(c->opt.order, c->nx, c->ny, c->nz, c->h[0], c->h[1], c->h[2], c->k2_d,
+    derived_kernel<<<1024, 256, 0, s>>>(c->opt.order, c->colloc, c->nx, c->ny, c->nz, c->h[0], c->h[1], c->h[2], c->k2_d,
                                         c->dk2_d[0], c->dk2_d[1], c->dk2_d[2], c->G_d, c->dk2_f[0], c->dk2_f[1],
                                         c->dk2_f[2], c->G_f, c->k2_f, c->k2_df, c->G_df);
     HELM_CUDA_TRY(cudaGetLastError());
@@ -634,7 +681,8 @@ helm_status launch_rhs(helm_ctx* c, const double2* f, double2* F, float4* fdf, c
         W.mix[q] = PDF::cst(h2 * h2 / (90.0 * hh[pr[q][0]] * hh[pr[q][0]] * hh[pr[q][1]] * hh[pr[q][1]]));
     W.h2_20 = PDF::cst(h2 / 20.0);
     W.h4_60 = (float)(h2 * h2 / 60.0);
-    rhs_df_kernel<<<dim3((c->nx + 127) / 128, c->ny, c->nz), 128, 0, s>>>(c->opt.order, c->nx, c->ny, c->nz, W, fdf,
+    rhs_df_kernel<<<dim3((c->nx + 127) / 128, c->ny, c->nz), 128, 0, s>>>(c->opt.order, c->colloc, c->nx, c->ny,
+                                                                         c->nz, W, fdf,
                                                                          c->k2_df,
                                        c->dk2_f[0], c->dk2_f[1], c->dk2_f[2], F);
     prof_end(c, s);

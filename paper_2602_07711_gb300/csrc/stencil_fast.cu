@@ -602,7 +602,7 @@ helm_status stencil_real_prepare(helm_ctx* c, cudaStream_t s) {
     return HELM_OK;
 }
 
-bool stencil_fast_supported(const helm_ctx* c) { return c->opt.order == 4 || c->opt.order == 6; }
+bool stencil_fast_supported(const helm_ctx* c) { return !c->colloc && (c->opt.order == 4 || c->opt.order == 6); }
 
 // Variants of the complex64 matvec a context can run: 0 = cp.async ring at four CTAs per SM, 1 = TMA ring
 // (even N_x, else the same as 0), 2 = cp.async ring at three CTAs per SM with more registers.

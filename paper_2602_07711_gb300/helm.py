@@ -361,14 +361,16 @@ def solve_batched(solvers, bs, x0s=None, stream=None):
 
 
 class Solver:
-    """One problem: grid, k^2 samples (complex128, host numpy or torch tensor), background k0, options."""
+    """One problem: grid, k^2 samples (complex128, host numpy or torch tensor), background k0, options.
+    staggered=False selects the collocated grid with the three-point ABC closure (EigT only)."""
 
     def __init__(self, n, k2, k0, order=4, L=(1.0, 1.0, 1.0), precond=HELM_PRECOND_EIGT, precision=HELM_PREC_FP32,
-                 restart=30, max_iter=300, rtol=1e-6, flexible=False, reorth=False, k0z2=None, stream=None):
+                 restart=30, max_iter=300, rtol=1e-6, flexible=False, reorth=False, k0z2=None, stream=None,
+                 staggered=True):
         nx, ny, nz = n
         self.shape = (nz, ny, nx)
         self.n = (nx, ny, nz)
-        self.grid = helm_grid(nx, ny, nz, L[0], L[1], L[2], 1)
+        self.grid = helm_grid(nx, ny, nz, L[0], L[1], L[2], int(bool(staggered)))
         self.options = helm_options(order, precond, precision, restart, max_iter, rtol, int(flexible), int(reorth))
         if isinstance(k2, np.ndarray):
             k2 = np.ascontiguousarray(k2, dtype=np.complex128)

@@ -57,3 +57,17 @@ def test_setup_rejects_bad_arguments_without_gpu_work(libpath):
     k2 = np.zeros(512, np.complex128)
     assert L.helm_setup(ctypes.byref(g), k2.ctypes.data, 1.0, None, ctypes.byref(o), None, ctypes.byref(ctx)) == 1
     assert L.helm_setup(None, None, 1.0, None, None, None, ctypes.byref(ctx)) == 1
+
+
+def test_collocated_grid_rejects_the_sine_preconditioners_without_gpu_work(libpath):
+    from paper_2602_07711_gb300 import helm
+    import numpy as np
+    L = helm.lib()
+    ctx = ctypes.c_void_p()
+    g = helm.helm_grid(8, 8, 8, 1.0, 1.0, 1.0, 0)          # collocated: EigT only
+    k2 = np.zeros(512, np.complex128)
+    for precond in (helm.HELM_PRECOND_PFFT, helm.HELM_PRECOND_FFT2):
+        o = helm.helm_options(4, precond, 0, 30, 100, 1e-6, 0, 0)
+        assert L.helm_setup(ctypes.byref(g), k2.ctypes.data, 1.0, None, ctypes.byref(o), None,
+                            ctypes.byref(ctx)) == 10
+        assert not ctx.value

@@ -1,0 +1,138 @@
+"""Collocated grids on the GPU path (nodes j h, h = L/(N-1), Sec. 2.1): the three-point second-order
+closure of the ABC in the operator (ghost U_0 = U_2 + 2 i k0 h U_1) and the EigT3 preconditioner
+(Lambda-bar with gamma = 2 i k0 h, zeta = 2, Sec. 4.1), against the oracle's 'collocated3' rule.
+
+Tolerances as in test_gpu_parity: complex128 1e-11, double-float 1e-10, complex64 stencil 2e-6, FP32
+preconditioner 3e-6 kappa(V_x) kappa(V_y), solution 1e-5.
+"""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle.eig1d import lambda_bar
+from oracle.eigt import EigT
+from oracle.gmres import gmres
+from oracle.grid import Grid
+from oracle.operators import Operator, derived_k2_fields
+from oracle.rhs import rhs4_sampled, rhs6_sampled
+from oracle.tridiag import thomas
+from paper_2602_07711_gb300 import HELM_PREC_FP32, HELM_PREC_TF32, Solver
+
+
+def _dev(a, dtype=torch.complex128):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(device="cuda", dtype=dtype)
+
+
+def _rel(a, b):
+    return np.abs(np.asarray(a) - np.asarray(b)).max() / np.abs(np.asarray(b)).max()
+
+
+def _rand(shape, seed):
+    r = np.random.default_rng(seed)
+    return r.standard_normal(shape) + 1j * r.standard_normal(shape)
+
+
+def _medium(n, L):
+    """Smooth complex k^2 on the collocated grid, about ten points per wavelength."""
+    g = Grid(*n, lx=L[0], ly=L[1], lz=L[2], staggered=False)
+    X, Y, Z = g.mesh()
+    k0 = 2 * math.pi / (10 * g.h[0])
+    k2 = k0 * k0 * (1 + 0.25 * np.exp(-((X - .5 * L[0]) ** 2 + (Y - .45 * L[1]) ** 2 + (Z - .55 * L[2]) ** 2) / 0.03)
+                    - 0.1 * np.exp(-((X - .3 * L[0]) ** 2 + (Y - .6 * L[1]) ** 2 + (Z - .4 * L[2]) ** 2) / 0.01)) + 0j
+    k2 = k2 + 1j * 0.01 * k0 * k0 * np.sin(3 * X)
+    return g, k2, k0
+
+
+# (n, L): ragged tiles; order 6 needs one h, so L_d = (N_d - 1) h
+CASES = {
+    2: [((40, 36, 33), (1.0, 0.9, 0.85))],
+    4: [((40, 36, 33), (1.0, 0.9, 0.85)), ((66, 10, 70), (1.0, 0.2, 0.9))],
+    6: [((40, 36, 33), (1.0, 35 / 39, 32 / 39)), ((70, 18, 66), (1.0, 17 / 69, 65 / 69))],
+}
+
+
+@pytest.mark.parametrize("order,case", [(o, c) for o in (2, 4, 6) for c in CASES[o]])
+def test_collocated_apply_A_matches_oracle(order, case):
+    n, L = case
+    g, k2, k0 = _medium(n, L)
+    S = Solver(n, k2, k0, order=order, L=L, staggered=False)
+    x = _rand(g.shape, 1)
+    ref = Operator(g, k2, k0, order)(x)          # rule 'collocated3' on a collocated grid
+    assert _rel(S.apply_A(_dev(x)).cpu().numpy(), ref) < 1e-11
+    assert _rel(S.apply_A(_dev(x, torch.complex64)).cpu().numpy(), ref) < 2e-6
+
+
+@pytest.mark.parametrize("order", [4, 6])
+def test_collocated_build_rhs_matches_oracle(order):
+    n, L = (40, 36, 33), (1.0, 35 / 39, 32 / 39)
+    g, k2, k0 = _medium(n, L)
+    f = _rand(g.shape, 2)
+    S = Solver(n, k2, k0, order=order, L=L, staggered=False)
+    F = S.build_rhs(_dev(f)).cpu().numpy()
+    if order == 4:
+        ref = rhs4_sampled(f, False, g.h)
+    else:
+        dk2, _ = derived_k2_fields(k2, False, g.h)
+        ref = rhs6_sampled(f, k2, dk2, False, g.h)
+    assert _rel(F, ref) < 1e-10
+
+
+@pytest.mark.parametrize("n,kh", [(4, 0.63), (5, 0.63), (17, 0.63), (33, 0.63), (64, 0.63), (127, 0.63),
+                                  (256, 0.63), (512, 0.63), (50, 0.43), (256, 1.0)])
+def test_collocated_eigensetup_diagonalises_lambda_bar(n, kh):
+    # one step h on every axis, so that k0 h = kh on the 8-node y and z axes too
+    L = (1.0, 7.0 / (n - 1), 7.0 / (n - 1))
+    g = Grid(n, 8, 8, lx=L[0], ly=L[1], lz=L[2], staggered=False)
+    k0 = kh / g.h[0]
+    S = Solver((n, 8, 8), np.full(g.shape, k0 * k0, complex), k0, order=2, L=L, staggered=False)
+    D, V, Vi = S.get_eig(0)
+    e = EigT(g, k0)
+    assert abs(e.gx - 2j * k0 * g.h[0]) < 1e-15 and e.zx == 2.0
+    assert np.abs(np.sort_complex(D) - np.sort_complex(e.Dx)).max() < 1e-10
+    assert np.abs(V @ np.diag(D) @ Vi - lambda_bar(n, e.gx, e.zx)).max() < 1e-10
+    assert np.abs(Vi @ V - np.eye(n)).max() < 1e-10
+
+
+@pytest.mark.parametrize("n,L", [((40, 36, 33), (1.0, 0.9, 0.825)), ((64, 64, 64), (1.0, 1.0, 1.0))])
+def test_collocated_precond_steps_match_oracle(n, L):
+    g, k2, k0 = _medium(n, L)
+    S = Solver(n, k2, k0, order=4, L=L, precision=HELM_PREC_FP32, staggered=False)
+    e = EigT(g, k0)
+    tol = 3e-6 * max(1.0, np.linalg.cond(e.Vx) * np.linalg.cond(e.Vy))
+    e.Dx, e.Vx, e.Vxi = S.get_eig(0)            # the GPU's own FP64 basis
+    e.Dy, e.Vy, e.Vyi = S.get_eig(1)
+    y = _rand(g.shape, 3)
+    fwd = S.precond_step(1, _dev(y, torch.complex64)).cpu().numpy()
+    ref_fwd = e.forward(y)
+    assert _rel(fwd, ref_fwd) < tol
+    sub, diag, sup = e.z_coefficients()
+    zs = S.precond_step(2, _dev(ref_fwd, torch.complex64)).cpu().numpy()
+    ref_z = thomas(sub, diag, sup, ref_fwd)
+    assert _rel(zs, ref_z) < tol
+    assert _rel(S.precond_step(3, _dev(ref_z, torch.complex64)).cpu().numpy(), e.inverse(ref_z)) < tol
+    assert _rel(S.apply_precond(_dev(y, torch.complex64)).cpu().numpy(), e.apply_Minv(y)) < tol
+
+
+@pytest.mark.parametrize("precision,flexible", [(HELM_PREC_FP32, False), (HELM_PREC_TF32, True)])
+def test_collocated_gmres_matches_oracle(precision, flexible):
+    n = 36
+    g, k2, k0 = _medium((n, n, n), (1.0, 1.0, 1.0))
+    S = Solver((n, n, n), k2, k0, order=4, precision=precision, flexible=flexible, rtol=1e-6, restart=30,
+               max_iter=200, staggered=False)
+    f = _rand(g.shape, 5)
+    F = S.build_rhs(_dev(f))
+    x, info = S.solve(F)
+    A = Operator(g, k2, k0, 4)
+    e = EigT(g, k0)
+    Fh = F.cpu().numpy()
+    xo, _ = gmres(A, e.apply_Minv, Fh, m=30, rtol=1e-12, max_it=400)
+    _, io6 = gmres(A, e.apply_Minv, Fh, m=30, rtol=1e-6, max_it=400, flexible=flexible)
+    xg = x.cpu().numpy()
+    assert info.status == 0 and info.relres_true <= 1e-6
+    assert np.linalg.norm(A(xg) - Fh) / np.linalg.norm(Fh) <= 1.5e-6
+    assert np.linalg.norm(xg - xo.reshape(g.shape)) / np.linalg.norm(xo) <= 1e-5
+    assert -1 <= info.iterations - io6["iterations"] <= 3
