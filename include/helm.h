@@ -114,6 +114,28 @@ enum { HELM_C64 = 0, HELM_C128 = 1 };
 helm_status helm_setup(const helm_grid* grid, const void* k2, double k0, const double* k0z2,
                        const helm_options* opt, void* stream, helm_ctx** out);
 
+/* Boundary closure of a collocated grid's operator (helm_set_closure). */
+enum { HELM_CLOSURE_THREE_POINT = 0, HELM_CLOSURE_HIGH_ORDER = 1 };
+
+/* helm_set_closure - choose how the operator A (helm_apply_A, the solver's matvec, helm_residual) fills
+ * the ghosts of a collocated grid.  The preconditioner keeps the three-point rule (EigT3) either way.
+ *   HELM_CLOSURE_THREE_POINT  U_0 = U_2 + 2 i k0 h U_1 per direction (the default).
+ *   HELM_CLOSURE_HIGH_ORDER   the high-order closure of the constant-k test problems (Sec. 2.1; the paper
+ *     gives no formula, this is our reading): per face, with B the boundary node, I its interior
+ *     neighbour and h the normal step, U_ghost = U_I + i k0 sum_{m=0..2} c_m (-1)^m L^m U_B with
+ *     c_m = 2 h^(2m+1)/(2m+1)! and L = k0^2 + the two tangential second derivatives (sixth-order
+ *     differences along the face, one-sided over eight nodes near its edges); faces filled x, then y,
+ *     then z, each covering the ghost columns filled before it.  This is the U part of the closure; the
+ *     closure's f part (s sum_m c_m sum_{j<m} (-L)^j d_n^(2(m-j)-1) f, s = +-1 on the far/near face) does
+ *     not involve U and belongs to the right-hand side the caller passes to helm_gmres_solve, which
+ *     helm_build_rhs does not form.
+ * Each matvec first copies its operand into a padded array and fills the ghosts (seven small launches).
+ * Memory: three padded copies ((N_x+2)(N_y+2)(N_z+2) points as complex64, complex128 and double-float)
+ * and two scratch faces, allocated here and freed by helm_destroy or by HELM_CLOSURE_THREE_POINT.
+ * Errors: HELM_ERR_ARG (bad value), HELM_ERR_UNSUPPORTED (staggered grid, or an N below 8),
+ * HELM_ERR_NOMEM. */
+helm_status helm_set_closure(helm_ctx* ctx, int closure);
+
 /* helm_build_rhs - modified right-hand side F of the scheme from samples of f (Eqs. scheme4, scheme6).
  *   f  complex128 samples, host or device;  F  complex128 device output.  Order 2: F = f.
  * Derivatives of f and k^2 are sampled-data readings (fourth-order differences, mirror extension). */

@@ -6,7 +6,9 @@ The compute path is the C-ABI library libhelm.so (include/helm.h), built in-tree
 This package only marshals arguments (torch tensors, streams) into that library.
 """
 from .helm import (HELM_C64, HELM_C128, HELM_PREC_FP32, HELM_PREC_TF32, HELM_PRECOND_EIGT,
-                   HELM_PRECOND_NONE, HELM_PRECOND_PFFT, HELM_PRECOND_FFT2, Batch, HelmError, Net, Solver, lib, library_path, solve_batched)
+                   HELM_PRECOND_NONE, HELM_PRECOND_PFFT, HELM_PRECOND_FFT2, HELM_CLOSURE_THREE_POINT,
+                   HELM_CLOSURE_HIGH_ORDER, Batch, HelmError, Net, Solver, lib, library_path, solve_batched)
 
 __all__ = ["Solver", "Net", "Batch", "solve_batched", "HelmError", "lib", "library_path", "HELM_C64", "HELM_C128", "HELM_PREC_FP32", "HELM_PREC_TF32",
-           "HELM_PRECOND_NONE", "HELM_PRECOND_EIGT", "HELM_PRECOND_PFFT", "HELM_PRECOND_FFT2"]
+           "HELM_PRECOND_NONE", "HELM_PRECOND_EIGT", "HELM_PRECOND_PFFT", "HELM_PRECOND_FFT2",
+           "HELM_CLOSURE_THREE_POINT", "HELM_CLOSURE_HIGH_ORDER"]

@@ -103,6 +103,11 @@ struct helm_ctx {
     double2 gam[3];                // corner entry of Lbar: two-point ghost factor (staggered), 2 i k0 h (collocated)
     double zeta[3];                // corner neighbour of Lbar: 1 staggered, 2 collocated
     int colloc = 0;                // collocated grid: ghost U_0 = U_2 + 2 i k0 h U_1 per direction
+    int ho = 0;                    // collocated high-order closure (helm_set_closure): padded operands
+    float2* ho_P32 = nullptr;      // padded (nx+2)(ny+2)(nz+2) copies of the operand, per storage type
+    double2* ho_P64 = nullptr;
+    float4* ho_Pdf = nullptr;
+    double2* ho_S = nullptr;       // scratch faces L U_B, both sides
     // coefficient fields
     double2* k2_d = nullptr;
     float2* k2_f = nullptr;
@@ -149,6 +154,11 @@ struct helm_ctx {
 // ---- launchers shared across translation units -----------------------------------------------
 // stencil.cu
 helm_status launch_derived_fields(helm_ctx* c, cudaStream_t s);
+// closure.cu: padded operand with the high-order collocated closure ghosts
+helm_status closure_fill_f32(helm_ctx* c, const float2* U, cudaStream_t s);
+helm_status closure_fill_f64(helm_ctx* c, const double2* U, cudaStream_t s);
+helm_status closure_fill_df(helm_ctx* c, const float4* U, cudaStream_t s);
+void closure_release(helm_ctx* c);
 helm_status launch_stencil_f32(helm_ctx* c, const float2* x, float2* y, const double* sigma, int sidx, cudaStream_t s);
 helm_status launch_stencil_f32_cls(helm_ctx* c, const float2* x, float2* y, const double* sigma, int sidx, int cls,
                                    cudaStream_t s);   // timed under profiling class cls

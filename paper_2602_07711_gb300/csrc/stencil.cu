@@ -105,6 +105,7 @@ template <class P>
 struct SParams {
     int nx, ny, nz;
     int colloc;                            // 1: collocated three-point closure, 0: staggered two-point
+    int padded;                            // 1: U is the padded array of the high-order closure (closure.cu)
     typename P::C gx, gy, gz;              // ghost factors (Eq. D_bc), or 2 i k0 h_d when collocated
     typename P::S ihx, ihy, ihz;           // 1/h_d^2
     typename P::S wxy, wxz, wyz;           // (ha^2 + hb^2)/(12 ha^2 hb^2), order 4
@@ -152,6 +153,13 @@ __device__ __forceinline__ int reflect_node(int v, int n) {
 template <class P>
 __device__ __forceinline__ typename P::C fetch_u(const SParams<P>& p, const typename P::M* __restrict__ U, int X, int Y,
                                                  int Z) {
+    if (p.padded) {
+        // ghosts already in place; tile padding beyond them reads the ghost layer
+        const int Xp = X < -1 ? -1 : (X > p.nx ? p.nx : X);
+        const int Yp = Y < -1 ? -1 : (Y > p.ny ? p.ny : Y);
+        const int Zp = Z < -1 ? -1 : (Z > p.nz ? p.nz : Z);
+        return P::ld(U, ((size_t)(Zp + 1) * (p.ny + 2) + (Yp + 1)) * (p.nx + 2) + (Xp + 1));
+    }
     if (p.colloc && (X < 0 || X >= p.nx || Y < 0 || Y >= p.ny || Z < 0 || Z >= p.nz))
         return fetch_u_colloc<P>(p, U, X, Y, Z);
     const int Xc = X < 0 ? 0 : (X >= p.nx ? p.nx - 1 : X);
@@ -403,6 +411,7 @@ SParams<P> make_params(const helm_ctx* c) {
     SParams<P> p;
     p.nx = c->nx; p.ny = c->ny; p.nz = c->nz;
     p.colloc = c->colloc;
+    p.padded = 0;
     const double hx = c->h[0], hy = c->h[1], hz = c->h[2];
     p.gx = P::hc(c->gam[0]); p.gy = P::hc(c->gam[1]); p.gz = P::hc(c->gam[2]);
     const double ihx = 1.0 / (hx * hx), ihy = 1.0 / (hy * hy), ihz = 1.0 / (hz * hz);
@@ -620,6 +629,12 @@ helm_status launch_stencil_f32_cls(helm_ctx* c, const float2* x, float2* y, cons
     for (int d = 0; d < 3; ++d) p.dk2[d] = c->dk2_f[d];
     p.G = c->G_f;
     prof_begin(c, s, cls);
+    if (c->ho) {
+        helm_status st = closure_fill_f32(c, x, s);
+        if (st != HELM_OK) { prof_end(c, s); return st; }
+        p.padded = 1;
+        x = c->ho_P32;
+    }
     launch_stencil<P32, 0>(c, p, x, y, sigma, sidx, nullptr, nullptr, nullptr, s);
     prof_end(c, s);
     HELM_CUDA_TRY(cudaGetLastError());
@@ -632,6 +647,12 @@ helm_status launch_stencil_f64(helm_ctx* c, const double2* x, double2* y, cudaSt
     for (int d = 0; d < 3; ++d) p.dk2[d] = c->dk2_d[d];
     p.G = c->G_d;
     prof_begin(c, s, PROF_OTHER);
+    if (c->ho) {
+        helm_status st = closure_fill_f64(c, x, s);
+        if (st != HELM_OK) { prof_end(c, s); return st; }
+        p.padded = 1;
+        x = c->ho_P64;
+    }
     launch_stencil<P64, 0>(c, p, x, y, nullptr, 0, nullptr, nullptr, nullptr, s);
     prof_end(c, s);
     HELM_CUDA_TRY(cudaGetLastError());
@@ -657,6 +678,12 @@ helm_status launch_residual(helm_ctx* c, const float4* x, const float4* F, float
     for (int d = 0; d < 3; ++d) p.dk2[d] = c->dk2_f[d];
     p.G = c->G_df;
     prof_begin(c, s, PROF_RESIDUAL);
+    if (c->ho) {
+        helm_status st = closure_fill_df(c, x, s);
+        if (st != HELM_OK) { prof_end(c, s); return st; }
+        p.padded = 1;
+        x = c->ho_Pdf;
+    }
     launch_stencil<PDF, 1>(c, p, x, (float4*)nullptr, nullptr, 0, F, r, part, s);
     prof_end(c, s);
     HELM_CUDA_TRY(cudaGetLastError());

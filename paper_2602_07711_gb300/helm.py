@@ -14,6 +14,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 library_path = os.path.join(HERE, "libhelm.so")
 
 HELM_PRECOND_NONE, HELM_PRECOND_EIGT, HELM_PRECOND_PFFT, HELM_PRECOND_FFT2 = 0, 1, 2, 3
+HELM_CLOSURE_THREE_POINT, HELM_CLOSURE_HIGH_ORDER = 0, 1
 HELM_PREC_FP32, HELM_PREC_TF32 = 0, 1
 HELM_C64, HELM_C128 = 0, 1
 
@@ -60,6 +61,7 @@ _SIGS = {
                              C.c_void_p, C.POINTER(C.c_void_p)]),
     "helm_build_rhs": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "helm_apply_A": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
+    "helm_set_closure": (C.c_int, [C.c_void_p, C.c_int]),
     "helm_apply_precond": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "helm_precond_step": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
     "helm_get_eig": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
@@ -155,6 +157,10 @@ def helm_build_rhs(ctx, f, F, stream=None):
 
 def helm_apply_A(ctx, x, y, dtype, stream=None):
     _check(lib().helm_apply_A(ctx, _ptr(x), _ptr(y), int(dtype), _stream(stream)), "helm_apply_A")
+
+
+def helm_set_closure(ctx, closure):
+    _check(lib().helm_set_closure(ctx, int(closure)), "helm_set_closure")
 
 
 def helm_apply_precond(ctx, r, z, stream=None):
@@ -397,6 +403,10 @@ class Solver:
         F = self._empty(torch.complex128)
         helm_build_rhs(self.ctx, f, F, stream)
         return F
+
+    def set_closure(self, closure):
+        """Collocated grids: HELM_CLOSURE_THREE_POINT (default) or HELM_CLOSURE_HIGH_ORDER for the operator."""
+        helm_set_closure(self.ctx, closure)
 
     def apply_A(self, x, stream=None):
         import torch

@@ -136,3 +136,87 @@ def test_collocated_gmres_matches_oracle(precision, flexible):
     assert np.linalg.norm(A(xg) - Fh) / np.linalg.norm(Fh) <= 1.5e-6
     assert np.linalg.norm(xg - xo.reshape(g.shape)) / np.linalg.norm(xo) <= 1e-5
     assert -1 <= info.iterations - io6["iterations"] <= 3
+
+
+# ---- high-order closure (helm_set_closure) against the oracle's 'collocated_ho' rule --------------------
+HO_CASES = {
+    4: [((40, 36, 33), (1.0, 0.9, 0.85)), ((16, 9, 12), (1.0, 0.6, 0.7))],
+    6: [((40, 36, 33), (1.0, 35 / 39, 32 / 39)), ((34, 8, 20), (1.0, 7 / 33, 19 / 33))],
+}
+
+
+def _ho_solver(n, L, order, k2, k0, **kw):
+    from paper_2602_07711_gb300 import HELM_CLOSURE_HIGH_ORDER
+    S = Solver(n, k2, k0, order=order, L=L, staggered=False, **kw)
+    S.set_closure(HELM_CLOSURE_HIGH_ORDER)
+    return S
+
+
+@pytest.mark.parametrize("order,case", [(o, c) for o in (4, 6) for c in HO_CASES[o]])
+def test_high_order_closure_apply_A_matches_oracle(order, case):
+    n, L = case
+    g, k2, k0 = _medium(n, L)
+    S = _ho_solver(n, L, order, k2, k0)
+    x = _rand(g.shape, 21)
+    ref = Operator(g, k2, k0, order, rule="collocated_ho")(x)
+    assert _rel(S.apply_A(_dev(x)).cpu().numpy(), ref) < 1e-11
+    assert _rel(S.apply_A(_dev(x, torch.complex64)).cpu().numpy(), ref) < 2e-6
+    # back to the three-point rule
+    from paper_2602_07711_gb300 import HELM_CLOSURE_THREE_POINT
+    S.set_closure(HELM_CLOSURE_THREE_POINT)
+    assert _rel(S.apply_A(_dev(x)).cpu().numpy(), Operator(g, k2, k0, order)(x)) < 1e-11
+
+
+def test_high_order_closure_residual_resolves_small_residuals():
+    n, L = (32, 32, 32), (1.0, 1.0, 1.0)
+    g, k2, k0 = _medium(n, L)
+    A = Operator(g, k2, k0, 6, rule="collocated_ho")
+    F = _rand(g.shape, 22)
+    x, _ = gmres(A, EigT(g, k0).apply_Minv, F, m=30, rtol=1e-13, max_it=600)
+    xp = x.reshape(g.shape) + 1e-9 * np.abs(x).max() * _rand(g.shape, 23)
+    r_ref = F - A(xp)
+    S = _ho_solver(n, L, 6, k2, k0)
+    n2, ni = S.residual(_dev(F), _dev(xp))
+    ref2 = np.linalg.norm(r_ref)
+    assert ref2 < 1e-6 * np.linalg.norm(F)
+    assert abs(n2 - ref2) <= 0.02 * ref2, (n2, ref2)
+    assert abs(ni - np.abs(r_ref).max()) <= 0.05 * np.abs(r_ref).max()
+
+
+@pytest.mark.parametrize("precision,flexible", [(HELM_PREC_FP32, False), (HELM_PREC_TF32, True)])
+def test_high_order_closure_gmres_matches_oracle(precision, flexible):
+    n = 36
+    L = (1.0, 1.0, 1.0)
+    g, k2, k0 = _medium((n, n, n), L)
+    S = _ho_solver((n, n, n), L, 6, k2, k0, precision=precision, flexible=flexible, rtol=1e-6, restart=30,
+                   max_iter=200)
+    F = _rand(g.shape, 24)
+    x, info = S.solve(_dev(F))
+    A = Operator(g, k2, k0, 6, rule="collocated_ho")
+    e = EigT(g, k0)
+    xo, _ = gmres(A, e.apply_Minv, F, m=30, rtol=1e-12, max_it=400)
+    _, io6 = gmres(A, e.apply_Minv, F, m=30, rtol=1e-6, max_it=400, flexible=flexible)
+    xg = x.cpu().numpy()
+    assert info.status == 0 and info.relres_true <= 1e-6
+    assert np.linalg.norm(A(xg) - F) / np.linalg.norm(F) <= 1.5e-6
+    assert np.linalg.norm(xg - xo.reshape(g.shape)) / np.linalg.norm(xo) <= 1e-5
+    assert -1 <= info.iterations - io6["iterations"] <= 3
+
+
+def test_set_closure_rejects_what_it_does_not_build():
+    from paper_2602_07711_gb300 import HELM_CLOSURE_HIGH_ORDER, HelmError
+    g, k2, k0 = _medium((16, 8, 8), (1.0, 7 / 15, 7 / 15))
+    S = Solver((16, 8, 8), k2, k0, order=4, L=(1.0, 7 / 15, 7 / 15), staggered=False)
+    with pytest.raises(HelmError) as e:
+        S.set_closure(7)
+    assert e.value.code == 1
+    gs = Grid(16, 8, 8, staggered=True)
+    St = Solver((16, 8, 8), np.full(gs.shape, k0 * k0, complex), k0, order=4)
+    with pytest.raises(HelmError) as e:
+        St.set_closure(HELM_CLOSURE_HIGH_ORDER)
+    assert e.value.code == 10
+    g7, k27, _ = _medium((16, 7, 8), (1.0, 6 / 15, 7 / 15))
+    S7 = Solver((16, 7, 8), k27, k0, order=4, L=(1.0, 6 / 15, 7 / 15), staggered=False)
+    with pytest.raises(HelmError) as e:
+        S7.set_closure(HELM_CLOSURE_HIGH_ORDER)
+    assert e.value.code == 10
