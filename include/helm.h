@@ -136,6 +136,33 @@ enum { HELM_CLOSURE_THREE_POINT = 0, HELM_CLOSURE_HIGH_ORDER = 1 };
  * HELM_ERR_NOMEM. */
 helm_status helm_set_closure(helm_ctx* ctx, int closure);
 
+/* helm_build_rhs_fields - right-hand side of Eq. scheme4 / scheme6 from fields the caller knows (e.g. an
+ * analytic f), in FP64; device complex128 buffers.
+ *   order 4: fields = f on the padded grid, (N_x+2)(N_y+2)(N_z+2) values, x fastest, node (i,j,l) of the
+ *            grid at padded index (i+1, j+1, l+1); F = f + sum_d (f_{+d} - 2 f + f_{-d})/12.
+ *   order 6: fields = 7 grid arrays back to back: f, lap f, f_xxxx + f_yyyy + f_zzzz,
+ *            f_xxyy + f_xxzz + f_yyzz, f_x, f_y, f_z; F = f + h^2/12 lap f + h^4/360 (pure) + h^4/90 (mixed)
+ *            - h^2/20 (k^2 f - h^2/3 sum_d (k^2)_d f_d) with the context's sampled (k^2)_d.
+ *   order 2: fields = f, F = f.
+ * Errors: HELM_ERR_ARG (null or host pointer). */
+helm_status helm_build_rhs_fields(helm_ctx* ctx, const void* fields, void* F, void* stream);
+
+/* helm_closure_face_count - number of complex128 values helm_closure_rhs reads (0 for a staggered grid). */
+long long helm_closure_face_count(helm_ctx* ctx);
+
+/* helm_closure_rhs - F_out = F_in - A(G_f): moves the f part of the high-order closure to the right-hand
+ * side (needs HELM_CLOSURE_HIGH_ORDER).  G_f is the ghost layer the closure gives for a zero interior
+ * and the caller's face data, filled x, then y, then z like the operator's ghosts; its f part on a face
+ * is s [c_1 f_n + c_2 (f_nnn - k0^2 f_n - lap_T f_n)] with s = -1 (near face) or +1 (far face).
+ *   faces  device complex128, for axis x, y, z in turn, side near then far, fields f_n, f_nnn,
+ *          lap_T f_n (derivatives along the axis, at the boundary coordinate), each over the face:
+ *          x faces [N_z][N_y] (nodes 1..N); y faces [N_z][N_x + 2]; z faces [N_y + 2][N_x + 2], where an
+ *          extent of N + 2 runs over the ghost column, the N nodes and the far ghost column (coordinates
+ *          -h .. L + h).  helm_closure_face_count gives the total.
+ *   F_in, F_out  device complex128 grids (may alias).  Synchronises the stream; allocates one grid.
+ * Errors: HELM_ERR_ARG, HELM_ERR_UNSUPPORTED (closure not selected), HELM_ERR_NOMEM, HELM_ERR_CUDA. */
+helm_status helm_closure_rhs(helm_ctx* ctx, const void* faces, const void* F_in, void* F_out, void* stream);
+
 /* helm_build_rhs - modified right-hand side F of the scheme from samples of f (Eqs. scheme4, scheme6).
  *   f  complex128 samples, host or device;  F  complex128 device output.  Order 2: F = f.
  * Derivatives of f and k^2 are sampled-data readings (fourth-order differences, mirror extension). */
@@ -174,7 +201,8 @@ helm_status helm_gmres_solve(helm_ctx* ctx, const void* b, void* x, helm_solve_i
 
 /* helm_gmres_solve_batched - nrhs right-hand sides for each of nprob problems, solved together (an
  * extension: the paper solves one problem at a time).
- *   ctxs   nprob distinct contexts (any sizes, orders and options; EigT or no preconditioner; no attached net)
+ *   ctxs   nprob distinct contexts (any sizes, orders and options; EigT or no preconditioner; no attached
+ *          net; the three-point closure on collocated grids)
  *   b[p]   complex128 device array [nrhs][nz][ny][nx] of problem p
  *   x[p]   complex128 device array of the same shape: x^0 on entry, the iterates on exit
  *   infos  nprob*nrhs entries (problem-major), may be NULL; seconds = wall time of the whole batch
@@ -184,7 +212,8 @@ helm_status helm_gmres_solve(helm_ctx* ctx, const void* b, void* x, helm_solve_i
  * synchronises once per group of pairs that fits in 60% of the free device memory.
  * Returns HELM_OK when every pair converged, else the status of the first pair that did not (each pair's
  * status is in infos).  Errors: HELM_ERR_ARG (NULL, host pointers, a context twice), HELM_ERR_UNSUPPORTED
- * (PFFT context or attached net), HELM_ERR_NOMEM, HELM_ERR_CUDA.  Synchronises `stream`. */
+ * (PFFT or FFT2 context, attached net, or the high-order closure), HELM_ERR_NOMEM, HELM_ERR_CUDA.
+ * Synchronises `stream`. */
 helm_status helm_gmres_solve_batched(helm_ctx* const* ctxs, int nprob, const void* const* b, void* const* x, int nrhs,
                                      helm_solve_info* infos, void* stream);
 

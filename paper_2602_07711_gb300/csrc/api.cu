@@ -229,6 +229,24 @@ helm_status helm_residual(helm_ctx* c, const void* b, const void* x, void* r, do
     return residual_run(c, (const double2*)b, (const double2*)x, (float2*)r, nrm2, nrmi, (cudaStream_t)stream);
 }
 
+helm_status helm_build_rhs_fields(helm_ctx* c, const void* fields, void* F, void* stream) {
+    if (!c || !fields || !F) return HELM_ERR_ARG;
+    if (!dev_ptr(fields) || !dev_ptr(F)) return HELM_ERR_ARG;
+    return launch_rhs_fields(c, (const double2*)fields, (double2*)F, (cudaStream_t)stream);
+}
+
+long long helm_closure_face_count(helm_ctx* c) {
+    if (!c || !c->colloc) return 0;
+    return (long long)closure_face_points(c);
+}
+
+helm_status helm_closure_rhs(helm_ctx* c, const void* faces, const void* F_in, void* F_out, void* stream) {
+    if (!c || !faces || !F_in || !F_out) return HELM_ERR_ARG;
+    if (!c->ho) return HELM_ERR_UNSUPPORTED;
+    if (!dev_ptr(faces) || !dev_ptr(F_in) || !dev_ptr(F_out)) return HELM_ERR_ARG;
+    return closure_rhs(c, (const double2*)faces, (const double2*)F_in, (double2*)F_out, (cudaStream_t)stream);
+}
+
 void helm_destroy(helm_ctx* c) { free_ctx(c); }
 
 }  // extern "C"

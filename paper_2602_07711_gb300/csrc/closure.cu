@@ -124,9 +124,12 @@ __global__ void ho_lap_kernel(Face f, Wts W, const M* __restrict__ P, double2* _
     S[id] = apply_L(f, W, P, base, f.sa, f.sb, ia, ib);
 }
 
-// U_G = U_I + i k0 (c0 U_B - c1 L U_B + c2 L^2 U_B) on both ghost planes of one direction
+// U_G = U_I + i k0 (c0 U_B - c1 L U_B + c2 L^2 U_B) on both ghost planes of one direction, plus (when fd
+// is given) the f part s [c1 f_n + c2 (f_nnn - k0^2 f_n - lap_T f_n)], s = -1 near face, +1 far face;
+// fd holds [side][field][ia][ib] with the fields f_n, f_nnn, lap_T f_n (derivatives along the axis).
 template <class M>
-__global__ void ho_ghost_kernel(Face f, Wts W, M* __restrict__ P, const double2* __restrict__ S) {
+__global__ void ho_ghost_kernel(Face f, Wts W, M* __restrict__ P, const double2* __restrict__ S,
+                                const double2* __restrict__ fd) {
     const long long per = (long long)f.la * f.lb;
     const long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (id >= 2 * per) return;
@@ -143,7 +146,15 @@ __global__ void ho_ghost_kernel(Face f, Wts W, M* __restrict__ P, const double2*
     const double2 v2 = apply_L(f, W, S, side * per, (long long)f.lb, 1LL, ia, ib);
     const double2 t = make_double2(f.c0 * ub.x - f.c1 * v1.x + f.c2 * v2.x, f.c0 * ub.y - f.c1 * v1.y + f.c2 * v2.y);
     // i k0 t
-    st2(P, plane_base(f, pg) + off, make_double2(ui.x - f.k0 * t.y, ui.y + f.k0 * t.x));
+    double2 g = make_double2(ui.x - f.k0 * t.y, ui.y + f.k0 * t.x);
+    if (fd) {
+        const long long fb = (long long)side * 3 * per + q;
+        const double2 fn = fd[fb], fnnn = fd[fb + per], flt = fd[fb + 2 * per];
+        const double sg = side ? 1.0 : -1.0, kk = f.k0 * f.k0;
+        g.x += sg * (f.c1 * fn.x + f.c2 * (fnnn.x - kk * fn.x - flt.x));
+        g.y += sg * (f.c1 * fn.y + f.c2 * (fnnn.y - kk * fn.y - flt.y));
+    }
+    st2(P, plane_base(f, pg) + off, g);
 }
 
 // Second-derivative weights on offsets o_k (Taylor conditions sum_k w_k o_k^q / q! = [q == 2]), FP64
@@ -208,28 +219,65 @@ Face make_face(const helm_ctx* c, int axis) {
     return f;
 }
 
+// U = nullptr: the interior is zero (the f part of the closure alone); faces = nullptr: no f part.
 template <class M>
-helm_status fill(helm_ctx* c, const M* U, M* P, cudaStream_t s) {
-    ho_copy_kernel<M><<<1024, 256, 0, s>>>(c->nx, c->ny, c->nz, U, P);
-    HELM_CUDA_TRY(cudaGetLastError());
+helm_status fill(helm_ctx* c, const M* U, M* P, const double2* faces, cudaStream_t s) {
+    if (U) {
+        ho_copy_kernel<M><<<1024, 256, 0, s>>>(c->nx, c->ny, c->nz, U, P);
+        HELM_CUDA_TRY(cudaGetLastError());
+    } else {
+        HELM_CUDA_TRY(cudaMemsetAsync(P, 0, (size_t)(c->nx + 2) * (c->ny + 2) * (c->nz + 2) * sizeof(M), s));
+    }
     const Wts W = make_weights();
+    long long foff = 0;
     for (int axis = 0; axis < 3; ++axis) {
         const Face f = make_face(c, axis);
         const long long tot = 2LL * f.la * f.lb;
         const unsigned blocks = (unsigned)((tot + 255) / 256);
         ho_lap_kernel<M><<<blocks, 256, 0, s>>>(f, W, P, c->ho_S);
         HELM_CUDA_TRY(cudaGetLastError());
-        ho_ghost_kernel<M><<<blocks, 256, 0, s>>>(f, W, P, c->ho_S);
+        ho_ghost_kernel<M><<<blocks, 256, 0, s>>>(f, W, P, c->ho_S, faces ? faces + foff : nullptr);
         HELM_CUDA_TRY(cudaGetLastError());
+        foff += 3 * tot;
     }
     return HELM_OK;
 }
 
+__global__ void sub_kernel(const double2* __restrict__ a, const double2* __restrict__ b, double2* __restrict__ out,
+                           size_t n) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        out[i] = make_double2(a[i].x - b[i].x, a[i].y - b[i].y);
+}
+
 }  // namespace
 
-helm_status closure_fill_f32(helm_ctx* c, const float2* U, cudaStream_t s) { return fill(c, U, c->ho_P32, s); }
-helm_status closure_fill_f64(helm_ctx* c, const double2* U, cudaStream_t s) { return fill(c, U, c->ho_P64, s); }
-helm_status closure_fill_df(helm_ctx* c, const float4* U, cudaStream_t s) { return fill(c, U, c->ho_Pdf, s); }
+size_t closure_face_points(const helm_ctx* c) {
+    size_t tot = 0;
+    for (int axis = 0; axis < 3; ++axis) {
+        const Face f = make_face(c, axis);
+        tot += 2 * 3 * (size_t)f.la * f.lb;
+    }
+    return tot;
+}
+
+helm_status closure_fill_f32(helm_ctx* c, const float2* U, cudaStream_t s) { return fill(c, U, c->ho_P32, nullptr, s); }
+helm_status closure_fill_f64(helm_ctx* c, const double2* U, cudaStream_t s) { return fill(c, U, c->ho_P64, nullptr, s); }
+helm_status closure_fill_df(helm_ctx* c, const float4* U, cudaStream_t s) { return fill(c, U, c->ho_Pdf, nullptr, s); }
+
+// F_out = F_in - A(G_f), G_f the ghosts of the closure's f part with a zero interior (FP64)
+helm_status closure_rhs(helm_ctx* c, const double2* faces, const double2* Fin, double2* Fout, cudaStream_t s) {
+    double2* y = nullptr;
+    if (cudaMalloc(&y, c->npts * sizeof(double2)) != cudaSuccess) { cudaGetLastError(); return HELM_ERR_NOMEM; }
+    helm_status st = fill<double2>(c, nullptr, c->ho_P64, faces, s);
+    if (st == HELM_OK) st = launch_stencil_f64_padded(c, c->ho_P64, y, s);
+    if (st == HELM_OK) {
+        sub_kernel<<<1024, 256, 0, s>>>(Fin, y, Fout, c->npts);
+        if (cudaGetLastError() != cudaSuccess) st = HELM_ERR_CUDA;
+    }
+    cudaStreamSynchronize(s);
+    cudaFree(y);
+    return st;
+}
 
 void closure_release(helm_ctx* c) {
     void* ps[] = {c->ho_P32, c->ho_P64, c->ho_Pdf, c->ho_S};

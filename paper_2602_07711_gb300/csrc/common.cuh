@@ -159,6 +159,10 @@ helm_status closure_fill_f32(helm_ctx* c, const float2* U, cudaStream_t s);
 helm_status closure_fill_f64(helm_ctx* c, const double2* U, cudaStream_t s);
 helm_status closure_fill_df(helm_ctx* c, const float4* U, cudaStream_t s);
 void closure_release(helm_ctx* c);
+size_t closure_face_points(const helm_ctx* c);
+helm_status closure_rhs(helm_ctx* c, const double2* faces, const double2* Fin, double2* Fout, cudaStream_t s);
+helm_status launch_stencil_f64_padded(helm_ctx* c, const double2* P, double2* y, cudaStream_t s);
+helm_status launch_rhs_fields(helm_ctx* c, const double2* fields, double2* F, cudaStream_t s);
 helm_status launch_stencil_f32(helm_ctx* c, const float2* x, float2* y, const double* sigma, int sidx, cudaStream_t s);
 helm_status launch_stencil_f32_cls(helm_ctx* c, const float2* x, float2* y, const double* sigma, int sidx, int cls,
                                    cudaStream_t s);   // timed under profiling class cls

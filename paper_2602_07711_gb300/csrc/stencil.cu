@@ -659,6 +659,66 @@ helm_status launch_stencil_f64(helm_ctx* c, const double2* x, double2* y, cudaSt
     return HELM_OK;
 }
 
+// y = A P for a padded operand whose ghosts are already in place (closure.cu), complex128
+helm_status launch_stencil_f64_padded(helm_ctx* c, const double2* P, double2* y, cudaStream_t s) {
+    SParams<P64> p = make_params<P64>(c);
+    p.k2 = c->k2_d;
+    for (int d = 0; d < 3; ++d) p.dk2[d] = c->dk2_d[d];
+    p.G = c->G_d;
+    p.padded = 1;
+    launch_stencil<P64, 0>(c, p, P, y, nullptr, 0, nullptr, nullptr, nullptr, s);
+    HELM_CUDA_TRY(cudaGetLastError());
+    return HELM_OK;
+}
+
+// Right-hand side of Eq. scheme4 / scheme6 from caller-supplied fields (FP64):
+//   order 4: fields = f on the padded grid (nx+2)(ny+2)(nz+2); F = f + sum_d (f_{+d} - 2 f + f_{-d}) / 12
+//   order 6: fields = [f, lap f, sum of pure fourth derivatives, sum of mixed fourth derivatives, f_x, f_y,
+//            f_z] on the grid; F = f + h^2/12 lap f + h^4/360 S4 + h^4/90 M4
+//                                  - h^2/20 (k^2 f - h^2/3 sum_d (k^2)_d f_d)
+__global__ void rhs_fields_kernel(int order, int nx, int ny, int nz, double h, const double2* __restrict__ fld,
+                                  const double2* __restrict__ k2, const double2* __restrict__ dkx,
+                                  const double2* __restrict__ dky, const double2* __restrict__ dkz,
+                                  double2* __restrict__ F) {
+    const size_t n = (size_t)nx * ny * nz;
+    for (size_t id = blockIdx.x * (size_t)blockDim.x + threadIdx.x; id < n; id += (size_t)gridDim.x * blockDim.x) {
+        if (order == 4) {
+            const int i = (int)(id % nx), j = (int)((id / nx) % ny), l = (int)(id / ((size_t)nx * ny));
+            const size_t sx = 1, sy = nx + 2, sz = (size_t)(nx + 2) * (ny + 2);
+            const size_t pc = (l + 1) * sz + (j + 1) * sy + (i + 1);
+            const double2 fc = fld[pc];
+            double2 acc = fc;
+            const size_t st[3] = {sx, sy, sz};
+            for (int d = 0; d < 3; ++d) {
+                const double2 a = fld[pc + st[d]], b = fld[pc - st[d]];
+                acc.x += (a.x - 2.0 * fc.x + b.x) / 12.0;
+                acc.y += (a.y - 2.0 * fc.y + b.y) / 12.0;
+            }
+            F[id] = acc;
+        } else if (order == 6) {
+            const double h2 = h * h, h4 = h2 * h2;
+            const double2 f = fld[id], lap = fld[n + id], s4 = fld[2 * n + id], m4 = fld[3 * n + id];
+            const double2 fx = fld[4 * n + id], fy = fld[5 * n + id], fz = fld[6 * n + id];
+            double2 acc = make_double2(f.x + h2 / 12.0 * lap.x + h4 / 360.0 * s4.x + h4 / 90.0 * m4.x,
+                                       f.y + h2 / 12.0 * lap.y + h4 / 360.0 * s4.y + h4 / 90.0 * m4.y);
+            const double2 kf = cmul(k2[id], f);
+            const double2 g = cadd(cadd(cmul(dkx[id], fx), cmul(dky[id], fy)), cmul(dkz[id], fz));
+            acc.x -= h2 / 20.0 * (kf.x - h2 / 3.0 * g.x);
+            acc.y -= h2 / 20.0 * (kf.y - h2 / 3.0 * g.y);
+            F[id] = acc;
+        } else {
+            F[id] = fld[id];
+        }
+    }
+}
+
+helm_status launch_rhs_fields(helm_ctx* c, const double2* fields, double2* F, cudaStream_t s) {
+    rhs_fields_kernel<<<1024, 256, 0, s>>>(c->opt.order, c->nx, c->ny, c->nz, c->h[0], fields, c->k2_d, c->dk2_d[0],
+                                           c->dk2_d[1], c->dk2_d[2], F);
+    HELM_CUDA_TRY(cudaGetLastError());
+    return HELM_OK;
+}
+
 // Number of CTAs of the residual launch (one partial pair per CTA).
 int residual_ctas(const helm_ctx* c) {
     dim3 g = stencil_grid(c);

@@ -62,6 +62,9 @@ _SIGS = {
     "helm_build_rhs": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "helm_apply_A": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
     "helm_set_closure": (C.c_int, [C.c_void_p, C.c_int]),
+    "helm_build_rhs_fields": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "helm_closure_face_count": (C.c_longlong, [C.c_void_p]),
+    "helm_closure_rhs": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "helm_apply_precond": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "helm_precond_step": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
     "helm_get_eig": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
@@ -161,6 +164,18 @@ def helm_apply_A(ctx, x, y, dtype, stream=None):
 
 def helm_set_closure(ctx, closure):
     _check(lib().helm_set_closure(ctx, int(closure)), "helm_set_closure")
+
+
+def helm_build_rhs_fields(ctx, fields, F, stream=None):
+    _check(lib().helm_build_rhs_fields(ctx, _ptr(fields), _ptr(F), _stream(stream)), "helm_build_rhs_fields")
+
+
+def helm_closure_face_count(ctx):
+    return int(lib().helm_closure_face_count(ctx))
+
+
+def helm_closure_rhs(ctx, faces, F_in, F_out, stream=None):
+    _check(lib().helm_closure_rhs(ctx, _ptr(faces), _ptr(F_in), _ptr(F_out), _stream(stream)), "helm_closure_rhs")
 
 
 def helm_apply_precond(ctx, r, z, stream=None):
@@ -407,6 +422,23 @@ class Solver:
     def set_closure(self, closure):
         """Collocated grids: HELM_CLOSURE_THREE_POINT (default) or HELM_CLOSURE_HIGH_ORDER for the operator."""
         helm_set_closure(self.ctx, closure)
+
+    def build_rhs_fields(self, fields, stream=None):
+        """F of the scheme from caller-known fields (complex128 device tensor; layout in helm.h)."""
+        import torch
+        F = self._empty(torch.complex128)
+        helm_build_rhs_fields(self.ctx, fields, F, stream)
+        return F
+
+    def closure_face_count(self):
+        return helm_closure_face_count(self.ctx)
+
+    def closure_rhs(self, faces, F, stream=None):
+        """F - A(G_f): the f part of the high-order closure moved to the right-hand side."""
+        import torch
+        out = self._empty(torch.complex128)
+        helm_closure_rhs(self.ctx, faces, F, out, stream)
+        return out
 
     def apply_A(self, x, stream=None):
         import torch

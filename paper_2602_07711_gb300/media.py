@@ -100,3 +100,59 @@ def layered(n, seed, ppw=8.0, nlayers=8, lo=0.7, hi=1.3, nspheres=3, rlo=0.05, r
         rel = torch.where(r2 <= rad[b] ** 2, torch.full_like(rel, con[b]), rel)
     k2 = (k0 * k0 * rel).to(torch.complex128)
     return _finish(k2, k0, (0.0, 0.0, 1.0), X, Y, Z, as_numpy)
+
+
+# ---- the manufactured test problem of Sec. 5.1 (collocated grid) ---------------------------------------
+def _phi(x, k0, n):
+    """n-th derivative of phi(x) = exp(i k0 x) + exp(-i k0 (x - 1)) - 2 (a = 0, b = 1)."""
+    v = (1j * k0) ** n * np.exp(1j * k0 * x) + (-1j * k0) ** n * np.exp(-1j * k0 * (x - 1.0))
+    return v - 2.0 if n == 0 else v
+
+
+def _f_deriv(X, Y, Z, k0, dx, dy, dz):
+    """Derivative (dx, dy, dz) of f = lap u + k0^2 u for u = phi(x) phi(y) phi(z).  With
+    phi'' = -k0^2 (phi + 2): f = -2 k0^2 [phi phi phi + phi_y phi_z + phi_x phi_z + phi_x phi_y]."""
+    one = lambda a, n: np.ones_like(a, dtype=np.complex128) if n == 0 else np.zeros_like(a, dtype=np.complex128)
+    px, py, pz = _phi(X, k0, dx), _phi(Y, k0, dy), _phi(Z, k0, dz)
+    return -2.0 * k0 * k0 * (px * py * pz + one(X, dx) * py * pz + px * one(Y, dy) * pz + px * py * one(Z, dz))
+
+
+def manufactured(n, k0, order):
+    """The separable test problem of Sec. 5.1 on the collocated grid of the unit cube (nodes j h,
+    h = 1/(n-1)), as inputs for helm_build_rhs_fields and helm_closure_rhs (numpy, complex128).
+
+    Returns dict(u = exact solution on the grid, k2 = k0^2 everywhere, fields = the right-hand side fields
+    of the scheme order (order 4: f on the padded grid; order 6: f, lap f, pure and mixed fourth-derivative
+    sums, f_x, f_y, f_z), faces = f_n, f_nnn, lap_T f_n on the six faces in the closure's layout)."""
+    h = 1.0 / (n - 1)
+    node = np.arange(n) * h
+    ext = np.arange(-1, n + 1) * h
+    Z, Y, X = np.meshgrid(node, node, node, indexing="ij")
+    u = _phi(X, k0, 0) * _phi(Y, k0, 0) * _phi(Z, k0, 0)
+    F = lambda a, b, c, P=(X, Y, Z): _f_deriv(P[0], P[1], P[2], k0, a, b, c)
+    if order == 4:
+        Zp, Yp, Xp = np.meshgrid(ext, ext, ext, indexing="ij")
+        fields = _f_deriv(Xp, Yp, Zp, k0, 0, 0, 0)
+    else:
+        fields = np.stack([F(0, 0, 0), F(2, 0, 0) + F(0, 2, 0) + F(0, 0, 2),
+                           F(4, 0, 0) + F(0, 4, 0) + F(0, 0, 4), F(2, 2, 0) + F(2, 0, 2) + F(0, 2, 2),
+                           F(1, 0, 0), F(0, 1, 0), F(0, 0, 1)])
+    faces = []
+    for axis in range(3):
+        # tangential axes in array order and their extents (ghost columns of earlier directions included)
+        ta, tb = (2, 1) if axis == 0 else ((2, 0) if axis == 1 else (1, 0))
+        ca = ext if ta < axis else node
+        cb = ext if tb < axis else node
+        A, B = np.meshgrid(ca, cb, indexing="ij")
+        for side in (0, 1):
+            coord = [None, None, None]
+            coord[axis] = np.full_like(A, 0.0 if side == 0 else 1.0)
+            coord[ta], coord[tb] = A, B
+            P = tuple(coord)
+            d = lambda k, t2=None: tuple((k if q == axis else (2 if q == t2 else 0)) for q in range(3))
+            fn = F(*d(1), P=P)
+            fnnn = F(*d(3), P=P)
+            lt = F(*d(1, ta), P=P) + F(*d(1, tb), P=P)
+            faces.extend([fn.ravel(), fnnn.ravel(), lt.ravel()])
+    return dict(u=u, k2=np.full(u.shape, k0 * k0, dtype=np.complex128), fields=np.ascontiguousarray(fields),
+                faces=np.concatenate(faces), h=h)

@@ -220,3 +220,90 @@ def test_set_closure_rejects_what_it_does_not_build():
     with pytest.raises(HelmError) as e:
         S7.set_closure(HELM_CLOSURE_HIGH_ORDER)
     assert e.value.code == 10
+
+
+# ---- the paper's high-order tables through the GPU path ----------------------------------------------
+K0_PAPER = math.sqrt(439.2)
+
+
+def _golden_high_order():
+    import os
+    rows = []
+    with open(os.path.join(os.path.dirname(__file__), "golden", "high_order_table.txt")) as fh:
+        for line in fh:
+            if line.strip() and not line.startswith("#"):
+                order, n, me, l2, n0 = line.split()
+                rows.append((int(order), int(n), me, float(l2), int(n0)))
+    return rows
+
+
+def _printed_half_unit(text):
+    mant, _, exp = text.lower().partition("e")
+    decimals = len(mant.split(".")[1]) if "." in mant else 0
+    return 0.5 * 10.0 ** (-decimals + (int(exp) if exp else 0))
+
+
+def _gpu_manufactured(order, N, **kw):
+    from paper_2602_07711_gb300 import HELM_CLOSURE_HIGH_ORDER, media
+    d = media.manufactured(N, K0_PAPER, order)
+    S = Solver((N, N, N), d["k2"], K0_PAPER, order=order, staggered=False, **kw)
+    S.set_closure(HELM_CLOSURE_HIGH_ORDER)
+    F = S.closure_rhs(_dev(d["faces"]), S.build_rhs_fields(_dev(d["fields"])))
+    return S, F, d
+
+
+@pytest.mark.parametrize("order", [4, 6])
+def test_closure_rhs_matches_oracle(order):
+    """F - A(G_f) of the high-order closure, built on the GPU from the analytic fields and face data."""
+    from oracle import manufactured as mf
+    from oracle.closure import pad_ghost_ho
+    from oracle.rhs import rhs4_padded, rhs6
+    N = 20
+    S, F, d = _gpu_manufactured(order, N)
+    g = Grid(N, N, N, staggered=False)
+    X, Y, Z = g.mesh()
+    k2 = np.full(g.shape, K0_PAPER ** 2, complex)
+    zero = (np.zeros(g.shape, complex),) * 3
+    op = Operator(g, k2, K0_PAPER, order, rule="collocated_ho", dk2=zero, lapk2=np.zeros(g.shape, complex))
+    if order == 4:
+        ax = np.arange(-1, N + 1) * g.h[0]
+        Zp, Yp, Xp = np.meshgrid(ax, ax, ax, indexing="ij")
+        Fo = rhs4_padded(mf.f_exact(Xp, Yp, Zp, K0_PAPER), g.h)
+    else:
+        f, lapf, s4, mix, df = mf.rhs6_fields(X, Y, Z, K0_PAPER)
+        Fo = rhs6(f, lapf, s4, mix, df, k2, zero, g.h)
+    ghost_f = pad_ghost_ho(np.zeros(g.shape, complex), K0_PAPER, g.h,
+                           fdiff=lambda X, Y, Z, dd: mf.f_exact(X, Y, Z, K0_PAPER, *dd))
+    ref = Fo - op.apply_padded(ghost_f)
+    assert S.closure_face_count() == d["faces"].size
+    assert _rel(F.cpu().numpy(), ref) < 1e-10
+
+
+@pytest.mark.parametrize("row", [r for r in _golden_high_order() if r[1] in (50, 64, 100)],
+                         ids=lambda r: f"o{r[0]}n{r[1]}")
+def test_paper_high_order_tables_on_the_gpu(row):
+    """Tables tab:fourth_order_results / tab:sixth_order_results reproduced by the GPU path: collocated
+    grid, high-order closure, EigT3-preconditioned GMRES(20) to rel-res 1e-10 (complex64 Krylov cycles
+    restarted from the double-float residual).  Same bounds as the oracle's pin: L2-err within 2% of the
+    printed value, max-err within 5% or the printed rounding."""
+    order, N, me_text, l2_paper, _ = row
+    S, F, d = _gpu_manufactured(order, N, precision=HELM_PREC_FP32, restart=20, rtol=1e-10, max_iter=400)
+    x, info = S.solve(F)
+    assert info.status == 0 and info.relres_true <= 1e-10
+    U, u = x.cpu().numpy(), d["u"]
+    l2 = np.linalg.norm(U - u) / np.linalg.norm(u)
+    me = np.abs(U - u).max()
+    me_paper = float(me_text)
+    assert abs(l2 - l2_paper) <= 0.02 * l2_paper, (l2, l2_paper)
+    assert abs(me - me_paper) <= max(0.05 * me_paper, _printed_half_unit(me_text)), (me, me_paper)
+
+
+def test_batches_reject_the_high_order_closure():
+    from paper_2602_07711_gb300 import HelmError, solve_batched
+    n = 16
+    g, k2, k0 = _medium((n, n, n), (1.0, 1.0, 1.0))
+    S = _ho_solver((n, n, n), (1.0, 1.0, 1.0), 4, k2, k0)
+    b = _dev(_rand((1,) + g.shape, 31))
+    with pytest.raises(HelmError) as e:
+        solve_batched([S], [b])
+    assert e.value.code == 10
