@@ -44,11 +44,12 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--e2e", type=int, default=1)
     p.add_argument("--max-iter", type=int, default=300)
-    p.add_argument("--workload", default="n256", choices=["n256", "batched", "pfft", "learned", "scatter"],
+    p.add_argument("--workload", default="n256", choices=["n256", "batched", "pfft", "learned", "scatter", "tables"],
                    help="n256: the headline solve; batched: 64 uneven problems x 4 right-hand sides in one "
                         "batched call; pfft: 512^3 layered medium, PFFT vs EigT; learned: 384^3 high-contrast "
                         "medium, learned correction vs plain EigT; scatter: the single-inclusion scattering "
-                        "problem of Sec. 5.2 at 100^3, 200^3, 400^3")
+                        "problem of Sec. 5.2 at 100^3, 200^3, 400^3; tables: the manufactured problem of "
+                        "Sec. 5.1 (collocated grid, high-order closure) at 50^3, 100^3, 200^3, orders 4 and 6")
     p.add_argument("--problems", type=int, default=64, help="batched workload: number of problems")
     p.add_argument("--autotune", type=int, default=0,
                    help="time the kernel variants on the grid before the run (default: the measured defaults)")
@@ -626,6 +627,62 @@ def run_scatter(args, rank, world, local):
         print(json.dumps(line), flush=True)
 
 
+# Tables tab:fourth_order_results / tab:sixth_order_results (Sec. 5.1): printed (max-err, L2-err, EigT3 N0,
+# EigT3 T_P seconds on one M3 Max core) for the grids timed here
+PAPER_TABLES = {(4, 50): (0.02, 5.25e-4, 8, 0.31), (4, 100): (1.25e-3, 3.12e-5, 5, 1.82),
+                (4, 200): (7.68e-5, 1.91e-6, 4, 17.6), (6, 50): (2.57e-4, 7.06e-6, 8, 0.26),
+                (6, 100): (3.71e-6, 9.97e-8, 5, 2.06), (6, 200): (5.63e-8, 1.49e-9, 4, 19.3)}
+
+
+def run_tables(args, rank, world, local):
+    """The manufactured test problem of Sec. 5.1 (k0^2 = 439.2, collocated grid, high-order closure) at
+    50^3, 100^3 and 200^3 for orders 4 and 6: EigT3 with FGMRES(20), TF32 transforms, to rel-res 1e-10 on the
+    FP64 true residual; errors against the exact solution beside the paper's printed values."""
+    import numpy as np
+    import torch
+
+    from paper_2602_07711_gb300 import HELM_CLOSURE_HIGH_ORDER, helm, media
+    torch.cuda.set_device(local)
+    k0 = math.sqrt(439.2)
+    out = {}
+    for (order, n), (me_p, l2_p, n0_p, tp_p) in PAPER_TABLES.items():
+        d = media.manufactured(n, k0, order)
+        S = helm.Solver((n, n, n), d["k2"], k0, order=order, precision=1, flexible=True, restart=20,
+                        max_iter=args.max_iter, rtol=1e-10, staggered=False)
+        S.set_closure(HELM_CLOSURE_HIGH_ORDER)
+        F = S.closure_rhs(torch.from_numpy(d["faces"]).cuda(), S.build_rhs_fields(torch.from_numpy(d["fields"]).cuda()))
+        x = torch.zeros_like(F)
+        S.solve(F, x0=x, check=False)
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        steps = max(1, args.steps)
+        torch.cuda.synchronize()
+        ev0.record()
+        for _ in range(steps):
+            x.zero_()
+            _, info = S.solve(F, x0=x, check=False)
+        ev1.record()
+        torch.cuda.synchronize()
+        dt = ev0.elapsed_time(ev1) / 1e3 / steps
+        U, u = x.cpu().numpy(), d["u"]
+        out["order%d-n%d" % (order, n)] = {
+            "time_to_rtol_s": dt, "iterations": info.iterations, "relres_true": info.relres_true,
+            "status": info.status, "l2_err": float(np.linalg.norm(U - u) / np.linalg.norm(u)),
+            "max_err": float(np.abs(U - u).max()), "paper": {"max_err": me_p, "l2_err": l2_p, "N0": n0_p,
+                                                              "T_P_s": tp_p}}
+        S.close()
+        torch.cuda.empty_cache()
+    if rank == 0:
+        r = out["order6-n200"]
+        v = 200 ** 3 * r["iterations"] / r["time_to_rtol_s"] / 1e6 * world
+        line = _base_line(args, world, v, r["time_to_rtol_s"] * args.steps, "manufactured-sec5.1-collocated",
+                          {"config": {"sizes": [50, 100, 200], "orders": [4, 6], "precond": "EigT3",
+                                      "closure": "high-order", "precision": "tf32", "krylov": "FGMRES(20)",
+                                      "rtol": 1e-10},
+                           "runs": out, "roofline": None, "cpu_baseline": None, "e2e": None})
+        print(json.dumps(line), flush=True)
+
+
 def run_learned(args, rank, world, local):
     """384^3, order 6, 8 points per wavelength, k^2/k0^2 in [0.5,1.8] (8 layers + 5 spheres): the U-Net is
     trained on the GPU on pairs from 96^3 solves of the same family, then FGMRES(30)+EigT with and without it."""
@@ -671,6 +728,8 @@ def main():
         run_pfft(args, rank, world, local)
     elif args.workload == "scatter":
         run_scatter(args, rank, world, local)
+    elif args.workload == "tables":
+        run_tables(args, rank, world, local)
     else:
         run_learned(args, rank, world, local)
     if world > 1:
