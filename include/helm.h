@@ -131,7 +131,9 @@ enum { HELM_CLOSURE_THREE_POINT = 0, HELM_CLOSURE_HIGH_ORDER = 1 };
  *     helm_build_rhs does not form.
  * Each matvec first copies its operand into a padded array and fills the ghosts (seven small launches).
  * Memory: three padded copies ((N_x+2)(N_y+2)(N_z+2) points as complex64, complex128 and double-float)
- * and two scratch faces, allocated here and freed by helm_destroy or by HELM_CLOSURE_THREE_POINT.
+ * and two scratch faces, allocated here and freed by helm_destroy or by HELM_CLOSURE_THREE_POINT.  The
+ * scratch is shared by every operator call of the context: issue them on one stream (or order them), and
+ * do not put the context in a batch (HELM_ERR_UNSUPPORTED there).
  * Errors: HELM_ERR_ARG (bad value), HELM_ERR_UNSUPPORTED (staggered grid, or an N below 8),
  * HELM_ERR_NOMEM. */
 helm_status helm_set_closure(helm_ctx* ctx, int closure);

@@ -228,7 +228,7 @@ helm_status fill(helm_ctx* c, const M* U, M* P, const double2* faces, cudaStream
     } else {
         HELM_CUDA_TRY(cudaMemsetAsync(P, 0, (size_t)(c->nx + 2) * (c->ny + 2) * (c->nz + 2) * sizeof(M), s));
     }
-    const Wts W = make_weights();
+    static const Wts W = make_weights();   // the same for every grid (weights times 1/h^2 per face)
     long long foff = 0;
     for (int axis = 0; axis < 3; ++axis) {
         const Face f = make_face(c, axis);
