@@ -236,8 +236,18 @@ def oracle_sample(n, order, m, iters=1):
     t = time.perf_counter()
     _, info = gmres(A, e.apply_Minv, F, m=m, rtol=1e-30, max_it=iters)
     dt = time.perf_counter() - t
-    cores = os.cpu_count()
-    return n ** 3 * info["iterations"] / dt / 1e6, dt, cores
+    return n ** 3 * info["iterations"] / dt / 1e6, dt, blas_threads()
+
+
+def blas_threads():
+    """Host threads the oracle's BLAS uses: the thread-count variables if set, else every core (the
+    element-wise NumPy work is single-threaded either way)."""
+    cores = os.cpu_count() or 1
+    for var in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+        v = os.environ.get(var, "")
+        if v.strip().isdigit() and int(v) > 0:
+            return min(cores, int(v))
+    return cores
 
 
 def run_reference(args, rank, world):
