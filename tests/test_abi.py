@@ -71,3 +71,12 @@ def test_collocated_grid_rejects_the_sine_preconditioners_without_gpu_work(libpa
         assert L.helm_setup(ctypes.byref(g), k2.ctypes.data, 1.0, None, ctypes.byref(o), None,
                             ctypes.byref(ctx)) == 10
         assert not ctx.value
+
+
+def test_closure_entry_points_reject_null_contexts_without_gpu_work(libpath):
+    from paper_2602_07711_gb300 import helm
+    L = helm.lib()
+    assert L.helm_set_closure(None, helm.HELM_CLOSURE_HIGH_ORDER) == 1
+    assert L.helm_closure_face_count(None) == 0
+    assert L.helm_build_rhs_fields(None, None, None, None) == 1
+    assert L.helm_closure_rhs(None, None, None, None, None) == 1
