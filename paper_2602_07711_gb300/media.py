@@ -1,7 +1,7 @@
 """Seeded synthetic workloads (inputs only: none of the solver's arithmetic lives here).
 
-Every workload is a scattering problem on the unit cube with a staggered grid (nodes h/2 + j h,
-h = 1/n, Sec. 5.2): a medium k^2(x), a background wavenumber k0, an incident plane wave
+Every workload but the last is a scattering problem on the unit cube with a staggered grid (nodes
+h/2 + j h, h = 1/n, Sec. 5.2): a medium k^2(x), a background wavenumber k0, an incident plane wave
 u_inc = exp(i k0 d.x) and the right-hand side f = -(k^2 - k0^2) u_inc (the form of Sec. 5.2).
 The generators return complex128 arrays indexed [z, y, x] (x fastest), built with torch in float64
 on the requested device so that the same numbers serve the CPU oracle and the GPU library.
@@ -13,6 +13,8 @@ Workloads (sizes and distributions of the paper's scattering tests):
   sphere           the single spherical inclusion of Sec. 5.2 (k^2 = 1050 + 2.26i inside r = 0.1 at
                    (0.5, 0.5, 0.7), 439.2 outside), d = +z
   layered          horizontal layers with k^2/k0^2 ~ U[lo, hi] plus spherical inclusions
+  manufactured     the separable test solution of Sec. 5.1 on the collocated grid (numpy, analytic): the
+                   exact u, the scheme's right-hand side fields and the closure's face data
 """
 import math
 
