@@ -21,6 +21,7 @@ from oracle.operators import Operator, derived_k2_fields
 from oracle.rhs import rhs4_sampled, rhs6_sampled
 from oracle.tridiag import thomas
 from paper_2602_07711_gb300 import HELM_PREC_FP32, HELM_PREC_TF32, Solver
+from paper_tables import high_order_rows, printed_half_unit
 
 
 def _dev(a, dtype=torch.complex128):
@@ -226,23 +227,6 @@ def test_set_closure_rejects_what_it_does_not_build():
 K0_PAPER = math.sqrt(439.2)
 
 
-def _golden_high_order():
-    import os
-    rows = []
-    with open(os.path.join(os.path.dirname(__file__), "golden", "high_order_table.txt")) as fh:
-        for line in fh:
-            if line.strip() and not line.startswith("#"):
-                order, n, me, l2, n0 = line.split()
-                rows.append((int(order), int(n), me, float(l2), int(n0)))
-    return rows
-
-
-def _printed_half_unit(text):
-    mant, _, exp = text.lower().partition("e")
-    decimals = len(mant.split(".")[1]) if "." in mant else 0
-    return 0.5 * 10.0 ** (-decimals + (int(exp) if exp else 0))
-
-
 def _gpu_manufactured(order, N, **kw):
     from paper_2602_07711_gb300 import HELM_CLOSURE_HIGH_ORDER, media
     d = media.manufactured(N, K0_PAPER, order)
@@ -279,7 +263,7 @@ def test_closure_rhs_matches_oracle(order):
     assert _rel(F.cpu().numpy(), ref) < 1e-10
 
 
-@pytest.mark.parametrize("row", [r for r in _golden_high_order() if r[1] in (50, 64, 100, 200)],
+@pytest.mark.parametrize("row", [r for r in high_order_rows() if r[1] in (50, 64, 100, 200)],
                          ids=lambda r: f"o{r[0]}n{r[1]}")
 def test_paper_high_order_tables_on_the_gpu(row):
     """Tables tab:fourth_order_results / tab:sixth_order_results reproduced by the GPU path: collocated
@@ -297,7 +281,7 @@ def test_paper_high_order_tables_on_the_gpu(row):
     me = np.abs(U - u).max()
     me_paper = float(me_text)
     assert abs(l2 - l2_paper) <= 0.02 * l2_paper, (l2, l2_paper)
-    assert abs(me - me_paper) <= max(0.05 * me_paper, _printed_half_unit(me_text)), (me, me_paper)
+    assert abs(me - me_paper) <= max(0.05 * me_paper, printed_half_unit(me_text)), (me, me_paper)
 
 
 def test_batches_reject_the_high_order_closure():

@@ -22,6 +22,7 @@ from oracle.operators import Operator, apply_A4, apply_A6, derived_k2_fields, pa
 from oracle.pfft import PFFT
 from oracle.rhs import f_derivative_fields, rhs4_padded, rhs6, rhs6_sampled
 from oracle.tridiag import thomas
+from paper_tables import high_order_rows, printed_half_unit
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 K0_PAPER = math.sqrt(439.2)
@@ -359,24 +360,7 @@ def test_closure_keeps_the_scheme_order(order):
     assert math.log2(errs[0] / errs[1]) > order - 0.2, errs
 
 
-def _golden_high_order():
-    rows = []
-    with open(os.path.join(GOLDEN, "high_order_table.txt")) as fh:
-        for line in fh:
-            if line.strip() and not line.startswith("#"):
-                order, n, me, l2, n0 = line.split()
-                rows.append((int(order), int(n), me, float(l2), int(n0)))
-    return rows
-
-
-def _printed_half_unit(text):
-    """Half a unit in the last printed digit of a table entry ('0.02' -> 0.005, '7.64e-03' -> 5e-6)."""
-    mant, _, exp = text.lower().partition("e")
-    decimals = len(mant.split(".")[1]) if "." in mant else 0
-    return 0.5 * 10.0 ** (-decimals + (int(exp) if exp else 0))
-
-
-@pytest.mark.parametrize("row", [r for r in _golden_high_order() if r[1] <= 100], ids=lambda r: f"o{r[0]}n{r[1]}")
+@pytest.mark.parametrize("row", [r for r in high_order_rows() if r[1] <= 100], ids=lambda r: f"o{r[0]}n{r[1]}")
 def test_paper_high_order_errors_and_iterations(row):
     """Tables tab:fourth_order_results / tab:sixth_order_results: the compact schemes with the high-order
     closure, EigT3-preconditioned GMRES(20) to rel-res 1e-10 from x0 = 0."""
@@ -396,7 +380,7 @@ def test_paper_high_order_errors_and_iterations(row):
     # the closure is our reading: the L2 error (a volume average) must agree to 2%, the pointwise maximum,
     # which sits next to the boundary, to 5% or the printed rounding
     assert abs(l2 - l2_paper) <= 0.02 * l2_paper, (l2, l2_paper)
-    assert abs(me - me_paper) <= max(0.05 * me_paper, _printed_half_unit(me_text)), (me, me_paper)
+    assert abs(me - me_paper) <= max(0.05 * me_paper, printed_half_unit(me_text)), (me, me_paper)
     # N0: the paper counts MATLAB's iterations, we count Arnoldi steps until the true residual is 1e-10
     assert n0_paper <= info["iterations"] <= n0_paper + 5, (info["iterations"], n0_paper)
 
