@@ -442,10 +442,10 @@ def _golden_scatter():
     return rows
 
 
-@pytest.mark.parametrize("row", [r for r in _golden_scatter() if r[0] <= 100])
+@pytest.mark.parametrize("row", [r for r in _golden_scatter() if r[0] <= 127])
 def test_paper_scattering_iterations(row):
     """The oracle's sixth-order GMRES(20) + EigT2 on the Sec. 5.2 inclusion reaches rel-res 1e-8 in the
-    printed number of inner iterations (the larger grids of the table take minutes on a CPU)."""
+    printed number of inner iterations at 100^3 and 127^3 (the larger grids take minutes on a CPU)."""
     N, n0_paper = row
     g = Grid(N, N, N, staggered=True)
     X, Y, Z = g.mesh()
