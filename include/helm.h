@@ -16,7 +16,10 @@
  *     before the GPU work finishes, except helm_setup and helm_gmres_solve, which synchronise `stream`.
  *   - Errors are returned as helm_status; the library never aborts or traps.  Device-side loops have
  *     iteration caps and report through a status word, read back by the synchronising calls.
- *   - A context must not be used from two host threads at once.  There is no global mutable state.
+ *   - A context must not be used from two host threads at once.  Process-wide state is limited to: the
+ *     launch-shape cache of helm_autotune (per grid size and order, guarded by a mutex), the per-thread text
+ *     of helm_last_error, and the static scratch array of helm_residual_noalloc (one per GPU, shared by
+ *     every call, so that overlapping calls of that entry point race).  Everything else lives in a context.
  */
 #ifndef HELM_H
 #define HELM_H
@@ -253,15 +256,20 @@ helm_status helm_residual(helm_ctx* ctx, const void* b, const void* x, void* r, 
                           void* stream);
 
 /* helm_residual_noalloc - the same residual and norms as helm_residual, for callers that cannot allocate
- * device memory (for instance while a CUDA graph is being captured, or inside a framework whose memory
- * pool is frozen after warm-up).  The paper has no counterpart: this is a library convenience.
+ * device memory while they run: an application that has handed the whole device to its own memory pool
+ * after warm-up, or a runtime that forbids cudaMalloc/cudaFree (which synchronise the device) between its
+ * steps.  helm_residual allocates its double-float copies of b and x on first use; this entry point keeps
+ * them in a fixed static device array instead.  The paper has no counterpart: this is a library
+ * convenience.
  *   b, x   complex128 device buffers;  r  complex64 device output (required);  nrm2, nrmi as above.
- * Allocates nothing: its scratch (double-float copies of b and x, per-CTA partial sums) is one static
- * device array of 65 MiB + 256 B that every GPU loading the library holds until exit.  Limit: at most
- * 2^21 = 2,097,152 grid points (128^3) and 65536 residual CTAs; larger problems return HELM_ERR_ARG.
- * The first call on a device looks up the array's device address; make that first call before any
- * stream capture.  All calls share the array (each call rewrites every part it reads), so calls that
- * overlap on the GPU race.  Synchronises `stream`. */
+ * Allocates nothing and calls no allocating library routine.  Its scratch (double-float copies of b and x,
+ * per-CTA partial sums, two result words) is one static device array of 65 MiB + 256 B that every GPU
+ * loading the library holds until the process exits.  Limit: at most 2^21 = 2,097,152 grid points (128^3)
+ * and 65536 residual CTAs; larger problems return HELM_ERR_ARG.  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress, with that device current).  Every call shares the array
+ * and rewrites each part of it that it reads before reading it, so calls whose GPU work overlaps (two
+ * streams, two host threads) race and must be serialised by the caller.  Like helm_residual it copies the
+ * two norms to host memory and synchronises `stream` before returning. */
 helm_status helm_residual_noalloc(helm_ctx* ctx, const void* b, const void* x, void* r, double* nrm2,
                                   double* nrmi, void* stream);
 
@@ -340,6 +348,15 @@ helm_status helm_net_stats(helm_net* net, double* host6);
  * (NULL detaches).  The context does not own the net.  Requires a flexible context and even nx, ny, nz
  * (else HELM_ERR_ARG); sizes the net's workspace for one field of the grid. */
 helm_status helm_attach_net(helm_ctx* ctx, helm_net* net);
+
+/* helm_set_wait_limit - bound, in polls, of every mbarrier wait of this context's tensor-core transform
+ * passes and of its TMA matvec (0 restores the default, 2^20).  A wait that runs out raises a device
+ * status bit; the CTA then skips its remaining work, waits (under a separate fixed bound) for the TMA loads
+ * and MMAs it still has in flight, frees its tensor memory and exits, and the next synchronising call
+ * (helm_gmres_solve, helm_gmres_solve_batched, helm_batch_run) returns HELM_ERR_ITER_LIMIT; the context
+ * stays usable.  A diagnosis and test hook: a limit of a few polls makes the waits run out on purpose.
+ * The paper has no counterpart.  Errors: HELM_ERR_ARG (NULL context, negative limit). */
+helm_status helm_set_wait_limit(helm_ctx* ctx, long long polls);
 
 /* helm_destroy - free the context and its device workspace (NULL is a no-op). */
 void helm_destroy(helm_ctx* ctx);

@@ -1,8 +1,9 @@
 // helm_residual_noalloc: the true residual r = b - A x (double-float arithmetic) for callers that must
-// not allocate device memory, e.g. code that runs while a CUDA graph is being captured, or inside a
-// framework whose memory pool is frozen after warm-up and forbids cudaMalloc/cudaFree mid-run.
-// The helm_residual entry point keeps its double-float copies of b and x and its per-CTA partial sums in
-// workspace it allocates on first use; this variant keeps them in one file-scope device array instead.
+// not allocate device memory while they run, e.g. an application whose memory pool owns the whole device
+// after warm-up, or a runtime that forbids cudaMalloc/cudaFree (both synchronise the device) between its
+// steps.  The helm_residual entry point keeps its double-float copies of b and x and its per-CTA partial
+// sums in workspace it allocates on first use; this variant keeps them in one file-scope device array
+// instead.  Like helm_residual it copies the two norms to host memory and synchronises the stream.
 #include "common.cuh"
 #include "dfloat.cuh"
 
