@@ -247,6 +247,12 @@ helm_status helm_closure_rhs(helm_ctx* c, const void* faces, const void* F_in, v
     return closure_rhs(c, (const double2*)faces, (const double2*)F_in, (double2*)F_out, (cudaStream_t)stream);
 }
 
+helm_status helm_set_wait_limit(helm_ctx* c, long long polls) {
+    if (!c || polls < 0) return HELM_ERR_ARG;
+    c->wait_limit = polls == 0 ? (1LL << 20) : polls;
+    return HELM_OK;
+}
+
 void helm_destroy(helm_ctx* c) { free_ctx(c); }
 
 }  // extern "C"

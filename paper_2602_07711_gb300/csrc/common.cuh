@@ -149,6 +149,7 @@ struct helm_ctx {
     int tune_dots = 2;                      // inner-product kernel variant (helm_autotune; 2 measured best)
     cudaStream_t last_stream = nullptr;
     Prof* prof = nullptr;
+    long long wait_limit = 1LL << 20;       // polls of each bounded mbarrier wait (helm_set_wait_limit)
 };
 
 // ---- launchers shared across translation units -----------------------------------------------

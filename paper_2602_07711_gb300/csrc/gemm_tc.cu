@@ -17,8 +17,10 @@
 //   warp 1      allocates tensor memory; one lane issues tcgen05.mma (M=128, N=128, K=8) and commits
 //               each stage back to the producer
 //   warps 2-5   epilogue: tcgen05.ld of the accumulator lanes they own, scale, vectorised stores
-// Every mbarrier wait is bounded; on expiry the CTA raises HELM_DEV_WAIT, skips its remaining work,
-// and still frees its tensor memory.  No cluster multicast is used.
+// Every mbarrier wait is bounded by the context's wait limit (a kernel argument); on expiry the CTA raises
+// HELM_DEV_WAIT and skips its remaining work.  Before it frees its tensor memory and exits, it drains what
+// it still has in flight under a separate fixed bound: the producer waits for the TMA loads it issued, the
+// MMA thread commits once more and waits for its MMAs.  No cluster multicast is used.
 #include "common.cuh"
 #include <cuda.h>
 #include <cudaTypedefs.h>
@@ -31,7 +33,7 @@ constexpr int XSTAGES = 3, YSTAGES = 2;
 constexpr int XEPI_LD = 20;                                  // x-pass staging row: 16 floats + 4 pad
 constexpr int XEPI_BYTES = 4 * 32 * XEPI_LD * 4;             // four epilogue warps x 32 rows
 constexpr int YEPI_LD = 36;                                  // y-pass staging row: 32 floats + 4 pad
-constexpr long WAIT_LIMIT = 1L << 20;
+constexpr long DRAIN_LIMIT = 1L << 22;          // bound of the drain waits after an expired wait
 
 struct TcState {
     PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
@@ -55,8 +57,8 @@ __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
 __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-    for (long it = 0; it < WAIT_LIMIT; ++it) {
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, long limit) {
+    for (long it = 0; it < limit; ++it) {
         uint32_t ok;
         asm volatile(
             "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
@@ -118,12 +120,26 @@ __device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::aft
         : "r"(taddr))
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
+// Drain after an expired wait: the producer thread waits, under the fixed drain bound, for the TMA loads
+// of the last `ns` pipeline iterations it issued (one per stage, so every barrier phase is unambiguous);
+// the MMA thread commits once more and waits for that commit, which completes after all its MMAs.
+__device__ __forceinline__ void drain_tma(const uint64_t* full, int ns, long issued) {
+    for (long it = issued > ns ? issued - ns : 0; it < issued; ++it)
+        mbar_wait(su32(&full[it % ns]), (uint32_t)((it / ns) & 1), DRAIN_LIMIT);
+}
+__device__ __forceinline__ void drain_mma(uint64_t* bar) {
+    mma_commit(su32(bar));
+    mbar_wait(su32(bar), 0, DRAIN_LIMIT);
+}
+
 // ---- x-pass: Out[M][N2] = alpha * A[M][K2] B[N2][K2]^T -------------------------------------------
 __global__ void __launch_bounds__(192, 1)
 xpass_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, float* __restrict__ out,
-                int M, int N2, int K2, float alpha, const double* __restrict__ alpha_dev, int aidx, unsigned* status) {
+                int M, int N2, int K2, float alpha, const double* __restrict__ alpha_dev, int aidx, unsigned* status,
+                long wlim) {
     extern __shared__ uint8_t dsm[];
-    __shared__ __align__(8) uint64_t full[XSTAGES], empty[XSTAGES], accf;
+    __shared__ __align__(8) uint64_t full[XSTAGES], empty[XSTAGES], accf, drainb;
+    __shared__ int fail_any;
     __shared__ uint32_t tslot;
     const uint32_t raw = su32(dsm);
     const uint32_t base = (raw + 1023u) & ~1023u;
@@ -133,6 +149,8 @@ xpass_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
     if (threadIdx.x == 0) {
         for (int s = 0; s < XSTAGES; ++s) { mbar_init(su32(&full[s]), 1); mbar_init(su32(&empty[s]), 1); }
         mbar_init(su32(&accf), 1);
+        mbar_init(su32(&drainb), 1);
+        fail_any = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 1) {
@@ -145,17 +163,19 @@ xpass_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
     fence_after();
     const uint32_t tmem = tslot;
     bool ok = true;
+    long issued = 0;   // pipeline iterations whose TMA loads the producer issued
     if (warp == 0) {
         if (lane == 0) {
             for (int kb = 0; kb < nk && ok; ++kb) {
                 const int s = kb % XSTAGES;
                 const uint32_t ph = (kb / XSTAGES) & 1;
-                if (kb >= XSTAGES) ok = mbar_wait(su32(&empty[s]), ph ^ 1);
+                if (kb >= XSTAGES) ok = mbar_wait(su32(&empty[s]), ph ^ 1, wlim);
                 if (!ok) break;
                 const uint32_t sa = base + s * 2 * TILE, sb = sa + TILE;
                 mbar_expect_tx(su32(&full[s]), 2 * TILE);
                 tma_2d(sa, &tmA, su32(&full[s]), kb * BK, m0);
                 tma_2d(sb, &tmB, su32(&full[s]), kb * BK, n0);
+                ++issued;
             }
         }
     } else if (warp == 1) {
@@ -164,7 +184,7 @@ xpass_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
             for (int kb = 0; kb < nk && ok; ++kb) {
                 const int s = kb % XSTAGES;
                 const uint32_t ph = (kb / XSTAGES) & 1;
-                ok = mbar_wait(su32(&full[s]), ph);
+                ok = mbar_wait(su32(&full[s]), ph, wlim);
                 if (!ok) break;
                 fence_after();
                 const uint32_t sa = base + s * 2 * TILE, sb = sa + TILE;
@@ -177,7 +197,7 @@ xpass_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
             mma_commit(su32(&accf));
         }
     } else {
-        ok = mbar_wait(su32(&accf), 0);
+        ok = mbar_wait(su32(&accf), 0, wlim);
         ok = __all_sync(0xffffffffu, ok);
         fence_after();
         const int q = warp & 3;
@@ -207,7 +227,15 @@ xpass_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
             }
         }
     }
-    if (!ok) atomicOr(status, (unsigned)HELM_DEV_WAIT);
+    if (!ok) {
+        atomicOr(status, (unsigned)HELM_DEV_WAIT);
+        fail_any = 1;
+    }
+    __syncthreads();
+    if (fail_any && lane == 0) {
+        if (warp == 0) drain_tma(full, XSTAGES, issued);
+        else if (warp == 1) drain_mma(&drainb);
+    }
     fence_before();
     __syncthreads();
     if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(BN) : "memory");
@@ -216,9 +244,10 @@ xpass_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
 // ---- y-pass: Out_l[ny][N2] = W Y_l, W = Wr + i Wi -------------------------------------------------
 __global__ void __launch_bounds__(192, 1)
 ypass_tc_kernel(const __grid_constant__ CUtensorMap tmW, const __grid_constant__ CUtensorMap tmY, float* __restrict__ out,
-                int ny, int N2, unsigned* status) {
+                int ny, int N2, unsigned* status, long wlim) {
     extern __shared__ uint8_t dsm[];
-    __shared__ __align__(8) uint64_t full[YSTAGES], empty[YSTAGES], accf;
+    __shared__ __align__(8) uint64_t full[YSTAGES], empty[YSTAGES], accf, drainb;
+    __shared__ int fail_any;
     __shared__ uint32_t tslot;
     const uint32_t raw = su32(dsm);
     const uint32_t base = (raw + 1023u) & ~1023u;
@@ -229,6 +258,8 @@ ypass_tc_kernel(const __grid_constant__ CUtensorMap tmW, const __grid_constant__
     if (threadIdx.x == 0) {
         for (int s = 0; s < YSTAGES; ++s) { mbar_init(su32(&full[s]), 1); mbar_init(su32(&empty[s]), 1); }
         mbar_init(su32(&accf), 1);
+        mbar_init(su32(&drainb), 1);
+        fail_any = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 1) {
@@ -241,12 +272,13 @@ ypass_tc_kernel(const __grid_constant__ CUtensorMap tmW, const __grid_constant__
     fence_after();
     const uint32_t tmem = tslot;
     bool ok = true;
+    long issued = 0;   // pipeline iterations whose TMA loads the producer issued
     if (warp == 0) {
         if (lane == 0) {
             for (int kb = 0; kb < nk && ok; ++kb) {
                 const int s = kb % YSTAGES;
                 const uint32_t ph = (kb / YSTAGES) & 1;
-                if (kb >= YSTAGES) ok = mbar_wait(su32(&empty[s]), ph ^ 1);
+                if (kb >= YSTAGES) ok = mbar_wait(su32(&empty[s]), ph ^ 1, wlim);
                 if (!ok) break;
                 const uint32_t sw = base + s * STAGE, sb = sw + 2 * TILE;
                 mbar_expect_tx(su32(&full[s]), STAGE);
@@ -254,6 +286,7 @@ ypass_tc_kernel(const __grid_constant__ CUtensorMap tmW, const __grid_constant__
                 tma_3d(sw + TILE, &tmW, su32(&full[s]), kb * BK, m0, 1);
 #pragma unroll
                 for (int b = 0; b < BN / 32; ++b) tma_3d(sb + b * 4096, &tmY, su32(&full[s]), n0 + 32 * b, kb * BK, l);
+                ++issued;
             }
         }
     } else if (warp == 1) {
@@ -262,7 +295,7 @@ ypass_tc_kernel(const __grid_constant__ CUtensorMap tmW, const __grid_constant__
             for (int kb = 0; kb < nk && ok; ++kb) {
                 const int s = kb % YSTAGES;
                 const uint32_t ph = (kb / YSTAGES) & 1;
-                ok = mbar_wait(su32(&full[s]), ph);
+                ok = mbar_wait(su32(&full[s]), ph, wlim);
                 if (!ok) break;
                 fence_after();
                 const uint32_t sw = base + s * STAGE, sb = sw + 2 * TILE;
@@ -279,7 +312,7 @@ ypass_tc_kernel(const __grid_constant__ CUtensorMap tmW, const __grid_constant__
             mma_commit(su32(&accf));
         }
     } else {
-        ok = mbar_wait(su32(&accf), 0);
+        ok = mbar_wait(su32(&accf), 0, wlim);
         ok = __all_sync(0xffffffffu, ok);
         fence_after();
         const int q = warp & 3;
@@ -321,7 +354,15 @@ ypass_tc_kernel(const __grid_constant__ CUtensorMap tmW, const __grid_constant__
             }
         }
     }
-    if (!ok) atomicOr(status, (unsigned)HELM_DEV_WAIT);
+    if (!ok) {
+        atomicOr(status, (unsigned)HELM_DEV_WAIT);
+        fail_any = 1;
+    }
+    __syncthreads();
+    if (fail_any && lane == 0) {
+        if (warp == 0) drain_tma(full, YSTAGES, issued);
+        else if (warp == 1) drain_mma(&drainb);
+    }
     fence_before();
     __syncthreads();
     if (warp == 1)
@@ -347,10 +388,11 @@ template <int BNT>
 __global__ void __launch_bounds__(192, 1)
 xpass_tc_pers_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                      float* __restrict__ out, int M, int N2, int K2, float alpha, const double* __restrict__ alpha_dev,
-                     int aidx, unsigned* status) {
+                     int aidx, unsigned* status, long wlim) {
     extern __shared__ uint8_t dsm[];
     constexpr int NS = PersX<BNT>::STAGES, BTILE = BNT * BK * 4, STAGE = TILE + BTILE;
-    __shared__ __align__(8) uint64_t full[NS], empty[NS], accf[2], acce[2];
+    __shared__ __align__(8) uint64_t full[NS], empty[NS], accf[2], acce[2], drainb;
+    __shared__ int fail_any;
     __shared__ uint32_t tslot;
     const uint32_t raw = su32(dsm);
     const uint32_t base = (raw + 1023u) & ~1023u;
@@ -361,6 +403,8 @@ xpass_tc_pers_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_const
     if (threadIdx.x == 0) {
         for (int s = 0; s < NS; ++s) { mbar_init(su32(&full[s]), 1); mbar_init(su32(&empty[s]), 1); }
         for (int b = 0; b < 2; ++b) { mbar_init(su32(&accf[b]), 1); mbar_init(su32(&acce[b]), 4); }
+        mbar_init(su32(&drainb), 1);
+        fail_any = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 1) {
@@ -373,6 +417,7 @@ xpass_tc_pers_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_const
     fence_after();
     const uint32_t tmem = tslot;
     bool ok = true;
+    long issued = 0;   // pipeline iterations whose TMA loads the producer issued
     if (warp == 0) {
         if (lane == 0) {
             long it = 0;
@@ -381,12 +426,13 @@ xpass_tc_pers_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_const
                 for (int kb = 0; kb < nk && ok; ++kb, ++it) {
                     const int s = (int)(it % NS);
                     const uint32_t ph = (uint32_t)((it / NS) & 1);
-                    if (it >= NS) ok = mbar_wait(su32(&empty[s]), ph ^ 1);
+                    if (it >= NS) ok = mbar_wait(su32(&empty[s]), ph ^ 1, wlim);
                     if (!ok) break;
                     const uint32_t sa = base + s * STAGE, sb = sa + TILE;
                     mbar_expect_tx(su32(&full[s]), STAGE);
                     tma_2d(sa, &tmA, su32(&full[s]), kb * BK, m0);
                     tma_2d(sb, &tmB, su32(&full[s]), kb * BK, n0);
+                    ++issued;
                 }
             }
         }
@@ -397,14 +443,14 @@ xpass_tc_pers_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_const
             int lt = 0;
             for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++lt) {
                 const int b = lt & 1;
-                if (lt >= 2) ok = mbar_wait(su32(&acce[b]), (uint32_t)(((lt >> 1) - 1) & 1));
+                if (lt >= 2) ok = mbar_wait(su32(&acce[b]), (uint32_t)(((lt >> 1) - 1) & 1), wlim);
                 if (!ok) break;
                 fence_after();
                 const uint32_t acc_t = tmem + (uint32_t)(b * BNT);
                 for (int kb = 0; kb < nk && ok; ++kb, ++it) {
                     const int s = (int)(it % NS);
                     const uint32_t ph = (uint32_t)((it / NS) & 1);
-                    ok = mbar_wait(su32(&full[s]), ph);
+                    ok = mbar_wait(su32(&full[s]), ph, wlim);
                     if (!ok) break;
                     fence_after();
                     const uint32_t sa = base + s * STAGE, sb = sa + TILE;
@@ -424,7 +470,7 @@ xpass_tc_pers_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_const
         for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++lt) {
             const int b = lt & 1;
             const int n0 = (t % ntn) * BNT, m0 = (t / ntn) * BM;
-            ok = __all_sync(0xffffffffu, mbar_wait(su32(&accf[b]), (uint32_t)((lt >> 1) & 1)));
+            ok = __all_sync(0xffffffffu, mbar_wait(su32(&accf[b]), (uint32_t)((lt >> 1) & 1), wlim));
             if (!ok) break;
             fence_after();
             // each thread holds one row of the accumulator; 16-column halves go through this warp's staging
@@ -467,7 +513,15 @@ xpass_tc_pers_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_const
             if (lane == 0) mbar_arrive(su32(&acce[b]));
         }
     }
-    if (!ok) atomicOr(status, (unsigned)HELM_DEV_WAIT);
+    if (!ok) {
+        atomicOr(status, (unsigned)HELM_DEV_WAIT);
+        fail_any = 1;
+    }
+    __syncthreads();
+    if (fail_any && lane == 0) {
+        if (warp == 0) drain_tma(full, NS, issued);
+        else if (warp == 1) drain_mma(&drainb);
+    }
     fence_before();
     __syncthreads();
     if (warp == 1)
@@ -484,10 +538,11 @@ constexpr size_t YP_SMEM = (size_t)YPS * 3 * TILE + 4 * 32 * YEPI_LD * 4 + 1024;
 
 __global__ void __launch_bounds__(192, 1)
 ypass_tc_pers_kernel(const __grid_constant__ CUtensorMap tmW, const __grid_constant__ CUtensorMap tmY,
-                     float* __restrict__ out, int ny, int N2, int nz, unsigned* status) {
+                     float* __restrict__ out, int ny, int N2, int nz, unsigned* status, long wlim) {
     extern __shared__ uint8_t dsm[];
     constexpr int STAGE = 3 * TILE;   // Wr tile, Wi tile, B tile (4 boxes of 32 K-rows x 128 bytes)
-    __shared__ __align__(8) uint64_t full[YPS], empty[YPS], accf[2], acce[2];
+    __shared__ __align__(8) uint64_t full[YPS], empty[YPS], accf[2], acce[2], drainb;
+    __shared__ int fail_any;
     __shared__ uint32_t tslot;
     const uint32_t raw = su32(dsm);
     const uint32_t base = (raw + 1023u) & ~1023u;
@@ -498,6 +553,8 @@ ypass_tc_pers_kernel(const __grid_constant__ CUtensorMap tmW, const __grid_const
     if (threadIdx.x == 0) {
         for (int s = 0; s < YPS; ++s) { mbar_init(su32(&full[s]), 1); mbar_init(su32(&empty[s]), 1); }
         for (int b = 0; b < 2; ++b) { mbar_init(su32(&accf[b]), 1); mbar_init(su32(&acce[b]), 4); }
+        mbar_init(su32(&drainb), 1);
+        fail_any = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 1) {
@@ -510,6 +567,7 @@ ypass_tc_pers_kernel(const __grid_constant__ CUtensorMap tmW, const __grid_const
     fence_after();
     const uint32_t tmem = tslot;
     bool ok = true;
+    long issued = 0;   // pipeline iterations whose TMA loads the producer issued
     if (warp == 0) {
         if (lane == 0) {
             long it = 0;
@@ -519,7 +577,7 @@ ypass_tc_pers_kernel(const __grid_constant__ CUtensorMap tmW, const __grid_const
                 for (int kb = 0; kb < nk && ok; ++kb, ++it) {
                     const int s = (int)(it % YPS);
                     const uint32_t ph = (uint32_t)((it / YPS) & 1);
-                    if (it >= YPS) ok = mbar_wait(su32(&empty[s]), ph ^ 1);
+                    if (it >= YPS) ok = mbar_wait(su32(&empty[s]), ph ^ 1, wlim);
                     if (!ok) break;
                     const uint32_t sw = base + s * STAGE, sb = sw + 2 * TILE;
                     mbar_expect_tx(su32(&full[s]), STAGE);
@@ -527,6 +585,7 @@ ypass_tc_pers_kernel(const __grid_constant__ CUtensorMap tmW, const __grid_const
                     tma_3d(sw + TILE, &tmW, su32(&full[s]), kb * BK, m0, 1);
 #pragma unroll
                     for (int q = 0; q < BN / 32; ++q) tma_3d(sb + q * 4096, &tmY, su32(&full[s]), n0 + 32 * q, kb * BK, l);
+                    ++issued;
                 }
             }
         }
@@ -537,14 +596,14 @@ ypass_tc_pers_kernel(const __grid_constant__ CUtensorMap tmW, const __grid_const
             int lt = 0;
             for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++lt) {
                 const int b = lt & 1;
-                if (lt >= 2) ok = mbar_wait(su32(&acce[b]), (uint32_t)(((lt >> 1) - 1) & 1));
+                if (lt >= 2) ok = mbar_wait(su32(&acce[b]), (uint32_t)(((lt >> 1) - 1) & 1), wlim);
                 if (!ok) break;
                 fence_after();
                 const uint32_t accP = tmem + (uint32_t)(b * 2 * BN), accQ = accP + BN;
                 for (int kb = 0; kb < nk && ok; ++kb, ++it) {
                     const int s = (int)(it % YPS);
                     const uint32_t ph = (uint32_t)((it / YPS) & 1);
-                    ok = mbar_wait(su32(&full[s]), ph);
+                    ok = mbar_wait(su32(&full[s]), ph, wlim);
                     if (!ok) break;
                     fence_after();
                     const uint32_t sw = base + s * STAGE, sb = sw + 2 * TILE;
@@ -569,7 +628,7 @@ ypass_tc_pers_kernel(const __grid_constant__ CUtensorMap tmW, const __grid_const
             const int b = lt & 1;
             const int mb = t % ntm, nb = (t / ntm) % ntn, l = t / (ntm * ntn);
             const int m0 = mb * BM, n0 = nb * BN;
-            ok = __all_sync(0xffffffffu, mbar_wait(su32(&accf[b]), (uint32_t)((lt >> 1) & 1)));
+            ok = __all_sync(0xffffffffu, mbar_wait(su32(&accf[b]), (uint32_t)((lt >> 1) & 1), wlim));
             if (!ok) break;
             fence_after();
             const int rbase = m0 + 32 * q;
@@ -609,7 +668,15 @@ ypass_tc_pers_kernel(const __grid_constant__ CUtensorMap tmW, const __grid_const
             if (lane == 0) mbar_arrive(su32(&acce[b]));
         }
     }
-    if (!ok) atomicOr(status, (unsigned)HELM_DEV_WAIT);
+    if (!ok) {
+        atomicOr(status, (unsigned)HELM_DEV_WAIT);
+        fail_any = 1;
+    }
+    __syncthreads();
+    if (fail_any && lane == 0) {
+        if (warp == 0) drain_tma(full, YPS, issued);
+        else if (warp == 1) drain_mma(&drainb);
+    }
     fence_before();
     __syncthreads();
     if (warp == 1)
@@ -759,16 +826,16 @@ helm_status tc_xpass(helm_ctx* c, int inverse, const float2* in, float2* out, fl
             const int ntiles = (N2 / 256) * (int)grid.y;
             const int pg = ntiles < g_sms ? ntiles : g_sms;
             xpass_tc_pers_kernel<256><<<pg, 192, PersX<256>::SMEM, s>>>(mapA, t->mapBx256[inverse], (float*)out, M, N2,
-                                                                         N2, alpha, alpha_dev, aidx, c->status_d);
+                                                                         N2, alpha, alpha_dev, aidx, c->status_d, (long)c->wait_limit);
         } else {
             const int ntiles = (int)(grid.x * grid.y);
             const int pg = ntiles < 2 * g_sms ? ntiles : 2 * g_sms;
             xpass_tc_pers_kernel<128><<<pg, 192, PersX<128>::SMEM, s>>>(mapA, t->mapBx[inverse], (float*)out, M, N2,
-                                                                         N2, alpha, alpha_dev, aidx, c->status_d);
+                                                                         N2, alpha, alpha_dev, aidx, c->status_d, (long)c->wait_limit);
         }
     } else {
         xpass_tc_kernel<<<grid, 192, xsmem(), s>>>(mapA, t->mapBx[inverse], (float*)out, M, N2, N2, alpha, alpha_dev,
-                                                    aidx, c->status_d);
+                                                    aidx, c->status_d, (long)c->wait_limit);
     }
     HELM_CUDA_TRY(cudaGetLastError());
     return HELM_OK;
@@ -787,9 +854,9 @@ helm_status tc_ypass(helm_ctx* c, int inverse, const float2* in, float2* out, cu
     if (c->tune_ypers && g_sms > 0) {
         const int ntiles = (int)(grid.x * grid.y * grid.z);
         const int pg = ntiles < g_sms ? ntiles : g_sms;
-        ypass_tc_pers_kernel<<<pg, 192, YP_SMEM, s>>>(t->mapWy[inverse], mapY, (float*)out, ny, N2, c->nz, c->status_d);
+        ypass_tc_pers_kernel<<<pg, 192, YP_SMEM, s>>>(t->mapWy[inverse], mapY, (float*)out, ny, N2, c->nz, c->status_d, (long)c->wait_limit);
     } else {
-        ypass_tc_kernel<<<grid, 192, ysmem(), s>>>(t->mapWy[inverse], mapY, (float*)out, ny, N2, c->status_d);
+        ypass_tc_kernel<<<grid, 192, ysmem(), s>>>(t->mapWy[inverse], mapY, (float*)out, ny, N2, c->status_d, (long)c->wait_limit);
     }
     HELM_CUDA_TRY(cudaGetLastError());
     return HELM_OK;

@@ -281,7 +281,7 @@ struct TLayout {
     static constexpr int BAR_OFF = FNS * STAGE;
     static constexpr int SMEM = BAR_OFF + FNS * 8 + 128;   // + alignment slack
 };
-constexpr long TWAIT_LIMIT = 1L << 22;
+constexpr long TDRAIN_LIMIT = 1L << 22;   // bound of the drain waits after an expired wait
 
 __device__ __forceinline__ uint32_t s32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 __device__ __forceinline__ void tbar_init(uint32_t bar) {
@@ -290,8 +290,8 @@ __device__ __forceinline__ void tbar_init(uint32_t bar) {
 __device__ __forceinline__ void tbar_expect(uint32_t bar, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
 }
-__device__ __forceinline__ bool tbar_wait(uint32_t bar, uint32_t parity) {
-    for (long it = 0; it < TWAIT_LIMIT; ++it) {
+__device__ __forceinline__ bool tbar_wait(uint32_t bar, uint32_t parity, long limit) {
+    for (long it = 0; it < limit; ++it) {
         uint32_t ok;
         asm volatile(
             "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
@@ -315,7 +315,7 @@ __global__ void __launch_bounds__(FNT, 4)
 stencil_tma_kernel(const __grid_constant__ CUtensorMap mU, const __grid_constant__ CUtensorMap mK,
                    const __grid_constant__ CUtensorMap mG, const __grid_constant__ CUtensorMap mGx,
                    const __grid_constant__ CUtensorMap mGy, const __grid_constant__ CUtensorMap mGz, FParams p,
-                   float2* __restrict__ Y, const double* __restrict__ sigma, int sidx, unsigned* status) {
+                   float2* __restrict__ Y, const double* __restrict__ sigma, int sidx, unsigned* status, long wlim) {
     typedef TLayout<ORDER> L;
     extern __shared__ unsigned char traw[];
     unsigned char* base = (unsigned char*)(((uintptr_t)traw + 127) & ~(uintptr_t)127);
@@ -350,14 +350,16 @@ stencil_tma_kernel(const __grid_constant__ CUtensorMap mU, const __grid_constant
         }
     };
     bool failed = false;
+    int r_fail = 0, r_last = 1;   // thread 0: relative index of its first unconfirmed plane, of its last issued one
     if (tid == 0) { issue(z0 - 1); issue(z0); }
 
     float2 cA = make_float2(0, 0), cX = cA, cY = cA, cZ = cA;
     float2 nA = cA, nX = cA, nY = cA, nZ = cA;
     for (int P = z0 - 1; P <= z1; ++P) {
         const int r = P - z0 + 1, sl = r & (FNS - 1);
-        if (!failed && !tbar_wait(sbase + L::BAR_OFF + 8 * sl, (r >> 2) & 1)) {
+        if (!failed && !tbar_wait(sbase + L::BAR_OFF + 8 * sl, (r >> 2) & 1, wlim)) {
             failed = true;
+            r_fail = r;
             if (tid == 0) atomicOr(status, HELM_DEV_WAIT);
         }
         float2* sU = reinterpret_cast<float2*>(base + sl * L::STAGE + L::U_OFF);
@@ -391,7 +393,10 @@ stencil_tma_kernel(const __grid_constant__ CUtensorMap mU, const __grid_constant
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // generic writes before later TMA writes
         __syncthreads();   // slot P prepared; every thread is done with plane P-1 (and the slot of P-2)
-        if (tid == 0 && P + 2 <= z1 && !failed) issue(P + 2);
+        if (tid == 0 && P + 2 <= z1 && !failed) {
+            issue(P + 2);
+            r_last = P + 2 - z0 + 1;
+        }
         float2 u[3][3];
         float2 kc, kf4 = make_float2(0, 0), kcs = kf4, dkx = kf4, dky = kf4;
 #pragma unroll
@@ -468,13 +473,12 @@ stencil_tma_kernel(const __grid_constant__ CUtensorMap mU, const __grid_constant
         }
     }
     if (failed && tid == 0) {
-        // let the copies still in flight land before the CTA's shared memory goes away (bounded)
-        for (int sl = 0; sl < FNS; ++sl) {
-            uint32_t dummy = 0;
-            (void)dummy;
-            tbar_wait(sbase + L::BAR_OFF + 8 * sl, 0);
-            tbar_wait(sbase + L::BAR_OFF + 8 * sl, 1);
-        }
+        // thread 0 stopped at plane r_fail: the planes it issued from there on may still be in flight; let
+        // them land before the CTA's shared memory goes away (at most four planes, one per slot, so every
+        // barrier phase is unambiguous; bounded).  A thread other than 0 that gave up leaves thread 0
+        // waiting for every plane it issued, as in a normal run.
+        for (int r = r_fail; r <= r_last; ++r)
+            tbar_wait(sbase + L::BAR_OFF + 8 * (r & (FNS - 1)), (r >> 2) & 1, TDRAIN_LIMIT);
     }
 }
 
@@ -633,10 +637,12 @@ helm_status launch_stencil_fast(helm_ctx* c, const float2* x, float2* y, const d
         if (encode3(m, &mU, x, c->nx, c->ny, c->nz, 2 * TPX, FPY) == HELM_OK) {
             if (c->opt.order == 6)
                 stencil_tma_kernel<6><<<grid, block, TLayout<6>::SMEM, s>>>(mU, m->mK, m->mF[0], m->mF[1], m->mF[2],
-                                                                           m->mF[3], p, y, sigma, sidx, c->status_d);
+                                                                           m->mF[3], p, y, sigma, sidx, c->status_d,
+                                                                           (long)c->wait_limit);
             else
                 stencil_tma_kernel<4><<<grid, block, TLayout<4>::SMEM, s>>>(mU, m->mK, m->mF[0], m->mF[1], m->mF[2],
-                                                                           m->mF[3], p, y, sigma, sidx, c->status_d);
+                                                                           m->mF[3], p, y, sigma, sidx, c->status_d,
+                                                                           (long)c->wait_limit);
             HELM_CUDA_TRY(cudaGetLastError());
             return HELM_OK;
         }

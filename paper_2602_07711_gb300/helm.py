@@ -80,6 +80,7 @@ _SIGS = {
                                 C.POINTER(C.c_double), C.c_void_p]),
     "helm_residual_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_double),
                                         C.POINTER(C.c_double), C.c_void_p]),
+    "helm_set_wait_limit": (C.c_int, [C.c_void_p, C.c_longlong]),
     "helm_profile": (C.c_int, [C.c_void_p, C.c_int]),
     "helm_profile_classes": (C.c_int, [C.c_void_p, C.c_uint]),
     "helm_profile_read": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int]),
@@ -273,6 +274,10 @@ def helm_residual_noalloc(ctx, b, x, r, stream=None):
     ni = C.c_double()
     code = lib().helm_residual_noalloc(ctx, _ptr(b), _ptr(x), _ptr(r), C.byref(n2), C.byref(ni), _stream(stream))
     return code, n2.value, ni.value
+
+
+def helm_set_wait_limit(ctx, polls):
+    _check(lib().helm_set_wait_limit(ctx, int(polls)), "helm_set_wait_limit")
 
 
 def helm_destroy(ctx):
@@ -490,6 +495,10 @@ class Solver:
 
     def get_eig(self, axis):
         return helm_get_eig(self.ctx, axis, self.n[axis])
+
+    def set_wait_limit(self, polls):
+        """Bound of the context's mbarrier waits in polls (0 = default); a diagnosis and test hook."""
+        helm_set_wait_limit(self.ctx, polls)
 
     def solve(self, b, x0=None, stream=None, check=True):
         """x such that A x = b (b complex128 on the device or in host memory)."""
