@@ -44,12 +44,15 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--e2e", type=int, default=1)
     p.add_argument("--max-iter", type=int, default=300)
-    p.add_argument("--workload", default="n256", choices=["n256", "batched", "pfft", "learned", "scatter", "tables"],
+    p.add_argument("--workload", default="n256",
+                   choices=["n256", "batched", "pfft", "learned", "scatter", "tables", "ksweep"],
                    help="n256: the headline solve; batched: 64 uneven problems x 4 right-hand sides in one "
                         "batched call; pfft: 512^3 layered medium, PFFT vs EigT; learned: 384^3 high-contrast "
                         "medium, learned correction vs plain EigT; scatter: the single-inclusion scattering "
                         "problem of Sec. 5.2 at 100^3, 200^3, 400^3; tables: the manufactured problem of "
-                        "Sec. 5.1 (collocated grid, high-order closure) at 50^3, 100^3, 200^3, orders 4 and 6")
+                        "Sec. 5.1 (collocated grid, high-order closure) at 50^3, 100^3, 200^3, orders 4 and 6; "
+                        "ksweep: the same problem for k = 10, 20, 50, 100 at 100^3 ... 511^3 (the wavenumber table "
+                        "of Sec. 5.1)")
     p.add_argument("--problems", type=int, default=64, help="batched workload: number of problems")
     p.add_argument("--autotune", type=int, default=0,
                    help="time the kernel variants on the grid before the run (default: the measured defaults)")
@@ -693,6 +696,71 @@ def run_tables(args, rank, world, local):
         print(json.dumps(line), flush=True)
 
 
+# Table tab:diff_k_results (Sec. 5.1): PFFT-GMRES N0 and T_P (seconds, one M3 Max core) of the test problem
+# for wavenumbers k = 10, 20, 50, 100 on 100^3 ... 511^3 grids
+PAPER_KSWEEP = {(100, 10): (4, 2.35), (100, 20): (5, 2.69), (100, 50): (9, 5.49), (100, 100): (34, 19.6),
+                (200, 10): (3, 20.9), (200, 20): (4, 25.0), (200, 50): (6, 34.4), (200, 100): (12, 62.0),
+                (400, 10): (3, 171), (400, 20): (3, 175), (400, 50): (5, 254), (400, 100): (7, 340),
+                (511, 10): (3, 312), (511, 20): (3, 312), (511, 50): (4, 384), (511, 100): (6, 527)}
+
+
+def run_ksweep(args, rank, world, local):
+    """Table tab:diff_k_results on the GPU path: the manufactured test problem of Sec. 5.1 (collocated grid,
+    high-order closure, sixth order) with k0 = k in {10, 20, 50, 100} on 100^3, 200^3, 400^3 and 511^3 grids,
+    preconditioned by EigT3, which inverts the same second-order operator as PFFT3 (the oracle pins
+    PFFT = EigT), FGMRES(20) with TF32 transforms to rel-res 1e-10.  The GPU eigensetup covers k0 h <= 1, so
+    k = 100 on the 100^3 grid (k0 h = 1.01) is reported as outside its range."""
+    import numpy as np
+    import torch
+
+    from paper_2602_07711_gb300 import HELM_CLOSURE_HIGH_ORDER, helm, media
+    torch.cuda.set_device(local)
+    out = {}
+    for (n, k), (n0_p, tp_p) in PAPER_KSWEEP.items():
+        key = "n%d-k%d" % (n, k)
+        if k / (n - 1.0) > 1.0:
+            out[key] = {"status": "k0 h = %.3f > 1: outside the GPU eigensetup's range" % (k / (n - 1.0)),
+                        "paper": {"N0": n0_p, "T_P_s": tp_p}}
+            continue
+        d = media.manufactured(n, float(k), 6)
+        S = helm.Solver((n, n, n), d["k2"], float(k), order=6, precision=1, flexible=True, restart=20,
+                        max_iter=args.max_iter, rtol=1e-10, staggered=False)
+        S.set_closure(HELM_CLOSURE_HIGH_ORDER)
+        F = S.closure_rhs(torch.from_numpy(d["faces"]).cuda(), S.build_rhs_fields(torch.from_numpy(d["fields"]).cuda()))
+        u = d["u"]
+        del d
+        x = torch.zeros_like(F)
+        S.solve(F, x0=x, check=False)
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        steps = max(1, args.steps)
+        torch.cuda.synchronize()
+        ev0.record()
+        for _ in range(steps):
+            x.zero_()
+            _, info = S.solve(F, x0=x, check=False)
+        ev1.record()
+        torch.cuda.synchronize()
+        dt = ev0.elapsed_time(ev1) / 1e3 / steps
+        U = x.cpu().numpy()
+        out[key] = {"time_to_rtol_s": dt, "iterations": info.iterations, "cycles": list(info.cycle_its[:info.restarts]),
+                    "relres_true": info.relres_true, "status": info.status,
+                    "l2_err": float(np.linalg.norm(U - u) / np.linalg.norm(u)),
+                    "paper": {"N0": n0_p, "T_P_s": tp_p}}
+        S.close()
+        del F, x, U, u
+        torch.cuda.empty_cache()
+    if rank == 0:
+        r = out["n511-k100"]
+        v = 511 ** 3 * r["iterations"] / r["time_to_rtol_s"] / 1e6 * world
+        line = _base_line(args, world, v, r["time_to_rtol_s"] * args.steps, "manufactured-sec5.1-ksweep",
+                          {"config": {"sizes": [100, 200, 400, 511], "k": [10, 20, 50, 100], "order": 6,
+                                      "precond": "EigT3 (= PFFT3's A_p^-1)", "closure": "high-order",
+                                      "precision": "tf32", "krylov": "FGMRES(20)", "rtol": 1e-10},
+                           "runs": out, "roofline": None, "cpu_baseline": None, "e2e": None})
+        print(json.dumps(line), flush=True)
+
+
 def run_learned(args, rank, world, local):
     """384^3, order 6, 8 points per wavelength, k^2/k0^2 in [0.5,1.8] (8 layers + 5 spheres): the U-Net is
     trained on the GPU on pairs from 96^3 solves of the same family, then FGMRES(30)+EigT with and without it."""
@@ -740,6 +808,8 @@ def main():
         run_scatter(args, rank, world, local)
     elif args.workload == "tables":
         run_tables(args, rank, world, local)
+    elif args.workload == "ksweep":
+        run_ksweep(args, rank, world, local)
     else:
         run_learned(args, rank, world, local)
     if world > 1:

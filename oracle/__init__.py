@@ -18,7 +18,7 @@ Module map (each function cites the passage it follows):
   eigt        EigT direct solver of A_p U = Y (Sec. 4.1, Eq. EIG_SOLVER)
   pfft        PFFT three-step solver (Sec. 4.2, Eq. PFFT_SOLVER)
   gmres       restarted right-preconditioned GMRES(m) and flexible GMRES (Sec. 5, [Saad])
-  metrics     rel-res, relmax-res, L2-err, max-err, relmax-err (Sec. 5.1)
+  metrics     L2-err, max-err (Sec. 5.1)
   model1d     the 1D model problem of Sec. 3 (Eqs. vect_eq, coef_gen, precond)
   manufactured  the separable test solution of Sec. 5.1
   closure     high-order ABC closure on collocated grids for the manufactured tests (reading of Sec. 2.1)

@@ -3,7 +3,7 @@ closure of the ABC in the operator (ghost U_0 = U_2 + 2 i k0 h U_1) and the EigT
 (Lambda-bar with gamma = 2 i k0 h, zeta = 2, Sec. 4.1), against the oracle's 'collocated3' rule.
 
 Tolerances as in test_gpu_parity: complex128 1e-11, double-float 1e-10, complex64 stencil 2e-6, FP32
-preconditioner 3e-6 kappa(V_x) kappa(V_y), solution 1e-5.
+transform passes 1.5e-6, z-solve and preconditioner per case (about 3x the measured error), solution 1e-5.
 """
 import math
 
@@ -98,23 +98,24 @@ def test_collocated_eigensetup_diagonalises_lambda_bar(n, kh):
     assert np.abs(Vi @ V - np.eye(n)).max() < 1e-10
 
 
-@pytest.mark.parametrize("n,L", [((40, 36, 33), (1.0, 0.9, 0.825)), ((64, 64, 64), (1.0, 1.0, 1.0))])
-def test_collocated_precond_steps_match_oracle(n, L):
+# z-solve / preconditioner bounds per case, about 3x the max-norm errors measured on a GB300 (2.3e-6 / 1.9e-6 at
+# 40 x 36 x 33, 4.5e-6 / 4.2e-6 at 64^3); transform passes 1.5e-6 (measured 3.8e-7 ... 7.4e-7)
+@pytest.mark.parametrize("n,L,tol", [((40, 36, 33), (1.0, 0.9, 0.825), 7e-6), ((64, 64, 64), (1.0, 1.0, 1.0), 1.4e-5)])
+def test_collocated_precond_steps_match_oracle(n, L, tol):
     g, k2, k0 = _medium(n, L)
     S = Solver(n, k2, k0, order=4, L=L, precision=HELM_PREC_FP32, staggered=False)
     e = EigT(g, k0)
-    tol = 3e-6 * max(1.0, np.linalg.cond(e.Vx) * np.linalg.cond(e.Vy))
     e.Dx, e.Vx, e.Vxi = S.get_eig(0)            # the GPU's own FP64 basis
     e.Dy, e.Vy, e.Vyi = S.get_eig(1)
     y = _rand(g.shape, 3)
     fwd = S.precond_step(1, _dev(y, torch.complex64)).cpu().numpy()
     ref_fwd = e.forward(y)
-    assert _rel(fwd, ref_fwd) < tol
+    assert _rel(fwd, ref_fwd) < 1.5e-6
     sub, diag, sup = e.z_coefficients()
     zs = S.precond_step(2, _dev(ref_fwd, torch.complex64)).cpu().numpy()
     ref_z = thomas(sub, diag, sup, ref_fwd)
     assert _rel(zs, ref_z) < tol
-    assert _rel(S.precond_step(3, _dev(ref_z, torch.complex64)).cpu().numpy(), e.inverse(ref_z)) < tol
+    assert _rel(S.precond_step(3, _dev(ref_z, torch.complex64)).cpu().numpy(), e.inverse(ref_z)) < 1.5e-6
     assert _rel(S.apply_precond(_dev(y, torch.complex64)).cpu().numpy(), e.apply_Minv(y)) < tol
 
 

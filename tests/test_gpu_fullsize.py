@@ -1,9 +1,14 @@
 """Parity at the full size of the headline workload, in the launch configuration bench.py times: 256^3,
 sixth order, the 20-bump medium of seeds 3/4 (~10 points per wavelength), TF32 EigT, FGMRES(30), rtol
 1e-6.  The FP64 oracle is evaluated on the whole field (each evaluation takes seconds on the host cores):
-the matvec element by element, the preconditioner in the GPU's own eigenbasis within the TF32 bound, the
-right-hand side, and the FP64 residual of the GPU's solution.
+the matvec element by element, the forward transform and the preconditioner in the GPU's own eigenbasis
+within the fixed TF32 bounds (measured 8.3e-4 and 1.7e-3 relative in the 2-norm at this size), the
+right-hand side, and the FP64 residual of the GPU's solution.  The solution itself is compared with the
+oracle's, solved to rel-res 1e-12, at 4096 seeded points (tests/golden/make_solution_sample.py writes them;
+the oracle's solve takes about an hour on eight host cores).
 """
+import os
+
 import numpy as np
 import pytest
 
@@ -50,11 +55,17 @@ def test_precond_full_size(case):
     e = EigT(g, k0)
     e.Dx, e.Vx, e.Vxi = S.get_eig(0)
     e.Dy, e.Vy, e.Vyi = S.get_eig(1)
-    kap = np.linalg.cond(e.Vx) * np.linalg.cond(e.Vy)
     y = _rand(g.shape, 32)
-    z = S.apply_precond(torch.from_numpy(y).cuda()).cpu().numpy()
+    yd = torch.from_numpy(y).cuda()
+    fwd = S.precond_step(1, yd).cpu().numpy()
+    ref = e.forward(y.astype(np.complex128))
+    assert np.linalg.norm(fwd - ref) / np.linalg.norm(ref) < 2e-3
+    assert np.abs(fwd - ref).max() / np.abs(ref).max() < 2.5e-3
+    del fwd, ref
+    z = S.apply_precond(yd).cpu().numpy()
     ref = e.apply_Minv(y.astype(np.complex128)).reshape(g.shape)
-    assert np.linalg.norm(z - ref) / np.linalg.norm(ref) < 2e-3 * kap
+    assert np.linalg.norm(z - ref) / np.linalg.norm(ref) < 4e-3
+    assert np.abs(z - ref).max() / np.abs(ref).max() < 5e-3
 
 
 def test_rhs_and_solution_full_size(case):
@@ -70,3 +81,24 @@ def test_rhs_and_solution_full_size(case):
     xg = x.cpu().numpy()
     # the FP64 residual of the GPU's solution, evaluated by the oracle on the whole field
     assert np.linalg.norm(A(xg).reshape(-1) - Fh.reshape(-1)) / np.linalg.norm(Fh) <= 1.5e-6
+
+
+SAMPLE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "bumps256_order6_solution_sample.txt")
+
+
+def test_solution_matches_oracle_at_sampled_points(case):
+    """The solution error the method targets (<= 1e-5 relative at rtol 1e-6), at the headline size: the
+    GPU's solution against the oracle's (rel-res 1e-12) at 4096 seeded points."""
+    import sys
+    sys.path.insert(0, os.path.dirname(SAMPLE))
+    from make_solution_sample import read
+    meta, idx, xo = read(SAMPLE)
+    assert meta["relres"] <= 1e-11
+    S = case["S"]
+    F = S.build_rhs(torch.from_numpy(case["f"]).cuda())
+    x, info = S.solve(F)
+    assert info.status == 0 and info.relres_true <= 1e-6
+    xs = x.reshape(-1)[torch.from_numpy(idx).cuda()].cpu().numpy()
+    assert np.linalg.norm(xs - xo) / np.linalg.norm(xo) <= 1e-5
+    assert np.abs(xs - xo).max() / np.abs(xo).max() <= 1e-5
+    assert abs(float(torch.linalg.vector_norm(x)) / meta["norm2"] - 1) <= 1e-5

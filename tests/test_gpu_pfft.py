@@ -1,8 +1,10 @@
 """PFFT preconditioner (Sec. 4.2) on the GPU against the oracle, through the C-ABI.
 
 The PFFT solve and the EigT solve both invert the same A_p exactly, so the GPU's PFFT output is checked
-against both the oracle's PFFT (face-Dirichlet sine basis) and its EigT.  complex64 arithmetic: relative
-2-norm error <= 2e-5 * kappa(V_x) kappa(V_y) (the boundary correction passes through the EigT bases).
+against both the oracle's PFFT (face-Dirichlet sine basis) and its EigT.  Fixed relative 2-norm bounds
+per case, about 3x the errors measured on a GB300: FP32 sine transforms 1.6e-5 (32 x 32 x 20), 7.7e-5
+(64 x 32 x 33), 1.0e-5 (16 x 64 x 8), 4.5e-6 (128 x 128 x 12); TF32 tensor-core sine products 1.4e-3 and
+1.5e-3 (as the TF32 EigT transforms).
 """
 import math
 
@@ -23,19 +25,18 @@ def _rand(shape, seed):
     return r.standard_normal(shape) + 1j * r.standard_normal(shape)
 
 
-@pytest.mark.parametrize("n,L", [((32, 32, 20), (1.0, 1.0, 0.625)), ((64, 32, 33), (1.0, 0.6, 0.5)),
-                                 ((16, 64, 8), (0.25, 1.0, 0.2)), ((128, 128, 12), (1.0, 1.0, 0.1))])
-def test_pfft_preconditioner_matches_oracle(n, L):
+@pytest.mark.parametrize("n,L,tol", [((32, 32, 20), (1.0, 1.0, 0.625), 5e-5), ((64, 32, 33), (1.0, 0.6, 0.5), 2.3e-4),
+                                     ((16, 64, 8), (0.25, 1.0, 0.2), 3e-5), ((128, 128, 12), (1.0, 1.0, 0.1), 1.5e-5)])
+def test_pfft_preconditioner_matches_oracle(n, L, tol):
     g = Grid(*n, lx=L[0], ly=L[1], lz=L[2], staggered=True)
     k0 = 2 * math.pi / (10 * g.h[0])
     S = Solver(n, np.full(g.shape, k0 * k0, complex), k0, order=4, L=L, precond=HELM_PRECOND_PFFT)
     y = _rand(g.shape, 7)
     z = S.apply_precond(torch.from_numpy(y).to("cuda", torch.complex64)).cpu().numpy()
     e = EigT(g, k0)
-    kap = np.linalg.cond(e.Vx) * np.linalg.cond(e.Vy)
     for ref in (PFFT(g, k0, variant="face").apply_Minv(y), e.apply_Minv(y)):
         err = np.linalg.norm(z - ref) / np.linalg.norm(ref)
-        assert err < 2e-5 * kap, (err, kap)
+        assert err < tol, err
 
 
 def test_pfft_gmres_matches_eigt_gmres():
@@ -54,18 +55,16 @@ def test_pfft_gmres_matches_eigt_gmres():
 @pytest.mark.parametrize("n,L", [((32, 32, 20), (1.0, 1.0, 0.625)), ((128, 64, 12), (1.0, 0.5, 0.1))])
 def test_pfft_tensor_core_transforms_match_oracle(n, L):
     """TF32 contexts run the sine transforms as tcgen05 products with the sine bases: the TF32 bound of
-    the EigT transforms applies (2e-3 x kappa in the 2-norm)."""
+    the EigT preconditioner applies (4e-3 in the 2-norm)."""
     g = Grid(*n, lx=L[0], ly=L[1], lz=L[2], staggered=True)
     k0 = 2 * math.pi / (10 * g.h[0])
     S = Solver(n, np.full(g.shape, k0 * k0, complex), k0, order=4, L=L, precond=HELM_PRECOND_PFFT,
                precision=HELM_PREC_TF32, flexible=True)
     y = _rand(g.shape, 8)
     z = S.apply_precond(torch.from_numpy(y).to("cuda", torch.complex64)).cpu().numpy()
-    e = EigT(g, k0)
-    kap = np.linalg.cond(e.Vx) * np.linalg.cond(e.Vy)
     ref = PFFT(g, k0, variant="face").apply_Minv(y)
     err = np.linalg.norm(z - ref) / np.linalg.norm(ref)
-    assert err < 2e-3 * kap, (err, kap)
+    assert err < 4e-3, err
 
 
 def test_pfft_tensor_core_fgmres_converges_like_eigt():

@@ -1,9 +1,12 @@
 """Tensor-core (tcgen05, TF32) eigenvector transforms against the CPU oracle, through the C-ABI.
 
 TF32 keeps 10 explicit mantissa bits (the weights are rounded to nearest, the streamed grid values are
-truncated by the tensor core), so each product carries a relative error below 2^-10 and the FP32
-accumulation over K = N terms grows it like sqrt(K) in the mean.  Bounds used below (relative):
-2-norm error <= 2e-3 * kappa, max-norm error <= 1e-2 * kappa, kappa = cond(V_x) cond(V_y) of the basis.
+truncated by the tensor core), so each product carries a relative error of about 2^-11 and the FP32
+accumulation adds little.  The measured relative errors on random complex inputs do not grow with N or with
+the conditioning of the bases: 8.0e-4 ... 8.4e-4 (2-norm) and 7.5e-4 ... 9.6e-4 (max-norm) for one
+transform, 1.5e-3 ... 1.8e-3 and 1.6e-3 ... 2.0e-3 for the whole preconditioner, from 32^3 to 256 x 256 x 8.
+The bounds below are fixed, about 2.5x those measurements; a transposed basis or one shifted by a column
+gives relative errors near 1.4 (tests/test_oracle_pins.py plants both in the oracle at 256 x 256 x 8).
 """
 import math
 
@@ -18,6 +21,11 @@ from oracle.gmres import gmres
 from oracle.grid import Grid
 from oracle.operators import Operator
 from paper_2602_07711_gb300 import HELM_PREC_FP32, HELM_PREC_TF32, Solver, media
+
+
+# relative error bounds of one TF32 transform (forward or inverse) and of the whole preconditioner
+TF32_PASS_2, TF32_PASS_MAX = 2e-3, 2.5e-3
+TF32_PRECOND_2, TF32_PRECOND_MAX = 4e-3, 5e-3
 
 
 def _dev(a, dtype=torch.complex64):
@@ -42,17 +50,16 @@ def test_tf32_transforms_match_oracle(n):
     e = EigT(g, k0)
     e.Dx, e.Vx, e.Vxi = S.get_eig(0)
     e.Dy, e.Vy, e.Vyi = S.get_eig(1)
-    kap = np.linalg.cond(e.Vx) * np.linalg.cond(e.Vy)
     y = _rand(g.shape, 5)
     fwd = S.precond_step(1, _dev(y)).cpu().numpy()
     e2, emax = _errs(fwd, e.forward(y))
-    assert e2 < 2e-3 * kap and emax < 1e-2 * kap, (e2, emax, kap)
+    assert e2 < TF32_PASS_2 and emax < TF32_PASS_MAX, (e2, emax)
     inv = S.precond_step(3, _dev(y)).cpu().numpy()
     e2, emax = _errs(inv, e.inverse(y))
-    assert e2 < 2e-3 * kap and emax < 1e-2 * kap, (e2, emax, kap)
+    assert e2 < TF32_PASS_2 and emax < TF32_PASS_MAX, (e2, emax)
     z = S.apply_precond(_dev(y)).cpu().numpy()
     e2, emax = _errs(z, e.apply_Minv(y))
-    assert e2 < 2e-3 * kap, (e2, kap)
+    assert e2 < TF32_PRECOND_2 and emax < TF32_PRECOND_MAX, (e2, emax)
 
 
 def test_tf32_fgmres_solution_matches_oracle():

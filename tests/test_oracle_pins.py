@@ -185,6 +185,44 @@ def test_gmres_one_iteration_on_second_order_operator(staggered):
     assert info["iterations"] == 1 and info["relres"] < 1e-12
 
 
+def _copy_eigt(e):
+    c = EigT.__new__(EigT)
+    c.__dict__.update(e.__dict__)
+    return c
+
+
+@pytest.mark.parametrize("mistake", ["transposed_Vxi", "row_shifted_Vxi", "transposed_Vyi", "conjugated_Vyi"])
+def test_transform_bounds_catch_a_wrong_basis(mistake):
+    """The fixed bounds of the GPU transform tests (2e-3 relative in the 2-norm for one TF32 pass, 4e-3 for
+    the preconditioner; EigT steps 2 and 4 of Sec. 4.1) lie far below what the plausible kernel mistakes
+    give.  Each mistake is planted in a copy of the oracle at the headline's 256 x 256 transform size."""
+    g = Grid(256, 256, 8, staggered=True)
+    k0 = 2 * math.pi / (10 * g.h[0])
+    e = EigT(g, k0)
+    y = _rand(g.shape, 5)
+    ref = e.forward(y)
+    bad = _copy_eigt(e)
+    if mistake == "transposed_Vxi":
+        bad.Vxi = e.Vxi.T.copy()
+    elif mistake == "row_shifted_Vxi":
+        bad.Vxi = np.roll(e.Vxi, 1, axis=0)
+    elif mistake == "transposed_Vyi":
+        bad.Vyi = e.Vyi.T.copy()
+    else:
+        bad.Vyi = e.Vyi.conj()
+    err = np.linalg.norm(bad.forward(y) - ref) / np.linalg.norm(ref)
+    assert err > 50 * 4e-3, err
+    # and the inverse transform with the same mistake in V
+    bad_inv = _copy_eigt(e)
+    bad_inv.Vx = e.Vx.T.copy() if "Vxi" in mistake else e.Vx
+    bad_inv.Vy = e.Vy.conj() if mistake == "conjugated_Vyi" else (e.Vy.T.copy() if "Vyi" in mistake else e.Vy)
+    if mistake == "row_shifted_Vxi":
+        bad_inv.Vx = np.roll(e.Vx, 1, axis=0)
+    ref_inv = e.inverse(y)
+    err = np.linalg.norm(bad_inv.inverse(y) - ref_inv) / np.linalg.norm(ref_inv)
+    assert err > 50 * 4e-3, err
+
+
 # ---- PFFT = EigT (Sec. 4.2) ------------------------------------------------------------------
 @pytest.mark.parametrize("variant", ["node", "face"])
 @pytest.mark.parametrize("staggered", [True, False])
