@@ -24,7 +24,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "time-to-rtol 1e-6 (s) & Mpts·iter/s at n=256³; mixed/learned vs plain EigT"
 UNIT = "Mpts·iter/s"
-PREC_NAMES = {"fp32": 0, "tf32": 1}
+PREC_NAMES = {"fp32": 0, "tf32": 1, "tf32x3": 2}
 CLASSES = ["stencil", "xpass", "ypass", "zsolve", "dots", "update", "small", "combine", "residual", "other",
            "learned"]
 
@@ -380,18 +380,41 @@ def run_ours(args, rank, world, local):
         e2e = {"value": pts * e_its / e_dt / 1e6 * world, "unit": UNIT,
                "h2d_bytes_per_step": 2 * 16 * pts, "d2h_bytes_per_step": 16 * pts,
                "time_to_rtol_s": e_dt / max(1, args.steps)}
-    # plain complex64 EigT-GMRES for comparison
+    # plain complex64 EigT-GMRES for comparison: the same warm-up, the same number of timed steps with CUDA
+    # events, and a per-class kernel table from profiled steps before its timed region
     plain = None
     if args.plain and precision != "fp32":
         P = make("fp32", False)
-        step(P)
+        for _ in range(max(1, args.warmup)):
+            step(P)
+        lib.helm_profile(P.ctx, 1)
+        lib.helm_profile_read(P.ctx, ms_arr, ln_arr, len(CLASSES), 1)
+        pinfos = [step(P) for _ in range(args.steps)]
+        lib.helm_profile_read(P.ctx, ms_arr, ln_arr, len(CLASSES), 1)
+        lib.helm_profile(P.ctx, 0)
+        p_ms = {c: ms_arr[i] for i, c in enumerate(CLASSES)}
+        p_ln = {c: ln_arr[i] for i, c in enumerate(CLASSES)}
         torch.cuda.synchronize()
-        t2 = time.perf_counter()
-        pi = step(P)
+        pe0 = torch.cuda.Event(enable_timing=True)
+        pe1 = torch.cuda.Event(enable_timing=True)
+        pe0.record(stream)
+        pinfos = [step(P) for _ in range(args.steps)]
+        pe1.record(stream)
         torch.cuda.synchronize()
-        pdt = time.perf_counter() - t2
-        plain = {"time_to_rtol_s": pdt, "iterations": pi.iterations, "Mpts_iter_s": pts * pi.iterations / pdt / 1e6,
-                 "relres_true": pi.relres_true}
+        pdt = pe0.elapsed_time(pe1) / 1e3 / args.steps
+        p_its = sum(i.iterations for i in pinfos) / len(pinfos)
+        p_alg = {}
+        for i in pinfos:
+            for c, a in algorithmic(n, order, cycles_of(i, args.restart), real_medium).items():
+                t_ = p_alg.setdefault(c, {"bytes": 0, "flops": 0, "launches": 0})
+                for k_ in a:
+                    t_[k_] += a[k_]
+        plain = {"time_to_rtol_s": pdt, "steps": args.steps, "iterations": pinfos[-1].iterations,
+                 "Mpts_iter_s": pts * p_its / pdt / 1e6, "relres_true": pinfos[-1].relres_true,
+                 "kernels": {c: {"ms": round(p_ms[c], 3), "launches": p_ln[c]} for c in CLASSES if p_ln[c]},
+                 "kernels_note": "per-class CUDA-event times over %d profiled solves before the timed region; the "
+                                 "transforms are the FP32 SIMT complex GEMM (cgemm_kernel)" % args.steps,
+                 "roofline": roofline(p_ms, p_ln, p_alg, "fp32", order, n, None)}
         P.close()
     # CPU oracle sample (rank 0, N = 1)
     cpu = None
@@ -706,17 +729,19 @@ PAPER_KSWEEP = {(100, 10): (4, 2.35), (100, 20): (5, 2.69), (100, 50): (9, 5.49)
 
 def run_ksweep(args, rank, world, local):
     """Table tab:diff_k_results on the GPU path: the manufactured test problem of Sec. 5.1 (collocated grid,
-    high-order closure, sixth order) with k0 = k in {10, 20, 50, 100} on 100^3, 200^3, 400^3 and 511^3 grids,
-    preconditioned by EigT3, which inverts the same second-order operator as PFFT3 (the oracle pins
-    PFFT = EigT), FGMRES(20) with TF32 transforms to rel-res 1e-10.  The GPU eigensetup covers k0 h <= 1, so
-    k = 100 on the 100^3 grid (k0 h = 1.01) is reported as outside its range."""
+    high-order closure, sixth order) with k0 = k in {10, 20, 50, 100} on 100^3, 200^3, 400^3 and 512^3 grids
+    (the paper's 511^3 row: the library needs an even point count), preconditioned by EigT3, which inverts
+    the same second-order operator as PFFT3 (the oracle pins PFFT = EigT), FGMRES(20) with TF32 transforms
+    to rel-res 1e-10.  The GPU eigensetup covers k0 h <= 1, so k = 100 on the 100^3 grid (k0 h = 1.01) is
+    reported as outside its range."""
     import numpy as np
     import torch
 
     from paper_2602_07711_gb300 import HELM_CLOSURE_HIGH_ORDER, helm, media
     torch.cuda.set_device(local)
     out = {}
-    for (n, k), (n0_p, tp_p) in PAPER_KSWEEP.items():
+    for (n_paper, k), (n0_p, tp_p) in PAPER_KSWEEP.items():
+        n = 512 if n_paper == 511 else n_paper
         key = "n%d-k%d" % (n, k)
         if k / (n - 1.0) > 1.0:
             out[key] = {"status": "k0 h = %.3f > 1: outside the GPU eigensetup's range" % (k / (n - 1.0)),
@@ -746,15 +771,16 @@ def run_ksweep(args, rank, world, local):
         out[key] = {"time_to_rtol_s": dt, "iterations": info.iterations, "cycles": list(info.cycle_its[:info.restarts]),
                     "relres_true": info.relres_true, "status": info.status,
                     "l2_err": float(np.linalg.norm(U - u) / np.linalg.norm(u)),
-                    "paper": {"N0": n0_p, "T_P_s": tp_p}}
+                    "paper": {"N0": n0_p, "T_P_s": tp_p, "grid": n_paper}}
+        print(key, json.dumps(out[key]), file=sys.stderr, flush=True)
         S.close()
         del F, x, U, u
         torch.cuda.empty_cache()
     if rank == 0:
-        r = out["n511-k100"]
-        v = 511 ** 3 * r["iterations"] / r["time_to_rtol_s"] / 1e6 * world
+        r = out["n512-k100"]
+        v = 512 ** 3 * r["iterations"] / r["time_to_rtol_s"] / 1e6 * world
         line = _base_line(args, world, v, r["time_to_rtol_s"] * args.steps, "manufactured-sec5.1-ksweep",
-                          {"config": {"sizes": [100, 200, 400, 511], "k": [10, 20, 50, 100], "order": 6,
+                          {"config": {"sizes": [100, 200, 400, 512], "k": [10, 20, 50, 100], "order": 6,
                                       "precond": "EigT3 (= PFFT3's A_p^-1)", "closure": "high-order",
                                       "precision": "tf32", "krylov": "FGMRES(20)", "rtol": 1e-10},
                            "runs": out, "roofline": None, "cpu_baseline": None, "e2e": None})

@@ -53,8 +53,9 @@ typedef enum {
  *   the three-point second-order closure of the ABC, U_0 = U_2 + 2 i k0 h U_1 per direction (edge and
  *   corner ghosts: the one-dimensional rules applied in turn), and the preconditioner is EigT3 (Lbar with
  *   gamma = 2 i k0 h, zeta = 2; Sec. 4.1).  k^2 and f are reflected about the boundary node.  The matvec
- *   and the residual run on the general stencil kernels (the fast ones are staggered).  EigT only
- *   (PFFT and FFT2: HELM_ERR_UNSUPPORTED); the 1D eigensetup needs k0 h <= 1 (HELM_ERR_EIG beyond). */
+ *   and the residual run on the general stencil kernels (the fast ones are staggered).  EigT (EigT3),
+ *   PFFT (PFFT3: the boundary correction spans the two outer layers, since zeta = 2) and FFT2; the 1D
+ *   eigensetup needs k0 h <= 1 (HELM_ERR_EIG beyond). */
 typedef struct {
     int nx, ny, nz;
     double lx, ly, lz;
@@ -62,7 +63,8 @@ typedef struct {
 } helm_grid;
 
 /* Preconditioner M^-1 = h_z^2 A_p^-1 (Sec. 4): none, EigT (Sec. 4.1) or PFFT (Sec. 4.2; needs N_x and N_y
- * powers of two <= 512; its sine solver uses the Dirichlet condition at the staggered face).  FFT2 is the
+ * powers of two <= 512; its sine solver uses the Dirichlet condition with the corner -1 of the staggered
+ * face, and the boundary correction makes the result that of A_p^-1 on either grid).  FFT2 is the
  * Dirichlet solve alone, M^-1 = h_z^2 (A_p^F)^-1 (Eq. TFprec; step 1 of PFFT without the boundary
  * correction): the FFT-based second-order preconditioner the paper compares against (Sec. 5), same size
  * limits as PFFT. */
@@ -73,8 +75,12 @@ enum { HELM_PRECOND_NONE = 0, HELM_PRECOND_EIGT = 1, HELM_PRECOND_PFFT = 2, HELM
  * the true residual, the right-hand side and the iterate double-float (about 44 bits) in every mode.
  *   HELM_PREC_FP32    complex64 on the CUDA cores (FFMA), the "plain complex64" method
  *   HELM_PREC_TF32    tcgen05 tensor cores, TF32 operands, FP32 accumulation in TMEM (one product); needs
- *                     even N_x                                                                          */
-enum { HELM_PREC_FP32 = 0, HELM_PREC_TF32 = 1 };
+ *                     even N_x.  Relative error of a transform about 8e-4.
+ *   HELM_PREC_TF32X3  split precision on the same tensor cores: every operand a = hi + lo with hi its TF32
+ *                     rounding and lo the TF32 rounding of the remainder, products hi hi + hi lo + lo hi
+ *                     (three MMAs) with FP32 accumulation: FP32-level transforms at three times the tensor
+ *                     work; needs even N_x.                                                             */
+enum { HELM_PREC_FP32 = 0, HELM_PREC_TF32 = 1, HELM_PREC_TF32X3 = 2 };
 
 typedef struct {
     int order;       /* 2, 4 (Eq. scheme4, any h_x, h_y, h_z) or 6 (Eq. scheme6, needs h_x = h_y = h_z)  */

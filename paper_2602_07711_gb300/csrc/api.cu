@@ -80,10 +80,8 @@ helm_status helm_setup(const helm_grid* grid, const void* k2, double k0, const d
     if (!(grid->lx > 0 && grid->ly > 0 && grid->lz > 0)) return HELM_ERR_ARG;
     if (opt->order != 2 && opt->order != 4 && opt->order != 6) return HELM_ERR_ARG;
     if (opt->restart < 1 || opt->restart > 64 || opt->max_iter < 1 || !(opt->rtol > 0)) return HELM_ERR_ARG;
-    if (opt->precond < 0 || opt->precond > 3 || opt->precision < 0 || opt->precision > 1) return HELM_ERR_ARG;
+    if (opt->precond < 0 || opt->precond > 3 || opt->precision < 0 || opt->precision > 2) return HELM_ERR_ARG;
     const int colloc = grid->staggered ? 0 : 1;
-    // the PFFT and FFT2 sine solvers are built for the staggered face
-    if (colloc && (opt->precond == HELM_PRECOND_PFFT || opt->precond == HELM_PRECOND_FFT2)) return HELM_ERR_UNSUPPORTED;
     // the Krylov kernels move two points per 16-byte access: the point count must be even
     if (((size_t)grid->nx * grid->ny * grid->nz) % 2 != 0) return HELM_ERR_UNSUPPORTED;
     if (grid->nz > 512) return HELM_ERR_UNSUPPORTED;

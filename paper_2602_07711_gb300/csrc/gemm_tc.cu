@@ -40,10 +40,14 @@ struct TcState {
     // operand sets: 0/1 EigT forward/inverse (V^-1, V), 2/3 PFFT sine transforms forward/inverse (S^T, S)
     float* Bx[4] = {nullptr, nullptr, nullptr, nullptr};   // x-pass real-embedded operands, [2N][2N]
     float* Wy[4] = {nullptr, nullptr, nullptr, nullptr};   // y-pass operands, [2][N_y][ldw] (re, im planes)
+    float* Bxl[4] = {nullptr, nullptr, nullptr, nullptr};  // 3xTF32: remainders of Bx and Wy
+    float* Wyl[4] = {nullptr, nullptr, nullptr, nullptr};
     int ldw = 0;
+    int split = 0;             // HELM_PREC_TF32X3
     CUtensorMap mapBx[4];
     CUtensorMap mapBx256[4];   // the same operands in 256-row boxes (256-wide x-pass tiles)
     CUtensorMap mapWy[4];
+    CUtensorMap mapBxl[4], mapBx256l[4], mapWyl[4];
 };
 
 __device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -130,6 +134,31 @@ __device__ __forceinline__ void drain_tma(const uint64_t* full, int ns, long iss
 __device__ __forceinline__ void drain_mma(uint64_t* bar) {
     mma_commit(su32(bar));
     mbar_wait(su32(bar), 0, DRAIN_LIMIT);
+}
+
+// ---- three-product split TF32 ("3xTF32") -----------------------------------------------------------
+// a = hi + lo with hi = a rounded to TF32 (10 explicit mantissa bits, round to nearest) and lo = a - hi
+// (exact in FP32, below 2^-11 |a|); a b ~ hi_a hi_b + hi_a lo_b + lo_a hi_b, the dropped lo_a lo_b and the
+// tensor core's truncation of lo to TF32 are below 2^-21 of the product.  The bases are split once at
+// set-up; the streamed grid tile is split in shared memory by four converter warps, element by element,
+// so the swizzled layout TMA wrote stays valid for both halves.
+__device__ __forceinline__ float tf32_rna(float a) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(a));
+    return __uint_as_float(r);
+}
+// one 16 KiB data tile (4096 floats) by 128 threads: hi in place, lo into the parallel tile
+__device__ __forceinline__ void split_tile(float4* hi, float4* lo, int t) {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const int k = t + 128 * i;
+        const float4 v = hi[k];
+        const float4 h = make_float4(tf32_rna(v.x), tf32_rna(v.y), tf32_rna(v.z), tf32_rna(v.w));
+        hi[k] = h;
+        lo[k] = make_float4(v.x - h.x, v.y - h.y, v.z - h.z, v.w - h.w);
+    }
+    // the MMAs read both tiles through the async proxy
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
 // ---- x-pass: Out[M][N2] = alpha * A[M][K2] B[N2][K2]^T -------------------------------------------
@@ -371,10 +400,12 @@ ypass_tc_kernel(const __grid_constant__ CUtensorMap tmW, const __grid_constant__
 
 // stage counts of the persistent x-pass: 128-wide tiles two CTAs per SM, 256-wide tiles one CTA per SM
 // (2 x 256 accumulator columns fill the tensor memory); 1024 bytes of slack align the ring
-template <int BNT>
+// the split (3xTF32) form holds the data tile, its remainder and both halves of the basis tile per stage
+template <int BNT, bool SPLIT = false>
 struct PersX {
-    static constexpr int STAGES = BNT == 256 ? 4 : XSTAGES;
-    static constexpr size_t SMEM = (size_t)STAGES * (BM * BK * 4 + BNT * BK * 4) + XEPI_BYTES + 1024;
+    static constexpr int STAGES = SPLIT ? (BNT == 256 ? 2 : 3) : (BNT == 256 ? 4 : XSTAGES);
+    static constexpr int STAGE_BYTES = (SPLIT ? 2 : 1) * (BM * BK * 4 + BNT * BK * 4);
+    static constexpr size_t SMEM = (size_t)STAGES * STAGE_BYTES + XEPI_BYTES + 1024;
 };
 
 // ---- persistent x-pass: one CTA walks many output tiles, the accumulator is double-buffered in tensor
@@ -384,14 +415,17 @@ struct PersX {
 // epilogue: accumulator buffer b holds a finished tile), acce[b] (epilogue -> MMA: buffer b drained; four
 // arrivals, one per epilogue warp).  Tiles are ordered N-fastest so that consecutive tiles of a CTA share
 // their A rows in L2.
-template <int BNT>
-__global__ void __launch_bounds__(192, 1)
+// SPLIT: 3xTF32 with tmBl the remainder of the basis; 320 threads, warps 6-9 split the data tiles.
+// Stage layout: [A | B] (TF32), [A hi | A lo | B hi | B lo] (SPLIT).
+template <int BNT, bool SPLIT>
+__global__ void __launch_bounds__(SPLIT ? 320 : 192, 1)
 xpass_tc_pers_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-                     float* __restrict__ out, int M, int N2, int K2, float alpha, const double* __restrict__ alpha_dev,
-                     int aidx, unsigned* status, long wlim) {
+                     const __grid_constant__ CUtensorMap tmBl, float* __restrict__ out, int M, int N2, int K2,
+                     float alpha, const double* __restrict__ alpha_dev, int aidx, unsigned* status, long wlim) {
     extern __shared__ uint8_t dsm[];
-    constexpr int NS = PersX<BNT>::STAGES, BTILE = BNT * BK * 4, STAGE = TILE + BTILE;
-    __shared__ __align__(8) uint64_t full[NS], empty[NS], accf[2], acce[2], drainb;
+    constexpr int NS = PersX<BNT, SPLIT>::STAGES, BTILE = BNT * BK * 4, STAGE = PersX<BNT, SPLIT>::STAGE_BYTES;
+    constexpr int AOFF_LO = TILE, BOFF = SPLIT ? 2 * TILE : TILE, BOFF_LO = BOFF + BTILE;
+    __shared__ __align__(8) uint64_t full[NS], empty[NS], conv[NS], accf[2], acce[2], drainb;
     __shared__ int fail_any;
     __shared__ uint32_t tslot;
     const uint32_t raw = su32(dsm);
@@ -401,7 +435,11 @@ xpass_tc_pers_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_const
     const int ntn = (N2 + BNT - 1) / BNT, ntm = (M + BM - 1) / BM, ntiles = ntn * ntm;
     float* epi = reinterpret_cast<float*>(dsm + (base - raw) + NS * STAGE);   // epilogue staging rows
     if (threadIdx.x == 0) {
-        for (int s = 0; s < NS; ++s) { mbar_init(su32(&full[s]), 1); mbar_init(su32(&empty[s]), 1); }
+        for (int s = 0; s < NS; ++s) {
+            mbar_init(su32(&full[s]), 1);
+            mbar_init(su32(&empty[s]), 1);
+            mbar_init(su32(&conv[s]), 4);
+        }
         for (int b = 0; b < 2; ++b) { mbar_init(su32(&accf[b]), 1); mbar_init(su32(&acce[b]), 4); }
         mbar_init(su32(&drainb), 1);
         fail_any = 0;
@@ -428,10 +466,11 @@ xpass_tc_pers_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_const
                     const uint32_t ph = (uint32_t)((it / NS) & 1);
                     if (it >= NS) ok = mbar_wait(su32(&empty[s]), ph ^ 1, wlim);
                     if (!ok) break;
-                    const uint32_t sa = base + s * STAGE, sb = sa + TILE;
-                    mbar_expect_tx(su32(&full[s]), STAGE);
+                    const uint32_t sa = base + s * STAGE, sb = sa + BOFF;
+                    mbar_expect_tx(su32(&full[s]), SPLIT ? TILE + 2 * BTILE : STAGE);
                     tma_2d(sa, &tmA, su32(&full[s]), kb * BK, m0);
                     tma_2d(sb, &tmB, su32(&full[s]), kb * BK, n0);
+                    if (SPLIT) tma_2d(sa + BOFF_LO, &tmBl, su32(&full[s]), kb * BK, n0);
                     ++issued;
                 }
             }
@@ -450,20 +489,28 @@ xpass_tc_pers_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_const
                 for (int kb = 0; kb < nk && ok; ++kb, ++it) {
                     const int s = (int)(it % NS);
                     const uint32_t ph = (uint32_t)((it / NS) & 1);
-                    ok = mbar_wait(su32(&full[s]), ph, wlim);
+                    ok = mbar_wait(su32(SPLIT ? &conv[s] : &full[s]), ph, wlim);
                     if (!ok) break;
                     fence_after();
-                    const uint32_t sa = base + s * STAGE, sb = sa + TILE;
+                    const uint32_t sa = base + s * STAGE, sb = sa + BOFF;
 #pragma unroll
-                    for (int kk = 0; kk < BK / 8; ++kk)
-                        mma_tf32(acc_t, sdesc(sa + kk * 32, 16, 1024), sdesc(sb + kk * 32, 16, 1024), idesc,
-                                 (kb | kk) ? 1u : 0u);
+                    for (int kk = 0; kk < BK / 8; ++kk) {
+                        const uint64_t ad = sdesc(sa + kk * 32, 16, 1024), bd = sdesc(sb + kk * 32, 16, 1024);
+                        if (SPLIT) {
+                            // small products first: lo_a hi_b + hi_a lo_b + hi_a hi_b
+                            mma_tf32(acc_t, sdesc(sa + AOFF_LO + kk * 32, 16, 1024), bd, idesc, (kb | kk) ? 1u : 0u);
+                            mma_tf32(acc_t, ad, sdesc(sa + BOFF_LO + kk * 32, 16, 1024), idesc, 1u);
+                            mma_tf32(acc_t, ad, bd, idesc, 1u);
+                        } else {
+                            mma_tf32(acc_t, ad, bd, idesc, (kb | kk) ? 1u : 0u);
+                        }
+                    }
                     mma_commit(su32(&empty[s]));
                 }
                 if (ok) mma_commit(su32(&accf[b]));
             }
         }
-    } else {
+    } else if (!SPLIT || warp < 6) {
         const int q = warp & 3;
         const float al = alpha * (alpha_dev ? (float)alpha_dev[aidx] : 1.f);
         int lt = 0;
@@ -512,6 +559,21 @@ xpass_tc_pers_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_const
             __syncwarp();
             if (lane == 0) mbar_arrive(su32(&acce[b]));
         }
+    } else {
+        // converter warps (SPLIT): split each data tile once its TMA loads have landed, then release the
+        // stage to the MMA thread (one arrival per warp)
+        const int ct = threadIdx.x - 192;
+        long it = 0;
+        for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x)
+            for (int kb = 0; kb < nk && ok; ++kb, ++it) {
+                const int s = (int)(it % NS);
+                ok = __all_sync(0xffffffffu, mbar_wait(su32(&full[s]), (uint32_t)((it / NS) & 1), wlim));
+                if (!ok) break;
+                float4* a = reinterpret_cast<float4*>(dsm + (base - raw) + (size_t)s * STAGE);
+                split_tile(a, a + AOFF_LO / 16, ct);
+                __syncwarp();
+                if (lane == 0) mbar_arrive(su32(&conv[s]));
+            }
     }
     if (!ok) {
         atomicOr(status, (unsigned)HELM_DEV_WAIT);
@@ -533,15 +595,26 @@ xpass_tc_pers_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_const
 // SM.  Tiles are ordered (slice, column block, row block) with the row block fastest, so that the two row
 // blocks of a data tile run at the same time on neighbouring CTAs and share it in L2.  Barriers as in the
 // persistent x-pass.
-constexpr int YPS = 4;                                         // pipeline stages
-constexpr size_t YP_SMEM = (size_t)YPS * 3 * TILE + 4 * 32 * YEPI_LD * 4 + 1024;
+// pipeline stages and shared memory; the split (3xTF32) form adds the remainders of W and of the data tile
+template <bool SPLIT>
+struct PersY {
+    static constexpr int STAGES = SPLIT ? 2 : 4;
+    static constexpr int STAGE_BYTES = (SPLIT ? 6 : 3) * TILE;
+    static constexpr size_t SMEM = (size_t)STAGES * STAGE_BYTES + 4 * 32 * YEPI_LD * 4 + 1024;
+};
 
-__global__ void __launch_bounds__(192, 1)
+// SPLIT: 3xTF32 with tmWl the remainder of W; 320 threads, warps 6-9 split the data tiles.
+// Stage layout: [Wr | Wi | D] (TF32), [Wr hi | Wi hi | D hi | Wr lo | Wi lo | D lo] (SPLIT); D is 4 boxes of
+// 32 K-rows x 128 bytes.
+template <bool SPLIT>
+__global__ void __launch_bounds__(SPLIT ? 320 : 192, 1)
 ypass_tc_pers_kernel(const __grid_constant__ CUtensorMap tmW, const __grid_constant__ CUtensorMap tmY,
-                     float* __restrict__ out, int ny, int N2, int nz, unsigned* status, long wlim) {
+                     const __grid_constant__ CUtensorMap tmWl, float* __restrict__ out, int ny, int N2, int nz,
+                     unsigned* status, long wlim) {
     extern __shared__ uint8_t dsm[];
-    constexpr int STAGE = 3 * TILE;   // Wr tile, Wi tile, B tile (4 boxes of 32 K-rows x 128 bytes)
-    __shared__ __align__(8) uint64_t full[YPS], empty[YPS], accf[2], acce[2], drainb;
+    constexpr int YPS = PersY<SPLIT>::STAGES, STAGE = PersY<SPLIT>::STAGE_BYTES;
+    constexpr int WLO = 3 * TILE, DLO = 5 * TILE;
+    __shared__ __align__(8) uint64_t full[YPS], empty[YPS], conv[YPS], accf[2], acce[2], drainb;
     __shared__ int fail_any;
     __shared__ uint32_t tslot;
     const uint32_t raw = su32(dsm);
@@ -551,7 +624,11 @@ ypass_tc_pers_kernel(const __grid_constant__ CUtensorMap tmW, const __grid_const
     const int ntm = (ny + BM - 1) / BM, ntn = (N2 + BN - 1) / BN, ntiles = ntm * ntn * nz;
     float* epi = reinterpret_cast<float*>(dsm + (base - raw) + YPS * STAGE);   // epilogue staging rows
     if (threadIdx.x == 0) {
-        for (int s = 0; s < YPS; ++s) { mbar_init(su32(&full[s]), 1); mbar_init(su32(&empty[s]), 1); }
+        for (int s = 0; s < YPS; ++s) {
+            mbar_init(su32(&full[s]), 1);
+            mbar_init(su32(&empty[s]), 1);
+            mbar_init(su32(&conv[s]), 4);
+        }
         for (int b = 0; b < 2; ++b) { mbar_init(su32(&accf[b]), 1); mbar_init(su32(&acce[b]), 4); }
         mbar_init(su32(&drainb), 1);
         fail_any = 0;
@@ -580,9 +657,13 @@ ypass_tc_pers_kernel(const __grid_constant__ CUtensorMap tmW, const __grid_const
                     if (it >= YPS) ok = mbar_wait(su32(&empty[s]), ph ^ 1, wlim);
                     if (!ok) break;
                     const uint32_t sw = base + s * STAGE, sb = sw + 2 * TILE;
-                    mbar_expect_tx(su32(&full[s]), STAGE);
+                    mbar_expect_tx(su32(&full[s]), SPLIT ? 5 * TILE : STAGE);
                     tma_3d(sw, &tmW, su32(&full[s]), kb * BK, m0, 0);
                     tma_3d(sw + TILE, &tmW, su32(&full[s]), kb * BK, m0, 1);
+                    if (SPLIT) {
+                        tma_3d(sw + WLO, &tmWl, su32(&full[s]), kb * BK, m0, 0);
+                        tma_3d(sw + WLO + TILE, &tmWl, su32(&full[s]), kb * BK, m0, 1);
+                    }
 #pragma unroll
                     for (int q = 0; q < BN / 32; ++q) tma_3d(sb + q * 4096, &tmY, su32(&full[s]), n0 + 32 * q, kb * BK, l);
                     ++issued;
@@ -603,7 +684,7 @@ ypass_tc_pers_kernel(const __grid_constant__ CUtensorMap tmW, const __grid_const
                 for (int kb = 0; kb < nk && ok; ++kb, ++it) {
                     const int s = (int)(it % YPS);
                     const uint32_t ph = (uint32_t)((it / YPS) & 1);
-                    ok = mbar_wait(su32(&full[s]), ph, wlim);
+                    ok = mbar_wait(su32(SPLIT ? &conv[s] : &full[s]), ph, wlim);
                     if (!ok) break;
                     fence_after();
                     const uint32_t sw = base + s * STAGE, sb = sw + 2 * TILE;
@@ -611,16 +692,28 @@ ypass_tc_pers_kernel(const __grid_constant__ CUtensorMap tmW, const __grid_const
                     for (int kk = 0; kk < BK / 8; ++kk) {
                         // MN-major: LBO = next 32-column chunk (4 KiB), SBO = next 4-row K group (512 B)
                         const uint64_t bd = sdesc(sb + kk * 1024, 4096, 512, 1);
+                        const uint64_t wr = sdesc(sw + kk * 32, 16, 1024), wi = sdesc(sw + TILE + kk * 32, 16, 1024);
                         const uint32_t acc = (kb | kk) ? 1u : 0u;
-                        mma_tf32(accP, sdesc(sw + kk * 32, 16, 1024), bd, idesc, acc);
-                        mma_tf32(accQ, sdesc(sw + TILE + kk * 32, 16, 1024), bd, idesc, acc);
+                        if (SPLIT) {
+                            // small products first: hi_W lo_D + lo_W hi_D + hi_W hi_D
+                            const uint64_t bl = sdesc(sw + DLO + kk * 1024, 4096, 512, 1);
+                            mma_tf32(accP, wr, bl, idesc, acc);
+                            mma_tf32(accQ, wi, bl, idesc, acc);
+                            mma_tf32(accP, sdesc(sw + WLO + kk * 32, 16, 1024), bd, idesc, 1u);
+                            mma_tf32(accQ, sdesc(sw + WLO + TILE + kk * 32, 16, 1024), bd, idesc, 1u);
+                            mma_tf32(accP, wr, bd, idesc, 1u);
+                            mma_tf32(accQ, wi, bd, idesc, 1u);
+                        } else {
+                            mma_tf32(accP, wr, bd, idesc, acc);
+                            mma_tf32(accQ, wi, bd, idesc, acc);
+                        }
                     }
                     mma_commit(su32(&empty[s]));
                 }
                 if (ok) mma_commit(su32(&accf[b]));
             }
         }
-    } else {
+    } else if (!SPLIT || warp < 6) {
         const int q = warp & 3;
         float* stg = epi + q * 32 * YEPI_LD;
         int lt = 0;
@@ -667,6 +760,20 @@ ypass_tc_pers_kernel(const __grid_constant__ CUtensorMap tmW, const __grid_const
             __syncwarp();
             if (lane == 0) mbar_arrive(su32(&acce[b]));
         }
+    } else {
+        // converter warps (SPLIT): split each data tile once its TMA loads have landed
+        const int ct = threadIdx.x - 192;
+        long it = 0;
+        for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x)
+            for (int kb = 0; kb < nk && ok; ++kb, ++it) {
+                const int s = (int)(it % YPS);
+                ok = __all_sync(0xffffffffu, mbar_wait(su32(&full[s]), (uint32_t)((it / YPS) & 1), wlim));
+                if (!ok) break;
+                unsigned char* st = dsm + (base - raw) + (size_t)s * STAGE;
+                split_tile(reinterpret_cast<float4*>(st + 2 * TILE), reinterpret_cast<float4*>(st + DLO), ct);
+                __syncwarp();
+                if (lane == 0) mbar_arrive(su32(&conv[s]));
+            }
     }
     if (!ok) {
         atomicOr(status, (unsigned)HELM_DEV_WAIT);
@@ -684,33 +791,40 @@ ypass_tc_pers_kernel(const __grid_constant__ CUtensorMap tmW, const __grid_const
 }
 
 // ---- operand preparation (set-up) ----------------------------------------------------------------
+// v rounded to TF32 (hi) and, when lo is wanted, the TF32 rounding of the remainder v - hi
 __device__ __forceinline__ float to_tf32(double v) {
     uint32_t r;
     asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"((float)v));
     return __uint_as_float(r);
 }
+__device__ __forceinline__ void put_split(float* hi, float* lo, size_t i, double v) {
+    const float h = to_tf32(v);
+    hi[i] = h;
+    if (lo) lo[i] = to_tf32(v - (double)h);
+}
 
-// B[2n][2k] from W_kn = src[n][k] (src row-major N x N complex128)
-__global__ void embed_x_kernel(int N, const double2* __restrict__ src, float* __restrict__ B) {
+// B[2n][2k] from W_kn = src[n][k] (src row-major N x N complex128); Bl (may be NULL) the remainders
+__global__ void embed_x_kernel(int N, const double2* __restrict__ src, float* __restrict__ B, float* __restrict__ Bl) {
     const size_t id = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
     if (id >= (size_t)N * N) return;
     const int n = (int)(id / N), k = (int)(id % N);
     const double2 w = src[(size_t)n * N + k];
     const size_t L2 = 2 * (size_t)N;
-    B[(2 * n) * L2 + 2 * k] = to_tf32(w.x);
-    B[(2 * n) * L2 + 2 * k + 1] = to_tf32(-w.y);
-    B[(2 * n + 1) * L2 + 2 * k] = to_tf32(w.y);
-    B[(2 * n + 1) * L2 + 2 * k + 1] = to_tf32(w.x);
+    put_split(B, Bl, (2 * n) * L2 + 2 * k, w.x);
+    put_split(B, Bl, (2 * n) * L2 + 2 * k + 1, -w.y);
+    put_split(B, Bl, (2 * n + 1) * L2 + 2 * k, w.y);
+    put_split(B, Bl, (2 * n + 1) * L2 + 2 * k + 1, w.x);
 }
 
-// W planes: re at [0][j'][j], im at [1][j'][j], row stride ldw (zero padded)
-__global__ void split_y_kernel(int N, int ldw, const double2* __restrict__ src, float* __restrict__ W) {
+// W planes: re at [0][j'][j], im at [1][j'][j], row stride ldw (zero padded); Wl (may be NULL) the remainders
+__global__ void split_y_kernel(int N, int ldw, const double2* __restrict__ src, float* __restrict__ W,
+                               float* __restrict__ Wl) {
     const size_t id = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
     if (id >= (size_t)N * ldw) return;
     const int r = (int)(id / ldw), k = (int)(id % ldw);
     const double2 w = k < N ? src[(size_t)r * N + k] : make_double2(0.0, 0.0);
-    W[(size_t)r * ldw + k] = to_tf32(w.x);
-    W[(size_t)N * ldw + (size_t)r * ldw + k] = to_tf32(w.y);
+    put_split(W, Wl, (size_t)r * ldw + k, w.x);
+    put_split(W, Wl, (size_t)N * ldw + (size_t)r * ldw + k, w.y);
 }
 
 helm_status encode(TcState* t, CUtensorMap* map, int rank, void* ptr, const cuuint64_t* dims, const cuuint64_t* strides,
@@ -726,15 +840,36 @@ size_t xsmem() { return (size_t)XSTAGES * 2 * TILE + 1024; }
 size_t ysmem() { return (size_t)YSTAGES * 3 * TILE + 1024; }
 int g_sms = 0;
 
+template <typename K>
+cudaError_t smem_attr(K kernel, size_t bytes) {
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+// the x-pass and y-pass operands of set i from FP64 sources (x: W_kn = srcx[n][k]; y: srcy)
+helm_status tc_fill_set(TcState* t, int nx, int ny, int i, const double2* srcx, const double2* srcy, cudaStream_t s) {
+    const size_t nb = (size_t)4 * nx * nx, nw = (size_t)2 * ny * t->ldw;
+    if (cudaMalloc(&t->Bx[i], nb * sizeof(float)) != cudaSuccess) { cudaGetLastError(); return HELM_ERR_NOMEM; }
+    if (cudaMalloc(&t->Wy[i], nw * sizeof(float)) != cudaSuccess) { cudaGetLastError(); return HELM_ERR_NOMEM; }
+    if (t->split) {
+        if (cudaMalloc(&t->Bxl[i], nb * sizeof(float)) != cudaSuccess) { cudaGetLastError(); return HELM_ERR_NOMEM; }
+        if (cudaMalloc(&t->Wyl[i], nw * sizeof(float)) != cudaSuccess) { cudaGetLastError(); return HELM_ERR_NOMEM; }
+    }
+    embed_x_kernel<<<(unsigned)((nx * (size_t)nx + 255) / 256), 256, 0, s>>>(nx, srcx, t->Bx[i], t->Bxl[i]);
+    split_y_kernel<<<(unsigned)((ny * (size_t)t->ldw + 255) / 256), 256, 0, s>>>(ny, t->ldw, srcy, t->Wy[i], t->Wyl[i]);
+    HELM_CUDA_TRY(cudaGetLastError());
+    return HELM_OK;
+}
+
 }  // namespace
 
 helm_status tc_encode_set(TcState* t, int nx, int ny, int i);
 
 helm_status tc_prepare(helm_ctx* c, cudaStream_t s) {
     if (c->nx % 2 != 0) return HELM_ERR_UNSUPPORTED;
-    if (c->opt.precision != HELM_PREC_TF32) return HELM_ERR_UNSUPPORTED;
+    if (c->opt.precision != HELM_PREC_TF32 && c->opt.precision != HELM_PREC_TF32X3) return HELM_ERR_UNSUPPORTED;
     TcState* t = new TcState();
     c->tmaps = t;
+    t->split = c->opt.precision == HELM_PREC_TF32X3;
     cudaDriverEntryPointQueryResult q;
     if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", (void**)&t->encode, 12000, cudaEnableDefault, &q) !=
             cudaSuccess || q != cudaDriverEntryPointSuccess || !t->encode) {
@@ -742,28 +877,21 @@ helm_status tc_prepare(helm_ctx* c, cudaStream_t s) {
         return HELM_ERR_CUDA;
     }
     const int nx = c->nx, ny = c->ny;
-    const size_t nb = (size_t)4 * nx * nx;
     t->ldw = (ny + 3) / 4 * 4;
-    const size_t nw = (size_t)2 * ny * t->ldw;
-    for (int i = 0; i < 2; ++i) {
-        if (cudaMalloc(&t->Bx[i], nb * sizeof(float)) != cudaSuccess) { cudaGetLastError(); return HELM_ERR_NOMEM; }
-        if (cudaMalloc(&t->Wy[i], nw * sizeof(float)) != cudaSuccess) { cudaGetLastError(); return HELM_ERR_NOMEM; }
-    }
-    // forward: W_kn = Vxi[n][k]; inverse: W_kn = Vx[n][k]
-    embed_x_kernel<<<(unsigned)((nx * (size_t)nx + 255) / 256), 256, 0, s>>>(nx, c->Vxi, t->Bx[0]);
-    embed_x_kernel<<<(unsigned)((nx * (size_t)nx + 255) / 256), 256, 0, s>>>(nx, c->Vx, t->Bx[1]);
-    split_y_kernel<<<(unsigned)((ny * (size_t)t->ldw + 255) / 256), 256, 0, s>>>(ny, t->ldw, c->Vyi, t->Wy[0]);
-    split_y_kernel<<<(unsigned)((ny * (size_t)t->ldw + 255) / 256), 256, 0, s>>>(ny, t->ldw, c->Vy, t->Wy[1]);
-    HELM_CUDA_TRY(cudaGetLastError());
+    helm_status st;
+    // forward: W_kn = Vxi[n][k], V_y^-1; inverse: W_kn = Vx[n][k], V_y
+    if ((st = tc_fill_set(t, nx, ny, 0, c->Vxi, c->Vyi, s)) != HELM_OK) return st;
+    if ((st = tc_fill_set(t, nx, ny, 1, c->Vx, c->Vy, s)) != HELM_OK) return st;
     for (int i = 0; i < 2; ++i)
         if (tc_encode_set(t, nx, ny, i) != HELM_OK) return HELM_ERR_CUDA;
-    HELM_CUDA_TRY(cudaFuncSetAttribute(xpass_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)xsmem()));
-    HELM_CUDA_TRY(cudaFuncSetAttribute(ypass_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ysmem()));
-    HELM_CUDA_TRY(cudaFuncSetAttribute(ypass_tc_pers_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)YP_SMEM));
-    HELM_CUDA_TRY(cudaFuncSetAttribute(xpass_tc_pers_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)PersX<128>::SMEM));
-    HELM_CUDA_TRY(cudaFuncSetAttribute(xpass_tc_pers_kernel<256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)PersX<256>::SMEM));
+    HELM_CUDA_TRY(smem_attr(xpass_tc_kernel, xsmem()));
+    HELM_CUDA_TRY(smem_attr(ypass_tc_kernel, ysmem()));
+    HELM_CUDA_TRY(smem_attr(ypass_tc_pers_kernel<false>, PersY<false>::SMEM));
+    HELM_CUDA_TRY(smem_attr(ypass_tc_pers_kernel<true>, PersY<true>::SMEM));
+    HELM_CUDA_TRY(smem_attr(xpass_tc_pers_kernel<128, false>, PersX<128, false>::SMEM));
+    HELM_CUDA_TRY(smem_attr(xpass_tc_pers_kernel<256, false>, PersX<256, false>::SMEM));
+    HELM_CUDA_TRY(smem_attr(xpass_tc_pers_kernel<128, true>, PersX<128, true>::SMEM));
+    HELM_CUDA_TRY(smem_attr(xpass_tc_pers_kernel<256, true>, PersX<256, true>::SMEM));
     HELM_CUDA_TRY(cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, c->device));
     return HELM_OK;
 }
@@ -773,15 +901,18 @@ helm_status tc_encode_set(TcState* t, int nx, int ny, int i) {
     const cuuint64_t d[2] = {(cuuint64_t)2 * nx, (cuuint64_t)2 * nx};
     const cuuint64_t st[1] = {(cuuint64_t)2 * nx * sizeof(float)};
     const cuuint32_t box[2] = {BK, BN};
-    if (encode(t, &t->mapBx[i], 2, t->Bx[i], d, st, box) != HELM_OK) return HELM_ERR_CUDA;
-    if ((2 * nx) % 256 == 0) {   // the only grids that take 256-wide tiles
-        const cuuint32_t box256[2] = {BK, 256};
-        if (encode(t, &t->mapBx256[i], 2, t->Bx[i], d, st, box256) != HELM_OK) return HELM_ERR_CUDA;
-    }
     const cuuint64_t dw[3] = {(cuuint64_t)ny, (cuuint64_t)ny, 2};
     const cuuint64_t sw[2] = {(cuuint64_t)t->ldw * sizeof(float), (cuuint64_t)t->ldw * ny * sizeof(float)};
     const cuuint32_t bw[3] = {BK, BM, 1};
-    if (encode(t, &t->mapWy[i], 3, t->Wy[i], dw, sw, bw) != HELM_OK) return HELM_ERR_CUDA;
+    const cuuint32_t box256[2] = {BK, 256};
+    for (int h = 0; h < (t->split ? 2 : 1); ++h) {
+        float* bx = h ? t->Bxl[i] : t->Bx[i];
+        float* wy = h ? t->Wyl[i] : t->Wy[i];
+        if (encode(t, h ? &t->mapBxl[i] : &t->mapBx[i], 2, bx, d, st, box) != HELM_OK) return HELM_ERR_CUDA;
+        if ((2 * nx) % 256 == 0)   // the only grids that take 256-wide tiles
+            if (encode(t, h ? &t->mapBx256l[i] : &t->mapBx256[i], 2, bx, d, st, box256) != HELM_OK) return HELM_ERR_CUDA;
+        if (encode(t, h ? &t->mapWyl[i] : &t->mapWy[i], 3, wy, dw, sw, bw) != HELM_OK) return HELM_ERR_CUDA;
+    }
     return HELM_OK;
 }
 
@@ -792,18 +923,11 @@ helm_status tc_prepare_sine(helm_ctx* c, const double2* Sx, const double2* Sy, c
     TcState* t = (TcState*)c->tmaps;
     if (!t) return HELM_ERR_UNSUPPORTED;
     const int nx = c->nx, ny = c->ny;
-    const size_t nb = (size_t)4 * nx * nx, nw = (size_t)2 * ny * t->ldw;
-    for (int i = 2; i < 4; ++i) {
-        if (cudaMalloc(&t->Bx[i], nb * sizeof(float)) != cudaSuccess) { cudaGetLastError(); return HELM_ERR_NOMEM; }
-        if (cudaMalloc(&t->Wy[i], nw * sizeof(float)) != cudaSuccess) { cudaGetLastError(); return HELM_ERR_NOMEM; }
-    }
-    // x-pass computes row . src^T: forward wants row . S_x (src = S_x^T), inverse row . S_x^T (src = S_x)
-    embed_x_kernel<<<(unsigned)((nx * (size_t)nx + 255) / 256), 256, 0, s>>>(nx, SxT, t->Bx[2]);
-    embed_x_kernel<<<(unsigned)((nx * (size_t)nx + 255) / 256), 256, 0, s>>>(nx, Sx, t->Bx[3]);
+    helm_status st;
+    // x-pass computes row . src^T: forward wants row . S_x (src = S_x^T), inverse row . S_x^T (src = S_x);
     // y-pass computes src . slice: forward S_y^T, inverse S_y
-    split_y_kernel<<<(unsigned)((ny * (size_t)t->ldw + 255) / 256), 256, 0, s>>>(ny, t->ldw, SyT, t->Wy[2]);
-    split_y_kernel<<<(unsigned)((ny * (size_t)t->ldw + 255) / 256), 256, 0, s>>>(ny, t->ldw, Sy, t->Wy[3]);
-    HELM_CUDA_TRY(cudaGetLastError());
+    if ((st = tc_fill_set(t, nx, ny, 2, SxT, SyT, s)) != HELM_OK) return st;
+    if ((st = tc_fill_set(t, nx, ny, 3, Sx, Sy, s)) != HELM_OK) return st;
     for (int i = 2; i < 4; ++i)
         if (tc_encode_set(t, nx, ny, i) != HELM_OK) return HELM_ERR_CUDA;
     return HELM_OK;
@@ -820,22 +944,37 @@ helm_status tc_xpass(helm_ctx* c, int inverse, const float2* in, float2* out, fl
     const cuuint32_t box[2] = {BK, BM};
     if (encode(t, &mapA, 2, (void*)in, d, st, box) != HELM_OK) return HELM_ERR_CUDA;
     dim3 grid((N2 + BN - 1) / BN, (M + BM - 1) / BM);
-    if (c->tune_tc == 1 && g_sms > 0) {
+    const long wl = (long)c->wait_limit;
+    float* o = (float*)out;
+    if (t->split && g_sms > 0) {
+        // 3xTF32: persistent kernels only
+        if (N2 % 256 == 0) {
+            const int ntiles = (N2 / 256) * (int)grid.y;
+            const int pg = ntiles < g_sms ? ntiles : g_sms;
+            xpass_tc_pers_kernel<256, true><<<pg, 320, PersX<256, true>::SMEM, s>>>(
+                mapA, t->mapBx256[inverse], t->mapBx256l[inverse], o, M, N2, N2, alpha, alpha_dev, aidx, c->status_d, wl);
+        } else {
+            const int ntiles = (int)(grid.x * grid.y);
+            const int pg = ntiles < g_sms ? ntiles : g_sms;
+            xpass_tc_pers_kernel<128, true><<<pg, 320, PersX<128, true>::SMEM, s>>>(
+                mapA, t->mapBx[inverse], t->mapBxl[inverse], o, M, N2, N2, alpha, alpha_dev, aidx, c->status_d, wl);
+        }
+    } else if (c->tune_tc == 1 && g_sms > 0) {
         if (N2 % 256 == 0) {
             // 256-wide tiles, one CTA per SM
             const int ntiles = (N2 / 256) * (int)grid.y;
             const int pg = ntiles < g_sms ? ntiles : g_sms;
-            xpass_tc_pers_kernel<256><<<pg, 192, PersX<256>::SMEM, s>>>(mapA, t->mapBx256[inverse], (float*)out, M, N2,
-                                                                         N2, alpha, alpha_dev, aidx, c->status_d, (long)c->wait_limit);
+            xpass_tc_pers_kernel<256, false><<<pg, 192, PersX<256, false>::SMEM, s>>>(
+                mapA, t->mapBx256[inverse], t->mapBx256[inverse], o, M, N2, N2, alpha, alpha_dev, aidx, c->status_d, wl);
         } else {
             const int ntiles = (int)(grid.x * grid.y);
             const int pg = ntiles < 2 * g_sms ? ntiles : 2 * g_sms;
-            xpass_tc_pers_kernel<128><<<pg, 192, PersX<128>::SMEM, s>>>(mapA, t->mapBx[inverse], (float*)out, M, N2,
-                                                                         N2, alpha, alpha_dev, aidx, c->status_d, (long)c->wait_limit);
+            xpass_tc_pers_kernel<128, false><<<pg, 192, PersX<128, false>::SMEM, s>>>(
+                mapA, t->mapBx[inverse], t->mapBx[inverse], o, M, N2, N2, alpha, alpha_dev, aidx, c->status_d, wl);
         }
     } else {
-        xpass_tc_kernel<<<grid, 192, xsmem(), s>>>(mapA, t->mapBx[inverse], (float*)out, M, N2, N2, alpha, alpha_dev,
-                                                    aidx, c->status_d, (long)c->wait_limit);
+        xpass_tc_kernel<<<grid, 192, xsmem(), s>>>(mapA, t->mapBx[inverse], o, M, N2, N2, alpha, alpha_dev, aidx,
+                                                    c->status_d, wl);
     }
     HELM_CUDA_TRY(cudaGetLastError());
     return HELM_OK;
@@ -851,12 +990,17 @@ helm_status tc_ypass(helm_ctx* c, int inverse, const float2* in, float2* out, cu
     const cuuint32_t box[3] = {32, BK, 1};
     if (encode(t, &mapY, 3, (void*)in, d, st, box, CU_TENSOR_MAP_SWIZZLE_128B_ATOM_32B) != HELM_OK) return HELM_ERR_CUDA;
     dim3 grid((N2 + BN - 1) / BN, (ny + BM - 1) / BM, c->nz);
-    if (c->tune_ypers && g_sms > 0) {
-        const int ntiles = (int)(grid.x * grid.y * grid.z);
-        const int pg = ntiles < g_sms ? ntiles : g_sms;
-        ypass_tc_pers_kernel<<<pg, 192, YP_SMEM, s>>>(t->mapWy[inverse], mapY, (float*)out, ny, N2, c->nz, c->status_d, (long)c->wait_limit);
+    const long wl = (long)c->wait_limit;
+    const int ntiles = (int)(grid.x * grid.y * grid.z);
+    const int pg = g_sms > 0 && ntiles > g_sms ? g_sms : ntiles;
+    if (t->split && g_sms > 0) {
+        ypass_tc_pers_kernel<true><<<pg, 320, PersY<true>::SMEM, s>>>(t->mapWy[inverse], mapY, t->mapWyl[inverse],
+                                                                     (float*)out, ny, N2, c->nz, c->status_d, wl);
+    } else if (c->tune_ypers && g_sms > 0) {
+        ypass_tc_pers_kernel<false><<<pg, 192, PersY<false>::SMEM, s>>>(t->mapWy[inverse], mapY, t->mapWy[inverse],
+                                                                       (float*)out, ny, N2, c->nz, c->status_d, wl);
     } else {
-        ypass_tc_kernel<<<grid, 192, ysmem(), s>>>(t->mapWy[inverse], mapY, (float*)out, ny, N2, c->status_d, (long)c->wait_limit);
+        ypass_tc_kernel<<<grid, 192, ysmem(), s>>>(t->mapWy[inverse], mapY, (float*)out, ny, N2, c->status_d, wl);
     }
     HELM_CUDA_TRY(cudaGetLastError());
     return HELM_OK;
@@ -865,7 +1009,12 @@ helm_status tc_ypass(helm_ctx* c, int inverse, const float2* in, float2* out, cu
 void tc_release(helm_ctx* c) {
     TcState* t = (TcState*)c->tmaps;
     if (!t) return;
-    for (int i = 0; i < 4; ++i) { cudaFree(t->Bx[i]); cudaFree(t->Wy[i]); }
+    for (int i = 0; i < 4; ++i) {
+        cudaFree(t->Bx[i]);
+        cudaFree(t->Wy[i]);
+        cudaFree(t->Bxl[i]);
+        cudaFree(t->Wyl[i]);
+    }
     delete t;
     c->tmaps = nullptr;
 }

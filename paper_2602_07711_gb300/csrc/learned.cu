@@ -12,12 +12,15 @@
 // Activations and weights are stored in BF16, every product is accumulated in FP32; training keeps FP32
 // master weights, FP32 activation gradients and Adam moments.  Layout [B][C][Z][Y][X].
 //
-// Kernels (written here): direct 3x3x3 convolution with a shared-memory halo tile per input channel
-// (forward, and data-gradient through flipped/transposed weights with the ReLU mask fused), weight
-// gradient as a tiled reduction with one atomic per CTA and tap, pooling/upsampling and their adjoints,
-// MSE, Adam, feature assembly and the correction step.
+// Kernels: the 3x3x3 convolutions run on the tcgen05 tensor cores as implicit GEMMs (conv_tc.cu: forward
+// and data gradient through flipped/transposed weights with the ReLU mask fused, weight gradient with the
+// taps' accumulators in tensor memory) whenever a layer has at most 64 outputs (widths up to 32); wider
+// layers take the direct kernels written here (a shared-memory halo tile per input channel, and the
+// weight gradient as a tiled reduction with one atomic per CTA and tap).  Also here: pooling/upsampling and
+// their adjoints, MSE, Adam, feature assembly and the correction step.
 #include "common.cuh"
 #include <cuda_bf16.h>
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -46,7 +49,21 @@ struct helm_net {
     // solver-side fields (complex64, one grid): v = sigma r, c, A M^-1 v, A c
     float2 *vbuf = nullptr, *cbuf = nullptr, *az0 = nullptr, *ac = nullptr;
     size_t fcap = 0;
+    bf16* wscr = nullptr;          // weights arranged for the tensor-core convolutions (one layer at a time)
+    unsigned* status = nullptr;    // device status word of the network's own calls (bounded waits)
 };
+
+// conv_tc.cu
+bool conv_tc_supported(int Cin, int Cout);
+bool wgrad_tc_supported(int Cin, int Cout);
+size_t conv_tc_scratch_bytes(int Cin, int Cout);
+helm_status conv_tc_prepare();
+template <typename TIN, typename TOUT>
+helm_status conv_tc(const TIN* in, int Cin, size_t in_bs, const __nv_bfloat16* w, int wmode, const float* bias,
+                    TOUT* out, int Cout, size_t out_bs, int B, int Z, int Y, int X, int relu,
+                    const __nv_bfloat16* mask, size_t mask_bs, __nv_bfloat16* wscr, unsigned* status, cudaStream_t s);
+helm_status wgrad_tc(const __nv_bfloat16* in, int Cin, size_t in_bs, const float* g, int Cout, size_t g_bs, int B, int Z,
+                     int Y, int X, float* gw, float* gb, unsigned* status, cudaStream_t s);
 
 namespace {
 
@@ -419,17 +436,28 @@ __global__ void target_kernel(const double2* __restrict__ xs, const double2* __r
 
 unsigned nblk(size_t n) { const size_t b = (n + 255) / 256; return (unsigned)(b > 4096 ? 4096 : b); }
 
+// the convolution of a layer: tensor cores where the shape allows, else the direct kernel
 template <typename TIN, typename TOUT>
-void conv(const TIN* in, int Cin, size_t in_bs, const bf16* w, int wmode, const float* bias, TOUT* out, int Cout,
-          size_t out_bs, int B, int Z, int Y, int X, int relu, const bf16* mask, size_t mask_bs, cudaStream_t s) {
+void conv(helm_net* n, const TIN* in, int Cin, size_t in_bs, const bf16* w, int wmode, const float* bias, TOUT* out,
+          int Cout, size_t out_bs, int B, int Z, int Y, int X, int relu, const bf16* mask, size_t mask_bs,
+          unsigned* status, cudaStream_t s) {
+    if (conv_tc_supported(Cin, Cout)) {
+        conv_tc<TIN, TOUT>(in, Cin, in_bs, w, wmode, bias, out, Cout, out_bs, B, Z, Y, X, relu, mask, mask_bs, n->wscr,
+                           status, s);
+        return;
+    }
     const int ntx = (X + TXC - 1) / TXC, nty = (Y + TYC - 1) / TYC, ntz = (Z + TZC - 1) / TZC;
     dim3 grid(ntx * nty, ntz, B * ((Cout + COT - 1) / COT));
     conv3_kernel<TIN, TOUT><<<grid, 256, 0, s>>>(in, Cin, in_bs, w, wmode, bias, out, Cout, out_bs, Z, Y, X, relu, mask,
                                                 mask_bs);
 }
 
-void wgrad(const bf16* in, int Cin, size_t in_bs, const float* g, int Cout, size_t g_bs, int B, int Z, int Y, int X,
-           float* gw, float* gb, cudaStream_t s) {
+void wgrad(helm_net* n, const bf16* in, int Cin, size_t in_bs, const float* g, int Cout, size_t g_bs, int B, int Z,
+           int Y, int X, float* gw, float* gb, cudaStream_t s) {
+    if (wgrad_tc_supported(Cin, Cout)) {
+        wgrad_tc(in, Cin, in_bs, g, Cout, g_bs, B, Z, Y, X, gw, gb, n->status, s);
+        return;
+    }
     dim3 grid(Cin, (Cout + COT - 1) / COT, 16);
     conv3_wgrad_kernel<<<grid, 256, 0, s>>>(in, Cin, in_bs, g, Cout, g_bs, B, Z, Y, X, gw, gb);
 }
@@ -478,24 +506,24 @@ helm_status ensure_grad_ws(helm_net* n) {
     return HELM_OK;
 }
 
-// forward of the workspace input n->x into n->y
-void forward(helm_net* n, cudaStream_t s) {
+// forward of the workspace input n->x into n->y (bounded-wait failures OR-ed into *status)
+void forward(helm_net* n, unsigned* status, cudaStream_t s) {
     const int c = n->c, B = n->B, Z = n->Z, Y = n->Y, X = n->X;
     const size_t vol = (size_t)Z * Y * X, hv = vol / 8;
     const bf16* W = n->Wb;
     const float* F = n->W;
     bf16* a2 = n->u + 2 * c * vol;   // skip channels live inside u
-    conv<bf16, bf16>(n->x, 5, 5 * vol, W + n->woff[0], 0, F + n->boff[0], n->a1, c, c * vol, B, Z, Y, X, 1, nullptr, 0, s);
-    conv<bf16, bf16>(n->a1, c, c * vol, W + n->woff[1], 0, F + n->boff[1], a2, c, 3 * c * vol, B, Z, Y, X, 1, nullptr, 0, s);
+    conv<bf16, bf16>(n, n->x, 5, 5 * vol, W + n->woff[0], 0, F + n->boff[0], n->a1, c, c * vol, B, Z, Y, X, 1, nullptr, 0, status, s);
+    conv<bf16, bf16>(n, n->a1, c, c * vol, W + n->woff[1], 0, F + n->boff[1], a2, c, 3 * c * vol, B, Z, Y, X, 1, nullptr, 0, status, s);
     avgpool2_kernel<<<nblk(B * c * hv), 256, 0, s>>>(a2, 3 * c * vol, n->p, c, B, Z, Y, X);
-    conv<bf16, bf16>(n->p, c, c * hv, W + n->woff[2], 0, F + n->boff[2], n->b1, 2 * c, 2 * c * hv, B, Z / 2, Y / 2, X / 2, 1,
-                     nullptr, 0, s);
-    conv<bf16, bf16>(n->b1, 2 * c, 2 * c * hv, W + n->woff[3], 0, F + n->boff[3], n->b2, 2 * c, 2 * c * hv, B, Z / 2, Y / 2,
-                     X / 2, 1, nullptr, 0, s);
+    conv<bf16, bf16>(n, n->p, c, c * hv, W + n->woff[2], 0, F + n->boff[2], n->b1, 2 * c, 2 * c * hv, B, Z / 2, Y / 2, X / 2, 1,
+                     nullptr, 0, status, s);
+    conv<bf16, bf16>(n, n->b1, 2 * c, 2 * c * hv, W + n->woff[3], 0, F + n->boff[3], n->b2, 2 * c, 2 * c * hv, B, Z / 2, Y / 2,
+                     X / 2, 1, nullptr, 0, status, s);
     upsample2_kernel<<<nblk(B * 2 * c * vol), 256, 0, s>>>(n->b2, n->u, 3 * c * vol, 2 * c, B, Z, Y, X);
-    conv<bf16, bf16>(n->u, 3 * c, 3 * c * vol, W + n->woff[4], 0, F + n->boff[4], n->d1, c, c * vol, B, Z, Y, X, 1, nullptr,
-                     0, s);
-    conv<bf16, float>(n->d1, c, c * vol, W + n->woff[5], 0, F + n->boff[5], n->y, 2, 2 * vol, B, Z, Y, X, 0, nullptr, 0, s);
+    conv<bf16, bf16>(n, n->u, 3 * c, 3 * c * vol, W + n->woff[4], 0, F + n->boff[4], n->d1, c, c * vol, B, Z, Y, X, 1, nullptr,
+                     0, status, s);
+    conv<bf16, float>(n, n->d1, c, c * vol, W + n->woff[5], 0, F + n->boff[5], n->y, 2, 2 * vol, B, Z, Y, X, 0, nullptr, 0, status, s);
 }
 
 }  // namespace
@@ -536,15 +564,23 @@ helm_status helm_net_create(int width, unsigned long long seed, helm_net** out) 
             h[n->woff[l] + k] = (float)(std * sqrt(-2.0 * log(u1)) * cos(2 * M_PI * u2));
         }
     }
+    size_t scr = 0;   // arranged weights of the largest layer, in either direction
+    for (int l = 0; l < 6; ++l) {
+        scr = std::max(scr, conv_tc_scratch_bytes(ci[l], co[l]));
+        scr = std::max(scr, conv_tc_scratch_bytes(co[l], ci[l]));
+    }
     bool ok = cudaMalloc(&n->W, off * 4) == cudaSuccess && cudaMalloc(&n->G, off * 4) == cudaSuccess &&
               cudaMalloc(&n->Mom, off * 4) == cudaSuccess && cudaMalloc(&n->Vel, off * 4) == cudaSuccess &&
-              cudaMalloc(&n->Wb, off * 2) == cudaSuccess && cudaMalloc(&n->stats, 16 * sizeof(double)) == cudaSuccess;
+              cudaMalloc(&n->Wb, off * 2) == cudaSuccess && cudaMalloc(&n->stats, 16 * sizeof(double)) == cudaSuccess &&
+              cudaMalloc(&n->wscr, scr) == cudaSuccess && cudaMalloc(&n->status, sizeof(unsigned)) == cudaSuccess;
     if (!ok) { cudaGetLastError(); helm_net_destroy(n); return HELM_ERR_NOMEM; }
     cudaMemcpy(n->W, h.data(), off * 4, cudaMemcpyHostToDevice);
     cudaMemset(n->G, 0, off * 4);
     cudaMemset(n->Mom, 0, off * 4);
     cudaMemset(n->Vel, 0, off * 4);
     cudaMemset(n->stats, 0, 16 * sizeof(double));
+    cudaMemset(n->status, 0, sizeof(unsigned));
+    if (conv_tc_prepare() != HELM_OK) { cudaGetLastError(); helm_net_destroy(n); return HELM_ERR_CUDA; }
     to_bf16_kernel<<<(unsigned)((off + 255) / 256), 256>>>(n->W, n->Wb, off);
     if (cudaDeviceSynchronize() != cudaSuccess) { cudaGetLastError(); helm_net_destroy(n); return HELM_ERR_CUDA; }
     *out = n;
@@ -554,7 +590,7 @@ helm_status helm_net_create(int width, unsigned long long seed, helm_net** out) 
 void helm_net_destroy(helm_net* n) {
     if (!n) return;
     void* ps[] = {n->W, n->G, n->Mom, n->Vel, n->Wb, n->stats, n->x, n->a1, n->u, n->d1, n->p, n->b1, n->b2, n->y,
-                  n->gA, n->gB, n->gU, n->gH1, n->gH2, n->vbuf, n->cbuf, n->az0, n->ac};
+                  n->gA, n->gB, n->gU, n->gH1, n->gH2, n->vbuf, n->cbuf, n->az0, n->ac, n->wscr, n->status};
     for (void* p : ps) if (p) cudaFree(p);
     delete n;
 }
@@ -576,6 +612,9 @@ helm_status helm_net_get_params(helm_net* n, float* host, size_t count) {
 helm_status helm_net_get_grads(helm_net* n, float* host, size_t count) {
     if (!n || !host || count != n->nparam) return HELM_ERR_ARG;
     HELM_CUDA_TRY(cudaMemcpy(host, n->G, count * 4, cudaMemcpyDeviceToHost));
+    unsigned st = 0;
+    HELM_CUDA_TRY(cudaMemcpy(&st, n->status, sizeof(unsigned), cudaMemcpyDeviceToHost));
+    if (st & HELM_DEV_WAIT) return HELM_ERR_ITER_LIMIT;
     return HELM_OK;
 }
 
@@ -592,7 +631,7 @@ helm_status helm_net_forward(helm_net* n, const void* x, float* y, int B, int Z,
     cudaStream_t s = (cudaStream_t)stream;
     const size_t pts = (size_t)B * Z * Y * X;
     HELM_CUDA_TRY(cudaMemcpyAsync(n->x, x, 5 * pts * 2, cudaMemcpyDeviceToDevice, s));
-    forward(n, s);
+    forward(n, n->status, s);
     HELM_CUDA_TRY(cudaMemcpyAsync(y, n->y, 2 * pts * 4, cudaMemcpyDeviceToDevice, s));
     HELM_CUDA_TRY(cudaGetLastError());
     return HELM_OK;
@@ -609,29 +648,29 @@ helm_status helm_net_backward(helm_net* n, const float* gy, void* stream) {
     float* G = n->G;
     const bf16* a2 = n->u + 2 * c * vol;
     // layer 6 (linear): d1 gradient with the ReLU mask of d1
-    wgrad(n->d1, c, c * vol, gy, 2, 2 * vol, B, Z, Y, X, G + n->woff[5], G + n->boff[5], s);
-    conv<float, float>(gy, 2, 2 * vol, W + n->woff[5], 1, nullptr, n->gB, c, c * vol, B, Z, Y, X, 0, n->d1, c * vol, s);
+    wgrad(n, n->d1, c, c * vol, gy, 2, 2 * vol, B, Z, Y, X, G + n->woff[5], G + n->boff[5], s);
+    conv<float, float>(n, gy, 2, 2 * vol, W + n->woff[5], 1, nullptr, n->gB, c, c * vol, B, Z, Y, X, 0, n->d1, c * vol, n->status, s);
     // layer 5: u gradient (no mask: u mixes up(b2) and a2, masks applied below)
-    wgrad(n->u, 3 * c, 3 * c * vol, n->gB, c, c * vol, B, Z, Y, X, G + n->woff[4], G + n->boff[4], s);
-    conv<float, float>(n->gB, c, c * vol, W + n->woff[4], 1, nullptr, n->gU, 3 * c, 3 * c * vol, B, Z, Y, X, 0, nullptr, 0, s);
+    wgrad(n, n->u, 3 * c, 3 * c * vol, n->gB, c, c * vol, B, Z, Y, X, G + n->woff[4], G + n->boff[4], s);
+    conv<float, float>(n, n->gB, c, c * vol, W + n->woff[4], 1, nullptr, n->gU, 3 * c, 3 * c * vol, B, Z, Y, X, 0, nullptr, 0, n->status, s);
     // up branch: adjoint of upsample2 with the ReLU mask of b2
     upsample2_adj_kernel<<<nblk(B * 2 * c * hv), 256, 0, s>>>(n->gU, 3 * c * vol, n->b2, n->gH1, 2 * c, B, Z, Y, X);
     // layer 4: b1 gradient with mask(b1)
-    wgrad(n->b1, 2 * c, 2 * c * hv, n->gH1, 2 * c, 2 * c * hv, B, Z / 2, Y / 2, X / 2, G + n->woff[3], G + n->boff[3], s);
-    conv<float, float>(n->gH1, 2 * c, 2 * c * hv, W + n->woff[3], 1, nullptr, n->gH2, 2 * c, 2 * c * hv, B, Z / 2, Y / 2,
-                       X / 2, 0, n->b1, 2 * c * hv, s);
+    wgrad(n, n->b1, 2 * c, 2 * c * hv, n->gH1, 2 * c, 2 * c * hv, B, Z / 2, Y / 2, X / 2, G + n->woff[3], G + n->boff[3], s);
+    conv<float, float>(n, n->gH1, 2 * c, 2 * c * hv, W + n->woff[3], 1, nullptr, n->gH2, 2 * c, 2 * c * hv, B, Z / 2, Y / 2,
+                       X / 2, 0, n->b1, 2 * c * hv, n->status, s);
     // layer 3: p gradient (no ReLU on p) into gH1 (c channels)
-    wgrad(n->p, c, c * hv, n->gH2, 2 * c, 2 * c * hv, B, Z / 2, Y / 2, X / 2, G + n->woff[2], G + n->boff[2], s);
-    conv<float, float>(n->gH2, 2 * c, 2 * c * hv, W + n->woff[2], 1, nullptr, n->gH1, c, c * hv, B, Z / 2, Y / 2, X / 2, 0,
-                       nullptr, 0, s);
+    wgrad(n, n->p, c, c * hv, n->gH2, 2 * c, 2 * c * hv, B, Z / 2, Y / 2, X / 2, G + n->woff[2], G + n->boff[2], s);
+    conv<float, float>(n, n->gH2, 2 * c, 2 * c * hv, W + n->woff[2], 1, nullptr, n->gH1, c, c * hv, B, Z / 2, Y / 2, X / 2, 0,
+                       nullptr, 0, n->status, s);
     // a2 gradient: skip part + adjoint of avgpool2, masked by a2
     skip_grad_kernel<<<nblk(B * c * vol), 256, 0, s>>>(n->gU + 2 * c * vol, 3 * c * vol, n->gH1, a2, 3 * c * vol, n->gA, c,
                                                        B, Z, Y, X);
     // layer 2: a1 gradient with mask(a1)
-    wgrad(n->a1, c, c * vol, n->gA, c, c * vol, B, Z, Y, X, G + n->woff[1], G + n->boff[1], s);
-    conv<float, float>(n->gA, c, c * vol, W + n->woff[1], 1, nullptr, n->gB, c, c * vol, B, Z, Y, X, 0, n->a1, c * vol, s);
+    wgrad(n, n->a1, c, c * vol, n->gA, c, c * vol, B, Z, Y, X, G + n->woff[1], G + n->boff[1], s);
+    conv<float, float>(n, n->gA, c, c * vol, W + n->woff[1], 1, nullptr, n->gB, c, c * vol, B, Z, Y, X, 0, n->a1, c * vol, n->status, s);
     // layer 1
-    wgrad(n->x, 5, 5 * vol, n->gB, c, c * vol, B, Z, Y, X, G + n->woff[0], G + n->boff[0], s);
+    wgrad(n, n->x, 5, 5 * vol, n->gB, c, c * vol, B, Z, Y, X, G + n->woff[0], G + n->boff[0], s);
     HELM_CUDA_TRY(cudaGetLastError());
     return HELM_OK;
 }
@@ -745,7 +784,7 @@ helm_status learned_post(helm_ctx* c, float2* z, cudaStream_t s) {
     prof_begin(c, s, PROF_LEARNED);
     sumsq_kernel<<<nblk(N), 256, 0, s>>>(z, N, acc + 1);
     feat_pair_kernel<<<nblk(N), 256, 0, s>>>(z, acc + 1, N, n->x + 2 * N, n->x + 3 * N);
-    forward(n, s);
+    forward(n, c->status_d, s);
     make_c_kernel<<<nblk(N), 256, 0, s>>>(n->y, acc, N, n->cbuf);
     prof_end(c, s);
     if ((st = launch_stencil_f32_cls(c, z, n->az0, nullptr, 0, PROF_LEARNED, s)) != HELM_OK) return st;

@@ -1,11 +1,13 @@
 // PFFT preconditioner (Sec. 4.2, Eq. PFFT_SOLVER): A_p U = Y solved with a sine-transform solver for A_p^F
-// (Eq. TFprec) and a boundary correction.  Staggered grid, two-point ABC (zeta = 1), Dirichlet at the
-// face for A_p^F (ghost -U_1, corner -1): its x/y eigenvectors are S[l][j] = c_j sin(pi j (2l+1)/(2N)),
-// eigenvalues 2 cos(pi j/N), j = 1..N (the DST-II basis: our reading of "Dirichlet" for the staggered grid).
+// (Eq. TFprec) and a boundary correction.  Dirichlet at the face for A_p^F (ghost -U_1, corner -1): its x/y
+// eigenvectors are S[l][j] = c_j sin(pi j (2l+1)/(2N)), eigenvalues 2 cos(pi j/N), j = 1..N (the DST-II
+// basis: our reading of "Dirichlet" for N = 2^k).  Staggered grids (PFFT2: two-point ABC, zeta = 1) and
+// collocated grids (PFFT3: three-point ABC, Lbar corner gamma = 2 i k0 h and corner neighbour zeta = 2).
 //
 //   1. Yh = S_y^T Y_l S_x (2D sine transform of every slice), Th = z-solve_F(Yh)
-//   2. Theta on the boundary frame only (rows j = 0, N-1, columns i = 0, N-1) from Th (sparse inverse
-//      transform); R = (A_p^F - A_p) Theta lives on the frame: alpha (-1 - gamma) Theta there.
+//   2. Theta on the boundary frame only (rows j = 0, N-1, columns i = 0, N-1; with zeta = 2 also the
+//      second layer j = 1, N-2 and i = 1, N-2) from Th (sparse inverse transform); R = (A_p^F - A_p) Theta
+//      lives on the frame: alpha [(-1 - gamma) Theta_boundary + (1 - zeta) Theta_second layer] there.
 //      Rbar = V_y^-1 R V_x^-T is a sum of four outer products per slice; Wbar = z-solve_EigT(Rbar) takes
 //      them as a generated right-hand side; W on the frame from Wbar (sparse inverse EigT transform).
 //   3. R2 = (A_p^F - A_p)(Theta + W) on the frame; its sine transform is again four outer products,
@@ -30,6 +32,7 @@ struct PfftState {
     float2 *dxF = nullptr, *dyF = nullptr;          // alpha_x 2cos(pi j/N_x), alpha_y 2cos(pi j/N_y)
     float2* Yh = nullptr;                           // transformed right-hand side (kept for step 3)
     float2 *fa = nullptr, *fb = nullptr, *fc = nullptr;   // frame work vectors [4][nz][nmax]
+    float2 *fb1 = nullptr, *fc1 = nullptr;          // second frame layer (zeta = 2): Theta, W
     float2 *P = nullptr, *Q = nullptr;              // outer-product factors [4][nz][ny], [4][nz][nx]
     float2* zfacF = nullptr;                        // Thomas factors of the z-systems of A_p^F
 };
@@ -289,14 +292,21 @@ __global__ void fill_kernel(float2* __restrict__ out, int nz, int n, const float
     out[id] = vec[(size_t)m * vstride + voff];
 }
 
-// c = s * (a + b) elementwise (frame values -> correction vectors)
-__global__ void frame_scale_kernel(const float2* __restrict__ a, const float2* __restrict__ b, float2* __restrict__ c,
-                                   size_t n, float2 s) {
+// c = s (a + b) + t (a1 + b1) elementwise (frame values -> correction vectors; b, b1 may be NULL, and a1
+// is NULL for a one-layer frame)
+__global__ void frame_scale_kernel(const float2* __restrict__ a, const float2* __restrict__ b, const float2* a1,
+                                   const float2* b1, float2* c, size_t n, float2 s, float2 t) {
     const size_t id = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
     if (id >= n) return;
     float2 v = a[id];
     if (b) v = cadd(v, b[id]);
-    c[id] = cmul(s, v);
+    float2 o = cmul(s, v);
+    if (a1) {
+        float2 w = a1[id];
+        if (b1) w = cadd(w, b1[id]);
+        o = cfma(t, w, o);
+    }
+    c[id] = o;
 }
 
 __global__ void to_c64_kernel(const double2* __restrict__ a, float2* __restrict__ b, size_t n) {
@@ -379,6 +389,8 @@ helm_status pfft_prepare(helm_ctx* c, cudaStream_t s) {
     if ((st = dmal(&P->Yh, c->npts))) return st;
     const size_t fv = (size_t)4 * nz * nm;
     if ((st = dmal(&P->fa, fv)) || (st = dmal(&P->fb, fv)) || (st = dmal(&P->fc, fv))) return st;
+    if (c->zeta[0] != 1.0 || c->zeta[1] != 1.0)
+        if ((st = dmal(&P->fb1, fv)) || (st = dmal(&P->fc1, fv))) return st;
     if ((st = dmal(&P->P, (size_t)4 * nz * ny)) || (st = dmal(&P->Q, (size_t)4 * nz * nx))) return st;
     if ((st = zsolve_factor_with(c, P->dxF, P->dyF, &P->zfacF, s))) return st;
     if (c->tmaps) {
@@ -424,7 +436,7 @@ void pfft_release(helm_ctx* c) {
     PfftState* P = (PfftState*)c->pfft;
     if (!P) return;
     void* ps[] = {P->twx, P->twy, P->fwx, P->fwy, P->gpx, P->gpy, P->gmx, P->gmy, P->Sx, P->Sy, P->Vx, P->Vxi,
-                  P->Vy, P->Vyi, P->dxF, P->dyF, P->Yh, P->fa, P->fb, P->fc, P->P, P->Q, P->zfacF};
+                  P->Vy, P->Vyi, P->dxF, P->dyF, P->Yh, P->fa, P->fb, P->fc, P->fb1, P->fc1, P->P, P->Q, P->zfacF};
     for (void* p : ps) if (p) cudaFree(p);
     delete P;
     c->pfft = nullptr;
@@ -462,19 +474,21 @@ helm_status dst2d(helm_ctx* c, PfftState* P, int inv, const float2* in, float2* 
     return HELM_OK;
 }
 
-// frame of M_y C M_x^T (rows 0, N-1 and columns 0, N-1 of every slice) into fr: [0] row 0, [1] row N-1
-// (length nx), [2] column 0, [3] column N-1 (length ny); wr0/wr1 = rows 0, N-1 of M_y; wc0/wc1 = rows
-// 0, N-1 of M_x; Mx, My full matrices.  Uses fa as scratch.
+// layer k of the frame of M_y C M_x^T (rows k, N-1-k and columns k, N-1-k of every slice) into fr: [0] row
+// k, [1] row N-1-k (length nx), [2] column k, [3] column N-1-k (length ny); the row weights are rows k,
+// N-1-k of M_y and of M_x; Mx, My full matrices.  Uses fa as scratch.
 helm_status frame_of(helm_ctx* c, PfftState* P, const float2* C, const float2* Mx, const float2* My, float2* fr,
-                     cudaStream_t s) {
+                     cudaStream_t s, int k = 0) {
     const int nx = P->nx, ny = P->ny, nz = P->nz, nm = nx > ny ? nx : ny;
     const size_t blk = (size_t)nz * nm;
     float2* TT = P->fa;
     float2* TB = P->fa + blk;
     float2* UL = P->fa + 2 * blk;
     float2* UR = P->fa + 3 * blk;
-    frame_cols_kernel<<<dim3((nx + 127) / 128, nz), 128, 0, s>>>(C, nx, ny, My, My + (size_t)(ny - 1) * ny, TT, TB, nm);
-    frame_rows_kernel<<<dim3((ny + 7) / 8, nz), 256, 0, s>>>(C, nx, ny, Mx, Mx + (size_t)(nx - 1) * nx, UL, UR, nm);
+    frame_cols_kernel<<<dim3((nx + 127) / 128, nz), 128, 0, s>>>(C, nx, ny, My + (size_t)k * ny,
+                                                                 My + (size_t)(ny - 1 - k) * ny, TT, TB, nm);
+    frame_rows_kernel<<<dim3((ny + 7) / 8, nz), 256, 0, s>>>(C, nx, ny, Mx + (size_t)k * nx,
+                                                             Mx + (size_t)(nx - 1 - k) * nx, UL, UR, nm);
     const float2 one = make_float2(1.f, 0.f);
     // rows: Theta[0][i] = sum_i' Mx[i][i'] TT[i'];  columns: Theta[j][0] = sum_j' My[j][j'] UL[j']
     launch_matvec(nz, s, Mx, nx, 0, TT, fr, nm, one, nullptr);
@@ -507,17 +521,23 @@ helm_status pfft_apply(helm_ctx* c, const float2* r, float2* z, const double* si
     const size_t blk = (size_t)nz * nm;
     helm_status st;
     const float2 one = make_float2(1.f, 0.f);
-    // (A_p^F - A_p) on the frame: alpha_d (-1 - gamma_d)
+    // (A_p^F - A_p) on the frame: alpha_d (-1 - gamma_d) times the boundary layer, plus alpha_d (1 - zeta_d)
+    // times the second layer (zeta = 2 on collocated grids; nothing for zeta = 1)
     const float2 ex = make_float2((float)(c->ax * (-1.0 - c->gam[0].x)), (float)(c->ax * (-c->gam[0].y)));
     const float2 ey = make_float2((float)(c->ay * (-1.0 - c->gam[1].x)), (float)(c->ay * (-c->gam[1].y)));
+    const float2 tx = make_float2((float)(c->ax * (1.0 - c->zeta[0])), 0.f);
+    const float2 ty = make_float2((float)(c->ay * (1.0 - c->zeta[1])), 0.f);
+    const bool two = P->fb1 != nullptr;
     // 1. Yh = S_y^T Y S_x ; Th = z-solve_F(Yh) -> tmp2 (z is free until the end)
     if ((st = dst2d(c, P, 0, r, P->Yh, 1.f, sigma, sidx, s)) != HELM_OK) return st;
     if ((st = launch_zsolve_fact(c, P->zfacF, P->Yh, z, nullptr, nullptr, s)) != HELM_OK) return st;
-    // 2. Theta on the frame (fb), R vectors (fc): rows scaled by e_y, columns by e_x
+    // 2. Theta on the frame (fb; second layer fb1), R vectors (fc): rows scaled by e_y, t_y, columns by e_x, t_x
     if ((st = frame_of(c, P, z, P->Sx, P->Sy, P->fb, s)) != HELM_OK) return st;
-    frame_scale_kernel<<<(unsigned)((2 * blk + 255) / 256), 256, 0, s>>>(P->fb, nullptr, P->fc, 2 * blk, ey);
-    frame_scale_kernel<<<(unsigned)((2 * blk + 255) / 256), 256, 0, s>>>(P->fb + 2 * blk, nullptr, P->fc + 2 * blk,
-                                                                        2 * blk, ex);
+    if (two && (st = frame_of(c, P, z, P->Sx, P->Sy, P->fb1, s, 1)) != HELM_OK) return st;
+    frame_scale_kernel<<<(unsigned)((2 * blk + 255) / 256), 256, 0, s>>>(P->fb, nullptr, two ? P->fb1 : nullptr,
+                                                                        nullptr, P->fc, 2 * blk, ey, ty);
+    frame_scale_kernel<<<(unsigned)((2 * blk + 255) / 256), 256, 0, s>>>(
+        P->fb + 2 * blk, nullptr, two ? P->fb1 + 2 * blk : nullptr, nullptr, P->fc + 2 * blk, 2 * blk, ex, tx);
     // Rbar = sum of four outer products: (Vyi e_0)(Vxi ryT)^T + (Vyi e_N)(Vxi ryB)^T + (Vyi cxL)(Vxi e_0)^T + ...
     //   P[0] = Vyi[:, 0], P[1] = Vyi[:, N-1], P[2] = Vyi cxL, P[3] = Vyi cxR
     //   Q[0] = Vxi ryT,   Q[1] = Vxi ryB,     Q[2] = Vxi[:, 0], Q[3] = Vxi[:, N-1]
@@ -543,10 +563,13 @@ helm_status pfft_apply(helm_ctx* c, const float2* r, float2* z, const double* si
     //    Wbar = z-solve_EigT(Rbar) into z; W on the frame (fc) from Wbar with the EigT bases
     if ((st = launch_zsolve_fact(c, c->zfac, nullptr, z, P->P, P->Q, s)) != HELM_OK) return st;
     if ((st = frame_of(c, P, z, P->Vx, P->Vy, P->fc, s)) != HELM_OK) return st;
-    // 3. R2 = (A_p^F - A_p)(Theta + W) on the frame -> fc (rows e_y, columns e_x)
-    frame_scale_kernel<<<(unsigned)((2 * blk + 255) / 256), 256, 0, s>>>(P->fb, P->fc, P->fc, 2 * blk, ey);
-    frame_scale_kernel<<<(unsigned)((2 * blk + 255) / 256), 256, 0, s>>>(P->fb + 2 * blk, P->fc + 2 * blk,
-                                                                        P->fc + 2 * blk, 2 * blk, ex);
+    if (two && (st = frame_of(c, P, z, P->Vx, P->Vy, P->fc1, s, 1)) != HELM_OK) return st;
+    // 3. R2 = (A_p^F - A_p)(Theta + W) on the frame -> fc (rows e_y, t_y, columns e_x, t_x)
+    frame_scale_kernel<<<(unsigned)((2 * blk + 255) / 256), 256, 0, s>>>(
+        P->fb, P->fc, two ? P->fb1 : nullptr, two ? P->fc1 : nullptr, P->fc, 2 * blk, ey, ty);
+    frame_scale_kernel<<<(unsigned)((2 * blk + 255) / 256), 256, 0, s>>>(
+        P->fb + 2 * blk, P->fc + 2 * blk, two ? P->fb1 + 2 * blk : nullptr, two ? P->fc1 + 2 * blk : nullptr,
+        P->fc + 2 * blk, 2 * blk, ex, tx);
     //    sine transform of R2 as four outer products:
     //   P[0] = S_y[0][:], P[1] = S_y[N-1][:], P[2] = S_y^T c2L, P[3] = S_y^T c2R
     //   Q[0] = S_x^T r2T, Q[1] = S_x^T r2B,   Q[2] = S_x[0][:], Q[3] = S_x[N-1][:]

@@ -16,7 +16,7 @@ __global__ void scale_copy_kernel(const float2* __restrict__ a, float2* __restri
         b[id] = make_float2(s * a[id].x, s * a[id].y);
 }
 
-bool use_tc(const helm_ctx* c) { return c->opt.precision == HELM_PREC_TF32; }
+bool use_tc(const helm_ctx* c) { return c->opt.precision != HELM_PREC_FP32; }
 
 helm_status xpass(helm_ctx* c, int inverse, const float2* in, float2* out, float alpha, const double* sigma, int sidx,
                   cudaStream_t s) {

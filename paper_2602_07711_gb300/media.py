@@ -129,11 +129,13 @@ def manufactured(n, k0, order):
     h = 1.0 / (n - 1)
     node = np.arange(n) * h
     ext = np.arange(-1, n + 1) * h
-    Z, Y, X = np.meshgrid(node, node, node, indexing="ij")
+    # sparse (broadcasting) meshes: the factors of the separable solution are evaluated on 1D coordinates
+    # and multiplied out, which gives the same numbers as full meshes at a fraction of the cost
+    Z, Y, X = np.meshgrid(node, node, node, indexing="ij", sparse=True)
     u = _phi(X, k0, 0) * _phi(Y, k0, 0) * _phi(Z, k0, 0)
     F = lambda a, b, c, P=(X, Y, Z): _f_deriv(P[0], P[1], P[2], k0, a, b, c)
     if order == 4:
-        Zp, Yp, Xp = np.meshgrid(ext, ext, ext, indexing="ij")
+        Zp, Yp, Xp = np.meshgrid(ext, ext, ext, indexing="ij", sparse=True)
         fields = _f_deriv(Xp, Yp, Zp, k0, 0, 0, 0)
     else:
         fields = np.stack([F(0, 0, 0), F(2, 0, 0) + F(0, 2, 0) + F(0, 0, 2),

@@ -26,7 +26,7 @@ N, SEED_MEDIUM, SEED_ANGLE, SAMPLES, SAMPLE_SEED = 256, 3, 4, 4096, 256
 OUT = os.path.join(HERE, "bumps256_order6_solution_sample.txt")
 
 
-def main():
+def main(n=N, out=OUT):
     from oracle.eigt import EigT
     from oracle.gmres import gmres
     from oracle.grid import Grid
@@ -34,25 +34,25 @@ def main():
     from oracle.rhs import rhs6_sampled
     from paper_2602_07711_gb300 import media
 
-    k2, f, k0 = media.bumps(N, SEED_MEDIUM, SEED_ANGLE)
-    g = Grid(N, N, N, staggered=True)
+    k2, f, k0 = media.bumps(n, SEED_MEDIUM, SEED_ANGLE)
+    g = Grid(n, n, n, staggered=True)
     A = Operator(g, k2, k0, 6)
     F = rhs6_sampled(f, k2, A.dk2, True, g.h)
     t = time.time()
     hist = []
     x, info = gmres(A, EigT(g, k0).apply_Minv, F, m=30, rtol=1e-12, max_it=400, history=hist)
     dt = time.time() - t
-    relres = float(np.linalg.norm(A(x) - F.ravel()) / np.linalg.norm(F))
-    idx = np.sort(np.random.default_rng(SAMPLE_SEED).choice(N ** 3, SAMPLES, replace=False))
+    relres = float(np.linalg.norm(np.asarray(A(x)).ravel() - F.ravel()) / np.linalg.norm(F))
+    idx = np.sort(np.random.default_rng(SAMPLE_SEED).choice(n ** 3, SAMPLES, replace=False))
     xs = x.ravel()[idx]
-    with open(OUT, "w") as fh:
-        fh.write("# oracle solution of media.bumps(256, 3, 4), sixth order, staggered grid, GMRES(30)+EigT to "
-                 "rel-res 1e-12 (tests/golden/make_solution_sample.py)\n")
+    with open(out, "w") as fh:
+        fh.write("# oracle solution of media.bumps(%d, 3, 4), sixth order, staggered grid, GMRES(30)+EigT to "
+                 "rel-res 1e-12 (tests/golden/make_solution_sample.py)\n" % n)
         fh.write("# iterations %d relres %.6e norm2 %.17e sample_seed %d solve_seconds %.0f\n"
                  % (info["iterations"], relres, np.linalg.norm(x), SAMPLE_SEED, dt))
         for i, v in zip(idx, xs):
             fh.write("%d %.17e %.17e\n" % (i, v.real, v.imag))
-    print("wrote", OUT, info["iterations"], relres, dt)
+    print("wrote", out, info["iterations"], relres, dt)
 
 
 def read(path=OUT):
@@ -66,4 +66,8 @@ def read(path=OUT):
 
 
 if __name__ == "__main__":
-    main()
+    # optional: a smaller grid and another output file (a quick check of the script itself)
+    if len(sys.argv) == 3:
+        main(int(sys.argv[1]), sys.argv[2])
+    else:
+        main()

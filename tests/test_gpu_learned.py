@@ -45,7 +45,11 @@ def _setup(width, shape, B, seed):
     return net, P, x, xd
 
 
-@pytest.mark.parametrize("width,shape,B", [(4, (6, 10, 12), 2), (8, (8, 18, 10), 1), (3, (4, 4, 34), 1)])
+# the convolutions run on the tensor cores (conv_tc.cu): widths that are not multiples of 16 (padded chunks),
+# grids narrower and wider than one 128-point row tile (x = 130, 136: a ragged second tile), batches, and the
+# width of the ~200K-parameter network (32; its 96-channel data gradient takes two output slices)
+@pytest.mark.parametrize("width,shape,B", [(4, (6, 10, 12), 2), (8, (8, 18, 10), 1), (3, (4, 4, 34), 1),
+                                           (32, (4, 6, 130), 1), (24, (6, 4, 20), 2)])
 def test_forward_matches_oracle(width, shape, B):
     net, P, x, xd = _setup(width, shape, B, 11)
     y = net.forward(xd).cpu().numpy().astype(np.float64)
@@ -53,7 +57,7 @@ def test_forward_matches_oracle(width, shape, B):
     assert _rel(y, yo) < 2e-2, _rel(y, yo)
 
 
-@pytest.mark.parametrize("width,shape,B", [(4, (6, 10, 12), 2), (6, (8, 8, 20), 1)])
+@pytest.mark.parametrize("width,shape,B", [(4, (6, 10, 12), 2), (6, (8, 8, 20), 1), (32, (4, 4, 136), 1)])
 def test_backward_matches_oracle(width, shape, B):
     net, P, x, xd = _setup(width, shape, B, 12)
     rng = np.random.default_rng(3)

@@ -109,3 +109,63 @@ def test_fft2_needs_many_more_iterations_than_eigt():
     d = np.linalg.norm(out[HELM_PRECOND_EIGT][0] - out[HELM_PRECOND_FFT2][0]) / np.linalg.norm(out[HELM_PRECOND_EIGT][0])
     assert d < 2e-5
     assert out[HELM_PRECOND_FFT2][1] >= 3 * out[HELM_PRECOND_EIGT][1]
+
+
+# ---- PFFT3: collocated grids (Sec. 4.2 with the three-point ABC: Lbar corner 2 i k0 h, zeta = 2) ------------
+# The correction (A_p^F - A_p) then reads the two outer layers of Theta and W; the result must still equal
+# the oracle's PFFT and EigT (which invert the same A_p).
+@pytest.mark.parametrize("n,L,tol", [((32, 32, 20), (1.0, 1.0, 0.625), 5e-5), ((64, 32, 33), (1.0, 0.6, 0.5), 2.3e-4)])
+def test_pfft3_collocated_preconditioner_matches_oracle(n, L, tol):
+    g = Grid(*n, lx=L[0], ly=L[1], lz=L[2], staggered=False)
+    k0 = 2 * math.pi / (10 * g.h[0])
+    S = Solver(n, np.full(g.shape, k0 * k0, complex), k0, order=4, L=L, precond=HELM_PRECOND_PFFT, staggered=False)
+    y = _rand(g.shape, 17)
+    z = S.apply_precond(torch.from_numpy(y).to("cuda", torch.complex64)).cpu().numpy()
+    for ref in (PFFT(g, k0, variant="face").apply_Minv(y), EigT(g, k0).apply_Minv(y)):
+        err = np.linalg.norm(z - ref) / np.linalg.norm(ref)
+        assert err < tol, err
+    # the one-layer correction of PFFT2 is not enough here: dropping the second layer is a visible error
+    e = EigT(g, k0)
+    P1 = PFFT(g, k0, variant="face")
+    zeta_x, zeta_y = P1.eigt.zx, P1.eigt.zy
+    P1.eigt.zx = P1.eigt.zy = 1.0          # oracle copy with the second-layer term dropped (planted mistake)
+    bad = P1.apply_Minv(y)
+    P1.eigt.zx, P1.eigt.zy = zeta_x, zeta_y
+    assert np.linalg.norm(bad - e.apply_Minv(y)) / np.linalg.norm(e.apply_Minv(y)) > 100 * tol
+
+
+def test_pfft3_tensor_core_matches_oracle():
+    n, L = (64, 32, 20), (1.0, 0.5, 0.3)
+    g = Grid(*n, lx=L[0], ly=L[1], lz=L[2], staggered=False)
+    k0 = 2 * math.pi / (10 * g.h[0])
+    S = Solver(n, np.full(g.shape, k0 * k0, complex), k0, order=4, L=L, precond=HELM_PRECOND_PFFT,
+               precision=HELM_PREC_TF32, flexible=True, staggered=False)
+    y = _rand(g.shape, 18)
+    z = S.apply_precond(torch.from_numpy(y).to("cuda", torch.complex64)).cpu().numpy()
+    ref = EigT(g, k0).apply_Minv(y)
+    assert np.linalg.norm(z - ref) / np.linalg.norm(ref) < 4e-3
+
+
+def test_pfft3_gmres_on_the_manufactured_problem_matches_eigt3():
+    """The paper's test problem of Sec. 5.1 (collocated grid, high-order closure, sixth order) with PFFT3 and
+    with EigT3: the same iterations (+-1) and the same solution."""
+    from paper_2602_07711_gb300 import HELM_CLOSURE_HIGH_ORDER
+    n = 64
+    k0 = math.sqrt(439.2)
+    d = media.manufactured(n, k0, 6)
+    out = {}
+    for pc in (HELM_PRECOND_EIGT, HELM_PRECOND_PFFT):
+        S = Solver((n, n, n), d["k2"], k0, order=6, precond=pc, flexible=True, rtol=1e-10, restart=20, max_iter=200,
+                   staggered=False)
+        S.set_closure(HELM_CLOSURE_HIGH_ORDER)
+        F = S.closure_rhs(torch.from_numpy(d["faces"]).cuda(), S.build_rhs_fields(torch.from_numpy(d["fields"]).cuda()))
+        x, info = S.solve(F)
+        assert info.status == 0 and info.relres_true <= 1e-10
+        out[pc] = (x.cpu().numpy(), info.iterations)
+        S.close()
+    xe, xp = out[HELM_PRECOND_EIGT][0], out[HELM_PRECOND_PFFT][0]
+    assert np.linalg.norm(xe - xp) / np.linalg.norm(xe) < 1e-8
+    assert abs(out[HELM_PRECOND_EIGT][1] - out[HELM_PRECOND_PFFT][1]) <= 1
+    # and the printed sixth-order accuracy of the scheme is reached (64^3: between the 50^3 and 100^3 rows)
+    u = d["u"]
+    assert 9.97e-8 < np.linalg.norm(xp - u) / np.linalg.norm(u) < 7.06e-6
