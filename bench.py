@@ -787,29 +787,77 @@ def run_ksweep(args, rank, world, local):
         print(json.dumps(line), flush=True)
 
 
+def _net_forward_ms(net, n, reps=5):
+    """CUDA-event time of one forward of the network on a single n^3 field (five bf16 input channels)."""
+    import torch
+    x = torch.randn((1, 5, n, n, n), device="cuda").to(torch.bfloat16)
+    net.forward(x)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(reps):
+        net.forward(x)
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
 def run_learned(args, rank, world, local):
-    """384^3, order 6, 8 points per wavelength, k^2/k0^2 in [0.5,1.8] (8 layers + 5 spheres): the U-Net is
-    trained on the GPU on pairs from 96^3 solves of the same family, then FGMRES(30)+EigT with and without it."""
-    import numpy as np
+    """The learned correction (an extension): a 3D U-Net of width 28 (about 217K parameters, the size class of
+    the learned-correction configuration), trained on the GPU with the tensor-core convolutions on pairs from
+    96^3 solves, then FGMRES(30)+EigT with and without it on two families:
+      high contrast  384^3, order 6, 8 points per wavelength, k^2/k0^2 in [0.5, 1.8] (8 layers + 5 spheres),
+                     trained on the same family (plain EigT-FGMRES(30) stagnates on it);
+      bumps          the headline's 20-bump medium at 256^3 (plain EigT converges), trained on 96^3 bump media.
+    Also the network's own cost: one forward at 256^3 and 384^3 (CUDA events), widths 8 and 28."""
     import torch
 
     from paper_2602_07711_gb300 import Net, learned
     torch.cuda.set_device(local)
+    width = 28
     n = 384 if args.n == 256 else args.n
-    t0 = time.perf_counter()
-    X, T = learned.generate_pairs(n=96, seeds=range(100, 116), iters=(0, 3, 8), arnoldi=4)
-    net = Net(8, seed=0)
-    log = learned.train(net, X, T, steps=300, batch=2)
-    train_s = time.perf_counter() - t0
-    val = learned.evaluate(net, *learned.generate_pairs(n=96, seeds=range(200, 202), iters=(0, 4), arnoldi=2))
-    r = learned.compare(net, n, 7, rtol=args.rtol, max_iter=args.max_iter, repeats=1)
+    out = {}
+    for fam, medium, nc, seed_c, train_seeds, its in (
+            ("high_contrast", learned.high_contrast, n, 7, range(100, 116), (0, 3, 8)),
+            ("bumps", learned.bumps_medium, 256, 3, range(300, 316), (0, 2, 4, 7))):
+        t0 = time.perf_counter()
+        X, T = learned.generate_pairs(n=96, seeds=train_seeds, iters=its, arnoldi=4, medium=medium,
+                                      ppw=8.0 if fam == "high_contrast" else 10.0)
+        gen_s = time.perf_counter() - t0
+        net = Net(width, seed=0)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        log = learned.train(net, X, T, steps=300, batch=2)
+        torch.cuda.synchronize()
+        train_s = time.perf_counter() - t1
+        val = learned.evaluate(net, *learned.generate_pairs(n=96, seeds=range(200, 202), iters=(0, 4), arnoldi=2,
+                                                            medium=medium,
+                                                            ppw=8.0 if fam == "high_contrast" else 10.0))
+        if fam == "bumps":
+            k2, f, k0 = learned.media.bumps(nc, 3, 4, device="cuda", as_numpy=False)
+            r = learned.compare(net, nc, 3, rtol=args.rtol, max_iter=args.max_iter, repeats=2,
+                                medium=lambda n_, s_, ppw=10.0: (k2, f, k0))
+        else:
+            r = learned.compare(net, nc, seed_c, rtol=args.rtol, max_iter=min(args.max_iter, 150), repeats=1,
+                                medium=medium)
+        out[fam] = {"n": nc, "pairs": int(X.shape[0]), "pair_generation_s": gen_s, "train_s": train_s,
+                    "train_steps": 300, "train_log": log[-3:], "val_loss_vs_zero": val, "compare": r}
+        del X, T, net
+        torch.cuda.empty_cache()
+    cost = {}
+    for w in (8, width):
+        net = Net(w, seed=1)
+        cost["width%d" % w] = {"params": int(net.nparam), "forward_ms_256": _net_forward_ms(net, 256),
+                               "forward_ms_384": _net_forward_ms(net, 384, reps=2)}
+        net.close()
     if rank == 0:
-        v = n ** 3 * r["learned"]["iterations"] / r["learned"]["seconds"] / 1e6
-        line = _base_line(args, world, v, r["learned"]["seconds"], "highcontrast-n%d-order6-seed7" % n,
-                          {"config": {"n": n, "net_width": 8, "params": int(net.nparam), "pairs": int(X.shape[0]),
-                                      "krylov": "FGMRES(%d)" % args.restart},
-                           "train_s": train_s, "train_log": log[-3:], "val_loss_vs_zero": val, "compare": r,
-                           "roofline": None, "cpu_baseline": None, "e2e": None})
+        rl = out["bumps"]["compare"]["learned"]
+        v = 256 ** 3 * rl["iterations"] / rl["seconds"] / 1e6
+        line = _base_line(args, world, v, rl["seconds"], "learned-correction-width%d" % width,
+                          {"config": {"net_width": width, "params": cost["width%d" % width]["params"],
+                                      "krylov": "FGMRES(%d)" % args.restart, "families": list(out)},
+                           "runs": out, "network_cost": cost, "roofline": None, "cpu_baseline": None, "e2e": None})
         print(json.dumps(line), flush=True)
 
 

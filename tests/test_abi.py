@@ -59,18 +59,22 @@ def test_setup_rejects_bad_arguments_without_gpu_work(libpath):
     assert L.helm_setup(None, None, 1.0, None, None, None, ctypes.byref(ctx)) == 1
 
 
-def test_collocated_grid_rejects_the_sine_preconditioners_without_gpu_work(libpath):
+def test_setup_checks_the_precision_and_the_wait_limit_without_gpu_work(libpath):
+    """HELM_PREC_FP32, _TF32 and _TF32X3 (the three-product split) are the arithmetic modes; anything else is
+    rejected before any device work, as is a wait limit without a context or below zero."""
     from paper_2602_07711_gb300 import helm
     import numpy as np
     L = helm.lib()
     ctx = ctypes.c_void_p()
-    g = helm.helm_grid(8, 8, 8, 1.0, 1.0, 1.0, 0)          # collocated: EigT only
+    g = helm.helm_grid(8, 8, 8, 1.0, 1.0, 1.0, 0)
     k2 = np.zeros(512, np.complex128)
-    for precond in (helm.HELM_PRECOND_PFFT, helm.HELM_PRECOND_FFT2):
-        o = helm.helm_options(4, precond, 0, 30, 100, 1e-6, 0, 0)
+    assert (helm.HELM_PREC_FP32, helm.HELM_PREC_TF32, helm.HELM_PREC_TF32X3) == (0, 1, 2)
+    for precision in (-1, 3):
+        o = helm.helm_options(4, helm.HELM_PRECOND_PFFT, precision, 30, 100, 1e-6, 1, 0)
         assert L.helm_setup(ctypes.byref(g), k2.ctypes.data, 1.0, None, ctypes.byref(o), None,
-                            ctypes.byref(ctx)) == 10
+                            ctypes.byref(ctx)) == 1
         assert not ctx.value
+    assert L.helm_set_wait_limit(None, 5) == 1
 
 
 def test_closure_entry_points_reject_null_contexts_without_gpu_work(libpath):
