@@ -13,9 +13,10 @@
 //   layout (8 rows of 16 bytes per core matrix), and a tap's shifted view of the slab is the same layout
 //   at another start address: the 27 taps read one slab, nothing is copied per tap.  The weights of the
 //   chunk (27 taps x N x 16, pre-arranged by arrange_w_kernel) arrive by one bulk copy.  Two stages.
-//   Warps 0-3 gather the slab (converting to BF16, zeros outside the grid) and later run the epilogue
-//   (bias, ReLU, optional mask, channel-first stores); warp 4 allocates tensor memory and one lane issues
-//   the MMAs (M = 128, N = Np, K = 16 each).
+//   Warps 0-7 gather the slab (8-point vector loads of the channel-first input, a register transpose into
+//   the cells, BF16, zeros outside the grid); warps 0-3 then run the epilogue (bias, ReLU, optional mask,
+//   channel-first stores); warp 8 allocates tensor memory and one lane issues the MMAs (M = 128, N = Np,
+//   K = 16 each).
 // Weight gradient:  gW[o][i][t] = sum_p g[o][p] in[i][p + off_t].
 //   A CTA owns one 16-channel chunk of i and walks a share of the 128-point row tiles.  Per tile: A = the
 //   gradient rows (M = 128 output channels, padded, K = 128 points, K-major cells of 8 points) and B = the
@@ -36,6 +37,9 @@ constexpr int CT_TX = 128;                         // output points per row (MMA
 constexpr int CT_SX = CT_TX + 2;                   // slab points per row (one halo point each side)
 constexpr int CT_NPMAX = 64;                       // largest padded output-channel count
 constexpr long CT_WAIT = 1L << 22;                 // bound of every mbarrier wait (polls)
+constexpr int CT_PW = 8;                           // producer warps (gather); warps 0-3 also run the epilogue
+constexpr int CT_THREADS = (CT_PW + 1) * 32;       // + one warp for tensor memory and the MMAs
+constexpr int CT_MW = CT_PW;                       // the MMA warp
 
 template <int TY>
 struct CtLayout {
@@ -44,11 +48,12 @@ struct CtLayout {
     static constexpr int SLAB = CELLS * 16;
     static constexpr int CG = 3 * SY * CT_SX * 16;              // bytes between the two channel groups
 };
-// forward: two rows per CTA; a stage is the slab and the chunk's weights
+// forward: two rows per CTA; a stage is the slab and the chunk's weights (27 x 2 x Np x 16 bytes); two stages
+// when there are several channel chunks, one (and so more CTAs per SM) when there is one
 constexpr int FW_TY = 2;
 constexpr int FW_WMAX = 27 * 2 * CT_NPMAX * 16;                 // 55,296 bytes
-constexpr int FW_STAGE = CtLayout<FW_TY>::SLAB + FW_WMAX;       // 105,216
-constexpr int FW_SMEM = 2 * FW_STAGE + 128;
+constexpr int FW_SMEM = 2 * (CtLayout<FW_TY>::SLAB + FW_WMAX) + 128;   // the largest request
+__host__ __device__ constexpr int fw_stage_bytes(int Np) { return CtLayout<FW_TY>::SLAB + 27 * 2 * Np * 16; }
 // weight gradient: one row per tile; a stage is the slab and the gradient tile (16 x 128 cells)
 constexpr int WG_G = 16 * 128 * 16;                             // 32,768
 constexpr int WG_STAGE = CtLayout<1>::SLAB + WG_G;              // 70,208
@@ -125,41 +130,79 @@ __device__ __forceinline__ uint32_t pack2(float a, float b) {
     return *reinterpret_cast<const uint32_t*>(&h);
 }
 
+// 8 consecutive values of one row (x = xb .. xb + 7) as four packed BF16 pairs: one 16-byte (BF16) or two
+// 16-byte (FP32) loads inside the row when aligned (rows of a multiple of 8 points), else per point, zeros
+// outside 0 .. X - 1
+__device__ __forceinline__ uint4 load8(const bf16* __restrict__ row, int xb, int X, bool vec) {
+    if (vec && xb >= 0 && xb + 8 <= X) return *reinterpret_cast<const uint4*>(row + xb);
+    float v[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) v[k] = (xb + k >= 0 && xb + k < X) ? __bfloat162float(row[xb + k]) : 0.f;
+    return make_uint4(pack2(v[0], v[1]), pack2(v[2], v[3]), pack2(v[4], v[5]), pack2(v[6], v[7]));
+}
+__device__ __forceinline__ uint4 load8(const float* __restrict__ row, int xb, int X, bool vec) {
+    if (vec && xb >= 0 && xb + 8 <= X) {
+        const float4 a = *reinterpret_cast<const float4*>(row + xb), b = *reinterpret_cast<const float4*>(row + xb + 4);
+        return make_uint4(pack2(a.x, a.y), pack2(a.z, a.w), pack2(b.x, b.y), pack2(b.z, b.w));
+    }
+    float v[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) v[k] = (xb + k >= 0 && xb + k < X) ? row[xb + k] : 0.f;
+    return make_uint4(pack2(v[0], v[1]), pack2(v[2], v[3]), pack2(v[4], v[5]), pack2(v[6], v[7]));
+}
+__device__ __forceinline__ uint32_t u4w(const uint4& q, int i) { return i == 0 ? q.x : (i == 1 ? q.y : (i == 2 ? q.z : q.w)); }
+
 // Fill the slab of one 16-channel chunk (channels c0 .. c0 + 15) for output rows y0 .. y0 + TY - 1 of plane
 // z: cell q = ((cg * 3 + dz) * SY + yr) * 130 + xi holds channels c0 + 8 cg .. + 7 of the input point
-// (z + dz - 1, y0 + yr - 1, x0 + xi - 1); zero outside the grid and beyond Cin.
+// (z + dz - 1, y0 + yr - 1, x0 + xi - 1); zero outside the grid and beyond Cin.  A work item is one row of
+// the slab and one group of 8 points x = x0 - 8 + 8 g (g = 0 .. 17, aligned when x0 is): it loads the 8
+// channels' rows of those points (8-point vector loads) and writes the 8 cells, a transpose of the
+// channel-first input into the channel-contiguous cells done on packed BF16 pairs (byte permutes).
 template <int TY, typename TIN>
 __device__ __forceinline__ void fill_slab(unsigned char* slab, const TIN* __restrict__ in, int Cin, int c0, int z,
                                           int y0, int x0, int Z, int Y, int X, int t, int nthreads) {
     typedef CtLayout<TY> L;
+    constexpr int NG = (CT_SX + 14) / 8;   // 18 groups cover x0 - 8 .. x0 + 135 (the slab is x0 - 1 .. x0 + 128)
     const size_t vol = (size_t)Z * Y * X;
-    for (int q = t; q < L::CELLS; q += nthreads) {
-        const int xi = q % CT_SX;
-        int r = q / CT_SX;
+    const bool vec = (X % 8) == 0;
+    for (int it = t; it < 2 * 3 * L::SY * NG; it += nthreads) {
+        const int g = it % NG;
+        int r = it / NG;
         const int yr = r % L::SY;
         r /= L::SY;
         const int dz = r % 3, cg = r / 3;
-        const int gz = z + dz - 1, gy = y0 + yr - 1, gx = x0 + xi - 1;
-        float v[8];
-        const bool inside = gz >= 0 && gz < Z && gy >= 0 && gy < Y && gx >= 0 && gx < X;
-        const size_t off = inside ? ((size_t)gz * Y + gy) * X + gx : 0;
+        const int gz = z + dz - 1, gy = y0 + yr - 1, xb = x0 - 8 + 8 * g;
+        const bool rowok = gz >= 0 && gz < Z && gy >= 0 && gy < Y;
+        const size_t roff = rowok ? ((size_t)gz * Y + gy) * X : 0;
+        uint4 row[8];   // channel j: the 8 points as BF16 pairs
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
             const int ch = c0 + 8 * cg + j;
-            v[j] = (inside && ch < Cin) ? ldf(in, (size_t)ch * vol + off) : 0.f;
+            row[j] = (rowok && ch < Cin) ? load8(in + (size_t)ch * vol + roff, xb, X, vec) : make_uint4(0u, 0u, 0u, 0u);
         }
-        *reinterpret_cast<uint4*>(slab + (size_t)q * 16) =
-            make_uint4(pack2(v[0], v[1]), pack2(v[2], v[3]), pack2(v[4], v[5]), pack2(v[6], v[7]));
+        unsigned char* rowp = slab + (size_t)(((cg * 3 + dz) * L::SY + yr) * CT_SX) * 16;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const int xi = 8 * g - 7 + k;   // slab index of the point xb + k
+            if (xi >= 0 && xi < CT_SX) {
+                // cell word m = (channel 2m, channel 2m + 1) at point k: the low (k even) or high (k odd) halves
+                const uint32_t sel = (k & 1) ? 0x7632u : 0x5410u;
+                uint32_t w[4];
+#pragma unroll
+                for (int m = 0; m < 4; ++m) w[m] = __byte_perm(u4w(row[2 * m], k >> 1), u4w(row[2 * m + 1], k >> 1), sel);
+                *reinterpret_cast<uint4*>(rowp + (size_t)xi * 16) = make_uint4(w[0], w[1], w[2], w[3]);
+            }
+        }
     }
 }
 
 // ---- forward / data gradient ------------------------------------------------------------------------------
 // wt: arranged weights [nkc][27][2][Np][8] (bf16); mask (optional): out *= (mask > 0)
 template <typename TIN, typename TOUT>
-__global__ void __launch_bounds__(160, 1)
+__global__ void __launch_bounds__(CT_THREADS, 3)
 conv_tc_kernel(const TIN* __restrict__ in, int Cin, size_t in_bs, const bf16* __restrict__ wt, int Np,
                const float* __restrict__ bias, TOUT* __restrict__ out, int Cout, size_t out_bs, int Z, int Y, int X,
-               int relu, const bf16* __restrict__ mask, size_t mask_bs, unsigned* status) {
+               int relu, const bf16* __restrict__ mask, size_t mask_bs, int nst, unsigned* status) {
     typedef CtLayout<FW_TY> L;
     extern __shared__ __align__(128) unsigned char csm[];
     unsigned char* base = (unsigned char*)(((uintptr_t)csm + 127) & ~(uintptr_t)127);
@@ -177,10 +220,11 @@ conv_tc_kernel(const TIN* __restrict__ in, int Cin, size_t in_bs, const bf16* __
     const int x0 = xt * CT_TX, y0 = yt * FW_TY;
     const int nkc = (Cin + 15) / 16;
     const uint32_t wbytes = 27u * 2u * (uint32_t)Np * 16u;
+    const size_t stage = (size_t)fw_stage_bytes(Np);   // a multiple of 16
     const uint32_t ncols = FW_TY * Np <= 32 ? 32 : (FW_TY * Np <= 64 ? 64 : 128);
     if (threadIdx.x == 0) {
         for (int s = 0; s < 2; ++s) {
-            bar_init(s32(&full[s]), 4);
+            bar_init(s32(&full[s]), CT_PW);
             bar_init(s32(&wfull[s]), 1);
             bar_init(s32(&empty[s]), 1);
         }
@@ -189,7 +233,7 @@ conv_tc_kernel(const TIN* __restrict__ in, int Cin, size_t in_bs, const bf16* __
         fail_any = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == 4) {
+    if (warp == CT_MW) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(s32(&tslot)), "r"(ncols)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
@@ -201,25 +245,25 @@ conv_tc_kernel(const TIN* __restrict__ in, int Cin, size_t in_bs, const bf16* __
     bool ok = true;
     int issued = 0;   // chunks whose weight copy thread 0 issued
     const TIN* inb = in + (size_t)b * in_bs;
-    if (warp < 4) {
+    if (warp < CT_PW) {
         for (int kc = 0; kc < nkc && ok; ++kc) {
-            const int s = kc & 1, u = kc >> 1;
+            const int s = kc % nst, u = kc / nst;
             if (u >= 1) ok = __all_sync(0xffffffffu, bar_wait(s32(&empty[s]), (uint32_t)((u - 1) & 1), CT_WAIT));
             if (!ok) break;
-            unsigned char* st = base + (size_t)s * FW_STAGE;
+            unsigned char* st = base + (size_t)s * stage;
             if (threadIdx.x == 0) {
                 bar_expect(s32(&wfull[s]), wbytes);
                 bulk_g2s(s32(st + L::SLAB), wt + (size_t)kc * 27 * 2 * Np * 8, wbytes, s32(&wfull[s]));
                 ++issued;
             }
-            fill_slab<FW_TY>(st, inb, Cin, 16 * kc, z, y0, x0, Z, Y, X, threadIdx.x, 128);
+            fill_slab<FW_TY>(st, inb, Cin, 16 * kc, z, y0, x0, Z, Y, X, threadIdx.x, CT_PW * 32);
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // the MMAs read the slab (async proxy)
             __syncwarp();
             if (lane == 0) bar_arrive(s32(&full[s]));
         }
-        // epilogue: this warp's 32 accumulator lanes are the points x0 + 32 (warp) + lane
-        if (ok) ok = __all_sync(0xffffffffu, bar_wait(s32(&accf), 0, CT_WAIT));
-        if (ok) {
+        // epilogue (warps 0-3): this warp's 32 accumulator lanes are the points x0 + 32 (warp) + lane
+        if (ok && warp < 4) ok = __all_sync(0xffffffffu, bar_wait(s32(&accf), 0, CT_WAIT));
+        if (ok && warp < 4) {
             tc_after();
             const size_t vol = (size_t)Z * Y * X;
             const int x = x0 + 32 * warp + lane;
@@ -248,11 +292,11 @@ conv_tc_kernel(const TIN* __restrict__ in, int Cin, size_t in_bs, const bf16* __
     } else if (lane == 0) {
         const uint32_t idesc = idesc_bf16(128, Np, 0, 0);
         for (int kc = 0; kc < nkc && ok; ++kc) {
-            const int s = kc & 1, u = kc >> 1;
+            const int s = kc % nst, u = kc / nst;
             ok = bar_wait(s32(&full[s]), (uint32_t)(u & 1), CT_WAIT) && bar_wait(s32(&wfull[s]), (uint32_t)(u & 1), CT_WAIT);
             if (!ok) break;
             tc_after();
-            const uint32_t slab = s32(base + (size_t)s * FW_STAGE), wsm = slab + L::SLAB;
+            const uint32_t slab = s32(base + (size_t)s * stage), wsm = slab + L::SLAB;
             for (int t = 0; t < 27; ++t) {
                 const int dz = t / 9, dy = (t / 3) % 3, dx = t % 3;
                 // B: tap t's weights [2 channel groups][Np][8]: next channel group (K) Np*16 bytes, next 8 outputs 128
@@ -275,24 +319,25 @@ conv_tc_kernel(const TIN* __restrict__ in, int Cin, size_t in_bs, const bf16* __
     __syncthreads();
     if (fail_any && lane == 0) {
         if (warp == 0) {
-            // the weight copies of the last (at most two) issued chunks may still be in flight
-            for (int kc = issued > 2 ? issued - 2 : 0; kc < issued; ++kc)
-                bar_wait(s32(&wfull[kc & 1]), (uint32_t)((kc >> 1) & 1), CT_WAIT);
-        } else if (warp == 4) {
+            // the weight copies of the last (at most nst) issued chunks may still be in flight
+            for (int kc = issued > nst ? issued - nst : 0; kc < issued; ++kc)
+                bar_wait(s32(&wfull[kc % nst]), (uint32_t)((kc / nst) & 1), CT_WAIT);
+        } else if (warp == CT_MW) {
             mma_commit(s32(&drainb));
             bar_wait(s32(&drainb), 0, CT_WAIT);
         }
     }
     tc_before();
     __syncthreads();
-    if (warp == 4) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols) : "memory");
+    if (warp == CT_MW)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols) : "memory");
 }
 
 // ---- weight gradient ---------------------------------------------------------------------------------
 // gw[o][i][t] += sum_{b, p} g[b][o][p] in[b][i][p + off_t] for the 16 input channels of chunk blockIdx.x;
 // Cout <= 128.  Tiles: (b, z, y, 128-point x block), CTA y takes tiles blockIdx.y, + gridDim.y, ...
 template <typename TG>
-__global__ void __launch_bounds__(160, 1)
+__global__ void __launch_bounds__(CT_THREADS, 1)
 wgrad_tc_kernel(const bf16* __restrict__ in, int Cin, size_t in_bs, const TG* __restrict__ g, int Cout, size_t g_bs,
                 int B, int Z, int Y, int X, float* __restrict__ gw, unsigned* status) {
     typedef CtLayout<1> L;
@@ -307,13 +352,13 @@ wgrad_tc_kernel(const bf16* __restrict__ in, int Cin, size_t in_bs, const TG* __
     const int ntiles = B * Z * Y * ntx;
     const size_t vol = (size_t)Z * Y * X;
     if (threadIdx.x == 0) {
-        for (int s = 0; s < WG_NS; ++s) { bar_init(s32(&full[s]), 4); bar_init(s32(&empty[s]), 1); }
+        for (int s = 0; s < WG_NS; ++s) { bar_init(s32(&full[s]), CT_PW); bar_init(s32(&empty[s]), 1); }
         bar_init(s32(&accf), 1);
         bar_init(s32(&drainb), 1);
         fail_any = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == 4) {
+    if (warp == CT_MW) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(s32(&tslot)), "r"(512)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
@@ -324,7 +369,7 @@ wgrad_tc_kernel(const bf16* __restrict__ in, int Cin, size_t in_bs, const TG* __
     const uint32_t tmem = tslot;
     bool ok = true;
     int nt = 0;   // tiles this CTA processed
-    if (warp < 4) {
+    if (warp < CT_PW) {
         for (int tile = blockIdx.y; tile < ntiles && ok; tile += gridDim.y, ++nt) {
             int r = tile;
             const int xt = r % ntx;
@@ -337,27 +382,22 @@ wgrad_tc_kernel(const bf16* __restrict__ in, int Cin, size_t in_bs, const TG* __
             if (u >= 1) ok = __all_sync(0xffffffffu, bar_wait(s32(&empty[s]), (uint32_t)((u - 1) & 1), CT_WAIT));
             if (!ok) break;
             unsigned char* st = base + (size_t)s * WG_STAGE;
-            fill_slab<1>(st, in + (size_t)bb * in_bs, Cin, 16 * kc, z, y, x0, Z, Y, X, threadIdx.x, 128);
+            fill_slab<1>(st, in + (size_t)bb * in_bs, Cin, 16 * kc, z, y, x0, Z, Y, X, threadIdx.x, CT_PW * 32);
             // gradient cells: cell (kq, o) = g[o][z][y][x0 + 8 kq .. + 7], layout [kq][o][8]; zero beyond Cout, X
             unsigned char* gs = st + L::SLAB;
             const TG* gb = g + (size_t)bb * g_bs + ((size_t)z * Y + y) * X;
-            for (int q = threadIdx.x; q < 16 * 128; q += 128) {
+            const bool vec = (X % 8) == 0;
+            for (int q = threadIdx.x; q < 16 * 128; q += CT_PW * 32) {
                 const int o = q % 128, kq = q / 128;
-                float v[8];
-#pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    const int x = x0 + 8 * kq + j;
-                    v[j] = (o < Cout && x < X) ? ldf(gb, (size_t)o * vol + x) : 0.f;
-                }
                 *reinterpret_cast<uint4*>(gs + (size_t)q * 16) =
-                    make_uint4(pack2(v[0], v[1]), pack2(v[2], v[3]), pack2(v[4], v[5]), pack2(v[6], v[7]));
+                    o < Cout ? load8(gb + (size_t)o * vol, x0 + 8 * kq, X, vec) : make_uint4(0u, 0u, 0u, 0u);
             }
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             __syncwarp();
             if (lane == 0) bar_arrive(s32(&full[s]));
         }
-        if (ok) ok = __all_sync(0xffffffffu, bar_wait(s32(&accf), 0, CT_WAIT));
-        if (ok && nt > 0) {
+        if (ok && warp < 4) ok = __all_sync(0xffffffffu, bar_wait(s32(&accf), 0, CT_WAIT));
+        if (ok && nt > 0 && warp < 4) {
             tc_after();
             const int o = 32 * warp + lane;
             for (int t = 0; t < 27; ++t) {
@@ -403,13 +443,14 @@ wgrad_tc_kernel(const bf16* __restrict__ in, int Cin, size_t in_bs, const TG* __
         fail_any = 1;
     }
     __syncthreads();
-    if (fail_any && warp == 4 && lane == 0) {
+    if (fail_any && warp == CT_MW && lane == 0) {
         mma_commit(s32(&drainb));
         bar_wait(s32(&drainb), 0, CT_WAIT);
     }
     tc_before();
     __syncthreads();
-    if (warp == 4) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512) : "memory");
+    if (warp == CT_MW)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512) : "memory");
 }
 
 // arranged[kc][t][cg][o][j] = W(o0 + o, 16 kc + 8 cg + j, t) for the output slice o0 .. o0 + Np - 1, zero beyond
@@ -493,9 +534,13 @@ helm_status conv_tc(const TIN* in, int Cin, size_t in_bs, const bf16* w, int wmo
         const int Co = std::min(Cout - o0, CT_NPMAX), Np = (Co + 15) / 16 * 16;
         const size_t na = (size_t)nkc * 27 * 2 * Np * 8;
         arrange_w_kernel<<<(unsigned)((na + 255) / 256), 256, 0, s>>>(w, Cin, Cout, o0, wmode, Np, nkc, wscr);
-        conv_tc_kernel<TIN, TOUT><<<(unsigned)tiles, 160, FW_SMEM, s>>>(
+        // one stage: a CTA's chunks follow one another, and the two to three CTAs an SM holds overlap each
+        // other's gathers, MMAs and epilogues instead
+        const int nst = 1;
+        const size_t smem = (size_t)nst * fw_stage_bytes(Np) + 128;
+        conv_tc_kernel<TIN, TOUT><<<(unsigned)tiles, CT_THREADS, smem, s>>>(
             in, Cin, in_bs, wscr, Np, bias ? bias + o0 : nullptr, out + (size_t)o0 * vol, Co, out_bs, Z, Y, X, relu,
-            mask ? mask + (size_t)o0 * vol : nullptr, mask_bs, status);
+            mask ? mask + (size_t)o0 * vol : nullptr, mask_bs, nst, status);
         HELM_CUDA_TRY(cudaGetLastError());
     }
     return HELM_OK;
@@ -518,7 +563,7 @@ helm_status wgrad_tc(const bf16* in, int Cin, size_t in_bs, const float* g, int 
     long per = (2L * sms + nkc - 1) / nkc;   // CTAs per chunk: about two waves over the SMs in all
     if (per > ntiles) per = ntiles;
     if (per < 1) per = 1;
-    wgrad_tc_kernel<float><<<dim3((unsigned)nkc, (unsigned)per), 160, WG_SMEM, s>>>(in, Cin, in_bs, g, Cout, g_bs, B, Z,
+    wgrad_tc_kernel<float><<<dim3((unsigned)nkc, (unsigned)per), CT_THREADS, WG_SMEM, s>>>(in, Cin, in_bs, g, Cout, g_bs, B, Z,
                                                                                       Y, X, gw, status);
     const size_t vol = (size_t)Z * Y * X;
     bias_grad_kernel<float><<<dim3((unsigned)Cout, 64), 256, 0, s>>>(g, Cout, g_bs, B, vol, gb);

@@ -50,6 +50,7 @@ struct KrylovWork {
     int m = 0, flexible = 0, NB = 0, nres = 0;
     int NBd = 0;             // CTAs of the inner-product kernel: one full wave of resident CTAs
     size_t npts = 0;
+    size_t vs = 0;           // distance between consecutive basis vectors of V and Z (npts unless interleaved)
     float2* V = nullptr;     // (m+1) stored vectors
     float2* Z = nullptr;     // m preconditioned vectors (flexible) or one scratch vector
     double* sigma = nullptr; // [m+1]
@@ -84,7 +85,8 @@ constexpr double kLookaheadDrop = 0.05;
 // compensated FP32 (Kahan), FP64 only across threads (GB300's FP64 rate made FP64 partial sums the
 // limiter).  npts is even.
 __global__ void __launch_bounds__(NT) dots_kernel(const float2* __restrict__ V, size_t npts, int nv,
-                                                 const float2* __restrict__ w, double2* __restrict__ part, int ld) {
+                                                 const float2* __restrict__ w, double2* __restrict__ part, int ld,
+                                                 size_t vs) {
     __shared__ double2 red[NT / 32][GRP];
     const int tid = threadIdx.x;
     const size_t n4 = npts / 2;
@@ -104,7 +106,7 @@ __global__ void __launch_bounds__(NT) dots_kernel(const float2* __restrict__ V, 
 #pragma unroll
             for (int q = 0; q < GRP; ++q)
                 if (q < ng) {
-                    const float4* __restrict__ V4 = reinterpret_cast<const float4*>(V + (size_t)(g0 + q) * npts);
+                    const float4* __restrict__ V4 = reinterpret_cast<const float4*>(V + (size_t)(g0 + q) * vs);
                     const float4 va = V4[id];
                     const float4 vb = two ? V4[id2] : make_float4(0.f, 0.f, 0.f, 0.f);
                     float re = va.x * wa.x, im = va.x * wa.y;
@@ -149,7 +151,8 @@ __global__ void __launch_bounds__(NT) dots_kernel(const float2* __restrict__ V, 
 // warp keeps two iterations of loads in flight instead of waiting a full memory latency per iteration.
 template <int G>
 __global__ void __launch_bounds__(NT) dots_pipe_kernel(const float2* __restrict__ V, size_t npts, int nv,
-                                                      const float2* __restrict__ w, double2* __restrict__ part, int ld) {
+                                                      const float2* __restrict__ w, double2* __restrict__ part, int ld,
+                                                      size_t vs) {
     __shared__ double2 red[NT / 32][G];
     const int tid = threadIdx.x;
     const size_t n4 = npts / 2;
@@ -163,7 +166,7 @@ __global__ void __launch_bounds__(NT) dots_pipe_kernel(const float2* __restrict_
         for (int q = 0; q < G; ++q) {
             ks[q] = make_float2(0, 0);
             kc[q] = make_float2(0, 0);
-            V4[q] = reinterpret_cast<const float4*>(V + (size_t)(g0 + (q < ng ? q : 0)) * npts);
+            V4[q] = reinterpret_cast<const float4*>(V + (size_t)(g0 + (q < ng ? q : 0)) * vs);
         }
         size_t id = blockIdx.x * (size_t)NT + tid;
         float4 wa = make_float4(0.f, 0.f, 0.f, 0.f), va[G];
@@ -256,7 +259,7 @@ __global__ void reduce_h_kernel(const double2* __restrict__ part, int NB, int ld
 // 16-byte load; the basis loop is unrolled by four so that four vector loads are in flight.
 __global__ void __launch_bounds__(NT) update_kernel(const float2* __restrict__ V, size_t npts, int nv,
                                                    const float2* __restrict__ coef, float2* __restrict__ w,
-                                                   double2* __restrict__ part, int ld) {
+                                                   double2* __restrict__ part, int ld, size_t vs) {
     __shared__ float2 cf[72];
     __shared__ double red[NT / 32];
     for (int i = threadIdx.x; i < nv; i += NT) cf[i] = coef[i];
@@ -270,7 +273,7 @@ __global__ void __launch_bounds__(NT) update_kernel(const float2* __restrict__ V
         for (; i + 4 <= nv; i += 4) {
             float4 v[4];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) v[q] = reinterpret_cast<const float4*>(V + (size_t)(i + q) * npts)[id];
+            for (int q = 0; q < 4; ++q) v[q] = reinterpret_cast<const float4*>(V + (size_t)(i + q) * vs)[id];
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 const float2 c = cf[i + q];
@@ -281,7 +284,7 @@ __global__ void __launch_bounds__(NT) update_kernel(const float2* __restrict__ V
             }
         }
         for (; i < nv; ++i) {
-            const float4 v = reinterpret_cast<const float4*>(V + (size_t)i * npts)[id];
+            const float4 v = reinterpret_cast<const float4*>(V + (size_t)i * vs)[id];
             const float2 c = cf[i];
             x.x -= c.x * v.x - c.y * v.y;
             x.y -= c.x * v.y + c.y * v.x;
@@ -384,7 +387,7 @@ __device__ __forceinline__ void acc2(float& S, float& C, float p) {
 }
 __global__ void __launch_bounds__(NT) combine_flex_kernel(const float2* __restrict__ Z, size_t npts, int k,
                                                          const double2* __restrict__ y, float4* __restrict__ x,
-                                                         const int* __restrict__ kdev) {
+                                                         const int* __restrict__ kdev, size_t vs) {
     __shared__ float4 ys[64];   // (re.hi, im.hi, re.lo, im.lo)
     if (kdev) k = *kdev;
     for (int i = threadIdx.x; i < k; i += NT) {
@@ -413,11 +416,11 @@ __global__ void __launch_bounds__(NT) combine_flex_kernel(const float2* __restri
         for (; i + 4 <= k; i += 4) {   // four loads in flight
             float2 zv[4];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) zv[q] = Z[(size_t)(i + q) * npts + id];
+            for (int q = 0; q < 4; ++q) zv[q] = Z[(size_t)(i + q) * vs + id];
 #pragma unroll
             for (int q = 0; q < 4; ++q) term(ys[i + q], zv[q]);
         }
-        for (; i < k; ++i) term(ys[i], Z[(size_t)i * npts + id]);
+        for (; i < k; ++i) term(ys[i], Z[(size_t)i * vs + id]);
         const cdf corr{df_quick(Sr, Cr), df_quick(Si, Ci)};
         x[id] = cdf_to4(cdf_add(cdf_from4(x[id]), corr));
     }
@@ -426,7 +429,7 @@ __global__ void __launch_bounds__(NT) combine_flex_kernel(const float2* __restri
 // right-preconditioned: u = sum_i (y_i sigma_i) V_i  (complex64; u is a complex64 preconditioner input)
 __global__ void __launch_bounds__(NT) combine_v_kernel(const float2* __restrict__ V, size_t npts, int k,
                                                       const double2* __restrict__ y, const double* __restrict__ sigma,
-                                                      float2* __restrict__ u, const int* __restrict__ kdev) {
+                                                      float2* __restrict__ u, const int* __restrict__ kdev, size_t vs) {
     __shared__ float2 ys[64];
     if (kdev) k = *kdev;
     for (int i = threadIdx.x; i < k; i += NT) {
@@ -436,7 +439,7 @@ __global__ void __launch_bounds__(NT) combine_v_kernel(const float2* __restrict_
     __syncthreads();
     for (size_t id = blockIdx.x * (size_t)NT + threadIdx.x; id < npts; id += (size_t)gridDim.x * NT) {
         float2 a = make_float2(0.f, 0.f);
-        for (int i = 0; i < k; ++i) a = cfma(ys[i], V[(size_t)i * npts + id], a);
+        for (int i = 0; i < k; ++i) a = cfma(ys[i], V[(size_t)i * vs + id], a);
         u[id] = a;
     }
 }
@@ -562,11 +565,11 @@ void free_work(KrylovWork* k) {
 
 int dots_ctas(const helm_ctx* c);
 int launch_dots(const helm_ctx* c, const float2* V, size_t npts, int nv, const float2* w, double2* part, int ld,
-                int nbd, cudaStream_t s);
+                int nbd, cudaStream_t s, size_t vs = 0);
 
 // Krylov workspace of restart length m for the context's grid; NB = CTAs of the Arnoldi kernels.
 helm_status alloc_work(helm_ctx* c, KrylovWork* k, int m, int flex, int NB) {
-    k->m = m; k->flexible = flex; k->npts = c->npts;
+    k->m = m; k->flexible = flex; k->npts = c->npts; k->vs = c->npts;
     k->NB = NB;
     k->NBd = dots_ctas(c);
     k->nres = residual_ctas(c);
@@ -618,15 +621,17 @@ int dots_ctas(const helm_ctx* c) {
     return m;   // partial buffers sized for any variant
 }
 
+// vs: distance between consecutive basis vectors (0 = npts, the single solve's contiguous basis)
 int launch_dots(const helm_ctx* c, const float2* V, size_t npts, int nv, const float2* w, double2* part, int ld,
-                int nbd, cudaStream_t s) {
+                int nbd, cudaStream_t s, size_t vs) {
     (void)nbd;
+    if (!vs) vs = npts;
     // variant 2 takes the four-wide kernel for up to four vectors (fewer registers, more resident CTAs)
     const int v = (c->tune_dots == 2 && nv <= 4) ? 1 : c->tune_dots;
     const int nb = dots_ctas_for(c, v);
-    if (v == 1) dots_pipe_kernel<4><<<nb, NT, 0, s>>>(V, npts, nv, w, part, ld);
-    else if (v == 2) dots_pipe_kernel<8><<<nb, NT, 0, s>>>(V, npts, nv, w, part, ld);
-    else dots_kernel<<<nb, NT, 0, s>>>(V, npts, nv, w, part, ld);
+    if (v == 1) dots_pipe_kernel<4><<<nb, NT, 0, s>>>(V, npts, nv, w, part, ld, vs);
+    else if (v == 2) dots_pipe_kernel<8><<<nb, NT, 0, s>>>(V, npts, nv, w, part, ld, vs);
+    else dots_kernel<<<nb, NT, 0, s>>>(V, npts, nv, w, part, ld, vs);
     return nb;
 }
 
@@ -754,7 +759,7 @@ helm_status gmres_run(helm_ctx* c, const double2* b_in, double2* x_in, helm_solv
                                                       k->coef, pass == 0);
                     prof_end(c, s);
                     prof_begin(c, s, PROF_UPDATE);
-                    update_kernel<<<ublocks, NT, 0, s>>>(k->V, npts, j + 1, k->coef, w, k->part, ld);
+                    update_kernel<<<ublocks, NT, 0, s>>>(k->V, npts, j + 1, k->coef, w, k->part, ld, npts);
                     prof_end(c, s);
                 }
                 prof_begin(c, s, PROF_SMALL);
@@ -799,12 +804,12 @@ helm_status gmres_run(helm_ctx* c, const double2* b_in, double2* x_in, helm_solv
             prof_end(c, s);
             if (flex) {
                 prof_begin(c, s, PROF_COMBINE);
-                combine_flex_kernel<<<NB, NT, 0, s>>>(k->Z, npts, kk, k->y, k->xdf, nullptr);
+                combine_flex_kernel<<<NB, NT, 0, s>>>(k->Z, npts, kk, k->y, k->xdf, nullptr, npts);
                 prof_end(c, s);
             } else {
                 float2* u = k->V + (size_t)kk * npts;   // V_kk is not needed by the update
                 prof_begin(c, s, PROF_COMBINE);
-                combine_v_kernel<<<NB, NT, 0, s>>>(k->V, npts, kk, k->y, k->sigma, u, nullptr);
+                combine_v_kernel<<<NB, NT, 0, s>>>(k->V, npts, kk, k->y, k->sigma, u, nullptr, npts);
                 prof_end(c, s);
                 if ((st = precond_apply(c, u, u, nullptr, 0, s)) != HELM_OK) return st;
                 prof_begin(c, s, PROF_COMBINE);
@@ -933,8 +938,8 @@ extern "C" helm_status helm_autotune(helm_ctx* c, int* nb_out, int* variant_out,
         float tmin = 1e30f;
         for (int rep = 0; rep < 4; ++rep) {
             cudaEventRecord(e0, s);
-            dots_kernel<<<nb, NT, 0, s>>>(V, npts, nv, w, part, ld);
-            update_kernel<<<nb, NT, 0, s>>>(V, npts, nv, coef, w, part, ld);
+            dots_kernel<<<nb, NT, 0, s>>>(V, npts, nv, w, part, ld, npts);
+            update_kernel<<<nb, NT, 0, s>>>(V, npts, nv, coef, w, part, ld, npts);
             cudaEventRecord(e1, s);
             cudaEventSynchronize(e1);
             float ms = 0.f;
@@ -1134,10 +1139,10 @@ helm_status lane_iteration(Lane& ln, int j, cudaGraphConditionalHandle hnext, in
     if ((st = launch_stencil_f32(c, z, w, nullptr, 0, s)) != HELM_OK) return st;
     const int passes = c->opt.reorth ? 2 : 1;
     for (int pass = 0; pass < passes; ++pass) {
-        const int nbd = launch_dots(c, k->V, npts, j + 1, w, k->part, ld, k->NBd, s);
+        const int nbd = launch_dots(c, k->V, npts, j + 1, w, k->part, ld, k->NBd, s, k->vs);
         reduce_h_kernel<<<j + 1, 128, 0, s>>>(k->part, nbd, ld, j + 1, k->sigma, k->H + (size_t)j * (m + 1), k->coef,
                                           pass == 0);
-        update_kernel<<<NB, NT, 0, s>>>(k->V, npts, j + 1, k->coef, w, k->part, ld);
+        update_kernel<<<NB, NT, 0, s>>>(k->V, npts, j + 1, k->coef, w, k->part, ld, k->vs);
     }
     givens_kernel<<<1, 256, 0, s>>>(k->part, NB, ld, j, m, k->H, k->cs, k->sn, k->g, k->sigma, k->ctrl_d);
     lane_iter_end_kernel<<<1, 32, 0, s>>>(k->ctrl_d, ln.L_d, j, hnext, has_next);
@@ -1154,9 +1159,9 @@ helm_status lane_cycle_end(Lane& ln, cudaStream_t s) {
     helm_status st;
     lsq_kernel<<<1, 32, 0, s>>>(k->H, k->g, 0, m, k->y, k->ctrl_d, kk);
     if (k->flexible) {
-        combine_flex_kernel<<<NB, NT, 0, s>>>(k->Z, npts, 0, k->y, k->xdf, kk);
+        combine_flex_kernel<<<NB, NT, 0, s>>>(k->Z, npts, 0, k->y, k->xdf, kk, k->vs);
     } else {
-        combine_v_kernel<<<NB, NT, 0, s>>>(k->V, npts, 0, k->y, k->sigma, k->Z, kk);
+        combine_v_kernel<<<NB, NT, 0, s>>>(k->V, npts, 0, k->y, k->sigma, k->Z, kk, k->vs);
         if ((st = lane_precond(ln, k->Z, k->Z, nullptr, 0, s)) != HELM_OK) return st;
         add_kernel<<<NB, NT, 0, s>>>(k->Z, k->xdf, npts);
     }

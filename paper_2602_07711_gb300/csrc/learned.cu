@@ -212,21 +212,24 @@ __global__ void avgpool2_kernel(const bf16* __restrict__ in, size_t in_bs, bf16*
     }
 }
 
-// out (full res, channels 0..C-1 of a [B][Cu] buffer) = upsample2(in)
+// out (full res, channels 0..C-1 of a [B][Cu] buffer) = upsample2(in): one thread per pair of output points
+// (x even, x + 1) of a row, which share their source value; grid.x = (x block, y, z), grid.y = (b, c)
 __global__ void upsample2_kernel(const bf16* __restrict__ in, bf16* __restrict__ out, size_t out_bs, int C, int B,
                                  int Z, int Y, int X) {
-    const size_t vol = (size_t)Z * Y * X;
-    const size_t n = (size_t)B * C * vol;
     const int Zh = Z / 2, Yh = Y / 2, Xh = X / 2;
-    for (size_t id = blockIdx.x * (size_t)blockDim.x + threadIdx.x; id < n; id += (size_t)gridDim.x * blockDim.x) {
-        size_t r = id;
-        const int x = r % X; r /= X;
-        const int y = r % Y; r /= Y;
-        const int z = r % Z; r /= Z;
-        const int c = r % C; const int b = (int)(r / C);
-        out[(size_t)b * out_bs + (size_t)c * vol + ((size_t)z * Y + y) * X + x] =
-            in[(((size_t)b * C + c) * Zh + z / 2) * Yh * Xh + (size_t)(y / 2) * Xh + x / 2];
-    }
+    const int nxb = (Xh + blockDim.x - 1) / blockDim.x;
+    int r = blockIdx.x;
+    const int xh = (r % nxb) * blockDim.x + threadIdx.x;
+    r /= nxb;
+    const int y = r % Y, z = r / Y;
+    if (xh >= Xh) return;
+    const int c = blockIdx.y % C, b = blockIdx.y / C;
+    const bf16 v = in[(((size_t)b * C + c) * Zh + z / 2) * ((size_t)Yh * Xh) + (size_t)(y / 2) * Xh + xh];
+    __nv_bfloat162 two;
+    two.x = v;
+    two.y = v;
+    bf16* o = out + (size_t)b * out_bs + (size_t)c * Z * Y * X + ((size_t)z * Y + y) * X + 2 * xh;
+    *reinterpret_cast<__nv_bfloat162*>(o) = two;
 }
 
 // g_half[b][c] = mask(b2 > 0) * sum of the 8 children of gu[b][c] (adjoint of upsample2)
@@ -520,7 +523,8 @@ void forward(helm_net* n, unsigned* status, cudaStream_t s) {
                      nullptr, 0, status, s);
     conv<bf16, bf16>(n, n->b1, 2 * c, 2 * c * hv, W + n->woff[3], 0, F + n->boff[3], n->b2, 2 * c, 2 * c * hv, B, Z / 2, Y / 2,
                      X / 2, 1, nullptr, 0, status, s);
-    upsample2_kernel<<<nblk(B * 2 * c * vol), 256, 0, s>>>(n->b2, n->u, 3 * c * vol, 2 * c, B, Z, Y, X);
+    upsample2_kernel<<<dim3((unsigned)((X / 2 + 127) / 128 * Y * Z), (unsigned)(B * 2 * c)), 128, 0, s>>>(
+        n->b2, n->u, 3 * c * vol, 2 * c, B, Z, Y, X);
     conv<bf16, bf16>(n, n->u, 3 * c, 3 * c * vol, W + n->woff[4], 0, F + n->boff[4], n->d1, c, c * vol, B, Z, Y, X, 1, nullptr,
                      0, status, s);
     conv<bf16, float>(n, n->d1, c, c * vol, W + n->woff[5], 0, F + n->boff[5], n->y, 2, 2 * vol, B, Z, Y, X, 0, nullptr, 0, status, s);
