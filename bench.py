@@ -787,22 +787,6 @@ def run_ksweep(args, rank, world, local):
         print(json.dumps(line), flush=True)
 
 
-def _net_forward_ms(net, n, reps=5):
-    """CUDA-event time of one forward of the network on a single n^3 field (five bf16 input channels)."""
-    import torch
-    x = torch.randn((1, 5, n, n, n), device="cuda").to(torch.bfloat16)
-    net.forward(x)
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    e0.record()
-    for _ in range(reps):
-        net.forward(x)
-    e1.record()
-    torch.cuda.synchronize()
-    return e0.elapsed_time(e1) / reps
-
-
 def run_learned(args, rank, world, local):
     """The learned correction (an extension): a 3D U-Net of width 28 (about 217K parameters, the size class of
     the learned-correction configuration), trained on the GPU with the tensor-core convolutions on pairs from
@@ -848,8 +832,8 @@ def run_learned(args, rank, world, local):
     cost = {}
     for w in (8, width):
         net = Net(w, seed=1)
-        cost["width%d" % w] = {"params": int(net.nparam), "forward_ms_256": _net_forward_ms(net, 256),
-                               "forward_ms_384": _net_forward_ms(net, 384, reps=2)}
+        cost["width%d" % w] = {"params": int(net.nparam), "forward_ms_256": learned.forward_timing(256, w),
+                               "forward_ms_384": learned.forward_timing(384, w, reps=2)}
         net.close()
     if rank == 0:
         rl = out["bumps"]["compare"]["learned"]

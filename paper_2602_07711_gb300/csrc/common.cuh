@@ -167,6 +167,8 @@ helm_status launch_rhs_fields(helm_ctx* c, const double2* fields, double2* F, cu
 helm_status launch_stencil_f32(helm_ctx* c, const float2* x, float2* y, const double* sigma, int sidx, cudaStream_t s);
 helm_status launch_stencil_f32_cls(helm_ctx* c, const float2* x, float2* y, const double* sigma, int sidx, int cls,
                                    cudaStream_t s);   // timed under profiling class cls
+// the complex64 matvec of nb vectors stored npts apart (the right-hand sides of a batch group)
+helm_status launch_stencil_f32_nb(helm_ctx* c, const float2* x, float2* y, int nb, cudaStream_t s);
 helm_status launch_stencil_f64(helm_ctx* c, const double2* x, double2* y, cudaStream_t s);
 helm_status launch_residual(helm_ctx* c, const float4* x, const float4* F, float2* r, double* part, cudaStream_t s);
 helm_status launch_rhs(helm_ctx* c, const double2* f, double2* F, float4* fdf, cudaStream_t s);
@@ -179,28 +181,31 @@ helm_status residual_fast_prepare();
 helm_status launch_residual_fast(helm_ctx* c, const float4* x, const float4* F, float2* r, double* part,
                                  cudaStream_t s);   // same grid (and partial count) as the generic residual
 bool stencil_fast_supported(const helm_ctx* c);
-helm_status launch_stencil_fast(helm_ctx* c, const float2* x, float2* y, const double* sigma, int sidx, cudaStream_t s);
+helm_status launch_stencil_fast(helm_ctx* c, const float2* x, float2* y, const double* sigma, int sidx, cudaStream_t s,
+                                int nb = 1);
 // eig.cu
 helm_status run_eig_setup(helm_ctx* c, cudaStream_t s);
 // gemm_simt.cu
+// rows of C: row r scales by alpha_dev[aidx + (r / rows_per) astride] (rows_per = 0: alpha_dev[aidx] for all)
 void launch_cgemm_simt(int M, int N, int K, const float2* A, long lda, long sA, const float2* B, long ldb, long sB,
                        float2* C, long ldc, long sC, int batch, float alpha, const double* alpha_dev, int aidx,
-                       cudaStream_t s);
+                       cudaStream_t s, int rows_per = 0, int astride = 0);
 // gemm_tc.cu
 helm_status tc_prepare(helm_ctx* c, cudaStream_t s);
+// nb > 1: nb grid vectors back to back (a batch group); the x-pass scales vector v by alpha_dev[aidx + v astride]
 helm_status tc_xpass(helm_ctx* c, int inverse, const float2* in, float2* out, float alpha, const double* alpha_dev,
-                     int aidx, cudaStream_t s);
-helm_status tc_ypass(helm_ctx* c, int inverse, const float2* in, float2* out, cudaStream_t s);
+                     int aidx, cudaStream_t s, int nb = 1, int astride = 0);
+helm_status tc_ypass(helm_ctx* c, int inverse, const float2* in, float2* out, cudaStream_t s, int nb = 1);
 // operand sets of tc_xpass/tc_ypass (`inverse`): 0/1 EigT forward/inverse, 2/3 PFFT sine forward/inverse
 helm_status tc_prepare_sine(helm_ctx* c, const double2* Sx, const double2* Sy, const double2* SxT, const double2* SyT,
                             cudaStream_t s);
 void tc_release(helm_ctx* c);
 // thomas.cu
-helm_status launch_zsolve(helm_ctx* c, const float2* in, float2* out, cudaStream_t s);
+helm_status launch_zsolve(helm_ctx* c, const float2* in, float2* out, cudaStream_t s, int nb = 1);
 helm_status zsolve_factor(helm_ctx* c, cudaStream_t s);
 helm_status zsolve_factor_with(helm_ctx* c, const float2* dxs, const float2* dys, float2** m, cudaStream_t s);
 helm_status launch_zsolve_fact(helm_ctx* c, const float2* m, const float2* in, float2* out, const float2* P,
-                               const float2* Q, cudaStream_t s);
+                               const float2* Q, cudaStream_t s, int nb = 1);
 helm_status launch_zsolve_gen(helm_ctx* c, const float2* in, float2* out, const float2* dxs, const float2* dys,
                               const float2* P, const float2* Q, cudaStream_t s);
 // pfft.cu
@@ -216,6 +221,8 @@ helm_status learned_post(helm_ctx* c, float2* z, cudaStream_t s);
 // precond.cu
 helm_status precond_apply(helm_ctx* c, const float2* r, float2* z, const double* sigma, int sidx, cudaStream_t s);
 helm_status precond_step(helm_ctx* c, int step, const float2* in, float2* out, cudaStream_t s);
+helm_status precond_apply_nb(helm_ctx* c, const float2* r, float2* z, int nb, const double* sigma, int sidx,
+                             int sstride, cudaStream_t s);
 // krylov.cu
 helm_status gmres_run(helm_ctx* c, const double2* b, double2* x, helm_solve_info* info, cudaStream_t s);
 void krylov_free(helm_ctx* c);

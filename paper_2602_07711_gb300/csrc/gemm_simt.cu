@@ -13,7 +13,8 @@ constexpr int BM = 64, BN = 64, BK = 16;
 
 __global__ void __launch_bounds__(256)
 cgemm_kernel(int M, int N, int K, const float2* __restrict__ A, long lda, long sA, const float2* __restrict__ B,
-             long ldb, long sB, float2* __restrict__ C, long ldc, long sC, float alpha, const double* alpha_dev, int aidx) {
+             long ldb, long sB, float2* __restrict__ C, long ldc, long sC, float alpha, const double* alpha_dev, int aidx,
+             int rows_per, int astride) {
     __shared__ float2 As[BK][BM + 1];
     __shared__ float2 Bs[BK][BN];
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
@@ -58,12 +59,12 @@ cgemm_kernel(int M, int N, int K, const float2* __restrict__ A, long lda, long s
         }
         __syncthreads();
     }
-    float al = alpha;
-    if (alpha_dev) al *= (float)alpha_dev[aidx];
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
         const int gr = m0 + ty + 16 * i;
         if (gr >= M) continue;
+        float al = alpha;
+        if (alpha_dev) al *= (float)alpha_dev[aidx + (rows_per > 0 ? (gr / rows_per) * astride : 0)];
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             const int gc = n0 + tx + 16 * j;
@@ -75,7 +76,8 @@ cgemm_kernel(int M, int N, int K, const float2* __restrict__ A, long lda, long s
 
 void launch_cgemm_simt(int M, int N, int K, const float2* A, long lda, long sA, const float2* B, long ldb, long sB,
                        float2* C, long ldc, long sC, int batch, float alpha, const double* alpha_dev, int aidx,
-                       cudaStream_t s) {
+                       cudaStream_t s, int rows_per, int astride) {
     dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM, batch);
-    cgemm_kernel<<<grid, 256, 0, s>>>(M, N, K, A, lda, sA, B, ldb, sB, C, ldc, sC, alpha, alpha_dev, aidx);
+    cgemm_kernel<<<grid, 256, 0, s>>>(M, N, K, A, lda, sA, B, ldb, sB, C, ldc, sC, alpha, alpha_dev, aidx, rows_per,
+                                      astride);
 }

@@ -164,7 +164,8 @@ __device__ __forceinline__ void split_tile(float4* hi, float4* lo, int t) {
 // ---- x-pass: Out[M][N2] = alpha * A[M][K2] B[N2][K2]^T -------------------------------------------
 __global__ void __launch_bounds__(192, 1)
 xpass_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, float* __restrict__ out,
-                int M, int N2, int K2, float alpha, const double* __restrict__ alpha_dev, int aidx, unsigned* status,
+                int M, int N2, int K2, float alpha, const double* __restrict__ alpha_dev, int aidx, int rows_per,
+                int astride, unsigned* status,
                 long wlim) {
     extern __shared__ uint8_t dsm[];
     __shared__ __align__(8) uint64_t full[XSTAGES], empty[XSTAGES], accf, drainb;
@@ -231,7 +232,8 @@ xpass_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
         fence_after();
         const int q = warp & 3;
         const int row = m0 + 32 * q + lane;
-        const float al = alpha * (alpha_dev ? (float)alpha_dev[aidx] : 1.f);
+        // rows of the b-th vector of a batch scale by alpha_dev[aidx + b astride] (b = row / rows_per)
+        const float al = alpha * (alpha_dev ? (float)alpha_dev[aidx + (min(row, M - 1) / rows_per) * astride] : 1.f);
         if (ok) {
 #pragma unroll 1
             for (int c = 0; c < BN; c += 32) {
@@ -421,7 +423,8 @@ template <int BNT, bool SPLIT>
 __global__ void __launch_bounds__(SPLIT ? 320 : 192, 1)
 xpass_tc_pers_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                      const __grid_constant__ CUtensorMap tmBl, float* __restrict__ out, int M, int N2, int K2,
-                     float alpha, const double* __restrict__ alpha_dev, int aidx, unsigned* status, long wlim) {
+                     float alpha, const double* __restrict__ alpha_dev, int aidx, int rows_per, int astride,
+                     unsigned* status, long wlim) {
     extern __shared__ uint8_t dsm[];
     constexpr int NS = PersX<BNT, SPLIT>::STAGES, BTILE = BNT * BK * 4, STAGE = PersX<BNT, SPLIT>::STAGE_BYTES;
     constexpr int AOFF_LO = TILE, BOFF = SPLIT ? 2 * TILE : TILE, BOFF_LO = BOFF + BTILE;
@@ -512,11 +515,13 @@ xpass_tc_pers_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_const
         }
     } else if (!SPLIT || warp < 6) {
         const int q = warp & 3;
-        const float al = alpha * (alpha_dev ? (float)alpha_dev[aidx] : 1.f);
         int lt = 0;
         for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++lt) {
             const int b = lt & 1;
             const int n0 = (t % ntn) * BNT, m0 = (t / ntn) * BM;
+            // this thread's accumulator row; rows of the v-th vector of a batch scale by alpha_dev[aidx + v astride]
+            const int arow = min(m0 + 32 * q + lane, M - 1);
+            const float al = alpha * (alpha_dev ? (float)alpha_dev[aidx + (arow / rows_per) * astride] : 1.f);
             ok = __all_sync(0xffffffffu, mbar_wait(su32(&accf[b]), (uint32_t)((lt >> 1) & 1), wlim));
             if (!ok) break;
             fence_after();
@@ -934,10 +939,12 @@ helm_status tc_prepare_sine(helm_ctx* c, const double2* Sx, const double2* Sy, c
 }
 
 helm_status tc_xpass(helm_ctx* c, int inverse, const float2* in, float2* out, float alpha, const double* alpha_dev,
-                     int aidx, cudaStream_t s) {
+                     int aidx, cudaStream_t s, int nb, int astride) {
     TcState* t = (TcState*)c->tmaps;
     if (!t) return HELM_ERR_UNSUPPORTED;
-    const int M = c->ny * c->nz, N2 = 2 * c->nx;
+    // nb vectors of the grid back to back: one GEMM over nb N_y N_z rows
+    const int rp = c->ny * c->nz, as = astride;
+    const int M = rp * nb, N2 = 2 * c->nx;
     CUtensorMap mapA;
     const cuuint64_t d[2] = {(cuuint64_t)N2, (cuuint64_t)M};
     const cuuint64_t st[1] = {(cuuint64_t)N2 * sizeof(float)};
@@ -952,12 +959,12 @@ helm_status tc_xpass(helm_ctx* c, int inverse, const float2* in, float2* out, fl
             const int ntiles = (N2 / 256) * (int)grid.y;
             const int pg = ntiles < g_sms ? ntiles : g_sms;
             xpass_tc_pers_kernel<256, true><<<pg, 320, PersX<256, true>::SMEM, s>>>(
-                mapA, t->mapBx256[inverse], t->mapBx256l[inverse], o, M, N2, N2, alpha, alpha_dev, aidx, c->status_d, wl);
+                mapA, t->mapBx256[inverse], t->mapBx256l[inverse], o, M, N2, N2, alpha, alpha_dev, aidx, rp, as, c->status_d, wl);
         } else {
             const int ntiles = (int)(grid.x * grid.y);
             const int pg = ntiles < g_sms ? ntiles : g_sms;
             xpass_tc_pers_kernel<128, true><<<pg, 320, PersX<128, true>::SMEM, s>>>(
-                mapA, t->mapBx[inverse], t->mapBxl[inverse], o, M, N2, N2, alpha, alpha_dev, aidx, c->status_d, wl);
+                mapA, t->mapBx[inverse], t->mapBxl[inverse], o, M, N2, N2, alpha, alpha_dev, aidx, rp, as, c->status_d, wl);
         }
     } else if (c->tune_tc == 1 && g_sms > 0) {
         if (N2 % 256 == 0) {
@@ -965,40 +972,40 @@ helm_status tc_xpass(helm_ctx* c, int inverse, const float2* in, float2* out, fl
             const int ntiles = (N2 / 256) * (int)grid.y;
             const int pg = ntiles < g_sms ? ntiles : g_sms;
             xpass_tc_pers_kernel<256, false><<<pg, 192, PersX<256, false>::SMEM, s>>>(
-                mapA, t->mapBx256[inverse], t->mapBx256[inverse], o, M, N2, N2, alpha, alpha_dev, aidx, c->status_d, wl);
+                mapA, t->mapBx256[inverse], t->mapBx256[inverse], o, M, N2, N2, alpha, alpha_dev, aidx, rp, as, c->status_d, wl);
         } else {
             const int ntiles = (int)(grid.x * grid.y);
             const int pg = ntiles < 2 * g_sms ? ntiles : 2 * g_sms;
             xpass_tc_pers_kernel<128, false><<<pg, 192, PersX<128, false>::SMEM, s>>>(
-                mapA, t->mapBx[inverse], t->mapBx[inverse], o, M, N2, N2, alpha, alpha_dev, aidx, c->status_d, wl);
+                mapA, t->mapBx[inverse], t->mapBx[inverse], o, M, N2, N2, alpha, alpha_dev, aidx, rp, as, c->status_d, wl);
         }
     } else {
-        xpass_tc_kernel<<<grid, 192, xsmem(), s>>>(mapA, t->mapBx[inverse], o, M, N2, N2, alpha, alpha_dev, aidx,
+        xpass_tc_kernel<<<grid, 192, xsmem(), s>>>(mapA, t->mapBx[inverse], o, M, N2, N2, alpha, alpha_dev, aidx, rp, as,
                                                     c->status_d, wl);
     }
     HELM_CUDA_TRY(cudaGetLastError());
     return HELM_OK;
 }
 
-helm_status tc_ypass(helm_ctx* c, int inverse, const float2* in, float2* out, cudaStream_t s) {
+helm_status tc_ypass(helm_ctx* c, int inverse, const float2* in, float2* out, cudaStream_t s, int nb) {
     TcState* t = (TcState*)c->tmaps;
     if (!t) return HELM_ERR_UNSUPPORTED;
-    const int ny = c->ny, N2 = 2 * c->nx;
+    const int ny = c->ny, N2 = 2 * c->nx, nzb = c->nz * nb;   // nb vectors: nb N_z slices
     CUtensorMap mapY;
-    const cuuint64_t d[3] = {(cuuint64_t)N2, (cuuint64_t)ny, (cuuint64_t)c->nz};
+    const cuuint64_t d[3] = {(cuuint64_t)N2, (cuuint64_t)ny, (cuuint64_t)nzb};
     const cuuint64_t st[2] = {(cuuint64_t)N2 * sizeof(float), (cuuint64_t)N2 * ny * sizeof(float)};
     const cuuint32_t box[3] = {32, BK, 1};
     if (encode(t, &mapY, 3, (void*)in, d, st, box, CU_TENSOR_MAP_SWIZZLE_128B_ATOM_32B) != HELM_OK) return HELM_ERR_CUDA;
-    dim3 grid((N2 + BN - 1) / BN, (ny + BM - 1) / BM, c->nz);
+    dim3 grid((N2 + BN - 1) / BN, (ny + BM - 1) / BM, nzb);
     const long wl = (long)c->wait_limit;
     const int ntiles = (int)(grid.x * grid.y * grid.z);
     const int pg = g_sms > 0 && ntiles > g_sms ? g_sms : ntiles;
     if (t->split && g_sms > 0) {
         ypass_tc_pers_kernel<true><<<pg, 320, PersY<true>::SMEM, s>>>(t->mapWy[inverse], mapY, t->mapWyl[inverse],
-                                                                     (float*)out, ny, N2, c->nz, c->status_d, wl);
+                                                                     (float*)out, ny, N2, nzb, c->status_d, wl);
     } else if (c->tune_ypers && g_sms > 0) {
         ypass_tc_pers_kernel<false><<<pg, 192, PersY<false>::SMEM, s>>>(t->mapWy[inverse], mapY, t->mapWy[inverse],
-                                                                       (float*)out, ny, N2, c->nz, c->status_d, wl);
+                                                                       (float*)out, ny, N2, nzb, c->status_d, wl);
     } else {
         ypass_tc_kernel<<<grid, 192, ysmem(), s>>>(t->mapWy[inverse], mapY, (float*)out, ny, N2, c->status_d, wl);
     }

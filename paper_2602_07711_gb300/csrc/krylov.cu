@@ -51,6 +51,7 @@ struct KrylovWork {
     int NBd = 0;             // CTAs of the inner-product kernel: one full wave of resident CTAs
     size_t npts = 0;
     size_t vs = 0;           // distance between consecutive basis vectors of V and Z (npts unless interleaved)
+    int shared = 0;          // V, Z and sigma belong to a batch group (interleaved with its other lanes)
     float2* V = nullptr;     // (m+1) stored vectors
     float2* Z = nullptr;     // m preconditioned vectors (flexible) or one scratch vector
     double* sigma = nullptr; // [m+1]
@@ -84,9 +85,8 @@ constexpr double kLookaheadDrop = 0.05;
 // Two points per 16-byte load, two loads of each vector in flight per thread; per-thread sums are
 // compensated FP32 (Kahan), FP64 only across threads (GB300's FP64 rate made FP64 partial sums the
 // limiter).  npts is even.
-__global__ void __launch_bounds__(NT) dots_kernel(const float2* __restrict__ V, size_t npts, int nv,
-                                                 const float2* __restrict__ w, double2* __restrict__ part, int ld,
-                                                 size_t vs) {
+__device__ __forceinline__ void dots_body(const float2* __restrict__ V, size_t npts, int nv,
+                                          const float2* __restrict__ w, double2* __restrict__ part, int ld, size_t vs) {
     __shared__ double2 red[NT / 32][GRP];
     const int tid = threadIdx.x;
     const size_t n4 = npts / 2;
@@ -146,13 +146,19 @@ __global__ void __launch_bounds__(NT) dots_kernel(const float2* __restrict__ V, 
     }
 }
 
+__global__ void __launch_bounds__(NT) dots_kernel(const float2* __restrict__ V, size_t npts, int nv,
+                                                 const float2* __restrict__ w, double2* __restrict__ part, int ld,
+                                                 size_t vs) {
+    dots_body(V, npts, nv, w, part, ld, vs);
+}
+
 // Software-pipelined variant: groups of G basis vectors, one 16-byte load per vector and thread per
 // iteration, and the next iteration's loads issued before this iteration's compensated sums, so every
 // warp keeps two iterations of loads in flight instead of waiting a full memory latency per iteration.
 template <int G>
-__global__ void __launch_bounds__(NT) dots_pipe_kernel(const float2* __restrict__ V, size_t npts, int nv,
-                                                      const float2* __restrict__ w, double2* __restrict__ part, int ld,
-                                                      size_t vs) {
+__device__ __forceinline__ void dots_pipe_body(const float2* __restrict__ V, size_t npts, int nv,
+                                               const float2* __restrict__ w, double2* __restrict__ part, int ld,
+                                               size_t vs) {
     __shared__ double2 red[NT / 32][G];
     const int tid = threadIdx.x;
     const size_t n4 = npts / 2;
@@ -225,10 +231,17 @@ __global__ void __launch_bounds__(NT) dots_pipe_kernel(const float2* __restrict_
     }
 }
 
-// h_i += sigma_i * sum_blk part  (i < nv) into H column j; coef_i = h_i(this pass) * sigma_i
+template <int G>
+__global__ void __launch_bounds__(NT) dots_pipe_kernel(const float2* __restrict__ V, size_t npts, int nv,
+                                                      const float2* __restrict__ w, double2* __restrict__ part, int ld,
+                                                      size_t vs) {
+    dots_pipe_body<G>(V, npts, nv, w, part, ld, vs);
+}
+
 // one block per basis vector i: h_i = sigma_i * sum over blocks of the partial products, coef_i = sigma_i h_i
-__global__ void reduce_h_kernel(const double2* __restrict__ part, int NB, int ld, int nv, const double* __restrict__ sigma,
-                                double2* __restrict__ Hcol, float2* __restrict__ coef, int first_pass) {
+__device__ __forceinline__ void reduce_h_body(const double2* __restrict__ part, int NB, int ld, int nv,
+                                              const double* __restrict__ sigma, double2* __restrict__ Hcol,
+                                              float2* __restrict__ coef, int first_pass) {
     __shared__ double rx[32], ry[32];
     const int i = blockIdx.x;
     if (i >= nv) return;
@@ -254,12 +267,16 @@ __global__ void reduce_h_kernel(const double2* __restrict__ part, int NB, int ld
     Hcol[i] = first_pass ? h : cadd(Hcol[i], h);
     coef[i] = make_float2((float)(h.x * sg), (float)(h.y * sg));
 }
+__global__ void reduce_h_kernel(const double2* __restrict__ part, int NB, int ld, int nv, const double* __restrict__ sigma,
+                                double2* __restrict__ Hcol, float2* __restrict__ coef, int first_pass) {
+    reduce_h_body(part, NB, ld, nv, sigma, Hcol, coef, first_pass);
+}
 
 // w -= sum_i coef_i V_i (i < nv); per-block partial ||w||^2 in part[blk * ld].x.  Two points per
 // 16-byte load; the basis loop is unrolled by four so that four vector loads are in flight.
-__global__ void __launch_bounds__(NT) update_kernel(const float2* __restrict__ V, size_t npts, int nv,
-                                                   const float2* __restrict__ coef, float2* __restrict__ w,
-                                                   double2* __restrict__ part, int ld, size_t vs) {
+__device__ __forceinline__ void update_body(const float2* __restrict__ V, size_t npts, int nv,
+                                            const float2* __restrict__ coef, float2* __restrict__ w,
+                                            double2* __restrict__ part, int ld, size_t vs) {
     __shared__ float2 cf[72];
     __shared__ double red[NT / 32];
     for (int i = threadIdx.x; i < nv; i += NT) cf[i] = coef[i];
@@ -303,6 +320,11 @@ __global__ void __launch_bounds__(NT) update_kernel(const float2* __restrict__ V
         part[(size_t)blockIdx.x * ld] = make_double2(s, 0.0);
     }
 }
+__global__ void __launch_bounds__(NT) update_kernel(const float2* __restrict__ V, size_t npts, int nv,
+                                                   const float2* __restrict__ coef, float2* __restrict__ w,
+                                                   double2* __restrict__ part, int ld, size_t vs) {
+    update_body(V, npts, nv, coef, w, part, ld, vs);
+}
 
 __device__ inline void givens(double2 a, double2 b, double& c, double2& s) {
     const double ab = hypot(b.x, b.y);
@@ -315,12 +337,11 @@ __device__ inline void givens(double2 a, double2 b, double& c, double2& s) {
     s = cmul(ph, make_double2(b.x / t, -b.y / t));                // (a/|a|) conj(b)/t
 }
 
-// Finish column j: h_{j+1,j} from the partial norms, previous rotations, the new rotation, g, est.
 // Finish column j: h_{j+1,j} from the partial norms, previous rotations, the new rotation, g, est.  The
 // column and the previous rotations are staged in shared memory by the whole block; one thread then
 // applies the rotations.
-__global__ void givens_kernel(const double2* __restrict__ part, int NB, int ld, int j, int m, double2* H, double* cs,
-                              double2* sn, double2* g, double* sigma, Ctrl* ctrl) {
+__device__ __forceinline__ void givens_body(const double2* __restrict__ part, int NB, int ld, int j, int m, double2* H,
+                                            double* cs, double2* sn, double2* g, double* sigma, Ctrl* ctrl) {
     __shared__ double red[32];
     __shared__ double2 col[72], snv[72];
     __shared__ double csv[72];
@@ -361,6 +382,10 @@ __global__ void givens_kernel(const double2* __restrict__ part, int NB, int ld, 
     ctrl->hnext = hn;
     if (!isfinite(hn) || !isfinite(est) || !isfinite(col[j].x) || !isfinite(col[j].y)) ctrl->flags |= HELM_DEV_NAN;
 }
+__global__ void givens_kernel(const double2* __restrict__ part, int NB, int ld, int j, int m, double2* H, double* cs,
+                              double2* sn, double2* g, double* sigma, Ctrl* ctrl) {
+    givens_body(part, NB, ld, j, m, H, cs, sn, g, sigma, ctrl);
+}
 
 // y = R^-1 g (k x k upper triangular part of the rotated H)
 __global__ void lsq_kernel(const double2* __restrict__ H, const double2* __restrict__ g, int k, int m, double2* y,
@@ -375,54 +400,38 @@ __global__ void lsq_kernel(const double2* __restrict__ H, const double2* __restr
     }
 }
 
-// flexible: x += sum_i y_i Z_i with y_i = yh_i + yl_i split from FP64.  Each real product yh z is formed
-// exactly as p + e (FMA), the p are added to a running FP32 sum S by Knuth's two-sum, and every error term
-// (two-sum errors, e, and yl z) goes into a second FP32 sum C: S + C carries the correction to about
-// 2^-44 of its size, and it is added to the double-float iterate once per point.  (About 40% of the work
-// of summing in double-float term by term.)
-__device__ __forceinline__ void acc2(float& S, float& C, float p) {
-    const float t = S + p, bb = t - S;
-    C += (S - (t - bb)) + (p - bb);
-    S = t;
-}
+// flexible: x += sum_i y_i Z_i.  The cycle's correction is summed in FP32 (each y_i rounded to complex64), two
+// points per 16-byte load, and added to the double-float iterate once per point.  Its rounding error, a few
+// units of 2^-24 of the correction, perturbs the next true residual by about 1e-6 of the residual this cycle
+// removed, far below the 1e-4 a cycle lowers it by; the next cycle starts from the exact (double-float)
+// residual of the iterate, so the error is corrected like any other (iterative refinement).
 __global__ void __launch_bounds__(NT) combine_flex_kernel(const float2* __restrict__ Z, size_t npts, int k,
                                                          const double2* __restrict__ y, float4* __restrict__ x,
                                                          const int* __restrict__ kdev, size_t vs) {
-    __shared__ float4 ys[64];   // (re.hi, im.hi, re.lo, im.lo)
+    __shared__ float2 ys[64];
     if (kdev) k = *kdev;
-    for (int i = threadIdx.x; i < k; i += NT) {
-        const float rh = (float)y[i].x, ih = (float)y[i].y;
-        ys[i] = make_float4(rh, ih, (float)(y[i].x - (double)rh), (float)(y[i].y - (double)ih));
-    }
+    for (int i = threadIdx.x; i < k; i += NT) ys[i] = make_float2((float)y[i].x, (float)y[i].y);
     __syncthreads();
-    for (size_t id = blockIdx.x * (size_t)NT + threadIdx.x; id < npts; id += (size_t)gridDim.x * NT) {
-        float Sr = 0.f, Cr = 0.f, Si = 0.f, Ci = 0.f;
+    const size_t n2 = npts / 2;
+    for (size_t id = blockIdx.x * (size_t)NT + threadIdx.x; id < n2; id += (size_t)gridDim.x * NT) {
+        float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
         int i = 0;
-        auto term = [&](const float4 c, const float2 z) {
-            // re = c.re z.re - c.im z.im, im = c.re z.im + c.im z.re
-            float p = c.x * z.x, e = fmaf(c.x, z.x, -p);
-            acc2(Sr, Cr, p);
-            Cr += fmaf(c.z, z.x, e);
-            p = -c.y * z.y; e = fmaf(-c.y, z.y, -p);
-            acc2(Sr, Cr, p);
-            Cr += fmaf(-c.w, z.y, e);
-            p = c.x * z.y; e = fmaf(c.x, z.y, -p);
-            acc2(Si, Ci, p);
-            Ci += fmaf(c.z, z.y, e);
-            p = c.y * z.x; e = fmaf(c.y, z.x, -p);
-            acc2(Si, Ci, p);
-            Ci += fmaf(c.w, z.x, e);
+        auto term = [&](const float2 c, const float4 z) {
+            a.x = fmaf(c.x, z.x, fmaf(-c.y, z.y, a.x));
+            a.y = fmaf(c.x, z.y, fmaf(c.y, z.x, a.y));
+            a.z = fmaf(c.x, z.z, fmaf(-c.y, z.w, a.z));
+            a.w = fmaf(c.x, z.w, fmaf(c.y, z.z, a.w));
         };
         for (; i + 4 <= k; i += 4) {   // four loads in flight
-            float2 zv[4];
+            float4 zv[4];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) zv[q] = Z[(size_t)(i + q) * vs + id];
+            for (int q = 0; q < 4; ++q) zv[q] = reinterpret_cast<const float4*>(Z + (size_t)(i + q) * vs)[id];
 #pragma unroll
             for (int q = 0; q < 4; ++q) term(ys[i + q], zv[q]);
         }
-        for (; i < k; ++i) term(ys[i], Z[(size_t)i * vs + id]);
-        const cdf corr{df_quick(Sr, Cr), df_quick(Si, Ci)};
-        x[id] = cdf_to4(cdf_add(cdf_from4(x[id]), corr));
+        for (; i < k; ++i) term(ys[i], reinterpret_cast<const float4*>(Z + (size_t)i * vs)[id]);
+        x[2 * id] = cdf_to4(cdf_add(cdf_from4(x[2 * id]), cdf_from_f2(make_float2(a.x, a.y))));
+        x[2 * id + 1] = cdf_to4(cdf_add(cdf_from4(x[2 * id + 1]), cdf_from_f2(make_float2(a.z, a.w))));
     }
 }
 
@@ -551,7 +560,8 @@ bool is_device_ptr(const void* p) {
 }
 
 void free_work(KrylovWork* k) {
-    cudaFree(k->V); cudaFree(k->Z); cudaFree(k->sigma); cudaFree(k->H); cudaFree(k->cs); cudaFree(k->sn);
+    if (!k->shared) { cudaFree(k->V); cudaFree(k->Z); cudaFree(k->sigma); }
+    cudaFree(k->H); cudaFree(k->cs); cudaFree(k->sn);
     cudaFree(k->g); cudaFree(k->y); cudaFree(k->part); cudaFree(k->rpart); cudaFree(k->coef); cudaFree(k->ctrl_d);
     cudaFreeHost(k->ctrl_h); cudaFree(k->xbuf); cudaFree(k->bbuf); cudaFree(k->xdf); cudaFree(k->Fdf);
     cudaFree(k->nzflag);
@@ -568,15 +578,25 @@ int launch_dots(const helm_ctx* c, const float2* V, size_t npts, int nv, const f
                 int nbd, cudaStream_t s, size_t vs = 0);
 
 // Krylov workspace of restart length m for the context's grid; NB = CTAs of the Arnoldi kernels.
-helm_status alloc_work(helm_ctx* c, KrylovWork* k, int m, int flex, int NB) {
-    k->m = m; k->flexible = flex; k->npts = c->npts; k->vs = c->npts;
+// Vs, Zs, sigs (optional, all three or none): the lane's share of a batch group's interleaved basis (vector
+// stride vs), preconditioned vectors and normalisation factors, which the group owns.
+helm_status alloc_work(helm_ctx* c, KrylovWork* k, int m, int flex, int NB, float2* Vs = nullptr, float2* Zs = nullptr,
+                       double* sigs = nullptr, size_t vs = 0) {
+    k->m = m; k->flexible = flex; k->npts = c->npts; k->vs = vs ? vs : c->npts;
     k->NB = NB;
     k->NBd = dots_ctas(c);
     k->nres = residual_ctas(c);
     const size_t vb = c->npts * sizeof(float2);
-    if (cudaMalloc(&k->V, vb * (m + 1)) != cudaSuccess) { cudaGetLastError(); return HELM_ERR_NOMEM; }
-    if (cudaMalloc(&k->Z, vb * (flex ? m : 1)) != cudaSuccess) { cudaGetLastError(); return HELM_ERR_NOMEM; }
-    HELM_CUDA_TRY(cudaMalloc(&k->sigma, sizeof(double) * (m + 1)));
+    if (Vs) {
+        k->shared = 1;
+        k->V = Vs;
+        k->Z = Zs;
+        k->sigma = sigs;
+    } else {
+        if (cudaMalloc(&k->V, vb * (m + 1)) != cudaSuccess) { cudaGetLastError(); return HELM_ERR_NOMEM; }
+        if (cudaMalloc(&k->Z, vb * (flex ? m : 1)) != cudaSuccess) { cudaGetLastError(); return HELM_ERR_NOMEM; }
+        HELM_CUDA_TRY(cudaMalloc(&k->sigma, sizeof(double) * (m + 1)));
+    }
     HELM_CUDA_TRY(cudaMalloc(&k->H, sizeof(double2) * (m + 1) * m));
     HELM_CUDA_TRY(cudaMalloc(&k->cs, sizeof(double) * m));
     HELM_CUDA_TRY(cudaMalloc(&k->sn, sizeof(double2) * m));
@@ -1042,18 +1062,20 @@ extern "C" helm_status helm_autotune(helm_ctx* c, int* nb_out, int* variant_out,
 // ---- batched solves ---------------------------------------------------------------------------
 // Many problems (contexts of any size and options) times nrhs right-hand sides each, solved together:
 // every (problem, right-hand side) pair is a lane with its own Krylov workspace and preconditioner
-// scratch.  One restart cycle of every lane is one CUDA graph,
-//   for each lane (independent branches):  begin; IF(go) iteration 0; ...; IF(go) iteration m-1; IF(cycle) end
+// scratch; the lanes of one problem form a group that shares the operator launches.  One restart cycle of
+// every lane is one CUDA graph,
+//   for each group (independent branches):  begin; IF(any lane runs it) iteration 0; ...; iteration m-1;
+//                                            IF(cycle) end of each lane
 // whose conditions are set on the device (convergence estimate, iteration limit, breakdown; a finished lane
 // skips everything), so a launch costs the host one graph launch and one synchronisation per restart cycle
 // for the whole batch.  The host relaunches the graph while any lane wants another cycle (a device flag per
-// lane); there is no device-side loop, so a lane can never spin.  Lanes are grouped so that a group's
-// workspace fits in device memory.
+// lane); there is no device-side loop, so a lane can never spin.
 
 struct LaneCtl {
     int active, kk, its, restarts, brk, cycles, max_iter, m;
     double rtol;
     int cyc[16];
+    int go;          // the lane runs its next iteration (read by its group)
 };
 
 namespace {
@@ -1068,28 +1090,97 @@ __device__ bool lane_wants_cycle(const Ctrl* ctrl, const LaneCtl* L) {
     return true;
 }
 
-__global__ void lane_begin_kernel(const Ctrl* __restrict__ ctrl, LaneCtl* L, int* more, cudaGraphConditionalHandle hit,
-                                  cudaGraphConditionalHandle hcyc) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    const bool go = lane_wants_cycle(ctrl, L);
-    if (!go) L->active = 0;
-    else L->cycles += 1;
-    L->kk = 0;
-    *more = go ? 1 : 0;
-    cudaGraphSetConditional(hit, go ? 1u : 0u);
-    cudaGraphSetConditional(hcyc, go ? 1u : 0u);
-}
-
-// end of iteration j: opens iteration j+1 (its own handle hnext; has_next = 0 after the last one)
-__global__ void lane_iter_end_kernel(const Ctrl* __restrict__ ctrl, LaneCtl* L, int j, cudaGraphConditionalHandle hnext,
-                                     int has_next) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+// end of iteration j of a lane that ran it: counts it and decides whether the lane runs iteration j+1
+// (has_next = 0 after the last iteration of a cycle)
+__device__ void lane_iter_step(const Ctrl* __restrict__ ctrl, LaneCtl* L, int j, int has_next) {
     L->its += 1;
     L->kk = j + 1;
     bool go = !(ctrl->flags & HELM_DEV_NAN) && ctrl->est > inner_threshold(L->rtol, ctrl->beta, ctrl->beta0) &&
               L->its < L->max_iter && j + 1 < L->m;
     if (!(ctrl->hnext > 0)) { go = false; L->brk = 1; }
-    if (has_next) cudaGraphSetConditional(hnext, go ? 1u : 0u);
+    L->go = (go && has_next) ? 1 : 0;
+}
+
+// The per-lane device pointers of a batch group, indexed by lane.  The group's Arnoldi kernels take their
+// lane from the grid (blockIdx.y, or blockIdx.x for the one-block-per-lane kernels) and return at once for a
+// lane that does not run the current iteration (L->go = 0), so one launch serves all the group's lanes.
+struct LaneDev {
+    float2* V;        // the lane's v_0; its basis vectors are vs apart (interleaved with the group's other lanes)
+    double2* part;
+    double2* H;
+    double* cs;
+    double2* sn;
+    double2* g;
+    double* sigma;
+    float2* coef;
+    Ctrl* ctrl;
+    LaneCtl* L;
+};
+
+// h = V^H w of every running lane (w = its v_{j+1} slot); VAR 0: dots_body, 4 or 8: dots_pipe_body<VAR>
+template <int VAR>
+__global__ void __launch_bounds__(NT) grp_dots_kernel(const LaneDev* __restrict__ lt, size_t npts, int nv, int j,
+                                                     int ld, size_t vs) {
+    const LaneDev& d = lt[blockIdx.y];
+    if (!d.L->go) return;
+    const float2* w = d.V + (size_t)(j + 1) * vs;
+    if constexpr (VAR == 0) dots_body(d.V, npts, nv, w, d.part, ld, vs);
+    else dots_pipe_body<VAR>(d.V, npts, nv, w, d.part, ld, vs);
+}
+
+__global__ void grp_reduce_h_kernel(const LaneDev* __restrict__ lt, int NB, int ld, int nv, int j, int m,
+                                    int first_pass) {
+    const LaneDev& d = lt[blockIdx.y];
+    if (!d.L->go) return;
+    reduce_h_body(d.part, NB, ld, nv, d.sigma, d.H + (size_t)j * (m + 1), d.coef, first_pass);
+}
+
+__global__ void __launch_bounds__(NT) grp_update_kernel(const LaneDev* __restrict__ lt, size_t npts, int nv, int j,
+                                                       int ld, size_t vs) {
+    const LaneDev& d = lt[blockIdx.y];
+    if (!d.L->go) return;
+    update_body(d.V, npts, nv, d.coef, d.V + (size_t)(j + 1) * vs, d.part, ld, vs);
+}
+
+__global__ void grp_givens_kernel(const LaneDev* __restrict__ lt, int NB, int ld, int j, int m) {
+    const LaneDev& d = lt[blockIdx.x];
+    if (!d.L->go) return;
+    givens_body(d.part, NB, ld, j, m, d.H, d.cs, d.sn, d.g, d.sigma, d.ctrl);
+}
+
+// end of the group's iteration j: steps every lane that ran it and opens iteration j+1 (handle hnext) when
+// any lane runs it
+__global__ void grp_iter_end_kernel(const LaneDev* __restrict__ lt, int nb, int j, cudaGraphConditionalHandle hnext,
+                                    int has_next) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    int any = 0;
+    for (int r = 0; r < nb; ++r) {
+        LaneCtl* L = lt[r].L;
+        if (!L->go) continue;
+        lane_iter_step(lt[r].ctrl, L, j, has_next);
+        any |= L->go;
+    }
+    if (has_next) cudaGraphSetConditional(hnext, any ? 1u : 0u);
+}
+
+// start of a restart cycle of the group: each lane decides whether it runs the cycle (more[r], its
+// cycle-end handle hcyc[r]); the group's iteration 0 (handle h0) runs when any lane does
+__global__ void grp_begin_kernel(const LaneDev* __restrict__ lt, int nb, int* more,
+                                 const cudaGraphConditionalHandle* __restrict__ hcyc, cudaGraphConditionalHandle h0) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    int any = 0;
+    for (int r = 0; r < nb; ++r) {
+        LaneCtl* L = lt[r].L;
+        const bool go = lane_wants_cycle(lt[r].ctrl, L);
+        if (!go) L->active = 0;
+        else L->cycles += 1;
+        L->kk = 0;
+        L->go = go ? 1 : 0;
+        more[r] = go ? 1 : 0;
+        cudaGraphSetConditional(hcyc[r], go ? 1u : 0u);
+        any |= go;
+    }
+    cudaGraphSetConditional(h0, any ? 1u : 0u);
 }
 
 __global__ void lane_cycle_end_kernel(const Ctrl* __restrict__ ctrl, LaneCtl* L, int* more) {
@@ -1124,30 +1215,6 @@ helm_status lane_precond(Lane& ln, const float2* r, float2* z, const double* sig
     helm_status st = precond_apply(ln.c, r, z, sigma, sidx, s);
     ln.c->tmp = save;
     return st;
-}
-
-helm_status lane_iteration(Lane& ln, int j, cudaGraphConditionalHandle hnext, int has_next, cudaStream_t s) {
-    helm_ctx* c = ln.c;
-    KrylovWork* k = &ln.w;
-    const size_t npts = c->npts;
-    const int m = k->m, ld = m + 1, NB = k->NB;
-    float2* vj = k->V + (size_t)j * npts;
-    float2* w = k->V + (size_t)(j + 1) * npts;
-    float2* z = k->flexible ? k->Z + (size_t)j * npts : k->Z;
-    helm_status st;
-    if ((st = lane_precond(ln, vj, z, k->sigma, j, s)) != HELM_OK) return st;
-    if ((st = launch_stencil_f32(c, z, w, nullptr, 0, s)) != HELM_OK) return st;
-    const int passes = c->opt.reorth ? 2 : 1;
-    for (int pass = 0; pass < passes; ++pass) {
-        const int nbd = launch_dots(c, k->V, npts, j + 1, w, k->part, ld, k->NBd, s, k->vs);
-        reduce_h_kernel<<<j + 1, 128, 0, s>>>(k->part, nbd, ld, j + 1, k->sigma, k->H + (size_t)j * (m + 1), k->coef,
-                                          pass == 0);
-        update_kernel<<<NB, NT, 0, s>>>(k->V, npts, j + 1, k->coef, w, k->part, ld, k->vs);
-    }
-    givens_kernel<<<1, 256, 0, s>>>(k->part, NB, ld, j, m, k->H, k->cs, k->sn, k->g, k->sigma, k->ctrl_d);
-    lane_iter_end_kernel<<<1, 32, 0, s>>>(k->ctrl_d, ln.L_d, j, hnext, has_next);
-    HELM_CUDA_TRY(cudaGetLastError());
-    return HELM_OK;
 }
 
 helm_status lane_cycle_end(Lane& ln, cudaStream_t s) {
@@ -1202,55 +1269,116 @@ helm_status add_cond(cudaGraph_t g, const cudaGraphNode_t* deps, size_t nd, cuda
     return HELM_OK;
 }
 
-// the nodes of one lane's restart cycle: begin; IF iterations; IF cycle end.  Every conditional node has its
-// own handle (default 0 at each launch); the begin kernel opens iteration 0 and the cycle end, iteration j
-// opens iteration j+1.
-helm_status build_lane(cudaGraph_t G, Lane& ln, cudaStream_t s) {
-    const int m = ln.w.m;
-    std::vector<cudaGraphConditionalHandle> hit(m);
-    cudaGraphConditionalHandle hcyc;
-    for (int j = 0; j < m; ++j) HELM_CUDA_TRY(cudaGraphConditionalHandleCreate(&hit[j], G, 0, cudaGraphCondAssignDefault));
-    HELM_CUDA_TRY(cudaGraphConditionalHandleCreate(&hcyc, G, 0, cudaGraphCondAssignDefault));
+// A group: the consecutive lanes of one context (its right-hand sides) in a plan.  Their basis vectors,
+// preconditioned vectors and normalisation factors are interleaved in group buffers (vector v_j of lane r
+// at V + (j nb + r) npts), so that each step of iteration j runs once for the whole group: one x-pass GEMM over
+// nb N_y N_z rows, one y-pass over nb N_z slices, one z-solve over nb N_x N_y lines, one matvec launch over nb
+// grids (the context's coefficients read once per tile for all of them), and one launch of each Arnoldi
+// kernel over all the lanes (a lane that has left the cycle returns at once).
+struct Group {
+    helm_ctx* c = nullptr;
+    int first = 0, nb = 0;          // lanes first .. first + nb - 1 of the plan
+    float2* V = nullptr;            // (m + 1) nb vectors
+    float2* Z = nullptr;            // m nb (flexible) or nb vectors
+    float2* tmp = nullptr;          // nb vectors: the group's preconditioner scratch (lane r's own: vector r)
+    double* sigma = nullptr;        // nb (m + 1)
+    LaneDev* lt = nullptr;          // device table of the lanes' pointers
+    cudaGraphConditionalHandle* hcyc = nullptr;   // device copy of the lanes' cycle-end handles
+};
+
+// The nodes of one group's restart cycle (every conditional node has its own handle, default 0 at each launch):
+//   begin (each lane decides whether it runs the cycle)
+//   -> IF(iteration 0) { M^-1 and A for all the group's vectors; Gram-Schmidt, norm and Givens rotation of
+//      every running lane; end (opens iteration 1 if any lane runs it) } -> ... -> IF(iteration m-1) { ... }
+//   -> IF(lane r cycle) { least squares, x update, true residual } for every lane r (branches).
+helm_status build_group(cudaGraph_t G, Group& gr, std::vector<Lane>& lanes, int* more, cudaStream_t s) {
+    helm_ctx* c = gr.c;
+    const int nb = gr.nb, m = lanes[gr.first].w.m, flex = c->opt.flexible, ld = m + 1;
+    const size_t npts = c->npts, vs = (size_t)nb * npts;
+    const KrylovWork& k0 = lanes[gr.first].w;
+    std::vector<cudaGraphConditionalHandle> hcyc(nb), hg(m);
+    for (int r = 0; r < nb; ++r)
+        HELM_CUDA_TRY(cudaGraphConditionalHandleCreate(&hcyc[r], G, 0, cudaGraphCondAssignDefault));
+    for (int j = 0; j < m; ++j) HELM_CUDA_TRY(cudaGraphConditionalHandleCreate(&hg[j], G, 0, cudaGraphCondAssignDefault));
+    HELM_CUDA_TRY(cudaMemcpy(gr.hcyc, hcyc.data(), sizeof(cudaGraphConditionalHandle) * nb, cudaMemcpyHostToDevice));
     helm_status st;
-    cudaGraphNode_t begin;
+    cudaGraphNode_t prev;
     {
+        const LaneDev* lt = gr.lt;
+        int n = nb;
+        const cudaGraphConditionalHandle* hc = gr.hcyc;
+        cudaGraphConditionalHandle h0 = hg[0];
+        void* args[] = {(void*)&lt, (void*)&n, (void*)&more, (void*)&hc, (void*)&h0};
         cudaKernelNodeParams kp = {};
-        const Ctrl* ctrl = ln.w.ctrl_d;
-        LaneCtl* L = ln.L_d;
-        int* more = ln.more;
-        cudaGraphConditionalHandle h0 = hit[0];
-        void* args[] = {(void*)&ctrl, (void*)&L, (void*)&more, (void*)&h0, (void*)&hcyc};
-        kp.func = (void*)lane_begin_kernel;
+        kp.func = (void*)grp_begin_kernel;
         kp.gridDim = dim3(1);
         kp.blockDim = dim3(32);
         kp.kernelParams = args;
-        HELM_CUDA_TRY(cudaGraphAddKernelNode(&begin, G, nullptr, 0, &kp));
+        HELM_CUDA_TRY(cudaGraphAddKernelNode(&prev, G, nullptr, 0, &kp));
     }
-    cudaGraphNode_t prev = begin;
+    const int passes = c->opt.reorth ? 2 : 1;
     for (int j = 0; j < m; ++j) {
-        cudaGraphNode_t node;
-        cudaGraph_t ib;
-        if ((st = add_cond(G, &prev, 1, hit[j], cudaGraphCondTypeIf, &node, &ib)) != HELM_OK) return st;
-        const cudaGraphConditionalHandle hn = j + 1 < m ? hit[j + 1] : hit[j];
+        cudaGraphNode_t gnode;
+        cudaGraph_t gb;
+        if ((st = add_cond(G, &prev, 1, hg[j], cudaGraphCondTypeIf, &gnode, &gb)) != HELM_OK) return st;
+        float2* vj = gr.V + (size_t)j * vs;
+        float2* zj = flex ? gr.Z + (size_t)j * vs : gr.Z;
+        float2* w = gr.V + (size_t)(j + 1) * vs;
         const int has_next = j + 1 < m ? 1 : 0;
-        if ((st = capture_into(ib, nullptr, 0, s, [&]() { return lane_iteration(ln, j, hn, has_next, s); })) != HELM_OK)
-            return st;
-        prev = node;
+        const cudaGraphConditionalHandle hn = has_next ? hg[j + 1] : hg[j];
+        st = capture_into(gb, nullptr, 0, s, [&]() {
+            float2* save = c->tmp;
+            c->tmp = gr.tmp;
+            helm_status e = precond_apply_nb(c, vj, zj, nb, gr.sigma, j, m + 1, s);
+            c->tmp = save;
+            if (e != HELM_OK) return e;
+            if ((e = launch_stencil_f32_nb(c, zj, w, nb, s)) != HELM_OK) return e;
+            const int nv = j + 1;
+            const int var = (c->tune_dots == 2 && nv <= 4) ? 1 : c->tune_dots;
+            const int nbd = dots_ctas_for(c, var);
+            for (int pass = 0; pass < passes; ++pass) {
+                const dim3 gd(nbd, nb);
+                if (var == 1) grp_dots_kernel<4><<<gd, NT, 0, s>>>(gr.lt, npts, nv, j, ld, vs);
+                else if (var == 2) grp_dots_kernel<8><<<gd, NT, 0, s>>>(gr.lt, npts, nv, j, ld, vs);
+                else grp_dots_kernel<0><<<gd, NT, 0, s>>>(gr.lt, npts, nv, j, ld, vs);
+                grp_reduce_h_kernel<<<dim3(nv, nb), 128, 0, s>>>(gr.lt, nbd, ld, nv, j, m, pass == 0);
+                grp_update_kernel<<<dim3(k0.NB, nb), NT, 0, s>>>(gr.lt, npts, nv, j, ld, vs);
+            }
+            grp_givens_kernel<<<nb, 256, 0, s>>>(gr.lt, k0.NB, ld, j, m);
+            grp_iter_end_kernel<<<1, 32, 0, s>>>(gr.lt, nb, j, hn, has_next);
+            HELM_CUDA_TRY(cudaGetLastError());
+            return HELM_OK;
+        });
+        if (st != HELM_OK) return st;
+        prev = gnode;
     }
-    cudaGraphNode_t cnode;
-    cudaGraph_t cb;
-    if ((st = add_cond(G, &prev, 1, hcyc, cudaGraphCondTypeIf, &cnode, &cb)) != HELM_OK) return st;
-    return capture_into(cb, nullptr, 0, s, [&]() { return lane_cycle_end(ln, s); });
+    for (int r = 0; r < nb; ++r) {
+        Lane& ln = lanes[gr.first + r];
+        cudaGraphNode_t cnode;
+        cudaGraph_t cb;
+        if ((st = add_cond(G, &prev, 1, hcyc[r], cudaGraphCondTypeIf, &cnode, &cb)) != HELM_OK) return st;
+        if ((st = capture_into(cb, nullptr, 0, s, [&]() { return lane_cycle_end(ln, s); })) != HELM_OK) return st;
+    }
+    return HELM_OK;
 }
 
 void free_lane(Lane& ln) {
     free_work(&ln.w);
     ln.w = KrylovWork();
-    cudaFree(ln.tmp);
     cudaFree(ln.L_d);
-    ln.tmp = nullptr;
+    ln.tmp = nullptr;   // a view of the group's scratch
     ln.L_d = nullptr;
     ln.more = nullptr;
+}
+
+void free_group(Group& g) {
+    cudaFree(g.V);
+    cudaFree(g.Z);
+    cudaFree(g.tmp);
+    cudaFree(g.sigma);
+    cudaFree(g.lt);
+    cudaFree(g.hcyc);
+    g = Group();
 }
 
 }  // namespace
@@ -1258,6 +1386,7 @@ void free_lane(Lane& ln) {
 // A batch plan: the lanes' workspaces and the instantiated restart-cycle graph, reusable across runs.
 struct helm_batch {
     std::vector<Lane> lanes;
+    std::vector<Group> groups;
     std::vector<helm_ctx*> ctxs;
     int nprob = 0, nrhs = 0;
     int* flags = nullptr;
@@ -1274,17 +1403,48 @@ void plan_free(helm_batch* P) {
     if (P->cs) cudaStreamDestroy(P->cs);
     cudaFree(P->flags);
     for (Lane& ln : P->lanes) free_lane(ln);
+    for (Group& g : P->groups) free_group(g);
+    P->groups.clear();
     P->X = nullptr; P->G = nullptr; P->cs = nullptr; P->flags = nullptr;
 }
 
-// workspace of every lane and the graph of one restart cycle of all lanes
+// workspace of every group and lane, and the graph of one restart cycle of all lanes
 helm_status plan_build(helm_batch* P) {
     helm_status st;
-    for (Lane& ln : P->lanes) {
-        helm_ctx* c = ln.c;
-        if ((st = alloc_work(c, &ln.w, c->opt.restart, c->opt.flexible, default_nb(c))) != HELM_OK) return st;
-        if (cudaMalloc(&ln.tmp, c->npts * sizeof(float2)) != cudaSuccess) { cudaGetLastError(); return HELM_ERR_NOMEM; }
-        HELM_CUDA_TRY(cudaMalloc(&ln.L_d, sizeof(LaneCtl)));
+    // groups: runs of consecutive lanes of the same context
+    for (size_t i = 0; i < P->lanes.size();) {
+        Group g;
+        g.c = P->lanes[i].c;
+        g.first = (int)i;
+        while (i < P->lanes.size() && P->lanes[i].c == g.c) ++i;
+        g.nb = (int)i - g.first;
+        P->groups.push_back(g);
+    }
+    for (Group& g : P->groups) {
+        helm_ctx* c = g.c;
+        const int m = c->opt.restart, flex = c->opt.flexible, nb = g.nb;
+        const size_t vb = c->npts * sizeof(float2);
+        auto A = [](void** p, size_t bytes) {
+            if (cudaMalloc(p, bytes) != cudaSuccess) { cudaGetLastError(); return false; }
+            return true;
+        };
+        if (!A((void**)&g.V, vb * (m + 1) * nb) || !A((void**)&g.Z, vb * (flex ? m : 1) * nb) ||
+            !A((void**)&g.tmp, vb * nb) || !A((void**)&g.sigma, sizeof(double) * (m + 1) * nb) ||
+            !A((void**)&g.lt, sizeof(LaneDev) * nb) || !A((void**)&g.hcyc, sizeof(cudaGraphConditionalHandle) * nb))
+            return HELM_ERR_NOMEM;
+        std::vector<LaneDev> lt(nb);
+        for (int r = 0; r < nb; ++r) {
+            Lane& ln = P->lanes[g.first + r];
+            if ((st = alloc_work(c, &ln.w, m, flex, default_nb(c), g.V + (size_t)r * c->npts,
+                                 g.Z + (size_t)r * c->npts, g.sigma + (size_t)r * (m + 1), (size_t)nb * c->npts)) !=
+                HELM_OK)
+                return st;
+            ln.tmp = g.tmp + (size_t)r * c->npts;
+            HELM_CUDA_TRY(cudaMalloc(&ln.L_d, sizeof(LaneCtl)));
+            const KrylovWork& k = ln.w;
+            lt[r] = LaneDev{k.V, k.part, k.H, k.cs, k.sn, k.g, k.sigma, k.coef, k.ctrl_d, ln.L_d};
+        }
+        HELM_CUDA_TRY(cudaMemcpy(g.lt, lt.data(), sizeof(LaneDev) * nb, cudaMemcpyHostToDevice));
     }
     HELM_CUDA_TRY(cudaMalloc(&P->flags, sizeof(int) * P->lanes.size()));
     for (size_t i = 0; i < P->lanes.size(); ++i) P->lanes[i].more = P->flags + i;
@@ -1294,7 +1454,8 @@ helm_status plan_build(helm_batch* P) {
     for (size_t p = 0; p < P->ctxs.size(); ++p)
         if (P->ctxs[p]->prof) { prof_on[p] = P->ctxs[p]->prof->enabled; P->ctxs[p]->prof->enabled = 0; }  // no event nodes
     st = HELM_OK;
-    for (size_t i = 0; st == HELM_OK && i < P->lanes.size(); ++i) st = build_lane(P->G, P->lanes[i], P->cs);
+    for (size_t i = 0; st == HELM_OK && i < P->groups.size(); ++i)
+        st = build_group(P->G, P->groups[i], P->lanes, P->flags + P->groups[i].first, P->cs);
     for (size_t p = 0; p < P->ctxs.size(); ++p)
         if (P->ctxs[p]->prof) P->ctxs[p]->prof->enabled = prof_on[p];
     if (st != HELM_OK) return st;

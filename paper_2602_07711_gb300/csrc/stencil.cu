@@ -641,6 +641,22 @@ helm_status launch_stencil_f32_cls(helm_ctx* c, const float2* x, float2* y, cons
     return HELM_OK;
 }
 
+helm_status launch_stencil_f32_nb(helm_ctx* c, const float2* x, float2* y, int nb, cudaStream_t s) {
+    if (nb == 1) return launch_stencil_f32(c, x, y, nullptr, 0, s);
+    if (stencil_fast_supported(c)) {
+        prof_begin(c, s, PROF_STENCIL);
+        helm_status st = launch_stencil_fast(c, x, y, nullptr, 0, s, nb);
+        prof_end(c, s);
+        return st;
+    }
+    // the general kernels (collocated grids, order 2) take one vector per launch
+    helm_status st;
+    for (int v = 0; v < nb; ++v)
+        if ((st = launch_stencil_f32(c, x + (size_t)v * c->npts, y + (size_t)v * c->npts, nullptr, 0, s)) != HELM_OK)
+            return st;
+    return HELM_OK;
+}
+
 helm_status launch_stencil_f64(helm_ctx* c, const double2* x, double2* y, cudaStream_t s) {
     SParams<P64> p = make_params<P64>(c);
     p.k2 = c->k2_d;

@@ -68,6 +68,8 @@ struct FParams {
     const float2* fld[4];         // G, g_x, g_y, g_z (order 6)
     const float* k2r;             // real k^2 (real-medium kernels)
     const float4* fr;             // real (G, g_x, g_y, g_z) per point (real-medium kernels, order 6)
+    int nb = 1;                   // vectors in one launch (the right-hand sides of a batch group), npts apart;
+                                  // blockIdx.z = z chunk * nb + vector
 };
 
 __device__ __forceinline__ void cp8(void* smem, const void* gmem) {
@@ -104,11 +106,17 @@ stencil_fast_kernel(FParams p, const float2* __restrict__ U, float2* __restrict_
     Stage* ring = reinterpret_cast<Stage*>(fsm);
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * FTX + tx;
     const int x0 = blockIdx.x * FTX, y0 = blockIdx.y * FTY;
-    const int z0 = blockIdx.z * FZCH;
+    const int vb = blockIdx.z % p.nb;   // the vector of the batch this CTA works on
+    const int z0 = (blockIdx.z / p.nb) * FZCH;
     const int z1 = min(z0 + FZCH, p.nz);
     const int gx = x0 + tx, gy = y0 + ty;
     const bool active = gx < p.nx && gy < p.ny;
     const float sg = sigma ? (float)sigma[sidx] : 1.f;
+    if (vb) {
+        const size_t off = (size_t)vb * p.nx * p.ny * p.nz;
+        U += off;
+        Y += off;
+    }
     // this thread's staging slots (fixed across planes): clamped in-plane offset in the low 30 bits,
     // bit 30 = x ghost, bit 31 = y ghost
     unsigned sl[2] = {0u, 0u};
@@ -612,7 +620,17 @@ bool stencil_fast_supported(const helm_ctx* c) { return !c->colloc && (c->opt.or
 // (even N_x, else the same as 0), 2 = cp.async ring at three CTAs per SM with more registers.
 int stencil_variants(const helm_ctx* c) { (void)c; return 3; }
 
-helm_status launch_stencil_fast(helm_ctx* c, const float2* x, float2* y, const double* sigma, int sidx, cudaStream_t s) {
+helm_status launch_stencil_fast(helm_ctx* c, const float2* x, float2* y, const double* sigma, int sidx, cudaStream_t s,
+                                int nb) {
+    if (nb > 1 && c->sfast && c->tune_stencil == 1) {
+        // the TMA form stages one vector: one launch per vector of the batch
+        helm_status st;
+        for (int v = 0; v < nb; ++v)
+            if ((st = launch_stencil_fast(c, x + (size_t)v * c->npts, y + (size_t)v * c->npts, sigma, sidx, s, 1)) !=
+                HELM_OK)
+                return st;
+        return HELM_OK;
+    }
     FParams p;
     p.nx = c->nx; p.ny = c->ny; p.nz = c->nz;
     p.gx = make_float2((float)c->gam[0].x, (float)c->gam[0].y);
@@ -630,7 +648,8 @@ helm_status launch_stencil_fast(helm_ctx* c, const float2* x, float2* y, const d
     p.k2 = c->k2_f;
     p.fld[0] = c->G_f;
     for (int d = 0; d < 3; ++d) p.fld[d + 1] = c->dk2_f[d];
-    dim3 grid((c->nx + FTX - 1) / FTX, (c->ny + FTY - 1) / FTY, (c->nz + FZCH - 1) / FZCH), block(FTX, FTY);
+    p.nb = nb;
+    dim3 grid((c->nx + FTX - 1) / FTX, (c->ny + FTY - 1) / FTY, (c->nz + FZCH - 1) / FZCH * nb), block(FTX, FTY);
     if (c->sfast && c->tune_stencil == 1) {
         FastMaps* m = (FastMaps*)c->sfast;
         CUtensorMap mU;

@@ -230,9 +230,14 @@ __global__ void __launch_bounds__(128) zfactor_kernel(ZParams p, float2* __restr
 __global__ void __launch_bounds__(128) zsolve_fact_kernel(int nx, int ny, int nz, float zz, const float2* __restrict__ m,
                                                          const float2* in, float2* out, const float2* __restrict__ P,
                                                          const float2* __restrict__ Q) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
+    // blockIdx.y = (right-hand side of a batch group) * ny + j; the factors m are shared
+    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y % ny, vb = blockIdx.y / ny;
     if (i >= nx) return;
-    const size_t plane = (size_t)nx * ny, base = (size_t)j * nx + i;
+    const size_t plane = (size_t)nx * ny, base = (size_t)j * nx + i, voff = (size_t)vb * plane * nz;
+    if (vb) {
+        if (in) in += voff;
+        out += voff;
+    }
     float2 d = f2(0.f, 0.f);
     for (int l0 = 0; l0 < nz; l0 += ZU) {
         float2 yv[ZU], mv[ZU];
@@ -305,16 +310,20 @@ __device__ __forceinline__ void zcommit() { asm volatile("cp.async.commit_group;
 __device__ __forceinline__ void zwait_ring() { asm volatile("cp.async.wait_group %0;\n" ::"n"(ZB - 1) : "memory"); }
 __device__ __forceinline__ void zwait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
+// nb > 1: nb right-hand side grids back to back (a batch group), sharing the factors m
 __global__ void __launch_bounds__(ZRT) zsolve_ring_kernel(int nx, int ny, int nz, float zz,
-                                                         const float4* __restrict__ m, const float4* in, float4* out) {
+                                                         const float4* __restrict__ m, const float4* in, float4* out,
+                                                         int nb) {
     extern __shared__ float4 zring[];   // [ZB * ZU2][2][ZRT]
     const int tid = threadIdx.x;
     const int hx = nx / 2, npairs = hx * ny;
     const int nblk = (nz + ZU2 - 1) / ZU2;
     const size_t plane = (size_t)hx * ny;   // in float4 (two lines) units
     auto slot = [&](int st, int a) -> float4* { return &zring[((size_t)st * 2 + a) * ZRT + tid]; };
-    for (int pr = blockIdx.x * ZRT + tid; pr < npairs; pr += gridDim.x * ZRT) {
+    for (int prb = blockIdx.x * ZRT + tid; prb < npairs * nb; prb += gridDim.x * ZRT) {
+        const int pr = prb % npairs, vb = prb / npairs;
         const size_t off = (size_t)pr;   // pair pr = (j, i/2) is float4 pr of every plane
+        const size_t voff = (size_t)vb * plane * nz;   // this right-hand side's grid (the factors are shared)
         // ---- forward: d_l = (y_l - a_l d_{l-1}) m_l, steps in increasing l
         auto fetch_f = [&](int b) {
             if (b < nblk) {
@@ -322,7 +331,7 @@ __global__ void __launch_bounds__(ZRT) zsolve_ring_kernel(int nx, int ny, int nz
                 for (int u = 0; u < ZU2; ++u) {
                     const int l = b * ZU2 + u;
                     if (l < nz) {
-                        zcp16(slot((b % ZB) * ZU2 + u, 0), in + off + (size_t)l * plane);
+                        zcp16(slot((b % ZB) * ZU2 + u, 0), in + voff + off + (size_t)l * plane);
                         zcp16(slot((b % ZB) * ZU2 + u, 1), m + off + (size_t)l * plane);
                     }
                 }
@@ -347,7 +356,7 @@ __global__ void __launch_bounds__(ZRT) zsolve_ring_kernel(int nx, int ny, int nz
                     const float a = l == 0 ? 0.f : (l == nz - 1 ? zz : 1.f);
                     d0 = cmul(csub(f2(y[u].x, y[u].y), cscale(d0, a)), f2(mm[u].x, mm[u].y));
                     d1 = cmul(csub(f2(y[u].z, y[u].w), cscale(d1, a)), f2(mm[u].z, mm[u].w));
-                    out[off + (size_t)l * plane] = make_float4(d0.x, d0.y, d1.x, d1.y);
+                    out[voff + off + (size_t)l * plane] = make_float4(d0.x, d0.y, d1.x, d1.y);
                 }
             }
         }
@@ -360,7 +369,7 @@ __global__ void __launch_bounds__(ZRT) zsolve_ring_kernel(int nx, int ny, int nz
                 for (int u = 0; u < ZU2; ++u) {
                     const int l = nz - 1 - (b * ZU2 + u);
                     if (l >= 0) {
-                        zcp16(slot((b % ZB) * ZU2 + u, 0), out + off + (size_t)l * plane);
+                        zcp16(slot((b % ZB) * ZU2 + u, 0), out + voff + off + (size_t)l * plane);
                         zcp16(slot((b % ZB) * ZU2 + u, 1), m + off + (size_t)l * plane);
                     }
                 }
@@ -385,7 +394,7 @@ __global__ void __launch_bounds__(ZRT) zsolve_ring_kernel(int nx, int ny, int nz
                     const float sup = l == nz - 1 ? 0.f : (l == 0 ? zz : 1.f);
                     x0 = csub(f2(dv[u].x, dv[u].y), cscale(cmul(f2(mm[u].x, mm[u].y), x0), sup));
                     x1 = csub(f2(dv[u].z, dv[u].w), cscale(cmul(f2(mm[u].z, mm[u].w), x1), sup));
-                    out[off + (size_t)l * plane] = make_float4(x0.x, x0.y, x1.x, x1.y);
+                    out[voff + off + (size_t)l * plane] = make_float4(x0.x, x0.y, x1.x, x1.y);
                 }
             }
         }
@@ -422,21 +431,22 @@ helm_status zsolve_factor(helm_ctx* c, cudaStream_t s) { return zsolve_factor_wi
 
 // factorised solve with factors m, optional input (NULL = 0) and optional generated right-hand side
 helm_status launch_zsolve_fact(helm_ctx* c, const float2* m, const float2* in, float2* out, const float2* P,
-                               const float2* Q, cudaStream_t s) {
+                               const float2* Q, cudaStream_t s, int nb) {
     prof_begin(c, s, PROF_ZSOLVE);
     if (!P && in && c->nx % 2 == 0 && c->tune_zring && c->zring_sms > 0) {
         const int sms = c->zring_sms;
-        const int npairs = c->nx / 2 * c->ny;
+        const int npairs = c->nx / 2 * c->ny * nb;
         const int need = (npairs + ZRT - 1) / ZRT;
         const int grid = need < sms * c->tune_zring ? need : sms * c->tune_zring;
         zsolve_ring_kernel<<<grid, ZRT, ZRING_BYTES, s>>>(c->nx, c->ny, c->nz, (float)c->zeta[2],
                                                          reinterpret_cast<const float4*>(m),
-                                                         reinterpret_cast<const float4*>(in), reinterpret_cast<float4*>(out));
+                                                         reinterpret_cast<const float4*>(in), reinterpret_cast<float4*>(out),
+                                                         nb);
         prof_end(c, s);
         HELM_CUDA_TRY(cudaGetLastError());
         return HELM_OK;
     }
-    dim3 grid((c->nx + 127) / 128, c->ny);
+    dim3 grid((c->nx + 127) / 128, c->ny * nb);
     zsolve_fact_kernel<<<grid, 128, 0, s>>>(c->nx, c->ny, c->nz, (float)c->zeta[2], m, in, out, P, Q);
     prof_end(c, s);
     HELM_CUDA_TRY(cudaGetLastError());
@@ -467,7 +477,14 @@ helm_status launch_zsolve_gen(helm_ctx* c, const float2* in, float2* out, const 
     return HELM_OK;
 }
 
-helm_status launch_zsolve(helm_ctx* c, const float2* in, float2* out, cudaStream_t s) {
-    if (!c->zfac) return launch_zsolve_gen(c, in, out, c->dxs, c->dys, nullptr, nullptr, s);
-    return launch_zsolve_fact(c, c->zfac, in, out, nullptr, nullptr, s);
+helm_status launch_zsolve(helm_ctx* c, const float2* in, float2* out, cudaStream_t s, int nb) {
+    if (!c->zfac) {
+        helm_status st;
+        for (int v = 0; v < nb; ++v)
+            if ((st = launch_zsolve_gen(c, in + (size_t)v * c->npts, out + (size_t)v * c->npts, c->dxs, c->dys, nullptr,
+                                        nullptr, s)) != HELM_OK)
+                return st;
+        return HELM_OK;
+    }
+    return launch_zsolve_fact(c, c->zfac, in, out, nullptr, nullptr, s, nb);
 }

@@ -160,3 +160,30 @@ def compare(net, n, seed, order=6, ppw=8.0, rtol=1e-6, max_iter=600, medium=high
     d = (sols["learned"] - sols["plain"]).abs().pow(2).sum().sqrt() / sols["plain"].abs().pow(2).sum().sqrt()
     out["solution_rel_diff"] = float(d)
     return out
+
+
+def forward_timing(n, width, reps=5, seed=1):
+    """CUDA-event milliseconds of one network forward on a single n^3 field (a fresh network of the given
+    width; the five input channels random)."""
+    import torch
+    net = helm.Net(width, seed=seed)
+    x = torch.randn((1, 5, n, n, n), device="cuda").to(torch.bfloat16)
+    net.forward(x)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(reps):
+        net.forward(x)
+    e1.record()
+    torch.cuda.synchronize()
+    net.close()
+    return e0.elapsed_time(e1) / reps
+
+
+if __name__ == "__main__":
+    # python -m paper_2602_07711_gb300.learned N WIDTH [REPS]: time the network's forward on one N^3 field
+    import sys
+    n_, w_ = int(sys.argv[1]), int(sys.argv[2])
+    reps_ = int(sys.argv[3]) if len(sys.argv) > 3 else 5
+    print("width %d, %d^3: %.3f ms per forward" % (w_, n_, forward_timing(n_, w_, reps_)))
