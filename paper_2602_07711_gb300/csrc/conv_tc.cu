@@ -181,12 +181,25 @@ __device__ __forceinline__ void fill_slab(unsigned char* slab, const TIN* __rest
             row[j] = (rowok && ch < Cin) ? load8(in + (size_t)ch * vol + roff, xb, X, vec) : make_uint4(0u, 0u, 0u, 0u);
         }
         unsigned char* rowp = slab + (size_t)(((cg * 3 + dz) * L::SY + yr) * CT_SX) * 16;
+        // Store slot k writes the cell of point k ^ sw (sw = g mod 8).  A thread's 8 cells are 128 contiguous
+        // bytes and neighbouring threads take neighbouring groups, so with the same order everywhere all the
+        // 16-byte stores of one warp instruction would hit the same four banks; rotated, they spread over all
+        // 32.  The rotation is applied to the loaded words (point pair k >> 1 is word k >> 1 of each row) and
+        // to the half selector (point parity), so every register index stays static.
+        const int sw = g & 7;
+        if (sw & 2)
+#pragma unroll
+            for (int j = 0; j < 8; ++j) row[j] = make_uint4(row[j].y, row[j].x, row[j].w, row[j].z);
+        if (sw & 4)
+#pragma unroll
+            for (int j = 0; j < 8; ++j) row[j] = make_uint4(row[j].z, row[j].w, row[j].x, row[j].y);
+        const uint32_t sel_even = (sw & 1) ? 0x7632u : 0x5410u, sel_odd = (sw & 1) ? 0x5410u : 0x7632u;
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
-            const int xi = 8 * g - 7 + k;   // slab index of the point xb + k
+            const int xi = 8 * g - 7 + (k ^ sw);   // slab index of the point xb + (k ^ sw)
             if (xi >= 0 && xi < CT_SX) {
-                // cell word m = (channel 2m, channel 2m + 1) at point k: the low (k even) or high (k odd) halves
-                const uint32_t sel = (k & 1) ? 0x7632u : 0x5410u;
+                // cell word m = (channel 2m, channel 2m + 1) at the point: the low (even point) or high halves
+                const uint32_t sel = (k & 1) ? sel_odd : sel_even;
                 uint32_t w[4];
 #pragma unroll
                 for (int m = 0; m < 4; ++m) w[m] = __byte_perm(u4w(row[2 * m], k >> 1), u4w(row[2 * m + 1], k >> 1), sel);

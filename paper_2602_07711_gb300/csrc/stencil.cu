@@ -574,6 +574,114 @@ __global__ void rhs_df_kernel(int order, int colloc, int nx, int ny, int nz, Rhs
     F[id] = cdf_to_double2(out);
 }
 
+// Sixth order, plane-marching form of the same right-hand side.  Regrouped by neighbour class, the
+// formula above is
+//   F = a0 f + sum_d a1_d (f_{+1,d} + f_{-1,d}) + sum_d a2_d (f_{+2,d} + f_{-2,d}) + sum_q m_q C_q
+//       - (h^2/20) k^2 f + (h^4/60) sum_d g_d f_d,
+// with C_q the sum of the four corners of the plane pair q (xy, xz, yz) and, from the three groups of terms
+// (second differences L_d, fourth differences Q_d, mixed differences M_q),
+//   a0 = 1 - 30 sum L_d + 6 sum Q_d + 4 sum M_q,  a1_d = 16 L_d - 4 Q_d - 2 sum_{q ni d} M_q,
+//   a2_d = Q_d - L_d,  m_q = M_q,
+// so each class is summed first and scaled once (ten double-float products instead of the per-term ones).
+// A CTA owns a 32 x 8 column tile and marches RZC planes in z; the planes z-2 .. z+3 sit in a six-slot
+// shared-memory ring filled by 16-byte cp.async from the mirror-extended halo (its in-plane offsets are
+// computed once per staging slot), so a point's 24 neighbours are shared-memory reads.
+struct Rhs6W {
+    df a0;
+    df a1[3];
+    df a2[3];
+    df m[3];          // pairs xy, xz, yz
+    df h2_20;
+    float h4_60;
+    float i2h[3];
+};
+constexpr int R6TX = 32, R6TY = 8, R6H = 2;
+constexpr int R6PX = R6TX + 2 * R6H, R6PY = R6TY + 2 * R6H, R6PTS = R6PX * R6PY;   // 36 x 12 staged points
+constexpr int R6NS = 6, R6ZC = 32;
+
+__device__ __forceinline__ void r6_cp16(void* smem, const void* gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+
+__global__ void __launch_bounds__(R6TX * R6TY) rhs6_plane_kernel(int colloc, int nx, int ny, int nz, Rhs6W W,
+                                                              const float4* __restrict__ fdf,
+                                                              const float4* __restrict__ k2df,
+                                                              const float2* __restrict__ dkx,
+                                                              const float2* __restrict__ dky,
+                                                              const float2* __restrict__ dkz,
+                                                              double2* __restrict__ F) {
+    __shared__ __align__(16) float4 ring[R6NS][R6PTS];
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * R6TX + tx;
+    const int x0 = blockIdx.x * R6TX, y0 = blockIdx.y * R6TY, z0 = blockIdx.z * R6ZC;
+    const int z1 = min(z0 + R6ZC, nz);
+    const size_t plane = (size_t)nx * ny;
+    size_t soff[2] = {0, 0};
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const int q = tid + k * R6TX * R6TY;
+        if (q < R6PTS) {
+            const int ly = q / R6PX, lx = q - ly * R6PX;
+            // points beyond the two-point halo of the grid are never read: clamp them into it first
+            const int X = mirror_ext(min(x0 + lx - R6H, nx + 1), nx, colloc);
+            const int Y = mirror_ext(min(y0 + ly - R6H, ny + 1), ny, colloc);
+            soff[k] = (size_t)Y * nx + X;
+        }
+    }
+    auto issue = [&](int P) {
+        if (P <= z1 + 1) {
+            float4* S = ring[(P + 2 * R6NS) % R6NS];
+            const size_t pb = (size_t)mirror_ext(P, nz, colloc) * plane;
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+                const int q = tid + k * R6TX * R6TY;
+                if (q < R6PTS) r6_cp16(&S[q], fdf + pb + soff[k]);
+            }
+        }
+        asm volatile("cp.async.commit_group;\n" ::: "memory");
+    };
+    for (int P = z0 - 2; P <= z0 + 2; ++P) issue(P);
+    const int gx = x0 + tx, gy = y0 + ty;
+    const bool active = gx < nx && gy < ny;
+    const int c = (ty + R6H) * R6PX + tx + R6H;
+    for (int z = z0; z < z1; ++z) {
+        asm volatile("cp.async.wait_group 0;\n" ::: "memory");   // planes up to z + 2 have landed
+        __syncthreads();                                         // ... for everyone; plane z - 3 is free
+        issue(z + 3);
+        if (!active) continue;
+        const float4* Sm2 = ring[(z - 2 + 2 * R6NS) % R6NS];
+        const float4* Sm1 = ring[(z - 1 + 2 * R6NS) % R6NS];
+        const float4* S0 = ring[z % R6NS];
+        const float4* Sp1 = ring[(z + 1) % R6NS];
+        const float4* Sp2 = ring[(z + 2) % R6NS];
+        auto L = [&](const float4* S, int o) { return cdf_from4(S[c + o]); };
+        const cdf fc = L(S0, 0);
+        const cdf xm = L(S0, -1), xp = L(S0, 1), ym = L(S0, -R6PX), yp = L(S0, R6PX), zm = L(Sm1, 0), zp = L(Sp1, 0);
+        cdf out = cdf_scale(fc, W.a0);
+        out = cdf_add(out, cdf_scale(cdf_add(xm, xp), W.a1[0]));
+        out = cdf_add(out, cdf_scale(cdf_add(ym, yp), W.a1[1]));
+        out = cdf_add(out, cdf_scale(cdf_add(zm, zp), W.a1[2]));
+        out = cdf_add(out, cdf_scale(cdf_add(L(S0, -2), L(S0, 2)), W.a2[0]));
+        out = cdf_add(out, cdf_scale(cdf_add(L(S0, -2 * R6PX), L(S0, 2 * R6PX)), W.a2[1]));
+        out = cdf_add(out, cdf_scale(cdf_add(L(Sm2, 0), L(Sp2, 0)), W.a2[2]));
+        const cdf cxy = cdf_add(cdf_add(L(S0, -R6PX - 1), L(S0, -R6PX + 1)), cdf_add(L(S0, R6PX - 1), L(S0, R6PX + 1)));
+        const cdf cxz = cdf_add(cdf_add(L(Sm1, -1), L(Sm1, 1)), cdf_add(L(Sp1, -1), L(Sp1, 1)));
+        const cdf cyz = cdf_add(cdf_add(L(Sm1, -R6PX), L(Sm1, R6PX)), cdf_add(L(Sp1, -R6PX), L(Sp1, R6PX)));
+        out = cdf_add(out, cdf_scale(cxy, W.m[0]));
+        out = cdf_add(out, cdf_scale(cxz, W.m[1]));
+        out = cdf_add(out, cdf_scale(cyz, W.m[2]));
+        const size_t id = (size_t)z * plane + (size_t)gy * nx + gx;
+        out = cdf_sub(out, cdf_scale(cdf_mul(cdf_from4(k2df[id]), fc), W.h2_20));
+        // (h^4/60) sum_d g_d f_d in FP32 from the leading parts, as in rhs_df_kernel
+        const float2 fdx = make_float2((xp.re.hi - xm.re.hi) * W.i2h[0], (xp.im.hi - xm.im.hi) * W.i2h[0]);
+        const float2 fdy = make_float2((yp.re.hi - ym.re.hi) * W.i2h[1], (yp.im.hi - ym.im.hi) * W.i2h[1]);
+        const float2 fdz = make_float2((zp.re.hi - zm.re.hi) * W.i2h[2], (zp.im.hi - zm.im.hi) * W.i2h[2]);
+        const float2 g = cadd(cadd(cmul(dkx[id], fdx), cmul(dky[id], fdy)), cmul(dkz[id], fdz));
+        out = cdf_add(out, cdf_from_f2(make_float2(W.h4_60 * g.x, W.h4_60 * g.y)));
+        F[id] = cdf_to_double2(out);
+    }
+}
+
 __global__ void f64_to_df_kernel(const double2* __restrict__ a, float4* __restrict__ b, size_t n) {
     const size_t stride = (size_t)gridDim.x * blockDim.x;
     for (size_t id0 = blockIdx.x * (size_t)blockDim.x + threadIdx.x; id0 < n; id0 += 4 * stride) {
@@ -784,6 +892,36 @@ helm_status launch_rhs(helm_ctx* c, const double2* f, double2* F, float4* fdf, c
         W.mix[q] = PDF::cst(h2 * h2 / (90.0 * hh[pr[q][0]] * hh[pr[q][0]] * hh[pr[q][1]] * hh[pr[q][1]]));
     W.h2_20 = PDF::cst(h2 / 20.0);
     W.h4_60 = (float)(h2 * h2 / 60.0);
+    if (c->opt.order == 6) {
+        double Ld[3], Qd[3], Mq[3];
+        for (int d = 0; d < 3; ++d) {
+            Ld[d] = h2 / (144.0 * hh[d] * hh[d]);
+            Qd[d] = h2 * h2 / (360.0 * hh[d] * hh[d] * hh[d] * hh[d]);
+        }
+        for (int q = 0; q < 3; ++q)
+            Mq[q] = h2 * h2 / (90.0 * hh[pr[q][0]] * hh[pr[q][0]] * hh[pr[q][1]] * hh[pr[q][1]]);
+        Rhs6W R;
+        double a0 = 1.0;
+        for (int d = 0; d < 3; ++d) a0 += -30.0 * Ld[d] + 6.0 * Qd[d] + 4.0 * Mq[d];
+        R.a0 = PDF::cst(a0);
+        for (int d = 0; d < 3; ++d) {
+            double mm = 0;
+            for (int q = 0; q < 3; ++q)
+                if (pr[q][0] == d || pr[q][1] == d) mm += Mq[q];
+            R.a1[d] = PDF::cst(16.0 * Ld[d] - 4.0 * Qd[d] - 2.0 * mm);
+            R.a2[d] = PDF::cst(Qd[d] - Ld[d]);
+            R.m[d] = PDF::cst(Mq[d]);
+            R.i2h[d] = W.i2h[d];
+        }
+        R.h2_20 = W.h2_20;
+        R.h4_60 = W.h4_60;
+        const dim3 grid((c->nx + R6TX - 1) / R6TX, (c->ny + R6TY - 1) / R6TY, (c->nz + R6ZC - 1) / R6ZC);
+        rhs6_plane_kernel<<<grid, dim3(R6TX, R6TY), 0, s>>>(c->colloc, c->nx, c->ny, c->nz, R, fdf, c->k2_df,
+                                                             c->dk2_f[0], c->dk2_f[1], c->dk2_f[2], F);
+        prof_end(c, s);
+        HELM_CUDA_TRY(cudaGetLastError());
+        return HELM_OK;
+    }
     rhs_df_kernel<<<dim3((c->nx + 127) / 128, c->ny, c->nz), 128, 0, s>>>(c->opt.order, c->colloc, c->nx, c->ny,
                                                                          c->nz, W, fdf,
                                                                          c->k2_df,
