@@ -281,7 +281,7 @@ __device__ __forceinline__ void update_body(const float2* __restrict__ V, size_t
     __shared__ double red[NT / 32];
     for (int i = threadIdx.x; i < nv; i += NT) cf[i] = coef[i];
     __syncthreads();
-    double acc = 0.0;
+    float fs = 0.f, fc = 0.f;   // per-thread compensated FP32 sum of |w|^2 (FP64 only across threads)
     const size_t n4 = npts / 2;
     float4* W4 = reinterpret_cast<float4*>(w);
     for (size_t id = blockIdx.x * (size_t)NT + threadIdx.x; id < n4; id += (size_t)gridDim.x * NT) {
@@ -309,8 +309,9 @@ __device__ __forceinline__ void update_body(const float2* __restrict__ V, size_t
             x.w -= c.x * v.w + c.y * v.z;
         }
         W4[id] = x;
-        acc += (double)fmaf(x.x, x.x, fmaf(x.y, x.y, fmaf(x.z, x.z, x.w * x.w)));
+        kahan_add(fs, fc, fmaf(x.x, x.x, fmaf(x.y, x.y, fmaf(x.z, x.z, x.w * x.w))));
     }
+    double acc = (double)fs - (double)fc;
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
     __syncthreads();
@@ -477,9 +478,10 @@ __global__ void to_df_kernel(const double2* __restrict__ a, float4* __restrict__
         for (int u = 0; u < 4; ++u) {
             const size_t id = id0 + u * stride;
             if (id < npts) {
-                const float rh = (float)v[u].x, ih = (float)v[u].y;
-                b[id] = make_float4(rh, ih, (float)(v[u].x - (double)rh), (float)(v[u].y - (double)ih));
-                any |= (v[u].x != 0.0 || v[u].y != 0.0);
+                b[id] = split4_bits(v[u]);
+                // nonzero test on the patterns (+-0 have only the sign bit)
+                any |= ((((unsigned long long)__double_as_longlong(v[u].x)) << 1) |
+                        (((unsigned long long)__double_as_longlong(v[u].y)) << 1)) != 0ull;
             }
         }
     }
@@ -497,7 +499,7 @@ __global__ void from_df_kernel(const float4* __restrict__ a, double2* __restrict
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             const size_t id = id0 + u * stride;
-            if (id < npts) b[id] = make_double2((double)v[u].x + (double)v[u].z, (double)v[u].y + (double)v[u].w);
+            if (id < npts) b[id] = df4_to_double2(v[u]);
         }
     }
 }
@@ -506,14 +508,15 @@ __global__ void from_df_kernel(const float4* __restrict__ a, double2* __restrict
 __global__ void __launch_bounds__(NT) residual_zero_kernel(const float4* __restrict__ F, float2* __restrict__ r,
                                                           size_t npts, double* __restrict__ part) {
     __shared__ double rs[NT / 32], rm[NT / 32];
-    double s = 0, mx = 0;
+    float fs = 0.f, fc = 0.f, fm = 0.f;   // per-thread compensated FP32 sum and max of |r|^2; FP64 across threads
     for (size_t id = blockIdx.x * (size_t)NT + threadIdx.x; id < npts; id += (size_t)gridDim.x * NT) {
         const float2 v = cdf_round(cdf_from4(F[id]));
         r[id] = v;
-        const double a2 = (double)v.x * v.x + (double)v.y * v.y;
-        s += a2;
-        mx = fmax(mx, a2);
+        const float a2 = fmaf(v.x, v.x, v.y * v.y);
+        kahan_add(fs, fc, a2);
+        fm = fmaxf(fm, a2);
     }
+    double s = (double)fs - (double)fc, mx = (double)fm;
     for (int o = 16; o > 0; o >>= 1) {
         s += __shfl_down_sync(0xffffffffu, s, o);
         mx = fmax(mx, __shfl_down_sync(0xffffffffu, mx, o));

@@ -33,9 +33,7 @@ void* g_scratch_dev[NA_MAX_DEVICES] = {nullptr};
 
 __global__ void na_to_df_kernel(const double2* __restrict__ a, float4* __restrict__ b, size_t n) {
     for (size_t id = blockIdx.x * (size_t)blockDim.x + threadIdx.x; id < n; id += (size_t)gridDim.x * blockDim.x) {
-        const double2 v = a[id];
-        const float rh = (float)v.x, ih = (float)v.y;
-        b[id] = make_float4(rh, ih, (float)(v.x - (double)rh), (float)(v.y - (double)ih));
+        b[id] = split4_bits(a[id]);
     }
 }
 

@@ -94,11 +94,14 @@ struct PDF {
         return df{h, (float)(v - (double)h)};
     }
     static __device__ __forceinline__ C zero() { return cdf_zero(); }
-    static __device__ __forceinline__ LC lo(C a) { return make_float2(a.re.hi, a.im.hi); }
+    static __device__ __forceinline__ LC lo(C a) { return a.hi; }
     static __device__ __forceinline__ C from_lo(LC a) { return cdf_from_f2(a); }
     static __device__ __forceinline__ void st(M* d, C v) { *d = cdf_to4(v); }
     static __device__ __forceinline__ float2 r32(C v) { return cdf_round(v); }
-    static __host__ C hc(double2 v) { return C{cst(v.x), cst(v.y)}; }
+    static __host__ C hc(double2 v) {
+        const S r = cst(v.x), i = cst(v.y);
+        return C{make_float2(r.hi, i.hi), make_float2(r.lo, i.lo)};
+    }
 };
 
 template <class P>
@@ -432,10 +435,7 @@ __device__ inline int mirror_stag(int i, int n) { return i < 0 ? -i - 1 : (i >= 
 // mirror about the face (staggered) or about the boundary node (collocated), for offsets of at most 2
 __device__ inline int mirror_ext(int i, int n, int colloc) { return colloc ? reflect_node(i, n) : mirror_stag(i, n); }
 
-__device__ __forceinline__ float4 split4(double2 v) {
-    const float rh = (float)v.x, ih = (float)v.y;
-    return make_float4(rh, ih, (float)(v.x - (double)rh), (float)(v.y - (double)ih));
-}
+__device__ __forceinline__ float4 split4(double2 v) { return split4_bits(v); }
 
 __global__ void derived_kernel(int order, int colloc, int nx, int ny, int nz, double hx, double hy, double hz,
                                const double2* __restrict__ k2, double2* dkx, double2* dky, double2* dkz, double2* G,
@@ -520,7 +520,7 @@ __global__ void rhs_df_kernel(int order, int colloc, int nx, int ny, int nz, Rhs
     // integer weights are applied as exact power-of-two scalings; the edge points of the mixed
     // differences are the line neighbours already loaded, so only the corners are new loads.
     auto p2 = [](cdf a, float sc) {   // a * sc, sc a power of two: exact
-        return cdf{df{a.re.hi * sc, a.re.lo * sc}, df{a.im.hi * sc, a.im.lo * sc}};
+        return cdf{mul2(a.hi, bc2(sc)), mul2(a.lo, bc2(sc))};
     };
     cdf s13[3], s04[3];
     float2 fd[3];
@@ -533,7 +533,7 @@ __global__ void rhs_df_kernel(int order, int colloc, int nx, int ny, int nz, Rhs
         o[d] = -2; const cdf vm2 = at(o[0], o[1], o[2]);
         s13[d] = cdf_add(vp1, vm1);
         s04[d] = cdf_add(vp2, vm2);
-        fd[d] = make_float2((vp1.re.hi - vm1.re.hi) * W.i2h[d], (vp1.im.hi - vm1.im.hi) * W.i2h[d]);
+        fd[d] = mul2(sub2(vp1.hi, vm1.hi), bc2(W.i2h[d]));
     }
     const cdf f30 = cdf_sub(p2(fc, 32.f), p2(fc, 2.f));   // 30 f
     const cdf f6 = cdf_add(p2(fc, 4.f), p2(fc, 2.f));     // 6 f
@@ -673,12 +673,12 @@ __global__ void __launch_bounds__(R6TX * R6TY) rhs6_plane_kernel(int colloc, int
         const size_t id = (size_t)z * plane + (size_t)gy * nx + gx;
         out = cdf_sub(out, cdf_scale(cdf_mul(cdf_from4(k2df[id]), fc), W.h2_20));
         // (h^4/60) sum_d g_d f_d in FP32 from the leading parts, as in rhs_df_kernel
-        const float2 fdx = make_float2((xp.re.hi - xm.re.hi) * W.i2h[0], (xp.im.hi - xm.im.hi) * W.i2h[0]);
-        const float2 fdy = make_float2((yp.re.hi - ym.re.hi) * W.i2h[1], (yp.im.hi - ym.im.hi) * W.i2h[1]);
-        const float2 fdz = make_float2((zp.re.hi - zm.re.hi) * W.i2h[2], (zp.im.hi - zm.im.hi) * W.i2h[2]);
+        const float2 fdx = mul2(sub2(xp.hi, xm.hi), bc2(W.i2h[0]));
+        const float2 fdy = mul2(sub2(yp.hi, ym.hi), bc2(W.i2h[1]));
+        const float2 fdz = mul2(sub2(zp.hi, zm.hi), bc2(W.i2h[2]));
         const float2 g = cadd(cadd(cmul(dkx[id], fdx), cmul(dky[id], fdy)), cmul(dkz[id], fdz));
         out = cdf_add(out, cdf_from_f2(make_float2(W.h4_60 * g.x, W.h4_60 * g.y)));
-        F[id] = cdf_to_double2(out);
+        F[id] = cdf_to_double2_fp64(out);
     }
 }
 

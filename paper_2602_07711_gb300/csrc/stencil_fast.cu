@@ -30,6 +30,7 @@
 //     every plane, so their offsets and ghost factors are computed once); a prepare pass per plane
 //     applies the ghost factors and forms KU = k^2 U once per staged point.
 #include "common.cuh"
+#include "packed.cuh"
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -87,14 +88,14 @@ __device__ __forceinline__ void cp16f(void* smem, const void* gmem) {
 __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
 
-__device__ __forceinline__ float2 f2add(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ float2 f2sub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
-__device__ __forceinline__ float2 f2scl(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
-__device__ __forceinline__ float2 f2fma(float s, float2 a, float2 b) {   // s a + b
-    return make_float2(fmaf(s, a.x, b.x), fmaf(s, a.y, b.y));
-}
+// complex64 helpers on packed pairs (one f32x2 instruction per operation, two for the product)
+__device__ __forceinline__ float2 f2add(float2 a, float2 b) { return add2(a, b); }
+__device__ __forceinline__ float2 f2sub(float2 a, float2 b) { return sub2(a, b); }
+__device__ __forceinline__ float2 f2scl(float2 a, float s) { return mul2(a, bc2(s)); }
+__device__ __forceinline__ float2 f2fma(float s, float2 a, float2 b) { return fma2(bc2(s), a, b); }   // s a + b
+// a b = a.x (b.x, b.y) + (-a.y, a.y) (b.y, b.x)
 __device__ __forceinline__ float2 f2mul(float2 a, float2 b) {
-    return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+    return fma2(make_float2(-a.y, a.y), swap2(b), mul2(bc2(a.x), b));
 }
 
 template <int ORDER, int MINB, bool RK = false>
@@ -733,7 +734,7 @@ __device__ __forceinline__ cdf cdf_sc(cdf a) {
     constexpr df s = dfc((double)NUM / (double)DEN);
     return cdf_scale(a, s);
 }
-__device__ __forceinline__ float2 hi2(cdf a) { return make_float2(a.re.hi, a.im.hi); }
+__device__ __forceinline__ float2 hi2(cdf a) { return a.hi; }
 
 template <int ORDER>
 __global__ void __launch_bounds__(FNT, 2)
@@ -753,7 +754,7 @@ residual_fast_kernel(RParams p, const float4* __restrict__ X, float2* __restrict
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
         const int q = tid + k * FNT;
-        sgam[k] = cdf{df{1.f, 0.f}, df{0.f, 0.f}};
+        sgam[k] = cdf{make_float2(1.f, 0.f), make_float2(0.f, 0.f)};
         if (q < FHALO) {
             const int ly = q / FPX, lx = q - ly * FPX;
             const int Xg = x0 + lx - 1, Yg = y0 + ly - 1;
@@ -793,7 +794,7 @@ residual_fast_kernel(RParams p, const float4* __restrict__ X, float2* __restrict
 
     cdf cA = cdf_zero(), nA = cdf_zero();
     float2 cX = make_float2(0, 0), cY = cX, cZ = cX, nX = cX, nY = cX, nZ = cX;
-    double ssum = 0.0, smax = 0.0;
+    float fsum = 0.f, fcmp = 0.f, fmx = 0.f;   // per-thread compensated FP32 sum and max of |r|^2
     issue(z0 - 1);
     issue(z0);
     for (int P = z0 - 1; P <= z1; ++P) {
@@ -866,9 +867,9 @@ residual_fast_kernel(RParams p, const float4* __restrict__ X, float2* __restrict
                 const cdf r = cdf_sub(cdf_from4(Sp.F[tid]), A);
                 const float2 rf = cdf_round(r);
                 rout[(size_t)(P - 1) * plane + poff] = rf;
-                const double a2 = (double)rf.x * rf.x + (double)rf.y * rf.y;
-                ssum += a2;
-                smax = fmax(smax, a2);
+                const float a2 = fmaf(rf.x, rf.x, rf.y * rf.y);
+                kahan_add(fsum, fcmp, a2);
+                fmx = fmaxf(fmx, a2);
             }
         }
         cA = nA; cX = nX; cY = nY; cZ = nZ;
@@ -897,6 +898,7 @@ residual_fast_kernel(RParams p, const float4* __restrict__ X, float2* __restrict
         nA = As; nX = Xs; nY = Ys; nZ = make_float2(-Zs.x, -Zs.y);
     }
     __shared__ double rs[FNT / 32], rm[FNT / 32];
+    double ssum = (double)fsum - (double)fcmp, smax = (double)fmx;   // FP64 across threads
     for (int o = 16; o > 0; o >>= 1) {
         ssum += __shfl_down_sync(0xffffffffu, ssum, o);
         smax = fmax(smax, __shfl_down_sync(0xffffffffu, smax, o));
@@ -917,7 +919,7 @@ int rsmem() { return (int)(FNS * sizeof(RStage<ORDER>)); }
 
 cdf cdf_host(double2 v) {
     const float rh = (float)v.x, ih = (float)v.y;
-    return cdf{df{rh, (float)(v.x - (double)rh)}, df{ih, (float)(v.y - (double)ih)}};
+    return cdf{make_float2(rh, ih), make_float2((float)(v.x - (double)rh), (float)(v.y - (double)ih))};
 }
 df df_host(double v) {
     const float h = (float)v;
