@@ -143,6 +143,10 @@ struct helm_ctx {
     int tune_nb = 0;                        // CTAs of the Arnoldi kernels chosen by helm_autotune (0 = default)
     int tune_stencil = 0;                   // complex64 matvec variant chosen by helm_autotune (0 = cp.async ring)
     int zring_sms = 0;                      // SM count, set with the ring kernel's attributes at set-up
+    int zpiv_ready = 0;                     // shared-memory attribute of the pivot-recomputing z-solve set
+    void* zck = nullptr;                    // pivot checkpoints of that z-solve ([block][line pair] float4)
+    int zpiv_off = 0;                       // set while capturing launches that may run concurrently (batch lanes)
+    size_t zck_bytes = 0;
     int tune_zring = 2;                     // factorised z-solve: CTAs per SM of the L2-resident ring kernel (0 = one thread per line)
     int tune_ypers = 1;                     // y-pass: 1 persistent with double-buffered accumulators, 0 one tile per CTA
     int tune_tc = 1;                        // x-pass on the tensor cores: 1 persistent, 0 one tile per CTA
@@ -201,6 +205,7 @@ helm_status tc_prepare_sine(helm_ctx* c, const double2* Sx, const double2* Sy, c
                             cudaStream_t s);
 void tc_release(helm_ctx* c);
 // thomas.cu
+helm_status zsolve_reserve(helm_ctx* c, int nb);
 helm_status launch_zsolve(helm_ctx* c, const float2* in, float2* out, cudaStream_t s, int nb = 1);
 helm_status zsolve_factor(helm_ctx* c, cudaStream_t s);
 helm_status zsolve_factor_with(helm_ctx* c, const float2* dxs, const float2* dys, float2** m, cudaStream_t s);

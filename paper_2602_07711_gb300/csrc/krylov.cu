@@ -1212,10 +1212,14 @@ size_t lane_bytes(const helm_ctx* c) {
 }
 
 // the preconditioner of a lane, on the lane's own scratch vector (the context's is shared by all its lanes)
+// (the lanes' cycle ends run as parallel branches: their z-solves take the stored-factor kernel, which
+// needs no per-context scratch)
 helm_status lane_precond(Lane& ln, const float2* r, float2* z, const double* sigma, int sidx, cudaStream_t s) {
     float2* save = ln.c->tmp;
     ln.c->tmp = ln.tmp;
+    ln.c->zpiv_off = 1;
     helm_status st = precond_apply(ln.c, r, z, sigma, sidx, s);
+    ln.c->zpiv_off = 0;
     ln.c->tmp = save;
     return st;
 }
@@ -1448,6 +1452,7 @@ helm_status plan_build(helm_batch* P) {
             lt[r] = LaneDev{k.V, k.part, k.H, k.cs, k.sn, k.g, k.sigma, k.coef, k.ctrl_d, ln.L_d};
         }
         HELM_CUDA_TRY(cudaMemcpy(g.lt, lt.data(), sizeof(LaneDev) * nb, cudaMemcpyHostToDevice));
+        if ((st = zsolve_reserve(c, nb)) != HELM_OK) return st;   // before capture
     }
     HELM_CUDA_TRY(cudaMalloc(&P->flags, sizeof(int) * P->lanes.size()));
     for (size_t i = 0; i < P->lanes.size(); ++i) P->lanes[i].more = P->flags + i;

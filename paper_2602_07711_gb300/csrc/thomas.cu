@@ -47,6 +47,36 @@ __device__ inline void note_pivot(float2 d, unsigned* status) {
     if (!(fabsf(d.x) + fabsf(d.y) > 1e-30f)) atomicOr(status, (unsigned)HELM_DEV_PIVOT);
 }
 
+// The steps of the factorised solve, every operation rounded as written (explicit fma/mul/add, so that no
+// kernel contracts differently): the set-up factors, the forward and backward sweeps over stored factors
+// and the sweeps that recompute the factors all produce the same bits.
+// pivot step: m_l = 1 / (b_l - a_l c'_{l-1}) with b_l = s + cz_l (+ gamma_z at the ends), then c'_l = sup_l m_l
+// (*dmag, when given: |Re| + |Im| of the pivot, for the tiny-pivot check of the set-up)
+__device__ __forceinline__ float2 zpivot(float2 s, float2 czl, bool end, float2 gz, float a, float sup, float2& c,
+                                         float* dmag = nullptr) {
+    float bx = __fadd_rn(s.x, czl.x), by = __fadd_rn(s.y, czl.y);
+    if (end) { bx = __fadd_rn(bx, gz.x); by = __fadd_rn(by, gz.y); }
+    const float dx = __fmaf_rn(-c.x, a, bx), dy = __fmaf_rn(-c.y, a, by);
+    if (dmag) *dmag = fabsf(dx) + fabsf(dy);
+    // 1/|pivot|^2 by the hardware reciprocal (at most one ulp off, one instruction: the recurrence is the
+    // critical path of every line), then m = conj(pivot) / |pivot|^2
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(__fmaf_rn(dx, dx, __fmul_rn(dy, dy))));
+    const float2 m = make_float2(__fmul_rn(dx, r), __fmul_rn(-dy, r));
+    c = make_float2(__fmul_rn(m.x, sup), __fmul_rn(m.y, sup));
+    return m;
+}
+// forward: d_l = (y_l - a_l d_{l-1}) m_l
+__device__ __forceinline__ float2 zfwd(float2 y, float2 d, float a, float2 m) {
+    const float tx = __fmaf_rn(-d.x, a, y.x), ty = __fmaf_rn(-d.y, a, y.y);
+    return make_float2(__fmaf_rn(tx, m.x, __fmul_rn(-ty, m.y)), __fmaf_rn(tx, m.y, __fmul_rn(ty, m.x)));
+}
+// backward: x_l = d_l - sup_l (m_l x_{l+1})
+__device__ __forceinline__ float2 zbwd(float2 d, float2 m, float2 x, float sup) {
+    const float px = __fmaf_rn(m.x, x.x, __fmul_rn(-m.y, x.y)), py = __fmaf_rn(m.x, x.y, __fmul_rn(m.y, x.x));
+    return make_float2(__fmaf_rn(-px, sup, d.x), __fmaf_rn(-py, sup, d.y));
+}
+
 template <int L, int MCH>
 __global__ void __launch_bounds__(L * 32)
 zsolve_kernel(ZParams p, const float2* in, float2* out, unsigned* status) {
@@ -210,19 +240,16 @@ __global__ void __launch_bounds__(128) zfactor_kernel(ZParams p, float2* __restr
     const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
     if (i >= p.nx) return;
     const size_t plane = (size_t)p.nx * p.ny, base = (size_t)j * p.nx + i;
-    const float2 dxy = cadd(p.dxs[i], p.dys[j]);
+    const float2 dxy = make_float2(__fadd_rn(p.dxs[i].x, p.dys[j].x), __fadd_rn(p.dxs[i].y, p.dys[j].y));
     float2 cprev = f2(0.f, 0.f);
     float minpiv = 1e30f;
     for (int l = 0; l < p.nz; ++l) {
-        float2 b = cadd(dxy, p.cz[l]);
-        if (l == 0 || l == p.nz - 1) b = cadd(b, p.gz);
         const float a = l == 0 ? 0.f : (l == p.nz - 1 ? p.zz : 1.f);
         const float sup = l == p.nz - 1 ? 0.f : (l == 0 ? p.zz : 1.f);
-        const float2 den = csub(b, cscale(cprev, a));
-        minpiv = fminf(minpiv, fabsf(den.x) + fabsf(den.y));
-        const float2 mi = crcp(den);
+        float dm;
+        const float2 mi = zpivot(dxy, p.cz[l], l == 0 || l == p.nz - 1, p.gz, a, sup, cprev, &dm);
+        minpiv = fminf(minpiv, dm);
         m[base + (size_t)l * plane] = mi;
-        cprev = cscale(mi, sup);
     }
     if (!(minpiv > 1e-30f)) atomicOr(status, (unsigned)HELM_DEV_PIVOT);
 }
@@ -264,7 +291,7 @@ __global__ void __launch_bounds__(128) zsolve_fact_kernel(int nx, int ny, int nz
             const int l = l0 + u;
             if (l < nz) {
                 const float a = l == 0 ? 0.f : (l == nz - 1 ? zz : 1.f);
-                d = cmul(csub(yv[u], cscale(d, a)), mv[u]);
+                d = zfwd(yv[u], d, a, mv[u]);
                 out[base + (size_t)l * plane] = d;
             }
         }
@@ -285,7 +312,7 @@ __global__ void __launch_bounds__(128) zsolve_fact_kernel(int nx, int ny, int nz
             const int l = l1 - 1 - u;
             if (l >= 0) {
                 const float sup = l == nz - 1 ? 0.f : (l == 0 ? zz : 1.f);
-                x = csub(dv[u], cscale(cmul(mv[u], x), sup));
+                x = zbwd(dv[u], mv[u], x, sup);
                 out[base + (size_t)l * plane] = x;
             }
         }
@@ -354,8 +381,8 @@ __global__ void __launch_bounds__(ZRT) zsolve_ring_kernel(int nx, int ny, int nz
                 const int l = b * ZU2 + u;
                 if (l < nz) {
                     const float a = l == 0 ? 0.f : (l == nz - 1 ? zz : 1.f);
-                    d0 = cmul(csub(f2(y[u].x, y[u].y), cscale(d0, a)), f2(mm[u].x, mm[u].y));
-                    d1 = cmul(csub(f2(y[u].z, y[u].w), cscale(d1, a)), f2(mm[u].z, mm[u].w));
+                    d0 = zfwd(f2(y[u].x, y[u].y), d0, a, f2(mm[u].x, mm[u].y));
+                    d1 = zfwd(f2(y[u].z, y[u].w), d1, a, f2(mm[u].z, mm[u].w));
                     out[voff + off + (size_t)l * plane] = make_float4(d0.x, d0.y, d1.x, d1.y);
                 }
             }
@@ -392,8 +419,119 @@ __global__ void __launch_bounds__(ZRT) zsolve_ring_kernel(int nx, int ny, int nz
                 const int l = nz - 1 - (b * ZU2 + u);
                 if (l >= 0) {
                     const float sup = l == nz - 1 ? 0.f : (l == 0 ? zz : 1.f);
-                    x0 = csub(f2(dv[u].x, dv[u].y), cscale(cmul(f2(mm[u].x, mm[u].y), x0), sup));
-                    x1 = csub(f2(dv[u].z, dv[u].w), cscale(cmul(f2(mm[u].z, mm[u].w), x1), sup));
+                    x0 = zbwd(f2(dv[u].x, dv[u].y), f2(mm[u].x, mm[u].y), x0, sup);
+                    x1 = zbwd(f2(dv[u].z, dv[u].w), f2(mm[u].z, mm[u].w), x1, sup);
+                    out[voff + off + (size_t)l * plane] = make_float4(x0.x, x0.y, x1.x, x1.y);
+                }
+            }
+        }
+        zwait_all();
+    }
+}
+
+// EigT form without the factor stream: the pivots depend only on the line's lateral shift
+// s_ij = alpha_x d_{x,i} + alpha_y d_{y,j} and the plane, so the forward sweep recomputes them step by step
+// (the same operations as zfactor_kernel, one reciprocal per step) and saves the recurrence's state
+// c'_{l-1} at the start of every block of ZU2 steps to a small scratch (2 bytes per point, [block][pair]
+// so that a warp's saves are one contiguous row); the backward sweep recomputes the ZU2 factors of a block
+// forward from its checkpoint into registers and then runs the block backwards.  HBM sees y read, the
+// forward values written over the output and read back (mostly from L2), and x written: the 8 bytes per
+// point of factors and their L2 footprint are gone.  A grid is one thread per pair of lines (32k threads
+// at 256^3, three to four 64-thread CTAs per SM), so latency is hidden by prefetch depth: a six-block ring
+// per thread (48 steps ahead, 48 KiB per CTA), and each backward block's checkpoint is loaded one block
+// ahead of its use.
+constexpr int ZPB = 6;   // ring depth (blocks) of the pivot-recomputing kernel
+constexpr size_t ZPIV_SMEM = (size_t)ZPB * ZU2 * ZRT * sizeof(float4);   // 48 KiB
+__device__ __forceinline__ void zwait_piv() { asm volatile("cp.async.wait_group %0;\n" ::"n"(ZPB - 1) : "memory"); }
+
+__global__ void __launch_bounds__(ZRT, 4) zsolve_piv_kernel(int nx, int ny, int nz, float zz, float2 gz,
+                                                           const float2* __restrict__ dxs,
+                                                           const float2* __restrict__ dys,
+                                                           const float2* __restrict__ cz, const float4* in, float4* out,
+                                                           float4* __restrict__ ck, int nb) {
+    extern __shared__ float4 zsm[];   // [ZPB * ZU2][ZRT]
+    const int tid = threadIdx.x;
+    const int hx = nx / 2, npairs = hx * ny, nall = npairs * nb;
+    const int nblk = (nz + ZU2 - 1) / ZU2;
+    const size_t plane = (size_t)hx * ny;   // in float4 (two lines) units
+    auto slot = [&](int st) -> float4* { return &zsm[(size_t)st * ZRT + tid]; };
+    for (int prb = blockIdx.x * ZRT + tid; prb < nall; prb += gridDim.x * ZRT) {
+        const int pr = prb % npairs, vb = prb / npairs;
+        const int j = pr / hx, i0 = 2 * (pr - j * hx);
+        const float2 s0 = make_float2(__fadd_rn(dxs[i0].x, dys[j].x), __fadd_rn(dxs[i0].y, dys[j].y));
+        const float2 s1 = make_float2(__fadd_rn(dxs[i0 + 1].x, dys[j].x), __fadd_rn(dxs[i0 + 1].y, dys[j].y));
+        const size_t off = (size_t)pr, voff = (size_t)vb * plane * nz;
+        // block blk of src (steps l = blk ZU2 + u) into ring position pos
+        auto fetch = [&](const float4* src, int blk, int pos) {
+            if (blk >= 0 && blk < nblk) {
+#pragma unroll
+                for (int u = 0; u < ZU2; ++u) {
+                    const int l = blk * ZU2 + u;
+                    if (l < nz) zcp16(slot((pos % ZPB) * ZU2 + u), src + voff + off + (size_t)l * plane);
+                }
+            }
+            zcommit();
+        };
+        // one pivot step of both lines: m_l and the new c'_l from c'_{l-1}
+        auto pivots = [&](int l, float2& c0, float2& c1, float2& m0, float2& m1) {
+            const float a = l == 0 ? 0.f : (l == nz - 1 ? zz : 1.f);
+            const float sup = l == nz - 1 ? 0.f : (l == 0 ? zz : 1.f);
+            const float2 czl = cz[l];
+            const bool end = l == 0 || l == nz - 1;
+            m0 = zpivot(s0, czl, end, gz, a, sup, c0);
+            m1 = zpivot(s1, czl, end, gz, a, sup, c1);
+        };
+        // ---- forward: d_l = (y_l - a_l d_{l-1}) m_l
+        for (int b = 0; b < ZPB - 1; ++b) fetch(in, b, b);
+        float2 d0 = f2(0.f, 0.f), d1 = d0, c0 = d0, c1 = d0;
+        for (int b = 0; b < nblk; ++b) {
+            fetch(in, b + ZPB - 1, b + ZPB - 1);
+            zwait_piv();   // block b has landed
+            ck[(size_t)b * nall + prb] = make_float4(c0.x, c0.y, c1.x, c1.y);
+            float4 y[ZU2];
+#pragma unroll
+            for (int u = 0; u < ZU2; ++u) y[u] = *slot((b % ZPB) * ZU2 + u);
+#pragma unroll
+            for (int u = 0; u < ZU2; ++u) {
+                const int l = b * ZU2 + u;
+                if (l < nz) {
+                    const float a = l == 0 ? 0.f : (l == nz - 1 ? zz : 1.f);
+                    float2 m0, m1;
+                    pivots(l, c0, c1, m0, m1);
+                    d0 = zfwd(f2(y[u].x, y[u].y), d0, a, m0);
+                    d1 = zfwd(f2(y[u].z, y[u].w), d1, a, m1);
+                    out[voff + off + (size_t)l * plane] = make_float4(d0.x, d0.y, d1.x, d1.y);
+                }
+            }
+        }
+        zwait_all();
+        __threadfence_block();
+        // ---- backward: x_l = d_l - sup_l m_l x_{l+1}, blocks in decreasing order
+        for (int b = 0; b < ZPB - 1; ++b) fetch(out, nblk - 1 - b, b);
+        float2 x0 = f2(0.f, 0.f), x1 = x0;
+        float4 cnext = ck[(size_t)(nblk - 1) * nall + prb];
+        for (int b = 0; b < nblk; ++b) {
+            fetch(out, nblk - 1 - (b + ZPB - 1), b + ZPB - 1);
+            const int blk = nblk - 1 - b;
+            const float4 cv = cnext;
+            if (blk > 0) cnext = ck[(size_t)(blk - 1) * nall + prb];   // the next block's checkpoint, early
+            float2 cc0 = f2(cv.x, cv.y), cc1 = f2(cv.z, cv.w);
+            float2 m0[ZU2], m1[ZU2];
+#pragma unroll
+            for (int u = 0; u < ZU2; ++u) {
+                const int l = blk * ZU2 + u;
+                m0[u] = m1[u] = f2(0.f, 0.f);
+                if (l < nz) pivots(l, cc0, cc1, m0[u], m1[u]);
+            }
+            zwait_piv();
+#pragma unroll
+            for (int uu = 0; uu < ZU2; ++uu) {
+                const int u = ZU2 - 1 - uu, l = blk * ZU2 + u;
+                if (l < nz) {
+                    const float4 dv = *slot((b % ZPB) * ZU2 + u);
+                    const float sup = l == nz - 1 ? 0.f : (l == 0 ? zz : 1.f);
+                    x0 = zbwd(f2(dv.x, dv.y), m0[u], x0, sup);
+                    x1 = zbwd(f2(dv.z, dv.w), m1[u], x1, sup);
                     out[voff + off + (size_t)l * plane] = make_float4(x0.x, x0.y, x1.x, x1.y);
                 }
             }
@@ -477,6 +615,22 @@ helm_status launch_zsolve_gen(helm_ctx* c, const float2* in, float2* out, const 
     return HELM_OK;
 }
 
+size_t zsolve_ck_bytes(const helm_ctx* c, int nb) {
+    return (size_t)((c->nz + ZU2 - 1) / ZU2) * (size_t)(c->nx / 2) * c->ny * nb * sizeof(float4);
+}
+
+// the pivot checkpoints of nb right-hand sides per z-solve launch (device memory of the context)
+helm_status zsolve_reserve(helm_ctx* c, int nb) {
+    const size_t bytes = zsolve_ck_bytes(c, nb);
+    if (bytes <= c->zck_bytes) return HELM_OK;
+    cudaFree(c->zck);
+    c->zck = nullptr;
+    c->zck_bytes = 0;
+    if (cudaMalloc(&c->zck, bytes) != cudaSuccess) { cudaGetLastError(); return HELM_ERR_NOMEM; }
+    c->zck_bytes = bytes;
+    return HELM_OK;
+}
+
 helm_status launch_zsolve(helm_ctx* c, const float2* in, float2* out, cudaStream_t s, int nb) {
     if (!c->zfac) {
         helm_status st;
@@ -484,6 +638,36 @@ helm_status launch_zsolve(helm_ctx* c, const float2* in, float2* out, cudaStream
             if ((st = launch_zsolve_gen(c, in + (size_t)v * c->npts, out + (size_t)v * c->npts, c->dxs, c->dys, nullptr,
                                         nullptr, s)) != HELM_OK)
                 return st;
+        return HELM_OK;
+    }
+    if (in && c->nx % 2 == 0 && c->tune_zring && c->zring_sms > 0 && !c->zpiv_off) {
+        // EigT: pivots recomputed from the shifts (the set-up factors' operations), checkpoints in a scratch
+        // of the context (grown here outside stream capture; a capturing caller reserves it beforehand)
+        const int npairs = c->nx / 2 * c->ny * nb;
+        if (zsolve_ck_bytes(c, nb) > c->zck_bytes) {
+            cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+            HELM_CUDA_TRY(cudaStreamIsCapturing(s, &cap));
+            if (cap != cudaStreamCaptureStatusNone) return launch_zsolve_fact(c, c->zfac, in, out, nullptr, nullptr, s, nb);
+            helm_status st;
+            if ((st = zsolve_reserve(c, nb)) != HELM_OK) return st;
+        }
+        if (!c->zpiv_ready) {
+            HELM_CUDA_TRY(cudaFuncSetAttribute(zsolve_piv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)ZPIV_SMEM));
+            c->zpiv_ready = 1;
+        }
+        prof_begin(c, s, PROF_ZSOLVE);
+        const int sms = c->zring_sms;
+        const int need = (npairs + ZRT - 1) / ZRT;
+        const int cap = sms * 2 * c->tune_zring;   // tune_zring 1..3: 2, 4 or 6 CTAs per SM (at most 4 resident)
+        const int grid = need < cap ? need : cap;
+        zsolve_piv_kernel<<<grid, ZRT, ZPIV_SMEM, s>>>(c->nx, c->ny, c->nz, (float)c->zeta[2],
+                                                        make_float2((float)c->gam[2].x, (float)c->gam[2].y), c->dxs,
+                                                        c->dys, c->cz, reinterpret_cast<const float4*>(in),
+                                                        reinterpret_cast<float4*>(out), reinterpret_cast<float4*>(c->zck),
+                                                        nb);
+        prof_end(c, s);
+        HELM_CUDA_TRY(cudaGetLastError());
         return HELM_OK;
     }
     return launch_zsolve_fact(c, c->zfac, in, out, nullptr, nullptr, s, nb);
