@@ -275,6 +275,181 @@ stencil_fast_kernel(FParams p, const float2* __restrict__ U, float2* __restrict_
     }
 }
 
+// Two rows per thread (real media): the kernel above is bound by shared-memory traffic (each point reads a
+// 3 x 3 patch of U and of KU per plane, and KU is written once per staged point).  Here a thread computes
+// the points (x, 2 t) and (x, 2 t + 1) of the same 32 x 8 tile from one 4 x 3 patch of U and of the real
+// k^2 (a third fewer reads per point) and forms k^2 U itself, so no KU plane is written; the ghost factors
+// are applied in shared memory only by tiles that touch the boundary (and on the ghost planes), so interior
+// tiles take one barrier per plane.  128 threads per CTA, each staging three halo points.
+template <int ORDER>
+struct F2Stage {
+    float2 u[FHALO];
+    float kr[FHALO];
+    float4 f4[ORDER == 6 ? FNT : 1];   // G, g_x, g_y, g_z at the tile's points
+};
+constexpr int F2T = FNT / 2;
+template <int ORDER>
+size_t fast2_smem() { return FNS * sizeof(F2Stage<ORDER>); }
+
+template <int ORDER, int MINB>
+__global__ void __launch_bounds__(F2T, MINB)
+stencil_fast2_kernel(FParams p, const float2* __restrict__ U, float2* __restrict__ Y, const double* __restrict__ sigma,
+                     int sidx) {
+    extern __shared__ __align__(16) unsigned char fsm[];
+    using Stage = F2Stage<ORDER>;
+    Stage* ring = reinterpret_cast<Stage*>(fsm);
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * FTX + tx;   // ty = 0 .. 3
+    const int x0 = blockIdx.x * FTX, y0 = blockIdx.y * FTY;
+    const int vb = blockIdx.z % p.nb;
+    const int z0 = (blockIdx.z / p.nb) * FZCH;
+    const int z1 = min(z0 + FZCH, p.nz);
+    const int gx = x0 + tx, gy0 = y0 + 2 * ty;
+    const bool act[2] = {gx < p.nx && gy0 < p.ny, gx < p.nx && gy0 + 1 < p.ny};
+    // the tile's halo reaches a ghost point in x or y (its interior points never need a ghost factor)
+    const bool edge = x0 == 0 || y0 == 0 || x0 + FTX >= p.nx || y0 + FTY >= p.ny;
+    const float sg = sigma ? (float)sigma[sidx] : 1.f;
+    if (vb) {
+        const size_t off = (size_t)vb * p.nx * p.ny * p.nz;
+        U += off;
+        Y += off;
+    }
+    unsigned sl[3] = {0u, 0u, 0u};
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const int q = tid + k * F2T;
+        if (q < FHALO) {
+            const int ly = q / FPX, lx = q - ly * FPX;
+            const int Xg = x0 + lx - 1, Yg = y0 + ly - 1;
+            const int Xc = min(max(Xg, 0), p.nx - 1), Yc = min(max(Yg, 0), p.ny - 1);
+            sl[k] = (unsigned)(Yc * p.nx + Xc) | (Xc != Xg ? 1u << 30 : 0u) | (Yc != Yg ? 1u << 31 : 0u);
+        }
+    }
+    const size_t plane = (size_t)p.nx * p.ny;
+    const int poff = gy0 * p.nx + gx;
+    const int fi = (2 * ty) * FTX + tx;   // the fields of point r at f4[fi + r FTX]
+
+    auto issue = [&](int P) {
+        if (P <= z1) {
+            Stage& S = ring[(P + FNS) % FNS];
+            const int Pc = min(max(P, 0), p.nz - 1);
+            const float2* Ub = U + (size_t)Pc * plane;
+            const float* Kb = p.k2r + (size_t)Pc * plane;
+#pragma unroll
+            for (int k = 0; k < 3; ++k)
+                if (tid + k * F2T < FHALO) {
+                    cp8(&S.u[tid + k * F2T], Ub + (sl[k] & 0x3FFFFFFFu));
+                    cp4(&S.kr[tid + k * F2T], Kb + (sl[k] & 0x3FFFFFFFu));
+                }
+            if (ORDER == 6 && P >= z0 && P < z1) {
+                const size_t g = (size_t)P * plane + poff;
+                if (act[0]) cp16f(&S.f4[fi], p.fr + g);
+                if (act[1]) cp16f(&S.f4[fi + FTX], p.fr + g + p.nx);
+            }
+        }
+        cp_commit();
+    };
+
+    float2 cA[2], cX[2], cY[2], cZ[2], nA[2], nX[2], nY[2], nZ[2];
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+        cA[r] = cX[r] = cY[r] = cZ[r] = make_float2(0, 0);
+        nA[r] = nX[r] = nY[r] = nZ[r] = make_float2(0, 0);
+    }
+    issue(z0 - 1);
+    issue(z0);
+    for (int P = z0 - 1; P <= z1; ++P) {
+        Stage& S = ring[(P + FNS) % FNS];
+        cp_wait1();
+        __syncthreads();          // plane P landed for everyone; everyone is done with planes P-1 and P-2
+        const bool zghost = P < 0 || P >= p.nz;
+        if (edge || zghost) {     // uniform per CTA and plane
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                const int q = tid + k * F2T;
+                if (q < FHALO && ((sl[k] >> 30) || zghost)) {
+                    float2 u = S.u[q];
+                    if (sl[k] & (1u << 30)) u = f2mul(u, p.gx);
+                    if (sl[k] & (1u << 31)) u = f2mul(u, p.gy);
+                    if (zghost) u = f2mul(u, p.gz);
+                    S.u[q] = u;
+                }
+            }
+            __syncthreads();
+        }
+        issue(P + 2);             // into the slot of plane P-2
+        float2 u[4][3], kv[4][3];
+#pragma unroll
+        for (int b = 0; b < 4; ++b)
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                const int i = (2 * ty + b) * FPX + tx + a;
+                u[b][a] = S.u[i];
+                kv[b][a] = f2scl(u[b][a], S.kr[i]);   // KU = k^2 U (k^2 at a ghost point is the mirror value)
+            }
+        const bool out_prev = P - 1 >= z0 && P - 1 < z1;
+        const bool do_mid = P >= z0 && P < z1;
+        const Stage& Sp = ring[(P - 1 + FNS) % FNS];
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            const float2 c = u[r + 1][1];
+            const float2 fx = f2add(u[r + 1][0], u[r + 1][2]), fy = f2add(u[r][1], u[r + 2][1]);
+            const float2 e = f2add(f2add(u[r][0], u[r][2]), f2add(u[r + 2][0], u[r + 2][2]));
+            const float2 kc = kv[r + 1][1];
+            const float2 kf4 = f2add(f2add(kv[r + 1][0], kv[r + 1][2]), f2add(kv[r][1], kv[r + 2][1]));
+            if (ORDER == 6) {
+                const float2 kcs = f2add(f2add(kv[r][0], kv[r][2]), f2add(kv[r + 2][0], kv[r + 2][2]));
+                const float2 dkx = f2sub(kv[r + 1][2], kv[r + 1][0]), dky = f2sub(kv[r + 2][1], kv[r][1]);
+                const float ih = p.ihx;
+                float2 As = f2scl(f2fma(1.f / 30.f, e, f2fma(0.1f, f2add(fx, fy), f2scl(c, 7.f / 15.f))), ih);
+                As = f2fma(1.f / 90.f, f2sub(kf4, kc), As);
+                const float2 dx1 = f2sub(u[r + 1][2], u[r + 1][0]), dy1 = f2sub(u[r + 2][1], u[r][1]);
+                const float2 Xs = f2scl(dx1, 1.f / 6.f), Ys = f2scl(dy1, 1.f / 6.f);
+                const float2 Zs = f2add(f2fma(p.hh6, kc, c), f2scl(f2fma(-4.f, c, f2add(fx, fy)), 1.f / 6.f));
+                if (out_prev) {
+                    const float2 A = f2add(cA[r], As);
+                    const float4 fv = Sp.f4[fi + r * FTX];
+                    float2 g = f2scl(f2add(cX[r], Xs), fv.y);
+                    g = f2fma(fv.z, f2add(cY[r], Ys), g);
+                    g = f2fma(fv.w, f2add(cZ[r], Zs), g);
+                    const float2 v = f2fma(p.h_20, g, A);
+                    if (act[r]) Y[(size_t)(P - 1) * plane + poff + r * p.nx] = f2scl(v, sg);
+                }
+                cA[r] = nA[r]; cX[r] = nX[r]; cY[r] = nY[r]; cZ[r] = nZ[r];
+                if (do_mid) {
+                    float2 Am = f2scl(f2fma(-64.f / 15.f, c, f2fma(0.1f, e, f2scl(f2add(fx, fy), 7.f / 15.f))), ih);
+                    Am = f2fma(14.f / 15.f, kc, Am);
+                    Am = f2fma(1.f / 90.f, f2sub(kcs, kf4), Am);
+                    Am = f2fma(p.h2_20 * S.f4[fi + r * FTX].x, c, Am);
+                    const float2 tdx = f2sub(f2add(u[r][2], u[r + 2][2]), f2add(u[r][0], u[r + 2][0]));
+                    const float2 tdy = f2sub(f2add(u[r + 2][0], u[r + 2][2]), f2add(u[r][0], u[r][2]));
+                    const float2 Xm = f2add(f2fma(p.hh6, dkx, dx1), f2scl(f2fma(-4.f, dx1, tdx), 1.f / 6.f));
+                    const float2 Ym = f2add(f2fma(p.hh6, dky, dy1), f2scl(f2fma(-4.f, dy1, tdy), 1.f / 6.f));
+                    cA[r] = f2add(cA[r], Am); cX[r] = f2add(cX[r], Xm); cY[r] = f2add(cY[r], Ym);
+                }
+                nA[r] = As; nX[r] = Xs; nY[r] = Ys; nZ[r] = make_float2(-Zs.x, -Zs.y);
+            } else {
+                const float2 As = f2fma(1.f / 12.f, kc,
+                                        f2add(f2scl(c, p.ihz),
+                                              f2add(f2scl(f2fma(-2.f, c, fx), p.wxz), f2scl(f2fma(-2.f, c, fy), p.wyz))));
+                if (out_prev && act[r]) Y[(size_t)(P - 1) * plane + poff + r * p.nx] = f2scl(f2add(cA[r], As), sg);
+                cA[r] = nA[r];
+                if (do_mid) {
+                    const float2 c2 = f2add(c, c), c4 = f2add(c2, c2);
+                    float2 Am = f2add(f2scl(f2sub(fx, c2), p.ihx), f2scl(f2sub(fy, c2), p.ihy));
+                    Am = f2fma(-2.f * p.ihz, c, Am);
+                    Am = f2fma(p.wxy, f2add(f2fma(-2.f, f2add(fx, fy), e), c4), Am);
+                    Am = f2fma(p.wxz, f2fma(-2.f, fx, c4), Am);
+                    Am = f2fma(p.wyz, f2fma(-2.f, fy, c4), Am);
+                    Am = f2fma(0.5f, kc, Am);
+                    Am = f2fma(1.f / 12.f, kf4, Am);
+                    cA[r] = f2add(cA[r], Am);
+                }
+                nA[r] = As;
+            }
+        }
+    }
+}
+
 template <int ORDER, bool RK = false>
 size_t fast_smem() { return FNS * sizeof(FStage<ORDER, RK>); }
 
@@ -528,6 +703,10 @@ helm_status stencil_fast_prepare(helm_ctx* c) {
                                        (int)fast_smem<4, true>()));
     HELM_CUDA_TRY(cudaFuncSetAttribute(stencil_fast_kernel<6, 3, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)fast_smem<6, true>()));
+    HELM_CUDA_TRY(cudaFuncSetAttribute(stencil_fast2_kernel<6, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)fast2_smem<6>()));
+    HELM_CUDA_TRY(cudaFuncSetAttribute(stencil_fast2_kernel<4, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)fast2_smem<4>()));
     HELM_CUDA_TRY(cudaFuncSetAttribute(stencil_tma_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        TLayout<4>::SMEM));
     HELM_CUDA_TRY(cudaFuncSetAttribute(stencil_tma_kernel<6>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -612,14 +791,16 @@ helm_status stencil_real_prepare(helm_ctx* c, cudaStream_t s) {
                                             c->dk2_f[2], c->k2r, c->fr);
     HELM_CUDA_TRY(cudaGetLastError());
     c->realk = 1;
+    if (c->opt.order == 6) c->tune_stencil = 3;   // two rows per thread
     return HELM_OK;
 }
 
 bool stencil_fast_supported(const helm_ctx* c) { return !c->colloc && (c->opt.order == 4 || c->opt.order == 6); }
 
 // Variants of the complex64 matvec a context can run: 0 = cp.async ring at four CTAs per SM, 1 = TMA ring
-// (even N_x, else the same as 0), 2 = cp.async ring at three CTAs per SM with more registers.
-int stencil_variants(const helm_ctx* c) { (void)c; return 3; }
+// (even N_x, else the same as 0), 2 = cp.async ring at three CTAs per SM with more registers, 3 = two rows
+// per thread (real media; else the same as 2).
+int stencil_variants(const helm_ctx* c) { (void)c; return 4; }
 
 helm_status launch_stencil_fast(helm_ctx* c, const float2* x, float2* y, const double* sigma, int sidx, cudaStream_t s,
                                 int nb) {
@@ -667,10 +848,17 @@ helm_status launch_stencil_fast(helm_ctx* c, const float2* x, float2* y, const d
             return HELM_OK;
         }
     }
-    const bool three = c->tune_stencil == 2;   // the variant with up to 85 registers, three CTAs per SM
+    const bool three = c->tune_stencil >= 2;   // the variant with up to 85 registers, three CTAs per SM
     if (c->realk) {
         p.k2r = c->k2r;
         p.fr = c->fr;
+        if (c->tune_stencil == 3) {   // two rows per thread
+            const dim3 block2(FTX, FTY / 2);
+            if (c->opt.order == 6) stencil_fast2_kernel<6, 4><<<grid, block2, fast2_smem<6>(), s>>>(p, x, y, sigma, sidx);
+            else stencil_fast2_kernel<4, 4><<<grid, block2, fast2_smem<4>(), s>>>(p, x, y, sigma, sidx);
+            HELM_CUDA_TRY(cudaGetLastError());
+            return HELM_OK;
+        }
         if (c->opt.order == 6) {
             if (three) stencil_fast_kernel<6, 3, true><<<grid, block, fast_smem<6, true>(), s>>>(p, x, y, sigma, sidx);
             else stencil_fast_kernel<6, 4, true><<<grid, block, fast_smem<6, true>(), s>>>(p, x, y, sigma, sidx);
