@@ -124,15 +124,21 @@ __device__ __forceinline__ cdf cdf_mul_f2(cdf a, float2 b) {
 // split: hi = v rounded to nearest even on the 52-bit mantissa; v - hi = d 2^(e-52) exactly with d an
 // integer of at most 29 bits, and lo = d rounded once to a float (two exact pieces of d joined by one fma)
 // times 2^(e-52).  Fast path for 2^-74 <= |v| < 2^127 (so that 2^(e-52) is a normal float).
+// The FP64 forms for the rare values outside the fast paths live in functions of their own (not inlined),
+// so that the compiler cannot predicate their FP64 instructions into the common path.
+static __device__ __noinline__ float2 df_split_fp64(double v) {
+    const float h = (float)v;
+    return make_float2(h, (float)(v - (double)h));
+}
+static __device__ __noinline__ double df_widen_fp64(float f) { return (double)f; }
+static __device__ __noinline__ double df_join_fp64(float hi, float lo) { return (double)hi + (double)lo; }
+
 __device__ __forceinline__ float2 df_split(double v) {
     const unsigned long long b = (unsigned long long)__double_as_longlong(v);
     const unsigned hw = (unsigned)(b >> 32);
+    if ((b << 1) == 0ull) return make_float2(__uint_as_float(hw & 0x80000000u), 0.f);   // +-0
     const int e = (int)((hw >> 20) & 0x7FFu) - 1023;
-    if (e < -74 || e > 126) {
-        if ((b << 1) == 0ull) return make_float2(__uint_as_float(hw & 0x80000000u), 0.f);   // +-0
-        const float h = (float)v;
-        return make_float2(h, (float)(v - (double)h));
-    }
+    if (e < -74 || e > 126) return df_split_fp64(v);
     const unsigned long long m = b & 0xFFFFFFFFFFFFFull;
     const unsigned mh = (unsigned)(m >> 29);                    // the top 23 mantissa bits
     const unsigned r = (unsigned)(m & 0x1FFFFFFFull);           // the 29 bits below them
@@ -152,11 +158,8 @@ __device__ __forceinline__ float2 df_split(double v) {
 __device__ __forceinline__ double df_widen(float f) {
     const unsigned u = __float_as_uint(f);
     const unsigned ef = (u >> 23) & 0xFFu;
-    if (ef == 0u) {
-        if ((u << 1) == 0u) return __longlong_as_double((long long)((unsigned long long)u << 32));   // +-0
-        return (double)f;
-    }
-    if (ef == 255u) return (double)f;
+    if ((u << 1) == 0u) return __longlong_as_double((long long)((unsigned long long)u << 32));   // +-0
+    if (ef == 0u || ef == 255u) return df_widen_fp64(f);
     const unsigned long long bits = ((unsigned long long)(u & 0x80000000u) << 32) |
                                     ((unsigned long long)(ef - 127u + 1023u) << 52) |
                                     ((unsigned long long)(u & 0x7FFFFFu) << 29);
@@ -175,7 +178,7 @@ __device__ __forceinline__ double df_join(float hi, float lo) {
     // (a power-of-two hi with lo of the other sign rounds on the finer grid below it: FP64 as well)
     if (eh == 0 || eh == 255 || el == 0 || el == 255 || G < 1 ||
         (((uh ^ ul) & 0x80000000u) && (uh & 0x7FFFFFu) == 0u))
-        return df_widen(hi) + df_widen(lo);
+        return df_join_fp64(hi, lo);
     const unsigned long long bh = ((unsigned long long)(uh & 0x80000000u) << 32) |
                                   ((unsigned long long)(eh - 127 + 1023) << 52) |
                                   ((unsigned long long)(uh & 0x7FFFFFu) << 29);
@@ -193,7 +196,7 @@ __device__ __forceinline__ double df_join(float hi, float lo) {
         }
     }
     const unsigned long long r = ((uh ^ ul) & 0x80000000u) ? bh - k : bh + k;
-    if ((r ^ bh) >> 52) return df_widen(hi) + df_widen(lo);            // left hi's binade
+    if ((r ^ bh) >> 52) return df_join_fp64(hi, lo);                   // left hi's binade
     return __longlong_as_double((long long)r);
 }
 __device__ __forceinline__ float4 split4_bits(double2 v) {
