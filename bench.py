@@ -152,7 +152,7 @@ def peaks():
 # unchanged: (class, n, order) -> bytes.  On the 20-bump medium (no attenuation: the real-medium matvec)
 # with restart cycles of 17 + 8 steps: dots_pipe_kernel<4>/<8> 1202.8 MB per launch averaged over the 25
 # launches of a solve (1148.8 MB algorithmic); stencil_fast_kernel<6,3,real> 471.9 MB read + 116.7 MB written.
-MEASURED_TRAFFIC = {("dots", 256, 6): 1202.8e6, ("stencil", 256, 6): 588.6e6}
+MEASURED_TRAFFIC = {("dots", 256, 6): 1202.8e6, ("stencil", 256, 6): 592.5e6}
 
 
 def roofline(prof_ms, prof_launch, alg, precision, order, n=None, variant=None):
