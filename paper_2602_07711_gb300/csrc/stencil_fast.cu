@@ -71,6 +71,7 @@ struct FParams {
     const float4* fr;             // real (G, g_x, g_y, g_z) per point (real-medium kernels, order 6)
     int nb = 1;                   // vectors in one launch (the right-hand sides of a batch group), npts apart;
                                   // blockIdx.z = z chunk * nb + vector
+    float i12h[3], i12h2[3];      // 1/(12 h_d), 1/(12 h_d^2): the in-kernel sixth-order fields
 };
 
 __device__ __forceinline__ void cp8(void* smem, const void* gmem) {
@@ -450,6 +451,217 @@ stencil_fast2_kernel(FParams p, const float2* __restrict__ U, float2* __restrict
     }
 }
 
+// Sixth order, real medium, fields formed in the kernel: the four order-6 fields g_d = d(k^2)/dx_d and
+// G = lap(k^2) - k^4 (fourth-order five-point differences, the staggered mirror extension at the faces,
+// exactly the definitions of the set-up's derived_kernel, here in FP32) are computed from a second ring of
+// k^2 planes with a two-point halo, so the kernel streams U, k^2 and w only: 20 instead of 36 bytes per
+// point.  Otherwise the two-row form above.  The k^2 ring holds the planes P-3 .. P+4 (eight slots; a plane
+// is fetched four iterations ahead and read for the last time two iterations later); at iteration P the
+// fields of plane P are formed (G is used at once, g one iteration later, in registers).
+constexpr int K2X = FTX + 4, K2Y = FTY + 4, K2PTS = K2X * K2Y;   // 36 x 12
+constexpr int K2NS = 8;
+struct F3Stage {
+    float2 u[FHALO];
+};
+constexpr size_t F3_SMEM = FNS * sizeof(F3Stage) + K2NS * K2PTS * sizeof(float);
+
+template <int MINB>
+__global__ void __launch_bounds__(F2T, MINB)
+stencil_fast3_kernel(FParams p, const float2* __restrict__ U, float2* __restrict__ Y, const double* __restrict__ sigma,
+                     int sidx) {
+    extern __shared__ __align__(16) unsigned char fsm[];
+    F3Stage* ring = reinterpret_cast<F3Stage*>(fsm);
+    float* kring = reinterpret_cast<float*>(fsm + FNS * sizeof(F3Stage));   // [K2NS][K2PTS]
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * FTX + tx;   // ty = 0 .. 3
+    const int x0 = blockIdx.x * FTX, y0 = blockIdx.y * FTY;
+    const int vb = blockIdx.z % p.nb;
+    const int z0 = (blockIdx.z / p.nb) * FZCH;
+    const int z1 = min(z0 + FZCH, p.nz);
+    const int gx = x0 + tx, gy0 = y0 + 2 * ty;
+    const bool act[2] = {gx < p.nx && gy0 < p.ny, gx < p.nx && gy0 + 1 < p.ny};
+    const bool edge = x0 == 0 || y0 == 0 || x0 + FTX >= p.nx || y0 + FTY >= p.ny;
+    const float sg = sigma ? (float)sigma[sidx] : 1.f;
+    if (vb) {
+        const size_t off = (size_t)vb * p.nx * p.ny * p.nz;
+        U += off;
+        Y += off;
+    }
+    // U staging slots (one-point halo, clamped, ghost flags) and k^2 staging slots (two-point halo, the
+    // staggered mirror: -1 -> 0, -2 -> 1, n -> n-1, n+1 -> n-2; points beyond are never read)
+    unsigned sl[3] = {0u, 0u, 0u};
+    int kl[4] = {0, 0, 0, 0};
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const int q = tid + k * F2T;
+        if (q < FHALO) {
+            const int ly = q / FPX, lx = q - ly * FPX;
+            const int Xg = x0 + lx - 1, Yg = y0 + ly - 1;
+            const int Xc = min(max(Xg, 0), p.nx - 1), Yc = min(max(Yg, 0), p.ny - 1);
+            sl[k] = (unsigned)(Yc * p.nx + Xc) | (Xc != Xg ? 1u << 30 : 0u) | (Yc != Yg ? 1u << 31 : 0u);
+        }
+    }
+    auto mir = [](int i, int n) { i = min(i, n + 1); return i < 0 ? -i - 1 : (i >= n ? 2 * n - 1 - i : i); };
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int q = tid + k * F2T;
+        if (q < K2PTS) {
+            const int ly = q / K2X, lx = q - ly * K2X;
+            kl[k] = mir(y0 + ly - 2, p.ny) * p.nx + mir(x0 + lx - 2, p.nx);
+        }
+    }
+    const size_t plane = (size_t)p.nx * p.ny;
+    const int poff = gy0 * p.nx + gx;
+
+    auto issue = [&](int P, int Pk) {   // U plane P (if in the window) and k^2 plane Pk (if in the window)
+        if (P <= z1) {
+            F3Stage& S = ring[(P + FNS) % FNS];
+            const int Pc = min(max(P, 0), p.nz - 1);
+            const float2* Ub = U + (size_t)Pc * plane;
+#pragma unroll
+            for (int k = 0; k < 3; ++k)
+                if (tid + k * F2T < FHALO) cp8(&S.u[tid + k * F2T], Ub + (sl[k] & 0x3FFFFFFFu));
+        }
+        if (Pk >= z0 - 2 && Pk <= z1 + 1) {
+            float* K = kring + ((Pk + 2 * K2NS) % K2NS) * K2PTS;
+            const float* Kb = p.k2r + (size_t)mir(Pk, p.nz) * plane;
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                if (tid + k * F2T < K2PTS) cp4(&K[tid + k * F2T], Kb + kl[k]);
+        }
+        cp_commit();
+    };
+    auto kp = [&](int P) -> const float* { return kring + ((P + 2 * K2NS) % K2NS) * K2PTS; };
+
+    float2 cA[2], cX[2], cY[2], cZ[2], nA[2], nX[2], nY[2], nZ[2];
+    float gpx[2], gpy[2], gpz[2];   // the gradient fields of the previous plane
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+        cA[r] = cX[r] = cY[r] = cZ[r] = make_float2(0, 0);
+        nA[r] = nX[r] = nY[r] = nZ[r] = make_float2(0, 0);
+        gpx[r] = gpy[r] = gpz[r] = 0.f;
+    }
+    // first group: U(z0-1) and k^2 planes z0-2 .. z0+1; second: U(z0), k^2(z0+2); iteration P: U(P+2), k^2(P+4)
+    {
+        if (z0 - 1 <= z1) {
+            F3Stage& S = ring[(z0 - 1 + FNS) % FNS];
+            const int Pc = min(max(z0 - 1, 0), p.nz - 1);
+#pragma unroll
+            for (int k = 0; k < 3; ++k)
+                if (tid + k * F2T < FHALO) cp8(&S.u[tid + k * F2T], U + (size_t)Pc * plane + (sl[k] & 0x3FFFFFFFu));
+        }
+        for (int Pk = z0 - 2; Pk <= z0 + 1; ++Pk) {
+            if (Pk > z1 + 1) break;
+            float* K = kring + ((Pk + 2 * K2NS) % K2NS) * K2PTS;
+            const float* Kb = p.k2r + (size_t)mir(Pk, p.nz) * plane;
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                if (tid + k * F2T < K2PTS) cp4(&K[tid + k * F2T], Kb + kl[k]);
+        }
+        cp_commit();
+    }
+    issue(z0, z0 + 2);
+    const int c0 = (2 * ty + 2) * K2X + tx + 2;   // the k^2 tile index of this thread's first point
+    for (int P = z0 - 1; P <= z1; ++P) {
+        F3Stage& S = ring[(P + FNS) % FNS];
+        cp_wait1();
+        __syncthreads();          // U(P) and k^2 up to P+2 landed for everyone; planes P-2 (U), P-4 (k^2) free
+        const bool zghost = P < 0 || P >= p.nz;
+        if (edge || zghost) {
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                const int q = tid + k * F2T;
+                if (q < FHALO && ((sl[k] >> 30) || zghost)) {
+                    float2 u = S.u[q];
+                    if (sl[k] & (1u << 30)) u = f2mul(u, p.gx);
+                    if (sl[k] & (1u << 31)) u = f2mul(u, p.gy);
+                    if (zghost) u = f2mul(u, p.gz);
+                    S.u[q] = u;
+                }
+            }
+            __syncthreads();
+        }
+        issue(P + 2, P + 4);
+        const bool out_prev = P - 1 >= z0 && P - 1 < z1;
+        const bool do_mid = P >= z0 && P < z1;
+        // k^2 of plane P at the patch (clamped plane: a ghost plane takes its mirror plane's values)
+        const float* K0 = kp(min(max(P, z0 - 2), z1 + 1));
+        float2 u[4][3];
+        float kk[4][3];
+#pragma unroll
+        for (int b = 0; b < 4; ++b)
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                u[b][a] = S.u[(2 * ty + b) * FPX + tx + a];
+                kk[b][a] = K0[(2 * ty + b + 1) * K2X + tx + a + 1];
+            }
+        const float* Km1 = kp(P - 1);
+        const float* Kp1 = kp(P + 1);
+        const float* Km2 = kp(P - 2);
+        const float* Kp2 = kp(P + 2);
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            // the fields of plane P at point r (patch row r + 1 is the point's row; the +-1 neighbours in x
+            // and y and one +-2 neighbour in y are patch values)
+            float Gf = 0.f, gfx = 0.f, gfy = 0.f, gfz = 0.f;
+            if (do_mid) {
+                const int c = c0 + r * K2X;
+                const float kc0 = kk[r + 1][1];
+                const float xm1 = kk[r + 1][0], xp1 = kk[r + 1][2], ym1 = kk[r][1], yp1 = kk[r + 2][1];
+                const float xm2 = K0[c - 2], xp2 = K0[c + 2];
+                const float ym2 = r == 1 ? kk[0][1] : K0[c - 2 * K2X];
+                const float yp2 = r == 0 ? kk[3][1] : K0[c + 2 * K2X];
+                const float zm1 = Km1[c], zp1 = Kp1[c], zm2 = Km2[c], zp2 = Kp2[c];
+                gfx = (8.f * (xp1 - xm1) - (xp2 - xm2)) * p.i12h[0];
+                gfy = (8.f * (yp1 - ym1) - (yp2 - ym2)) * p.i12h[1];
+                gfz = (8.f * (zp1 - zm1) - (zp2 - zm2)) * p.i12h[2];
+                const float lap = (16.f * (xp1 + xm1) - (xp2 + xm2) - 30.f * kc0) * p.i12h2[0] +
+                                  (16.f * (yp1 + ym1) - (yp2 + ym2) - 30.f * kc0) * p.i12h2[1] +
+                                  (16.f * (zp1 + zm1) - (zp2 + zm2) - 30.f * kc0) * p.i12h2[2];
+                Gf = fmaf(-kc0, kc0, lap);
+            }
+            const float2 c = u[r + 1][1];
+            const float2 fx = f2add(u[r + 1][0], u[r + 1][2]), fy = f2add(u[r][1], u[r + 2][1]);
+            const float2 e = f2add(f2add(u[r][0], u[r][2]), f2add(u[r + 2][0], u[r + 2][2]));
+            // KU = k^2 U at the 3 x 3 patch of point r, formed where it is needed
+            const float2 kxm = f2scl(u[r + 1][0], kk[r + 1][0]), kxp = f2scl(u[r + 1][2], kk[r + 1][2]);
+            const float2 kym = f2scl(u[r][1], kk[r][1]), kyp = f2scl(u[r + 2][1], kk[r + 2][1]);
+            const float2 kc = f2scl(c, kk[r + 1][1]);
+            const float2 kf4 = f2add(f2add(kxm, kxp), f2add(kym, kyp));
+            const float2 kcs = f2fma(kk[r][0], u[r][0], f2fma(kk[r][2], u[r][2], f2fma(kk[r + 2][0], u[r + 2][0],
+                                                                                 f2scl(u[r + 2][2], kk[r + 2][2]))));
+            const float2 dkx = f2sub(kxp, kxm), dky = f2sub(kyp, kym);
+            const float ih = p.ihx;
+            float2 As = f2scl(f2fma(1.f / 30.f, e, f2fma(0.1f, f2add(fx, fy), f2scl(c, 7.f / 15.f))), ih);
+            As = f2fma(1.f / 90.f, f2sub(kf4, kc), As);
+            const float2 dx1 = f2sub(u[r + 1][2], u[r + 1][0]), dy1 = f2sub(u[r + 2][1], u[r][1]);
+            const float2 Xs = f2scl(dx1, 1.f / 6.f), Ys = f2scl(dy1, 1.f / 6.f);
+            const float2 Zs = f2add(f2fma(p.hh6, kc, c), f2scl(f2fma(-4.f, c, f2add(fx, fy)), 1.f / 6.f));
+            if (out_prev) {
+                const float2 A = f2add(cA[r], As);
+                float2 g = f2scl(f2add(cX[r], Xs), gpx[r]);
+                g = f2fma(gpy[r], f2add(cY[r], Ys), g);
+                g = f2fma(gpz[r], f2add(cZ[r], Zs), g);
+                const float2 v = f2fma(p.h_20, g, A);
+                if (act[r]) Y[(size_t)(P - 1) * plane + poff + r * p.nx] = f2scl(v, sg);
+            }
+            cA[r] = nA[r]; cX[r] = nX[r]; cY[r] = nY[r]; cZ[r] = nZ[r];
+            if (do_mid) {
+                float2 Am = f2scl(f2fma(-64.f / 15.f, c, f2fma(0.1f, e, f2scl(f2add(fx, fy), 7.f / 15.f))), ih);
+                Am = f2fma(14.f / 15.f, kc, Am);
+                Am = f2fma(1.f / 90.f, f2sub(kcs, kf4), Am);
+                Am = f2fma(p.h2_20 * Gf, c, Am);
+                const float2 tdx = f2sub(f2add(u[r][2], u[r + 2][2]), f2add(u[r][0], u[r + 2][0]));
+                const float2 tdy = f2sub(f2add(u[r + 2][0], u[r + 2][2]), f2add(u[r][0], u[r][2]));
+                const float2 Xm = f2add(f2fma(p.hh6, dkx, dx1), f2scl(f2fma(-4.f, dx1, tdx), 1.f / 6.f));
+                const float2 Ym = f2add(f2fma(p.hh6, dky, dy1), f2scl(f2fma(-4.f, dy1, tdy), 1.f / 6.f));
+                cA[r] = f2add(cA[r], Am); cX[r] = f2add(cX[r], Xm); cY[r] = f2add(cY[r], Ym);
+            }
+            nA[r] = As; nX[r] = Xs; nY[r] = Ys; nZ[r] = make_float2(-Zs.x, -Zs.y);
+            gpx[r] = gfx; gpy[r] = gfy; gpz[r] = gfz;
+        }
+    }
+}
+
 template <int ORDER, bool RK = false>
 size_t fast_smem() { return FNS * sizeof(FStage<ORDER, RK>); }
 
@@ -707,6 +919,8 @@ helm_status stencil_fast_prepare(helm_ctx* c) {
                                        (int)fast2_smem<6>()));
     HELM_CUDA_TRY(cudaFuncSetAttribute(stencil_fast2_kernel<4, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)fast2_smem<4>()));
+    HELM_CUDA_TRY(cudaFuncSetAttribute(stencil_fast3_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)F3_SMEM));
     HELM_CUDA_TRY(cudaFuncSetAttribute(stencil_tma_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        TLayout<4>::SMEM));
     HELM_CUDA_TRY(cudaFuncSetAttribute(stencil_tma_kernel<6>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -791,7 +1005,7 @@ helm_status stencil_real_prepare(helm_ctx* c, cudaStream_t s) {
                                             c->dk2_f[2], c->k2r, c->fr);
     HELM_CUDA_TRY(cudaGetLastError());
     c->realk = 1;
-    if (c->opt.order == 6) c->tune_stencil = 3;   // two rows per thread
+    if (c->opt.order == 6) c->tune_stencil = 3;   // two rows per thread (variant 4, the fields formed in the kernel, moves half the bytes but issues 40% more instructions: slower alone)
     return HELM_OK;
 }
 
@@ -799,8 +1013,9 @@ bool stencil_fast_supported(const helm_ctx* c) { return !c->colloc && (c->opt.or
 
 // Variants of the complex64 matvec a context can run: 0 = cp.async ring at four CTAs per SM, 1 = TMA ring
 // (even N_x, else the same as 0), 2 = cp.async ring at three CTAs per SM with more registers, 3 = two rows
-// per thread (real media; else the same as 2).
-int stencil_variants(const helm_ctx* c) { (void)c; return 4; }
+// per thread (real media; else the same as 2), 4 = two rows with the sixth-order fields formed in the kernel
+// (real media, order 6; else the same as 3).
+int stencil_variants(const helm_ctx* c) { (void)c; return 5; }
 
 helm_status launch_stencil_fast(helm_ctx* c, const float2* x, float2* y, const double* sigma, int sidx, cudaStream_t s,
                                 int nb) {
@@ -831,6 +1046,10 @@ helm_status launch_stencil_fast(helm_ctx* c, const float2* x, float2* y, const d
     p.fld[0] = c->G_f;
     for (int d = 0; d < 3; ++d) p.fld[d + 1] = c->dk2_f[d];
     p.nb = nb;
+    for (int d = 0; d < 3; ++d) {
+        p.i12h[d] = (float)(1.0 / (12.0 * c->h[d]));
+        p.i12h2[d] = (float)(1.0 / (12.0 * c->h[d] * c->h[d]));
+    }
     dim3 grid((c->nx + FTX - 1) / FTX, (c->ny + FTY - 1) / FTY, (c->nz + FZCH - 1) / FZCH * nb), block(FTX, FTY);
     if (c->sfast && c->tune_stencil == 1) {
         FastMaps* m = (FastMaps*)c->sfast;
@@ -852,7 +1071,13 @@ helm_status launch_stencil_fast(helm_ctx* c, const float2* x, float2* y, const d
     if (c->realk) {
         p.k2r = c->k2r;
         p.fr = c->fr;
-        if (c->tune_stencil == 3) {   // two rows per thread
+        if (c->tune_stencil == 4 && c->opt.order == 6) {   // two rows per thread, fields formed in the kernel
+            const dim3 block2(FTX, FTY / 2);
+            stencil_fast3_kernel<4><<<grid, block2, F3_SMEM, s>>>(p, x, y, sigma, sidx);
+            HELM_CUDA_TRY(cudaGetLastError());
+            return HELM_OK;
+        }
+        if (c->tune_stencil >= 3) {   // two rows per thread
             const dim3 block2(FTX, FTY / 2);
             if (c->opt.order == 6) stencil_fast2_kernel<6, 4><<<grid, block2, fast2_smem<6>(), s>>>(p, x, y, sigma, sidx);
             else stencil_fast2_kernel<4, 4><<<grid, block2, fast2_smem<4>(), s>>>(p, x, y, sigma, sidx);
