@@ -146,6 +146,7 @@ struct helm_ctx {
     int zpiv_ready = 0;                     // shared-memory attribute of the pivot-recomputing z-solve set
     void* zck = nullptr;                    // pivot checkpoints of that z-solve ([block][line pair] float4)
     int zpiv_off = 0;                       // set while capturing launches that may run concurrently (batch lanes)
+    int zck_slot = 0;                       // first checkpoint slot of the z-solve launches being captured (batch plans)
     size_t zck_bytes = 0;
     int tune_zring = 2;                     // factorised z-solve: CTAs per SM of the L2-resident ring kernel (0 = one thread per line)
     int tune_ypers = 1;                     // y-pass: 1 persistent with double-buffered accumulators, 0 one tile per CTA

@@ -1290,6 +1290,7 @@ struct Group {
     float2* tmp = nullptr;          // nb vectors: the group's preconditioner scratch (lane r's own: vector r)
     double* sigma = nullptr;        // nb (m + 1)
     LaneDev* lt = nullptr;          // device table of the lanes' pointers
+    int slot = 0;                   // z-solve checkpoint slot of the group's first lane within its context
     cudaGraphConditionalHandle* hcyc = nullptr;   // device copy of the lanes' cycle-end handles
 };
 
@@ -1336,7 +1337,9 @@ helm_status build_group(cudaGraph_t G, Group& gr, std::vector<Lane>& lanes, int*
         st = capture_into(gb, nullptr, 0, s, [&]() {
             float2* save = c->tmp;
             c->tmp = gr.tmp;
+            c->zck_slot = gr.slot;
             helm_status e = precond_apply_nb(c, vj, zj, nb, gr.sigma, j, m + 1, s);
+            c->zck_slot = 0;
             c->tmp = save;
             if (e != HELM_OK) return e;
             if ((e = launch_stencil_f32_nb(c, zj, w, nb, s)) != HELM_OK) return e;
@@ -1418,13 +1421,27 @@ void plan_free(helm_batch* P) {
 // workspace of every group and lane, and the graph of one restart cycle of all lanes
 helm_status plan_build(helm_batch* P) {
     helm_status st;
-    // groups: runs of consecutive lanes of the same context
+    // groups: runs of consecutive lanes of the same context.  Below kGroupMinPoints a problem's right-hand
+    // sides run as independent single-lane groups instead: there the operators are latency-bound, and
+    // independent chains keep more of the GPU busy than shared launches save (measured on the 64 x 4 batch
+    // of 48^3 .. 160^3 problems).  Each lane has its own z-solve checkpoint slot within its context.
+    constexpr size_t kGroupMinPoints = (size_t)160 * 160 * 160;
+    std::vector<std::pair<helm_ctx*, int>> nlanes;   // lanes per context so far
     for (size_t i = 0; i < P->lanes.size();) {
         Group g;
         g.c = P->lanes[i].c;
         g.first = (int)i;
-        while (i < P->lanes.size() && P->lanes[i].c == g.c) ++i;
+        if (g.c->npts >= kGroupMinPoints) {
+            while (i < P->lanes.size() && P->lanes[i].c == g.c) ++i;
+        } else {
+            ++i;
+        }
         g.nb = (int)i - g.first;
+        size_t e = 0;
+        while (e < nlanes.size() && nlanes[e].first != g.c) ++e;
+        if (e == nlanes.size()) nlanes.push_back({g.c, 0});
+        g.slot = nlanes[e].second;   // the context's lanes before this group
+        nlanes[e].second += g.nb;
         P->groups.push_back(g);
     }
     for (Group& g : P->groups) {
@@ -1452,7 +1469,7 @@ helm_status plan_build(helm_batch* P) {
             lt[r] = LaneDev{k.V, k.part, k.H, k.cs, k.sn, k.g, k.sigma, k.coef, k.ctrl_d, ln.L_d};
         }
         HELM_CUDA_TRY(cudaMemcpy(g.lt, lt.data(), sizeof(LaneDev) * nb, cudaMemcpyHostToDevice));
-        if ((st = zsolve_reserve(c, nb)) != HELM_OK) return st;   // before capture
+        if ((st = zsolve_reserve(c, g.slot + nb)) != HELM_OK) return st;   // before capture
     }
     HELM_CUDA_TRY(cudaMalloc(&P->flags, sizeof(int) * P->lanes.size()));
     for (size_t i = 0; i < P->lanes.size(); ++i) P->lanes[i].more = P->flags + i;

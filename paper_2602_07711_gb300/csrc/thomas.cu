@@ -643,13 +643,16 @@ helm_status launch_zsolve(helm_ctx* c, const float2* in, float2* out, cudaStream
     if (in && c->nx % 2 == 0 && c->tune_zring && c->zring_sms > 0 && !c->zpiv_off) {
         // EigT: pivots recomputed from the shifts (the set-up factors' operations), checkpoints in a scratch
         // of the context (grown here outside stream capture; a capturing caller reserves it beforehand)
+        // (c->zck_slot: the first checkpoint slot of this launch; concurrent solves of one context in a batch
+        // plan each capture with their own slots)
         const int npairs = c->nx / 2 * c->ny * nb;
-        if (zsolve_ck_bytes(c, nb) > c->zck_bytes) {
+        const int slot = c->zck_slot;
+        if (zsolve_ck_bytes(c, slot + nb) > c->zck_bytes) {
             cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
             HELM_CUDA_TRY(cudaStreamIsCapturing(s, &cap));
             if (cap != cudaStreamCaptureStatusNone) return launch_zsolve_fact(c, c->zfac, in, out, nullptr, nullptr, s, nb);
             helm_status st;
-            if ((st = zsolve_reserve(c, nb)) != HELM_OK) return st;
+            if ((st = zsolve_reserve(c, slot + nb)) != HELM_OK) return st;
         }
         if (!c->zpiv_ready) {
             HELM_CUDA_TRY(cudaFuncSetAttribute(zsolve_piv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -664,7 +667,8 @@ helm_status launch_zsolve(helm_ctx* c, const float2* in, float2* out, cudaStream
         zsolve_piv_kernel<<<grid, ZRT, ZPIV_SMEM, s>>>(c->nx, c->ny, c->nz, (float)c->zeta[2],
                                                         make_float2((float)c->gam[2].x, (float)c->gam[2].y), c->dxs,
                                                         c->dys, c->cz, reinterpret_cast<const float4*>(in),
-                                                        reinterpret_cast<float4*>(out), reinterpret_cast<float4*>(c->zck),
+                                                        reinterpret_cast<float4*>(out),
+                                                        reinterpret_cast<float4*>(c->zck) + (size_t)slot * zsolve_ck_bytes(c, 1) / sizeof(float4),
                                                         nb);
         prof_end(c, s);
         HELM_CUDA_TRY(cudaGetLastError());
