@@ -202,6 +202,11 @@ helm_status helm_get_eig(helm_ctx* ctx, int axis, void* D, void* V, void* Vinv);
  *   b     complex128 right-hand side F (from helm_build_rhs), host or device.
  *   x     complex128, host or device; on entry x^0, on exit the iterate (also on NOT_CONVERGED).
  *   info  filled on return (may be NULL).
+ * Host buffers: page-locked host memory that is mapped into the device address space (cudaHostAlloc, or
+ * cudaHostRegister with mapping; the default for page-locked memory under unified addressing) is read and
+ * written by the kernels directly over the host link, without staging copies; any other host memory is
+ * copied to device buffers of the context and back.  The caller must not touch b or x until the call
+ * returns.
  * Krylov vectors are complex64; inner products accumulate in compensated FP32 per thread and FP64 across
  * threads; the Hessenberg matrix and Givens rotations are FP64 on the GPU; x accumulates in double-float
  * (~44 bits); the stopping test uses the true residual in double-float.  A restart cycle ends after m

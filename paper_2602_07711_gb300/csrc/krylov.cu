@@ -562,6 +562,14 @@ bool is_device_ptr(const void* p) {
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+// The device address of page-locked, mapped host memory (cudaHostAlloc / registered), else NULL: kernels
+// then read the caller's vector over the host link directly instead of staging it with a copy first.
+void* mapped_host_ptr(const void* p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) { cudaGetLastError(); return nullptr; }
+    return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
 void free_work(KrylovWork* k) {
     if (!k->shared) { cudaFree(k->V); cudaFree(k->Z); cudaFree(k->sigma); }
     cudaFree(k->H); cudaFree(k->cs); cudaFree(k->sn);
@@ -726,15 +734,19 @@ helm_status gmres_run(helm_ctx* c, const double2* b_in, double2* x_in, helm_solv
     if ((st = ensure_slots(k)) != HELM_OK) return st;
     const size_t npts = c->npts, vbytes = npts * sizeof(double2);
     const int m = c->opt.restart, flex = c->opt.flexible;
+    // device memory is used in place; mapped page-locked host memory is read (b, x0) and written (x) by the
+    // conversion kernels through its device address; other host memory is staged by copies
     const bool xdev = is_device_ptr(x_in), bdev = is_device_ptr(b_in);
-    double2* x = x_in;
-    const double2* b = b_in;
-    if (!xdev) {
+    double2* const xmap = xdev ? nullptr : (double2*)mapped_host_ptr(x_in);
+    const double2* const bmap = bdev ? nullptr : (const double2*)mapped_host_ptr(b_in);
+    double2* x = xdev ? x_in : xmap;
+    const double2* b = bdev ? b_in : bmap;
+    if (!x) {
         if (!k->xbuf) HELM_CUDA_TRY(cudaMalloc(&k->xbuf, vbytes));
         HELM_CUDA_TRY(cudaMemcpyAsync(k->xbuf, x_in, vbytes, cudaMemcpyHostToDevice, s));
         x = k->xbuf;
     }
-    if (!bdev) {
+    if (!b) {
         if (!k->bbuf) HELM_CUDA_TRY(cudaMalloc(&k->bbuf, vbytes));
         HELM_CUDA_TRY(cudaMemcpyAsync(k->bbuf, b_in, vbytes, cudaMemcpyHostToDevice, s));
         b = k->bbuf;
@@ -849,7 +861,7 @@ helm_status gmres_run(helm_ctx* c, const double2* b_in, double2* x_in, helm_solv
     unsigned dstat = 0;
     from_df_kernel<<<NB, NT, 0, s>>>(k->xdf, x, npts);
     HELM_CUDA_TRY(cudaMemcpyAsync(&dstat, c->status_d, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
-    if (!xdev) HELM_CUDA_TRY(cudaMemcpyAsync(x_in, x, vbytes, cudaMemcpyDeviceToHost, s));
+    if (!xdev && !xmap) HELM_CUDA_TRY(cudaMemcpyAsync(x_in, x, vbytes, cudaMemcpyDeviceToHost, s));
     HELM_CUDA_TRY(cudaStreamSynchronize(s));
     if (result == HELM_OK && (dstat & HELM_DEV_PIVOT)) result = HELM_ERR_PIVOT;
     if (dstat & HELM_DEV_WAIT) result = HELM_ERR_ITER_LIMIT;
