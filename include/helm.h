@@ -248,8 +248,8 @@ helm_status helm_batch_run(helm_batch* batch, helm_solve_info* infos, void* stre
 void helm_batch_destroy(helm_batch* batch);
 
 /* helm_autotune - time, on this context's grid, the candidate CTA counts of the Arnoldi update and combine
- * kernels, the variants of the complex64 matvec (0: cp.async plane ring at four CTAs per SM, 1: TMA plane
- * ring, 2: cp.async ring at three CTAs per SM) and of the inner-product kernel (0: groups of eight, 1/2:
+ * kernels, the variants of the complex64 matvec (see helm_set_matvec_variant) and of the inner-product
+ * kernel (0: groups of eight, 1/2:
  * software-pipelined groups of four/eight); in TF32 contexts the tensor-core transform passes (persistent
  * with double-buffered accumulators, or one tile per CTA), timed on a preconditioner application; in EigT
  * contexts with even N_x the factorised z-solve (the L2-resident kernel at 1-3 CTAs per SM, or one thread
@@ -368,6 +368,17 @@ helm_status helm_attach_net(helm_ctx* ctx, helm_net* net);
  * stays usable.  A diagnosis and test hook: a limit of a few polls makes the waits run out on purpose.
  * The paper has no counterpart.  Errors: HELM_ERR_ARG (NULL context, negative limit). */
 helm_status helm_set_wait_limit(helm_ctx* ctx, long long polls);
+
+/* helm_set_matvec_variant - pin the kernel of the context's complex64 matvec (staggered grids of order 4
+ * or 6; other contexts use the general stencil kernel whatever is set):
+ *   0  cp.async plane ring, one output per thread, four CTAs per SM
+ *   1  TMA plane ring (even N_x; else as 0)
+ *   2  cp.async plane ring, three CTAs per SM (the default for complex k^2)
+ *   3  two outputs per thread, k^2 U in registers (real k^2; the default for a real medium; else as 2)
+ *   4  as 3 with the sixth-order fields formed from a two-point-halo k^2 ring (real k^2, order 6; else as 3)
+ * All compute the same operator (Eqs. scheme4/scheme6) in complex64; they differ in speed and bytes moved.
+ * helm_autotune overrides the choice with the fastest.  Errors: HELM_ERR_ARG (NULL, out of range). */
+helm_status helm_set_matvec_variant(helm_ctx* ctx, int variant);
 
 /* helm_destroy - free the context and its device workspace (NULL is a no-op). */
 void helm_destroy(helm_ctx* ctx);

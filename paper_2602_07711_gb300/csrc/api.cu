@@ -251,6 +251,12 @@ helm_status helm_set_wait_limit(helm_ctx* c, long long polls) {
     return HELM_OK;
 }
 
+helm_status helm_set_matvec_variant(helm_ctx* c, int variant) {
+    if (!c || variant < 0 || variant >= stencil_variants(c)) return HELM_ERR_ARG;
+    c->tune_stencil = variant;
+    return HELM_OK;
+}
+
 void helm_destroy(helm_ctx* c) { free_ctx(c); }
 
 }  // extern "C"

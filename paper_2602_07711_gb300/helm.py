@@ -81,6 +81,7 @@ _SIGS = {
     "helm_residual_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_double),
                                         C.POINTER(C.c_double), C.c_void_p]),
     "helm_set_wait_limit": (C.c_int, [C.c_void_p, C.c_longlong]),
+    "helm_set_matvec_variant": (C.c_int, [C.c_void_p, C.c_int]),
     "helm_profile": (C.c_int, [C.c_void_p, C.c_int]),
     "helm_profile_classes": (C.c_int, [C.c_void_p, C.c_uint]),
     "helm_profile_read": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int]),
@@ -278,6 +279,10 @@ def helm_residual_noalloc(ctx, b, x, r, stream=None):
 
 def helm_set_wait_limit(ctx, polls):
     _check(lib().helm_set_wait_limit(ctx, int(polls)), "helm_set_wait_limit")
+
+
+def helm_set_matvec_variant(ctx, variant):
+    _check(lib().helm_set_matvec_variant(ctx, int(variant)), "helm_set_matvec_variant")
 
 
 def helm_destroy(ctx):
@@ -499,6 +504,10 @@ class Solver:
     def set_wait_limit(self, polls):
         """Bound of the context's mbarrier waits in polls (0 = default); a diagnosis and test hook."""
         helm_set_wait_limit(self.ctx, polls)
+
+    def set_matvec_variant(self, variant):
+        """Pin the complex64 matvec kernel (0-4, include/helm.h); helm_autotune would pick the fastest."""
+        helm_set_matvec_variant(self.ctx, variant)
 
     def solve(self, b, x0=None, stream=None, check=True):
         """x such that A x = b (b complex128 on the device or in host memory)."""

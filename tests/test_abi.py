@@ -75,6 +75,7 @@ def test_setup_checks_the_precision_and_the_wait_limit_without_gpu_work(libpath)
                             ctypes.byref(ctx)) == 1
         assert not ctx.value
     assert L.helm_set_wait_limit(None, 5) == 1
+    assert L.helm_set_matvec_variant(None, 0) == 1
 
 
 def test_closure_entry_points_reject_null_contexts_without_gpu_work(libpath):

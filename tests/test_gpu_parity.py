@@ -76,6 +76,28 @@ def test_apply_A_matches_oracle(order, case):
 
 
 @pytest.mark.parametrize("order", [4, 6])
+@pytest.mark.parametrize("real", [False, True])
+def test_every_matvec_variant_matches_oracle(order, real):
+    """helm_set_matvec_variant 0-4 (cp.async at four or three CTAs per SM, TMA ring, two outputs per thread,
+    two outputs with the order-6 fields formed in the kernel) on a complex and on a real medium (the real
+    forms stage k^2 as float; on a complex medium variants 3 and 4 fall back), at two ragged sizes."""
+    for n, L in (((40, 36, 33), (1.0, 0.9, 0.825)), ((70, 18, 66), (70 / 70, 18 / 70, 66 / 70))):
+        g, k2, k0 = _medium(n, L)
+        if real:
+            k2 = k2.real + 0j
+        S = Solver(n, k2, k0, order=order, L=L)
+        x = _rand(g.shape, 3)
+        ref = Operator(g, k2, k0, order)(x)
+        for v in range(5):
+            S.set_matvec_variant(v)
+            y64 = S.apply_A(_dev(x, torch.complex64)).cpu().numpy()
+            assert _rel(y64, ref) < 2e-6, (n, v)
+        with pytest.raises(Exception):
+            S.set_matvec_variant(5)
+        S.close()
+
+
+@pytest.mark.parametrize("order", [4, 6])
 def test_build_rhs_matches_oracle(order):
     n, L = (40, 36, 33), (1.0, 0.9, 0.825)
     g, k2, k0 = _medium(n, L)
