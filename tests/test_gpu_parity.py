@@ -8,7 +8,7 @@ Tolerances (relative, max-norm over the output unless stated):
   complex64 z-solve / preconditioner (FP32)                     per case, about 3x the measured error
                                                                (long z-lines amplify rounding: 300 planes
                                                                measured 6.5e-5 against 2.9e-6 at 33)
-  GMRES solution at rtol 1e-6 vs oracle solved to 1e-12         1e-5 in the relative 2-norm (the benchmark spec)
+  GMRES solution at rtol 1e-6 vs oracle solved to 1e-12         1e-5 in the relative 2-norm (the accuracy target)
 Sizes span several tiles plus ragged tails (x not a multiple of 32, y not of 8, z not of 32).
 """
 import math
