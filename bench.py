@@ -24,7 +24,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "time-to-rtol 1e-6 (s) & Mpts·iter/s at n=256³; mixed/learned vs plain EigT"
 UNIT = "Mpts·iter/s"
-PREC_NAMES = {"fp32": 0, "tf32": 1, "tf32x3": 2}
+PREC_NAMES = {"fp32": 0, "tf32": 1, "tf32x3": 2, "bf16": 3, "fp16": 4}
 CLASSES = ["stencil", "xpass", "ypass", "zsolve", "dots", "update", "small", "combine", "residual", "other",
            "learned"]
 
@@ -112,10 +112,11 @@ class ClockSampler:
 
 
 # ---- per-class algorithmic work -----------------------------------------------------------------
-def algorithmic(n, order, cycles_iters, real_medium=False):
+def algorithmic(n, order, cycles_iters, real_medium=False, precision="tf32"):
     """Bytes (and flops) the kernels of one solve must move, by class (per-point byte counts of each kernel class).
     A medium without attenuation takes the real-medium matvec: k^2 as float, the order-6 fields as one
-    real float4 per point."""
+    real float4 per point.  The BF16 chain: x class = complex64 -> BF16 conversion (12 B/pt) and forward
+    pass (8) + inverse pass (BF16 in, complex64 out: 12); y passes 8 B/pt each; z-solve y and x in BF16 (8)."""
     pts = n ** 3
     out = {}
     if real_medium:
@@ -124,9 +125,14 @@ def algorithmic(n, order, cycles_iters, real_medium=False):
         st_b = (24 if order == 4 else 56) * pts
     its = sum(cycles_iters)
     out["stencil"] = {"bytes": st_b * its, "launches": its}
-    out["xpass"] = {"bytes": 16 * pts * 2 * its, "flops": 8 * n * pts * 2 * its, "launches": 2 * its}
-    out["ypass"] = {"bytes": 16 * pts * 2 * its, "flops": 8 * n * pts * 2 * its, "launches": 2 * its}
-    out["zsolve"] = {"bytes": 24 * pts * its, "launches": its}      # y, multipliers m, x
+    if precision in ("bf16", "fp16"):
+        out["xpass"] = {"bytes": 32 * pts * its, "flops": 8 * n * pts * 2 * its, "launches": 2 * its}
+        out["ypass"] = {"bytes": 8 * pts * 2 * its, "flops": 8 * n * pts * 2 * its, "launches": 2 * its}
+        out["zsolve"] = {"bytes": 8 * pts * its, "launches": its}
+    else:
+        out["xpass"] = {"bytes": 16 * pts * 2 * its, "flops": 8 * n * pts * 2 * its, "launches": 2 * its}
+        out["ypass"] = {"bytes": 16 * pts * 2 * its, "flops": 8 * n * pts * 2 * its, "launches": 2 * its}
+        out["zsolve"] = {"bytes": 24 * pts * its, "launches": its}      # y, multipliers m, x
     db = ub = 0
     for k in cycles_iters:
         for j in range(k):
@@ -170,6 +176,11 @@ def roofline(prof_ms, prof_launch, alg, precision, order, n=None, variant=None):
         ach = a["flops"] / a["launches"] / avg_s / 1e12
         return {"kernel": cls, "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
                 "frac": ach / peak, "traffic": None, "peak_source": "152 SM x 128 FP32 lanes x 2 x max clock"}
+    if cls in ("xpass", "ypass") and precision in ("bf16", "fp16"):
+        peak = pk["bf16_tflops_sustained"]
+        ach = a["flops"] / a["launches"] / avg_s / 1e12
+        return {"kernel": cls, "bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                "frac": ach / peak, "traffic": None, "peak_source": src + " bf16 sustained"}
     if cls in ("xpass", "ypass"):
         peak = pk["bf16_tflops_sustained"] * (1.1 / 2.25)                      # TF32 = BF16 x nominal ratio
         ach = a["flops"] / a["launches"] / avg_s / 1e12
@@ -356,7 +367,7 @@ def run_ours(args, rank, world, local):
     # algorithmic bytes of the timed solves
     alg_tot = {}
     for i in infos:
-        for c, a in algorithmic(n, order, cycles_of(i, args.restart), real_medium).items():
+        for c, a in algorithmic(n, order, cycles_of(i, args.restart), real_medium, precision).items():
             t_ = alg_tot.setdefault(c, {"bytes": 0, "flops": 0, "launches": 0})
             for k_ in a:
                 t_[k_] += a[k_]

@@ -70,17 +70,30 @@ typedef struct {
  * limits as PFFT. */
 enum { HELM_PRECOND_NONE = 0, HELM_PRECOND_EIGT = 1, HELM_PRECOND_PFFT = 2, HELM_PRECOND_FFT2 = 3 };
 
-/* Arithmetic of the eigenvector transforms (EigT steps 2 and 4).  The stencil, the z-solves and the
- * Krylov vectors are complex64 in every mode; the Hessenberg/Givens update and the 1D eigensetup are FP64,
- * the true residual, the right-hand side and the iterate double-float (about 44 bits) in every mode.
+/* Arithmetic of the eigenvector transforms (EigT steps 2 and 4).  The stencil and the Krylov vectors are
+ * complex64 in every mode, the z-solves compute in FP32; the Hessenberg/Givens update and the 1D eigensetup
+ * are FP64, the true residual, the right-hand side and the iterate double-float (about 44 bits) in every
+ * mode.
  *   HELM_PREC_FP32    complex64 on the CUDA cores (FFMA), the "plain complex64" method
  *   HELM_PREC_TF32    tcgen05 tensor cores, TF32 operands, FP32 accumulation in TMEM (one product); needs
  *                     even N_x.  Relative error of a transform about 8e-4.
  *   HELM_PREC_TF32X3  split precision on the same tensor cores: every operand a = hi + lo with hi its TF32
  *                     rounding and lo the TF32 rounding of the remainder, products hi hi + hi lo + lo hi
  *                     (three MMAs) with FP32 accumulation: FP32-level transforms at three times the tensor
- *                     work; needs even N_x.                                                             */
-enum { HELM_PREC_FP32 = 0, HELM_PREC_TF32 = 1, HELM_PREC_TF32X3 = 2 };
+ *                     work; needs even N_x.
+ *   HELM_PREC_BF16    tcgen05 tensor cores with BF16 operands (round to nearest even, 8-bit significand)
+ *                     and FP32 accumulation in TMEM, and the grids between the passes of the EigT chain
+ *                     stored in BF16 (the z-solve reads and writes BF16 and computes in FP32): half the
+ *                     bytes of the TF32 chain and twice its MMA rate; relative error of the whole
+ *                     preconditioner about 1e-2.  EigT only (the PFFT and helm_precond_step passes run in
+ *                     TF32); needs N_x a multiple of 4; single solves (helm_gmres_solve_batched returns
+ *                     HELM_ERR_UNSUPPORTED for such contexts).
+ *   HELM_PREC_FP16    the same chain with FP16 operands and grids (TF32's 11-bit significand, so about
+ *                     TF32's accuracy): every stored grid is scaled by a power of two fixed at set-up from
+ *                     bounds that rule out overflow for any input (spectral norms of the eigenvector
+ *                     matrices, kappa(V_z) / min |lambda| for the z-solves); the last pass undoes them.
+ *                     Same limits as BF16, and k0z2 (helm_setup) must be constant.                      */
+enum { HELM_PREC_FP32 = 0, HELM_PREC_TF32 = 1, HELM_PREC_TF32X3 = 2, HELM_PREC_BF16 = 3, HELM_PREC_FP16 = 4 };
 
 typedef struct {
     int order;       /* 2, 4 (Eq. scheme4, any h_x, h_y, h_z) or 6 (Eq. scheme6, needs h_x = h_y = h_z)  */

@@ -41,7 +41,7 @@ void free_ctx(helm_ctx* c) {
     prof_release(c);
     void* ps[] = {c->k2_d, c->k2_f, c->dk2_d[0], c->dk2_d[1], c->dk2_d[2], c->dk2_f[0], c->dk2_f[1], c->dk2_f[2],
                   c->G_d, c->G_f, c->Dx, c->Dy, c->Vx, c->Vxi, c->Vy, c->Vyi, c->XF, c->XI, c->YF, c->YI,
-                  c->dxs, c->dys, c->cz, c->tmp, c->status_d, c->k2_df, c->G_df, c->rhs_scratch, c->zfac, c->zck};
+                  c->dxs, c->dys, c->cz, c->tmp, c->status_d, c->k2_df, c->G_df, c->rhs_scratch, c->zfac, c->zck, c->h16n};
     for (void* p : ps) if (p) cudaFree(p);
     delete c;
 }
@@ -80,7 +80,7 @@ helm_status helm_setup(const helm_grid* grid, const void* k2, double k0, const d
     if (!(grid->lx > 0 && grid->ly > 0 && grid->lz > 0)) return HELM_ERR_ARG;
     if (opt->order != 2 && opt->order != 4 && opt->order != 6) return HELM_ERR_ARG;
     if (opt->restart < 1 || opt->restart > 64 || opt->max_iter < 1 || !(opt->rtol > 0)) return HELM_ERR_ARG;
-    if (opt->precond < 0 || opt->precond > 3 || opt->precision < 0 || opt->precision > 2) return HELM_ERR_ARG;
+    if (opt->precond < 0 || opt->precond > 3 || opt->precision < 0 || opt->precision > 4) return HELM_ERR_ARG;
     const int colloc = grid->staggered ? 0 : 1;
     // the Krylov kernels move two points per 16-byte access: the point count must be even
     if (((size_t)grid->nx * grid->ny * grid->nz) % 2 != 0) return HELM_ERR_UNSUPPORTED;
@@ -134,6 +134,7 @@ helm_status helm_setup(const helm_grid* grid, const void* k2, double k0, const d
     TRY(launch_derived_fields(c, s));
     TRY(stencil_fast_prepare(c));
     TRY(stencil_real_prepare(c, s));
+    TRY(residual_real_prepare(c, s));
     // eigen set-up
     TRY(dalloc(&c->Dx, c->nx)); TRY(dalloc(&c->Dy, c->ny));
     TRY(dalloc(&c->Vx, (size_t)c->nx * c->nx)); TRY(dalloc(&c->Vxi, (size_t)c->nx * c->nx));
@@ -156,6 +157,10 @@ helm_status helm_setup(const helm_grid* grid, const void* k2, double k0, const d
     }
     if (opt->precision != HELM_PREC_FP32) {
         if (c->nx % 2 != 0) { free_ctx(c); return HELM_ERR_UNSUPPORTED; }
+        if (opt->precision == HELM_PREC_FP16 && k0z2) {   // the FP16 stage bounds assume a constant k0 in z
+            for (int l = 1; l < c->nz; ++l)
+                if (k0z2[l] != k0z2[0]) { free_ctx(c); return HELM_ERR_UNSUPPORTED; }
+        }
         TRY(tc_prepare(c, s));
     }
     if (opt->precond != HELM_PRECOND_NONE) TRY(zsolve_factor(c, s));

@@ -133,7 +133,12 @@ struct helm_ctx {
     void* pfft = nullptr;                   // PFFT tables and scratch (pfft.cu)
     float* k2r = nullptr;                   // real k^2 and real (G, g_x, g_y, g_z) for media without attenuation
     float4* fr = nullptr;
+    float2* rkq = nullptr;                  // sixth-order residual, real media: k^2 h^2 / 3 (double-float)
+    float4* rg4 = nullptr;                  // ... (3/2) h^4 G (double-float), (3/2) h^3 (g_x, g_y) (FP32)
+    float* rgz = nullptr;                   // ... (3/2) h^3 g_z
     int realk = 0;
+    float h16s[6] = {1.f, 1.f, 1.f, 1.f, 1.f, 1.f};   // FP16 chain: input, four stage scales, final factor
+    double* h16n = nullptr;                 // FP16 chain: 1/||r||, ||r|| and partial sums (helm_apply_precond)
     void* sfast = nullptr;                  // TMA descriptors of the stencil's fixed operands (stencil_fast.cu)
     // scratch
     float2* tmp = nullptr;                  // one complex64 grid vector
@@ -183,6 +188,8 @@ helm_status stencil_real_prepare(helm_ctx* c, cudaStream_t s);
 void stencil_fast_release(helm_ctx* c);
 int stencil_variants(const helm_ctx* c);
 helm_status residual_fast_prepare();
+helm_status residual_real_prepare(helm_ctx* c, cudaStream_t s);
+void residual_real_release(helm_ctx* c);
 helm_status launch_residual_fast(helm_ctx* c, const float4* x, const float4* F, float2* r, double* part,
                                  cudaStream_t s);   // same grid (and partial count) as the generic residual
 bool stencil_fast_supported(const helm_ctx* c);
@@ -201,6 +208,12 @@ helm_status tc_prepare(helm_ctx* c, cudaStream_t s);
 helm_status tc_xpass(helm_ctx* c, int inverse, const float2* in, float2* out, float alpha, const double* alpha_dev,
                      int aidx, cudaStream_t s, int nb = 1, int astride = 0);
 helm_status tc_ypass(helm_ctx* c, int inverse, const float2* in, float2* out, cudaStream_t s, int nb = 1);
+helm_status tc_xpass_h16(helm_ctx* c, int inverse, const void* in, void* out, int out_h16, float alpha,
+                         const double* alpha_dev, int aidx, cudaStream_t s, int nb = 1, int astride = 0);
+helm_status tc_ypass_h16(helm_ctx* c, int inverse, const void* in, void* out, float alpha, cudaStream_t s, int nb = 1);
+helm_status h16_scales(helm_ctx* c, cudaStream_t s);
+helm_status launch_zsolve_h16(helm_ctx* c, const void* in, void* out, float4* dscr, float oscale, cudaStream_t s,
+                              int nb = 1);
 // operand sets of tc_xpass/tc_ypass (`inverse`): 0/1 EigT forward/inverse, 2/3 PFFT sine forward/inverse
 helm_status tc_prepare_sine(helm_ctx* c, const double2* Sx, const double2* Sy, const double2* SxT, const double2* SyT,
                             cudaStream_t s);

@@ -114,6 +114,46 @@ __device__ __forceinline__ cdf cdf_mul_f2(cdf a, float2 b) {
     Y.lo.x = -Y.lo.x;
     return cdf_add(X, Y);
 }
+// ---- unnormalised pairs: compensated sums of many double-float terms --------------------------
+// Within one long sum the renormalisation after every step can be left out: the high parts are summed in
+// FP32 with the exact two-sum error of every addition (and the exact FMA error of every product), and those
+// errors, together with the terms' low parts, are summed in a second FP32 accumulator.  hi + lo is the
+// value (lo is not bounded by ulp(hi)); the absolute error stays near (number of terms) x 2^-48 x the sum
+// of the terms' magnitudes, the behaviour of the compensated summation and dot product of Ogita, Rump and
+// Oishi ("Accurate sum and dot product", SIAM J. Sci. Comput. 26, 2005).  Used by the sixth-order residual,
+// whose ~40 additions per point would otherwise each end in a quick two-sum.
+__device__ __forceinline__ cdf cp_add(cdf a, cdf b) {
+    const float2 s = add2(a.hi, b.hi);
+    const float2 bb = sub2(s, a.hi);
+    const float2 t = add2(sub2(a.hi, sub2(s, bb)), sub2(b.hi, bb));
+    return cdf{s, add2(add2(a.lo, b.lo), t)};
+}
+__device__ __forceinline__ cdf cp_sub(cdf a, cdf b) {
+    const float2 s = sub2(a.hi, b.hi);
+    const float2 bb = sub2(s, a.hi);
+    const float2 t = sub2(sub2(a.hi, sub2(s, bb)), add2(b.hi, bb));   // (a - (s - bb)) + (-b - bb)
+    return cdf{s, add2(sub2(a.lo, b.lo), t)};
+}
+// a + b with b a plain complex64 value
+__device__ __forceinline__ cdf cp_add_f2(cdf a, float2 b) {
+    const float2 s = add2(a.hi, b);
+    const float2 bb = sub2(s, a.hi);
+    const float2 t = add2(sub2(a.hi, sub2(s, bb)), sub2(b, bb));
+    return cdf{s, add2(a.lo, t)};
+}
+// a times the float k: the high parts' product with its exact FMA error, the low parts times k
+__device__ __forceinline__ cdf cp_mulk(cdf a, float k) {
+    const float2 p = mul2(a.hi, bc2(k));
+    const float2 t = make_float2(fmaf(a.hi.x, k, -p.x), fmaf(a.hi.y, k, -p.y));
+    return cdf{p, fma2(a.lo, bc2(k), t)};
+}
+// a times the double-float scalar s
+__device__ __forceinline__ cdf cp_mul(cdf a, df s) {
+    const float2 p = mul2(a.hi, bc2(s.hi));
+    float2 t = make_float2(fmaf(a.hi.x, s.hi, -p.x), fmaf(a.hi.y, s.hi, -p.y));
+    t = fma2(a.hi, bc2(s.lo), t);
+    return cdf{p, fma2(a.lo, bc2(s.hi), t)};
+}
 // ---- FP64 <-> double-float on the bit patterns --------------------------------------------------
 // GB300's FP64 and FP64-conversion pipes run at a small fraction of its FP32 and integer rate (a stream of
 // double -> double-float conversions ran at a third of HBM bandwidth on them), so the conversions of the

@@ -25,6 +25,7 @@
 // (the end entries weigh one half).  The straight continuation path is reliable for |gamma| <= 2
 // (k0 h <= 1, at least six points per wavelength); beyond that the check reports HELM_ERR_EIG.
 #include "common.cuh"
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -224,5 +225,118 @@ helm_status run_eig_setup(helm_ctx* c, cudaStream_t s) {
                                                                           nullptr, c->YF, c->YI, c->dys);
         HELM_CUDA_TRY(cudaGetLastError());
     }
+    return HELM_OK;
+}
+
+// ---- stage scales of the FP16 transform chain (HELM_PREC_FP16) ------------------------------------------
+// FP16 keeps TF32's 11-bit significand but overflows above 65504, so every grid the chain stores is scaled by a
+// power of two chosen here, at set-up, from bounds that hold for any input: the chain's input is the unit
+// vector times 2^12 (the conversion applies the Arnoldi normalisation, or 1 / ||r||), and the Frobenius norm
+// of each stage's output is at most the spectral norm of its operator times that of its input.  The x-pass
+// applies V_x^-T (or V_x^T), the y-pass V_y^-1 (or V_y), row- and slice-wise, so their gains are the
+// largest singular values of those matrices; the z-systems T_ij = Lbar_z + s_ij I (constant k0) diagonalise
+// as V_z (D_z + s_ij) V_z^-1, so ||T_ij^-1|| <= kappa(V_z) / min_m |d_zm + s_ij|, with s_ij = a_x d_xi +
+// a_y d_yj + h_z^2 k0^2 - 2 (a_x + a_y).  The spectral norms come from 60 power iterations (which approach
+// them from below) and take a safety factor 1.5; each stage's output bound is then brought to at most 2^15
+// (the largest element of a grid is at most its Frobenius norm), and the last pass undoes the scales.
+namespace {
+double spec_norm_host(const std::vector<double2>& A, int n) {
+    std::vector<double> xr(n), xi(n), yr(n), yi(n);
+    for (int i = 0; i < n; ++i) { xr[i] = 1.0 + 0.37 * ((i * 7919) % 13); xi[i] = 0.11 * ((i * 104729) % 5); }
+    double sig = 0.0;
+    for (int it = 0; it < 60; ++it) {
+        double nn = 0.0;
+        for (int i = 0; i < n; ++i) nn += xr[i] * xr[i] + xi[i] * xi[i];
+        nn = std::sqrt(nn);
+        for (int i = 0; i < n; ++i) { xr[i] /= nn; xi[i] /= nn; }
+        for (int r = 0; r < n; ++r) {          // y = A x
+            double ar = 0.0, ai = 0.0;
+            for (int k = 0; k < n; ++k) {
+                const double2 a = A[(size_t)r * n + k];
+                ar += a.x * xr[k] - a.y * xi[k];
+                ai += a.x * xi[k] + a.y * xr[k];
+            }
+            yr[r] = ar; yi[r] = ai;
+        }
+        double ny = 0.0;
+        for (int r = 0; r < n; ++r) ny += yr[r] * yr[r] + yi[r] * yi[r];
+        sig = std::sqrt(ny);                    // ||A x|| for the unit x
+        for (int k = 0; k < n; ++k) { xr[k] = 0.0; xi[k] = 0.0; }
+        for (int r = 0; r < n; ++r)             // x = A^H y
+            for (int k = 0; k < n; ++k) {
+                const double2 a = A[(size_t)r * n + k];
+                xr[k] += a.x * yr[r] + a.y * yi[r];
+                xi[k] += a.x * yi[r] - a.y * yr[r];
+            }
+    }
+    return sig;
+}
+std::vector<double2> to_host(const double2* d, size_t n) {
+    std::vector<double2> h(n);
+    if (cudaMemcpy(h.data(), d, n * sizeof(double2), cudaMemcpyDeviceToHost) != cudaSuccess) h.clear();
+    return h;
+}
+float pow2_scale(double bound) {   // 2^e with bound * 2^e <= 2^15
+    const int e = 15 - (int)std::ceil(std::log2(bound));
+    return std::ldexp(1.0f, e);
+}
+}  // namespace
+
+helm_status h16_scales(helm_ctx* c, cudaStream_t s) {
+    HELM_CUDA_TRY(cudaStreamSynchronize(s));
+    const int nx = c->nx, ny = c->ny, nz = c->nz;
+    double2 *Dz = nullptr, *Vz = nullptr, *Vzi = nullptr;
+    unsigned long long* chk = nullptr;
+    if (cudaMalloc(&Dz, nz * sizeof(double2)) != cudaSuccess || cudaMalloc(&Vz, (size_t)nz * nz * sizeof(double2)) != cudaSuccess ||
+        cudaMalloc(&Vzi, (size_t)nz * nz * sizeof(double2)) != cudaSuccess ||
+        cudaMalloc(&chk, 2 * sizeof(unsigned long long)) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(Dz); cudaFree(Vz); cudaFree(Vzi); cudaFree(chk);
+        return HELM_ERR_NOMEM;
+    }
+    helm_status st = eig_one_axis(nz, c->gam[2], c->zeta[2], Dz, Vz, Vzi, chk, s);
+    if (st == HELM_OK && cudaStreamSynchronize(s) != cudaSuccess) st = HELM_ERR_CUDA;
+    std::vector<double2> hVxi, hVyi, hVy, hVz, hVzi, hDx, hDy, hDz;
+    if (st == HELM_OK) {
+        hVxi = to_host(c->Vxi, (size_t)nx * nx);
+        hVyi = to_host(c->Vyi, (size_t)ny * ny); hVy = to_host(c->Vy, (size_t)ny * ny);
+        hVz = to_host(Vz, (size_t)nz * nz); hVzi = to_host(Vzi, (size_t)nz * nz);
+        hDx = to_host(c->Dx, nx); hDy = to_host(c->Dy, ny); hDz = to_host(Dz, nz);
+        if (hVxi.empty() || hVyi.empty() || hVy.empty() || hVz.empty() || hVzi.empty() || hDx.empty() ||
+            hDy.empty() || hDz.empty())
+            st = HELM_ERR_CUDA;
+    }
+    cudaFree(Dz); cudaFree(Vz); cudaFree(Vzi); cudaFree(chk);
+    if (st != HELM_OK) return st;
+    const double safety = 1.5;
+    const double sxi = safety * spec_norm_host(hVxi, nx), syi = safety * spec_norm_host(hVyi, ny);
+    const double sy = safety * spec_norm_host(hVy, ny);
+    const double kz = safety * spec_norm_host(hVz, nz) * safety * spec_norm_host(hVzi, nz);
+    const double hz2 = c->h[2] * c->h[2];
+    const double base = hz2 * c->k0 * c->k0 - 2.0 * (c->ax + c->ay);
+    double lmin = 1e300;
+    for (int i = 0; i < nx; ++i)
+        for (int j = 0; j < ny; ++j) {
+            const double sr = c->ax * hDx[i].x + c->ay * hDy[j].x + base, si = c->ax * hDx[i].y + c->ay * hDy[j].y;
+            for (int m = 0; m < nz; ++m) {
+                const double lr = sr + hDz[m].x, li = si + hDz[m].y;
+                lmin = std::min(lmin, lr * lr + li * li);
+            }
+        }
+    lmin = std::sqrt(lmin);
+    if (!(lmin > 0.0) || !std::isfinite(sxi * syi * sy * kz)) return HELM_ERR_EIG;
+    const double gz = kz / lmin;
+    float sc[5];
+    sc[0] = 4096.f;
+    double F = 4096.0;   // Frobenius-norm bound of the stored grid after each stage
+    const double gain[4] = {sxi, syi, gz, sy};
+    for (int k = 0; k < 4; ++k) {
+        sc[k + 1] = pow2_scale(gain[k] * F);
+        F = gain[k] * F * sc[k + 1];
+    }
+    double prod = 1.0;
+    for (int k = 0; k < 5; ++k) prod *= sc[k];
+    for (int k = 0; k < 5; ++k) c->h16s[k] = sc[k];
+    c->h16s[5] = (float)(hz2 / prod);
     return HELM_OK;
 }

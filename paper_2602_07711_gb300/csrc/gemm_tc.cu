@@ -24,6 +24,8 @@
 #include "common.cuh"
 #include <cuda.h>
 #include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 namespace {
 
@@ -48,6 +50,13 @@ struct TcState {
     CUtensorMap mapBx256[4];   // the same operands in 256-row boxes (256-wide x-pass tiles)
     CUtensorMap mapWy[4];
     CUtensorMap mapBxl[4], mapBx256l[4], mapWyl[4];
+    // HELM_PREC_BF16 / HELM_PREC_FP16: the EigT operand sets 0/1 rounded to that type (h16 = 1 BF16, 2 FP16;
+    // row stride ldwb of the y-pass planes)
+    int h16 = 0;
+    int ldwb = 0;
+    uint16_t* Bxb[2] = {nullptr, nullptr};
+    uint16_t* Wyb[2] = {nullptr, nullptr};
+    CUtensorMap mapBxb[2], mapBxb256[2], mapWyb[2];
 };
 
 __device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -106,6 +115,33 @@ __device__ __forceinline__ void mma_tf32(uint32_t d, uint64_t a, uint64_t b, uin
     asm volatile(
         "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\ntcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
         "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+// instruction descriptor, kind::f16: D = F32 (1), A = B = BF16 (1) or F16 (0), majors, N >> 3, M >> 4
+// (H: 1 = BF16, 2 = FP16 operands)
+__host__ __device__ constexpr uint32_t idesc_h16(int H, int M, int N, int a_mn, int b_mn) {
+    return (1u << 4) | ((H == 1 ? 1u : 0u) << 7) | ((H == 1 ? 1u : 0u) << 10) | ((uint32_t)a_mn << 15) |
+           ((uint32_t)b_mn << 16) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+__device__ __forceinline__ void mma_f16kind(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\ntcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+template <int H>
+__device__ __forceinline__ void mma_op(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    if (H) mma_f16kind(d, a, b, idesc, acc);   // kind::f16; the operand type is in idesc
+    else mma_tf32(d, a, b, idesc, acc);
+}
+// two floats rounded to nearest even BF16 (H = 1) or FP16 (H = 2, clamped to the finite range), packed low
+// half first (memory order)
+template <int H>
+__device__ __forceinline__ uint32_t pack16(float lo, float hi) {
+    if (H == 2) {
+        const __half2 v = __floats2half2_rn(fminf(fmaxf(lo, -65504.f), 65504.f), fminf(fmaxf(hi, -65504.f), 65504.f));
+        return *reinterpret_cast<const uint32_t*>(&v);
+    }
+    const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<const uint32_t*>(&v);
 }
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
@@ -419,14 +455,19 @@ struct PersX {
 // their A rows in L2.
 // SPLIT: 3xTF32 with tmBl the remainder of the basis; 320 threads, warps 6-9 split the data tiles.
 // Stage layout: [A | B] (TF32), [A hi | A lo | B hi | B lo] (SPLIT).
-template <int BNT, bool SPLIT>
+// H: 16-bit operands, 1 = BF16, 2 = FP16 (kind::f16; a 128-byte swizzle row holds 64 of them, so a stage
+// carries twice the K depth of the TF32 form in the same bytes); OBF: the output rounded to that type
+// (row-major pairs).
+template <int BNT, bool SPLIT, int H = 0, bool OBF = false>
 __global__ void __launch_bounds__(SPLIT ? 320 : 192, 1)
 xpass_tc_pers_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-                     const __grid_constant__ CUtensorMap tmBl, float* __restrict__ out, int M, int N2, int K2,
+                     const __grid_constant__ CUtensorMap tmBl, void* __restrict__ outv, int M, int N2, int K2,
                      float alpha, const double* __restrict__ alpha_dev, int aidx, int rows_per, int astride,
                      unsigned* status, long wlim) {
     extern __shared__ uint8_t dsm[];
     constexpr int NS = PersX<BNT, SPLIT>::STAGES, BTILE = BNT * BK * 4, STAGE = PersX<BNT, SPLIT>::STAGE_BYTES;
+    constexpr int KE = H ? 2 * BK : BK;    // K elements per stage (128 bytes per operand row)
+    float* out = reinterpret_cast<float*>(outv);
     constexpr int AOFF_LO = TILE, BOFF = SPLIT ? 2 * TILE : TILE, BOFF_LO = BOFF + BTILE;
     __shared__ __align__(8) uint64_t full[NS], empty[NS], conv[NS], accf[2], acce[2], drainb;
     __shared__ int fail_any;
@@ -434,7 +475,7 @@ xpass_tc_pers_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_const
     const uint32_t raw = su32(dsm);
     const uint32_t base = (raw + 1023u) & ~1023u;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int nk = (K2 + BK - 1) / BK;
+    const int nk = (K2 + KE - 1) / KE;
     const int ntn = (N2 + BNT - 1) / BNT, ntm = (M + BM - 1) / BM, ntiles = ntn * ntm;
     float* epi = reinterpret_cast<float*>(dsm + (base - raw) + NS * STAGE);   // epilogue staging rows
     if (threadIdx.x == 0) {
@@ -471,16 +512,16 @@ xpass_tc_pers_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_const
                     if (!ok) break;
                     const uint32_t sa = base + s * STAGE, sb = sa + BOFF;
                     mbar_expect_tx(su32(&full[s]), SPLIT ? TILE + 2 * BTILE : STAGE);
-                    tma_2d(sa, &tmA, su32(&full[s]), kb * BK, m0);
-                    tma_2d(sb, &tmB, su32(&full[s]), kb * BK, n0);
-                    if (SPLIT) tma_2d(sa + BOFF_LO, &tmBl, su32(&full[s]), kb * BK, n0);
+                    tma_2d(sa, &tmA, su32(&full[s]), kb * KE, m0);
+                    tma_2d(sb, &tmB, su32(&full[s]), kb * KE, n0);
+                    if (SPLIT) tma_2d(sa + BOFF_LO, &tmBl, su32(&full[s]), kb * KE, n0);
                     ++issued;
                 }
             }
         }
     } else if (warp == 1) {
         if (lane == 0) {
-            const uint32_t idesc = idesc_tf32(BM, BNT, 0, 0);
+            const uint32_t idesc = H ? idesc_h16(H, BM, BNT, 0, 0) : idesc_tf32(BM, BNT, 0, 0);
             long it = 0;
             int lt = 0;
             for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++lt) {
@@ -505,7 +546,7 @@ xpass_tc_pers_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_const
                             mma_tf32(acc_t, ad, sdesc(sa + BOFF_LO + kk * 32, 16, 1024), idesc, 1u);
                             mma_tf32(acc_t, ad, bd, idesc, 1u);
                         } else {
-                            mma_tf32(acc_t, ad, bd, idesc, (kb | kk) ? 1u : 0u);
+                            mma_op<H>(acc_t, ad, bd, idesc, (kb | kk) ? 1u : 0u);
                         }
                     }
                     mma_commit(su32(&empty[s]));
@@ -534,6 +575,36 @@ xpass_tc_pers_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_const
                 uint32_t r[32];
                 TMEM_LD32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * BNT + c), r);
                 tmem_wait_ld();
+                if (OBF) {
+                    // the thread's 32 columns as 16 16-bit pairs (64 bytes) into its staging row, then 16-byte
+                    // pieces of four rows per instruction: 64-byte row segments in global memory
+                    uint32_t* su = reinterpret_cast<uint32_t*>(stg);
+#pragma unroll
+                    for (int v = 0; v < 16; v += 4)
+                        *reinterpret_cast<uint4*>(su + lane * XEPI_LD + v) =
+                            make_uint4(pack16<H>(al * __uint_as_float(r[2 * v]), al * __uint_as_float(r[2 * v + 1])),
+                                       pack16<H>(al * __uint_as_float(r[2 * v + 2]), al * __uint_as_float(r[2 * v + 3])),
+                                       pack16<H>(al * __uint_as_float(r[2 * v + 4]), al * __uint_as_float(r[2 * v + 5])),
+                                       pack16<H>(al * __uint_as_float(r[2 * v + 6]), al * __uint_as_float(r[2 * v + 7])));
+                    __syncwarp();
+                    uint16_t* ob = reinterpret_cast<uint16_t*>(outv);
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        const int rr = 8 * i + (lane >> 2), cc = 4 * (lane & 3);
+                        const int grow = rbase + rr, gcol = n0 + c + 2 * cc;
+                        const uint4 v = *reinterpret_cast<const uint4*>(su + rr * XEPI_LD + cc);
+                        if (grow < M && gcol < N2) {
+                            uint16_t* dst = ob + (size_t)grow * N2 + gcol;
+                            if (gcol + 8 <= N2) *reinterpret_cast<uint4*>(dst) = v;
+                            else {
+                                const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+                                for (int e = 0; e < 4 && gcol + 2 * e < N2; ++e) reinterpret_cast<uint32_t*>(dst)[e] = w[e];
+                            }
+                        }
+                    }
+                    __syncwarp();
+                    continue;
+                }
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
 #pragma unroll
@@ -611,21 +682,28 @@ struct PersY {
 // SPLIT: 3xTF32 with tmWl the remainder of W; 320 threads, warps 6-9 split the data tiles.
 // Stage layout: [Wr | Wi | D] (TF32), [Wr hi | Wi hi | D hi | Wr lo | Wi lo | D lo] (SPLIT); D is 4 boxes of
 // 32 K-rows x 128 bytes.
-template <bool SPLIT>
+// H: 16-bit operands and output (1 = BF16, 2 = FP16), the output scaled by alpha.  W (K-major) as in the
+// TF32 form with 64 K elements per 128-byte row;
+// the data tile is two boxes of 64 columns x 64 K-rows in the ordinary 128-byte swizzle (16-byte chunks),
+// the canonical MN-major layout of 16-bit operands: LBO = the next 64-column chunk (8 KiB), SBO = the next
+// 8-row K group (1 KiB), 2 KiB per MMA K-step of 16.
+template <bool SPLIT, int H = 0>
 __global__ void __launch_bounds__(SPLIT ? 320 : 192, 1)
 ypass_tc_pers_kernel(const __grid_constant__ CUtensorMap tmW, const __grid_constant__ CUtensorMap tmY,
-                     const __grid_constant__ CUtensorMap tmWl, float* __restrict__ out, int ny, int N2, int nz,
-                     unsigned* status, long wlim) {
+                     const __grid_constant__ CUtensorMap tmWl, void* __restrict__ outv, int ny, int N2, int nz,
+                     unsigned* status, long wlim, float alpha = 1.f) {
     extern __shared__ uint8_t dsm[];
     constexpr int YPS = PersY<SPLIT>::STAGES, STAGE = PersY<SPLIT>::STAGE_BYTES;
     constexpr int WLO = 3 * TILE, DLO = 5 * TILE;
+    constexpr int KE = H ? 2 * BK : BK;
+    float* out = reinterpret_cast<float*>(outv);
     __shared__ __align__(8) uint64_t full[YPS], empty[YPS], conv[YPS], accf[2], acce[2], drainb;
     __shared__ int fail_any;
     __shared__ uint32_t tslot;
     const uint32_t raw = su32(dsm);
     const uint32_t base = (raw + 1023u) & ~1023u;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int nk = (ny + BK - 1) / BK;
+    const int nk = (ny + KE - 1) / KE;
     const int ntm = (ny + BM - 1) / BM, ntn = (N2 + BN - 1) / BN, ntiles = ntm * ntn * nz;
     float* epi = reinterpret_cast<float*>(dsm + (base - raw) + YPS * STAGE);   // epilogue staging rows
     if (threadIdx.x == 0) {
@@ -663,21 +741,26 @@ ypass_tc_pers_kernel(const __grid_constant__ CUtensorMap tmW, const __grid_const
                     if (!ok) break;
                     const uint32_t sw = base + s * STAGE, sb = sw + 2 * TILE;
                     mbar_expect_tx(su32(&full[s]), SPLIT ? 5 * TILE : STAGE);
-                    tma_3d(sw, &tmW, su32(&full[s]), kb * BK, m0, 0);
-                    tma_3d(sw + TILE, &tmW, su32(&full[s]), kb * BK, m0, 1);
+                    tma_3d(sw, &tmW, su32(&full[s]), kb * KE, m0, 0);
+                    tma_3d(sw + TILE, &tmW, su32(&full[s]), kb * KE, m0, 1);
                     if (SPLIT) {
                         tma_3d(sw + WLO, &tmWl, su32(&full[s]), kb * BK, m0, 0);
                         tma_3d(sw + WLO + TILE, &tmWl, su32(&full[s]), kb * BK, m0, 1);
                     }
+                    if (H) {
 #pragma unroll
-                    for (int q = 0; q < BN / 32; ++q) tma_3d(sb + q * 4096, &tmY, su32(&full[s]), n0 + 32 * q, kb * BK, l);
+                        for (int q = 0; q < BN / 64; ++q) tma_3d(sb + q * 8192, &tmY, su32(&full[s]), n0 + 64 * q, kb * KE, l);
+                    } else {
+#pragma unroll
+                        for (int q = 0; q < BN / 32; ++q) tma_3d(sb + q * 4096, &tmY, su32(&full[s]), n0 + 32 * q, kb * BK, l);
+                    }
                     ++issued;
                 }
             }
         }
     } else if (warp == 1) {
         if (lane == 0) {
-            const uint32_t idesc = idesc_tf32(BM, BN, 0, 1);
+            const uint32_t idesc = H ? idesc_h16(H, BM, BN, 0, 1) : idesc_tf32(BM, BN, 0, 1);
             long it = 0;
             int lt = 0;
             for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++lt) {
@@ -696,7 +779,8 @@ ypass_tc_pers_kernel(const __grid_constant__ CUtensorMap tmW, const __grid_const
 #pragma unroll
                     for (int kk = 0; kk < BK / 8; ++kk) {
                         // MN-major: LBO = next 32-column chunk (4 KiB), SBO = next 4-row K group (512 B)
-                        const uint64_t bd = sdesc(sb + kk * 1024, 4096, 512, 1);
+                        // (BF16: next 64-column chunk 8 KiB, next 8-row group 1 KiB, layout 2)
+                        const uint64_t bd = H ? sdesc(sb + kk * 2048, 8192, 1024, 2) : sdesc(sb + kk * 1024, 4096, 512, 1);
                         const uint64_t wr = sdesc(sw + kk * 32, 16, 1024), wi = sdesc(sw + TILE + kk * 32, 16, 1024);
                         const uint32_t acc = (kb | kk) ? 1u : 0u;
                         if (SPLIT) {
@@ -709,8 +793,8 @@ ypass_tc_pers_kernel(const __grid_constant__ CUtensorMap tmW, const __grid_const
                             mma_tf32(accP, wr, bd, idesc, 1u);
                             mma_tf32(accQ, wi, bd, idesc, 1u);
                         } else {
-                            mma_tf32(accP, wr, bd, idesc, acc);
-                            mma_tf32(accQ, wi, bd, idesc, acc);
+                            mma_op<H>(accP, wr, bd, idesc, acc);
+                            mma_op<H>(accQ, wi, bd, idesc, acc);
                         }
                     }
                     mma_commit(su32(&empty[s]));
@@ -736,6 +820,39 @@ ypass_tc_pers_kernel(const __grid_constant__ CUtensorMap tmW, const __grid_const
                 TMEM_LD32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * 2 * BN + c), p);
                 TMEM_LD32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * 2 * BN + BN + c), qq);
                 tmem_wait_ld();
+                if (H) {
+                    // 16 complex values (re = P_re - Q_im, im = P_im + Q_re) as 16-bit pairs: 64 bytes per row
+                    uint32_t* su = reinterpret_cast<uint32_t*>(stg);
+#pragma unroll
+                    for (int v = 0; v < 16; v += 4) {
+                        uint32_t w[4];
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            const int k = 2 * (v + e);
+                            w[e] = pack16<H>(alpha * (__uint_as_float(p[k]) - __uint_as_float(qq[k + 1])),
+                                             alpha * (__uint_as_float(p[k + 1]) + __uint_as_float(qq[k])));
+                        }
+                        *reinterpret_cast<uint4*>(su + lane * XEPI_LD + v) = make_uint4(w[0], w[1], w[2], w[3]);
+                    }
+                    __syncwarp();
+                    uint16_t* ob = reinterpret_cast<uint16_t*>(outv);
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        const int rr = 8 * i + (lane >> 2), cc = 4 * (lane & 3);
+                        const int grow = rbase + rr, gcol = n0 + c + 2 * cc;
+                        const uint4 v = *reinterpret_cast<const uint4*>(su + rr * XEPI_LD + cc);
+                        if (grow < ny && gcol < N2) {
+                            uint16_t* dst = ob + ((size_t)l * ny + grow) * N2 + gcol;
+                            if (gcol + 8 <= N2) *reinterpret_cast<uint4*>(dst) = v;
+                            else {
+                                const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+                                for (int e = 0; e < 4 && gcol + 2 * e < N2; ++e) reinterpret_cast<uint32_t*>(dst)[e] = w[e];
+                            }
+                        }
+                    }
+                    __syncwarp();
+                    continue;
+                }
 #pragma unroll
                 for (int v = 0; v < 32; v += 4)
                     *reinterpret_cast<float4*>(stg + lane * YEPI_LD + v) =
@@ -832,10 +949,39 @@ __global__ void split_y_kernel(int N, int ldw, const double2* __restrict__ src, 
     put_split(W, Wl, (size_t)N * ldw + (size_t)r * ldw + k, w.y);
 }
 
+// 16-bit (round to nearest even from FP64) copies of an operand set: the same layouts as the TF32 ones
+template <int H>
+__device__ __forceinline__ uint16_t h16_bits(double v) {
+    if (H == 2) return __half_as_ushort(__double2half(v));
+    return __bfloat16_as_ushort(__double2bfloat16(v));
+}
+template <int H>
+__global__ void embed_x_h16_kernel(int N, const double2* __restrict__ src, uint16_t* __restrict__ B) {
+    const size_t id = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    if (id >= (size_t)N * N) return;
+    const int n = (int)(id / N), k = (int)(id % N);
+    const double2 w = src[(size_t)n * N + k];
+    const size_t L2 = 2 * (size_t)N;
+    B[(2 * n) * L2 + 2 * k] = h16_bits<H>(w.x);
+    B[(2 * n) * L2 + 2 * k + 1] = h16_bits<H>(-w.y);
+    B[(2 * n + 1) * L2 + 2 * k] = h16_bits<H>(w.y);
+    B[(2 * n + 1) * L2 + 2 * k + 1] = h16_bits<H>(w.x);
+}
+template <int H>
+__global__ void split_y_h16_kernel(int N, int ldw, const double2* __restrict__ src, uint16_t* __restrict__ W) {
+    const size_t id = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    if (id >= (size_t)N * ldw) return;
+    const int r = (int)(id / ldw), k = (int)(id % ldw);
+    const double2 w = k < N ? src[(size_t)r * N + k] : make_double2(0.0, 0.0);
+    W[(size_t)r * ldw + k] = h16_bits<H>(w.x);
+    W[(size_t)N * ldw + (size_t)r * ldw + k] = h16_bits<H>(w.y);
+}
+
 helm_status encode(TcState* t, CUtensorMap* map, int rank, void* ptr, const cuuint64_t* dims, const cuuint64_t* strides,
-                   const cuuint32_t* box, CUtensorMapSwizzle swz = CU_TENSOR_MAP_SWIZZLE_128B) {
+                   const cuuint32_t* box, CUtensorMapSwizzle swz = CU_TENSOR_MAP_SWIZZLE_128B,
+                   CUtensorMapDataType dt = CU_TENSOR_MAP_DATA_TYPE_FLOAT32) {
     cuuint32_t es[3] = {1, 1, 1};
-    CUresult r = t->encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, rank, ptr, dims, strides, box, es,
+    CUresult r = t->encode(map, dt, rank, ptr, dims, strides, box, es,
                            CU_TENSOR_MAP_INTERLEAVE_NONE, swz, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS ? HELM_OK : HELM_ERR_CUDA;
@@ -871,10 +1017,13 @@ helm_status tc_encode_set(TcState* t, int nx, int ny, int i);
 
 helm_status tc_prepare(helm_ctx* c, cudaStream_t s) {
     if (c->nx % 2 != 0) return HELM_ERR_UNSUPPORTED;
-    if (c->opt.precision != HELM_PREC_TF32 && c->opt.precision != HELM_PREC_TF32X3) return HELM_ERR_UNSUPPORTED;
+    const int h16 = c->opt.precision == HELM_PREC_BF16 ? 1 : c->opt.precision == HELM_PREC_FP16 ? 2 : 0;
+    if (c->opt.precision != HELM_PREC_TF32 && c->opt.precision != HELM_PREC_TF32X3 && !h16) return HELM_ERR_UNSUPPORTED;
+    if (h16 && c->nx % 4 != 0) return HELM_ERR_UNSUPPORTED;
     TcState* t = new TcState();
     c->tmaps = t;
     t->split = c->opt.precision == HELM_PREC_TF32X3;
+    t->h16 = h16;
     cudaDriverEntryPointQueryResult q;
     if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", (void**)&t->encode, 12000, cudaEnableDefault, &q) !=
             cudaSuccess || q != cudaDriverEntryPointSuccess || !t->encode) {
@@ -889,6 +1038,57 @@ helm_status tc_prepare(helm_ctx* c, cudaStream_t s) {
     if ((st = tc_fill_set(t, nx, ny, 1, c->Vx, c->Vy, s)) != HELM_OK) return st;
     for (int i = 0; i < 2; ++i)
         if (tc_encode_set(t, nx, ny, i) != HELM_OK) return HELM_ERR_CUDA;
+    if (t->h16 == 1) {   // BF16 has FP32's range: no stage scales
+        for (int k = 0; k < 5; ++k) c->h16s[k] = 1.f;
+        c->h16s[5] = (float)(c->h[2] * c->h[2]);
+    }
+    if (t->h16 == 2) {   // FP16: power-of-two stage scales from the set-up bounds, and the norm scratch
+        helm_status sst = h16_scales(c, s);
+        if (sst != HELM_OK) return sst;
+        if (cudaMalloc(&c->h16n, (2 + 1024) * sizeof(double)) != cudaSuccess) { cudaGetLastError(); return HELM_ERR_NOMEM; }
+    }
+    if (t->h16) {
+        // the EigT sets in 16 bits (the TF32 sets above serve helm_precond_step and the PFFT passes)
+        t->ldwb = (ny + 7) / 8 * 8;
+        const size_t nb = (size_t)4 * nx * nx, nw = (size_t)2 * ny * t->ldwb;
+        const double2* sx[2] = {c->Vxi, c->Vx};
+        const double2* sy[2] = {c->Vyi, c->Vy};
+        for (int i = 0; i < 2; ++i) {
+            if (cudaMalloc(&t->Bxb[i], nb * sizeof(uint16_t)) != cudaSuccess) { cudaGetLastError(); return HELM_ERR_NOMEM; }
+            if (cudaMalloc(&t->Wyb[i], nw * sizeof(uint16_t)) != cudaSuccess) { cudaGetLastError(); return HELM_ERR_NOMEM; }
+            const unsigned gx = (unsigned)((nx * (size_t)nx + 255) / 256), gy = (unsigned)((ny * (size_t)t->ldwb + 255) / 256);
+            if (h16 == 2) {
+                embed_x_h16_kernel<2><<<gx, 256, 0, s>>>(nx, sx[i], t->Bxb[i]);
+                split_y_h16_kernel<2><<<gy, 256, 0, s>>>(ny, t->ldwb, sy[i], t->Wyb[i]);
+            } else {
+                embed_x_h16_kernel<1><<<gx, 256, 0, s>>>(nx, sx[i], t->Bxb[i]);
+                split_y_h16_kernel<1><<<gy, 256, 0, s>>>(ny, t->ldwb, sy[i], t->Wyb[i]);
+            }
+            HELM_CUDA_TRY(cudaGetLastError());
+            const cuuint64_t d[2] = {(cuuint64_t)2 * nx, (cuuint64_t)2 * nx};
+            const cuuint64_t st[1] = {(cuuint64_t)2 * nx * sizeof(uint16_t)};
+            const cuuint32_t box[2] = {2 * BK, BN}, box256[2] = {2 * BK, 256};
+            const cuuint64_t dw[3] = {(cuuint64_t)ny, (cuuint64_t)ny, 2};
+            const cuuint64_t sw[2] = {(cuuint64_t)t->ldwb * sizeof(uint16_t), (cuuint64_t)t->ldwb * ny * sizeof(uint16_t)};
+            const cuuint32_t bw[3] = {2 * BK, BM, 1};
+            const CUtensorMapDataType bt = h16 == 2 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+            if (encode(t, &t->mapBxb[i], 2, t->Bxb[i], d, st, box, CU_TENSOR_MAP_SWIZZLE_128B, bt) != HELM_OK) return HELM_ERR_CUDA;
+            if ((2 * nx) % 256 == 0 &&
+                encode(t, &t->mapBxb256[i], 2, t->Bxb[i], d, st, box256, CU_TENSOR_MAP_SWIZZLE_128B, bt) != HELM_OK)
+                return HELM_ERR_CUDA;
+            if (encode(t, &t->mapWyb[i], 3, t->Wyb[i], dw, sw, bw, CU_TENSOR_MAP_SWIZZLE_128B, bt) != HELM_OK) return HELM_ERR_CUDA;
+        }
+        HELM_CUDA_TRY(smem_attr(xpass_tc_pers_kernel<128, false, 1, true>, PersX<128, false>::SMEM));
+        HELM_CUDA_TRY(smem_attr(xpass_tc_pers_kernel<256, false, 1, true>, PersX<256, false>::SMEM));
+        HELM_CUDA_TRY(smem_attr(xpass_tc_pers_kernel<128, false, 1, false>, PersX<128, false>::SMEM));
+        HELM_CUDA_TRY(smem_attr(xpass_tc_pers_kernel<256, false, 1, false>, PersX<256, false>::SMEM));
+        HELM_CUDA_TRY(smem_attr(xpass_tc_pers_kernel<128, false, 2, true>, PersX<128, false>::SMEM));
+        HELM_CUDA_TRY(smem_attr(xpass_tc_pers_kernel<256, false, 2, true>, PersX<256, false>::SMEM));
+        HELM_CUDA_TRY(smem_attr(xpass_tc_pers_kernel<128, false, 2, false>, PersX<128, false>::SMEM));
+        HELM_CUDA_TRY(smem_attr(xpass_tc_pers_kernel<256, false, 2, false>, PersX<256, false>::SMEM));
+        HELM_CUDA_TRY(smem_attr(ypass_tc_pers_kernel<false, 1>, PersY<false>::SMEM));
+        HELM_CUDA_TRY(smem_attr(ypass_tc_pers_kernel<false, 2>, PersY<false>::SMEM));
+    }
     HELM_CUDA_TRY(smem_attr(xpass_tc_kernel, xsmem()));
     HELM_CUDA_TRY(smem_attr(ypass_tc_kernel, ysmem()));
     HELM_CUDA_TRY(smem_attr(ypass_tc_pers_kernel<false>, PersY<false>::SMEM));
@@ -1013,9 +1213,80 @@ helm_status tc_ypass(helm_ctx* c, int inverse, const float2* in, float2* out, cu
     return HELM_OK;
 }
 
+// 16-bit transform chain (HELM_PREC_BF16, HELM_PREC_FP16): x-pass from a 16-bit grid (N_y N_z nb rows of
+// 2 N_x) to a 16-bit or, when out_h16 is 0, an FP32 (complex64) grid, scaled as tc_xpass
+template <int H, bool OBF>
+void xpass_h16_launch(TcState* t, helm_ctx* c, int inverse, const CUtensorMap& mapA, void* out, int M, int N2,
+                      float alpha, const double* alpha_dev, int aidx, int rp, int astride, cudaStream_t s) {
+    const long wl = (long)c->wait_limit;
+    const int mt = (M + BM - 1) / BM;
+    if (N2 % 256 == 0) {
+        const int ntiles = (N2 / 256) * mt, pg = ntiles < g_sms ? ntiles : g_sms;
+        xpass_tc_pers_kernel<256, false, H, OBF><<<pg, 192, PersX<256, false>::SMEM, s>>>(
+            mapA, t->mapBxb256[inverse], t->mapBxb256[inverse], out, M, N2, N2, alpha, alpha_dev, aidx, rp, astride,
+            c->status_d, wl);
+    } else {
+        const int ntiles = ((N2 + BN - 1) / BN) * mt, pg = ntiles < 2 * g_sms ? ntiles : 2 * g_sms;
+        xpass_tc_pers_kernel<128, false, H, OBF><<<pg, 192, PersX<128, false>::SMEM, s>>>(
+            mapA, t->mapBxb[inverse], t->mapBxb[inverse], out, M, N2, N2, alpha, alpha_dev, aidx, rp, astride,
+            c->status_d, wl);
+    }
+}
+
+helm_status tc_xpass_h16(helm_ctx* c, int inverse, const void* in, void* out, int out_h16, float alpha,
+                         const double* alpha_dev, int aidx, cudaStream_t s, int nb, int astride) {
+    TcState* t = (TcState*)c->tmaps;
+    if (!t || !t->h16 || g_sms <= 0) return HELM_ERR_UNSUPPORTED;
+    const int rp = c->ny * c->nz;
+    const int M = rp * nb, N2 = 2 * c->nx;
+    CUtensorMap mapA;
+    const cuuint64_t d[2] = {(cuuint64_t)N2, (cuuint64_t)M};
+    const cuuint64_t st[1] = {(cuuint64_t)N2 * sizeof(uint16_t)};
+    const cuuint32_t box[2] = {2 * BK, BM};
+    const CUtensorMapDataType dt = t->h16 == 2 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+    if (encode(t, &mapA, 2, (void*)in, d, st, box, CU_TENSOR_MAP_SWIZZLE_128B, dt) != HELM_OK) return HELM_ERR_CUDA;
+    if (t->h16 == 2) {
+        if (out_h16) xpass_h16_launch<2, true>(t, c, inverse, mapA, out, M, N2, alpha, alpha_dev, aidx, rp, astride, s);
+        else xpass_h16_launch<2, false>(t, c, inverse, mapA, out, M, N2, alpha, alpha_dev, aidx, rp, astride, s);
+    } else {
+        if (out_h16) xpass_h16_launch<1, true>(t, c, inverse, mapA, out, M, N2, alpha, alpha_dev, aidx, rp, astride, s);
+        else xpass_h16_launch<1, false>(t, c, inverse, mapA, out, M, N2, alpha, alpha_dev, aidx, rp, astride, s);
+    }
+    HELM_CUDA_TRY(cudaGetLastError());
+    return HELM_OK;
+}
+
+// y-pass of the 16-bit chain: 16-bit slices in, 16-bit slices out (scaled by alpha)
+helm_status tc_ypass_h16(helm_ctx* c, int inverse, const void* in, void* out, float alpha, cudaStream_t s, int nb) {
+    TcState* t = (TcState*)c->tmaps;
+    if (!t || !t->h16 || g_sms <= 0) return HELM_ERR_UNSUPPORTED;
+    const int ny = c->ny, N2 = 2 * c->nx, nzb = c->nz * nb;
+    CUtensorMap mapY;
+    const cuuint64_t d[3] = {(cuuint64_t)N2, (cuuint64_t)ny, (cuuint64_t)nzb};
+    const cuuint64_t st[2] = {(cuuint64_t)N2 * sizeof(uint16_t), (cuuint64_t)N2 * ny * sizeof(uint16_t)};
+    const cuuint32_t box[3] = {64, 2 * BK, 1};
+    const CUtensorMapDataType dt = t->h16 == 2 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+    if (encode(t, &mapY, 3, (void*)in, d, st, box, CU_TENSOR_MAP_SWIZZLE_128B, dt) != HELM_OK) return HELM_ERR_CUDA;
+    const long wl = (long)c->wait_limit;
+    const int ntiles = ((N2 + BN - 1) / BN) * ((ny + BM - 1) / BM) * nzb;
+    const int pg = ntiles > g_sms ? g_sms : ntiles;
+    if (t->h16 == 2)
+        ypass_tc_pers_kernel<false, 2><<<pg, 192, PersY<false>::SMEM, s>>>(t->mapWyb[inverse], mapY, t->mapWyb[inverse],
+                                                                          out, ny, N2, nzb, c->status_d, wl, alpha);
+    else
+        ypass_tc_pers_kernel<false, 1><<<pg, 192, PersY<false>::SMEM, s>>>(t->mapWyb[inverse], mapY, t->mapWyb[inverse],
+                                                                          out, ny, N2, nzb, c->status_d, wl, alpha);
+    HELM_CUDA_TRY(cudaGetLastError());
+    return HELM_OK;
+}
+
 void tc_release(helm_ctx* c) {
     TcState* t = (TcState*)c->tmaps;
     if (!t) return;
+    for (int i = 0; i < 2; ++i) {
+        cudaFree(t->Bxb[i]);
+        cudaFree(t->Wyb[i]);
+    }
     for (int i = 0; i < 4; ++i) {
         cudaFree(t->Bx[i]);
         cudaFree(t->Wy[i]);

@@ -6,6 +6,8 @@
 // context's scratch vector.  An optional device scale sigma[sidx] multiplies r (lazy normalisation
 // of the Arnoldi vectors).
 #include "common.cuh"
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 namespace {
 
@@ -17,6 +19,117 @@ __global__ void scale_copy_kernel(const float2* __restrict__ a, float2* __restri
 }
 
 bool use_tc(const helm_ctx* c) { return c->opt.precision != HELM_PREC_FP32; }
+
+// complex64 -> 16-bit pairs (H = 1 BF16, 2 FP16 clamped to the finite range; round to nearest even), the
+// entry of the 16-bit chain: two points per float4, times s0 and the Arnoldi scale sigma[sidx] (else inv[0])
+template <int H>
+__device__ __forceinline__ uint32_t cpack16(float lo, float hi) {
+    if (H == 2) {
+        const __half2 v = __floats2half2_rn(fminf(fmaxf(lo, -65504.f), 65504.f), fminf(fmaxf(hi, -65504.f), 65504.f));
+        return *reinterpret_cast<const uint32_t*>(&v);
+    }
+    const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<const uint32_t*>(&v);
+}
+template <int H>
+__global__ void c64_to_h16_kernel(const float4* __restrict__ a, uint2* __restrict__ b, size_t n2, float s0,
+                                  const double* __restrict__ sigma, int sidx, const double* __restrict__ inv) {
+    const float sc = s0 * (sigma ? (float)sigma[sidx] : inv ? (float)inv[0] : 1.f);
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    for (size_t i0 = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i0 < n2; i0 += 4 * stride) {
+        float4 v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const size_t i = i0 + u * stride;
+            v[u] = i < n2 ? a[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const size_t i = i0 + u * stride;
+            if (i < n2) b[i] = make_uint2(cpack16<H>(sc * v[u].x, sc * v[u].y), cpack16<H>(sc * v[u].z, sc * v[u].w));
+        }
+    }
+}
+
+// ||r||_2 of a complex64 grid: per-block FP64 partial sums, then one block writes 1/||r|| (0 for r = 0) and ||r||
+constexpr int NRM_BLOCKS = 1024;
+__global__ void norm_part_kernel(const float2* __restrict__ r, size_t n, double* __restrict__ part) {
+    double acc = 0.0;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const float2 v = r[i];
+        acc += (double)v.x * v.x + (double)v.y * v.y;
+    }
+    __shared__ double sh[256];
+    sh[threadIdx.x] = acc;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
+}
+__global__ void norm_final_kernel(const double* __restrict__ part, int nparts, double* __restrict__ out) {
+    __shared__ double sh[256];
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < nparts; i += blockDim.x) acc += part[i];
+    sh[threadIdx.x] = acc;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const double nr = sqrt(sh[0]);
+        out[0] = nr > 0.0 ? 1.0 / nr : 0.0;
+        out[1] = nr;
+    }
+}
+
+// EigT with 16-bit intermediate grids (HELM_PREC_BF16, HELM_PREC_FP16): r (complex64) -> 16 bits ->
+// x-pass -> y-pass -> z-solve -> y-pass -> x-pass -> z (complex64), every stored grid times its power-of-two
+// stage scale c->h16s (FP16; all 1 for BF16, whose range is FP32's), the last pass undoing them.  The two
+// 16-bit grids live in the halves of the context's scratch vector (T0, T1); the z-solve keeps its FP32
+// forward values in z, which is free until the last pass, so r may alias z.
+helm_status precond_h16(helm_ctx* c, const float2* r, float2* z, const double* sigma, int sidx, cudaStream_t s) {
+    helm_status st;
+    const size_t n = c->npts;
+    const int H = c->opt.precision == HELM_PREC_FP16 ? 2 : 1;
+    uint16_t* T0 = reinterpret_cast<uint16_t*>(c->tmp);
+    uint16_t* T1 = T0 + 2 * n;
+    const float* sc = c->h16s;
+    const double* inv = nullptr;
+    const double* nrm = nullptr;
+    prof_begin(c, s, PROF_XPASS);
+    if (H == 2 && !sigma) {   // no Arnoldi scale: normalise by ||r|| here, restore it in the last pass
+        norm_part_kernel<<<NRM_BLOCKS, 256, 0, s>>>(r, n, c->h16n + 2);
+        norm_final_kernel<<<1, 256, 0, s>>>(c->h16n + 2, NRM_BLOCKS, c->h16n);
+        inv = c->h16n;
+        nrm = c->h16n + 1;
+    }
+    if (H == 2)
+        c64_to_h16_kernel<2><<<2048, 256, 0, s>>>(reinterpret_cast<const float4*>(r), reinterpret_cast<uint2*>(T0), n / 2,
+                                                  sc[0], sigma, sidx, inv);
+    else
+        c64_to_h16_kernel<1><<<2048, 256, 0, s>>>(reinterpret_cast<const float4*>(r), reinterpret_cast<uint2*>(T0), n / 2,
+                                                  sc[0], sigma, sidx, inv);
+    HELM_CUDA_TRY(cudaGetLastError());
+    st = tc_xpass_h16(c, 0, T0, T1, 1, sc[1], nullptr, 0, s);
+    prof_end(c, s);
+    if (st != HELM_OK) return st;
+    prof_begin(c, s, PROF_YPASS);
+    st = tc_ypass_h16(c, 0, T1, T0, sc[2], s);
+    prof_end(c, s);
+    if (st != HELM_OK) return st;
+    if ((st = launch_zsolve_h16(c, T0, T0, reinterpret_cast<float4*>(z), sc[3], s)) != HELM_OK) return st;
+    prof_begin(c, s, PROF_YPASS);
+    st = tc_ypass_h16(c, 1, T0, T1, sc[4], s);
+    prof_end(c, s);
+    if (st != HELM_OK) return st;
+    prof_begin(c, s, PROF_XPASS);
+    st = tc_xpass_h16(c, 1, T1, z, 0, sc[5], nrm, 0, s);
+    prof_end(c, s);
+    return st;
+}
 
 // nb > 1: nb grid vectors back to back (a batch group); vector v is scaled by sigma[sidx + v sstride]
 helm_status xpass(helm_ctx* c, int inverse, const float2* in, float2* out, float alpha, const double* sigma, int sidx,
@@ -83,6 +196,7 @@ static helm_status precond_base(helm_ctx* c, const float2* r, float2* z, const d
         prof_end(c, s);
         return st;
     }
+    if (c->opt.precision == HELM_PREC_BF16 || c->opt.precision == HELM_PREC_FP16) return precond_h16(c, r, z, sigma, sidx, s);
     const float hz2 = (float)(c->h[2] * c->h[2]);
     if ((st = xpass(c, 0, r, c->tmp, 1.f, sigma, sidx, s)) != HELM_OK) return st;
     if ((st = ypass(c, 0, c->tmp, z, s)) != HELM_OK) return st;
@@ -107,7 +221,9 @@ helm_status precond_apply_nb(helm_ctx* c, const float2* r, float2* z, int nb, co
         HELM_CUDA_TRY(cudaGetLastError());
         return HELM_OK;
     }
-    if (c->opt.precond != HELM_PRECOND_EIGT || c->net) return HELM_ERR_UNSUPPORTED;
+    if (c->opt.precond != HELM_PRECOND_EIGT || c->net || c->opt.precision == HELM_PREC_BF16 ||
+        c->opt.precision == HELM_PREC_FP16)
+        return HELM_ERR_UNSUPPORTED;
     const float hz2 = (float)(c->h[2] * c->h[2]);
     if ((st = xpass(c, 0, r, c->tmp, 1.f, sigma, sidx, s, nb, sstride)) != HELM_OK) return st;
     if ((st = ypass(c, 0, c->tmp, z, s, nb)) != HELM_OK) return st;

@@ -583,15 +583,20 @@ __global__ void rhs_df_kernel(int order, int colloc, int nx, int ny, int nz, Rhs
 //   a0 = 1 - 30 sum L_d + 6 sum Q_d + 4 sum M_q,  a1_d = 16 L_d - 4 Q_d - 2 sum_{q ni d} M_q,
 //   a2_d = Q_d - L_d,  m_q = M_q,
 // so each class is summed first and scaled once (ten double-float products instead of the per-term ones).
+// The whole sum is one unnormalised double-float pair (compensated summation: one two-sum per addition,
+// FMA-exact products, the errors gathered in the low part), joined to FP64 once at the end.
 // A CTA owns a 32 x 8 column tile and marches RZC planes in z; the planes z-2 .. z+3 sit in a six-slot
 // shared-memory ring filled by 16-byte cp.async from the mirror-extended halo (its in-plane offsets are
-// computed once per staging slot), so a point's 24 neighbours are shared-memory reads.
+// computed once per staging slot), so a point's 24 neighbours are shared-memory reads.  REAL (media
+// without attenuation): k^2 from the residual's real field Kq = k^2 h^2 / 3, so (h^2/20) k^2 f = (3/20) Kq f,
+// and the gradients as real floats.
 struct Rhs6W {
     df a0;
     df a1[3];
     df a2[3];
     df m[3];          // pairs xy, xz, yz
     df h2_20;
+    df c3_20;         // 3/20
     float h4_60;
     float i2h[3];
 };
@@ -604,9 +609,12 @@ __device__ __forceinline__ void r6_cp16(void* smem, const void* gmem) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
 }
 
+template <bool REAL>
 __global__ void __launch_bounds__(R6TX * R6TY) rhs6_plane_kernel(int colloc, int nx, int ny, int nz, Rhs6W W,
                                                               const float4* __restrict__ fdf,
                                                               const float4* __restrict__ k2df,
+                                                              const float2* __restrict__ kq,
+                                                              const float4* __restrict__ fr,
                                                               const float2* __restrict__ dkx,
                                                               const float2* __restrict__ dky,
                                                               const float2* __restrict__ dkz,
@@ -657,27 +665,41 @@ __global__ void __launch_bounds__(R6TX * R6TY) rhs6_plane_kernel(int colloc, int
         auto L = [&](const float4* S, int o) { return cdf_from4(S[c + o]); };
         const cdf fc = L(S0, 0);
         const cdf xm = L(S0, -1), xp = L(S0, 1), ym = L(S0, -R6PX), yp = L(S0, R6PX), zm = L(Sm1, 0), zp = L(Sp1, 0);
-        cdf out = cdf_scale(fc, W.a0);
-        out = cdf_add(out, cdf_scale(cdf_add(xm, xp), W.a1[0]));
-        out = cdf_add(out, cdf_scale(cdf_add(ym, yp), W.a1[1]));
-        out = cdf_add(out, cdf_scale(cdf_add(zm, zp), W.a1[2]));
-        out = cdf_add(out, cdf_scale(cdf_add(L(S0, -2), L(S0, 2)), W.a2[0]));
-        out = cdf_add(out, cdf_scale(cdf_add(L(S0, -2 * R6PX), L(S0, 2 * R6PX)), W.a2[1]));
-        out = cdf_add(out, cdf_scale(cdf_add(L(Sm2, 0), L(Sp2, 0)), W.a2[2]));
-        const cdf cxy = cdf_add(cdf_add(L(S0, -R6PX - 1), L(S0, -R6PX + 1)), cdf_add(L(S0, R6PX - 1), L(S0, R6PX + 1)));
-        const cdf cxz = cdf_add(cdf_add(L(Sm1, -1), L(Sm1, 1)), cdf_add(L(Sp1, -1), L(Sp1, 1)));
-        const cdf cyz = cdf_add(cdf_add(L(Sm1, -R6PX), L(Sm1, R6PX)), cdf_add(L(Sp1, -R6PX), L(Sp1, R6PX)));
-        out = cdf_add(out, cdf_scale(cxy, W.m[0]));
-        out = cdf_add(out, cdf_scale(cxz, W.m[1]));
-        out = cdf_add(out, cdf_scale(cyz, W.m[2]));
         const size_t id = (size_t)z * plane + (size_t)gy * nx + gx;
-        out = cdf_sub(out, cdf_scale(cdf_mul(cdf_from4(k2df[id]), fc), W.h2_20));
+        float2 kql = make_float2(0.f, 0.f);
+        float4 kv = make_float4(0.f, 0.f, 0.f, 0.f), fv = kv;
+        if (REAL) {
+            kql = kq[id];
+            fv = fr[id];
+        } else {
+            kv = k2df[id];
+        }
+        cdf out = cp_mul(fc, W.a0);
+        out = cp_add(out, cp_mul(cp_add(xm, xp), W.a1[0]));
+        out = cp_add(out, cp_mul(cp_add(ym, yp), W.a1[1]));
+        out = cp_add(out, cp_mul(cp_add(zm, zp), W.a1[2]));
+        out = cp_add(out, cp_mul(cp_add(L(S0, -2), L(S0, 2)), W.a2[0]));
+        out = cp_add(out, cp_mul(cp_add(L(S0, -2 * R6PX), L(S0, 2 * R6PX)), W.a2[1]));
+        out = cp_add(out, cp_mul(cp_add(L(Sm2, 0), L(Sp2, 0)), W.a2[2]));
+        const cdf cxy = cp_add(cp_add(L(S0, -R6PX - 1), L(S0, -R6PX + 1)), cp_add(L(S0, R6PX - 1), L(S0, R6PX + 1)));
+        const cdf cxz = cp_add(cp_add(L(Sm1, -1), L(Sm1, 1)), cp_add(L(Sp1, -1), L(Sp1, 1)));
+        const cdf cyz = cp_add(cp_add(L(Sm1, -R6PX), L(Sm1, R6PX)), cp_add(L(Sp1, -R6PX), L(Sp1, R6PX)));
+        out = cp_add(out, cp_mul(cxy, W.m[0]));
+        out = cp_add(out, cp_mul(cxz, W.m[1]));
+        out = cp_add(out, cp_mul(cyz, W.m[2]));
         // (h^4/60) sum_d g_d f_d in FP32 from the leading parts, as in rhs_df_kernel
         const float2 fdx = mul2(sub2(xp.hi, xm.hi), bc2(W.i2h[0]));
         const float2 fdy = mul2(sub2(yp.hi, ym.hi), bc2(W.i2h[1]));
         const float2 fdz = mul2(sub2(zp.hi, zm.hi), bc2(W.i2h[2]));
-        const float2 g = cadd(cadd(cmul(dkx[id], fdx), cmul(dky[id], fdy)), cmul(dkz[id], fdz));
-        out = cdf_add(out, cdf_from_f2(make_float2(W.h4_60 * g.x, W.h4_60 * g.y)));
+        float2 g;
+        if (REAL) {
+            out = cp_sub(out, cp_mul(cp_mul(fc, df{kql.x, kql.y}), W.c3_20));
+            g = fma2(bc2(fv.w), fdz, fma2(bc2(fv.z), fdy, mul2(bc2(fv.y), fdx)));
+        } else {
+            out = cp_sub(out, cp_mul(cdf_mul(cdf_from4(kv), fc), W.h2_20));
+            g = cadd(cadd(cmul(dkx[id], fdx), cmul(dky[id], fdy)), cmul(dkz[id], fdz));
+        }
+        out = cp_add_f2(out, mul2(bc2(W.h4_60), g));
         F[id] = cdf_to_double2_fp64(out);
     }
 }
@@ -914,10 +936,17 @@ helm_status launch_rhs(helm_ctx* c, const double2* f, double2* F, float4* fdf, c
             R.i2h[d] = W.i2h[d];
         }
         R.h2_20 = W.h2_20;
+        R.c3_20 = PDF::cst(3.0 / 20.0);
         R.h4_60 = W.h4_60;
         const dim3 grid((c->nx + R6TX - 1) / R6TX, (c->ny + R6TY - 1) / R6TY, (c->nz + R6ZC - 1) / R6ZC);
-        rhs6_plane_kernel<<<grid, dim3(R6TX, R6TY), 0, s>>>(c->colloc, c->nx, c->ny, c->nz, R, fdf, c->k2_df,
-                                                             c->dk2_f[0], c->dk2_f[1], c->dk2_f[2], F);
+        if (c->rkq && c->fr)
+            rhs6_plane_kernel<true><<<grid, dim3(R6TX, R6TY), 0, s>>>(c->colloc, c->nx, c->ny, c->nz, R, fdf, c->k2_df,
+                                                                      c->rkq, c->fr, c->dk2_f[0], c->dk2_f[1],
+                                                                      c->dk2_f[2], F);
+        else
+            rhs6_plane_kernel<false><<<grid, dim3(R6TX, R6TY), 0, s>>>(c->colloc, c->nx, c->ny, c->nz, R, fdf, c->k2_df,
+                                                                       c->rkq, c->fr, c->dk2_f[0], c->dk2_f[1],
+                                                                       c->dk2_f[2], F);
         prof_end(c, s);
         HELM_CUDA_TRY(cudaGetLastError());
         return HELM_OK;

@@ -957,6 +957,7 @@ void stencil_fast_release(helm_ctx* c) {
     c->k2r = nullptr;
     c->fr = nullptr;
     c->realk = 0;
+    residual_real_release(c);
 }
 
 namespace {
@@ -1339,12 +1340,250 @@ df df_host(double v) {
     return df{h, (float)(v - (double)h)};
 }
 
+// ---- the true residual, sixth order, real media: two rows per thread, compensated sums ------------
+// For a medium without attenuation the sixth-order operator, divided by c_L = 1/(30 h^2), contributes per
+// plane Q of the z-march (the factors of the kernel above times 30 h^2):
+//   as a neighbour plane (Q = P -+ 1):  14 c + 3 f + e + (kf - kc)
+//   as the centre plane (Q = P):        14 f + 3 e - 128 c + (84 kc + kcs - kf) + Gq c
+// with c, f, e the centre value, the sum of the four in-plane face neighbours and of the four in-plane
+// corners of U, kc, kf, kcs the same sums of Kq U, Kq = k^2 h^2 / 3, Gq = (3/2) h^4 G; the gradient terms
+// (h/20) g_d D_d become (3/2) h^3 g_d D_d, taken in FP32 from the leading parts as above.  Then A x =
+// c_L S and r = F - c_L S.  Every sum is an unnormalised double-float pair (one two-sum per addition, the
+// errors gathered in the low part), every product by a constant one FMA-exact product: about half the
+// instructions of the renormalised form.  A thread computes the points (x, 2t) and (x, 2t + 1) of the
+// 32 x 8 tile from one 4 x 3 patch of U and Kq; x, Kq, F and the per-point fields stream into a four-slot
+// cp.async ring; the ghost factors are applied in shared memory only by tiles touching the boundary and on
+// the ghost planes.  Same grid and per-CTA partial sums as the kernel above.
+struct R6Stage {
+    float4 u[FHALO];     // x on the halo (re.hi, im.hi, re.lo, im.lo)
+    float2 kq[FHALO];    // Kq on the halo (hi, lo)
+    float4 F[FNT];       // F at the tile's points
+    float4 g4[FNT];      // (Gq hi, Gq lo, gq_x, gq_y)
+    float gz[FNT];       // gq_z
+};
+constexpr size_t R6_SMEM = FNS * sizeof(R6Stage);   // 69,504 bytes: three CTAs per SM
+
+struct R6Params {
+    int nx, ny, nz;
+    cdf gx, gy, gz;      // ghost factors
+    df cL;               // 1 / (30 h^2)
+    const float2* kq;
+    const float4* g4;
+    const float* gzq;
+    const float4* F;
+};
+
+__global__ void __launch_bounds__(F2T, 3)
+residual_real6_kernel(R6Params p, const float4* __restrict__ X, float2* __restrict__ rout, double* __restrict__ part) {
+    extern __shared__ __align__(16) unsigned char r6sm[];
+    R6Stage* ring = reinterpret_cast<R6Stage*>(r6sm);
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * FTX + tx;   // ty = 0 .. 3
+    const int x0 = blockIdx.x * FTX, y0 = blockIdx.y * FTY;
+    const int z0 = blockIdx.z * FZCH;
+    const int z1 = min(z0 + FZCH, p.nz);
+    const int gx = x0 + tx, gy0 = y0 + 2 * ty;
+    const bool act[2] = {gx < p.nx && gy0 < p.ny, gx < p.nx && gy0 + 1 < p.ny};
+    const bool edge = x0 == 0 || y0 == 0 || x0 + FTX >= p.nx || y0 + FTY >= p.ny;
+    unsigned sl[3] = {0u, 0u, 0u};
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const int q = tid + k * F2T;
+        if (q < FHALO) {
+            const int ly = q / FPX, lx = q - ly * FPX;
+            const int Xg = x0 + lx - 1, Yg = y0 + ly - 1;
+            const int Xc = min(max(Xg, 0), p.nx - 1), Yc = min(max(Yg, 0), p.ny - 1);
+            sl[k] = (unsigned)(Yc * p.nx + Xc) | (Xc != Xg ? 1u << 30 : 0u) | (Yc != Yg ? 1u << 31 : 0u);
+        }
+    }
+    const size_t plane = (size_t)p.nx * p.ny;
+    const int poff = gy0 * p.nx + gx;
+    const int fi = (2 * ty) * FTX + tx;   // point r of this thread at index fi + r FTX of the per-point arrays
+
+    auto issue = [&](int P) {
+        if (P <= z1) {
+            R6Stage& S = ring[(P + FNS) % FNS];
+            const int Pc = min(max(P, 0), p.nz - 1);
+            const float4* Xb = X + (size_t)Pc * plane;
+            const float2* Kb = p.kq + (size_t)Pc * plane;
+#pragma unroll
+            for (int k = 0; k < 3; ++k)
+                if (tid + k * F2T < FHALO) {
+                    cp16f(&S.u[tid + k * F2T], Xb + (sl[k] & 0x3FFFFFFFu));
+                    cp8(&S.kq[tid + k * F2T], Kb + (sl[k] & 0x3FFFFFFFu));
+                }
+            if (P >= z0 && P < z1) {
+                const size_t g = (size_t)P * plane + poff;
+#pragma unroll
+                for (int r = 0; r < 2; ++r)
+                    if (act[r]) {
+                        cp16f(&S.F[fi + r * FTX], p.F + g + r * p.nx);
+                        cp16f(&S.g4[fi + r * FTX], p.g4 + g + r * p.nx);
+                        cp4(&S.gz[fi + r * FTX], p.gzq + g + r * p.nx);
+                    }
+            }
+        }
+        cp_commit();
+    };
+
+    cdf cS[2], nS[2];
+    float2 cX[2], cY[2], cZ[2], nX[2], nY[2], nZ[2];
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+        cS[r] = nS[r] = cdf_zero();
+        cX[r] = cY[r] = cZ[r] = nX[r] = nY[r] = nZ[r] = make_float2(0.f, 0.f);
+    }
+    float fsum = 0.f, fcmp = 0.f, fmx = 0.f;
+    issue(z0 - 1);
+    issue(z0);
+    for (int P = z0 - 1; P <= z1; ++P) {
+        R6Stage& S = ring[(P + FNS) % FNS];
+        cp_wait1();
+        __syncthreads();          // plane P landed for everyone; everyone is done with planes P-1 and P-2
+        const bool zghost = P < 0 || P >= p.nz;
+        if (edge || zghost) {     // uniform per CTA and plane
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                const int q = tid + k * F2T;
+                if (q < FHALO && ((sl[k] >> 30) || zghost)) {
+                    cdf u = cdf_from4(S.u[q]);
+                    if (sl[k] & (1u << 30)) u = cdf_mul(u, p.gx);
+                    if (sl[k] & (1u << 31)) u = cdf_mul(u, p.gy);
+                    if (zghost) u = cdf_mul(u, p.gz);
+                    S.u[q] = cdf_to4(u);
+                }
+            }
+            __syncthreads();
+        }
+        issue(P + 2);             // into the slot of plane P-2
+        // per patch row b (halo row 2t + b): centre column, the pair sum of the side columns and their
+        // leading-part difference, for U and for Kq U
+        cdf um[4], hu[4], km[4], hk[4];
+        float2 du[4], dk[4];
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            const int i = (2 * ty + b) * FPX + tx;
+            const cdf u0 = cdf_from4(S.u[i]), u1 = cdf_from4(S.u[i + 1]), u2 = cdf_from4(S.u[i + 2]);
+            const float2 q0 = S.kq[i], q1 = S.kq[i + 1], q2 = S.kq[i + 2];
+            const cdf k0 = cp_mul(u0, df{q0.x, q0.y}), k1 = cp_mul(u1, df{q1.x, q1.y}), k2 = cp_mul(u2, df{q2.x, q2.y});
+            um[b] = u1;
+            hu[b] = cp_add(u0, u2);
+            du[b] = sub2(u2.hi, u0.hi);
+            km[b] = k1;
+            hk[b] = cp_add(k0, k2);
+            dk[b] = sub2(k2.hi, k0.hi);
+        }
+        const bool out_prev = P - 1 >= z0 && P - 1 < z1;
+        const bool do_mid = P >= z0 && P < z1;
+        const R6Stage& Sp = ring[(P - 1 + FNS) % FNS];
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            const cdf c = um[r + 1];
+            const cdf f = cp_add(hu[r + 1], cp_add(um[r], um[r + 2]));
+            const cdf e = cp_add(hu[r], hu[r + 2]);
+            const cdf kc = km[r + 1];
+            const cdf kf = cp_add(hk[r + 1], cp_add(km[r], km[r + 2]));
+            // this plane as a neighbour plane
+            const cdf nb = cp_add(cp_add(cp_mulk(c, 14.f), cp_mulk(f, 3.f)), cp_add(e, cp_sub(kf, kc)));
+            const float2 dx1 = du[r + 1], dy1 = sub2(um[r + 2].hi, um[r].hi);
+            const float2 Xs = f2scl(dx1, 1.f / 6.f), Ys = f2scl(dy1, 1.f / 6.f);
+            const float2 Zs = f2add(f2fma(0.5f, kc.hi, c.hi), f2scl(f2fma(-4.f, c.hi, f.hi), 1.f / 6.f));
+            if (out_prev && act[r]) {
+                const int j = fi + r * FTX;
+                const float4 gv = Sp.g4[j];
+                float2 g = f2scl(f2add(cX[r], Xs), gv.z);
+                g = f2fma(gv.w, f2add(cY[r], Ys), g);
+                g = f2fma(Sp.gz[j], f2add(cZ[r], Zs), g);
+                const cdf Ssum = cp_add_f2(cp_add(cS[r], nb), g);
+                const cdf R = cp_sub(cdf_from4(Sp.F[j]), cp_mul(Ssum, p.cL));
+                const float2 rf = add2(R.hi, R.lo);
+                rout[(size_t)(P - 1) * plane + poff + r * p.nx] = rf;
+                const float a2 = fmaf(rf.x, rf.x, rf.y * rf.y);
+                kahan_add(fsum, fcmp, a2);
+                fmx = fmaxf(fmx, a2);
+            }
+            cS[r] = nS[r]; cX[r] = nX[r]; cY[r] = nY[r]; cZ[r] = nZ[r];
+            if (do_mid) {
+                const cdf kcs = cp_add(hk[r], hk[r + 2]);
+                const float4 gv = S.g4[fi + r * FTX];
+                cdf ce = cp_sub(cp_add(cp_mulk(f, 14.f), cp_mulk(e, 3.f)), cdf{f2scl(c.hi, 128.f), f2scl(c.lo, 128.f)});
+                ce = cp_add(ce, cp_sub(cp_add(cp_mulk(kc, 84.f), kcs), kf));
+                ce = cp_add(ce, cp_mul(c, df{gv.x, gv.y}));
+                const float2 tdx = f2add(du[r], du[r + 2]), tdy = f2sub(hu[r + 2].hi, hu[r].hi);
+                const float2 dky = sub2(km[r + 2].hi, km[r].hi);
+                const float2 Xm = f2add(f2fma(0.5f, dk[r + 1], dx1), f2scl(f2fma(-4.f, dx1, tdx), 1.f / 6.f));
+                const float2 Ym = f2add(f2fma(0.5f, dky, dy1), f2scl(f2fma(-4.f, dy1, tdy), 1.f / 6.f));
+                cS[r] = cp_add(cS[r], ce);
+                cX[r] = f2add(cX[r], Xm);
+                cY[r] = f2add(cY[r], Ym);
+            }
+            nS[r] = nb; nX[r] = Xs; nY[r] = Ys; nZ[r] = make_float2(-Zs.x, -Zs.y);
+        }
+    }
+    __shared__ double rs[F2T / 32], rm[F2T / 32];
+    double ssum = (double)fsum - (double)fcmp, smax = (double)fmx;
+    for (int o = 16; o > 0; o >>= 1) {
+        ssum += __shfl_down_sync(0xffffffffu, ssum, o);
+        smax = fmax(smax, __shfl_down_sync(0xffffffffu, smax, o));
+    }
+    if ((tid & 31) == 0) { rs[tid >> 5] = ssum; rm[tid >> 5] = smax; }
+    __syncthreads();
+    if (tid == 0) {
+        double s = 0, m = 0;
+        for (int w = 0; w < F2T / 32; ++w) { s += rs[w]; m = fmax(m, rm[w]); }
+        const int cta = (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+        part[2 * cta] = s;
+        part[2 * cta + 1] = sqrt(m);
+    }
+}
+
+// the residual's real-medium fields from the FP64 set-up fields (real parts; Im k^2 = 0 everywhere)
+__global__ void resid6_fields_kernel(size_t n, double h, const double2* __restrict__ k2, const double2* __restrict__ G,
+                                     const double2* __restrict__ gx, const double2* __restrict__ gy,
+                                     const double2* __restrict__ gz, float2* __restrict__ kq, float4* __restrict__ g4,
+                                     float* __restrict__ gzq) {
+    const double h2 = h * h, cq = h2 / 3.0, cg = 1.5 * h2 * h2, cd = 1.5 * h2 * h;
+    for (size_t id = blockIdx.x * (size_t)blockDim.x + threadIdx.x; id < n; id += (size_t)gridDim.x * blockDim.x) {
+        const double k = k2[id].x * cq, g = G[id].x * cg;
+        const float kh = (float)k, gh = (float)g;
+        kq[id] = make_float2(kh, (float)(k - (double)kh));
+        g4[id] = make_float4(gh, (float)(g - (double)gh), (float)(gx[id].x * cd), (float)(gy[id].x * cd));
+        gzq[id] = (float)(gz[id].x * cd);
+    }
+}
+
 }  // namespace
 
 helm_status residual_fast_prepare() {
     HELM_CUDA_TRY(cudaFuncSetAttribute(residual_fast_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, rsmem<4>()));
     HELM_CUDA_TRY(cudaFuncSetAttribute(residual_fast_kernel<6>, cudaFuncAttributeMaxDynamicSharedMemorySize, rsmem<6>()));
+    HELM_CUDA_TRY(cudaFuncSetAttribute(residual_real6_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)R6_SMEM));
     return HELM_OK;
+}
+
+// Fields of the sixth-order real-medium residual (after stencil_real_prepare found Im k^2 = 0): 28 bytes
+// per point.  Without them the residual takes the complex-medium kernel.
+helm_status residual_real_prepare(helm_ctx* c, cudaStream_t s) {
+    if (!c->realk || c->opt.order != 6) return HELM_OK;
+    if (cudaMalloc(&c->rkq, c->npts * sizeof(float2)) != cudaSuccess ||
+        cudaMalloc(&c->rg4, c->npts * sizeof(float4)) != cudaSuccess ||
+        cudaMalloc(&c->rgz, c->npts * sizeof(float)) != cudaSuccess) {
+        cudaGetLastError();
+        residual_real_release(c);
+        return HELM_ERR_NOMEM;
+    }
+    resid6_fields_kernel<<<1024, 256, 0, s>>>(c->npts, c->h[0], c->k2_d, c->G_d, c->dk2_d[0], c->dk2_d[1], c->dk2_d[2],
+                                              c->rkq, c->rg4, c->rgz);
+    HELM_CUDA_TRY(cudaGetLastError());
+    return HELM_OK;
+}
+
+void residual_real_release(helm_ctx* c) {
+    cudaFree(c->rkq);
+    cudaFree(c->rg4);
+    cudaFree(c->rgz);
+    c->rkq = nullptr;
+    c->rg4 = nullptr;
+    c->rgz = nullptr;
 }
 
 // grid of the residual kernels: 32 x 8 columns, 32-plane chunks (one partial pair per CTA)
@@ -1367,7 +1606,14 @@ helm_status launch_residual_fast(helm_ctx* c, const float4* x, const float4* F, 
     for (int d = 0; d < 3; ++d) p.g[d] = c->dk2_f[d];
     p.F = F;
     dim3 grid((c->nx + FTX - 1) / FTX, (c->ny + FTY - 1) / FTY, (c->nz + FZCH - 1) / FZCH), block(FTX, FTY);
-    if (c->opt.order == 6)
+    if (c->opt.order == 6 && c->rkq) {
+        R6Params q;
+        q.nx = c->nx; q.ny = c->ny; q.nz = c->nz;
+        q.gx = p.gx; q.gy = p.gy; q.gz = p.gz;
+        q.cL = df_host(1.0 / (30.0 * hx * hx));
+        q.kq = c->rkq; q.g4 = c->rg4; q.gzq = c->rgz; q.F = F;
+        residual_real6_kernel<<<grid, dim3(FTX, FTY / 2), R6_SMEM, s>>>(q, x, r, part);
+    } else if (c->opt.order == 6)
         residual_fast_kernel<6><<<grid, block, rsmem<6>(), s>>>(p, x, r, part);
     else
         residual_fast_kernel<4><<<grid, block, rsmem<4>(), s>>>(p, x, r, part);

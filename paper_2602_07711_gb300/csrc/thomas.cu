@@ -15,6 +15,8 @@
 // This partitioned kernel solves the systems when no set-up factors exist; every EigT and PFFT context
 // factorises its systems at set-up, so the factorised forms below serve the solver.
 #include "common.cuh"
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 namespace {
 
@@ -444,12 +446,48 @@ constexpr int ZPB = 6;   // ring depth (blocks) of the pivot-recomputing kernel
 constexpr size_t ZPIV_SMEM = (size_t)ZPB * ZU2 * ZRT * sizeof(float4);   // 48 KiB
 __device__ __forceinline__ void zwait_piv() { asm volatile("cp.async.wait_group %0;\n" ::"n"(ZPB - 1) : "memory"); }
 
+__device__ __forceinline__ void zcp8(void* smem, const void* gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+// a pair of lines' complex values from / to four 16-bit values (memory order re0, im0, re1, im1), H = 1 BF16,
+// 2 FP16 (clamped to the finite range); widening is exact
+template <int H>
+__device__ __forceinline__ float4 h4_to_f4(uint2 w) {
+    if (H == 2) {
+        const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&w.x));
+        const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&w.y));
+        return make_float4(a.x, a.y, b.x, b.y);
+    }
+    return make_float4(__uint_as_float(w.x << 16), __uint_as_float(w.x & 0xFFFF0000u), __uint_as_float(w.y << 16),
+                       __uint_as_float(w.y & 0xFFFF0000u));
+}
+template <int H>
+__device__ __forceinline__ uint32_t zpack16(float lo, float hi) {
+    if (H == 2) {
+        const __half2 v = __floats2half2_rn(fminf(fmaxf(lo, -65504.f), 65504.f), fminf(fmaxf(hi, -65504.f), 65504.f));
+        return *reinterpret_cast<const uint32_t*>(&v);
+    }
+    const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<const uint32_t*>(&v);
+}
+
+// H (1 BF16, 2 FP16): y read and x written (times oscale) in 16 bits (uint2 per line pair), the forward
+// values d kept in FP32 in dscr (a complex64-sized grid of the caller); H = 0: float4 in and out and
+// dscr = out (d over the output).
+template <int H>
 __global__ void __launch_bounds__(ZRT, 4) zsolve_piv_kernel(int nx, int ny, int nz, float zz, float2 gz,
                                                            const float2* __restrict__ dxs,
                                                            const float2* __restrict__ dys,
-                                                           const float2* __restrict__ cz, const float4* in, float4* out,
-                                                           float4* __restrict__ ck, int nb) {
+                                                           const float2* __restrict__ cz, const void* inv, void* outv,
+                                                           float4* dscr, float4* __restrict__ ck, int nb,
+                                                           float oscale = 1.f) {
+    constexpr bool BF = H != 0;
     extern __shared__ float4 zsm[];   // [ZPB * ZU2][ZRT]
+    const float4* in = reinterpret_cast<const float4*>(inv);
+    const uint2* inb = reinterpret_cast<const uint2*>(inv);
+    float4* out = BF ? dscr : reinterpret_cast<float4*>(outv);   // where d goes (and comes back from)
+    uint2* outb = reinterpret_cast<uint2*>(outv);
     const int tid = threadIdx.x;
     const int hx = nx / 2, npairs = hx * ny, nall = npairs * nb;
     const int nblk = (nz + ZU2 - 1) / ZU2;
@@ -472,6 +510,18 @@ __global__ void __launch_bounds__(ZRT, 4) zsolve_piv_kernel(int nx, int ny, int 
             }
             zcommit();
         };
+        // the same for the BF16 input (8 bytes per step into the first half of a slot)
+        auto fetch_in = [&](int blk, int pos) {
+            if (!BF) { fetch(in, blk, pos); return; }
+            if (blk >= 0 && blk < nblk) {
+#pragma unroll
+                for (int u = 0; u < ZU2; ++u) {
+                    const int l = blk * ZU2 + u;
+                    if (l < nz) zcp8(slot((pos % ZPB) * ZU2 + u), inb + voff + off + (size_t)l * plane);
+                }
+            }
+            zcommit();
+        };
         // one pivot step of both lines: m_l and the new c'_l from c'_{l-1}
         auto pivots = [&](int l, float2& c0, float2& c1, float2& m0, float2& m1) {
             const float a = l == 0 ? 0.f : (l == nz - 1 ? zz : 1.f);
@@ -482,15 +532,17 @@ __global__ void __launch_bounds__(ZRT, 4) zsolve_piv_kernel(int nx, int ny, int 
             m1 = zpivot(s1, czl, end, gz, a, sup, c1);
         };
         // ---- forward: d_l = (y_l - a_l d_{l-1}) m_l
-        for (int b = 0; b < ZPB - 1; ++b) fetch(in, b, b);
+        for (int b = 0; b < ZPB - 1; ++b) fetch_in(b, b);
         float2 d0 = f2(0.f, 0.f), d1 = d0, c0 = d0, c1 = d0;
         for (int b = 0; b < nblk; ++b) {
-            fetch(in, b + ZPB - 1, b + ZPB - 1);
+            fetch_in(b + ZPB - 1, b + ZPB - 1);
             zwait_piv();   // block b has landed
             ck[(size_t)b * nall + prb] = make_float4(c0.x, c0.y, c1.x, c1.y);
             float4 y[ZU2];
 #pragma unroll
-            for (int u = 0; u < ZU2; ++u) y[u] = *slot((b % ZPB) * ZU2 + u);
+            for (int u = 0; u < ZU2; ++u)
+                y[u] = BF ? h4_to_f4<H>(*reinterpret_cast<const uint2*>(slot((b % ZPB) * ZU2 + u)))
+                          : *slot((b % ZPB) * ZU2 + u);
 #pragma unroll
             for (int u = 0; u < ZU2; ++u) {
                 const int l = b * ZU2 + u;
@@ -532,7 +584,10 @@ __global__ void __launch_bounds__(ZRT, 4) zsolve_piv_kernel(int nx, int ny, int 
                     const float sup = l == nz - 1 ? 0.f : (l == 0 ? zz : 1.f);
                     x0 = zbwd(f2(dv.x, dv.y), m0[u], x0, sup);
                     x1 = zbwd(f2(dv.z, dv.w), m1[u], x1, sup);
-                    out[voff + off + (size_t)l * plane] = make_float4(x0.x, x0.y, x1.x, x1.y);
+                    if (BF)
+                        outb[voff + off + (size_t)l * plane] =
+                            make_uint2(zpack16<H>(oscale * x0.x, oscale * x0.y), zpack16<H>(oscale * x1.x, oscale * x1.y));
+                    else out[voff + off + (size_t)l * plane] = make_float4(x0.x, x0.y, x1.x, x1.y);
                 }
             }
         }
@@ -654,25 +709,64 @@ helm_status launch_zsolve(helm_ctx* c, const float2* in, float2* out, cudaStream
             helm_status st;
             if ((st = zsolve_reserve(c, slot + nb)) != HELM_OK) return st;
         }
-        if (!c->zpiv_ready) {
-            HELM_CUDA_TRY(cudaFuncSetAttribute(zsolve_piv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        if (!(c->zpiv_ready & 1)) {
+            HELM_CUDA_TRY(cudaFuncSetAttribute(zsolve_piv_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                (int)ZPIV_SMEM));
-            c->zpiv_ready = 1;
+            c->zpiv_ready |= 1;
         }
         prof_begin(c, s, PROF_ZSOLVE);
         const int sms = c->zring_sms;
         const int need = (npairs + ZRT - 1) / ZRT;
         const int cap = sms * 2 * c->tune_zring;   // tune_zring 1..3: 2, 4 or 6 CTAs per SM (at most 4 resident)
         const int grid = need < cap ? need : cap;
-        zsolve_piv_kernel<<<grid, ZRT, ZPIV_SMEM, s>>>(c->nx, c->ny, c->nz, (float)c->zeta[2],
-                                                        make_float2((float)c->gam[2].x, (float)c->gam[2].y), c->dxs,
-                                                        c->dys, c->cz, reinterpret_cast<const float4*>(in),
-                                                        reinterpret_cast<float4*>(out),
-                                                        reinterpret_cast<float4*>(c->zck) + (size_t)slot * zsolve_ck_bytes(c, 1) / sizeof(float4),
-                                                        nb);
+        zsolve_piv_kernel<0><<<grid, ZRT, ZPIV_SMEM, s>>>(c->nx, c->ny, c->nz, (float)c->zeta[2],
+                                                               make_float2((float)c->gam[2].x, (float)c->gam[2].y), c->dxs,
+                                                               c->dys, c->cz, in, out, reinterpret_cast<float4*>(out),
+                                                               reinterpret_cast<float4*>(c->zck) + (size_t)slot * zsolve_ck_bytes(c, 1) / sizeof(float4),
+                                                               nb);
         prof_end(c, s);
         HELM_CUDA_TRY(cudaGetLastError());
         return HELM_OK;
     }
     return launch_zsolve_fact(c, c->zfac, in, out, nullptr, nullptr, s, nb);
+}
+
+// The z-solves of the 16-bit transform chain (HELM_PREC_BF16, HELM_PREC_FP16): the pivot-recomputing kernel
+// with 16-bit y and x (in may equal out; x scaled by oscale) and the FP32 forward values in dscr (npts * nb
+// complex64 of the caller).  No fallback: a launch under stream capture without reserved checkpoints
+// returns HELM_ERR_UNSUPPORTED.
+helm_status launch_zsolve_h16(helm_ctx* c, const void* in, void* out, float4* dscr, float oscale, cudaStream_t s, int nb) {
+    const int H = c->opt.precision == HELM_PREC_FP16 ? 2 : 1;
+    if (c->nx % 2 != 0 || c->zring_sms <= 0) return HELM_ERR_UNSUPPORTED;
+    const int slot = c->zck_slot;
+    if (zsolve_ck_bytes(c, slot + nb) > c->zck_bytes) {
+        cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+        HELM_CUDA_TRY(cudaStreamIsCapturing(s, &cap));
+        if (cap != cudaStreamCaptureStatusNone) return HELM_ERR_UNSUPPORTED;
+        helm_status st;
+        if ((st = zsolve_reserve(c, slot + nb)) != HELM_OK) return st;
+    }
+    if (!(c->zpiv_ready & (2 << (H - 1)))) {
+        if (H == 2)
+            HELM_CUDA_TRY(cudaFuncSetAttribute(zsolve_piv_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ZPIV_SMEM));
+        else
+            HELM_CUDA_TRY(cudaFuncSetAttribute(zsolve_piv_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ZPIV_SMEM));
+        c->zpiv_ready |= 2 << (H - 1);
+    }
+    prof_begin(c, s, PROF_ZSOLVE);
+    const int npairs = c->nx / 2 * c->ny * nb;
+    const int need = (npairs + ZRT - 1) / ZRT;
+    const int cap = c->zring_sms * 2 * (c->tune_zring > 0 ? c->tune_zring : 1);
+    const int grid = need < cap ? need : cap;
+    float4* ck = reinterpret_cast<float4*>(c->zck) + (size_t)slot * zsolve_ck_bytes(c, 1) / sizeof(float4);
+    const float2 gz = make_float2((float)c->gam[2].x, (float)c->gam[2].y);
+    if (H == 2)
+        zsolve_piv_kernel<2><<<grid, ZRT, ZPIV_SMEM, s>>>(c->nx, c->ny, c->nz, (float)c->zeta[2], gz, c->dxs, c->dys, c->cz,
+                                                           in, out, dscr, ck, nb, oscale);
+    else
+        zsolve_piv_kernel<1><<<grid, ZRT, ZPIV_SMEM, s>>>(c->nx, c->ny, c->nz, (float)c->zeta[2], gz, c->dxs, c->dys, c->cz,
+                                                           in, out, dscr, ck, nb, oscale);
+    prof_end(c, s);
+    HELM_CUDA_TRY(cudaGetLastError());
+    return HELM_OK;
 }

@@ -15,7 +15,7 @@ library_path = os.path.join(HERE, "libhelm.so")
 
 HELM_PRECOND_NONE, HELM_PRECOND_EIGT, HELM_PRECOND_PFFT, HELM_PRECOND_FFT2 = 0, 1, 2, 3
 HELM_CLOSURE_THREE_POINT, HELM_CLOSURE_HIGH_ORDER = 0, 1
-HELM_PREC_FP32, HELM_PREC_TF32, HELM_PREC_TF32X3 = 0, 1, 2
+HELM_PREC_FP32, HELM_PREC_TF32, HELM_PREC_TF32X3, HELM_PREC_BF16, HELM_PREC_FP16 = 0, 1, 2, 3, 4
 HELM_C64, HELM_C128 = 0, 1
 
 STATUS = {0: "HELM_OK", 1: "HELM_ERR_ARG", 2: "HELM_ERR_CUDA", 3: "HELM_ERR_NOMEM", 4: "HELM_ERR_EIG",

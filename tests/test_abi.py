@@ -60,16 +60,17 @@ def test_setup_rejects_bad_arguments_without_gpu_work(libpath):
 
 
 def test_setup_checks_the_precision_and_the_wait_limit_without_gpu_work(libpath):
-    """HELM_PREC_FP32, _TF32 and _TF32X3 (the three-product split) are the arithmetic modes; anything else is
-    rejected before any device work, as is a wait limit without a context or below zero."""
+    """HELM_PREC_FP32, _TF32, _TF32X3 (the three-product split), _BF16 and _FP16 are the arithmetic modes; anything
+    else is rejected before any device work, as is a wait limit without a context or below zero."""
     from paper_2602_07711_gb300 import helm
     import numpy as np
     L = helm.lib()
     ctx = ctypes.c_void_p()
     g = helm.helm_grid(8, 8, 8, 1.0, 1.0, 1.0, 0)
     k2 = np.zeros(512, np.complex128)
-    assert (helm.HELM_PREC_FP32, helm.HELM_PREC_TF32, helm.HELM_PREC_TF32X3) == (0, 1, 2)
-    for precision in (-1, 3):
+    assert (helm.HELM_PREC_FP32, helm.HELM_PREC_TF32, helm.HELM_PREC_TF32X3, helm.HELM_PREC_BF16,
+            helm.HELM_PREC_FP16) == (0, 1, 2, 3, 4)
+    for precision in (-1, 5):
         o = helm.helm_options(4, helm.HELM_PRECOND_PFFT, precision, 30, 100, 1e-6, 1, 0)
         assert L.helm_setup(ctypes.byref(g), k2.ctypes.data, 1.0, None, ctypes.byref(o), None,
                             ctypes.byref(ctx)) == 1

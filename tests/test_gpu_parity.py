@@ -98,9 +98,14 @@ def test_every_matvec_variant_matches_oracle(order, real):
 
 
 @pytest.mark.parametrize("order", [4, 6])
-def test_build_rhs_matches_oracle(order):
+@pytest.mark.parametrize("real", [False, True])
+def test_build_rhs_matches_oracle(order, real):
+    """On a real medium the sixth-order right-hand side takes its real form (k^2 from the residual's
+    real field, real gradients)."""
     n, L = (40, 36, 33), (1.0, 0.9, 0.825)
     g, k2, k0 = _medium(n, L)
+    if real:
+        k2 = k2.real + 0j
     f = _rand(g.shape, 2)
     S = Solver(n, k2, k0, order=order, L=L)
     F = S.build_rhs(_dev(f)).cpu().numpy()
@@ -230,6 +235,48 @@ def test_residual_resolves_small_residuals(order):
     assert ref2 < 1e-6 * np.linalg.norm(F)
     assert abs(n2 - ref2) <= 0.02 * ref2, (n2, ref2)
     assert abs(ni - np.abs(r_ref).max()) <= 0.05 * np.abs(r_ref).max()
+
+
+@pytest.mark.parametrize("order,n,L,complex_k", [
+    (6, (40, 36, 33), (1.0, 0.9, 0.825), False),   # real medium: the two-row compensated-sum kernel
+    (6, (70, 20, 65), (1.0, 20 / 70, 65 / 70), False),
+    (6, (40, 36, 33), (1.0, 0.9, 0.825), True),    # complex medium: the renormalised double-float kernel
+    (4, (40, 36, 33), (1.0, 0.9, 0.85), False),
+])
+def test_residual_vector_matches_oracle_elementwise(order, n, L, complex_k):
+    """r = F - A x of helm_residual against the FP64 oracle at every point, for F = A x + d with
+    |d| ~ 1e-9 |A x| (so that F - A x cancels nine digits).  x is a plane wave modulated by a smooth envelope
+    plus a small random part, nonzero on the boundary (every ghost factor is used).  Bound per point:
+    the complex64 rounding of r (2^-23 |r|) plus the double-float error, 1e-11 h^-2 max|x|: ~40 additions
+    of error <= 2^-44 of the terms' magnitudes, which sum to about 8.5 h^-2 |x|, plus, at order 6, the FP32
+    rounding of the gradient terms (h/20) g_d D_d that both kernels take from the leading parts, 2^-19
+    (h/20) sum_d |g_d| max|x| at the point (D_d sums ~10 FP32 terms of size |x|: error ~2^-20.4 |x|).
+    FP32 arithmetic for the whole operator would miss the bound by three orders of magnitude (2^-24 x 8.5
+    h^-2 |x|).  The norms follow from the same bound by the triangle inequality."""
+    g, k2, k0 = _medium(n, L)
+    if not complex_k:
+        k2 = k2.real + 0j
+    X, Y, Z = g.mesh()
+    x = np.exp(1j * k0 * (0.6 * X + 0.48 * Y + 0.64 * Z)) * (1 + 0.3 * np.sin(5 * X + 2 * Y) * np.cos(3 * Z))
+    x = x + 1e-3 * _rand(g.shape, 21)
+    A = Operator(g, k2, k0, order)
+    Ax = A(x)
+    F = Ax + 1e-9 * np.abs(Ax).max() * _rand(g.shape, 22)
+    r_ref = F - A(x)
+    S = Solver(n, k2, k0, order=order, L=L)
+    r = torch.empty(g.shape, dtype=torch.complex64, device="cuda")
+    from paper_2602_07711_gb300 import helm
+    n2, ni = helm.helm_residual(S.ctx, _dev(F), _dev(x), r)
+    S.close()
+    rg = r.cpu().numpy().astype(np.complex128)
+    bound = 2.0 ** -23 * np.abs(r_ref) + 1e-11 * np.abs(x).max() / g.h[0] ** 2
+    if order == 6:
+        dk2, _ = derived_k2_fields(k2, True, g.h)
+        bound = bound + 2.0 ** -19 * (g.h[0] / 20) * sum(np.abs(d) for d in dk2) * np.abs(x).max()
+    err = np.abs(rg - r_ref)
+    assert np.all(err <= bound), (float((err / bound).max()), float(np.abs(r_ref).max()))
+    assert abs(n2 - np.linalg.norm(r_ref)) <= np.linalg.norm(bound)
+    assert abs(ni - np.abs(r_ref).max()) <= bound.max()
 
 
 @pytest.mark.parametrize("rtol", [1e-6, 1e-8])
