@@ -136,8 +136,14 @@ def algorithmic(n, order, cycles_iters, real_medium=False, precision="tf32"):
     db = ub = 0
     for k in cycles_iters:
         for j in range(k):
-            db += 8 * (j + 2) * pts        # j+1 basis vectors + w
-            ub += 8 * (j + 3) * pts        # j+1 basis vectors + w read, w written
+            if precision == "fp16":
+                # FP16 basis: j+1 basis vectors at 4 B/pt, w (complex64) once per group of eight vectors;
+                # the update reads them and w and writes only the new FP16 vector
+                db += (4 * (j + 1) + 8 * ((j + 8) // 8)) * pts
+                ub += (4 * (j + 1) + 8 + 4) * pts
+            else:
+                db += 8 * (j + 2) * pts        # j+1 basis vectors + w
+                ub += 8 * (j + 3) * pts        # j+1 basis vectors + w read, w written
     out["dots"] = {"bytes": db, "launches": its}
     out["update"] = {"bytes": ub, "launches": its}
     return out
@@ -158,7 +164,9 @@ def peaks():
 # unchanged: (class, n, order) -> bytes.  On the 20-bump medium (no attenuation: the real-medium matvec)
 # with restart cycles of 17 + 8 steps: dots_pipe_kernel<4>/<8> 1202.8 MB per launch averaged over the 25
 # launches of a solve (1148.8 MB algorithmic); stencil_fast_kernel<6,3,real> 471.9 MB read + 116.7 MB written.
-MEASURED_TRAFFIC = {("dots", 256, 6): 1202.8e6, ("stencil", 256, 6): 592.5e6}
+# DRAM bytes per launch from an ncu capture of the named kernel class (256^3, order 6), per precision mode
+MEASURED_TRAFFIC = {("dots", 256, 6, "tf32"): 1202.8e6, ("stencil", 256, 6, "tf32"): 592.5e6,
+                    ("stencil", 256, 6, "fp16"): 592.5e6}
 
 
 def roofline(prof_ms, prof_launch, alg, precision, order, n=None, variant=None):
@@ -189,7 +197,7 @@ def roofline(prof_ms, prof_launch, alg, precision, order, n=None, variant=None):
     peak = pk["hbm_gbs"]
     ach = a["bytes"] / a["launches"] / avg_s / 1e9
     return {"kernel": cls, "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
-            "traffic": MEASURED_TRAFFIC.get((cls, n, order)) if variant == "default" else None,
+            "traffic": MEASURED_TRAFFIC.get((cls, n, order, precision)) if variant == "default" else None,
             "peak_source": src + " hbm_gbs",
             "algorithmic_bytes_per_launch": a["bytes"] / a["launches"]}
 
@@ -297,8 +305,8 @@ def run_ours(args, rank, world, local):
     dev = torch.device("cuda", local)
     n, order = args.n, args.order
     precision = args.precision
-    if precision == "auto":
-        precision = "tf32"
+    if precision == "auto":   # the FP16 chain (N_x a multiple of 4), else TF32
+        precision = "fp16" if n % 4 == 0 else "tf32"
     k2, f, k0 = media.bumps(n, 3, 4, device=dev, as_numpy=False)
     real_medium = bool((k2.imag == 0).all())
     stream = torch.cuda.current_stream()

@@ -212,6 +212,8 @@ helm_status tc_xpass_h16(helm_ctx* c, int inverse, const void* in, void* out, in
                          const double* alpha_dev, int aidx, cudaStream_t s, int nb = 1, int astride = 0);
 helm_status tc_ypass_h16(helm_ctx* c, int inverse, const void* in, void* out, float alpha, cudaStream_t s, int nb = 1);
 helm_status h16_scales(helm_ctx* c, cudaStream_t s);
+helm_status precond_h16_basis(helm_ctx* c, const uint16_t* V16, float2* z, const double* cs, int cidx, cudaStream_t s);
+helm_status to_h16_basis(helm_ctx* c, const float2* r, uint16_t* V16, const double* sigma, int sidx, cudaStream_t s);
 helm_status launch_zsolve_h16(helm_ctx* c, const void* in, void* out, float4* dscr, float oscale, cudaStream_t s,
                               int nb = 1);
 // operand sets of tc_xpass/tc_ypass (`inverse`): 0/1 EigT forward/inverse, 2/3 PFFT sine forward/inverse

@@ -10,6 +10,7 @@
 // The iterate x is complex128.  Each cycle ends with the FP64 true residual r = F - A x (Sec. 5.1 rel-res),
 // which decides convergence and seeds the next cycle.
 #include "common.cuh"
+#include <cuda_fp16.h>
 #include "dfloat.cuh"
 #include <algorithm>
 #include <chrono>
@@ -41,10 +42,15 @@ struct Ctrl {
 // and single-inclusion media from 100^3 to 400^3, 1e-4 gave the shortest solves of 1e-5 ... 1e-2.
 // In terms of est = |g_{j+1}| / beta_0: stop when est <= max(rtol, kInnerFloor * beta_k / beta_0).
 constexpr double kInnerFloor = 1e-4;
-__host__ __device__ inline double inner_threshold(double rtol, double beta_k, double beta0) {
-    const double f = beta0 > 0 ? kInnerFloor * beta_k / beta0 : 0.0;
+__host__ __device__ inline double inner_threshold(double rtol, double beta_k, double beta0, double floor = kInnerFloor) {
+    const double f = beta0 > 0 ? floor * beta_k / beta0 : 0.0;
     return rtol > f ? rtol : f;
 }
+// The FP16 Krylov basis (HELM_PREC_FP16, flexible single solves) holds each basis vector to 2^-11 relative,
+// so the Arnoldi relation itself is exact only to a few 1e-4 and a cycle cannot lower the residual by
+// 1e-4 reliably; its cycles stop at 1e-3 (measured on the 20-bump medium: the FP16 basis then needs no more
+// inner iterations than the complex64 one at 128^3, two more with 1e-4 cycles).
+constexpr double kInnerFloorH16 = 1e-3;
 
 struct KrylovWork {
     int m = 0, flexible = 0, NB = 0, nres = 0;
@@ -72,6 +78,10 @@ struct KrylovWork {
     unsigned* nzflag = nullptr;
     Ctrl* slots_h = nullptr;         // pinned [m]: the controls after each iteration of a cycle
     cudaEvent_t* ev_slot = nullptr;  // [m]: recorded after each slot's copy
+    // FP16 basis: v_i = c16[i] V16_i, V16 (m+1) FP16 grids of 2 npts halves; w16s = s0 / ||w|| of the step
+    uint16_t* V16 = nullptr;
+    double* c16 = nullptr;           // [m+1]
+    double* w16s = nullptr;          // [1]
 };
 
 namespace {
@@ -327,6 +337,188 @@ __global__ void __launch_bounds__(NT) update_kernel(const float2* __restrict__ V
     update_body(V, npts, nv, coef, w, part, ld, vs);
 }
 
+// ---- FP16 Krylov basis (HELM_PREC_FP16, flexible single solves) ------------------------------------
+// v_i = c16[i] V16_i with V16_i an FP16 grid (two complex points per 8-byte load); w stays complex64.
+// Inner products conj(V16_i) . w for i < nv and ||w||^2 (slot nv of part) in one pass.  Packed f32x2
+// arithmetic: with v = (vr, vi) and the broadcast pairs (wr, wr), (wi, wi) of the point (formed once per
+// point for all G vectors), P += v (wr, wr) and Q += v (wi, wi) per vector, and at the end
+// conj(v) w = (P.x + Q.y, Q.x - P.y): two FMA2 per vector and point.  Plain FP32 sums per thread (a basis
+// held to 2^-11 needs no compensation), FP64 across threads.
+__device__ __forceinline__ float2 h2f(uint32_t u) { return __half22float2(*reinterpret_cast<const __half2*>(&u)); }
+template <int G>
+__global__ void __launch_bounds__(NT) dots16_kernel(const uint16_t* __restrict__ V16, size_t npts, int nv,
+                                                   const float2* __restrict__ w, double2* __restrict__ part, int ld) {
+    __shared__ double2 red[NT / 32][G + 1];
+    const int tid = threadIdx.x;
+    const size_t n4 = npts / 2;
+    const size_t stride = (size_t)gridDim.x * NT;
+    const float4* __restrict__ W4 = reinterpret_cast<const float4*>(w);
+    for (int g0 = 0; g0 < nv; g0 += G) {
+        const int ng = min(G, nv - g0);
+        const bool first = g0 == 0;
+        float2 P[G], Q[G];
+        float2 nn = make_float2(0.f, 0.f);   // ||w||^2 (first group)
+        const uint2* __restrict__ V2[G];
+#pragma unroll
+        for (int q = 0; q < G; ++q) {
+            P[q] = make_float2(0.f, 0.f);
+            Q[q] = make_float2(0.f, 0.f);
+            V2[q] = reinterpret_cast<const uint2*>(V16 + (size_t)(g0 + (q < ng ? q : 0)) * 2 * npts);
+        }
+        size_t id = blockIdx.x * (size_t)NT + tid;
+        float4 wa = make_float4(0.f, 0.f, 0.f, 0.f);
+        uint2 va[G];
+#pragma unroll
+        for (int q = 0; q < G; ++q) va[q] = make_uint2(0u, 0u);
+        if (id < n4) {
+            wa = W4[id];
+#pragma unroll
+            for (int q = 0; q < G; ++q) if (q < ng) va[q] = V2[q][id];
+        }
+        for (; id < n4; id += stride) {
+            const size_t nid = id + stride;
+            float4 wb = make_float4(0.f, 0.f, 0.f, 0.f);
+            uint2 vb[G];
+#pragma unroll
+            for (int q = 0; q < G; ++q) vb[q] = make_uint2(0u, 0u);
+            if (nid < n4) {
+                wb = W4[nid];
+#pragma unroll
+                for (int q = 0; q < G; ++q)
+                    if (q < ng) vb[q] = V2[q][nid];
+            }
+            const float2 r0 = bc2(wa.x), i0 = bc2(wa.y), r1 = bc2(wa.z), i1 = bc2(wa.w);
+#pragma unroll
+            for (int q = 0; q < G; ++q) {
+                const float2 v0 = h2f(va[q].x), v1 = h2f(va[q].y);
+                P[q] = fma2(v1, r1, fma2(v0, r0, P[q]));
+                Q[q] = fma2(v1, i1, fma2(v0, i0, Q[q]));
+            }
+            if (first) nn = fma2(make_float2(wa.z, wa.w), make_float2(wa.z, wa.w), fma2(make_float2(wa.x, wa.y), make_float2(wa.x, wa.y), nn));
+            wa = wb;
+#pragma unroll
+            for (int q = 0; q < G; ++q) va[q] = vb[q];
+        }
+        double2 acc[G + 1];
+#pragma unroll
+        for (int q = 0; q < G; ++q) acc[q] = make_double2((double)P[q].x + (double)Q[q].y, (double)Q[q].x - (double)P[q].y);
+        acc[G] = make_double2((double)nn.x + (double)nn.y, 0.0);
+#pragma unroll
+        for (int q = 0; q <= G; ++q)
+            for (int o = 16; o > 0; o >>= 1) {
+                acc[q].x += __shfl_down_sync(0xffffffffu, acc[q].x, o);
+                acc[q].y += __shfl_down_sync(0xffffffffu, acc[q].y, o);
+            }
+        if ((tid & 31) == 0)
+#pragma unroll
+            for (int q = 0; q <= G; ++q) red[tid >> 5][q] = acc[q];
+        __syncthreads();
+        if (tid < ng || (first && tid == G)) {
+            double2 sum = make_double2(0, 0);
+            for (int wi = 0; wi < NT / 32; ++wi) { sum.x += red[wi][tid].x; sum.y += red[wi][tid].y; }
+            part[(size_t)blockIdx.x * ld + (tid == G ? nv : g0 + tid)] = sum;
+        }
+        __syncthreads();
+    }
+}
+// blocks i < nv: h_i = c16[i] sum_b part[b][i], coef_i = c16[i] h_i; block nv: w16s = s0 / ||w||
+__global__ void reduce16_kernel(const double2* __restrict__ part, int NB, int ld, int nv, const double* __restrict__ c16,
+                                double2* __restrict__ Hcol, float2* __restrict__ coef, float s0, double* __restrict__ w16s) {
+    __shared__ double rx[32], ry[32];
+    const int i = blockIdx.x;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    double sx = 0, sy = 0;
+    for (int b = threadIdx.x; b < NB; b += blockDim.x) {
+        const double2 v = part[(size_t)b * ld + i];
+        sx += v.x;
+        sy += v.y;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        sx += __shfl_down_sync(0xffffffffu, sx, o);
+        sy += __shfl_down_sync(0xffffffffu, sy, o);
+    }
+    if (lane == 0) { rx[wid] = sx; ry[wid] = sy; }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    sx = 0;
+    sy = 0;
+    for (int w = 0; w < nw; ++w) { sx += rx[w]; sy += ry[w]; }
+    if (i == nv) {
+        const double nr = sqrt(sx);
+        w16s[0] = nr > 0.0 ? (double)s0 / nr : 0.0;
+        return;
+    }
+    const double cg = c16[i];
+    const double2 h = make_double2(sx * cg, sy * cg);
+    Hcol[i] = h;
+    coef[i] = make_float2((float)(h.x * cg), (float)(h.y * cg));
+}
+// V16_out = FP16(w16s (w - sum_i coef_i V16_i)) (clamped to the finite range; ||.||_F <= s0 since the
+// projection does not lengthen w); per-block partial ||w - sum||^2 in part[blk * ld].x.  Packed form: with
+// the broadcast pairs (cr, cr), (ci, ci) of each coefficient (staged in shared memory), T1 += v (cr, cr),
+// T2 += v (ci, ci), and sum coef_i v_i = (T1.x - T2.y, T1.y + T2.x).
+__global__ void __launch_bounds__(NT) update16_kernel(const uint16_t* __restrict__ V16, size_t npts, int nv,
+                                                     const float2* __restrict__ coef, const float2* __restrict__ w,
+                                                     uint16_t* __restrict__ Vout, const double* __restrict__ w16s,
+                                                     double2* __restrict__ part, int ld) {
+    __shared__ float4 cf[72];   // (cr, cr, ci, ci)
+    __shared__ double red[NT / 32];
+    for (int i = threadIdx.x; i < nv; i += NT) cf[i] = make_float4(coef[i].x, coef[i].x, coef[i].y, coef[i].y);
+    __syncthreads();
+    const float sc = (float)w16s[0];
+    float2 nn = make_float2(0.f, 0.f);
+    const size_t n4 = npts / 2;
+    const float4* W4 = reinterpret_cast<const float4*>(w);
+    uint2* O2 = reinterpret_cast<uint2*>(Vout);
+    for (size_t id = blockIdx.x * (size_t)NT + threadIdx.x; id < n4; id += (size_t)gridDim.x * NT) {
+        const float4 x = W4[id];
+        float2 A0 = make_float2(0.f, 0.f), B0 = A0, A1 = A0, B1 = A0;   // T1, T2 of the two points
+        int i = 0;
+        for (; i + 4 <= nv; i += 4) {
+            uint2 u[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) u[q] = reinterpret_cast<const uint2*>(V16 + (size_t)(i + q) * 2 * npts)[id];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const float4 c = cf[i + q];
+                const float2 v0 = h2f(u[q].x), v1 = h2f(u[q].y);
+                A0 = fma2(v0, make_float2(c.x, c.y), A0);
+                B0 = fma2(v0, make_float2(c.z, c.w), B0);
+                A1 = fma2(v1, make_float2(c.x, c.y), A1);
+                B1 = fma2(v1, make_float2(c.z, c.w), B1);
+            }
+        }
+        for (; i < nv; ++i) {
+            const uint2 u = reinterpret_cast<const uint2*>(V16 + (size_t)i * 2 * npts)[id];
+            const float4 c = cf[i];
+            const float2 v0 = h2f(u.x), v1 = h2f(u.y);
+            A0 = fma2(v0, make_float2(c.x, c.y), A0);
+            B0 = fma2(v0, make_float2(c.z, c.w), B0);
+            A1 = fma2(v1, make_float2(c.x, c.y), A1);
+            B1 = fma2(v1, make_float2(c.z, c.w), B1);
+        }
+        const float2 y0 = make_float2(x.x - (A0.x - B0.y), x.y - (A0.y + B0.x));
+        const float2 y1 = make_float2(x.z - (A1.x - B1.y), x.w - (A1.y + B1.x));
+        const __half2 a = __floats2half2_rn(fminf(fmaxf(sc * y0.x, -65504.f), 65504.f), fminf(fmaxf(sc * y0.y, -65504.f), 65504.f));
+        const __half2 b = __floats2half2_rn(fminf(fmaxf(sc * y1.x, -65504.f), 65504.f), fminf(fmaxf(sc * y1.y, -65504.f), 65504.f));
+        O2[id] = make_uint2(*reinterpret_cast<const uint32_t*>(&a), *reinterpret_cast<const uint32_t*>(&b));
+        nn = fma2(y1, y1, fma2(y0, y0, nn));
+    }
+    double acc = (double)nn.x + (double)nn.y;
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double sum = 0;
+        for (int wi = 0; wi < NT / 32; ++wi) sum += red[wi];
+        part[(size_t)blockIdx.x * ld] = make_double2(sum, 0.0);
+    }
+}
+// c16[j] = sigma[j] / w16s (v_j = sigma_j (w - sum) = c16[j] V16_j); j = 0 (a restart): c16[0] = 1 / s0
+__global__ void c16_kernel(const double* __restrict__ sigma, int j, const double* __restrict__ w16s, double* c16, float s0) {
+    if (threadIdx.x == 0) c16[j] = j == 0 ? 1.0 / (double)s0 : (w16s[0] > 0.0 ? sigma[j] / w16s[0] : 0.0);
+}
+
 __device__ inline void givens(double2 a, double2 b, double& c, double2& s) {
     const double ab = hypot(b.x, b.y);
     if (ab == 0.0) { c = 1.0; s = make_double2(0, 0); return; }
@@ -383,9 +575,15 @@ __device__ __forceinline__ void givens_body(const double2* __restrict__ part, in
     ctrl->hnext = hn;
     if (!isfinite(hn) || !isfinite(est) || !isfinite(col[j].x) || !isfinite(col[j].y)) ctrl->flags |= HELM_DEV_NAN;
 }
+// (with the FP16 basis also c16[j+1] = sigma_{j+1} / w16s, the scale of V16_{j+1}: one thread after the body)
 __global__ void givens_kernel(const double2* __restrict__ part, int NB, int ld, int j, int m, double2* H, double* cs,
-                              double2* sn, double2* g, double* sigma, Ctrl* ctrl) {
+                              double2* sn, double2* g, double* sigma, Ctrl* ctrl, const double* w16s = nullptr,
+                              double* c16 = nullptr) {
     givens_body(part, NB, ld, j, m, H, cs, sn, g, sigma, ctrl);
+    if (c16 && threadIdx.x == 0) {
+        __threadfence_block();
+        c16[j + 1] = w16s[0] > 0.0 ? sigma[j + 1] / w16s[0] : 0.0;
+    }
 }
 
 // y = R^-1 g (k x k upper triangular part of the rotated H)
@@ -576,6 +774,7 @@ void free_work(KrylovWork* k) {
     cudaFree(k->g); cudaFree(k->y); cudaFree(k->part); cudaFree(k->rpart); cudaFree(k->coef); cudaFree(k->ctrl_d);
     cudaFreeHost(k->ctrl_h); cudaFree(k->xbuf); cudaFree(k->bbuf); cudaFree(k->xdf); cudaFree(k->Fdf);
     cudaFree(k->nzflag);
+    cudaFree(k->V16); cudaFree(k->c16); cudaFree(k->w16s);
     cudaFreeHost(k->slots_h);
     if (k->ev_slot) {
         for (int j = 0; j < k->m; ++j)
@@ -757,6 +956,20 @@ helm_status gmres_run(helm_ctx* c, const double2* b_in, double2* x_in, helm_solv
     int its = 0, restarts = 0;
     int cyc[16] = {0};
     helm_status result = HELM_ERR_NOT_CONVERGED;
+    // HELM_PREC_FP16, flexible, one Gram-Schmidt pass: the Krylov basis in FP16 (v_i = c16[i] V16_i), the
+    // preconditioner reading it directly, the cycles ending at kInnerFloorH16
+    const bool h16b = c->opt.precision == HELM_PREC_FP16 && flex && !c->opt.reorth && !c->net &&
+                      c->opt.precond == HELM_PRECOND_EIGT && c->tmaps;
+    const float s0 = c->h16s[0];
+    if (h16b && !k->V16) {
+        if (cudaMalloc(&k->V16, (size_t)(m + 1) * npts * 2 * sizeof(uint16_t)) != cudaSuccess ||
+            cudaMalloc(&k->c16, (m + 1) * sizeof(double)) != cudaSuccess || cudaMalloc(&k->w16s, sizeof(double)) != cudaSuccess) {
+            cudaGetLastError();
+            cudaFree(k->V16); cudaFree(k->c16); cudaFree(k->w16s);
+            k->V16 = nullptr; k->c16 = nullptr; k->w16s = nullptr;
+            return HELM_ERR_NOMEM;
+        }
+    }
     // internal double-float copies of b and x; x0 = 0 is recognised and then r0 = b without a matvec
     unsigned xnz = 0;
     HELM_CUDA_TRY(cudaMemsetAsync(k->nzflag, 0, sizeof(unsigned), s));
@@ -782,6 +995,31 @@ helm_status gmres_run(helm_ctx* c, const double2* b_in, double2* x_in, helm_solv
                 float2* w = k->V + (size_t)(j + 1) * npts;
                 float2* z = flex ? k->Z + (size_t)j * npts : k->Z;
                 helm_status e;
+                if (h16b) {
+                    float2* wv = k->V + npts;   // complex64 scratch: A z_j, orthogonalised into V16_{j+1}
+                    uint16_t* Vj = k->V16 + (size_t)j * 2 * npts;
+                    if ((e = precond_h16_basis(c, Vj, z, k->c16, j, s)) != HELM_OK) return e;
+                    if ((e = launch_stencil_f32(c, z, wv, nullptr, 0, s)) != HELM_OK) return e;
+                    prof_begin(c, s, PROF_DOTS);
+                    dots16_kernel<8><<<k->NBd, NT, 0, s>>>(k->V16, npts, j + 1, wv, k->part, ld);
+                    prof_end(c, s);
+                    prof_begin(c, s, PROF_SMALL);
+                    reduce16_kernel<<<j + 2, 128, 0, s>>>(k->part, k->NBd, ld, j + 1, k->c16, k->H + (size_t)j * (m + 1),
+                                                          k->coef, s0, k->w16s);
+                    prof_end(c, s);
+                    prof_begin(c, s, PROF_UPDATE);
+                    update16_kernel<<<ublocks, NT, 0, s>>>(k->V16, npts, j + 1, k->coef, wv, Vj + 2 * npts, k->w16s,
+                                                           k->part, ld);
+                    prof_end(c, s);
+                    prof_begin(c, s, PROF_SMALL);
+                    givens_kernel<<<1, 256, 0, s>>>(k->part, NB, ld, j, m, k->H, k->cs, k->sn, k->g, k->sigma, k->ctrl_d,
+                                                    k->w16s, k->c16);
+                    prof_end(c, s);
+                    HELM_CUDA_TRY(cudaGetLastError());
+                    HELM_CUDA_TRY(cudaMemcpyAsync(&k->slots_h[j], k->ctrl_d, sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
+                    HELM_CUDA_TRY(cudaEventRecord(k->ev_slot[j], s));
+                    return HELM_OK;
+                }
                 if ((e = precond_apply(c, vj, z, k->sigma, j, s)) != HELM_OK) return e;
                 if ((e = launch_stencil_f32(c, z, w, nullptr, 0, s)) != HELM_OK) return e;
                 const int passes = c->opt.reorth ? 2 : 1;
@@ -810,7 +1048,12 @@ helm_status gmres_run(helm_ctx* c, const double2* b_in, double2* x_in, helm_solv
             // enqueued beyond the end of the cycle leaves columns j+1.. of H and g[j+2] behind, which the
             // least-squares solve of the first kk columns does not read; the control block is restored.
             double est_prev = k->ctrl_h->beta / beta0;
-            const double thr = inner_threshold(c->opt.rtol, k->ctrl_h->beta, beta0);
+            const double thr = inner_threshold(c->opt.rtol, k->ctrl_h->beta, beta0, h16b ? kInnerFloorH16 : kInnerFloor);
+            if (h16b) {   // v_0 = r / beta into V16_0 (r is V_0 of the true residual), c16[0] = 1 / s0
+                if ((st = to_h16_basis(c, k->V, k->V16, k->sigma, 0, s)) != HELM_OK) return st;
+                c16_kernel<<<1, 32, 0, s>>>(k->sigma, 0, k->w16s, k->c16, s0);
+                HELM_CUDA_TRY(cudaGetLastError());
+            }
             for (int j = 0; j < m; ++j) {
                 if (launched <= j) {
                     if ((st = enqueue(j)) != HELM_OK) return st;

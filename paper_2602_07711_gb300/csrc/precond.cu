@@ -205,6 +205,45 @@ static helm_status precond_base(helm_ctx* c, const float2* r, float2* z, const d
     return xpass(c, 1, c->tmp, z, hz2, nullptr, 0, s);
 }
 
+// z = M^-1 v for v = cs[cidx] V16 with V16 an FP16 grid whose Frobenius norm is at most the chain's input
+// bound h16s[0] (the FP16 Krylov basis of HELM_PREC_FP16): the chain of precond_h16 without its conversion,
+// the last pass scaled by cs[cidx] h16s[0] on top of the stage factor.  z is complex64 and must not alias V16.
+helm_status precond_h16_basis(helm_ctx* c, const uint16_t* V16, float2* z, const double* cs, int cidx, cudaStream_t s) {
+    helm_status st;
+    if (c->opt.precision != HELM_PREC_FP16 || c->opt.precond != HELM_PRECOND_EIGT || c->net) return HELM_ERR_UNSUPPORTED;
+    const size_t n = c->npts;
+    uint16_t* T0 = reinterpret_cast<uint16_t*>(c->tmp);
+    uint16_t* T1 = T0 + 2 * n;
+    const float* sc = c->h16s;
+    prof_begin(c, s, PROF_XPASS);
+    st = tc_xpass_h16(c, 0, V16, T1, 1, sc[1], nullptr, 0, s);
+    prof_end(c, s);
+    if (st != HELM_OK) return st;
+    prof_begin(c, s, PROF_YPASS);
+    st = tc_ypass_h16(c, 0, T1, T0, sc[2], s);
+    prof_end(c, s);
+    if (st != HELM_OK) return st;
+    if ((st = launch_zsolve_h16(c, T0, T0, reinterpret_cast<float4*>(z), sc[3], s)) != HELM_OK) return st;
+    prof_begin(c, s, PROF_YPASS);
+    st = tc_ypass_h16(c, 1, T0, T1, sc[4], s);
+    prof_end(c, s);
+    if (st != HELM_OK) return st;
+    prof_begin(c, s, PROF_XPASS);
+    st = tc_xpass_h16(c, 1, T1, z, 0, sc[5] * sc[0], cs, cidx, s);
+    prof_end(c, s);
+    return st;
+}
+
+// complex64 r -> FP16 grid scaled by s0 sigma[sidx] (the first basis vector of a cycle)
+helm_status to_h16_basis(helm_ctx* c, const float2* r, uint16_t* V16, const double* sigma, int sidx, cudaStream_t s) {
+    prof_begin(c, s, PROF_SMALL);
+    c64_to_h16_kernel<2><<<2048, 256, 0, s>>>(reinterpret_cast<const float4*>(r), reinterpret_cast<uint2*>(V16), c->npts / 2,
+                                              c->h16s[0], sigma, sidx, nullptr);
+    prof_end(c, s);
+    HELM_CUDA_TRY(cudaGetLastError());
+    return HELM_OK;
+}
+
 // M^-1 for nb vectors back to back (the right-hand sides of a batch group): one x-pass GEMM over all their
 // rows, one y-pass over all their slices, one z-solve over all their lines.  Vector v is scaled by
 // sigma[sidx + v sstride] on the way in.  EigT or no preconditioner; the context's scratch vector must hold

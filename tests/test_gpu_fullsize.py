@@ -1,8 +1,9 @@
 """Parity at the full size of the headline workload, in the launch configuration bench.py times: 256^3,
-sixth order, the 20-bump medium of seeds 3/4 (~10 points per wavelength), TF32 EigT, FGMRES(30), rtol
-1e-6.  The FP64 oracle is evaluated on the whole field (each evaluation takes seconds on the host cores):
-the matvec element by element, the forward transform and the preconditioner in the GPU's own eigenbasis
-within the fixed TF32 bounds (measured 8.3e-4 and 1.7e-3 relative in the 2-norm at this size), the
+sixth order, the 20-bump medium of seeds 3/4 (~10 points per wavelength), FP16 EigT (the bench's default)
+and TF32 EigT, FGMRES(30), rtol 1e-6.  The FP64 oracle is evaluated on the whole field (each evaluation
+takes seconds on the host cores): the matvec element by element, the forward transform (a TF32 pass in both
+modes) and the preconditioner in the GPU's own eigenbasis within fixed bounds (TF32 measured 8.3e-4 and
+1.7e-3 relative in the 2-norm at this size; the FP16 chain's bound is that of tests/test_gpu_h16.py), the
 right-hand side, and the FP64 residual of the GPU's solution.  The solution itself is compared with the
 oracle's, solved to rel-res 1e-12, at 4096 seeded points (tests/golden/make_solution_sample.py writes them;
 the oracle's solve takes about an hour on eight host cores).
@@ -19,19 +20,24 @@ from oracle.eigt import EigT
 from oracle.grid import Grid
 from oracle.operators import Operator, derived_k2_fields
 from oracle.rhs import rhs6_sampled
-from paper_2602_07711_gb300 import HELM_PREC_TF32, Solver, media
+from paper_2602_07711_gb300 import HELM_PREC_FP16, HELM_PREC_TF32, Solver, media
 
 N = 256
+# relative bounds (2-norm, max-norm) of the whole preconditioner per mode.  FP16 measured 4.8e-3 in the
+# 2-norm at this size (1.3e-3 at 256 x 256 x 8): its stage scales come from worst-case gains (sigma(V^-1)
+# ~10 per transform, kappa(V_z) / min |lambda| ~5300 for the z-solves, whose typical gain is ~1), so at
+# N_z = 256 the typical z-solve outputs sit near the FP16 subnormal range and lose bits.
+PRECOND_BOUNDS = {HELM_PREC_TF32: (4e-3, 5e-3), HELM_PREC_FP16: (1.2e-2, 2e-2)}
 
 
-@pytest.fixture(scope="module")
-def case():
+@pytest.fixture(scope="module", params=[HELM_PREC_FP16, HELM_PREC_TF32], ids=["fp16", "tf32"])
+def case(request):
     k2, f, k0 = media.bumps(N, 3, 4)
-    S = Solver((N, N, N), k2, k0, order=6, precision=HELM_PREC_TF32, flexible=True, rtol=1e-6, restart=30,
+    S = Solver((N, N, N), k2, k0, order=6, precision=request.param, flexible=True, rtol=1e-6, restart=30,
                max_iter=300)
     g = Grid(N, N, N, staggered=True)
     A = Operator(g, k2, k0, 6)
-    yield {"k2": k2, "f": f, "k0": k0, "S": S, "g": g, "A": A}
+    yield {"k2": k2, "f": f, "k0": k0, "S": S, "g": g, "A": A, "prec": request.param}
     S.close()
 
 
@@ -64,8 +70,11 @@ def test_precond_full_size(case):
     del fwd, ref
     z = S.apply_precond(yd).cpu().numpy()
     ref = e.apply_Minv(y.astype(np.complex128)).reshape(g.shape)
-    assert np.linalg.norm(z - ref) / np.linalg.norm(ref) < 4e-3
-    assert np.abs(z - ref).max() / np.abs(ref).max() < 5e-3
+    b2, bmax = PRECOND_BOUNDS[case["prec"]]
+    print("full-size preconditioner", case["prec"], np.linalg.norm(z - ref) / np.linalg.norm(ref),
+          np.abs(z - ref).max() / np.abs(ref).max())
+    assert np.linalg.norm(z - ref) / np.linalg.norm(ref) < b2
+    assert np.abs(z - ref).max() / np.abs(ref).max() < bmax
 
 
 def test_rhs_and_solution_full_size(case):
