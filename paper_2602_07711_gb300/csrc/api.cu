@@ -41,7 +41,7 @@ void free_ctx(helm_ctx* c) {
     prof_release(c);
     void* ps[] = {c->k2_d, c->k2_f, c->dk2_d[0], c->dk2_d[1], c->dk2_d[2], c->dk2_f[0], c->dk2_f[1], c->dk2_f[2],
                   c->G_d, c->G_f, c->Dx, c->Dy, c->Vx, c->Vxi, c->Vy, c->Vyi, c->XF, c->XI, c->YF, c->YI,
-                  c->dxs, c->dys, c->cz, c->tmp, c->status_d, c->k2_df, c->G_df, c->rhs_scratch, c->zfac, c->zck, c->h16n};
+                  c->dxs, c->dys, c->cz, c->tmp, c->status_d, c->k2_df, c->G_df, c->rhs_scratch, c->zfac, c->zck, c->h16n, c->h16d};
     for (void* p : ps) if (p) cudaFree(p);
     delete c;
 }

@@ -139,6 +139,8 @@ struct helm_ctx {
     int realk = 0;
     float h16s[6] = {1.f, 1.f, 1.f, 1.f, 1.f, 1.f};   // FP16 chain: input, four stage scales, final factor
     double* h16n = nullptr;                 // FP16 chain: 1/||r||, ||r|| and partial sums (helm_apply_precond)
+    double* h16d = nullptr;                 // FP16 chain, per application: ||T1||^2, ||T2||^2, ||T3||^2, -, s2, s3, s4, 1/(s2 s3 s4)
+    float h16g[3] = {1.f, 1.f, 1.f};        // FP16 chain: norm bounds of the y-pass forward, z-solve, y-pass inverse
     void* sfast = nullptr;                  // TMA descriptors of the stencil's fixed operands (stencil_fast.cu)
     // scratch
     float2* tmp = nullptr;                  // one complex64 grid vector
@@ -209,13 +211,15 @@ helm_status tc_xpass(helm_ctx* c, int inverse, const float2* in, float2* out, fl
                      int aidx, cudaStream_t s, int nb = 1, int astride = 0);
 helm_status tc_ypass(helm_ctx* c, int inverse, const float2* in, float2* out, cudaStream_t s, int nb = 1);
 helm_status tc_xpass_h16(helm_ctx* c, int inverse, const void* in, void* out, int out_h16, float alpha,
-                         const double* alpha_dev, int aidx, cudaStream_t s, int nb = 1, int astride = 0);
-helm_status tc_ypass_h16(helm_ctx* c, int inverse, const void* in, void* out, float alpha, cudaStream_t s, int nb = 1);
+                         const double* alpha_dev, int aidx, cudaStream_t s, int nb = 1, int astride = 0,
+                         const double* alpha_dev2 = nullptr, double* nsq_out = nullptr);
+helm_status tc_ypass_h16(helm_ctx* c, int inverse, const void* in, void* out, float alpha, cudaStream_t s, int nb = 1,
+                         double* h16d = nullptr, float gain = 1.f);
 helm_status h16_scales(helm_ctx* c, cudaStream_t s);
 helm_status precond_h16_basis(helm_ctx* c, const uint16_t* V16, float2* z, const double* cs, int cidx, cudaStream_t s);
 helm_status to_h16_basis(helm_ctx* c, const float2* r, uint16_t* V16, const double* sigma, int sidx, cudaStream_t s);
 helm_status launch_zsolve_h16(helm_ctx* c, const void* in, void* out, float4* dscr, float oscale, cudaStream_t s,
-                              int nb = 1);
+                              int nb = 1, double* h16d = nullptr, float gain = 1.f);
 // operand sets of tc_xpass/tc_ypass (`inverse`): 0/1 EigT forward/inverse, 2/3 PFFT sine forward/inverse
 helm_status tc_prepare_sine(helm_ctx* c, const double2* Sx, const double2* Sy, const double2* SxT, const double2* SyT,
                             cudaStream_t s);

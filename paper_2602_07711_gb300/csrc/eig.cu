@@ -230,15 +230,17 @@ helm_status run_eig_setup(helm_ctx* c, cudaStream_t s) {
 
 // ---- stage scales of the FP16 transform chain (HELM_PREC_FP16) ------------------------------------------
 // FP16 keeps TF32's 11-bit significand but overflows above 65504, so every grid the chain stores is scaled by a
-// power of two chosen here, at set-up, from bounds that hold for any input: the chain's input is the unit
-// vector times 2^12 (the conversion applies the Arnoldi normalisation, or 1 / ||r||), and the Frobenius norm
-// of each stage's output is at most the spectral norm of its operator times that of its input.  The x-pass
+// power of two from bounds that hold for any input: the chain's input is the unit vector times 2^12 (the
+// conversion applies the Arnoldi normalisation, or 1 / ||r||), and the Frobenius norm of each stage's output
+// is at most the spectral norm of its operator times that of its input.  The first pass's scale is fixed
+// here; every later stage takes its scale at run time from its input's measured Frobenius norm times the
+// operator bound computed here, so the worst cases of the stages do not compound.  The x-pass
 // applies V_x^-T (or V_x^T), the y-pass V_y^-1 (or V_y), row- and slice-wise, so their gains are the
 // largest singular values of those matrices; the z-systems T_ij = Lbar_z + s_ij I (constant k0) diagonalise
 // as V_z (D_z + s_ij) V_z^-1, so ||T_ij^-1|| <= kappa(V_z) / min_m |d_zm + s_ij|, with s_ij = a_x d_xi +
 // a_y d_yj + h_z^2 k0^2 - 2 (a_x + a_y).  The spectral norms come from 60 power iterations (which approach
-// them from below) and take a safety factor 1.5; each stage's output bound is then brought to at most 2^15
-// (the largest element of a grid is at most its Frobenius norm), and the last pass undoes the scales.
+// them from below) and take a safety factor 1.5; each stage's output bound is brought to at most 2^15 (the
+// largest element of a grid is at most its Frobenius norm), and the last pass undoes the scales.
 namespace {
 double spec_norm_host(const std::vector<double2>& A, int n) {
     std::vector<double> xr(n), xi(n), yr(n), yi(n);
@@ -326,17 +328,14 @@ helm_status h16_scales(helm_ctx* c, cudaStream_t s) {
     lmin = std::sqrt(lmin);
     if (!(lmin > 0.0) || !std::isfinite(sxi * syi * sy * kz)) return HELM_ERR_EIG;
     const double gz = kz / lmin;
-    float sc[5];
-    sc[0] = 4096.f;
-    double F = 4096.0;   // Frobenius-norm bound of the stored grid after each stage
-    const double gain[4] = {sxi, syi, gz, sy};
-    for (int k = 0; k < 4; ++k) {
-        sc[k + 1] = pow2_scale(gain[k] * F);
-        F = gain[k] * F * sc[k + 1];
-    }
-    double prod = 1.0;
-    for (int k = 0; k < 5; ++k) prod *= sc[k];
-    for (int k = 0; k < 5; ++k) c->h16s[k] = sc[k];
-    c->h16s[5] = (float)(hz2 / prod);
+    // static: the input (2^12) and the x-pass forward (its input's norm is that bound); the later stages
+    // scale at run time from their input's measured norm times the gains kept here (c->h16g)
+    c->h16s[0] = 4096.f;
+    c->h16s[1] = pow2_scale(sxi * 4096.0);
+    c->h16s[2] = c->h16s[3] = c->h16s[4] = 1.f;
+    c->h16s[5] = (float)(hz2 / (4096.0 * (double)c->h16s[1]));
+    c->h16g[0] = (float)syi;
+    c->h16g[1] = (float)gz;
+    c->h16g[2] = (float)sy;
     return HELM_OK;
 }

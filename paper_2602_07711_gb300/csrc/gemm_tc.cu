@@ -134,6 +134,14 @@ __device__ __forceinline__ void mma_op(uint32_t d, uint64_t a, uint64_t b, uint3
 }
 // two floats rounded to nearest even BF16 (H = 1) or FP16 (H = 2, clamped to the finite range), packed low
 // half first (memory order)
+// FP16 chain: the power-of-two scale 2^e with gain sqrt(nsq) 2^e <= 2^15 (nsq the squared Frobenius norm of the
+// stage's input, gain the stage operator's norm bound), 1 for an all-zero input
+__device__ __forceinline__ float stage_scale(double gain, double nsq) {
+    if (!(nsq > 0.0)) return 1.f;
+    int e = 15 - (int)ceil(log2(gain * sqrt(nsq)));
+    e = e < -100 ? -100 : (e > 100 ? 100 : e);
+    return ldexpf(1.f, e);
+}
 template <int H>
 __device__ __forceinline__ uint32_t pack16(float lo, float hi) {
     if (H == 2) {
@@ -463,7 +471,8 @@ __global__ void __launch_bounds__(SPLIT ? 320 : 192, 1)
 xpass_tc_pers_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                      const __grid_constant__ CUtensorMap tmBl, void* __restrict__ outv, int M, int N2, int K2,
                      float alpha, const double* __restrict__ alpha_dev, int aidx, int rows_per, int astride,
-                     unsigned* status, long wlim) {
+                     unsigned* status, long wlim, const double* __restrict__ alpha_dev2 = nullptr,
+                     double* __restrict__ nsq_out = nullptr) {
     extern __shared__ uint8_t dsm[];
     constexpr int NS = PersX<BNT, SPLIT>::STAGES, BTILE = BNT * BK * 4, STAGE = PersX<BNT, SPLIT>::STAGE_BYTES;
     constexpr int KE = H ? 2 * BK : BK;    // K elements per stage (128 bytes per operand row)
@@ -557,12 +566,14 @@ xpass_tc_pers_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_const
     } else if (!SPLIT || warp < 6) {
         const int q = warp & 3;
         int lt = 0;
+        float nacc = 0.f;   // squared norm of what this thread stored (OBF, nsq_out)
+        const float al2 = alpha_dev2 ? (float)alpha_dev2[0] : 1.f;
         for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++lt) {
             const int b = lt & 1;
             const int n0 = (t % ntn) * BNT, m0 = (t / ntn) * BM;
             // this thread's accumulator row; rows of the v-th vector of a batch scale by alpha_dev[aidx + v astride]
             const int arow = min(m0 + 32 * q + lane, M - 1);
-            const float al = alpha * (alpha_dev ? (float)alpha_dev[aidx + (arow / rows_per) * astride] : 1.f);
+            const float al = alpha * al2 * (alpha_dev ? (float)alpha_dev[aidx + (arow / rows_per) * astride] : 1.f);
             ok = __all_sync(0xffffffffu, mbar_wait(su32(&accf[b]), (uint32_t)((lt >> 1) & 1), wlim));
             if (!ok) break;
             fence_after();
@@ -579,6 +590,12 @@ xpass_tc_pers_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_const
                     // the thread's 32 columns as 16 16-bit pairs (64 bytes) into its staging row, then 16-byte
                     // pieces of four rows per instruction: 64-byte row segments in global memory
                     uint32_t* su = reinterpret_cast<uint32_t*>(stg);
+                    if (nsq_out && m0 + 32 * q + lane < M)
+#pragma unroll
+                        for (int v = 0; v < 32; ++v) {
+                            const float x = al * __uint_as_float(r[v]);
+                            if (n0 + c + v < N2) nacc = fmaf(x, x, nacc);
+                        }
 #pragma unroll
                     for (int v = 0; v < 16; v += 4)
                         *reinterpret_cast<uint4*>(su + lane * XEPI_LD + v) =
@@ -634,6 +651,11 @@ xpass_tc_pers_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_const
             fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(su32(&acce[b]));
+        }
+        if (nsq_out) {
+            double d = (double)nacc;
+            for (int o = 16; o > 0; o >>= 1) d += __shfl_down_sync(0xffffffffu, d, o);
+            if (lane == 0) atomicAdd(nsq_out, d);
         }
     } else {
         // converter warps (SPLIT): split each data tile once its TMA loads have landed, then release the
@@ -691,7 +713,8 @@ template <bool SPLIT, int H = 0>
 __global__ void __launch_bounds__(SPLIT ? 320 : 192, 1)
 ypass_tc_pers_kernel(const __grid_constant__ CUtensorMap tmW, const __grid_constant__ CUtensorMap tmY,
                      const __grid_constant__ CUtensorMap tmWl, void* __restrict__ outv, int ny, int N2, int nz,
-                     unsigned* status, long wlim, float alpha = 1.f) {
+                     unsigned* status, long wlim, float alpha = 1.f, double* __restrict__ h16d = nullptr,
+                     float gain = 1.f, int role = 0) {
     extern __shared__ uint8_t dsm[];
     constexpr int YPS = PersY<SPLIT>::STAGES, STAGE = PersY<SPLIT>::STAGE_BYTES;
     constexpr int WLO = 3 * TILE, DLO = 5 * TILE;
@@ -806,6 +829,18 @@ ypass_tc_pers_kernel(const __grid_constant__ CUtensorMap tmW, const __grid_const
         const int q = warp & 3;
         float* stg = epi + q * 32 * YEPI_LD;
         int lt = 0;
+        // FP16 chain with dynamic stage scales (h16d): role 0 (forward) scales by the bound of ||T1|| (h16d[0]),
+        // records it in h16d[4] and accumulates its own output's squared norm into h16d[1]; role 1 (inverse)
+        // scales by that of ||T3|| (h16d[2]), records h16d[6] and the undo factor 1/(s2 s3 s4) in h16d[7]
+        float nacc = 0.f;
+        if (h16d) {
+            const float sc = stage_scale((double)gain, h16d[role == 0 ? 0 : 2]);
+            if (blockIdx.x == 0 && threadIdx.x == 64) {
+                h16d[role == 0 ? 4 : 6] = sc;
+                if (role == 1) h16d[7] = 1.0 / (h16d[4] * h16d[5] * (double)sc);
+            }
+            alpha *= sc;
+        }
         for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++lt) {
             const int b = lt & 1;
             const int mb = t % ntm, nb = (t / ntm) % ntn, l = t / (ntm * ntn);
@@ -829,8 +864,10 @@ ypass_tc_pers_kernel(const __grid_constant__ CUtensorMap tmW, const __grid_const
 #pragma unroll
                         for (int e = 0; e < 4; ++e) {
                             const int k = 2 * (v + e);
-                            w[e] = pack16<H>(alpha * (__uint_as_float(p[k]) - __uint_as_float(qq[k + 1])),
-                                             alpha * (__uint_as_float(p[k + 1]) + __uint_as_float(qq[k])));
+                            const float re = alpha * (__uint_as_float(p[k]) - __uint_as_float(qq[k + 1]));
+                            const float im = alpha * (__uint_as_float(p[k + 1]) + __uint_as_float(qq[k]));
+                            w[e] = pack16<H>(re, im);
+                            if (h16d && role == 0 && rbase + lane < ny && n0 + c + k < N2) nacc = fmaf(re, re, fmaf(im, im, nacc));
                         }
                         *reinterpret_cast<uint4*>(su + lane * XEPI_LD + v) = make_uint4(w[0], w[1], w[2], w[3]);
                     }
@@ -881,6 +918,11 @@ ypass_tc_pers_kernel(const __grid_constant__ CUtensorMap tmW, const __grid_const
             fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(su32(&acce[b]));
+        }
+        if (h16d && role == 0) {
+            double d = (double)nacc;
+            for (int o = 16; o > 0; o >>= 1) d += __shfl_down_sync(0xffffffffu, d, o);
+            if (lane == 0) atomicAdd(h16d + 1, d);
         }
     } else {
         // converter warps (SPLIT): split each data tile once its TMA loads have landed
@@ -1045,7 +1087,12 @@ helm_status tc_prepare(helm_ctx* c, cudaStream_t s) {
     if (t->h16 == 2) {   // FP16: power-of-two stage scales from the set-up bounds, and the norm scratch
         helm_status sst = h16_scales(c, s);
         if (sst != HELM_OK) return sst;
-        if (cudaMalloc(&c->h16n, (2 + 1024) * sizeof(double)) != cudaSuccess) { cudaGetLastError(); return HELM_ERR_NOMEM; }
+        if (cudaMalloc(&c->h16n, (2 + 1024) * sizeof(double)) != cudaSuccess ||
+            cudaMalloc(&c->h16d, 8 * sizeof(double)) != cudaSuccess) {
+            cudaGetLastError();
+            return HELM_ERR_NOMEM;
+        }
+        HELM_CUDA_TRY(cudaMemsetAsync(c->h16d, 0, 8 * sizeof(double), s));
     }
     if (t->h16) {
         // the EigT sets in 16 bits (the TF32 sets above serve helm_precond_step and the PFFT passes)
@@ -1217,24 +1264,26 @@ helm_status tc_ypass(helm_ctx* c, int inverse, const float2* in, float2* out, cu
 // 2 N_x) to a 16-bit or, when out_h16 is 0, an FP32 (complex64) grid, scaled as tc_xpass
 template <int H, bool OBF>
 void xpass_h16_launch(TcState* t, helm_ctx* c, int inverse, const CUtensorMap& mapA, void* out, int M, int N2,
-                      float alpha, const double* alpha_dev, int aidx, int rp, int astride, cudaStream_t s) {
+                      float alpha, const double* alpha_dev, int aidx, int rp, int astride, cudaStream_t s,
+                      const double* alpha_dev2, double* nsq_out) {
     const long wl = (long)c->wait_limit;
     const int mt = (M + BM - 1) / BM;
     if (N2 % 256 == 0) {
         const int ntiles = (N2 / 256) * mt, pg = ntiles < g_sms ? ntiles : g_sms;
         xpass_tc_pers_kernel<256, false, H, OBF><<<pg, 192, PersX<256, false>::SMEM, s>>>(
             mapA, t->mapBxb256[inverse], t->mapBxb256[inverse], out, M, N2, N2, alpha, alpha_dev, aidx, rp, astride,
-            c->status_d, wl);
+            c->status_d, wl, alpha_dev2, nsq_out);
     } else {
         const int ntiles = ((N2 + BN - 1) / BN) * mt, pg = ntiles < 2 * g_sms ? ntiles : 2 * g_sms;
         xpass_tc_pers_kernel<128, false, H, OBF><<<pg, 192, PersX<128, false>::SMEM, s>>>(
             mapA, t->mapBxb[inverse], t->mapBxb[inverse], out, M, N2, N2, alpha, alpha_dev, aidx, rp, astride,
-            c->status_d, wl);
+            c->status_d, wl, alpha_dev2, nsq_out);
     }
 }
 
 helm_status tc_xpass_h16(helm_ctx* c, int inverse, const void* in, void* out, int out_h16, float alpha,
-                         const double* alpha_dev, int aidx, cudaStream_t s, int nb, int astride) {
+                         const double* alpha_dev, int aidx, cudaStream_t s, int nb, int astride,
+                         const double* alpha_dev2, double* nsq_out) {
     TcState* t = (TcState*)c->tmaps;
     if (!t || !t->h16 || g_sms <= 0) return HELM_ERR_UNSUPPORTED;
     const int rp = c->ny * c->nz;
@@ -1246,18 +1295,19 @@ helm_status tc_xpass_h16(helm_ctx* c, int inverse, const void* in, void* out, in
     const CUtensorMapDataType dt = t->h16 == 2 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
     if (encode(t, &mapA, 2, (void*)in, d, st, box, CU_TENSOR_MAP_SWIZZLE_128B, dt) != HELM_OK) return HELM_ERR_CUDA;
     if (t->h16 == 2) {
-        if (out_h16) xpass_h16_launch<2, true>(t, c, inverse, mapA, out, M, N2, alpha, alpha_dev, aidx, rp, astride, s);
-        else xpass_h16_launch<2, false>(t, c, inverse, mapA, out, M, N2, alpha, alpha_dev, aidx, rp, astride, s);
+        if (out_h16) xpass_h16_launch<2, true>(t, c, inverse, mapA, out, M, N2, alpha, alpha_dev, aidx, rp, astride, s, alpha_dev2, nsq_out);
+        else xpass_h16_launch<2, false>(t, c, inverse, mapA, out, M, N2, alpha, alpha_dev, aidx, rp, astride, s, alpha_dev2, nsq_out);
     } else {
-        if (out_h16) xpass_h16_launch<1, true>(t, c, inverse, mapA, out, M, N2, alpha, alpha_dev, aidx, rp, astride, s);
-        else xpass_h16_launch<1, false>(t, c, inverse, mapA, out, M, N2, alpha, alpha_dev, aidx, rp, astride, s);
+        if (out_h16) xpass_h16_launch<1, true>(t, c, inverse, mapA, out, M, N2, alpha, alpha_dev, aidx, rp, astride, s, alpha_dev2, nsq_out);
+        else xpass_h16_launch<1, false>(t, c, inverse, mapA, out, M, N2, alpha, alpha_dev, aidx, rp, astride, s, alpha_dev2, nsq_out);
     }
     HELM_CUDA_TRY(cudaGetLastError());
     return HELM_OK;
 }
 
 // y-pass of the 16-bit chain: 16-bit slices in, 16-bit slices out (scaled by alpha)
-helm_status tc_ypass_h16(helm_ctx* c, int inverse, const void* in, void* out, float alpha, cudaStream_t s, int nb) {
+helm_status tc_ypass_h16(helm_ctx* c, int inverse, const void* in, void* out, float alpha, cudaStream_t s, int nb,
+                         double* h16d, float gain) {
     TcState* t = (TcState*)c->tmaps;
     if (!t || !t->h16 || g_sms <= 0) return HELM_ERR_UNSUPPORTED;
     const int ny = c->ny, N2 = 2 * c->nx, nzb = c->nz * nb;
@@ -1272,7 +1322,8 @@ helm_status tc_ypass_h16(helm_ctx* c, int inverse, const void* in, void* out, fl
     const int pg = ntiles > g_sms ? g_sms : ntiles;
     if (t->h16 == 2)
         ypass_tc_pers_kernel<false, 2><<<pg, 192, PersY<false>::SMEM, s>>>(t->mapWyb[inverse], mapY, t->mapWyb[inverse],
-                                                                          out, ny, N2, nzb, c->status_d, wl, alpha);
+                                                                          out, ny, N2, nzb, c->status_d, wl, alpha, h16d,
+                                                                          gain, inverse);
     else
         ypass_tc_pers_kernel<false, 1><<<pg, 192, PersY<false>::SMEM, s>>>(t->mapWyb[inverse], mapY, t->mapWyb[inverse],
                                                                           out, ny, N2, nzb, c->status_d, wl, alpha);

@@ -85,6 +85,36 @@ __global__ void norm_final_kernel(const double* __restrict__ part, int nparts, d
     }
 }
 
+// The passes of the 16-bit chain from the 16-bit input In to the complex64 z (T0, T1: the halves of the
+// context's scratch vector; In may be T0).  BF16: the static factors of c->h16s (all 1 but the last).  FP16:
+// the x-pass forward scales statically (its input's norm is bounded by h16s[0]), every later stage by the
+// bound of its input's measured norm (c->h16d, reset here), and the last pass undoes those scales.
+helm_status h16_chain(helm_ctx* c, const uint16_t* In, uint16_t* T1, float2* z, float alpha_last, const double* adev,
+                      int aidx, cudaStream_t s) {
+    helm_status st;
+    uint16_t* T0 = reinterpret_cast<uint16_t*>(c->tmp);
+    const float* sc = c->h16s;
+    double* d = c->opt.precision == HELM_PREC_FP16 ? c->h16d : nullptr;
+    if (d) HELM_CUDA_TRY(cudaMemsetAsync(d, 0, 3 * sizeof(double), s));
+    prof_begin(c, s, PROF_XPASS);
+    st = tc_xpass_h16(c, 0, In, T1, 1, sc[1], nullptr, 0, s, 1, 0, nullptr, d);
+    prof_end(c, s);
+    if (st != HELM_OK) return st;
+    prof_begin(c, s, PROF_YPASS);
+    st = tc_ypass_h16(c, 0, T1, T0, sc[2], s, 1, d, c->h16g[0]);
+    prof_end(c, s);
+    if (st != HELM_OK) return st;
+    if ((st = launch_zsolve_h16(c, T0, T0, reinterpret_cast<float4*>(z), sc[3], s, 1, d, c->h16g[1])) != HELM_OK) return st;
+    prof_begin(c, s, PROF_YPASS);
+    st = tc_ypass_h16(c, 1, T0, T1, sc[4], s, 1, d, c->h16g[2]);
+    prof_end(c, s);
+    if (st != HELM_OK) return st;
+    prof_begin(c, s, PROF_XPASS);
+    st = tc_xpass_h16(c, 1, T1, z, 0, alpha_last, adev, aidx, s, 1, 0, d ? d + 7 : nullptr, nullptr);
+    prof_end(c, s);
+    return st;
+}
+
 // EigT with 16-bit intermediate grids (HELM_PREC_BF16, HELM_PREC_FP16): r (complex64) -> 16 bits ->
 // x-pass -> y-pass -> z-solve -> y-pass -> x-pass -> z (complex64), every stored grid times its power-of-two
 // stage scale c->h16s (FP16; all 1 for BF16, whose range is FP32's), the last pass undoing them.  The two
@@ -113,22 +143,8 @@ helm_status precond_h16(helm_ctx* c, const float2* r, float2* z, const double* s
         c64_to_h16_kernel<1><<<2048, 256, 0, s>>>(reinterpret_cast<const float4*>(r), reinterpret_cast<uint2*>(T0), n / 2,
                                                   sc[0], sigma, sidx, inv);
     HELM_CUDA_TRY(cudaGetLastError());
-    st = tc_xpass_h16(c, 0, T0, T1, 1, sc[1], nullptr, 0, s);
     prof_end(c, s);
-    if (st != HELM_OK) return st;
-    prof_begin(c, s, PROF_YPASS);
-    st = tc_ypass_h16(c, 0, T1, T0, sc[2], s);
-    prof_end(c, s);
-    if (st != HELM_OK) return st;
-    if ((st = launch_zsolve_h16(c, T0, T0, reinterpret_cast<float4*>(z), sc[3], s)) != HELM_OK) return st;
-    prof_begin(c, s, PROF_YPASS);
-    st = tc_ypass_h16(c, 1, T0, T1, sc[4], s);
-    prof_end(c, s);
-    if (st != HELM_OK) return st;
-    prof_begin(c, s, PROF_XPASS);
-    st = tc_xpass_h16(c, 1, T1, z, 0, sc[5], nrm, 0, s);
-    prof_end(c, s);
-    return st;
+    return h16_chain(c, T0, T1, z, sc[5], nrm, 0, s);
 }
 
 // nb > 1: nb grid vectors back to back (a batch group); vector v is scaled by sigma[sidx + v sstride]
@@ -209,29 +225,9 @@ static helm_status precond_base(helm_ctx* c, const float2* r, float2* z, const d
 // bound h16s[0] (the FP16 Krylov basis of HELM_PREC_FP16): the chain of precond_h16 without its conversion,
 // the last pass scaled by cs[cidx] h16s[0] on top of the stage factor.  z is complex64 and must not alias V16.
 helm_status precond_h16_basis(helm_ctx* c, const uint16_t* V16, float2* z, const double* cs, int cidx, cudaStream_t s) {
-    helm_status st;
     if (c->opt.precision != HELM_PREC_FP16 || c->opt.precond != HELM_PRECOND_EIGT || c->net) return HELM_ERR_UNSUPPORTED;
-    const size_t n = c->npts;
-    uint16_t* T0 = reinterpret_cast<uint16_t*>(c->tmp);
-    uint16_t* T1 = T0 + 2 * n;
-    const float* sc = c->h16s;
-    prof_begin(c, s, PROF_XPASS);
-    st = tc_xpass_h16(c, 0, V16, T1, 1, sc[1], nullptr, 0, s);
-    prof_end(c, s);
-    if (st != HELM_OK) return st;
-    prof_begin(c, s, PROF_YPASS);
-    st = tc_ypass_h16(c, 0, T1, T0, sc[2], s);
-    prof_end(c, s);
-    if (st != HELM_OK) return st;
-    if ((st = launch_zsolve_h16(c, T0, T0, reinterpret_cast<float4*>(z), sc[3], s)) != HELM_OK) return st;
-    prof_begin(c, s, PROF_YPASS);
-    st = tc_ypass_h16(c, 1, T0, T1, sc[4], s);
-    prof_end(c, s);
-    if (st != HELM_OK) return st;
-    prof_begin(c, s, PROF_XPASS);
-    st = tc_xpass_h16(c, 1, T1, z, 0, sc[5] * sc[0], cs, cidx, s);
-    prof_end(c, s);
-    return st;
+    uint16_t* T1 = reinterpret_cast<uint16_t*>(c->tmp) + 2 * c->npts;
+    return h16_chain(c, V16, T1, z, c->h16s[5] * c->h16s[0], cs, cidx, s);
 }
 
 // complex64 r -> FP16 grid scaled by s0 sigma[sidx] (the first basis vector of a cycle)

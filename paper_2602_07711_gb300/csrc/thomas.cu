@@ -481,8 +481,23 @@ __global__ void __launch_bounds__(ZRT, 4) zsolve_piv_kernel(int nx, int ny, int 
                                                            const float2* __restrict__ dys,
                                                            const float2* __restrict__ cz, const void* inv, void* outv,
                                                            float4* dscr, float4* __restrict__ ck, int nb,
-                                                           float oscale = 1.f) {
+                                                           float oscale = 1.f, double* __restrict__ h16d = nullptr,
+                                                           float gain = 1.f) {
     constexpr bool BF = H != 0;
+    // FP16 chain with dynamic stage scales (h16d): the output scale from the bound of ||T2|| (h16d[1]),
+    // recorded in h16d[5]; the squared norm of what is stored accumulates into h16d[2]
+    float nacc = 0.f;
+    if (BF && h16d) {
+        const double n2 = h16d[1];
+        float sc = 1.f;
+        if (n2 > 0.0) {
+            int e = 15 - (int)ceil(log2((double)gain * sqrt(n2)));
+            e = e < -100 ? -100 : (e > 100 ? 100 : e);
+            sc = ldexpf(1.f, e);
+        }
+        oscale *= sc;
+        if (blockIdx.x == 0 && threadIdx.x == 0) h16d[5] = sc;
+    }
     extern __shared__ float4 zsm[];   // [ZPB * ZU2][ZRT]
     const float4* in = reinterpret_cast<const float4*>(inv);
     const uint2* inb = reinterpret_cast<const uint2*>(inv);
@@ -584,14 +599,21 @@ __global__ void __launch_bounds__(ZRT, 4) zsolve_piv_kernel(int nx, int ny, int 
                     const float sup = l == nz - 1 ? 0.f : (l == 0 ? zz : 1.f);
                     x0 = zbwd(f2(dv.x, dv.y), m0[u], x0, sup);
                     x1 = zbwd(f2(dv.z, dv.w), m1[u], x1, sup);
-                    if (BF)
-                        outb[voff + off + (size_t)l * plane] =
-                            make_uint2(zpack16<H>(oscale * x0.x, oscale * x0.y), zpack16<H>(oscale * x1.x, oscale * x1.y));
+                    if (BF) {
+                        const float a = oscale * x0.x, b2 = oscale * x0.y, c2 = oscale * x1.x, d2 = oscale * x1.y;
+                        outb[voff + off + (size_t)l * plane] = make_uint2(zpack16<H>(a, b2), zpack16<H>(c2, d2));
+                        nacc = fmaf(a, a, fmaf(b2, b2, fmaf(c2, c2, fmaf(d2, d2, nacc))));
+                    }
                     else out[voff + off + (size_t)l * plane] = make_float4(x0.x, x0.y, x1.x, x1.y);
                 }
             }
         }
         zwait_all();
+    }
+    if (BF && h16d) {
+        double d = (double)nacc;
+        for (int o = 16; o > 0; o >>= 1) d += __shfl_down_sync(0xffffffffu, d, o);
+        if ((threadIdx.x & 31) == 0) atomicAdd(h16d + 2, d);
     }
 }
 
@@ -735,7 +757,8 @@ helm_status launch_zsolve(helm_ctx* c, const float2* in, float2* out, cudaStream
 // with 16-bit y and x (in may equal out; x scaled by oscale) and the FP32 forward values in dscr (npts * nb
 // complex64 of the caller).  No fallback: a launch under stream capture without reserved checkpoints
 // returns HELM_ERR_UNSUPPORTED.
-helm_status launch_zsolve_h16(helm_ctx* c, const void* in, void* out, float4* dscr, float oscale, cudaStream_t s, int nb) {
+helm_status launch_zsolve_h16(helm_ctx* c, const void* in, void* out, float4* dscr, float oscale, cudaStream_t s, int nb,
+                              double* h16d, float gain) {
     const int H = c->opt.precision == HELM_PREC_FP16 ? 2 : 1;
     if (c->nx % 2 != 0 || c->zring_sms <= 0) return HELM_ERR_UNSUPPORTED;
     const int slot = c->zck_slot;
@@ -762,7 +785,7 @@ helm_status launch_zsolve_h16(helm_ctx* c, const void* in, void* out, float4* ds
     const float2 gz = make_float2((float)c->gam[2].x, (float)c->gam[2].y);
     if (H == 2)
         zsolve_piv_kernel<2><<<grid, ZRT, ZPIV_SMEM, s>>>(c->nx, c->ny, c->nz, (float)c->zeta[2], gz, c->dxs, c->dys, c->cz,
-                                                           in, out, dscr, ck, nb, oscale);
+                                                           in, out, dscr, ck, nb, oscale, h16d, gain);
     else
         zsolve_piv_kernel<1><<<grid, ZRT, ZPIV_SMEM, s>>>(c->nx, c->ny, c->nz, (float)c->zeta[2], gz, c->dxs, c->dys, c->cz,
                                                            in, out, dscr, ck, nb, oscale);

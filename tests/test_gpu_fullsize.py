@@ -23,11 +23,11 @@ from oracle.rhs import rhs6_sampled
 from paper_2602_07711_gb300 import HELM_PREC_FP16, HELM_PREC_TF32, Solver, media
 
 N = 256
-# relative bounds (2-norm, max-norm) of the whole preconditioner per mode.  FP16 measured 4.8e-3 in the
-# 2-norm at this size (1.3e-3 at 256 x 256 x 8): its stage scales come from worst-case gains (sigma(V^-1)
-# ~10 per transform, kappa(V_z) / min |lambda| ~5300 for the z-solves, whose typical gain is ~1), so at
-# N_z = 256 the typical z-solve outputs sit near the FP16 subnormal range and lose bits.
-PRECOND_BOUNDS = {HELM_PREC_TF32: (4e-3, 5e-3), HELM_PREC_FP16: (1.2e-2, 2e-2)}
+# relative bounds (2-norm, max-norm) of the whole preconditioner per mode, about 2.5x the measurements at
+# this size: TF32 1.7e-3 / 1.7e-3, FP16 1.0e-3 / 1.26e-3 (its stages scale from their inputs' measured norms;
+# with scales fixed at set-up from worst-case gains the z-solve outputs sat near the FP16 subnormal range
+# and the error was 4.8e-3)
+PRECOND_BOUNDS = {HELM_PREC_TF32: (4e-3, 5e-3), HELM_PREC_FP16: (2.5e-3, 3.2e-3)}
 
 
 @pytest.fixture(scope="module", params=[HELM_PREC_FP16, HELM_PREC_TF32], ids=["fp16", "tf32"])
