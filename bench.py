@@ -137,9 +137,10 @@ def algorithmic(n, order, cycles_iters, real_medium=False, precision="tf32"):
     for k in cycles_iters:
         for j in range(k):
             if precision == "fp16":
-                # FP16 basis: j+1 basis vectors at 4 B/pt, w (complex64) once per group of eight vectors;
-                # the update reads them and w and writes only the new FP16 vector
-                db += (4 * (j + 1) + 8 * ((j + 8) // 8)) * pts
+                # FP16 basis: j+1 basis vectors at 4 B/pt and w (complex64) once (the staged inner products,
+                # j + 2 <= 32; beyond, once per group of eight vectors); the update reads them and w and
+                # writes only the new FP16 vector
+                db += (4 * (j + 1) + (8 if j + 2 <= 32 else 8 * ((j + 8) // 8))) * pts
                 ub += (4 * (j + 1) + 8 + 4) * pts
             else:
                 db += 8 * (j + 2) * pts        # j+1 basis vectors + w

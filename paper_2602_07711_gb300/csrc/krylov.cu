@@ -82,6 +82,7 @@ struct KrylovWork {
     uint16_t* V16 = nullptr;
     double* c16 = nullptr;           // [m+1]
     double* w16s = nullptr;          // [1]
+    int db_ready = 0;                // shared-memory attribute of the staged inner-product kernel set
 };
 
 namespace {
@@ -421,6 +422,129 @@ __global__ void __launch_bounds__(NT) dots16_kernel(const uint16_t* __restrict__
         __syncthreads();
     }
 }
+// Staged form (nv + 1 <= 32): one CTA per SM walks chunks of T points; a producer warp copies w (8 B/pt) and
+// the nv basis chunks (4 B/pt each) of a chunk into a three-stage shared-memory ring with bulk copies
+// (cp.async.bulk, completion by mbarrier transaction count), so the bytes in flight per SM (up to three
+// 64 KiB stages) do not depend on registers; eight consumer warps take the nv inner products and ||w||^2
+// (item nv) by item (warp k: items k, k + 8, ...), two FMA2 per point and item as above, FP32 per chunk and
+// FP64 across chunks.  Every wait is bounded by wlim (HELM_DEV_WAIT on expiry); the producer waits for the
+// copies it issued before the CTA exits.
+constexpr int DB_NS = 3, DB_CW = 8, DB_NT = (DB_CW + 1) * 32;
+constexpr int DB_STAGE = 64 * 1024;
+constexpr size_t DB_SMEM = (size_t)DB_NS * DB_STAGE;
+constexpr long DB_DRAIN = 1L << 22;
+__device__ __forceinline__ uint32_t db_su(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ bool db_wait(uint32_t bar, uint32_t parity, long limit) {
+    for (long it = 0; it < limit; ++it) {
+        uint32_t ok;
+        asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+                     : "=r"(ok) : "r"(bar), "r"(parity) : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+__device__ __forceinline__ void db_bulk(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"(src), "r"(bytes), "r"(bar) : "memory");
+}
+__global__ void __launch_bounds__(DB_NT, 1) dots16b_kernel(const uint16_t* __restrict__ V16, size_t npts, int nv,
+                                                          const float2* __restrict__ w, double2* __restrict__ part,
+                                                          int ld, int T, unsigned* status, long wlim) {
+    extern __shared__ __align__(128) unsigned char dbs[];
+    __shared__ __align__(8) uint64_t full[DB_NS], empty[DB_NS];
+    __shared__ int fail;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const long nch = (long)((npts + T - 1) / T);
+    const long mine = nch > blockIdx.x ? (nch - 1 - blockIdx.x) / gridDim.x + 1 : 0;   // chunks of this CTA
+    if (threadIdx.x == 0) {
+        for (int q = 0; q < DB_NS; ++q) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(db_su(&full[q])), "r"(1) : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(db_su(&empty[q])), "r"(DB_CW) : "memory");
+        }
+        fail = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    bool ok = true;
+    if (warp == DB_CW) {   // producer
+        long issued = 0;
+        if (lane == 0) {
+            for (long k = 0; k < mine && ok; ++k) {
+                const int q = (int)(k % DB_NS);
+                if (k >= DB_NS) ok = db_wait(db_su(&empty[q]), (uint32_t)(((k / DB_NS) - 1) & 1), wlim);
+                if (!ok) break;
+                const size_t start = (size_t)(blockIdx.x + k * gridDim.x) * T;
+                const uint32_t cnt = (uint32_t)min((size_t)T, npts - start);
+                const uint32_t base = db_su(dbs + (size_t)q * DB_STAGE);
+                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(db_su(&full[q])),
+                             "r"(cnt * 8u + (uint32_t)nv * cnt * 4u) : "memory");
+                db_bulk(base, w + start, cnt * 8u, db_su(&full[q]));
+                for (int i = 0; i < nv; ++i)
+                    db_bulk(base + (uint32_t)T * 8u + (uint32_t)i * T * 4u, V16 + (size_t)i * 2 * npts + 2 * start, cnt * 4u,
+                            db_su(&full[q]));
+                ++issued;
+            }
+            if (!ok) {
+                atomicOr(status, (unsigned)HELM_DEV_WAIT);
+                fail = 1;
+            }
+            // the copies in flight land before the CTA leaves (the consumers may have stopped waiting)
+            for (long k = issued > DB_NS ? issued - DB_NS : 0; k < issued; ++k)
+                db_wait(db_su(&full[k % DB_NS]), (uint32_t)((k / DB_NS) & 1), DB_DRAIN);
+        }
+    } else {               // consumers: items warp, warp + 8, ... (< nv + 1)
+        double2 acc[4];
+        for (int u = 0; u < 4; ++u) acc[u] = make_double2(0.0, 0.0);
+        for (long k = 0; k < mine && ok; ++k) {
+            const int q = (int)(k % DB_NS);
+            ok = __all_sync(0xffffffffu, db_wait(db_su(&full[q]), (uint32_t)((k / DB_NS) & 1), wlim));
+            if (!ok) break;
+            const size_t start = (size_t)(blockIdx.x + k * gridDim.x) * T;
+            const int cnt = (int)min((size_t)T, npts - start);
+            const float2* sw = reinterpret_cast<const float2*>(dbs + (size_t)q * DB_STAGE);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int i = warp + u * DB_CW;
+                if (i > nv) break;
+                float2 P = make_float2(0.f, 0.f), Q = P;
+                if (i < nv) {
+                    const uint32_t* sv = reinterpret_cast<const uint32_t*>(dbs + (size_t)q * DB_STAGE + (size_t)T * 8 +
+                                                                           (size_t)i * T * 4);
+                    for (int p = lane; p < cnt; p += 32) {
+                        const float2 wv = sw[p], v = h2f(sv[p]);
+                        P = fma2(v, bc2(wv.x), P);
+                        Q = fma2(v, bc2(wv.y), Q);
+                    }
+                    acc[u].x += (double)P.x + (double)Q.y;
+                    acc[u].y += (double)Q.x - (double)P.y;
+                } else {
+                    for (int p = lane; p < cnt; p += 32) {
+                        const float2 wv = sw[p];
+                        P = fma2(wv, wv, P);
+                    }
+                    acc[u].x += (double)P.x + (double)P.y;
+                }
+            }
+            __syncwarp();
+            if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(db_su(&empty[q])) : "memory");
+        }
+        if (!ok && lane == 0) {
+            atomicOr(status, (unsigned)HELM_DEV_WAIT);
+            fail = 1;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int i = warp + u * DB_CW;
+            for (int o = 16; o > 0; o >>= 1) {
+                acc[u].x += __shfl_down_sync(0xffffffffu, acc[u].x, o);
+                acc[u].y += __shfl_down_sync(0xffffffffu, acc[u].y, o);
+            }
+            if (lane == 0 && i <= nv) part[(size_t)blockIdx.x * ld + i] = acc[u];
+        }
+    }
+    __syncthreads();
+}
+
 // blocks i < nv: h_i = c16[i] sum_b part[b][i], coef_i = c16[i] h_i; block nv: w16s = s0 / ||w||
 __global__ void reduce16_kernel(const double2* __restrict__ part, int NB, int ld, int nv, const double* __restrict__ c16,
                                 double2* __restrict__ Hcol, float2* __restrict__ coef, float s0, double* __restrict__ w16s) {
@@ -1001,10 +1125,24 @@ helm_status gmres_run(helm_ctx* c, const double2* b_in, double2* x_in, helm_solv
                     if ((e = precond_h16_basis(c, Vj, z, k->c16, j, s)) != HELM_OK) return e;
                     if ((e = launch_stencil_f32(c, z, wv, nullptr, 0, s)) != HELM_OK) return e;
                     prof_begin(c, s, PROF_DOTS);
-                    dots16_kernel<8><<<k->NBd, NT, 0, s>>>(k->V16, npts, j + 1, wv, k->part, ld);
+                    int nbd16 = k->NBd;
+                    if (j + 2 <= 32 && c->zring_sms > 0 && c->zring_sms <= std::max(k->NB, k->NBd)) {
+                        // staged form: T points per chunk so that one stage holds w and the j + 1 basis chunks
+                        const int T = std::max(64, (int)(DB_STAGE / (8 + 4 * (j + 1))) / 64 * 64);
+                        nbd16 = c->zring_sms;
+                        if (!k->db_ready) {
+                            HELM_CUDA_TRY(cudaFuncSetAttribute(dots16b_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                               (int)DB_SMEM));
+                            k->db_ready = 1;
+                        }
+                        dots16b_kernel<<<nbd16, DB_NT, DB_SMEM, s>>>(k->V16, npts, j + 1, wv, k->part, ld, T, c->status_d,
+                                                                     (long)c->wait_limit);
+                    } else {
+                        dots16_kernel<8><<<k->NBd, NT, 0, s>>>(k->V16, npts, j + 1, wv, k->part, ld);
+                    }
                     prof_end(c, s);
                     prof_begin(c, s, PROF_SMALL);
-                    reduce16_kernel<<<j + 2, 128, 0, s>>>(k->part, k->NBd, ld, j + 1, k->c16, k->H + (size_t)j * (m + 1),
+                    reduce16_kernel<<<j + 2, 128, 0, s>>>(k->part, nbd16, ld, j + 1, k->c16, k->H + (size_t)j * (m + 1),
                                                           k->coef, s0, k->w16s);
                     prof_end(c, s);
                     prof_begin(c, s, PROF_UPDATE);
