@@ -86,8 +86,8 @@ enum { HELM_PRECOND_NONE = 0, HELM_PRECOND_EIGT = 1, HELM_PRECOND_PFFT = 2, HELM
  *                     stored in BF16 (the z-solve reads and writes BF16 and computes in FP32): half the
  *                     bytes of the TF32 chain and twice its MMA rate; relative error of the whole
  *                     preconditioner about 1e-2.  EigT only (the PFFT and helm_precond_step passes run in
- *                     TF32); needs N_x a multiple of 4; single solves (helm_gmres_solve_batched returns
- *                     HELM_ERR_UNSUPPORTED for such contexts).
+ *                     TF32); needs N_x a multiple of 4; in helm_gmres_solve_batched only with flexible GMRES
+ *                     (HELM_ERR_UNSUPPORTED otherwise).
  *   HELM_PREC_FP16    the same chain with FP16 operands and grids (TF32's 11-bit significand, so about
  *                     TF32's accuracy): every stored grid is scaled by a power of two fixed at set-up from
  *                     bounds that rule out overflow for any input (spectral norms of the eigenvector

@@ -1949,8 +1949,12 @@ helm_status check_batch_args(helm_ctx* const* ctxs, int nprob, const void* const
         helm_ctx* c = ctxs[p];
         if (!c || !b[p] || !x[p]) return HELM_ERR_ARG;
         // the high-order closure's padded operands are one per context: lanes of a graph could race on them
-        if (c->opt.precond == HELM_PRECOND_PFFT || c->opt.precond == HELM_PRECOND_FFT2 || c->net || c->ho ||
-            c->opt.precision == HELM_PREC_BF16 || c->opt.precision == HELM_PREC_FP16)
+        if (c->opt.precond == HELM_PRECOND_PFFT || c->opt.precond == HELM_PRECOND_FFT2 || c->net || c->ho)
+            return HELM_ERR_UNSUPPORTED;
+        // the 16-bit chains run in the lanes' group iterations only: their z-solves keep per-context state
+        // (checkpoint slots, stage norms), which concurrent cycle-end preconditioners of non-flexible lanes
+        // would share
+        if ((c->opt.precision == HELM_PREC_BF16 || c->opt.precision == HELM_PREC_FP16) && !c->opt.flexible)
             return HELM_ERR_UNSUPPORTED;
         if (!is_device_ptr(b[p]) || !is_device_ptr(x[p])) return HELM_ERR_ARG;
         for (int q = 0; q < p; ++q)

@@ -31,10 +31,14 @@ __device__ __forceinline__ uint32_t cpack16(float lo, float hi) {
     const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
     return *reinterpret_cast<const uint32_t*>(&v);
 }
+// (nb vectors back to back, vector v scaled by sigma[sidx + v sstride]: blockIdx.y = v)
 template <int H>
 __global__ void c64_to_h16_kernel(const float4* __restrict__ a, uint2* __restrict__ b, size_t n2, float s0,
-                                  const double* __restrict__ sigma, int sidx, const double* __restrict__ inv) {
-    const float sc = s0 * (sigma ? (float)sigma[sidx] : inv ? (float)inv[0] : 1.f);
+                                  const double* __restrict__ sigma, int sidx, const double* __restrict__ inv,
+                                  int sstride = 0) {
+    const float sc = s0 * (sigma ? (float)sigma[sidx + blockIdx.y * sstride] : inv ? (float)inv[0] : 1.f);
+    a += (size_t)blockIdx.y * n2;
+    b += (size_t)blockIdx.y * n2;
     const size_t stride = (size_t)gridDim.x * blockDim.x;
     for (size_t i0 = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i0 < n2; i0 += 4 * stride) {
         float4 v[4];
@@ -90,27 +94,27 @@ __global__ void norm_final_kernel(const double* __restrict__ part, int nparts, d
 // the x-pass forward scales statically (its input's norm is bounded by h16s[0]), every later stage by the
 // bound of its input's measured norm (c->h16d, reset here), and the last pass undoes those scales.
 helm_status h16_chain(helm_ctx* c, const uint16_t* In, uint16_t* T1, float2* z, float alpha_last, const double* adev,
-                      int aidx, cudaStream_t s) {
+                      int aidx, cudaStream_t s, int nb = 1) {
     helm_status st;
     uint16_t* T0 = reinterpret_cast<uint16_t*>(c->tmp);
     const float* sc = c->h16s;
     double* d = c->opt.precision == HELM_PREC_FP16 ? c->h16d : nullptr;
     if (d) HELM_CUDA_TRY(cudaMemsetAsync(d, 0, 3 * sizeof(double), s));
     prof_begin(c, s, PROF_XPASS);
-    st = tc_xpass_h16(c, 0, In, T1, 1, sc[1], nullptr, 0, s, 1, 0, nullptr, d);
+    st = tc_xpass_h16(c, 0, In, T1, 1, sc[1], nullptr, 0, s, nb, 0, nullptr, d);
     prof_end(c, s);
     if (st != HELM_OK) return st;
     prof_begin(c, s, PROF_YPASS);
-    st = tc_ypass_h16(c, 0, T1, T0, sc[2], s, 1, d, c->h16g[0]);
+    st = tc_ypass_h16(c, 0, T1, T0, sc[2], s, nb, d, c->h16g[0]);
     prof_end(c, s);
     if (st != HELM_OK) return st;
-    if ((st = launch_zsolve_h16(c, T0, T0, reinterpret_cast<float4*>(z), sc[3], s, 1, d, c->h16g[1])) != HELM_OK) return st;
+    if ((st = launch_zsolve_h16(c, T0, T0, reinterpret_cast<float4*>(z), sc[3], s, nb, d, c->h16g[1])) != HELM_OK) return st;
     prof_begin(c, s, PROF_YPASS);
-    st = tc_ypass_h16(c, 1, T0, T1, sc[4], s, 1, d, c->h16g[2]);
+    st = tc_ypass_h16(c, 1, T0, T1, sc[4], s, nb, d, c->h16g[2]);
     prof_end(c, s);
     if (st != HELM_OK) return st;
     prof_begin(c, s, PROF_XPASS);
-    st = tc_xpass_h16(c, 1, T1, z, 0, alpha_last, adev, aidx, s, 1, 0, d ? d + 7 : nullptr, nullptr);
+    st = tc_xpass_h16(c, 1, T1, z, 0, alpha_last, adev, aidx, s, nb, 0, d ? d + 7 : nullptr, nullptr);
     prof_end(c, s);
     return st;
 }
@@ -256,9 +260,24 @@ helm_status precond_apply_nb(helm_ctx* c, const float2* r, float2* z, int nb, co
         HELM_CUDA_TRY(cudaGetLastError());
         return HELM_OK;
     }
-    if (c->opt.precond != HELM_PRECOND_EIGT || c->net || c->opt.precision == HELM_PREC_BF16 ||
-        c->opt.precision == HELM_PREC_FP16)
-        return HELM_ERR_UNSUPPORTED;
+    if (c->opt.precond != HELM_PRECOND_EIGT || c->net) return HELM_ERR_UNSUPPORTED;
+    if (c->opt.precision == HELM_PREC_BF16 || c->opt.precision == HELM_PREC_FP16) {
+        // the 16-bit chain over the nb vectors (each pass acts on every vector's rows, slices or lines on
+        // their own, so each vector's stage bounds hold; the measured norms are the group's)
+        const size_t n = c->npts;
+        uint16_t* T0 = reinterpret_cast<uint16_t*>(c->tmp);
+        uint16_t* T1 = T0 + 2 * n * nb;
+        prof_begin(c, s, PROF_XPASS);
+        if (c->opt.precision == HELM_PREC_FP16)
+            c64_to_h16_kernel<2><<<dim3(512, nb), 256, 0, s>>>(reinterpret_cast<const float4*>(r), reinterpret_cast<uint2*>(T0),
+                                                              n / 2, c->h16s[0], sigma, sidx, nullptr, sstride);
+        else
+            c64_to_h16_kernel<1><<<dim3(512, nb), 256, 0, s>>>(reinterpret_cast<const float4*>(r), reinterpret_cast<uint2*>(T0),
+                                                              n / 2, c->h16s[0], sigma, sidx, nullptr, sstride);
+        HELM_CUDA_TRY(cudaGetLastError());
+        prof_end(c, s);
+        return h16_chain(c, T0, T1, z, c->h16s[5], nullptr, 0, s, nb);
+    }
     const float hz2 = (float)(c->h[2] * c->h[2]);
     if ((st = xpass(c, 0, r, c->tmp, 1.f, sigma, sidx, s, nb, sstride)) != HELM_OK) return st;
     if ((st = ypass(c, 0, c->tmp, z, s, nb)) != HELM_OK) return st;
