@@ -141,6 +141,7 @@ struct helm_ctx {
     double* h16n = nullptr;                 // FP16 chain: 1/||r||, ||r|| and partial sums (helm_apply_precond)
     double* h16d = nullptr;                 // FP16 chain, per application: ||T1||^2, ||T2||^2, ||T3||^2, -, s2, s3, s4, 1/(s2 s3 s4)
     float h16g[3] = {1.f, 1.f, 1.f};        // FP16 chain: norm bounds of the y-pass forward, z-solve, y-pass inverse
+    cudaEvent_t h16_join = nullptr;         // FP16 basis: an event the chain's last pass waits for (the step's scale)
     void* sfast = nullptr;                  // TMA descriptors of the stencil's fixed operands (stencil_fast.cu)
     // scratch
     float2* tmp = nullptr;                  // one complex64 grid vector

@@ -83,6 +83,12 @@ struct KrylovWork {
     double* c16 = nullptr;           // [m+1]
     double* w16s = nullptr;          // [1]
     int db_ready = 0;                // shared-memory attribute of the staged inner-product kernel set
+    // the Givens step of the FP16-basis solve on a side stream: ev_upd[j] after the update of step j (main
+    // stream), ev_giv[j] after its Givens step (side stream), which the next step joins before the last pass
+    // of its preconditioner
+    cudaStream_t side = nullptr;
+    cudaEvent_t* ev_upd = nullptr;
+    cudaEvent_t* ev_giv = nullptr;
 };
 
 namespace {
@@ -905,6 +911,13 @@ void free_work(KrylovWork* k) {
             if (k->ev_slot[j]) cudaEventDestroy(k->ev_slot[j]);
         delete[] k->ev_slot;
     }
+    for (cudaEvent_t* ev : {k->ev_upd, k->ev_giv})
+        if (ev) {
+            for (int j = 0; j < k->m; ++j)
+                if (ev[j]) cudaEventDestroy(ev[j]);
+            delete[] ev;
+        }
+    if (k->side) cudaStreamDestroy(k->side);
 }
 
 int dots_ctas(const helm_ctx* c);
@@ -1085,6 +1098,15 @@ helm_status gmres_run(helm_ctx* c, const double2* b_in, double2* x_in, helm_solv
     const bool h16b = c->opt.precision == HELM_PREC_FP16 && flex && !c->opt.reorth && !c->net &&
                       c->opt.precond == HELM_PRECOND_EIGT && c->tmaps;
     const float s0 = c->h16s[0];
+    if (h16b && !k->side) {
+        HELM_CUDA_TRY(cudaStreamCreateWithFlags(&k->side, cudaStreamNonBlocking));
+        k->ev_upd = new cudaEvent_t[m]();
+        k->ev_giv = new cudaEvent_t[m]();
+        for (int j = 0; j < m; ++j) {
+            HELM_CUDA_TRY(cudaEventCreateWithFlags(&k->ev_upd[j], cudaEventDisableTiming));
+            HELM_CUDA_TRY(cudaEventCreateWithFlags(&k->ev_giv[j], cudaEventDisableTiming));
+        }
+    }
     if (h16b && !k->V16) {
         if (cudaMalloc(&k->V16, (size_t)(m + 1) * npts * 2 * sizeof(uint16_t)) != cudaSuccess ||
             cudaMalloc(&k->c16, (m + 1) * sizeof(double)) != cudaSuccess || cudaMalloc(&k->w16s, sizeof(double)) != cudaSuccess) {
@@ -1122,7 +1144,10 @@ helm_status gmres_run(helm_ctx* c, const double2* b_in, double2* x_in, helm_solv
                 if (h16b) {
                     float2* wv = k->V + npts;   // complex64 scratch: A z_j, orthogonalised into V16_{j+1}
                     uint16_t* Vj = k->V16 + (size_t)j * 2 * npts;
-                    if ((e = precond_h16_basis(c, Vj, z, k->c16, j, s)) != HELM_OK) return e;
+                    c->h16_join = j > 0 ? k->ev_giv[j - 1] : nullptr;   // the last pass reads c16[j]
+                    e = precond_h16_basis(c, Vj, z, k->c16, j, s);
+                    c->h16_join = nullptr;
+                    if (e != HELM_OK) return e;
                     if ((e = launch_stencil_f32(c, z, wv, nullptr, 0, s)) != HELM_OK) return e;
                     prof_begin(c, s, PROF_DOTS);
                     int nbd16 = k->NBd;
@@ -1149,13 +1174,15 @@ helm_status gmres_run(helm_ctx* c, const double2* b_in, double2* x_in, helm_solv
                     update16_kernel<<<ublocks, NT, 0, s>>>(k->V16, npts, j + 1, k->coef, wv, Vj + 2 * npts, k->w16s,
                                                            k->part, ld);
                     prof_end(c, s);
-                    prof_begin(c, s, PROF_SMALL);
-                    givens_kernel<<<1, 256, 0, s>>>(k->part, NB, ld, j, m, k->H, k->cs, k->sn, k->g, k->sigma, k->ctrl_d,
-                                                    k->w16s, k->c16);
-                    prof_end(c, s);
+                    // the Givens step on the side stream: the next step's first passes do not need it
+                    HELM_CUDA_TRY(cudaEventRecord(k->ev_upd[j], s));
+                    HELM_CUDA_TRY(cudaStreamWaitEvent(k->side, k->ev_upd[j], 0));
+                    givens_kernel<<<1, 256, 0, k->side>>>(k->part, NB, ld, j, m, k->H, k->cs, k->sn, k->g, k->sigma,
+                                                          k->ctrl_d, k->w16s, k->c16);
                     HELM_CUDA_TRY(cudaGetLastError());
-                    HELM_CUDA_TRY(cudaMemcpyAsync(&k->slots_h[j], k->ctrl_d, sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
-                    HELM_CUDA_TRY(cudaEventRecord(k->ev_slot[j], s));
+                    HELM_CUDA_TRY(cudaMemcpyAsync(&k->slots_h[j], k->ctrl_d, sizeof(Ctrl), cudaMemcpyDeviceToHost, k->side));
+                    HELM_CUDA_TRY(cudaEventRecord(k->ev_slot[j], k->side));
+                    HELM_CUDA_TRY(cudaEventRecord(k->ev_giv[j], k->side));
                     return HELM_OK;
                 }
                 if ((e = precond_apply(c, vj, z, k->sigma, j, s)) != HELM_OK) return e;
@@ -1194,11 +1221,17 @@ helm_status gmres_run(helm_ctx* c, const double2* b_in, double2* x_in, helm_solv
             }
             for (int j = 0; j < m; ++j) {
                 if (launched <= j) {
-                    if ((st = enqueue(j)) != HELM_OK) return st;
+                    if ((st = enqueue(j)) != HELM_OK) {
+                        if (k->side) cudaStreamSynchronize(k->side);
+                        return st;
+                    }
                     launched = j + 1;
                 }
                 if (j + 1 < m && its + 2 <= c->opt.max_iter && est_prev * kLookaheadDrop > thr) {
-                    if ((st = enqueue(j + 1)) != HELM_OK) return st;
+                    if ((st = enqueue(j + 1)) != HELM_OK) {
+                        if (k->side) cudaStreamSynchronize(k->side);
+                        return st;
+                    }
                     launched = j + 2;
                 }
                 HELM_CUDA_TRY(cudaEventSynchronize(k->ev_slot[j]));
@@ -1212,6 +1245,7 @@ helm_status gmres_run(helm_ctx* c, const double2* b_in, double2* x_in, helm_solv
                 if (!(cj.hnext > 0)) { breakdown = true; break; }
             }
             *k->ctrl_h = k->slots_h[kk - 1];
+            if (h16b) HELM_CUDA_TRY(cudaStreamWaitEvent(s, k->ev_giv[launched - 1], 0));   // every Givens step of the cycle
             if (launched > kk)
                 HELM_CUDA_TRY(cudaMemcpyAsync(k->ctrl_d, &k->slots_h[kk - 1], sizeof(Ctrl), cudaMemcpyHostToDevice, s));
             if (k->ctrl_h->flags & HELM_DEV_NAN) { result = HELM_ERR_NAN; break; }

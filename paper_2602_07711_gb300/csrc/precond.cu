@@ -114,6 +114,7 @@ helm_status h16_chain(helm_ctx* c, const uint16_t* In, uint16_t* T1, float2* z, 
     prof_end(c, s);
     if (st != HELM_OK) return st;
     prof_begin(c, s, PROF_XPASS);
+    if (c->h16_join) HELM_CUDA_TRY(cudaStreamWaitEvent(s, c->h16_join, 0));
     st = tc_xpass_h16(c, 1, T1, z, 0, alpha_last, adev, aidx, s, nb, 0, d ? d + 7 : nullptr, nullptr);
     prof_end(c, s);
     return st;
