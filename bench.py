@@ -116,7 +116,9 @@ def algorithmic(n, order, cycles_iters, real_medium=False, precision="tf32"):
     """Bytes (and flops) the kernels of one solve must move, by class (per-point byte counts of each kernel class).
     A medium without attenuation takes the real-medium matvec: k^2 as float, the order-6 fields as one
     real float4 per point.  The BF16 chain: x class = complex64 -> BF16 conversion (12 B/pt) and forward
-    pass (8) + inverse pass (BF16 in, complex64 out: 12); y passes 8 B/pt each; z-solve y and x in BF16 (8)."""
+    pass (8) + inverse pass (BF16 in, complex64 out: 12); y passes 8 B/pt each; z-solve y and x in BF16 (8).
+    FP16 (with the FP16 Krylov basis of the flexible solve): the forward x-pass reads the FP16 basis vector
+    itself, so the x class is 8 + 12 B/pt."""
     pts = n ** 3
     out = {}
     if real_medium:
@@ -126,7 +128,8 @@ def algorithmic(n, order, cycles_iters, real_medium=False, precision="tf32"):
     its = sum(cycles_iters)
     out["stencil"] = {"bytes": st_b * its, "launches": its}
     if precision in ("bf16", "fp16"):
-        out["xpass"] = {"bytes": 32 * pts * its, "flops": 8 * n * pts * 2 * its, "launches": 2 * its}
+        out["xpass"] = {"bytes": (20 if precision == "fp16" else 32) * pts * its, "flops": 8 * n * pts * 2 * its,
+                        "launches": 2 * its}
         out["ypass"] = {"bytes": 8 * pts * 2 * its, "flops": 8 * n * pts * 2 * its, "launches": 2 * its}
         out["zsolve"] = {"bytes": 8 * pts * its, "launches": its}
     else:
