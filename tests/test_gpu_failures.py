@@ -1,7 +1,8 @@
 """Failure detection through the C-ABI, in forms that fault, trap or hang no GPU: bad data injected on the
 host (a NaN in the right-hand side), a solve capped at max_iter, and the bounded mbarrier waits of the
-tensor-core transforms made to run out by a limit of one poll (the waits return, the kernels drain what
-they have in flight, free their tensor memory and report HELM_ERR_ITER_LIMIT; the context stays usable).
+tensor-core transforms (and, with the FP16 Krylov basis, of the inner products staged by bulk copies) made
+to run out by a limit of one poll (the waits return, the kernels drain what they have in flight, free
+their tensor memory and report HELM_ERR_ITER_LIMIT; the context stays usable).
 """
 import numpy as np
 import pytest
@@ -9,7 +10,7 @@ import pytest
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-from paper_2602_07711_gb300 import HELM_PREC_TF32, Solver, media
+from paper_2602_07711_gb300 import HELM_PREC_FP16, HELM_PREC_TF32, Solver, media
 
 HELM_ERR_NAN, HELM_ERR_NOT_CONVERGED, HELM_ERR_ITER_LIMIT = 6, 8, 9
 
@@ -56,20 +57,21 @@ def test_solve_capped_at_max_iter_returns_not_converged_with_the_last_iterate():
     S3.close()
 
 
-def test_expired_tensor_core_waits_return_iter_limit_and_leave_the_context_usable():
+@pytest.mark.parametrize("prec", [HELM_PREC_TF32, HELM_PREC_FP16])
+def test_expired_tensor_core_waits_return_iter_limit_and_leave_the_context_usable(prec):
     n = 64
     k2, f, k0 = media.bumps(n, 21, 22)
     fd = torch.from_numpy(f).cuda()
-    S = Solver((n, n, n), k2, k0, order=6, precision=HELM_PREC_TF32, flexible=True, rtol=1e-6, max_iter=4)
+    S = Solver((n, n, n), k2, k0, order=6, precision=prec, flexible=True, rtol=1e-6, max_iter=4)
     F = S.build_rhs(fd)
     S.set_wait_limit(1)        # one poll: the epilogue cannot see a whole tile finished in one poll
     _, info = S.solve(F, check=False)
     assert info.status == HELM_ERR_ITER_LIMIT
     # back to the default bound: the same context solves, and agrees with a fresh one
     S.set_wait_limit(0)
-    ref = Solver((n, n, n), k2, k0, order=6, precision=HELM_PREC_TF32, flexible=True, rtol=1e-6, max_iter=300)
+    ref = Solver((n, n, n), k2, k0, order=6, precision=prec, flexible=True, rtol=1e-6, max_iter=300)
     xr, ir = ref.solve(F)
-    S2 = Solver((n, n, n), k2, k0, order=6, precision=HELM_PREC_TF32, flexible=True, rtol=1e-6, max_iter=300)
+    S2 = Solver((n, n, n), k2, k0, order=6, precision=prec, flexible=True, rtol=1e-6, max_iter=300)
     S2.set_wait_limit(1)
     S2.solve(F, check=False)
     S2.set_wait_limit(0)
