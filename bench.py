@@ -243,13 +243,9 @@ def cycles_of(info, m):
 
 
 # ---- CPU oracle (reference arm and cpu_baseline) ------------------------------------------------
-def oracle_sample(n, order, m, iters=1):
-    """Time `iters` inner iterations of the oracle's GMRES on the full workload (the set-up of its
-    coefficient fields and eigendecompositions excluded).  Returns (Mpts*iter/s, seconds, cores)."""
-    import numpy as np
-
+def oracle_setup(n, order):
+    """The oracle's operator, EigT preconditioner and right-hand side for the full workload, and k0."""
     from oracle.eigt import EigT
-    from oracle.gmres import gmres
     from oracle.grid import Grid
     from oracle.operators import Operator
     from oracle.rhs import rhs6_sampled
@@ -259,10 +255,24 @@ def oracle_sample(n, order, m, iters=1):
     A = Operator(g, k2, k0, order)
     e = EigT(g, k0)
     F = rhs6_sampled(f, k2, A.dk2, True, g.h) if order == 6 else f
+    return A, e, F, k0
+
+
+def oracle_iterations(setup, n, m, iters=1):
+    """Time `iters` inner iterations of the oracle's GMRES on a prepared workload.  Returns
+    (Mpts*iter/s, seconds, cores)."""
+    from oracle.gmres import gmres
+    A, e, F, _ = setup
     t = time.perf_counter()
     _, info = gmres(A, e.apply_Minv, F, m=m, rtol=1e-30, max_it=iters)
     dt = time.perf_counter() - t
     return n ** 3 * info["iterations"] / dt / 1e6, dt, blas_threads()
+
+
+def oracle_sample(n, order, m, iters=1):
+    """Time `iters` inner iterations of the oracle's GMRES on the full workload (the set-up of its
+    coefficient fields and eigendecompositions excluded).  Returns (Mpts*iter/s, seconds, cores)."""
+    return oracle_iterations(oracle_setup(n, order), n, m, iters)
 
 
 def blas_threads():
@@ -279,21 +289,30 @@ def blas_threads():
 def run_reference(args, rank, world):
     if rank != 0:
         return
-    for _ in range(args.warmup if args.warmup < 1 else 1):
-        pass
+    # one set-up for all steps; one untimed warm-up iteration when W >= 1 (an iteration of the oracle takes
+    # tens of seconds, so W of them would not fit the few minutes the arm may take)
+    setup = oracle_setup(args.n, args.order)
+    warm = 1 if args.warmup >= 1 else 0
+    for _ in range(warm):
+        oracle_iterations(setup, args.n, args.restart, iters=1)
     vals, secs = [], []
     for _ in range(args.steps):
-        v, dt, cores = oracle_sample(args.n, args.order, args.restart, iters=1)
+        v, dt, cores = oracle_iterations(setup, args.n, args.restart, iters=1)
         vals.append(v)
         secs.append(dt)
     value = sum(vals) / len(vals)
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(secs) / len(secs),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
-            "data": "synthetic", "config": {"workload": "bumps20-n%d-order%d-seed3-angle4" % (args.n, args.order)},
+            "data": "synthetic",
+            "config": {"workload": "bumps20-n%d-order%d-seed3-angle4" % (args.n, args.order), "n": args.n,
+                       "order": args.order, "k0": setup[3], "precond": "EigT",
+                       "precision": "complex128", "krylov": "GMRES(%d)" % args.restart, "rtol": args.rtol,
+                       "parallelism": "single"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": "1 inner GMRES(30)+EigT iteration of the complex128 oracle per step on the "
-                                       "full %d^3 workload (set-up excluded)" % args.n},
+                                       "full %d^3 workload (set-up excluded, done once; %d untimed warm-up "
+                                       "iteration)" % (args.n, warm)},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
