@@ -483,6 +483,7 @@ def run_ours(args, rank, world, local):
                        "parallelism": "replicas" if world > 1 else "single"},
             "time_to_rtol_s": elapsed / args.steps,
             "iterations": [i.iterations for i in infos],
+            "cycles": cycles_of(infos[-1], args.restart),
             "relres_true": [i.relres_true for i in infos],
             "status": [i.status for i in infos],
             "setup_s": setup_s,
