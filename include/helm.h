@@ -70,10 +70,10 @@ typedef struct {
  * limits as PFFT. */
 enum { HELM_PRECOND_NONE = 0, HELM_PRECOND_EIGT = 1, HELM_PRECOND_PFFT = 2, HELM_PRECOND_FFT2 = 3 };
 
-/* Arithmetic of the eigenvector transforms (EigT steps 2 and 4).  The stencil and the Krylov vectors are
- * complex64 in every mode, the z-solves compute in FP32; the Hessenberg/Givens update and the 1D eigensetup
- * are FP64, the true residual, the right-hand side and the iterate double-float (about 44 bits) in every
- * mode.
+/* Arithmetic of the eigenvector transforms (EigT steps 2 and 4).  The stencil is complex64 in every mode and
+ * the Krylov vectors too, except in flexible single solves with HELM_PREC_FP16 (below); the z-solves compute
+ * in FP32; the Hessenberg/Givens update and the 1D eigensetup are FP64, the true residual, the right-hand
+ * side and the iterate double-float (about 44 bits) in every mode.
  *   HELM_PREC_FP32    complex64 on the CUDA cores (FFMA), the "plain complex64" method
  *   HELM_PREC_TF32    tcgen05 tensor cores, TF32 operands, FP32 accumulation in TMEM (one product); needs
  *                     even N_x.  Relative error of a transform about 8e-4.
@@ -89,10 +89,13 @@ enum { HELM_PRECOND_NONE = 0, HELM_PRECOND_EIGT = 1, HELM_PRECOND_PFFT = 2, HELM
  *                     TF32); needs N_x a multiple of 4; in helm_gmres_solve_batched only with flexible GMRES
  *                     (HELM_ERR_UNSUPPORTED otherwise).
  *   HELM_PREC_FP16    the same chain with FP16 operands and grids (TF32's 11-bit significand, so about
- *                     TF32's accuracy): every stored grid is scaled by a power of two fixed at set-up from
- *                     bounds that rule out overflow for any input (spectral norms of the eigenvector
- *                     matrices, kappa(V_z) / min |lambda| for the z-solves); the last pass undoes them.
- *                     Same limits as BF16, and k0z2 (helm_setup) must be constant.                      */
+ *                     TF32's accuracy): every stored grid carries a power-of-two scale that rules out
+ *                     overflow for any input, from operator bounds computed at set-up (spectral norms of
+ *                     the eigenvector matrices, kappa(V_z) / min |lambda| for the z-solves) times, after the
+ *                     first pass, the Frobenius norm the producing pass measured; the last pass undoes
+ *                     them.  Flexible single solves with EigT (one Gram-Schmidt pass, no learned
+ *                     correction) also keep the Krylov basis in FP16, one scale per vector.  Same limits as
+ *                     BF16, and k0z2 (helm_setup) must be constant.                                     */
 enum { HELM_PREC_FP32 = 0, HELM_PREC_TF32 = 1, HELM_PREC_TF32X3 = 2, HELM_PREC_BF16 = 3, HELM_PREC_FP16 = 4 };
 
 typedef struct {
