@@ -3,7 +3,7 @@
 Every operand of the x- and y-pass MMAs is a 16-bit value and the grids between the passes are stored in
 16 bits (the z-solve reads and writes them and computes in FP32).  BF16 keeps an 8-bit significand (round
 to nearest even: relative error up to 2^-9), FP16 TF32's 11 bits (up to 2^-11) inside power-of-two stage
-scales fixed at set-up from bounds that rule out overflow.  The chain carries about six such roundings
+scales that rule out overflow (operator bounds from set-up times the norms the passes measure).  The chain carries about six such roundings
 where the TF32 chain carries four TF32 truncations (up to 2^-10 each).  The bounds are fixed, at about 2.5x
 the errors measured on a GB300 (recorded beside them); a transposed basis or one shifted by a column gives
 relative errors near 1.4.
