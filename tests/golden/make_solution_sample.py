@@ -3,7 +3,7 @@
 Problem: the sixth-order scheme (Eq. scheme6) on the staggered 256^3 grid of the unit cube (Sec. 5.2
 grid), the 20-bump medium media.bumps(256, 3, 4) (~10 points per wavelength), its modified right-hand
 side from the sampled f, solved by the oracle's right-preconditioned GMRES(30) with EigT (Sec. 4.1) to
-rel-res 1e-12.  The solve takes about an hour on eight host cores and 12 GB of memory, so the test suite
+rel-res 1e-12.  The solve took 1306 s (about 22 minutes) on eight host cores and 12 GB of memory, so the test suite
 reads its result from the text file this script writes instead of running it:
 
     python tests/golden/make_solution_sample.py            # writes bumps256_order6_solution_sample.txt

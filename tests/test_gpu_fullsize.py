@@ -3,10 +3,10 @@ sixth order, the 20-bump medium of seeds 3/4 (~10 points per wavelength), FP16 E
 and TF32 EigT, FGMRES(30), rtol 1e-6.  The FP64 oracle is evaluated on the whole field (each evaluation
 takes seconds on the host cores): the matvec element by element, the forward transform (a TF32 pass in both
 modes) and the preconditioner in the GPU's own eigenbasis within fixed bounds (TF32 measured 8.3e-4 and
-1.7e-3 relative in the 2-norm at this size; the FP16 chain's bound is that of tests/test_gpu_h16.py), the
-right-hand side, and the FP64 residual of the GPU's solution.  The solution itself is compared with the
-oracle's, solved to rel-res 1e-12, at 4096 seeded points (tests/golden/make_solution_sample.py writes them;
-the oracle's solve takes about an hour on eight host cores).
+1.7e-3 relative in the 2-norm at this size, the FP16 chain 1.0e-3; PRECOND_BOUNDS below), the right-hand
+side, and the FP64 residual of the GPU's solution.  The solution itself is compared with the oracle's,
+solved to rel-res 1e-12, at 4096 seeded points (tests/golden/make_solution_sample.py writes them; the
+oracle's solve took 1306 s, about 22 minutes, on eight host cores).
 """
 import os
 
