@@ -86,3 +86,16 @@ def test_closure_entry_points_reject_null_contexts_without_gpu_work(libpath):
     assert L.helm_closure_face_count(None) == 0
     assert L.helm_build_rhs_fields(None, None, None, None) == 1
     assert L.helm_closure_rhs(None, None, None, None, None) == 1
+
+
+def test_missing_library_raises_instead_of_falling_back(monkeypatch, tmp_path):
+    """Without libhelm.so every entry point raises: there is no CPU or other fallback on the product path."""
+    import numpy as np
+
+    from paper_2602_07711_gb300 import helm
+    monkeypatch.setattr(helm, "library_path", str(tmp_path / "libhelm.so"))
+    monkeypatch.setattr(helm, "_lib", None)
+    with pytest.raises(RuntimeError, match="libhelm.so not found"):
+        helm.lib()
+    with pytest.raises(RuntimeError, match="libhelm.so not found"):
+        helm.Solver((8, 8, 8), np.ones((8, 8, 8), complex), 1.0, order=4)
