@@ -492,6 +492,11 @@ def run_ours(args, rank, world, local):
             "kernels_note": "per-class CUDA-event times over %d profiled steps before the timed region; in the timed "
                             "region only the %s launches carry events (roofline)" % (args.steps, dominant),
             "gpu_launches": launches,
+            "gpu_launches_note": "the library's classified kernel launches (its per-class profiler count over the "
+                                 "profiled steps, which launch what the timed steps launch); the Givens step on "
+                                 "the second stream (one per inner iteration) and the conversion and zero-fill "
+                                 "launches of each solve are not classified and not counted (at 256^3: 247 of "
+                                 "the 279 launches of a solve)",
             "clocks": clk,
             "e2e": e2e,
             "plain_eigt": plain,
