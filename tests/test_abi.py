@@ -99,3 +99,37 @@ def test_missing_library_raises_instead_of_falling_back(monkeypatch, tmp_path):
         helm.lib()
     with pytest.raises(RuntimeError, match="libhelm.so not found"):
         helm.Solver((8, 8, 8), np.ones((8, 8, 8), complex), 1.0, order=4)
+
+
+def test_header_is_c99_and_a_c_program_links_and_calls_the_library(libpath, tmp_path):
+    """include/helm.h compiles as strict C99 and a C program links against libhelm.so and calls it (only
+    entry points that do no GPU work: the version, status strings, and a rejected set-up)."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "abi.c"
+    src.write_text(r'''
+#include <stdio.h>
+#include <string.h>
+#include "helm.h"
+int main(void) {
+    helm_ctx* ctx = (helm_ctx*)&ctx;
+    helm_status st = helm_setup(NULL, NULL, 1.0, NULL, NULL, NULL, &ctx);
+    if (st != HELM_ERR_ARG || ctx != NULL) return 2;
+    if (strncmp(helm_version(), "helm-gb300", 10) != 0) return 3;
+    if (strcmp(helm_status_str(HELM_OK), helm_status_str(HELM_ERR_ARG)) == 0) return 4;
+    printf("%s\n", helm_status_str(st));
+    return 0;
+}
+''')
+    exe = tmp_path / "abi"
+    libdir = os.path.dirname(libpath)
+    r = subprocess.run([cc, "-std=c99", "-Wall", "-Wextra", "-Werror", "-pedantic", "-I", os.path.join(ROOT, "include"),
+                        str(src), "-o", str(exe), "-L", libdir, "-lhelm", "-Wl,-rpath," + libdir],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=60)
+    assert r.returncode == 0, (r.returncode, r.stdout, r.stderr)
+    assert r.stdout.strip()
