@@ -539,7 +539,9 @@ extern "C" {
 size_t helm_net_num_params(const helm_net* n) { return n ? n->nparam : 0; }
 
 helm_status helm_net_create(int width, unsigned long long seed, helm_net** out) {
-    if (!out || width < 1 || width > 64) return HELM_ERR_ARG;
+    if (!out) return HELM_ERR_ARG;
+    *out = nullptr;   // on every error return
+    if (width < 1 || width > 64) return HELM_ERR_ARG;
     helm_net* n = new helm_net();
     n->c = width;
     const int c = width;

@@ -133,3 +133,32 @@ int main(void) {
     r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=60)
     assert r.returncode == 0, (r.returncode, r.stdout, r.stderr)
     assert r.stdout.strip()
+
+
+def test_every_entry_point_rejects_a_null_context_without_gpu_work(libpath):
+    """A NULL context (or net, or batch) is HELM_ERR_ARG for every call that takes one, constructors given
+    bad arguments return HELM_ERR_ARG with *out = NULL, size queries return 0 and destroy(NULL) is a no-op."""
+    from paper_2602_07711_gb300 import helm
+    C = ctypes
+    L = helm.lib()
+    skip = {"helm_net_create", "helm_batch_create", "helm_gmres_solve_batched", "helm_setup", "helm_autotune"}
+    checked = 0
+    for name, (rt, args) in helm._SIGS.items():
+        if rt is not C.c_int or not args or args[0] is not C.c_void_p or name in skip:
+            continue
+        vals = [0 if a in (C.c_int, C.c_uint, C.c_longlong, C.c_size_t) else 0.0 if a in (C.c_float, C.c_double)
+                else None for a in args]
+        assert getattr(L, name)(*vals) == 1, name
+        checked += 1
+    assert checked >= 25
+    h = C.c_void_p(1)
+    assert L.helm_net_create(0, 0, C.byref(h)) == 1 and h.value is None
+    assert L.helm_net_create(8, 0, None) == 1
+    h = C.c_void_p(1)
+    assert L.helm_batch_create(None, 0, None, None, 0, None, C.byref(h)) == 1 and h.value is None
+    assert L.helm_gmres_solve_batched(None, 0, None, None, 0, None, None) == 1
+    assert L.helm_autotune(None, None, None, None, None) == 1
+    assert L.helm_closure_face_count(None) == 0 and L.helm_net_num_params(None) == 0
+    L.helm_destroy(None)
+    L.helm_batch_destroy(None)
+    L.helm_net_destroy(None)
