@@ -126,7 +126,6 @@ helm_status h16_chain(helm_ctx* c, const uint16_t* In, uint16_t* T1, float2* z, 
 // 16-bit grids live in the halves of the context's scratch vector (T0, T1); the z-solve keeps its FP32
 // forward values in z, which is free until the last pass, so r may alias z.
 helm_status precond_h16(helm_ctx* c, const float2* r, float2* z, const double* sigma, int sidx, cudaStream_t s) {
-    helm_status st;
     const size_t n = c->npts;
     const int H = c->opt.precision == HELM_PREC_FP16 ? 2 : 1;
     uint16_t* T0 = reinterpret_cast<uint16_t*>(c->tmp);

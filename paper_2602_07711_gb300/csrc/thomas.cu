@@ -45,10 +45,6 @@ __device__ inline float2 crcp(float2 b) {
     return make_float2(b.x * r, -b.y * r);
 }
 
-__device__ inline void note_pivot(float2 d, unsigned* status) {
-    if (!(fabsf(d.x) + fabsf(d.y) > 1e-30f)) atomicOr(status, (unsigned)HELM_DEV_PIVOT);
-}
-
 // The steps of the factorised solve, every operation rounded as written (explicit fma/mul/add, so that no
 // kernel contracts differently): the set-up factors, the forward and backward sweeps over stored factors
 // and the sweeps that recompute the factors all produce the same bits.
