@@ -7,7 +7,6 @@ The k^2 f and f_d parts come from Delta_h(k^2 U) of Eq. scheme6, which do not in
 Our reading: "nabla^4 f" of Eq. scheme6 is the sum of pure fourth derivatives; with this
 reading (and only with it) the scheme has sixth-order truncation error.
 """
-import numpy as np
 
 from .operators import pad_coef
 

@@ -6,7 +6,6 @@ If the library has not been built, every entry point raises instead of falling b
 """
 import ctypes as C
 import os
-import time
 
 import numpy as np
 

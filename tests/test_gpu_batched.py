@@ -4,14 +4,13 @@ solve of the same pair gives: the same kernels run on the same data in the same 
 are equal and the solutions agree to rounding; the single solve itself is checked against the oracle in
 test_gpu_parity.py, and the true residual of every batched solution is checked here as well.
 """
-import numpy as np
 import pytest
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-from paper_2602_07711_gb300 import (HELM_PREC_FP32, HELM_PREC_TF32, HELM_PRECOND_PFFT, Batch, HelmError, Solver,
-                                    helm, media, solve_batched)
+from paper_2602_07711_gb300 import (HELM_PREC_FP32, HELM_PREC_TF32, HELM_PRECOND_PFFT, Batch, Solver, helm, media,
+                                    solve_batched)
 
 
 def _problem(n, seed, ppw, nrhs, order, precision, flexible, restart=30, max_iter=300, rtol=1e-6):

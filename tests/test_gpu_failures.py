@@ -4,7 +4,6 @@ tensor-core transforms (and, with the FP16 Krylov basis, of the inner products s
 to run out by a limit of one poll (the waits return, the kernels drain what they have in flight, free
 their tensor memory and report HELM_ERR_ITER_LIMIT; the context stays usable).
 """
-import numpy as np
 import pytest
 
 torch = pytest.importorskip("torch")

@@ -6,7 +6,6 @@ and accumulate in float32.  Seven stored tensors lie between input and output, s
 relative error of a few times 2^-9 in the 2-norm: the bound used is 2e-2 (4e-2 for gradients, which pass
 through the stored activations twice).  A wrong index, tap flip or mask gives errors of order 1.
 """
-import math
 
 import numpy as np
 import pytest
@@ -17,7 +16,7 @@ pytestmark = pytest.mark.gpu
 from oracle import learned as OL
 from oracle.eigt import EigT
 from oracle.grid import Grid
-from paper_2602_07711_gb300 import HELM_PREC_TF32, Net, Solver, helm, learned, media
+from paper_2602_07711_gb300 import HELM_PREC_TF32, Net, Solver, helm, learned
 
 
 def bf16_round(a):

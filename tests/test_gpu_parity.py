@@ -25,7 +25,7 @@ from oracle.grid import Grid
 from oracle.operators import Operator, derived_k2_fields
 from oracle.rhs import rhs4_sampled, rhs6_sampled
 from oracle.tridiag import thomas
-from paper_2602_07711_gb300 import HELM_PREC_FP32, HELM_PRECOND_EIGT, Solver, media
+from paper_2602_07711_gb300 import HELM_PREC_FP32, Solver, media
 
 
 def _dev(a, dtype=torch.complex128):

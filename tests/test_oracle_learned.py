@@ -1,7 +1,6 @@
 """Pins of the learned-correction oracle (no GPU): the hand-written backward agrees with central finite
 differences of the loss in float64, and the convolution agrees with a direct sum."""
 import numpy as np
-import pytest
 
 from oracle import learned as L
 

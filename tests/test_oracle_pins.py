@@ -18,9 +18,9 @@ from oracle.eigt import EigT
 from oracle.gmres import gmres
 from oracle.grid import Grid, gamma_two_point
 from oracle.model1d import d_r, matrices
-from oracle.operators import Operator, apply_A4, apply_A6, derived_k2_fields, pad_coef
+from oracle.operators import Operator, apply_A4, apply_A6, derived_k2_fields
 from oracle.pfft import PFFT
-from oracle.rhs import f_derivative_fields, rhs4_padded, rhs6, rhs6_sampled
+from oracle.rhs import rhs4_padded, rhs6, rhs6_sampled
 from oracle.tridiag import thomas
 from paper_tables import high_order_rows, printed_half_unit
 
