@@ -125,8 +125,8 @@ typedef struct {
 enum { HELM_C64 = 0, HELM_C128 = 1 };
 
 /* helm_setup - build a solver context.
- *   grid     grid of the problem (Sec. 2.1 / Sec. 5.2); every N >= 4, N_z <= 512, N_x N_y N_z even;
- *            N_x even for the tensor-core modes.
+ *   grid     grid of the problem (Sec. 2.1 / Sec. 5.2); every N >= 4, N_z <= 512, N_x N_y N_z even and
+ *            below 2^31; N_x even for the tensor-core modes.
  *   k2       k^2(x,y,z) samples, complex128, N_x*N_y*N_z, host or device (Eq. problem).
  *   k0       background wavenumber of the ABC and of the preconditioner, real (Eq. background).
  *   k0z2     optional depth profile k0^2(z_l), N_z doubles (host), for K_z of Sec. 4.1; NULL = k0^2.

@@ -85,6 +85,8 @@ helm_status helm_setup(const helm_grid* grid, const void* k2, double k0, const d
     // the Krylov kernels move two points per 16-byte access: the point count must be even
     if (((size_t)grid->nx * grid->ny * grid->nz) % 2 != 0) return HELM_ERR_UNSUPPORTED;
     if (grid->nz > 512) return HELM_ERR_UNSUPPORTED;
+    // point indices fit a signed 32-bit integer (grid offsets themselves are size_t)
+    if ((size_t)grid->nx * grid->ny * grid->nz >= ((size_t)1 << 31)) return HELM_ERR_UNSUPPORTED;
     cudaStream_t s = (cudaStream_t)stream;
     helm_ctx* c = new helm_ctx();
     cudaGetDevice(&c->device);

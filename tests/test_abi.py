@@ -162,3 +162,15 @@ def test_every_entry_point_rejects_a_null_context_without_gpu_work(libpath):
     L.helm_destroy(None)
     L.helm_batch_destroy(None)
     L.helm_net_destroy(None)
+
+
+def test_setup_rejects_grids_of_2_to_the_31_points_without_gpu_work(libpath):
+    from paper_2602_07711_gb300 import helm
+    import numpy as np
+    L = helm.lib()
+    ctx = ctypes.c_void_p(1)
+    g = helm.helm_grid(4096, 4096, 128, 1.0, 1.0, 1.0, 1)   # 2^31 points: rejected before any CUDA call
+    o = helm.helm_options(4, 1, 0, 30, 100, 1e-6, 0, 0)
+    k2 = np.zeros(8, np.complex128)                          # not read
+    assert L.helm_setup(ctypes.byref(g), k2.ctypes.data, 1.0, None, ctypes.byref(o), None, ctypes.byref(ctx)) == 10
+    assert ctx.value is None
